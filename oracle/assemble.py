@@ -1,0 +1,403 @@
+"""Eqs. (A), (Q), (prec) and the right-hand side (oracle; test infrastructure).
+
+Readings of the paper used here:
+* Eq. (Q) is printed as det(J) J^{-T} K J^{-1}; the chain rule with
+  J_ij = d x_i / d zeta_j gives grad_x u = J^{-T} grad_zeta u, hence
+  Q = |det J| J^{-1} K J^{-T}. This module uses the latter (K = kappa I).
+* The scalar index of Eq. (Vh) makes direction 1 the fastest; P is built by
+  that index: the 1D factor K_k (or M_k) acts on i_k.
+* Quadrature: (p+1)-point Gauss per element per direction (the paper's rule
+  is not stated); exact for the 1D pencils.
+* The stiffness matrix is held as a (2p+1)^d offset ("stencil") array
+  S[o, row], o = sum_k (delta_k + p) (2p+1)^(k-1), row = sum_k i_k n^(k-1),
+  entry A[row, row + delta]; couplings that leave the index box are 0.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import spline
+
+
+class Geometry:
+    """Spline map F(zeta) = sum_i C_i B_i(zeta) (Section 2.1)."""
+
+    def __init__(self, ctrl, knots, p):
+        self.ctrl = np.asarray(ctrl, dtype=np.float64)    # [c][i_d]..[i_1]
+        self.knots = [np.asarray(k, dtype=np.float64) for k in knots]
+        self.p = int(p)
+        self.d = len(self.knots)
+
+    def eval_grid(self, pts):
+        """F and its Jacobian on the tensor grid of 1D point sets pts[k]
+        (direction k). Returns F[c, q_d, ..., q_1] and J[q_d, ..., q_1, c, j]
+        with J_cj = dF_c / dzeta_j."""
+        d = self.d
+        vals, ders, lo = [], [], []
+        for k in range(d):
+            V = spline.basis_table(self.knots[k], self.p, pts[k])
+            D = spline.basis_table(self.knots[k], self.p, pts[k], deriv=True)
+            nz = np.nonzero(np.any(V != 0, axis=0) | np.any(D != 0, axis=0))[0]
+            a, b = nz.min(), nz.max() + 1
+            vals.append(V[:, a:b]); ders.append(D[:, a:b]); lo.append((a, b))
+        # restrict the net to the control points that can be nonzero
+        sl = (slice(None),) + tuple(slice(*lo[k]) for k in reversed(range(d)))
+        C = self.ctrl[sl]
+
+        def contract(tables):
+            # tables[k] acts on direction k; array axes are [c, dir d, ..., dir 1]
+            T = C
+            for k in range(d):
+                ax = d - k  # axis of direction k in T
+                T = np.moveaxis(np.tensordot(T, tables[k], axes=([ax], [1])), -1, ax)
+            return T
+
+        F = contract(vals)
+        J = np.empty(F.shape[1:] + (d, d))
+        for j in range(d):
+            tabs = [ders[k] if k == j else vals[k] for k in range(d)]
+            Tj = contract(tabs)
+            for c in range(d):
+                J[..., c, j] = Tj[c]
+        return F, J
+
+
+def q_matrix(J, kappa=1.0):
+    """Q = kappa |det J| J^{-1} J^{-T} at every point (reading of Eq. (Q));
+    also returns det J."""
+    det = np.linalg.det(J)
+    Jinv = np.linalg.inv(J)
+    Q = kappa * np.abs(det)[..., None, None] * (Jinv @ np.swapaxes(Jinv, -1, -2))
+    return Q, det
+
+
+class Discretization:
+    """Degree-p tensor B-spline space with homogeneous Dirichlet conditions on
+    a spline-mapped patch (Eqs. (Vh), (A))."""
+
+    def __init__(self, knots, p, geometry: Geometry, kappa=1.0, nq=None):
+        self.knots = [np.asarray(k, dtype=np.float64) for k in knots]
+        self.p = int(p)
+        self.d = len(self.knots)
+        self.geo = geometry
+        self.kappa = float(kappa)
+        self.nq = self.p + 1 if nq is None else int(nq)
+        self.m = [len(k) - self.p - 1 for k in self.knots]   # 1D space dims
+        self.n = [mk - 2 for mk in self.m]                   # Dirichlet dofs
+        self.N = int(np.prod(self.n))
+        self.qz, self.qw, self.spans = [], [], []
+        for k in self.knots:
+            z, w, s = spline.gauss_points(k, self.nq)
+            self.qz.append(z); self.qw.append(w); self.spans.append(s)
+        self.nel = [len(s) for s in self.spans]
+
+    @classmethod
+    def from_problem(cls, prob, nq=None):
+        geo = Geometry(prob.ctrl, prob.knots, prob.p)
+        return cls(prob.knots, prob.p, geo, prob.kappa, nq)
+
+    # ---- 1D pencils (Section 3) -------------------------------------------
+    def pencil(self, k, full=False):
+        """(K_k, M_k): 1D stiffness and mass matrices of direction k by
+        Gauss quadrature; Dirichlet rows/columns removed unless full."""
+        z, w = self.qz[k].ravel(), self.qw[k].ravel()
+        V = spline.basis_table(self.knots[k], self.p, z)
+        D = spline.basis_table(self.knots[k], self.p, z, deriv=True)
+        M = (V * w[:, None]).T @ V
+        K = (D * w[:, None]).T @ D
+        if not full:
+            M, K = M[1:-1, 1:-1], K[1:-1, 1:-1]
+        return K, M
+
+    # ---- element-by-element quantities ------------------------------------
+    def _box(self, elo, ehi):
+        """Quadrature data on a box of elements [elo_k, ehi_k) per direction:
+        local basis values/derivatives, weights, Q and det J on the box grid."""
+        p, nq, d = self.p, self.nq, self.d
+        V, D, W, I0, pts = [], [], [], [], []
+        for k in range(d):
+            z = self.qz[k][elo[k]:ehi[k]]
+            s = self.spans[k][elo[k]:ehi[k]]
+            Vt = spline.basis_table(self.knots[k], p, z.ravel()).reshape(z.shape + (-1,))
+            Dt = spline.basis_table(self.knots[k], p, z.ravel(), deriv=True).reshape(z.shape + (-1,))
+            cols = s[:, None] - p + np.arange(p + 1)[None, :]       # full indices
+            V.append(np.take_along_axis(Vt, cols[:, None, :].repeat(nq, 1), 2))
+            D.append(np.take_along_axis(Dt, cols[:, None, :].repeat(nq, 1), 2))
+            W.append(self.qw[k][elo[k]:ehi[k]])
+            I0.append(s - p)
+            pts.append(z.ravel())
+        F, J = self.geo.eval_grid(pts)
+        Q, det = q_matrix(J, self.kappa)
+        return dict(V=V, D=D, W=W, I0=I0, F=F, Q=Q, det=det)
+
+    @staticmethod
+    def _tprod(factors):
+        """Tensor product over directions of per-element factors f_k[E, g, a]
+        -> [E, G, A] with direction 1 fastest in G and A."""
+        T = np.ones((factors[0].shape[0], 1, 1))
+        for f in reversed(factors):          # slowest direction first
+            E, G, A = T.shape
+            T = (T[:, :, None, :, None] * f[:, None, :, None, :]).reshape(
+                E, G * f.shape[1], A * f.shape[2])
+        return T
+
+    def _element_lists(self, box, elo, ehi):
+        d = self.d
+        ranges = [np.arange(ehi[k] - elo[k]) for k in range(d)]
+        grid = np.meshgrid(*ranges[::-1], indexing="ij")
+        return [grid[d - 1 - k].ravel() for k in range(d)]   # local element idx per dir
+
+    def _gather_grid(self, arr, eidx):
+        """Values of a box-grid array arr[q_d..q_1, ...] at each element's
+        own quadrature points -> [E, G, ...] (G with direction 1 fastest)."""
+        d, nq = self.d, self.nq
+        g = np.arange(nq)
+        idx = []
+        for k in reversed(range(d)):   # slowest direction first
+            gi = eidx[k][:, None] * nq + g[None, :]
+            shape = [len(eidx[k])] + [1] * d
+            shape[1 + (d - 1 - k)] = nq
+            idx.append(gi.reshape(shape))
+        out = arr[tuple(idx)]
+        return out.reshape((len(eidx[0]), nq ** d) + arr.shape[d:])
+
+    def element_matrices(self, box, eidx):
+        """Local matrices L[e, a, b] = sum_q w_q grad B_a^T Q grad B_b
+        (Eq. (A)) for the elements eidx of a box."""
+        d = self.d
+        V = [box["V"][k][eidx[k]] for k in range(d)]
+        D = [box["D"][k][eidx[k]] for k in range(d)]
+        W = self._tprod([box["W"][k][eidx[k]][:, :, None] for k in range(d)])[:, :, 0]
+        G = np.stack([self._tprod([D[k] if k == r else V[k] for k in range(d)])
+                      for r in range(d)], axis=-1)            # [E, G, A, r]
+        Qe = self._gather_grid(box["Q"], eidx)                # [E, G, r, s]
+        H = np.einsum("eg,egrs,egbs->egbr", W, Qe, G)
+        E, Gn, A, _ = G.shape
+        L = np.matmul(G.transpose(0, 2, 1, 3).reshape(E, A, Gn * d),
+                      H.transpose(0, 1, 3, 2).reshape(E, Gn * d, A))
+        return L
+
+    def _local_full_indices(self, box, eidx):
+        """Full (Dirichlet-included) multi-index of each local function:
+        list over directions of [E, A] arrays."""
+        d, p = self.d, self.p
+        out = []
+        for k in range(d):
+            base = box["I0"][k][eidx[k]]                     # [E]
+            ak = np.arange(p + 1)
+            shape = [1] * d
+            shape[d - 1 - k] = p + 1
+            loc = np.broadcast_to(ak.reshape(shape), [p + 1] * d).ravel()
+            out.append(base[:, None] + loc[None, :])
+        return out
+
+    # ---- stiffness matrix ---------------------------------------------------
+    def n_offsets(self):
+        return (2 * self.p + 1) ** self.d
+
+    def offset_index(self, delta):
+        """o = sum_k (delta_k + p) (2p+1)^(k-1) for a list/array of deltas."""
+        w = 2 * self.p + 1
+        return sum((np.asarray(delta[k]) + self.p) * w ** k for k in range(self.d))
+
+    def row_index(self, i):
+        """Scalar Dirichlet index of Eq. (Vh) (0-based), direction 1 fastest."""
+        r, s = 0, 1
+        for k in range(self.d):
+            r = r + np.asarray(i[k]) * s
+            s *= self.n[k]
+        return r
+
+    def assemble_stencil(self, chunk_planes=1):
+        """Full stiffness matrix A as the offset array S[o, row]."""
+        d, p = self.d, self.p
+        S = np.zeros(self.n_offsets() * self.N)
+        last = d - 1
+        for e0 in range(0, self.nel[last], chunk_planes):
+            elo = [0] * d
+            ehi = list(self.nel)
+            elo[last], ehi[last] = e0, min(e0 + chunk_planes, self.nel[last])
+            self._scatter_box(S, elo, ehi, rows=None)
+        return S.reshape(self.n_offsets(), self.N)
+
+    def _scatter_box(self, S, elo, ehi, rows=None):
+        d = self.d
+        box = self._box(elo, ehi)
+        eidx = self._element_lists(box, elo, ehi)
+        L = self.element_matrices(box, eidx)
+        I = self._local_full_indices(box, eidx)               # full indices
+        A = L.shape[1]
+        valid_r = np.ones(L.shape[:2], bool)
+        for k in range(d):
+            valid_r &= (I[k] >= 1) & (I[k] <= self.m[k] - 2)
+        row = self.row_index([I[k] - 1 for k in range(d)])      # [E, A]
+        # pairs (a, b): row from a, column offset from b - a
+        rowp = np.broadcast_to(row[:, :, None], L.shape)
+        valid = valid_r[:, :, None] & valid_r[:, None, :]
+        delta = [I[k][:, None, :] - I[k][:, :, None] for k in range(d)]
+        o = self.offset_index(delta)
+        if rows is not None:
+            valid &= np.isin(rowp, rows)
+        flat = (o * self.N + rowp)[valid]
+        if rows is not None:
+            np.add.at(S, flat, L[valid])
+        else:
+            S += np.bincount(flat, weights=L[valid], minlength=S.size)
+        return S
+
+    def assemble_rows(self, rows_multi):
+        """Rows of A for the given Dirichlet multi-indices (list of tuples,
+        direction 1 first), computed from the elements of each row's support
+        only. Returns S_rows[len(rows), n_offsets]."""
+        d, p = self.d, self.p
+        out = np.zeros((len(rows_multi), self.n_offsets()))
+        for r, i in enumerate(rows_multi):
+            # full index I_k = i_k + 1; support elements s - p <= I <= s
+            elo, ehi = [], []
+            for k in range(d):
+                I = i[k] + 1
+                es = [e for e, s in enumerate(self.spans[k]) if s - p <= I <= s]
+                elo.append(min(es)); ehi.append(max(es) + 1)
+            S = np.zeros(self.n_offsets() * self.N)
+            row = int(self.row_index(i))
+            self._scatter_box(S, elo, ehi, rows=np.array([row]))
+            out[r] = S.reshape(self.n_offsets(), self.N)[:, row]
+        return out
+
+    # ---- right-hand side ----------------------------------------------------
+    def assemble_rhs(self, f, chunk_planes=4):
+        """b_i = int f(F(zeta)) B_i(zeta) |det J| dzeta with f a callable of
+        the physical coordinates (x_1, ..., x_d)."""
+        d = self.d
+        b = np.zeros(self.N)
+        last = d - 1
+        for e0 in range(0, self.nel[last], chunk_planes):
+            elo = [0] * d
+            ehi = list(self.nel)
+            elo[last], ehi[last] = e0, min(e0 + chunk_planes, self.nel[last])
+            box = self._box(elo, ehi)
+            eidx = self._element_lists(box, elo, ehi)
+            V = [box["V"][k][eidx[k]] for k in range(d)]
+            W = self._tprod([box["W"][k][eidx[k]][:, :, None] for k in range(d)])[:, :, 0]
+            Bh = self._tprod(V)                                   # [E, G, A]
+            X = [self._gather_grid(box["F"][c], eidx) for c in range(d)]
+            det = self._gather_grid(box["det"], eidx)
+            fv = f(*X) * np.abs(det) * W                          # [E, G]
+            loc = np.einsum("eg,ega->ea", fv, Bh)
+            I = self._local_full_indices(box, eidx)
+            valid = np.ones(loc.shape, bool)
+            for k in range(d):
+                valid &= (I[k] >= 1) & (I[k] <= self.m[k] - 2)
+            row = self.row_index([I[k] - 1 for k in range(d)])
+            b += np.bincount(row[valid], weights=loc[valid], minlength=self.N)
+        return b
+
+    # ---- discretization error ------------------------------------------------
+    def l2_error(self, u_dofs, u_exact, extra_q=2, chunk_planes=4):
+        """|| u - u_h ||_{L2(Omega)} with u_h = sum_i u_i B_i (Dirichlet dofs
+        zero), by a Gauss rule with p+1+extra_q points per direction."""
+        fine = Discretization(self.knots, self.p, self.geo, self.kappa, self.p + 1 + extra_q)
+        d = self.d
+        U = np.zeros(tuple(reversed(self.m)))
+        U[tuple(slice(1, -1) for _ in range(d))] = np.asarray(u_dofs).reshape(tuple(reversed(self.n)))
+        err2 = 0.0
+        last = d - 1
+        for e0 in range(0, fine.nel[last], chunk_planes):
+            elo = [0] * d
+            ehi = list(fine.nel)
+            elo[last], ehi[last] = e0, min(e0 + chunk_planes, fine.nel[last])
+            box = fine._box(elo, ehi)
+            eidx = fine._element_lists(box, elo, ehi)
+            V = [box["V"][k][eidx[k]] for k in range(d)]
+            W = fine._tprod([box["W"][k][eidx[k]][:, :, None] for k in range(d)])[:, :, 0]
+            Bh = fine._tprod(V)
+            I = fine._local_full_indices(box, eidx)
+            coef = U[tuple(I[k] for k in reversed(range(d)))]          # [E, A]
+            uh = np.einsum("ega,ea->eg", Bh, coef)
+            X = [fine._gather_grid(box["F"][c], eidx) for c in range(d)]
+            det = fine._gather_grid(box["det"], eidx)
+            err2 += np.sum(W * np.abs(det) * (u_exact(*X) - uh) ** 2)
+        return float(np.sqrt(err2))
+
+    # ---- dense reference objects for tiny problems --------------------------
+    def dense_A_bruteforce(self, full=False):
+        """A by one global quadrature sum over the whole tensor grid of
+        quadrature points with global (not element-local) basis tables:
+        A = sum_q w_q G(q)^T Q(q) G(q). Tiny problems only."""
+        d = self.d
+        pts = [self.qz[k].ravel() for k in range(d)]
+        wts = [self.qw[k].ravel() for k in range(d)]
+        V = [spline.basis_table(self.knots[k], self.p, pts[k]) for k in range(d)]
+        Dr = [spline.basis_table(self.knots[k], self.p, pts[k], deriv=True) for k in range(d)]
+        if not full:
+            V = [v[:, 1:-1] for v in V]
+            Dr = [x[:, 1:-1] for x in Dr]
+        _, J = self.geo.eval_grid(pts)
+        Q, _ = q_matrix(J, self.kappa)
+        Q = Q.reshape(-1, d, d)
+
+        def kron_all(tabs):  # rows: q (dir 1 fastest), cols: dof (dir 1 fastest)
+            T = tabs[-1]
+            for k in range(d - 2, -1, -1):
+                T = np.einsum("qi,rj->qrij", T, tabs[k]).reshape(
+                    T.shape[0] * tabs[k].shape[0], T.shape[1] * tabs[k].shape[1])
+            return T
+
+        Wq = kron_all([w[:, None] for w in wts])[:, 0]
+        G = np.stack([kron_all([Dr[k] if k == r else V[k] for k in range(d)])
+                      for r in range(d)], axis=-1)                 # [q, dof, r]
+        return np.einsum("q,qir,qrs,qjs->ij", Wq, G, Q, G)
+
+    def dense_P(self):
+        """Eq. (prec) in Kronecker form with K_k acting on index i_k:
+        P = sum_k (x)_{l} (K_l if l == k else M_l), direction 1 fastest."""
+        pens = [self.pencil(k) for k in range(self.d)]
+        P = 0
+        for k in range(self.d):
+            T = np.ones((1, 1))
+            for l in reversed(range(self.d)):
+                T = np.kron(T, pens[l][0] if l == k else pens[l][1])
+            P = P + T
+        return P
+
+
+def stencil_to_csr(disc: Discretization, S):
+    """Sparse CSR form of an offset array S[o, row]."""
+    d, p, N = disc.d, disc.p, disc.N
+    rows, cols, vals = [], [], []
+    idx = np.arange(N)
+    multi = []
+    rem = idx.copy()
+    for k in range(d):
+        multi.append(rem % disc.n[k]); rem //= disc.n[k]
+    for delta in itertools.product(range(-p, p + 1), repeat=d):
+        delta = delta[::-1]  # product varies the last slot fastest; keep dir 1 fastest
+        o = int(disc.offset_index(delta))
+        ok = np.ones(N, bool)
+        for k in range(d):
+            ok &= (multi[k] + delta[k] >= 0) & (multi[k] + delta[k] < disc.n[k])
+        col = disc.row_index([multi[k] + delta[k] for k in range(d)])
+        rows.append(idx[ok]); cols.append(col[ok]); vals.append(S[o][ok])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(N, N))
+
+
+def apply_stencil(disc: Discretization, S, x):
+    """y[row] = sum_o S[o, row] x[row + delta(o)], zero outside the box."""
+    d, p = disc.d, disc.p
+    X = x.reshape(tuple(reversed(disc.n)))
+    Y = np.zeros_like(X)
+    Sv = S.reshape((-1,) + tuple(reversed(disc.n)))
+    for delta in itertools.product(range(-p, p + 1), repeat=d):
+        delta = delta[::-1]
+        o = int(disc.offset_index(delta))
+        dst, src = [], []
+        for k in reversed(range(d)):          # array axes: slowest first
+            dk, nk = delta[k], disc.n[k]
+            dst.append(slice(max(0, -dk), min(nk, nk - dk)))
+            src.append(slice(max(0, dk), min(nk, nk + dk)))
+        Y[tuple(dst)] += Sv[o][tuple(dst)] * X[tuple(src)]
+    return Y.ravel()
