@@ -1,0 +1,174 @@
+/*
+ * igafd — GB300-native PCG for single-patch isogeometric Poisson problems,
+ * preconditioned by the fast-diagonalization (FD) solve of the Kronecker-sum
+ * matrix P (Sangalli & Tani, "Isogeometric preconditioners based on fast
+ * solvers for the Sylvester equation").
+ *
+ * C ABI: plain pointers and sizes only. All "_dev" pointers are CUDA device
+ * pointers on the device that was current at igafd_setup_patch; "stream" is
+ * a cudaStream_t passed as void* (NULL = legacy default stream).
+ *
+ * Conventions
+ *  - Dof vectors are FP64, length N = n_1 * ... * n_d, with the scalar index
+ *    of Eq. (Vh): i = i_1 + n_1 (i_2 + n_2 i_3) (direction 1 fastest), where
+ *    n_k = m_k - 2 counts the B-splines of direction k that vanish on the
+ *    boundary (homogeneous Dirichlet conditions). Device vectors must be
+ *    8-byte aligned; 256-byte alignment gives the best bandwidth.
+ *  - The patch owns every device buffer it uses. Only igafd_setup_patch
+ *    allocates; apply/solve entry points never allocate.
+ *  - Errors are returned as igafd_status, never trapped on the device. After a
+ *    device-side limit is hit, the status says so and the context stays usable.
+ *  - Calls on one patch must not overlap in time on different streams (the
+ *    patch's workspace is shared by its entry points).
+ */
+#ifndef IGAFD_H
+#define IGAFD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct igafd_patch igafd_patch;
+
+typedef enum {
+  IGAFD_OK = 0,
+  IGAFD_ERR_ARG = -1,           /* invalid argument (sizes, knots, NULLs) */
+  IGAFD_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  IGAFD_ERR_NOT_SPD = -3,       /* Cholesky of a 1D mass matrix failed */
+  IGAFD_ERR_EIG = -4,           /* Jacobi eigen-solve hit its sweep limit */
+  IGAFD_ERR_FOLDED = -5,        /* det J <= 0 at a quadrature point */
+  IGAFD_ERR_BREAKDOWN = -6,     /* PCG: (p, Ap) <= 0 or non-finite */
+  IGAFD_ERR_NOT_CONVERGED = -7, /* PCG: iteration cap reached */
+  IGAFD_ERR_TIMEOUT = -8,       /* a bounded device wait ran out */
+  IGAFD_ERR_OOM = -9            /* device allocation failed in setup */
+} igafd_status;
+
+/* Arithmetic of the preconditioner's mode-k contractions. The outer PCG
+ * (inner products, residual recurrence, A stencil) is always FP64. */
+typedef enum {
+  IGAFD_FP64 = 0,   /* FP64 contractions and divide: FD is exactly P^{-1} */
+  IGAFD_FP32 = 1,   /* FP32 SIMT contractions, FP32 divide */
+  IGAFD_BF16 = 2,   /* tcgen05 kind::f16 with bf16 operands, FP32 accumulate */
+  IGAFD_FP16 = 3    /* tcgen05 kind::f16 with fp16 operands, FP32 accumulate */
+} igafd_dtype;
+
+/* Single-patch problem (Section 2.1, Eqs. (A), (Q)):
+ *   -div(kappa grad u) = f on Omega = F([0,1]^d), u = 0 on the boundary,
+ * discretised by degree-p tensor B-splines on open knot vectors.
+ * All pointers are host pointers, read only during igafd_setup_patch. */
+typedef struct {
+  int dim;                          /* 2 or 3 */
+  int p;                            /* spline degree, 1 <= p <= 7 */
+  const int *n_knots;               /* [dim] knot-vector lengths (m_k + p + 1) */
+  const double *const *knots;       /* [dim] open knot vectors on [0,1], interior
+                                       multiplicity <= p (Eq. (knot-vector)) */
+  int geo_p;                        /* degree of the geometry map F, 1..7 */
+  const int *geo_n_knots;           /* [dim] */
+  const double *const *geo_knots;   /* [dim] knot vectors of F */
+  const double *ctrl;               /* control net of F: [dim][g_d]..[g_1]
+                                       (coordinate slowest, direction 1 fastest),
+                                       g_k = geo_n_knots[k] - geo_p - 1 */
+  double kappa;                     /* constant scalar coefficient K = kappa I */
+} igafd_patch_desc;
+
+typedef struct {
+  int dim, p;
+  int n[3];            /* dofs per direction (1 for unused directions) */
+  long long N;         /* total dofs */
+  int nel[3];          /* elements per direction */
+  int n_offsets;       /* (2p+1)^dim stencil offsets */
+  double min_detJ;     /* min det J over all quadrature points */
+  double q_bound;      /* Prop. 1 estimate sup lambda_max(Q) / inf lambda_min(Q)
+                          over the quadrature points */
+  double setup_ms;     /* device time of the last igafd_setup_patch */
+  double eig_ms;       /* of which the generalized eigendecompositions */
+  long long stencil_bytes;
+} igafd_patch_info;
+
+typedef struct {
+  double tol;          /* relative residual tolerance ||r|| <= tol ||b|| */
+  int max_iter;        /* iteration cap (products with A inside the loop) */
+  int true_every;      /* recompute r = b - A x every this many iterations
+                          (0 = only to confirm convergence) */
+  igafd_dtype prec_dtype;
+  int flexible;        /* 1: beta = (r+, z+ - z)/(r, z); 0: Fletcher-Reeves */
+  int x0_given;        /* 1: x_dev holds the initial guess; 0: x0 = 0 */
+  int check_every;     /* host polls the device convergence flag every this
+                          many iterations (>= 1); later iterations are skipped
+                          on the device once converged, so x is unaffected */
+} igafd_pcg_opts;
+
+typedef struct {
+  int iterations;      /* products with A inside the loop */
+  int status;          /* igafd_status of the solve */
+  double relres;       /* final recurrence ||r||/||b|| */
+  double true_relres;  /* final ||b - A x|| / ||b|| */
+  int true_checks;     /* true-residual recomputations performed */
+} igafd_pcg_info;
+
+/* Build a patch: 1D pencils K_k, M_k by (p+1)-point Gauss quadrature
+ * (Section 3, Eq. (prec)), their FP64 generalized eigendecompositions
+ * K_k U_k = M_k U_k D_k, U_k^T M_k U_k = I (Algorithm 1 line 1, Section 4.1,
+ * Eq. (eigen3d)), and the stiffness matrix A of Eq. (A) with
+ * Q = kappa |det J| J^{-1} J^{-T} as a (2p+1)^d-point FP64 stencil
+ * (Section 2.1). Allocates all device memory the patch will use.
+ * Errors: ARG (bad sizes/knots), OOM, NOT_SPD, EIG, FOLDED, CUDA.
+ * On error *out is NULL and nothing is leaked. */
+igafd_status igafd_setup_patch(const igafd_patch_desc *desc, void *stream,
+                               igafd_patch **out);
+
+void igafd_destroy_patch(igafd_patch *patch);
+
+igafd_status igafd_patch_query(const igafd_patch *patch, igafd_patch_info *info);
+
+/* Copy the generalized eigenpairs of direction k (0-based) to host memory:
+ * U_host[i * n_k + j] = (U_k)_{ij} (column j is the eigenvector of D_host[j]),
+ * eigenvalues ascending, each column signed so its largest-magnitude entry is
+ * positive. Either pointer may be NULL. Synchronises the device. */
+igafd_status igafd_get_eigen(const igafd_patch *patch, int k, double *U_host,
+                             double *D_host);
+
+/* Copy the stencil of A to device memory dst_dev[o * N + row], with
+ * o = sum_k (delta_k + p) (2p+1)^(k-1): entry A[row, row + delta]; entries
+ * whose column leaves the index box are 0 (Section 2.1, sparsity of A). */
+igafd_status igafd_copy_stencil(const igafd_patch *patch, double *dst_dev,
+                                void *stream);
+
+/* y = A x (Eq. (A)); x_dev and y_dev are length-N device vectors that must
+ * not overlap. */
+igafd_status igafd_apply_A(igafd_patch *patch, const double *x_dev,
+                           double *y_dev, void *stream);
+
+/* z = P^{-1} r by fast diagonalization (Algorithm 1 in 2D, Algorithm 3 in
+ * 3D, with the forward step applying U_k^T and the backward step U_k):
+ * forward mode-k products, divide by D_1 (+) ... (+) D_d, backward mode-k
+ * products. With IGAFD_FP64 the result equals P^{-1} r up to rounding;
+ * other dtypes give an inexact P^{-1}. r_dev and z_dev must not overlap. */
+igafd_status igafd_apply_prec(igafd_patch *patch, igafd_dtype dtype,
+                              const double *r_dev, double *z_dev, void *stream);
+
+/* b_i = int f(F(zeta)) B_i(zeta) |det J| dzeta for the manufactured
+ * solution u = prod_k sin(pi x_k), f = d pi^2 u (Eq. (poisson) with
+ * kappa = 1, right-hand side of the Galerkin system). */
+igafd_status igafd_load_rhs_sine(igafd_patch *patch, double *b_dev, void *stream);
+
+/* Solve A x = b by conjugate gradients preconditioned with P (Section 3),
+ * P^{-1} applied by fast diagonalization in opts->prec_dtype. x_dev is the
+ * initial guess if opts->x0_given, and receives the solution (the best
+ * iterate on failure). Synchronises with the host only to poll the
+ * convergence flag. Returns the solve status (also in info->status). */
+igafd_status igafd_pcg_solve(igafd_patch *patch, const igafd_pcg_opts *opts,
+                             const double *b_dev, double *x_dev,
+                             igafd_pcg_info *info, void *stream);
+
+/* Default options: tol 1e-8, max_iter 1000, true_every 50, FP64,
+ * Fletcher-Reeves, x0 = 0, check_every 4. */
+void igafd_pcg_default_opts(igafd_pcg_opts *opts);
+
+const char *igafd_status_str(igafd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IGAFD_H */

@@ -1,0 +1,136 @@
+// Internal definitions shared by the igafd CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/igafd.h"
+
+#define IGAFD_MAXP 7
+#define IGAFD_MAXDIM 3
+
+// Return IGAFD_ERR_CUDA from the enclosing function when a runtime call fails.
+#define IGAFD_CUDA(call)                                                   \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      fprintf(stderr, "igafd: %s failed: %s (%s:%d)\n", #call,             \
+              cudaGetErrorString(e_), __FILE__, __LINE__);                 \
+      return IGAFD_ERR_CUDA;                                               \
+    }                                                                      \
+  } while (0)
+
+#define IGAFD_TRY(expr)                         \
+  do {                                          \
+    igafd_status s_ = (expr);                   \
+    if (s_ != IGAFD_OK) return s_;              \
+  } while (0)
+
+// Per-direction quadrature tables (device), nq = p + 1 Gauss points per
+// element: index t = e * nq + g runs over the 1D quadrature points.
+struct Dir1D {
+  int n;          // dofs (Dirichlet-reduced)
+  int m;          // B-splines of the discretisation
+  int nel;        // non-empty knot spans
+  int gm;         // B-splines of the geometry map
+  double *knots;  // [m + p + 1]
+  double *gknots; // [gm + geo_p + 1]
+  int *span;      // [nel] knot-span index s of each element (locals s-p..s)
+  double *z, *w;  // [nel*nq] Gauss points and weights
+  double *bv, *bd;  // [nel*nq*(p+1)] local basis values / derivatives
+  int *gspan;       // [nel*nq] geometry span at each point
+  double *gv, *gd;  // [nel*nq*(geo_p+1)] geometry basis values / derivatives
+};
+
+// Scalars of the PCG recurrence kept on the device.
+enum {
+  S_RHO = 0,      // (r, z)
+  S_PQ,           // (p, A p)
+  S_ALPHA,
+  S_BETA,
+  S_RR,           // (r, r)
+  S_RZOLD,        // (r_{k+1}, z_k) for the flexible beta
+  S_BB,           // (b, b)
+  S_DONE,         // 1.0 once converged / broken down
+  S_ITER,         // iterations executed
+  S_STATUS,       // 0 ok, -6 breakdown
+  S_TRUE_RR,      // last true residual (r, r)
+  S_COUNT
+};
+
+struct FDMixed;   // mixed-precision FD workspace (fd_mixed.cu)
+
+struct igafd_patch {
+  int dev;
+  int dim, p, geo_p;
+  int n[3], nel[3];
+  long long N;
+  int n_off;
+  double kappa;
+  Dir1D dir[3];
+  double *ctrl;                 // [dim][gm_d]..[gm_1]
+  // generalized eigenpairs: U[k][i*n + j], D[k][j]; inv_lam[N] = 1/(D1+D2+D3)
+  double *U[3], *D[3];
+  float *U32[3];
+  double *inv_lam;
+  float *inv_lam32;
+  // stiffness stencil [n_off][N]
+  double *stencil;
+  // FD workspace
+  double *fd_a, *fd_b;          // N each
+  // PCG workspace
+  double *r, *z, *pv, *q, *xt;  // N each (xt: true-residual scratch)
+  double *partial;              // [PARTIAL_SLOTS][MAX_BLOCKS]
+  unsigned int *counter;        // last-block counters
+  double *scal;                 // [S_COUNT]
+  double *host_scal;            // pinned mirror of scal
+  FDMixed *mixed;
+  // diagnostics
+  double min_detJ, q_bound, setup_ms, eig_ms;
+  int *err_flag;                // device error flags from setup kernels
+};
+
+// Reductions: fixed-size partial arrays, deterministic order.
+#define IGAFD_RED_BLOCKS 1184   // 152 SMs * 8 (multiple of the SM count)
+#define IGAFD_PARTIAL_SLOTS 4
+
+// ---- internal entry points (implemented in the .cu files) ----------------
+igafd_status igafd_setup_tables(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s);
+igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s);
+igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s);
+// FD apply; kernels do nothing while *done_flag != 0 (done_flag may be null)
+igafd_status igafd_fd64_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
+                              double *done_flag);
+igafd_status igafd_fd32_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
+                              double *done_flag);
+igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, double *z,
+                               cudaStream_t s, double *done_flag);
+igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s);
+void igafd_fd_tc_free(igafd_patch *P);
+// y = A x (b == null) or y = b - A x; see stencil.cu
+igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
+                                  int pcg, int skip_done, cudaStream_t s);
+
+// ---- device helpers ---------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sh32) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh32[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    t = lane < nw ? sh32[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}

@@ -1,0 +1,653 @@
+// Patch setup on the device: per-direction quadrature/basis tables, the
+// geometry map, the (2p+1)^d stiffness stencil of Eq. (A) and the
+// manufactured right-hand side.
+//
+// Quadrature: (p+1)-point Gauss-Legendre per element and direction.
+// Q = kappa |det J| J^{-1} J^{-T} (chain rule with J_ij = dx_i/dzeta_j; the
+// paper prints the transposes the other way round in Eq. (Q)).
+#include "common.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace {
+
+// Device-visible view of the patch tables (passed by value to kernels).
+struct PV {
+  int dim, p, gp, nq;
+  int n[3], nel[3], gm[3];
+  const int *span[3];
+  const double *w[3], *bv[3], *bd[3], *gv[3], *gd[3];
+  const int *gspan[3];
+  const double *ctrl;
+  double kappa;
+};
+
+PV make_view(const igafd_patch *P) {
+  PV v{};
+  v.dim = P->dim; v.p = P->p; v.gp = P->geo_p; v.nq = P->p + 1;
+  for (int k = 0; k < 3; ++k) {
+    v.n[k] = P->n[k]; v.nel[k] = P->nel[k]; v.gm[k] = P->dir[k].gm;
+    v.span[k] = P->dir[k].span; v.w[k] = P->dir[k].w;
+    v.bv[k] = P->dir[k].bv; v.bd[k] = P->dir[k].bd;
+    v.gv[k] = P->dir[k].gv; v.gd[k] = P->dir[k].gd; v.gspan[k] = P->dir[k].gspan;
+  }
+  v.ctrl = P->ctrl; v.kappa = P->kappa;
+  return v;
+}
+
+// Nonzero degree-p B-splines B_{s-p..s} and their derivatives at u in span s
+// (triangular Cox-de Boor scheme; derivatives from the degree p-1 values).
+__device__ void bspline_local(const double *xi, int s, double u, int p, double *N, double *dN) {
+  double left[IGAFD_MAXP + 1], right[IGAFD_MAXP + 1], prev[IGAFD_MAXP + 1];
+  N[0] = 1.0;
+  prev[0] = 1.0;
+  for (int j = 1; j <= p; ++j) {
+    left[j] = u - xi[s + 1 - j];
+    right[j] = xi[s + j] - u;
+    double saved = 0.0;
+    for (int r = 0; r < j; ++r) {
+      double den = right[r + 1] + left[j - r];
+      double t = den != 0.0 ? N[r] / den : 0.0;
+      N[r] = saved + right[r + 1] * t;
+      saved = left[j - r] * t;
+    }
+    N[j] = saved;
+    if (j == p - 1)
+      for (int r = 0; r <= j; ++r) prev[r] = N[r];
+  }
+  // prev[b] = B_{s-p+1+b, p-1}, b = 0..p-1
+  for (int a = 0; a <= p; ++a) {
+    int i = s - p + a;
+    double d = 0.0;
+    if (a >= 1) {
+      double den = xi[i + p] - xi[i];
+      if (den != 0.0) d += p * prev[a - 1] / den;
+    }
+    if (a <= p - 1) {
+      double den = xi[i + p + 1] - xi[i + 1];
+      if (den != 0.0) d -= p * prev[a] / den;
+    }
+    dN[a] = d;
+  }
+}
+
+// i-th node (ascending) and weight of the nq-point Gauss-Legendre rule on
+// [-1, 1] by Newton's method on the Legendre polynomial P_nq.
+__device__ void gauss_node(int nq, int i, double *x, double *w) {
+  int ir = nq - 1 - i;  // Newton guess ordering is descending
+  double z = cos(M_PI * (ir + 0.75) / (nq + 0.5));
+  double dp = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= nq; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1; p1 = p2;
+    }
+    if (nq == 1) { p1 = z; p0 = 1.0; }
+    dp = nq * (z * p1 - p0) / (z * z - 1.0);
+    double dz = p1 / dp;
+    z -= dz;
+    if (fabs(dz) < 1e-16) break;
+  }
+  {
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= nq; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1; p1 = p2;
+    }
+    dp = nq * (z * p1 - p0) / (z * z - 1.0);
+  }
+  *x = z;
+  *w = 2.0 / ((1.0 - z * z) * dp * dp);
+}
+
+// One thread per 1D quadrature point of one direction.
+__global__ void tables_kernel(Dir1D D, int p, int gp) {
+  int nq = p + 1;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= D.nel * nq) return;
+  int e = t / nq, g = t % nq;
+  int s = D.span[e];
+  double a = D.knots[s], b = D.knots[s + 1];
+  double xg, wg;
+  gauss_node(nq, g, &xg, &wg);
+  double z = 0.5 * (a + b) + 0.5 * (b - a) * xg;
+  D.z[t] = z;
+  D.w[t] = 0.5 * (b - a) * wg;
+  double N[IGAFD_MAXP + 1], dN[IGAFD_MAXP + 1];
+  bspline_local(D.knots, s, z, p, N, dN);
+  for (int i = 0; i <= p; ++i) {
+    D.bv[t * (p + 1) + i] = N[i];
+    D.bd[t * (p + 1) + i] = dN[i];
+  }
+  // geometry span: xi_gs <= z < xi_{gs+1}, gs in [gp, gm-1]
+  int lo = gp, hi = D.gm - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (D.gknots[mid] <= z) lo = mid; else hi = mid - 1;
+  }
+  D.gspan[t] = lo;
+  bspline_local(D.gknots, lo, z, gp, N, dN);
+  for (int i = 0; i <= gp; ++i) {
+    D.gv[t * (gp + 1) + i] = N[i];
+    D.gd[t * (gp + 1) + i] = dN[i];
+  }
+}
+
+// x = F(zeta) and J = dF/dzeta at the quadrature point with 1D indices t[k].
+template <int DIM>
+__device__ void geo_eval(const PV &v, const int *t, double *x, double (*J)[3]) {
+  const int gp = v.gp, ga = gp + 1;
+  const double *gv[3], *gd[3];
+  int g0[3];
+  for (int k = 0; k < DIM; ++k) {
+    gv[k] = v.gv[k] + (size_t)t[k] * ga;
+    gd[k] = v.gd[k] + (size_t)t[k] * ga;
+    g0[k] = v.gspan[k][t[k]] - gp;
+  }
+  for (int c = 0; c < DIM; ++c) {
+    x[c] = 0.0;
+    for (int j = 0; j < DIM; ++j) J[c][j] = 0.0;
+  }
+  if (DIM == 2) {
+    for (int c = 0; c < 2; ++c) {
+      const double *C = v.ctrl + (size_t)c * v.gm[0] * v.gm[1];
+      for (int a2 = 0; a2 < ga; ++a2) {
+        const double *row = C + (size_t)(g0[1] + a2) * v.gm[0] + g0[0];
+        double s0 = 0.0, s1 = 0.0;
+        for (int a1 = 0; a1 < ga; ++a1) {
+          s0 += row[a1] * gv[0][a1];
+          s1 += row[a1] * gd[0][a1];
+        }
+        x[c] += s0 * gv[1][a2];
+        J[c][0] += s1 * gv[1][a2];
+        J[c][1] += s0 * gd[1][a2];
+      }
+    }
+  } else {
+    for (int c = 0; c < 3; ++c) {
+      const double *C = v.ctrl + (size_t)c * v.gm[0] * v.gm[1] * v.gm[2];
+      for (int a3 = 0; a3 < ga; ++a3) {
+        double v3 = gv[2][a3], d3 = gd[2][a3];
+        for (int a2 = 0; a2 < ga; ++a2) {
+          const double *row =
+              C + ((size_t)(g0[2] + a3) * v.gm[1] + (g0[1] + a2)) * v.gm[0] + g0[0];
+          double s0 = 0.0, s1 = 0.0;
+          for (int a1 = 0; a1 < ga; ++a1) {
+            s0 += row[a1] * gv[0][a1];
+            s1 += row[a1] * gd[0][a1];
+          }
+          double v2 = gv[1][a2], d2 = gd[1][a2];
+          x[c] += s0 * v2 * v3;
+          J[c][0] += s1 * v2 * v3;
+          J[c][1] += s0 * d2 * v3;
+          J[c][2] += s0 * v2 * d3;
+        }
+      }
+    }
+  }
+}
+
+// Q = kappa |det J| J^{-1} J^{-T}; returns det J. Q stored symmetric:
+// 2D [00, 11, 01], 3D [00, 11, 22, 01, 02, 12].
+template <int DIM>
+__device__ double q_from_J(const double (*J)[3], double kappa, double *Q) {
+  if (DIM == 2) {
+    double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    double id = 1.0 / det;
+    double Ji[2][2] = {{J[1][1] * id, -J[0][1] * id}, {-J[1][0] * id, J[0][0] * id}};
+    double sc = kappa * fabs(det);
+    Q[0] = sc * (Ji[0][0] * Ji[0][0] + Ji[0][1] * Ji[0][1]);
+    Q[1] = sc * (Ji[1][0] * Ji[1][0] + Ji[1][1] * Ji[1][1]);
+    Q[2] = sc * (Ji[0][0] * Ji[1][0] + Ji[0][1] * Ji[1][1]);
+    return det;
+  } else {
+    double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    double id = 1.0 / det;
+    double Ji[3][3];
+    Ji[0][0] = c00 * id;
+    Ji[1][0] = c01 * id;
+    Ji[2][0] = c02 * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    double sc = kappa * fabs(det);
+    const int rr[6] = {0, 1, 2, 0, 0, 1}, ss[6] = {0, 1, 2, 1, 2, 2};
+    for (int q = 0; q < 6; ++q) {
+      double acc = 0.0;
+      for (int c = 0; c < 3; ++c) acc += Ji[rr[q]][c] * Ji[ss[q]][c];
+      Q[q] = sc * acc;
+    }
+    return det;
+  }
+}
+
+__device__ __forceinline__ int qidx(int r, int s, int dim) {
+  if (r == s) return r;
+  if (dim == 2) return 2;
+  int lo = r < s ? r : s, hi = r < s ? s : r;
+  return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+
+// Extreme eigenvalues of a symmetric 2x2 / 3x3 matrix (closed form).
+template <int DIM>
+__device__ void sym_eig_extremes(const double *Q, double *lmin, double *lmax) {
+  if (DIM == 2) {
+    double m = 0.5 * (Q[0] + Q[1]);
+    double d = sqrt(0.25 * (Q[0] - Q[1]) * (Q[0] - Q[1]) + Q[2] * Q[2]);
+    *lmin = m - d; *lmax = m + d;
+  } else {
+    double a = Q[0], b = Q[1], c = Q[2], d = Q[3], e = Q[5], f = Q[4];
+    double p1 = d * d + f * f + e * e;
+    double q = (a + b + c) / 3.0;
+    double p2 = (a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + 2.0 * p1;
+    double pp = sqrt(p2 / 6.0);
+    if (pp < 1e-300) { *lmin = *lmax = q; return; }
+    double B00 = (a - q) / pp, B11 = (b - q) / pp, B22 = (c - q) / pp;
+    double B01 = d / pp, B02 = f / pp, B12 = e / pp;
+    double detB = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) +
+                  B02 * (B01 * B12 - B11 * B02);
+    double r = fmin(1.0, fmax(-1.0, 0.5 * detB));
+    double phi = acos(r) / 3.0;
+    double e1 = q + 2.0 * pp * cos(phi);
+    double e3 = q + 2.0 * pp * cos(phi + 2.0 * M_PI / 3.0);
+    *lmax = e1; *lmin = e3;
+  }
+}
+
+// Geometry diagnostics over every quadrature point: min det J and the Prop. 1
+// extremes sup lambda_max(Q), inf lambda_min(Q) (per-block partials).
+template <int DIM>
+__global__ void geo_check_kernel(PV v, long long nqp, double *part) {
+  __shared__ double sh[32];
+  double mdet = 1e300, lmin = 1e300, lmax = -1e300;
+  const int nq = v.nq;
+  const long long tot1 = (long long)v.nel[0] * nq, tot2 = (long long)v.nel[1] * nq;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nqp;
+       i += (long long)gridDim.x * blockDim.x) {
+    int t[3];
+    t[0] = (int)(i % tot1);
+    t[1] = (int)((i / tot1) % tot2);
+    t[2] = DIM == 3 ? (int)(i / (tot1 * tot2)) : 0;
+    double x[3], J[3][3], Q[6];
+    geo_eval<DIM>(v, t, x, J);
+    double det = q_from_J<DIM>(J, v.kappa, Q);
+    mdet = fmin(mdet, det);
+    double a, b;
+    sym_eig_extremes<DIM>(Q, &a, &b);
+    lmin = fmin(lmin, a);
+    lmax = fmax(lmax, b);
+  }
+  // block min/max via negation trick on sums is not possible; use shuffles
+  for (int o = 16; o > 0; o >>= 1) {
+    mdet = fmin(mdet, __shfl_xor_sync(0xffffffffu, mdet, o));
+    lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+    lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  }
+  __shared__ double s3[3][32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { s3[0][wid] = mdet; s3[1][wid] = lmin; s3[2][wid] = lmax; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mdet = fmin(mdet, s3[0][w]); lmin = fmin(lmin, s3[1][w]); lmax = fmax(lmax, s3[2][w]);
+    }
+    part[3 * blockIdx.x + 0] = mdet;
+    part[3 * blockIdx.x + 1] = lmin;
+    part[3 * blockIdx.x + 2] = lmax;
+  }
+  (void)sh;
+}
+
+// Stiffness assembly, one thread block per element of one colour class
+// (element index = colour mod (p+1) per direction), so that no two blocks of
+// a launch touch the same stencil entry: plain read-modify-write, fixed
+// summation order, deterministic.
+//
+// Local matrix L[a][b] = sum_g sum_{r,s} Q_rs(g) dB_a/dzeta_r dB_b/dzeta_s,
+// evaluated by sum factorisation over the tensor quadrature points: for each
+// (r, s) contract direction 1, then direction 2, and accumulate by the
+// derivative pattern of direction 3 (or 2 in 2D), then contract the last
+// direction per output entry.
+template <int DIM>
+__global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
+                                double *__restrict__ stencil, long long N) {
+  extern __shared__ double sm[];
+  const int p = v.p, A = p + 1, nq = p + 1, W = 2 * p + 1;
+  const int nqd = DIM == 3 ? nq * nq * nq : nq * nq;
+  const int nQ = DIM == 3 ? 6 : 3;
+  // element of this block
+  int bid = blockIdx.x;
+  int e1 = c1 + (p + 1) * (bid % ne1);
+  int e2 = c2 + (p + 1) * ((bid / ne1) % ne2);
+  int e3 = DIM == 3 ? c3 + (p + 1) * (bid / (ne1 * ne2)) : 0;
+  int e[3] = {e1, e2, e3};
+  double *Qs = sm;                          // [nQ][nqd]
+  double *F = Qs + nQ * nqd;                // [DIM][2][A][nq]: basis value/deriv per direction
+  double *T1 = F + DIM * 2 * A * nq;        // 3D: [A*A][nq][nq], 2D: unused
+  double *G = T1 + (DIM == 3 ? A * A * nq * nq : 0);  // 3D: [4][A*A][A*A][nq], 2D: [4][A*A][nq]
+  const int AA = A * A;
+  const int Gsz = DIM == 3 ? 4 * AA * AA * nq : 4 * AA * nq;
+  // tables
+  for (int i = threadIdx.x; i < DIM * 2 * A * nq; i += blockDim.x) {
+    int g = i % nq, a = (i / nq) % A, vd = (i / (nq * A)) % 2, k = i / (2 * nq * A);
+    size_t t = (size_t)e[k] * nq + g;
+    F[i] = (vd ? v.bd[k] : v.bv[k])[t * A + a];
+  }
+  for (int i = threadIdx.x; i < Gsz; i += blockDim.x) G[i] = 0.0;
+  // Q at the element's quadrature points, with weights folded in
+  for (int g = threadIdx.x; g < nqd; g += blockDim.x) {
+    int gq[3] = {g % nq, (g / nq) % nq, DIM == 3 ? g / (nq * nq) : 0};
+    int t[3];
+    for (int k = 0; k < DIM; ++k) t[k] = e[k] * nq + gq[k];
+    double x[3], J[3][3], Q[6];
+    geo_eval<DIM>(v, t, x, J);
+    q_from_J<DIM>(J, v.kappa, Q);
+    double wt = 1.0;
+    for (int k = 0; k < DIM; ++k) wt *= v.w[k][t[k]];
+    for (int q = 0; q < nQ; ++q) Qs[q * nqd + g] = Q[q] * wt;
+  }
+  __syncthreads();
+#define FV(k, vd, a, g) F[(((k) * 2 + (vd)) * A + (a)) * nq + (g)]
+  for (int r = 0; r < DIM; ++r) {
+    for (int s = 0; s < DIM; ++s) {
+      const double *Qrs = Qs + qidx(r, s, DIM) * nqd;
+      const int ra = (r == 0), sa = (s == 0);       // derivative pattern, dir 1
+      const int rb = (r == 1), sb = (s == 1);       // dir 2
+      if (DIM == 3) {
+        // T1[a1b1][g2][g3] = sum_g1 f1(a1,g1) f1'(b1,g1) Q(g1,g2,g3)
+        for (int i = threadIdx.x; i < AA * nq * nq; i += blockDim.x) {
+          int g23 = i % (nq * nq), ab = i / (nq * nq);
+          int a1 = ab % A, b1 = ab / A;
+          double acc = 0.0;
+          for (int g1 = 0; g1 < nq; ++g1)
+            acc += FV(0, ra, a1, g1) * FV(0, sa, b1, g1) * Qrs[g23 * nq + g1];
+          T1[i] = acc;
+        }
+        __syncthreads();
+        // G[pat3][a1b1][a2b2][g3] += sum_g2 f2(a2,g2) f2'(b2,g2) T1[a1b1][g2][g3]
+        const int pat = 2 * (r == 2) + (s == 2);
+        double *Gp = G + (size_t)pat * AA * AA * nq;
+        for (int i = threadIdx.x; i < AA * AA * nq; i += blockDim.x) {
+          int g3 = i % nq, ab2 = (i / nq) % AA, ab1 = i / (nq * AA);
+          int a2 = ab2 % A, b2 = ab2 / A;
+          double acc = 0.0;
+          for (int g2 = 0; g2 < nq; ++g2)
+            acc += FV(1, rb, a2, g2) * FV(1, sb, b2, g2) * T1[(ab1 * nq + g3) * nq + g2];
+          Gp[i] += acc;
+        }
+        __syncthreads();
+      } else {
+        // G[pat2][a1b1][g2] += sum_g1 f1 f1' Q(g1, g2)
+        const int pat = 2 * (r == 1) + (s == 1);
+        double *Gp = G + (size_t)pat * AA * nq;
+        for (int i = threadIdx.x; i < AA * nq; i += blockDim.x) {
+          int g2 = i % nq, ab = i / nq;
+          int a1 = ab % A, b1 = ab / A;
+          double acc = 0.0;
+          for (int g1 = 0; g1 < nq; ++g1)
+            acc += FV(0, ra, a1, g1) * FV(0, sa, b1, g1) * Qrs[g2 * nq + g1];
+          Gp[i] += acc;
+        }
+        __syncthreads();
+      }
+    }
+  }
+  // Output entries (a, delta): consecutive threads take consecutive a_1 with
+  // the same offset, so their stencil addresses are contiguous.
+  const int last = DIM - 1;
+  long long Nn1 = v.n[0], Nn2 = v.n[1];
+  int nent = 1;
+  for (int k = 0; k < DIM; ++k) nent *= A * W;
+  for (int i = threadIdx.x; i < nent; i += blockDim.x) {
+    int rem = i;
+    int a[3], dl[3], b[3];
+    bool ok = true;
+    for (int k = 0; k < DIM; ++k) {
+      a[k] = rem % A; rem /= A;
+      dl[k] = rem % W - p; rem /= W;
+      b[k] = a[k] + dl[k];
+      ok = ok && b[k] >= 0 && b[k] < A;
+    }
+    if (!ok) continue;
+    // global Dirichlet indices: full index I = span - p + a, reduced i = I - 1
+    long long row = 0, stride = 1;
+    for (int k = 0; k < DIM; ++k) {
+      int I = v.span[k][e[k]] - p + a[k];
+      int J = I + dl[k];
+      if (I < 1 || I > v.n[k] || J < 1 || J > v.n[k]) { ok = false; break; }
+      row += (long long)(I - 1) * stride;
+      stride *= v.n[k];
+    }
+    if (!ok) continue;
+    double val = 0.0;
+    if (DIM == 3) {
+      int ab1 = a[0] + A * b[0], ab2 = a[1] + A * b[1];
+      for (int pat = 0; pat < 4; ++pat) {
+        const double *Gp = G + (((size_t)pat * AA + ab1) * AA + ab2) * nq;
+        int da = pat >> 1, db = pat & 1;
+        for (int g3 = 0; g3 < nq; ++g3)
+          val += FV(last, da, a[2], g3) * FV(last, db, b[2], g3) * Gp[g3];
+      }
+    } else {
+      int ab1 = a[0] + A * b[0];
+      for (int pat = 0; pat < 4; ++pat) {
+        const double *Gp = G + ((size_t)pat * AA + ab1) * nq;
+        int da = pat >> 1, db = pat & 1;
+        for (int g2 = 0; g2 < nq; ++g2)
+          val += FV(last, da, a[1], g2) * FV(last, db, b[1], g2) * Gp[g2];
+      }
+    }
+    int o = 0, ws = 1;
+    for (int k = 0; k < DIM; ++k) { o += (dl[k] + p) * ws; ws *= W; }
+    stencil[(size_t)o * N + row] += val;
+  }
+  (void)Nn1; (void)Nn2;
+#undef FV
+}
+
+// Right-hand side for u = prod sin(pi x_k), f = d pi^2 u, one block per
+// element of a colour class (same colouring as the stiffness assembly).
+template <int DIM>
+__global__ void rhs_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2, double *b) {
+  extern __shared__ double sm[];
+  const int p = v.p, A = p + 1, nq = p + 1;
+  const int nqd = DIM == 3 ? nq * nq * nq : nq * nq;
+  int bid = blockIdx.x;
+  int e[3];
+  e[0] = c1 + (p + 1) * (bid % ne1);
+  e[1] = c2 + (p + 1) * ((bid / ne1) % ne2);
+  e[2] = DIM == 3 ? c3 + (p + 1) * (bid / (ne1 * ne2)) : 0;
+  double *fw = sm;  // [nqd]
+  for (int g = threadIdx.x; g < nqd; g += blockDim.x) {
+    int gq[3] = {g % nq, (g / nq) % nq, DIM == 3 ? g / (nq * nq) : 0};
+    int t[3];
+    for (int k = 0; k < DIM; ++k) t[k] = e[k] * nq + gq[k];
+    double x[3], J[3][3], Q[6];
+    geo_eval<DIM>(v, t, x, J);
+    double det = q_from_J<DIM>(J, 1.0, Q);
+    double f = DIM * M_PI * M_PI;
+    double wt = fabs(det);
+    for (int k = 0; k < DIM; ++k) {
+      f *= sin(M_PI * x[k]);
+      wt *= v.w[k][t[k]];
+    }
+    fw[g] = f * wt;
+  }
+  __syncthreads();
+  int nloc = 1;
+  for (int k = 0; k < DIM; ++k) nloc *= A;
+  for (int i = threadIdx.x; i < nloc; i += blockDim.x) {
+    int a[3] = {i % A, (i / A) % A, DIM == 3 ? i / (A * A) : 0};
+    long long row = 0, stride = 1;
+    bool ok = true;
+    for (int k = 0; k < DIM; ++k) {
+      int I = v.span[k][e[k]] - p + a[k];
+      if (I < 1 || I > v.n[k]) { ok = false; break; }
+      row += (long long)(I - 1) * stride;
+      stride *= v.n[k];
+    }
+    if (!ok) continue;
+    double acc = 0.0;
+    for (int g = 0; g < nqd; ++g) {
+      int gq[3] = {g % nq, (g / nq) % nq, DIM == 3 ? g / (nq * nq) : 0};
+      double bv = 1.0;
+      for (int k = 0; k < DIM; ++k) bv *= v.bv[k][((size_t)e[k] * nq + gq[k]) * A + a[k]];
+      acc += bv * fw[g];
+    }
+    b[row] += acc;
+  }
+}
+
+size_t assemble_smem(int dim, int p) {
+  size_t A = p + 1, nq = p + 1, AA = A * A;
+  size_t nqd = dim == 3 ? nq * nq * nq : nq * nq;
+  size_t nQ = dim == 3 ? 6 : 3;
+  size_t s = nQ * nqd + dim * 2 * A * nq;
+  if (dim == 3) s += AA * nq * nq + 4 * AA * AA * nq;
+  else s += 4 * AA * nq;
+  return s * sizeof(double);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+static igafd_status dalloc(void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return IGAFD_ERR_OOM;
+  }
+  return IGAFD_OK;
+}
+
+igafd_status igafd_setup_tables(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
+  const int p = P->p, gp = P->geo_p, nq = p + 1;
+  size_t ctrl_count = (size_t)P->dim;
+  for (int k = 0; k < 3; ++k) {
+    Dir1D &D = P->dir[k];
+    if (k >= P->dim) {
+      continue;
+    }
+    std::vector<int> spans;
+    const double *kn = d->knots[k];
+    int nk = d->n_knots[k];
+    for (int i = p; i < nk - p - 1; ++i)
+      if (kn[i] < kn[i + 1]) spans.push_back(i);
+    D.m = nk - p - 1;
+    D.n = D.m - 2;
+    D.nel = (int)spans.size();
+    D.gm = d->geo_n_knots[k] - gp - 1;
+    ctrl_count *= D.gm;
+    int nt = D.nel * nq;
+    IGAFD_TRY(dalloc((void **)&D.knots, nk * sizeof(double)));
+    IGAFD_TRY(dalloc((void **)&D.gknots, d->geo_n_knots[k] * sizeof(double)));
+    IGAFD_TRY(dalloc((void **)&D.span, D.nel * sizeof(int)));
+    IGAFD_TRY(dalloc((void **)&D.z, nt * sizeof(double)));
+    IGAFD_TRY(dalloc((void **)&D.w, nt * sizeof(double)));
+    IGAFD_TRY(dalloc((void **)&D.bv, (size_t)nt * (p + 1) * sizeof(double)));
+    IGAFD_TRY(dalloc((void **)&D.bd, (size_t)nt * (p + 1) * sizeof(double)));
+    IGAFD_TRY(dalloc((void **)&D.gspan, nt * sizeof(int)));
+    IGAFD_TRY(dalloc((void **)&D.gv, (size_t)nt * (gp + 1) * sizeof(double)));
+    IGAFD_TRY(dalloc((void **)&D.gd, (size_t)nt * (gp + 1) * sizeof(double)));
+    IGAFD_CUDA(cudaMemcpyAsync(D.knots, kn, nk * sizeof(double), cudaMemcpyHostToDevice, s));
+    IGAFD_CUDA(cudaMemcpyAsync(D.gknots, d->geo_knots[k], d->geo_n_knots[k] * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+    IGAFD_CUDA(cudaMemcpyAsync(D.span, spans.data(), D.nel * sizeof(int),
+                               cudaMemcpyHostToDevice, s));
+    // the host vector must outlive the async copy
+    IGAFD_CUDA(cudaStreamSynchronize(s));
+    tables_kernel<<<(nt + 127) / 128, 128, 0, s>>>(D, p, gp);
+    IGAFD_CUDA(cudaGetLastError());
+    P->n[k] = D.n;
+    P->nel[k] = D.nel;
+  }
+  IGAFD_TRY(dalloc((void **)&P->ctrl, ctrl_count * sizeof(double)));
+  IGAFD_CUDA(cudaMemcpyAsync(P->ctrl, d->ctrl, ctrl_count * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+  IGAFD_CUDA(cudaStreamSynchronize(s));
+  return IGAFD_OK;
+}
+
+igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s) {
+  PV v = make_view(P);
+  const int p = P->p, dim = P->dim;
+  // geometry diagnostics
+  long long nqp = 1;
+  for (int k = 0; k < dim; ++k) nqp *= (long long)P->nel[k] * (p + 1);
+  double *part = P->partial;  // >= 3 * 592 doubles available
+  const int gblocks = 592;
+  if (dim == 3) geo_check_kernel<3><<<gblocks, 256, 0, s>>>(v, nqp, part);
+  else geo_check_kernel<2><<<gblocks, 256, 0, s>>>(v, nqp, part);
+  IGAFD_CUDA(cudaGetLastError());
+  std::vector<double> h(3 * gblocks);
+  IGAFD_CUDA(cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  IGAFD_CUDA(cudaStreamSynchronize(s));
+  double mdet = 1e300, lmin = 1e300, lmax = -1e300;
+  for (int b = 0; b < gblocks; ++b) {
+    mdet = fmin(mdet, h[3 * b]);
+    lmin = fmin(lmin, h[3 * b + 1]);
+    lmax = fmax(lmax, h[3 * b + 2]);
+  }
+  P->min_detJ = mdet;
+  P->q_bound = lmax / lmin;
+  if (!(mdet > 0.0)) return IGAFD_ERR_FOLDED;
+  // stiffness stencil
+  IGAFD_CUDA(cudaMemsetAsync(P->stencil, 0, (size_t)P->n_off * P->N * sizeof(double), s));
+  size_t smem = assemble_smem(dim, p);
+  if (smem > 200 * 1024) return IGAFD_ERR_ARG;
+  if (dim == 3) {
+    IGAFD_CUDA(cudaFuncSetAttribute(assemble_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  } else {
+    IGAFD_CUDA(cudaFuncSetAttribute(assemble_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  }
+  const int C = p + 1;
+  for (int c3 = 0; c3 < (dim == 3 ? C : 1); ++c3)
+    for (int c2 = 0; c2 < C; ++c2)
+      for (int c1 = 0; c1 < C; ++c1) {
+        int ne1 = c1 < P->nel[0] ? (P->nel[0] - c1 + C - 1) / C : 0;
+        int ne2 = c2 < P->nel[1] ? (P->nel[1] - c2 + C - 1) / C : 0;
+        int ne3 = dim == 3 ? (c3 < P->nel[2] ? (P->nel[2] - c3 + C - 1) / C : 0) : 1;
+        long long nb = (long long)ne1 * ne2 * ne3;
+        if (nb == 0) continue;
+        if (dim == 3)
+          assemble_kernel<3><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, P->N);
+        else
+          assemble_kernel<2><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, 0, ne1, ne2, P->stencil, P->N);
+        IGAFD_CUDA(cudaGetLastError());
+      }
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_load_rhs_sine(igafd_patch *P, double *b, void *stream) {
+  if (!P || !b) return IGAFD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  IGAFD_CUDA(cudaSetDevice(P->dev));
+  PV v = make_view(P);
+  const int p = P->p, dim = P->dim, C = p + 1;
+  size_t smem = (size_t)(dim == 3 ? C * C * C : C * C) * sizeof(double);
+  IGAFD_CUDA(cudaMemsetAsync(b, 0, P->N * sizeof(double), s));
+  for (int c3 = 0; c3 < (dim == 3 ? C : 1); ++c3)
+    for (int c2 = 0; c2 < C; ++c2)
+      for (int c1 = 0; c1 < C; ++c1) {
+        int ne1 = c1 < P->nel[0] ? (P->nel[0] - c1 + C - 1) / C : 0;
+        int ne2 = c2 < P->nel[1] ? (P->nel[1] - c2 + C - 1) / C : 0;
+        int ne3 = dim == 3 ? (c3 < P->nel[2] ? (P->nel[2] - c3 + C - 1) / C : 0) : 1;
+        long long nb = (long long)ne1 * ne2 * ne3;
+        if (nb == 0) continue;
+        if (dim == 3) rhs_kernel<3><<<(unsigned)nb, 128, smem, s>>>(v, c1, c2, c3, ne1, ne2, b);
+        else rhs_kernel<2><<<(unsigned)nb, 128, smem, s>>>(v, c1, c2, 0, ne1, ne2, b);
+        IGAFD_CUDA(cudaGetLastError());
+      }
+  return IGAFD_OK;
+}

@@ -1,0 +1,220 @@
+"""ctypes binding of the igafd C ABI (include/igafd.h).
+
+Argument marshalling only: every computation runs in libigafd.so. Device
+vectors are torch CUDA tensors (float64, contiguous); streams are taken from
+torch's current stream. There is no CPU fallback: if the library is missing
+or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libigafd.so")
+
+FP64, FP32, BF16, FP16 = 0, 1, 2, 3
+DTYPES = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error",
+          -3: "1D mass matrix not positive definite", -4: "eigen-solve did not converge",
+          -5: "geometry map folds (det J <= 0)", -6: "PCG breakdown",
+          -7: "PCG did not converge", -8: "device wait timed out", -9: "out of device memory"}
+OK, ERR_ARG, ERR_CUDA, ERR_NOT_SPD, ERR_EIG, ERR_FOLDED, ERR_BREAKDOWN, ERR_NOT_CONVERGED, \
+    ERR_TIMEOUT, ERR_OOM = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+
+
+class IgafdError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"igafd {what}: {STATUS.get(status, status)} ({status})")
+
+
+class PatchDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("p", C.c_int),
+                ("n_knots", C.POINTER(C.c_int)), ("knots", C.POINTER(C.POINTER(C.c_double))),
+                ("geo_p", C.c_int), ("geo_n_knots", C.POINTER(C.c_int)),
+                ("geo_knots", C.POINTER(C.POINTER(C.c_double))),
+                ("ctrl", C.POINTER(C.c_double)), ("kappa", C.c_double)]
+
+
+class PatchInfo(C.Structure):
+    _fields_ = [("dim", C.c_int), ("p", C.c_int), ("n", C.c_int * 3), ("N", C.c_longlong),
+                ("nel", C.c_int * 3), ("n_offsets", C.c_int), ("min_detJ", C.c_double),
+                ("q_bound", C.c_double), ("setup_ms", C.c_double), ("eig_ms", C.c_double),
+                ("stencil_bytes", C.c_longlong)]
+
+
+class PCGOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("true_every", C.c_int),
+                ("prec_dtype", C.c_int), ("flexible", C.c_int), ("x0_given", C.c_int),
+                ("check_every", C.c_int)]
+
+
+class PCGInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("relres", C.c_double),
+                ("true_relres", C.c_double), ("true_checks", C.c_int)]
+
+
+_lib = None
+
+EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "igafd_get_eigen",
+           "igafd_copy_stencil", "igafd_apply_A", "igafd_apply_prec", "igafd_load_rhs_sine",
+           "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str"]
+
+
+def lib():
+    """Load libigafd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1602_01636_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    L.igafd_setup_patch.argtypes = [C.POINTER(PatchDesc), vp, C.POINTER(vp)]
+    L.igafd_destroy_patch.argtypes = [vp]
+    L.igafd_destroy_patch.restype = None
+    L.igafd_patch_query.argtypes = [vp, C.POINTER(PatchInfo)]
+    L.igafd_get_eigen.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.igafd_copy_stencil.argtypes = [vp, vp, vp]
+    L.igafd_apply_A.argtypes = [vp, vp, vp, vp]
+    L.igafd_apply_prec.argtypes = [vp, C.c_int, vp, vp, vp]
+    L.igafd_load_rhs_sine.argtypes = [vp, vp, vp]
+    L.igafd_pcg_solve.argtypes = [vp, C.POINTER(PCGOpts), vp, vp, C.POINTER(PCGInfo), vp]
+    L.igafd_pcg_default_opts.argtypes = [C.POINTER(PCGOpts)]
+    L.igafd_pcg_default_opts.restype = None
+    L.igafd_status_str.argtypes = [C.c_int]
+    L.igafd_status_str.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("igafd_destroy_patch", "igafd_pcg_default_opts", "igafd_status_str"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(st, what):
+    if st != OK:
+        raise IgafdError(st, what)
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_ptr(t, n=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Patch:
+    """A single-patch problem set up on the current CUDA device."""
+
+    def __init__(self, knots, p, ctrl, kappa=1.0, geo_knots=None, geo_p=None):
+        L = lib()
+        dim = len(knots)
+        geo_knots = knots if geo_knots is None else geo_knots
+        geo_p = p if geo_p is None else geo_p
+        self._keep = []
+        kn = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+        gk = [np.ascontiguousarray(k, dtype=np.float64) for k in geo_knots]
+        ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
+        self._keep += kn + gk + [ctrl]
+        dp = C.POINTER(C.c_double)
+        d = PatchDesc()
+        d.dim, d.p, d.geo_p, d.kappa = dim, p, geo_p, float(kappa)
+        d.n_knots = (C.c_int * dim)(*[len(k) for k in kn])
+        d.knots = (dp * dim)(*[k.ctypes.data_as(dp) for k in kn])
+        d.geo_n_knots = (C.c_int * dim)(*[len(k) for k in gk])
+        d.geo_knots = (dp * dim)(*[k.ctypes.data_as(dp) for k in gk])
+        d.ctrl = ctrl.ctypes.data_as(dp)
+        h = C.c_void_p()
+        _check(L.igafd_setup_patch(C.byref(d), _stream(), C.byref(h)), "setup_patch")
+        self.h = h
+        self.info = self.query()
+        self.dim = dim
+        self.n = tuple(self.info.n[k] for k in range(dim))
+        self.N = int(self.info.N)
+
+    @classmethod
+    def from_problem(cls, prob):
+        return cls(prob.knots, prob.p, prob.ctrl, prob.kappa)
+
+    def query(self):
+        info = PatchInfo()
+        _check(lib().igafd_patch_query(self.h, C.byref(info)), "patch_query")
+        return info
+
+    def eigen(self, k):
+        n = self.info.n[k]
+        U = np.empty((n, n))
+        D = np.empty(n)
+        dp = C.POINTER(C.c_double)
+        _check(lib().igafd_get_eigen(self.h, k, U.ctypes.data_as(dp), D.ctypes.data_as(dp)),
+               "get_eigen")
+        return D, U
+
+    def stencil(self):
+        import torch
+        out = torch.empty((self.info.n_offsets, self.N), dtype=torch.float64, device="cuda")
+        _check(lib().igafd_copy_stencil(self.h, C.c_void_p(out.data_ptr()), _stream()),
+               "copy_stencil")
+        return out
+
+    def apply_A(self, x, y=None):
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        _check(lib().igafd_apply_A(self.h, _dev_ptr(x, self.N), _dev_ptr(y, self.N), _stream()),
+               "apply_A")
+        return y
+
+    def apply_prec(self, r, z=None, dtype="fp64"):
+        import torch
+        z = torch.empty_like(r) if z is None else z
+        _check(lib().igafd_apply_prec(self.h, DTYPES[dtype], _dev_ptr(r, self.N),
+                                      _dev_ptr(z, self.N), _stream()), "apply_prec")
+        return z
+
+    def load_rhs_sine(self, b=None):
+        import torch
+        b = torch.empty(self.N, dtype=torch.float64, device="cuda") if b is None else b
+        _check(lib().igafd_load_rhs_sine(self.h, _dev_ptr(b, self.N), _stream()), "load_rhs")
+        return b
+
+    def pcg(self, b, x=None, tol=1e-8, max_iter=1000, dtype="fp64", flexible=None,
+            true_every=50, check_every=4, raise_on_error=True):
+        """Solve A x = b; returns (x, PCGInfo)."""
+        import torch
+        o = PCGOpts()
+        lib().igafd_pcg_default_opts(C.byref(o))
+        o.tol, o.max_iter, o.true_every, o.check_every = tol, max_iter, true_every, check_every
+        o.prec_dtype = DTYPES[dtype]
+        o.flexible = int(dtype != "fp64") if flexible is None else int(flexible)
+        o.x0_given = 0 if x is None else 1
+        x = torch.zeros_like(b) if x is None else x
+        info = PCGInfo()
+        st = lib().igafd_pcg_solve(self.h, C.byref(o), _dev_ptr(b, self.N), _dev_ptr(x, self.N),
+                                   C.byref(info), _stream())
+        if raise_on_error and st not in (OK, ERR_NOT_CONVERGED):
+            raise IgafdError(st, "pcg_solve")
+        return x, info
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().igafd_destroy_patch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

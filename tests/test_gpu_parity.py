@@ -1,0 +1,214 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances (FP64 path): the GPU and the oracle evaluate the same sums in a
+different order, so entries agree to a few ulps of the largest term:
+stencil 1e-13 of max|A|, products with A 1e-12 of max|y|, the FD apply
+1e-11 relative (two triangular-factor eigenbases, six dense products),
+PCG iterates and converged solutions 1e-10 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import assemble, fd, pcg
+from gpu_util import need_gpu, make_patch, to_dev, rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("2d-ragged", lambda: synth.Problem(2, (70, 45), 3)),
+    ("2d-p1", lambda: synth.Problem(2, (17, 9), 1)),
+    ("3d-deformed", lambda: synth.Problem(3, (13, 9, 11), 3, [0.05, -0.03, 0.02])),
+    ("3d-p2", lambda: synth.Problem(3, (10, 12, 7), 2, [0.08, 0.02, -0.04])),
+    ("3d-p4", lambda: synth.Problem(3, (9, 8, 10), 4, [-0.03, 0.04, 0.01])),
+]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+def case(request, torch):
+    prob = request.param[1]()
+    disc = assemble.Discretization.from_problem(prob)
+    S = disc.assemble_stencil()
+    patch = make_patch(prob)
+    yield prob, disc, S, patch
+    patch.close()
+
+
+def test_sizes(case):
+    prob, disc, S, patch = case
+    assert patch.n == tuple(disc.n)
+    assert patch.info.n_offsets == S.shape[0]
+
+
+def test_eigen_invariants_and_values(case):
+    prob, disc, S, patch = case
+    for k in range(prob.dim):
+        K, M = disc.pencil(k)
+        D, U = patch.eigen(k)
+        Do, _ = fd.generalized_eig(K, M)
+        assert np.abs(D - Do).max() <= 1e-12 * Do.max()
+        assert np.abs(U.T @ M @ U - np.eye(len(D))).max() <= 1e-12
+        assert np.abs(U.T @ K @ U - np.diag(D)).max() <= 1e-12 * D.max()
+
+
+def test_stencil_entries(case):
+    prob, disc, S, patch = case
+    Sg = patch.stencil().cpu().numpy()
+    assert np.abs(Sg - S).max() <= 1e-13 * np.abs(S).max()
+
+
+def test_apply_A(case):
+    prob, disc, S, patch = case
+    x = synth.random_vector(disc.N, 11)
+    y = patch.apply_A(to_dev(x)).cpu().numpy()
+    yo = assemble.apply_stencil(disc, S, x)
+    assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
+
+
+def test_apply_prec_fp64(case):
+    prob, disc, S, patch = case
+    F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
+    r = synth.random_vector(disc.N, 12)
+    z = patch.apply_prec(to_dev(r)).cpu().numpy()
+    assert rel(z, F.apply(r)) <= 1e-11
+
+
+def test_apply_prec_fp32(case):
+    prob, disc, S, patch = case
+    F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
+    r = synth.random_vector(disc.N, 13)
+    z = patch.apply_prec(to_dev(r), dtype="fp32").cpu().numpy()
+    assert rel(z, F.apply(r)) <= 1e-4
+
+
+def test_rhs_sine(case):
+    prob, disc, S, patch = case
+    f = {2: lambda x, y: 2 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y),
+         3: lambda x, y, z: 3 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)}
+    bo = disc.assemble_rhs(f[prob.dim])
+    b = patch.load_rhs_sine().cpu().numpy()
+    assert np.abs(b - bo).max() <= 1e-13 * np.abs(bo).max()
+
+
+def test_pcg_fixed_iterates(case):
+    """x_k after exactly k iterations (no stopping test) equals the oracle's."""
+    prob, disc, S, patch = case
+    A = assemble.stencil_to_csr(disc, S)
+    F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
+    b = synth.random_rhs(disc.N, 5)
+    k = 6
+    ro = pcg.pcg(lambda v: A @ v, b, F.apply, fixed_iters=k)
+    x, info = patch.pcg(to_dev(b), tol=0.0, max_iter=k)
+    assert info.iterations == k
+    assert rel(x.cpu().numpy(), ro.x) <= 1e-10
+
+
+def test_pcg_converged_solution(case):
+    prob, disc, S, patch = case
+    A = assemble.stencil_to_csr(disc, S)
+    F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
+    b = synth.random_rhs(disc.N, 6)
+    ro = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-13, max_iter=500)
+    assert ro.converged
+    x, info = patch.pcg(to_dev(b), tol=1e-12, max_iter=500)
+    assert info.status == 0 and info.true_relres <= 1e-12
+    assert rel(x.cpu().numpy(), ro.x) <= 1e-10
+    # the iteration count equals the oracle's at the same tolerance
+    r8 = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-8, max_iter=500)
+    _, i8 = patch.pcg(to_dev(b), tol=1e-8, max_iter=500)
+    assert i8.iterations == r8.iters
+
+
+def test_pcg_fp32_preconditioner(case):
+    prob, disc, S, patch = case
+    A = assemble.stencil_to_csr(disc, S)
+    F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
+    b = synth.random_rhs(disc.N, 7)
+    ro = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-13, max_iter=500)
+    r8 = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-8, max_iter=500)
+    x, info = patch.pcg(to_dev(b), tol=1e-8, max_iter=500, dtype="fp32")
+    assert info.status == 0
+    assert info.iterations <= r8.iters + 2
+    assert rel(x.cpu().numpy(), ro.x) <= 1e-7
+
+
+def test_identity_map_one_iteration(torch):
+    """Config-1 workload: 2D unit square, n = 64, p = 3: P = A, one iteration."""
+    prob = synth.unit_square(64, 3)
+    disc = assemble.Discretization.from_problem(prob)
+    patch = make_patch(prob)
+    b = patch.load_rhs_sine()
+    x, info = patch.pcg(b, tol=1e-8)
+    assert info.status == 0 and info.iterations == 1
+    S = disc.assemble_stencil()
+    A = assemble.stencil_to_csr(disc, S)
+    bo = disc.assemble_rhs(lambda x, y: 2 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y))
+    xo = np.linalg.solve(A.toarray(), bo)
+    assert rel(x.cpu().numpy(), xo) <= 1e-10
+    patch.close()
+
+
+def test_zero_rhs_and_errors(torch):
+    from paper_1602_01636_gb300 import igafd
+    prob = synth.Problem(3, (8, 7, 9), 2, [0.02, 0.01, -0.02])
+    patch = make_patch(prob)
+    b = torch.zeros(patch.N, dtype=torch.float64, device="cuda")
+    x, info = patch.pcg(b)
+    assert info.status == 0 and info.iterations == 0 and float(x.abs().max()) == 0.0
+    # iteration cap
+    b = to_dev(synth.random_rhs(patch.N, 1))
+    x, info = patch.pcg(b, tol=1e-14, max_iter=2, raise_on_error=False)
+    assert info.status == igafd.ERR_NOT_CONVERGED and info.iterations == 2
+    # non-finite right-hand side -> breakdown status, no trap
+    b[3] = float("nan")
+    x, info = patch.pcg(b, raise_on_error=False)
+    assert info.status == igafd.ERR_BREAKDOWN
+    patch.close()
+    # folded geometry is reported at set-up
+    bad = synth.Problem(3, (8, 8, 8), 2, [1.5, 1.5, 1.5])
+    with pytest.raises(igafd.IgafdError) as e:
+        make_patch(bad)
+    assert e.value.status == igafd.ERR_FOLDED
+
+
+def test_full_size_sampled(torch):
+    """3D deformed cube, n = 128, p = 3 (2.1M dofs, 5.75 GB stencil): sampled
+    stencil rows against the oracle's per-row assembly, the full FD apply
+    against the oracle's FD, and the FP64 solve's residual on sampled rows."""
+    prob = synth.deformed_cube(128, 3, seed=0)
+    disc = assemble.Discretization.from_problem(prob)
+    patch = make_patch(prob)
+    g = synth.rng(99)
+    rows = [tuple(int(v) for v in g.integers(0, 128, 3)) for _ in range(12)]
+    rows += [(0, 0, 0), (127, 127, 127), (0, 64, 127), (3, 2, 1)]
+    So = disc.assemble_rows(rows)
+    Sg = patch.stencil()
+    idx = torch.tensor([disc.row_index(i) for i in rows], device="cuda")
+    Sg_rows = Sg[:, idx].T.cpu().numpy()
+    del Sg
+    assert np.abs(Sg_rows - So).max() <= 1e-13 * np.abs(So).max()
+    F = fd.FD([disc.pencil(k) for k in range(3)])
+    r = synth.random_vector(disc.N, 21)
+    z = patch.apply_prec(to_dev(r)).cpu().numpy()
+    assert rel(z, F.apply(r)) <= 1e-11
+    b = synth.random_rhs(disc.N, 22)
+    x, info = patch.pcg(to_dev(b), tol=1e-8)
+    assert info.status == 0 and info.true_relres <= 1e-8
+    xh = x.cpu().numpy().reshape(128, 128, 128)
+    res = []
+    for r_i, i in enumerate(rows):
+        acc = 0.0
+        for o in range(343):
+            d1, d2, d3 = o % 7 - 3, (o // 7) % 7 - 3, o // 49 - 3
+            j = (i[0] + d1, i[1] + d2, i[2] + d3)
+            if all(0 <= j[k] < 128 for k in range(3)):
+                acc += So[r_i, o] * xh[j[2], j[1], j[0]]
+        res.append(b[disc.row_index(i)] - acc)
+    assert np.abs(res).max() <= 1e-6 * np.abs(b).max()
+    patch.close()
