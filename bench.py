@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark: PCG time-to-solution and preconditioner applies/s on the 3D
+deformed cube, n = 128 dofs per direction, p = 3 (2,097,152 dofs), relative
+residual 1e-8, mixed-precision FD preconditioner vs the FP64 one, on GB300.
+
+A step is one full PCG solve (stiffness stencil, FD preconditioner, vector
+updates, true-residual confirmation) on inputs already resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype fp32|bf16|fp16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, timed on host cores
+
+Multi-GPU (torchrun): replicas only (each rank solves its own copy; the
+method has no cross-GPU exchange on one patch here), max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG solve s and prec-applies/s, 3D n=128 p=3 @1e-8: mixed vs FP64 on GB300"
+UNIT = "s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default=None, help="FD dtype of the mixed solve")
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(n, p):
+    return (f"3D Poisson, deformed unit cube (seeded sine displacement, a_k~U(-0.05,0.05)), "
+            f"kappa=1, p={p}, n={n} dofs/direction ({n ** 3:,} dofs), A as a "
+            f"{(2 * p + 1) ** 3}-point FP64 stencil, manufactured RHS, PCG+FD tol 1e-8")
+
+
+# ----------------------------------------------------------------- oracle leg --
+class OracleSample:
+    """The FP64 CPU oracle on a bounded sample of the workload: its iteration
+    count from a full solve of the same recipe at n=16, and its per-iteration
+    cost measured at the full size (one FD apply, one stencil apply with the
+    full-size (2p+1)^3 x N coefficient array, five vector operations)."""
+
+    def __init__(self, n, p, tol):
+        import numpy as np
+        import synth
+        from oracle import assemble, fd, pcg
+        self.np, self.fd_mod, self.assemble = np, fd, assemble
+        small = synth.deformed_cube(16, p, seed=0)
+        ds = assemble.Discretization.from_problem(small)
+        A = assemble.stencil_to_csr(ds, ds.assemble_stencil())
+        Fs = fd.FD([ds.pencil(k) for k in range(3)])
+        f = lambda x, y, z: 3 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+        res = pcg.pcg(lambda v: A @ v, ds.assemble_rhs(f), Fs.apply, tol=tol)
+        self.iters = res.iters
+        prob = synth.deformed_cube(n, p, seed=0)
+        self.disc = assemble.Discretization.from_problem(prob)
+        self.F = fd.FD([self.disc.pencil(k) for k in range(3)])
+        self.S = np.ones((self.disc.n_offsets(), self.disc.N))
+        self.r = synth.random_vector(self.disc.N, 3)
+        self.cores = os.cpu_count()
+
+    def step(self):
+        np = self.np
+        t0 = time.perf_counter()
+        z = self.F.apply(self.r)
+        t1 = time.perf_counter()
+        y = self.assemble.apply_stencil(self.disc, self.S, self.r)
+        t2 = time.perf_counter()
+        x = np.zeros_like(self.r)
+        a = float(self.r @ y)
+        x += 1e-3 * z
+        r2 = self.r - 1e-3 * y
+        rr = float(r2 @ r2)
+        z2 = z + 1e-3 * x
+        t3 = time.perf_counter()
+        del a, rr, z2
+        per_it = (t1 - t0) + (t2 - t1) + (t3 - t2)
+        return self.iters * per_it, dict(fd_s=t1 - t0, stencil_s=t2 - t1, vec_s=t3 - t2)
+
+    def describe(self, parts):
+        return (f"oracle iteration count {self.iters} from its full n=16 solve of the same recipe; "
+                f"per-iteration cost timed at n={self.disc.n[0]}: FD apply {parts['fd_s']:.3f}s "
+                f"(numpy/BLAS), stencil apply {parts['stencil_s']:.3f}s, vector ops "
+                f"{parts['vec_s']:.3f}s; value = iterations x per-iteration cost (assembly excluded)")
+
+
+def cpu_baseline_entry(n, p, tol, reps=1):
+    o = OracleSample(n, p, tol)
+    vals, parts = [], None
+    for _ in range(reps):
+        v, parts = o.step()
+        vals.append(v)
+    v = statistics.median(vals)
+    return {"value": v, "unit": UNIT, "cores": o.cores, "kind": "oracle", "sample": o.describe(parts)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    o = OracleSample(args.n, args.p, args.tol)
+    for _ in range(args.warmup):
+        o.step()
+    vals, parts = [], None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, parts = o.step()
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.n, args.p), "n": args.n, "p": args.p,
+                       "tol": args.tol, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": o.cores, "kind": "oracle",
+                             "sample": o.describe(parts)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm ------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def start(self):
+        self.t_begin = self.t_end = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        for r in rows:
+            try:
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if self.t_begin and self.t_end and not (self.t_begin - 0.15 <= ts <= self.t_end + 0.15):
+                    continue
+                sm.append(float(r[2]))
+                mx = float(r[3])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[6:10]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id(torch):
+    """nvidia-smi identifier of the current device (UUID when available)."""
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        first = vis.split(",")[0].strip() if vis else ""
+        return first if first else str(torch.cuda.current_device())
+
+
+def stencil_traffic(p, n):
+    """dram bytes per launch of the stencil kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_1602_01636_gb300", "csrc", "stencil.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"stencil_n{n}_p{p}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_sha = re.search(r"stencil\.cu sha256\[:16\]:\s*([0-9a-f]+)", txt)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_tr or m_sha.group(1) != sha:
+        return None
+    return float(m_tr.group(1))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_1602_01636_gb300 import igafd, build as libbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    libbuild.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n, p = args.n, args.p
+    dtype = args.dtype or "fp32"
+    prob = synth.deformed_cube(n, p, seed=0)
+    patch = igafd.Patch.from_problem(prob)
+    N = patch.N
+    b = patch.load_rhs_sine()
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # FP64-preconditioned reference solve on the GPU (comparison leg)
+    patch.pcg(b, x, tol=args.tol, dtype="fp64")
+    e0, e1 = ev(), ev()
+    e0.record()
+    x64, inf64 = patch.pcg(b, torch.zeros_like(b), tol=args.tol, dtype="fp64", timing=True)
+    e1.record()
+    torch.cuda.synchronize()
+    fp64_s = e0.elapsed_time(e1) / 1e3
+
+    # mixed solve: warm-up, then K timed steps
+    for _ in range(args.warmup):
+        patch.pcg(b, x, tol=args.tol, dtype=dtype)
+    torch.cuda.synchronize()
+    clocks = Clocks(gpu_id(torch))
+    clocks.start()
+    time.sleep(1.0)   # let the sampler come up before the timed region
+    barrier()
+    torch.cuda.synchronize()
+    l0 = igafd.kernel_launches()
+    t0, t1 = ev(), ev()
+    infos = []
+    clocks.mark("t_begin")
+    t0.record()
+    for _ in range(args.steps):
+        _, inf = patch.pcg(b, x, tol=args.tol, dtype=dtype, timing=True)
+        infos.append(inf)
+    t1.record()
+    torch.cuda.synchronize()
+    clocks.mark("t_end")
+    barrier()
+    ck = clocks.stop()
+    launches = igafd.kernel_launches() - l0
+    ms_step = t0.elapsed_time(t1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    it_mixed = infos[-1].iterations
+    st_ms = sum(i.stencil_ms for i in infos) / sum(i.iterations for i in infos)
+    x_mixed = x.clone()
+    diff = float(torch.linalg.norm(x_mixed - x64) / torch.linalg.norm(x64))
+
+    # preconditioner applies/s (back-to-back, device-resident)
+    r = torch.randn(N, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+
+    def applies_per_s(dt, reps):
+        for _ in range(3):
+            patch.apply_prec(r, z, dtype=dt)
+        a, c = ev(), ev()
+        a.record()
+        for _ in range(reps):
+            patch.apply_prec(r, z, dtype=dt)
+        c.record()
+        torch.cuda.synchronize()
+        return reps / (a.elapsed_time(c) / 1e3)
+
+    aps_mixed = applies_per_s(dtype, 100)
+    aps_fp64 = applies_per_s("fp64", 20)
+
+    # end to end through the public API: pinned host b -> device, solve, x -> host
+    bh = b.cpu().pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    bd = torch.empty_like(b)
+    xd = torch.zeros_like(b)
+    for _ in range(2):
+        bd.copy_(bh, non_blocking=True)
+        patch.pcg(bd, xd, tol=args.tol, dtype=dtype)
+        xh.copy_(xd, non_blocking=True)
+    torch.cuda.synchronize()
+    a, c = ev(), ev()
+    a.record()
+    for _ in range(args.steps):
+        bd.copy_(bh, non_blocking=True)
+        patch.pcg(bd, xd, tol=args.tol, dtype=dtype)
+        xh.copy_(xd, non_blocking=True)
+    c.record()
+    torch.cuda.synchronize()
+    e2e_s = a.elapsed_time(c) / 1e3 / args.steps
+
+    # Roofline of the dominant kernel (the A stencil). Its FP64 FMAs are
+    # 2 per nonzero coupling; on GB300 the FP64 pipe (2 DFMA/clk/SM) binds
+    # before HBM, so the bound is ALU with peak 152 SMs x 2 FMA x 2 FLOP x
+    # max SM clock. The algorithmic bytes (full (2p+1)^3 row + x + y) are
+    # reported beside it against the measured HBM copy bandwidth.
+    cnt1 = [sum(min(i, p) + min(nk - 1 - i, p) + 1 for i in range(nk)) for nk in patch.n]
+    nnz = cnt1[0] * cnt1[1] * cnt1[2]
+    flops = 2.0 * nnz
+    st_s = st_ms / 1e3
+    bytes_per_row = (2 * p + 1) ** 3 * 8 + 16
+    alg_bytes = bytes_per_row * N
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sm_clk = peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = 152 * 2 * 2 * sm_clk * 1e6 / 1e12      # TFLOP/s
+    traffic = stencil_traffic(p, n)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_entry(n, p, args.tol)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms_step / 1e3, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f64+f32", "bf16": "f64+bf16", "fp16": "f64+f16", "fp64": "f64"}[dtype],
+            "data": "synthetic",
+            "config": {"workload": workload_name(n, p), "n": n, "p": p, "dofs": N, "tol": args.tol,
+                       "fd_dtype": dtype, "rhs": "manufactured u=sin(pi x)sin(pi y)sin(pi z)",
+                       "l2": "inputs larger than L2: the 5.75 GB stencil is streamed every iteration",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "iterations": {"mixed": it_mixed, "fp64": inf64.iterations},
+            "fp64_solve_s": fp64_s,
+            "prec_applies_per_s": {"mixed": aps_mixed, "fp64": aps_fp64},
+            "mixed_vs_fp64_solution_rel_diff": diff,
+            "true_relres": {"mixed": infos[-1].true_relres, "fp64": inf64.true_relres},
+            "setup_ms": patch.info.setup_ms, "eig_ms": patch.info.eig_ms,
+            "phase_ms_per_step": {"stencil": sum(i.stencil_ms for i in infos) / len(infos),
+                                  "prec": sum(i.prec_ms for i in infos) / len(infos)},
+            "roofline": {"bound": "alu", "kernel": "stencil_kernel (q = A p, fused (p, q))",
+                         "achieved": flops / st_s / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": flops / st_s / 1e12 / fp64_peak, "traffic": traffic,
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x sm_max_mhz",
+                         "flops_per_launch": flops, "launch_ms": st_ms,
+                         "hbm": {"achieved": alg_bytes / st_s / 1e9, "peak": hbm_peak,
+                                 "unit": "GB/s", "frac": alg_bytes / st_s / 1e9 / hbm_peak,
+                                 "peak_source": hbm_src + " (hbm_gbs)",
+                                 "alg_bytes_per_launch": alg_bytes}},
+            "clocks": ck,
+            "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+                    "d2h_bytes_per_step": 8 * N},
+            "gpu_launches": launches,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    patch.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

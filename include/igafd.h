@@ -96,6 +96,9 @@ typedef struct {
   int check_every;     /* host polls the device convergence flag every this
                           many iterations (>= 1); later iterations are skipped
                           on the device once converged, so x is unaffected */
+  int timing;          /* 1: record CUDA events around the A stencil and the
+                          FD apply of every iteration (fills the *_ms fields
+                          of igafd_pcg_info); polls at most every 32 iterations */
 } igafd_pcg_opts;
 
 typedef struct {
@@ -104,6 +107,9 @@ typedef struct {
   double relres;       /* final recurrence ||r||/||b|| */
   double true_relres;  /* final ||b - A x|| / ||b|| */
   int true_checks;     /* true-residual recomputations performed */
+  double solve_ms;     /* device time of the whole solve (timing = 1) */
+  double stencil_ms;   /* summed device time of the in-loop A products */
+  double prec_ms;      /* summed device time of the in-loop FD applies */
 } igafd_pcg_info;
 
 /* Build a patch: 1D pencils K_k, M_k by (p+1)-point Gauss quadrature
@@ -162,10 +168,14 @@ igafd_status igafd_pcg_solve(igafd_patch *patch, const igafd_pcg_opts *opts,
                              igafd_pcg_info *info, void *stream);
 
 /* Default options: tol 1e-8, max_iter 1000, true_every 50, FP64,
- * Fletcher-Reeves, x0 = 0, check_every 4. */
+ * Fletcher-Reeves, x0 = 0, check_every 4, timing off. */
 void igafd_pcg_default_opts(igafd_pcg_opts *opts);
 
 const char *igafd_status_str(igafd_status s);
+
+/* Number of kernels this library has enqueued in this process so far (all
+ * devices, all patches); for launch accounting by benchmarks. */
+long long igafd_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -58,6 +58,8 @@ void free_patch(igafd_patch *P) {
   cudaFree(P->r); cudaFree(P->z); cudaFree(P->pv); cudaFree(P->q); cudaFree(P->xt);
   cudaFree(P->partial); cudaFree(P->counter); cudaFree(P->scal); cudaFree(P->err_flag);
   igafd_fd_tc_free(P);
+  for (int i = 0; i < IGAFD_NEV; ++i)
+    if (P->ev[i]) cudaEventDestroy(P->ev[i]);
   if (P->host_scal) cudaFreeHost(P->host_scal);
   if (cur >= 0) cudaSetDevice(cur);
   free(P);
@@ -100,6 +102,7 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
     P->host_scal = nullptr;
     return IGAFD_ERR_OOM;
   }
+  for (int i = 0; i < IGAFD_NEV; ++i) IGAFD_CUDA(cudaEventCreate(&P->ev[i]));
   IGAFD_CUDA(cudaMemsetAsync(P->counter, 0, 8 * sizeof(unsigned), s));
   IGAFD_CUDA(cudaMemsetAsync(P->scal, 0, (S_COUNT + 1) * sizeof(double), s));
   IGAFD_TRY(igafd_setup_pencils_eig(P, s));
@@ -128,6 +131,7 @@ extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *strea
     if (!valid_open_knots(d->knots[k], d->n_knots[k], d->p)) return IGAFD_ERR_ARG;
     if (!valid_open_knots(d->geo_knots[k], d->geo_n_knots[k], d->geo_p)) return IGAFD_ERR_ARG;
     if (d->n_knots[k] - d->p - 1 < 3) return IGAFD_ERR_ARG;   // at least one interior dof
+    if (d->n_knots[k] - d->p - 3 > 1024) return IGAFD_ERR_ARG; // eigen-solver limit
   }
   igafd_patch *P = (igafd_patch *)calloc(1, sizeof(igafd_patch));
   if (!P) return IGAFD_ERR_OOM;

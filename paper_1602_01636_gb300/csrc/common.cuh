@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 
@@ -9,6 +10,7 @@
 
 #define IGAFD_MAXP 7
 #define IGAFD_MAXDIM 3
+#define IGAFD_NEV 130   // 4 per iteration for 32 iterations + 2
 
 // Return IGAFD_ERR_CUDA from the enclosing function when a runtime call fails.
 #define IGAFD_CUDA(call)                                                   \
@@ -86,6 +88,7 @@ struct igafd_patch {
   double *scal;                 // [S_COUNT]
   double *host_scal;            // pinned mirror of scal
   FDMixed *mixed;
+  cudaEvent_t ev[IGAFD_NEV];    // phase-timing events (PCG with timing on)
   // diagnostics
   double min_detJ, q_bound, setup_ms, eig_ms;
   int *err_flag;                // device error flags from setup kernels
@@ -111,6 +114,10 @@ void igafd_fd_tc_free(igafd_patch *P);
 // y = A x (b == null) or y = b - A x; see stencil.cu
 igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
                                   int pcg, int skip_done, cudaStream_t s);
+
+// Kernels enqueued by this library (process-wide), for launch accounting.
+extern std::atomic<long long> g_igafd_launches;
+#define IGAFD_LAUNCHED(n) g_igafd_launches.fetch_add((n), std::memory_order_relaxed)
 
 // ---- device helpers ---------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {

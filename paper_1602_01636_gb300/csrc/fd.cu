@@ -101,6 +101,7 @@ template <typename TA, typename TB, typename TC, typename ACC>
 igafd_status launch_gemm(const GemmArgs &g, cudaStream_t s) {
   dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.batch);
   mode_gemm_kernel<TA, TB, TC, ACC><<<grid, 256, 0, s>>>(g);
+  IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }

@@ -191,7 +191,12 @@ extern "C" void igafd_pcg_default_opts(igafd_pcg_opts *o) {
   o->flexible = 0;
   o->x0_given = 0;
   o->check_every = 4;
+  o->timing = 0;
 }
+
+std::atomic<long long> g_igafd_launches{0};
+
+extern "C" long long igafd_kernel_launches(void) { return g_igafd_launches.load(); }
 
 static igafd_status read_scalars(igafd_patch *P, cudaStream_t s) {
   IGAFD_CUDA(cudaMemcpyAsync(P->host_scal, P->scal, S_COUNT * sizeof(double),
@@ -217,9 +222,15 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
   const double tol2 = o.tol * o.tol;
   const int flex = o.flexible ? 1 : 0;
   igafd_pcg_info inf{};
+  const bool timing = o.timing != 0;
+  if (timing && o.check_every > 32) o.check_every = 32;
+  cudaEvent_t *ev = P->ev;
+  if (timing) IGAFD_CUDA(cudaEventRecord(ev[IGAFD_NEV - 2], s));
 
   init_scalars_kernel<<<1, 32, 0, s>>>(scal);
+  IGAFD_LAUNCHED(1);
   norm2_kernel<<<G, B, 0, s>>>(b, N, scal, S_BB, P->partial, P->counter);
+  IGAFD_LAUNCHED(1);
   // r0 = b - A x0
   if (o.x0_given) {
     IGAFD_TRY(igafd_stencil_launch(P, x, P->r, b, 1, 0, s));
@@ -245,6 +256,7 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
   // z0 = P^{-1} r0, rho0 = (r0, z0), p0 = z0
   IGAFD_TRY(fd_apply(P, o.prec_dtype, P->r, P->z, s, nullptr));
   dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 1, flex, 0);
+  IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaMemcpyAsync(P->pv, P->z, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   IGAFD_CUDA(cudaGetLastError());
 
@@ -257,19 +269,35 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
     for (int c = 0; c < chunk; ++c) {
       ++k;
       // q = A p, alpha = rho / (p, q)
+      if (timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c], s));
       IGAFD_TRY(igafd_stencil_launch(P, P->pv, P->q, nullptr, 1, 1, s));
+      if (timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 1], s));
       update_xr_kernel<<<G, B, 0, s>>>(x, P->r, P->pv, P->q, P->z, N, scal, P->partial,
                                        P->counter, tol2, flex);
+  IGAFD_LAUNCHED(1);
       if (o.true_every > 0 && k % o.true_every == 0) {
         IGAFD_TRY(igafd_stencil_launch(P, x, P->r, b, 1, 1, s));
         ++inf.true_checks;
       }
+      if (timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 2], s));
       IGAFD_TRY(fd_apply(P, o.prec_dtype, P->r, P->z, s, done));
+      if (timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 3], s));
       dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, flex, 1);
+  IGAFD_LAUNCHED(1);
       update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 1);
+  IGAFD_LAUNCHED(1);
       IGAFD_CUDA(cudaGetLastError());
     }
     IGAFD_TRY(read_scalars(P, s));
+    if (timing) {
+      for (int c = 0; c < chunk; ++c) {
+        float a = 0.f, b2 = 0.f;
+        cudaEventElapsedTime(&a, ev[4 * c], ev[4 * c + 1]);
+        cudaEventElapsedTime(&b2, ev[4 * c + 2], ev[4 * c + 3]);
+        inf.stencil_ms += a;
+        inf.prec_ms += b2;
+      }
+    }
     const double *h = P->host_scal;
     if (h[S_DONE] != 0.0) {
       rec_rr = h[S_RR];
@@ -289,9 +317,12 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
       // not confirmed: continue from the true residual
       if ((int)h[S_ITER] >= o.max_iter) { finished = true; break; }
       set_scalar_kernel<<<1, 32, 0, s>>>(scal, S_DONE, 0.0);
+  IGAFD_LAUNCHED(1);
       IGAFD_TRY(fd_apply(P, o.prec_dtype, P->r, P->z, s, nullptr));
       dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, flex, 0);
+  IGAFD_LAUNCHED(1);
       update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 0);
+  IGAFD_LAUNCHED(1);
       IGAFD_CUDA(cudaGetLastError());
       k = (int)h[S_ITER];
     }
@@ -307,6 +338,13 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
   }
   inf.true_relres = sqrt(P->host_scal[S_TRUE_RR] / bb);
   inf.status = status;
+  if (timing) {
+    IGAFD_CUDA(cudaEventRecord(ev[IGAFD_NEV - 1], s));
+    IGAFD_CUDA(cudaEventSynchronize(ev[IGAFD_NEV - 1]));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[IGAFD_NEV - 2], ev[IGAFD_NEV - 1]);
+    inf.solve_ms = t;
+  }
   if (info) *info = inf;
   return status;
 }

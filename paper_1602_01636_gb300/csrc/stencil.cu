@@ -126,6 +126,7 @@ igafd_status launch_p(int p, dim3 grid, cudaStream_t s, const double *S, const d
   case PP:                                                                               \
     stencil_kernel<DIM, PP, MODE><<<grid, 256, 0, s>>>(S, x, y, b, n[0], n[1], n[2], N,  \
                                                         partial, counter, scal, pcg, done); \
+    IGAFD_LAUNCHED(1);                                                                   \
     break;
   switch (p) {
     IGAFD_CASE(1)

@@ -50,19 +50,21 @@ class PatchInfo(C.Structure):
 class PCGOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("true_every", C.c_int),
                 ("prec_dtype", C.c_int), ("flexible", C.c_int), ("x0_given", C.c_int),
-                ("check_every", C.c_int)]
+                ("check_every", C.c_int), ("timing", C.c_int)]
 
 
 class PCGInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("relres", C.c_double),
-                ("true_relres", C.c_double), ("true_checks", C.c_int)]
+                ("true_relres", C.c_double), ("true_checks", C.c_int),
+                ("solve_ms", C.c_double), ("stencil_ms", C.c_double), ("prec_ms", C.c_double)]
 
 
 _lib = None
 
 EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "igafd_get_eigen",
            "igafd_copy_stencil", "igafd_apply_A", "igafd_apply_prec", "igafd_load_rhs_sine",
-           "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str"]
+           "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str",
+           "igafd_kernel_launches"]
 
 
 def lib():
@@ -89,11 +91,19 @@ def lib():
     L.igafd_pcg_default_opts.restype = None
     L.igafd_status_str.argtypes = [C.c_int]
     L.igafd_status_str.restype = C.c_char_p
+    L.igafd_kernel_launches.argtypes = []
+    L.igafd_kernel_launches.restype = C.c_longlong
     for name in EXPORTS:
-        if name not in ("igafd_destroy_patch", "igafd_pcg_default_opts", "igafd_status_str"):
+        if name not in ("igafd_destroy_patch", "igafd_pcg_default_opts", "igafd_status_str",
+                        "igafd_kernel_launches"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
+
+
+def kernel_launches():
+    """Kernels the library has enqueued in this process so far."""
+    return int(lib().igafd_kernel_launches())
 
 
 def _check(st, what):
@@ -190,16 +200,18 @@ class Patch:
         _check(lib().igafd_load_rhs_sine(self.h, _dev_ptr(b, self.N), _stream()), "load_rhs")
         return b
 
-    def pcg(self, b, x=None, tol=1e-8, max_iter=1000, dtype="fp64", flexible=None,
-            true_every=50, check_every=4, raise_on_error=True):
-        """Solve A x = b; returns (x, PCGInfo)."""
+    def pcg(self, b, x=None, x0=False, tol=1e-8, max_iter=1000, dtype="fp64", flexible=None,
+            true_every=50, check_every=4, timing=False, raise_on_error=True):
+        """Solve A x = b; returns (x, PCGInfo). x is the output buffer (allocated
+        when None); its contents are the initial guess only when x0=True."""
         import torch
         o = PCGOpts()
         lib().igafd_pcg_default_opts(C.byref(o))
         o.tol, o.max_iter, o.true_every, o.check_every = tol, max_iter, true_every, check_every
         o.prec_dtype = DTYPES[dtype]
         o.flexible = int(dtype != "fp64") if flexible is None else int(flexible)
-        o.x0_given = 0 if x is None else 1
+        o.x0_given = int(bool(x0) and x is not None)
+        o.timing = int(bool(timing))
         x = torch.zeros_like(b) if x is None else x
         info = PCGInfo()
         st = lib().igafd_pcg_solve(self.h, C.byref(o), _dev_ptr(b, self.N), _dev_ptr(x, self.N),
