@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only set-up, warm-up and the timed mixed solves (for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -252,6 +254,17 @@ def run_ours(args):
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
+
+    if args.profile:
+        for _ in range(args.warmup):
+            patch.pcg(b, x, tol=args.tol, dtype=dtype)
+        for _ in range(args.steps):
+            _, inf = patch.pcg(b, x, tol=args.tol, dtype=dtype)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "iterations": inf.iterations, "n": n, "p": p,
+                          "fd_dtype": dtype}), flush=True)
+        patch.close()
+        return
 
     # FP64-preconditioned reference solve on the GPU (comparison leg)
     patch.pcg(b, x, tol=args.tol, dtype="fp64")
