@@ -173,6 +173,28 @@ void igafd_pcg_default_opts(igafd_pcg_opts *opts);
 
 const char *igafd_status_str(igafd_status s);
 
+/* Fast-diagonalization apply z = P^{-1} r in FP64 that allocates no memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (code running while another library owns all device
+ * memory through its own pool, latency-critical loops that cannot accept an
+ * allocation's implicit device synchronisation, plugins handed buffers but no
+ * allocation rights). The caller passes everything: dim (2 or 3), n[dim]
+ * (host) dofs per direction, U[dim] and D[dim] (host arrays of device
+ * pointers to U_k, row-major n_k x n_k with U[k][i*n_k + j] = (U_k)_{ij}, and
+ * to the eigenvalues D_k, e.g. as returned by igafd_get_eigen), r and z
+ * (device, length N, not overlapping). The two intermediate tensors live in
+ * a file-scope static device array of 2 * IGAFD_STATIC_FD_MAX_DOFS doubles
+ * (16 MiB), which every GPU that loads the library holds until the process
+ * exits. N = prod n_k above IGAFD_STATIC_FD_MAX_DOFS returns IGAFD_ERR_ARG
+ * (with a message on stderr). The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and caches
+ * it; make that first call before any stream capture. All calls share the
+ * array, so calls whose kernels overlap on the GPU race: serialise them. */
+#define IGAFD_STATIC_FD_MAX_DOFS 1048576
+igafd_status igafd_apply_prec_static(int dim, const int *n, const double *const *U,
+                                     const double *const *D, const double *r_dev,
+                                     double *z_dev, void *stream);
+
 /* Number of kernels this library has enqueued in this process so far (all
  * devices, all patches); for launch accounting by benchmarks. */
 long long igafd_kernel_launches(void);
