@@ -55,7 +55,8 @@ void free_patch(igafd_patch *P) {
   }
   cudaFree(P->ctrl); cudaFree(P->inv_lam); cudaFree(P->inv_lam32); cudaFree(P->stencil);
   cudaFree(P->fd_a); cudaFree(P->fd_b);
-  cudaFree(P->r); cudaFree(P->z); cudaFree(P->pv); cudaFree(P->q); cudaFree(P->xt);
+  cudaFree(P->r); cudaFree(P->z); cudaFree(P->pv_base); cudaFree(P->xpad_base);
+  cudaFree(P->q); cudaFree(P->xt);
   cudaFree(P->partial); cudaFree(P->counter); cudaFree(P->scal); cudaFree(P->err_flag);
   igafd_fd_tc_free(P);
   for (int i = 0; i < IGAFD_NEV; ++i)
@@ -84,12 +85,19 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
   }
   IGAFD_TRY(alloc(&P->inv_lam, (size_t)N));
   IGAFD_TRY(alloc(&P->inv_lam32, (size_t)N));
-  IGAFD_TRY(alloc(&P->stencil, (size_t)P->n_off * N));
+  P->Np = igafd_stencil_row_stride(N);
+  IGAFD_TRY(alloc(&P->stencil, (size_t)P->n_off * P->Np));
   IGAFD_TRY(alloc(&P->fd_a, (size_t)N));
   IGAFD_TRY(alloc(&P->fd_b, (size_t)N));
   IGAFD_TRY(alloc(&P->r, (size_t)N));
   IGAFD_TRY(alloc(&P->z, (size_t)N));
-  IGAFD_TRY(alloc(&P->pv, (size_t)N));
+  P->halo = igafd_stencil_halo(P->p, P->n);
+  IGAFD_TRY(alloc(&P->pv_base, (size_t)(N + 2 * P->halo)));
+  IGAFD_TRY(alloc(&P->xpad_base, (size_t)(N + 2 * P->halo)));
+  IGAFD_CUDA(cudaMemsetAsync(P->pv_base, 0, (N + 2 * P->halo) * sizeof(double), s));
+  IGAFD_CUDA(cudaMemsetAsync(P->xpad_base, 0, (N + 2 * P->halo) * sizeof(double), s));
+  P->pv = P->pv_base + P->halo;
+  P->xpad = P->xpad_base + P->halo;
   IGAFD_TRY(alloc(&P->q, (size_t)N));
   IGAFD_TRY(alloc(&P->xt, (size_t)N));
   IGAFD_TRY(alloc(&P->partial, (size_t)IGAFD_PARTIAL_SLOTS * IGAFD_RED_BLOCKS));
@@ -139,7 +147,8 @@ extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *strea
   P->p = d->p;
   P->geo_p = d->geo_p;
   P->kappa = d->kappa;
-  if (cudaGetDevice(&P->dev) != cudaSuccess) {
+  if (cudaGetDevice(&P->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev) != cudaSuccess) {
     free(P);
     return IGAFD_ERR_CUDA;
   }
@@ -207,8 +216,9 @@ extern "C" igafd_status igafd_get_eigen(const igafd_patch *P, int k, double *U_h
 extern "C" igafd_status igafd_copy_stencil(const igafd_patch *P, double *dst, void *stream) {
   if (!P || !dst) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
-  IGAFD_CUDA(cudaMemcpyAsync(dst, P->stencil, (size_t)P->n_off * P->N * sizeof(double),
-                             cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  IGAFD_CUDA(cudaMemcpy2DAsync(dst, P->N * sizeof(double), P->stencil, P->Np * sizeof(double),
+                               P->N * sizeof(double), P->n_off, cudaMemcpyDeviceToDevice,
+                               (cudaStream_t)stream));
   return IGAFD_OK;
 }
 

@@ -77,12 +77,18 @@ struct igafd_patch {
   float *U32[3];
   double *inv_lam;
   float *inv_lam32;
-  // stiffness stencil [n_off][N]
+  // stiffness stencil [n_off][Np], Np = N rounded up to the stencil tile
   double *stencil;
+  long long Np;
+  int num_sms;
   // FD workspace
   double *fd_a, *fd_b;          // N each
   // PCG workspace
-  double *r, *z, *pv, *q, *xt;  // N each (xt: true-residual scratch)
+  double *r, *z, *q, *xt;       // N each (xt: true-residual scratch)
+  // zero-padded vectors read by the stencil (halo elements on both ends):
+  // pv = PCG search direction, xpad = copy of a caller's x
+  double *pv, *xpad, *pv_base, *xpad_base;
+  long long halo;
   double *partial;              // [PARTIAL_SLOTS][MAX_BLOCKS]
   unsigned int *counter;        // last-block counters
   double *scal;                 // [S_COUNT]
@@ -114,6 +120,8 @@ void igafd_fd_tc_free(igafd_patch *P);
 // y = A x (b == null) or y = b - A x; see stencil.cu
 igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
                                   int pcg, int skip_done, cudaStream_t s);
+long long igafd_stencil_row_stride(long long N);   // Np for a given N
+long long igafd_stencil_halo(int p, const int *n);   // zero halo of padded vectors
 
 // Kernels enqueued by this library (process-wide), for launch accounting.
 extern std::atomic<long long> g_igafd_launches;

@@ -318,7 +318,7 @@ __global__ void geo_check_kernel(PV v, long long nqp, double *part) {
 // direction per output entry.
 template <int DIM>
 __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
-                                double *__restrict__ stencil, long long N) {
+                                double *__restrict__ stencil, long long Np) {
   extern __shared__ double sm[];
   const int p = v.p, A = p + 1, nq = p + 1, W = 2 * p + 1;
   const int nqd = DIM == 3 ? nq * nq * nq : nq * nq;
@@ -447,7 +447,7 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
     }
     int o = 0, ws = 1;
     for (int k = 0; k < DIM; ++k) { o += (dl[k] + p) * ws; ws *= W; }
-    stencil[(size_t)o * N + row] += val;
+    stencil[(size_t)o * Np + row] += val;
   }
   (void)Nn1; (void)Nn2;
 #undef FV
@@ -601,7 +601,7 @@ igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s) {
   P->q_bound = lmax / lmin;
   if (!(mdet > 0.0)) return IGAFD_ERR_FOLDED;
   // stiffness stencil
-  IGAFD_CUDA(cudaMemsetAsync(P->stencil, 0, (size_t)P->n_off * P->N * sizeof(double), s));
+  IGAFD_CUDA(cudaMemsetAsync(P->stencil, 0, (size_t)P->n_off * P->Np * sizeof(double), s));
   size_t smem = assemble_smem(dim, p);
   if (smem > 200 * 1024) return IGAFD_ERR_ARG;
   if (dim == 3) {
@@ -621,9 +621,9 @@ igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s) {
         long long nb = (long long)ne1 * ne2 * ne3;
         if (nb == 0) continue;
         if (dim == 3)
-          assemble_kernel<3><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, P->N);
+          assemble_kernel<3><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, P->Np);
         else
-          assemble_kernel<2><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, 0, ne1, ne2, P->stencil, P->N);
+          assemble_kernel<2><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, 0, ne1, ne2, P->stencil, P->Np);
         IGAFD_CUDA(cudaGetLastError());
       }
   return IGAFD_OK;

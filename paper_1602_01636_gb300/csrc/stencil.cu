@@ -1,24 +1,72 @@
 // y = A x with A stored as a (2p+1)^d-point FP64 stencil, offset-major:
-// S[o][row], o = sum_k (delta_k + p)(2p+1)^(k-1) (Section 2.1: an interior
-// row of A couples to (2p+1)^d columns). Also r = b - A x (true residual).
+// S[o][row] with row stride Np (N rounded up to the tile), o = sum_k
+// (delta_k + p)(2p+1)^(k-1) (Section 2.1: an interior row of A couples to
+// (2p+1)^d columns). Also r = b - A x (true residual).
 //
-// One thread per row (grid-stride over a fixed grid that is a multiple of the
-// SM count); coefficients are streamed once (evict-first loads), x is read
-// through the read-only cache (it stays resident in L2). Couplings that leave
-// the index box are skipped, so x is never read out of bounds. Optional
-// fused partial dot products with a deterministic last-block reduction.
+// On GB300 the 343 FP64 FMAs of a p = 3 row take longer on the FP64 pipe
+// (2 FMA/clk/SM) than its 2.7 KB of coefficients take to stream from HBM, so
+// the kernel is built to keep the FP64 pipe fed from shared memory: a
+// persistent grid of CTAs walks 256-row tiles; for every (delta_2, delta_3)
+// group a producer warp brings the 2p+1 coefficient runs of the tile
+// (contiguous 2 KB each) and the contiguous window of x they multiply into a
+// shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion
+// on mbarriers), several groups ahead of the eight compute warps. x is read
+// from a copy with a zero halo of p planes on both ends, and couplings that
+// leave the index box are stored as 0, so every row runs the same
+// branch-free (2p+1)^d FMAs and no read leaves the allocation. Every
+// mbarrier wait is bounded: on timeout the kernel records an error, waits
+// (bounded) for its own copies and returns. Optional fused dot with a
+// deterministic last-block reduction.
 #include "common.cuh"
 
 namespace {
 
-__device__ __forceinline__ double ld_stream(const double *p) {
-  double v;
-  asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
-  return v;
+constexpr int kTile = 256;     // rows per tile = threads per CTA
+constexpr int kStages = 4;     // groups in flight per CTA
+constexpr long long kSpin = 1ll << 26;   // mbarrier poll limit (~seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (long long i = 0; i < kSpin; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
 // Last block of a grid-stride reduction: returns true in every thread of the
-// block that finished last (all partials visible), resets the counter.
+// block that finished last (all partials visible).
 __device__ __forceinline__ bool last_block(unsigned int *counter) {
   __shared__ bool am_last;
   __threadfence();
@@ -37,74 +85,179 @@ __device__ double sum_partials(const double *part, int n, double *sh32) {
   return block_sum(v, sh32);
 }
 
-// mode 0: y = A x, partial (x, y) -> alpha = rho / (x, y) (PCG step) when
-//         scal != null; mode 1: y = b - A x, partial (y, y) -> true (r, r).
+struct StencilArgs {
+  const double *S;    // [n_off][Np]
+  const double *x;    // interior pointer of a zero-padded vector (halo H)
+  double *y;
+  const double *b;    // MODE 1
+  int n1, n2, n3;
+  long long N, Np;
+  long long ntiles;
+  double *partial;    // null: no dot
+  unsigned *counter;
+  double *scal;       // PCG scalars (pcg != 0)
+  int pcg;
+  const double *done; // skip when *done != 0
+  int *err;           // set on an mbarrier timeout
+};
+
+template <int P>
+struct Geom {
+  static constexpr int W = 2 * P + 1;
+  static constexpr int XW = (kTile + 2 * P + 2 + 1) & ~1;   // x window (even count)
+  static constexpr int STAGE = W * kTile + XW;               // doubles per ring stage
+};
+
+// Warp-specialised pipeline: warps 0..7 compute one row each per tile;
+// warp 8 (one elected lane) streams, for every (delta_2, delta_3) group, the
+// 2p+1 coefficient runs of the tile and the x window they multiply into a
+// ring of kStages shared-memory stages (full/empty mbarriers). The FP64 FMAs
+// read both operands from shared memory.
+//
+// MODE 0: y = A x, dot (x, y) -> alpha = rho / (x, y) when pcg.
+// MODE 1: y = b - A x, dot (y, y) -> true (r, r) when pcg.
 template <int DIM, int P, int MODE>
-__global__ void __launch_bounds__(256) stencil_kernel(const double *__restrict__ S,
-                                                      const double *__restrict__ x,
-                                                      double *__restrict__ y,
-                                                      const double *__restrict__ b, int n1, int n2,
-                                                      int n3, long long N, double *partial,
-                                                      unsigned int *counter, double *scal,
-                                                      int pcg, const double *done) {
-  if (done && *done != 0.0) return;
-  constexpr int W = 2 * P + 1;
-  const long long n12 = (long long)n1 * n2;
+__global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) {
+  if (a.done && *a.done != 0.0) return;
+  using Gm = Geom<P>;
+  constexpr int W = Gm::W;
+  constexpr int G = DIM == 3 ? W * W : W;        // (delta_2, delta_3) groups per tile
+  constexpr uint32_t kStageBytes = Gm::STAGE * sizeof(double);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double *ring = reinterpret_cast<double *>(smem_raw);              // [kStages][STAGE]
+  uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * Gm::STAGE);
+  uint64_t *empty = full + kStages;
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long my_tiles =
+      a.ntiles > blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long total = my_tiles * G;
+  const long long n12 = (long long)a.n1 * a.n2;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kTile / 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncthreads();
+
   double dot = 0.0;
-  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < N;
-       row += (long long)gridDim.x * blockDim.x) {
-    const int i1 = (int)(row % n1);
-    const int i2 = (int)((row / n1) % n2);
-    const int i3 = DIM == 3 ? (int)(row / n12) : 0;
+  if (warp == kTile / 32) {
+    // ---------------- producer warp ----------------
+    if (lane == 0) {
+      long long issued = 0;
+      bool ok = true;
+      for (long long s = 0; s < total && ok; ++s) {
+        const int slot = (int)(s % kStages);
+        if (s >= kStages) {
+          const uint32_t par = (uint32_t)(((s / kStages) - 1) & 1);
+          long long it = 0;
+          while (!mbar_try_wait(&empty[slot], par)) {
+            if (s_abort || ++it > kSpin) { ok = false; break; }
+          }
+          if (!ok) break;
+        }
+        const long long tile = blockIdx.x + (s / G) * (long long)gridDim.x;
+        const int g = (int)(s % G);
+        const int d2 = g % W - P, d3 = DIM == 3 ? g / W - P : 0;
+        const int ob = (DIM == 3 ? (d3 + P) * W * W : 0) + (d2 + P) * W;
+        const long long row0 = tile * kTile;
+        long long x0 = row0 + (long long)d3 * n12 + (long long)d2 * a.n1 - P;
+        x0 -= (x0 & 1);                                   // 16-byte aligned start
+        double *st = ring + (size_t)slot * Gm::STAGE;
+        uint64_t *bar = &full[slot];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_tx(bar, kStageBytes);
+        for (int d1 = 0; d1 < W; ++d1)
+          bulk_g2s(st + d1 * kTile, a.S + (size_t)(ob + d1) * a.Np + row0, kTile * sizeof(double), bar);
+        bulk_g2s(st + W * kTile, a.x + x0, Gm::XW * sizeof(double), bar);
+        ++issued;
+      }
+      if (!ok) {
+        s_abort = 1;
+        atomicExch(a.err, (int)IGAFD_ERR_TIMEOUT);
+      }
+      // never leave with copies in flight: wait (bounded) for the last stages issued
+      for (long long q = issued - kStages > 0 ? issued - kStages : 0; q < issued; ++q)
+        mbar_wait(&full[q % kStages], (uint32_t)((q / kStages) & 1));
+    }
+  } else {
+    // ---------------- compute warps ----------------
     double acc0 = 0.0, acc1 = 0.0;
-    const int lo1 = max(-P, -i1), hi1 = min(P, n1 - 1 - i1);
-#pragma unroll 1
-    for (int d3 = (DIM == 3 ? -P : 0); d3 <= (DIM == 3 ? P : 0); ++d3) {
-      if (DIM == 3 && (i3 + d3 < 0 || i3 + d3 >= n3)) continue;
-#pragma unroll 1
-      for (int d2 = -P; d2 <= P; ++d2) {
-        if (i2 + d2 < 0 || i2 + d2 >= n2) continue;
-        const long long base = row + (long long)d3 * n12 + (long long)d2 * n1;
-        const int ob = (DIM == 3 ? (d3 + P) * W * W : 0) + (d2 + P) * W + P;
-        const double *Srow = S + (long long)ob * N + row;
-        if (lo1 == -P && hi1 == P) {
+    long long row = 0;
+    bool live = false;
+    for (long long s = 0; s < total; ++s) {
+      const int g = (int)(s % G);
+      if (g == 0) {
+        const long long tile = blockIdx.x + (s / G) * (long long)gridDim.x;
+        row = tile * kTile + tid;
+        live = row < a.N;
+        acc0 = acc1 = 0.0;
+      }
+      const int slot = (int)(s % kStages);
+      const uint32_t par = (uint32_t)((s / kStages) & 1);
+      long long it = 0;
+      bool ok = true;
+      while (!mbar_try_wait(&full[slot], par)) {
+        if (s_abort || ++it > kSpin) { ok = false; break; }
+      }
+      if (!ok) {
+        s_abort = 1;
+        atomicExch(a.err, (int)IGAFD_ERR_TIMEOUT);
+        break;
+      }
+      const int d2 = g % W - P, d3 = DIM == 3 ? g / W - P : 0;
+      const long long row0 = row - tid;
+      const long long xs0 = row0 + (long long)d3 * n12 + (long long)d2 * a.n1 - P;
+      const int sh = (int)(xs0 & 1);                      // window starts at xs0 - sh
+      const double *st = ring + (size_t)slot * Gm::STAGE;
+      const double *cf = st + tid;
+      const double *xw = st + W * kTile + tid + sh;       // xw[j] = x[row + off - P + j]
 #pragma unroll
-          for (int d1 = -P; d1 <= P; ++d1) {
-            double a = ld_stream(Srow + (long long)d1 * N);
-            double v = __ldg(x + base + d1);
-            if (d1 & 1) acc1 = fma(a, v, acc1); else acc0 = fma(a, v, acc0);
-          }
+      for (int j = 0; j < W; ++j) {
+        const double c = cf[j * kTile];
+        const double v = xw[j];
+        if (j & 1) acc1 = fma(c, v, acc1); else acc0 = fma(c, v, acc0);
+      }
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot])) : "memory");
+      if (g == G - 1 && live) {
+        const double ax = acc0 + acc1;
+        if (MODE == 0) {
+          a.y[row] = ax;
+          dot = fma(a.x[row], ax, dot);
         } else {
-          for (int d1 = lo1; d1 <= hi1; ++d1) {
-            double a = ld_stream(Srow + (long long)d1 * N);
-            double v = __ldg(x + base + d1);
-            acc0 = fma(a, v, acc0);
-          }
+          const double rr = a.b[row] - ax;
+          a.y[row] = rr;
+          dot = fma(rr, rr, dot);
         }
       }
     }
-    double ax = acc0 + acc1;
-    if (MODE == 0) {
-      y[row] = ax;
-      dot = fma(x[row], ax, dot);
-    } else {
-      double rr = b[row] - ax;
-      y[row] = rr;
-      dot = fma(rr, rr, dot);
-    }
   }
-  if (!partial) return;
+  __syncthreads();
+  if (s_abort) {
+    if (tid == 0 && a.pcg) {
+      a.scal[S_STATUS] = (double)IGAFD_ERR_TIMEOUT;
+      a.scal[S_DONE] = 1.0;
+    }
+    return;
+  }
+  if (!a.partial) return;
   __shared__ double sh32[32];
-  double bs = block_sum(dot, sh32);
-  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
-  if (!last_block(counter)) return;
-  double tot = sum_partials(partial, gridDim.x, sh32);
-  if (threadIdx.x == 0) {
-    *counter = 0u;
-    if (pcg) {
+  const double bs = block_sum(dot, sh32);
+  if (tid == 0) a.partial[blockIdx.x] = bs;
+  if (!last_block(a.counter)) return;
+  const double tot = sum_partials(a.partial, gridDim.x, sh32);
+  if (tid == 0) {
+    *a.counter = 0u;
+    if (a.pcg) {
+      double *scal = a.scal;
       if (MODE == 0) {
         scal[S_PQ] = tot;
-        double alpha = scal[S_RHO] / tot;
+        const double alpha = scal[S_RHO] / tot;
         if (!(tot > 0.0) || !isfinite(alpha)) {
           scal[S_STATUS] = (double)IGAFD_ERR_BREAKDOWN;
           scal[S_DONE] = 1.0;
@@ -118,48 +271,87 @@ __global__ void __launch_bounds__(256) stencil_kernel(const double *__restrict__
   }
 }
 
-template <int DIM, int MODE>
-igafd_status launch_p(int p, dim3 grid, cudaStream_t s, const double *S, const double *x, double *y,
-                      const double *b, const int *n, long long N, double *partial, unsigned *counter,
-                      double *scal, int pcg, const double *done) {
-#define IGAFD_CASE(PP)                                                                   \
-  case PP:                                                                               \
-    stencil_kernel<DIM, PP, MODE><<<grid, 256, 0, s>>>(S, x, y, b, n[0], n[1], n[2], N,  \
-                                                        partial, counter, scal, pcg, done); \
-    IGAFD_LAUNCHED(1);                                                                   \
-    break;
-  switch (p) {
-    IGAFD_CASE(1)
-    IGAFD_CASE(2)
-    IGAFD_CASE(3)
-    IGAFD_CASE(4)
-    IGAFD_CASE(5)
-    IGAFD_CASE(6)
-    IGAFD_CASE(7)
-    default:
-      return IGAFD_ERR_ARG;
+template <int DIM, int P, int MODE>
+igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, cudaStream_t s) {
+  const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
+  auto kern = stencil_tma_kernel<DIM, P, MODE>;
+  static int per_sm = 0;   // resident CTAs per SM for this instantiation
+  if (per_sm == 0) {
+    IGAFD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nb = 0;
+    IGAFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kTile + 32, smem));
+    per_sm = nb > 0 ? nb : 1;
   }
-#undef IGAFD_CASE
+  long long grid = (long long)num_sms * per_sm;
+  if (grid > grid_cap) grid = grid_cap;
+  if (grid < 1) grid = 1;
+  kern<<<(int)grid, kTile + 32, smem, s>>>(a);
+  IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 
+template <int DIM, int MODE>
+igafd_status launch_p(int p, const StencilArgs &a, long long cap, int sms, cudaStream_t s) {
+  switch (p) {
+    case 1: return launch_one<DIM, 1, MODE>(a, cap, sms, s);
+    case 2: return launch_one<DIM, 2, MODE>(a, cap, sms, s);
+    case 3: return launch_one<DIM, 3, MODE>(a, cap, sms, s);
+    case 4: return launch_one<DIM, 4, MODE>(a, cap, sms, s);
+    case 5: return launch_one<DIM, 5, MODE>(a, cap, sms, s);
+    case 6: return launch_one<DIM, 6, MODE>(a, cap, sms, s);
+    case 7: return launch_one<DIM, 7, MODE>(a, cap, sms, s);
+    default: return IGAFD_ERR_ARG;
+  }
+}
+
 }  // namespace
+
+long long igafd_stencil_row_stride(long long N) { return (N + kTile - 1) / kTile * kTile; }
+
+// Zero halo (in elements) around padded vectors, so every x window of every
+// tile and offset group lies inside the allocation: p (n_1 n_2 + n_1 + 1)
+// + a tile + slack, rounded to 256 bytes.
+long long igafd_stencil_halo(int p, const int *n) {
+  long long h = (long long)p * ((long long)n[0] * n[1] + n[0] + 1) + kTile + 16;
+  return (h + 31) / 32 * 32;
+}
 
 // Internal: y = A x (b == null) or y = b - A x. With pcg != 0 the fused dot
 // feeds the PCG scalars; with skip_done != 0 the kernel does nothing once the
 // PCG convergence flag is set.
 igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
                                   int pcg, int skip_done, cudaStream_t s) {
-  dim3 grid(IGAFD_RED_BLOCKS);
-  double *partial = pcg ? P->partial : nullptr;
-  double *scal = pcg ? P->scal : nullptr;
-  const double *done = skip_done ? P->scal + S_DONE : nullptr;
-  unsigned *counter = P->counter;
-  if (P->dim == 3) {
-    if (b) return launch_p<3, 1>(P->p, grid, s, P->stencil, x, y, b, P->n, P->N, partial, counter, scal, pcg, done);
-    return launch_p<3, 0>(P->p, grid, s, P->stencil, x, y, b, P->n, P->N, partial, counter, scal, pcg, done);
+  // the kernel reads x windows that reach p planes beyond the box: use a
+  // zero-padded copy unless x already is one (the PCG search direction)
+  if (x != P->pv && x != P->xpad) {
+    IGAFD_CUDA(cudaMemcpyAsync(P->xpad, x, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    x = P->xpad;
   }
-  if (b) return launch_p<2, 1>(P->p, grid, s, P->stencil, x, y, b, P->n, P->N, partial, counter, scal, pcg, done);
-  return launch_p<2, 0>(P->p, grid, s, P->stencil, x, y, b, P->n, P->N, partial, counter, scal, pcg, done);
+  StencilArgs a{};
+  a.S = P->stencil;
+  a.x = x;
+  a.y = y;
+  a.b = b;
+  a.n1 = P->n[0];
+  a.n2 = P->n[1];
+  a.n3 = P->n[2];
+  a.N = P->N;
+  a.Np = P->Np;
+  a.ntiles = (P->N + kTile - 1) / kTile;
+  a.partial = pcg ? P->partial : nullptr;
+  a.counter = P->counter;
+  a.scal = pcg ? P->scal : nullptr;
+  a.pcg = pcg;
+  a.done = skip_done ? P->scal + S_DONE : nullptr;
+  a.err = P->err_flag;
+  // persistent grid: the resident CTAs of every SM, never more than the
+  // tiles or the partial-sum slots
+  long long cap = a.ntiles < IGAFD_RED_BLOCKS ? a.ntiles : IGAFD_RED_BLOCKS;
+  if (P->dim == 3) {
+    if (b) return launch_p<3, 1>(P->p, a, cap, P->num_sms, s);
+    return launch_p<3, 0>(P->p, a, cap, P->num_sms, s);
+  }
+  if (b) return launch_p<2, 1>(P->p, a, cap, P->num_sms, s);
+  return launch_p<2, 0>(P->p, a, cap, P->num_sms, s);
 }
