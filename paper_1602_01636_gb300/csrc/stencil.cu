@@ -21,8 +21,15 @@
 
 namespace {
 
-constexpr int kTile = 256;     // rows per tile = threads per CTA
-constexpr int kStages = 4;     // groups in flight per CTA
+#ifndef IGAFD_STENCIL_STAGES
+#define IGAFD_STENCIL_STAGES 4
+#endif
+#ifndef IGAFD_STENCIL_NACC
+#define IGAFD_STENCIL_NACC 1
+#endif
+constexpr int kTile = 256;                        // rows per tile = compute threads per CTA
+constexpr int kStages = IGAFD_STENCIL_STAGES;     // offset groups in flight per CTA
+constexpr int kAcc = IGAFD_STENCIL_NACC;          // independent FMA chains per row
 constexpr long long kSpin = 1ll << 26;   // mbarrier poll limit (~seconds)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -186,7 +193,9 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
     }
   } else {
     // ---------------- compute warps ----------------
-    double acc0 = 0.0, acc1 = 0.0;
+    double acc[kAcc];
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) acc[i] = 0.0;
     long long row = 0;
     bool live = false;
     for (long long s = 0; s < total; ++s) {
@@ -195,7 +204,8 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
         const long long tile = blockIdx.x + (s / G) * (long long)gridDim.x;
         row = tile * kTile + tid;
         live = row < a.N;
-        acc0 = acc1 = 0.0;
+#pragma unroll
+        for (int i = 0; i < kAcc; ++i) acc[i] = 0.0;
       }
       const int slot = (int)(s % kStages);
       const uint32_t par = (uint32_t)((s / kStages) & 1);
@@ -217,15 +227,13 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
       const double *cf = st + tid;
       const double *xw = st + W * kTile + tid + sh;       // xw[j] = x[row + off - P + j]
 #pragma unroll
-      for (int j = 0; j < W; ++j) {
-        const double c = cf[j * kTile];
-        const double v = xw[j];
-        if (j & 1) acc1 = fma(c, v, acc1); else acc0 = fma(c, v, acc0);
-      }
+      for (int j = 0; j < W; ++j) acc[j % kAcc] = fma(cf[j * kTile], xw[j], acc[j % kAcc]);
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot])) : "memory");
       if (g == G - 1 && live) {
-        const double ax = acc0 + acc1;
+        double ax = acc[0];
+#pragma unroll
+        for (int i = 1; i < kAcc; ++i) ax += acc[i];
         if (MODE == 0) {
           a.y[row] = ax;
           dot = fma(a.x[row], ax, dot);
