@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--dtype", default=None, help="FD dtype of the mixed solve")
+    ap.add_argument("--dtype", default=None,
+                    help="FD dtype of the mixed solve: tf32 (default), bf16, fp16 (tensor cores) or fp32")
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -244,7 +245,7 @@ def run_ours(args):
             dist.barrier()
 
     n, p = args.n, args.p
-    dtype = args.dtype or "fp32"
+    dtype = args.dtype or "tf32"
     prob = synth.deformed_cube(n, p, seed=0)
     patch = igafd.Patch.from_problem(prob)
     N = patch.N
@@ -374,7 +375,8 @@ def run_ours(args):
             "metric": METRIC, "value": ms_step / 1e3, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f64+f32", "bf16": "f64+bf16", "fp16": "f64+f16", "fp64": "f64"}[dtype],
+            "dtype": {"fp32": "f64+f32", "tf32": "f64+tf32", "bf16": "f64+bf16", "fp16": "f64+f16",
+                      "fp64": "f64"}[dtype],
             "data": "synthetic",
             "config": {"workload": workload_name(n, p), "n": n, "p": p, "dofs": N, "tol": args.tol,
                        "fd_dtype": dtype, "rhs": "manufactured u=sin(pi x)sin(pi y)sin(pi z)",

@@ -49,7 +49,9 @@ typedef enum {
   IGAFD_FP64 = 0,   /* FP64 contractions and divide: FD is exactly P^{-1} */
   IGAFD_FP32 = 1,   /* FP32 SIMT contractions, FP32 divide */
   IGAFD_BF16 = 2,   /* tcgen05 kind::f16 with bf16 operands, FP32 accumulate */
-  IGAFD_FP16 = 3    /* tcgen05 kind::f16 with fp16 operands, FP32 accumulate */
+  IGAFD_FP16 = 3,   /* tcgen05 kind::f16 with fp16 operands (power-of-two scaled
+                       per 128-row tile and per U_k), FP32 accumulate */
+  IGAFD_TF32 = 4    /* tcgen05 kind::tf32, FP32 accumulate */
 } igafd_dtype;
 
 /* Single-patch problem (Section 2.1, Eqs. (A), (Q)):
@@ -149,7 +151,9 @@ igafd_status igafd_apply_A(igafd_patch *patch, const double *x_dev,
  * 3D, with the forward step applying U_k^T and the backward step U_k):
  * forward mode-k products, divide by D_1 (+) ... (+) D_d, backward mode-k
  * products. With IGAFD_FP64 the result equals P^{-1} r up to rounding;
- * other dtypes give an inexact P^{-1}. r_dev and z_dev must not overlap. */
+ * other dtypes give an inexact P^{-1}. The tensor-core dtypes (BF16, FP16,
+ * TF32) need n_k <= 256 and return IGAFD_ERR_ARG otherwise. r_dev and z_dev
+ * must not overlap. */
 igafd_status igafd_apply_prec(igafd_patch *patch, igafd_dtype dtype,
                               const double *r_dev, double *z_dev, void *stream);
 

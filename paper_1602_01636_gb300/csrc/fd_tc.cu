@@ -1,11 +1,483 @@
-// Placeholder for the tensor-core (tcgen05) mixed-precision FD; replaced by
-// the real implementation. Returns IGAFD_ERR_ARG so no caller silently gets a
-// different precision.
+// Fast-diagonalization apply on the 5th-generation tensor cores (tcgen05),
+// operands in TF32, BF16 or FP16, FP32 accumulation in tensor memory.
+//
+// Algorithm 3 (Algorithm 1 in 2D) is run as 2d mode products, each a GEMM
+//   out[j][m] = sum_i in[m][i] * B[j][i]
+// over the tensor viewed as rows m (the other directions) by the contracted
+// direction i, which is always the fastest one: every product writes its
+// result transposed (new index slowest), so the next direction to contract
+// becomes the contiguous one. After the d forward products the layout is the
+// original one again (the divide by D_1 (+) D_2 (+) D_3 is fused there), and
+// likewise after the d backward products. Forward products use
+// B = U_k^T (out_j = sum_i U_k[i][j] in_i), backward ones B = U_k.
+//
+// Per CTA: a 128-row tile of `in`; K is walked in 64-element chunks through a
+// two-stage shared-memory ring in the canonical K-major 128-byte-swizzled
+// layout; one thread issues tcgen05.mma (M = 128, N = n_k padded to 16) into
+// a TMEM accumulator; eight warps read it back (tcgen05.ld) and store the
+// transposed, rescaled result. Intermediates are FP32 in global memory;
+// operands are rounded to the chosen type when they are staged. FP16
+// operands use a power-of-two scale per tile (and per U_k) so that nothing
+// overflows; the scales are removed exactly in the epilogue.
 #include "common.cuh"
 
-igafd_status igafd_fd_tc_init(igafd_patch *, cudaStream_t) { return IGAFD_OK; }
-void igafd_fd_tc_free(igafd_patch *) {}
-igafd_status igafd_fd_tc_apply(igafd_patch *, igafd_dtype, const double *, double *, cudaStream_t,
-                               double *) {
-  return IGAFD_ERR_ARG;
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <vector>
+
+namespace {
+
+constexpr int kM = 128;          // rows per tile (MMA M)
+constexpr int kKC = 64;          // K elements per stage
+constexpr int kThreads = 256;
+constexpr long long kSpin = 1ll << 26;
+
+enum OpType { OP_TF32 = 0, OP_BF16 = 1, OP_FP16 = 2 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// SM100 shared-memory matrix descriptor, K-major, 128-byte swizzle:
+// start >> 4 in [0,14), LBO >> 4 in [16,30) (unused for this layout),
+// SBO >> 4 in [32,46) (1024 B between 8-row groups), version 1 in [46,48),
+// layout 2 (SWIZZLE_128B) in [61,64).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(16 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Byte offset of (row, kbyte) in a K-major tile of `rows` rows stored as
+// 128-byte K atoms [katom][row][128 B], 16-byte chunks XOR-swizzled by row%8.
+__device__ __forceinline__ uint32_t sw128_off(int row, int kbyte, int rows) {
+  const int katom = kbyte >> 7, kb = kbyte & 127, chunk = kb >> 4;
+  return katom * rows * 128 + (row >> 3) * 1024 + (row & 7) * 128 +
+         (((chunk ^ (row & 7)) << 4) | (kb & 15));
+}
+
+template <int OP> struct Op;
+template <> struct Op<OP_TF32> {
+  static constexpr int kBytes = 4;
+  static constexpr uint32_t kFmt = 2;
+  // round to nearest TF32 (the MMA would otherwise drop the low mantissa bits)
+  __device__ static void put(unsigned char *p, float v) {
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+    *(uint32_t *)p = t;
+  }
+};
+template <> struct Op<OP_BF16> {
+  static constexpr int kBytes = 2;
+  static constexpr uint32_t kFmt = 1;
+  __device__ static void put(unsigned char *p, float v) { *(__nv_bfloat16 *)p = __float2bfloat16_rn(v); }
+};
+template <> struct Op<OP_FP16> {
+  static constexpr int kBytes = 2;
+  static constexpr uint32_t kFmt = 0;
+  __device__ static void put(unsigned char *p, float v) { *(__half *)p = __float2half_rn(v); }
+};
+
+struct PassArgs {
+  const void *in;        // [M][K] (double for the first pass, float otherwise)
+  int in_f64;
+  int in_aligned;        // `in` is 16-byte aligned (vector loads allowed)
+  void *out;             // [N][M] (double for the last pass, float otherwise)
+  int out_f64;
+  const unsigned char *Bimg;  // B = U_k^T (forward) or U_k, pre-staged: per K chunk the
+                              // exact shared-memory image of the B stage
+  float b_scale;         // power of two folded into the FP16 image of B
+  const float *inv_lam;  // divide epilogue (null: none), indexed like out
+  long long M;
+  int K, N, Np;          // Np: N padded to a multiple of 16 (MMA N)
+  int tmem_cols;
+  const double *done;    // skip when *done != 0
+  int *err;
+};
+
+template <int OP>
+__global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
+  if (a.done && *a.done != 0.0) return;
+  using T = Op<OP>;
+  constexpr int kRowBytes = kKC * T::kBytes;                 // bytes of one stage row
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base =
+      (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int stageA = kM * kRowBytes;                         // multiple of 1024
+  const int stageB = a.Np * kRowBytes;
+  unsigned char *sA[2] = {base, base + stageA + stageB};
+  unsigned char *sB[2] = {base + stageA, base + 2 * stageA + stageB};
+  __shared__ uint64_t bar[2];     // MMA completion per stage
+  __shared__ uint64_t bbar[2];    // B-image bulk copy per stage
+  __shared__ uint32_t tmem_base;
+  __shared__ float s_red[kThreads / 32];
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long m0 = (long long)blockIdx.x * kM;
+  const int mrows = (int)((a.M - m0) < kM ? (a.M - m0) : kM);
+  const int K = a.K;
+  const int nchunks = (K + kKC - 1) / kKC;
+
+  // per-tile power-of-two scale for FP16 operands
+  float a_scale = 1.0f;
+  if (OP == OP_FP16) {
+    float mx = 0.0f;
+    for (int i = tid; i < mrows * K; i += kThreads) {
+      const long long idx = (m0 + i / K) * K + i % K;
+      const float v = a.in_f64 ? (float)((const double *)a.in)[idx] : ((const float *)a.in)[idx];
+      mx = fmaxf(mx, fabsf(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_red[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      float m = 0.0f;
+      for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, s_red[w]);
+      s_red[0] = m;
+    }
+    __syncthreads();
+    const float m = s_red[0];
+    // largest power of two with m * scale <= 2^14
+    a_scale = m > 0.0f ? exp2f(14.0f - ceilf(log2f(m))) : 1.0f;
+  }
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | (T::kFmt << 7) | (T::kFmt << 10) |
+                         ((uint32_t)(a.Np >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+
+  auto wait_on = [&](uint64_t *b, uint32_t parity) -> bool {
+    for (long long it = 0; it < kSpin; ++it) {
+      uint32_t ok;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(smem_u32(b)), "r"(parity)
+          : "memory");
+      if (ok) return true;
+    }
+    return false;
+  };
+  auto wait_bar = [&](int st, uint32_t parity) -> bool { return wait_on(&bar[st], parity); };
+
+  for (int c = 0; c < nchunks; ++c) {
+    const int st = c & 1;
+    if (c >= 2) {   // the MMAs that read this stage two chunks ago must be done
+      if (!wait_bar(st, (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+      __syncthreads();
+      if (s_fail) break;
+    }
+    const int k0 = c * kKC;
+    // stage B: one bulk copy of the pre-staged image of this K chunk
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)stageB;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bbar[st])),
+                   "r"(bytes)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(sB[st])),
+          "l"(a.Bimg + (size_t)c * stageB), "r"(bytes), "r"(smem_u32(&bbar[st]))
+          : "memory");
+    }
+    // stage A: warp w takes rows 16w..16w+15, lane l columns k0+2l, k0+2l+1;
+    // all sixteen loads are issued before the swizzled, rounded stores
+    {
+      float2 v[16];
+      const bool vec = a.in_aligned && (K % 2 == 0) && (k0 + kKC <= K);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int rr = warp * 16 + i;
+        const int k = k0 + 2 * lane;
+        v[i] = make_float2(0.f, 0.f);
+        if (rr < mrows) {
+          const long long idx = (m0 + rr) * K + k;
+          if (vec) {
+            if (a.in_f64) {
+              const double2 d = *reinterpret_cast<const double2 *>((const double *)a.in + idx);
+              v[i] = make_float2((float)d.x, (float)d.y);
+            } else {
+              v[i] = *reinterpret_cast<const float2 *>((const float *)a.in + idx);
+            }
+          } else {
+            if (k < K) v[i].x = a.in_f64 ? (float)((const double *)a.in)[idx] : ((const float *)a.in)[idx];
+            if (k + 1 < K)
+              v[i].y = a.in_f64 ? (float)((const double *)a.in)[idx + 1] : ((const float *)a.in)[idx + 1];
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int rr = warp * 16 + i;
+        T::put(sA[st] + sw128_off(rr, (2 * lane) * T::kBytes, kM), v[i].x * a_scale);
+        T::put(sA[st] + sw128_off(rr, (2 * lane + 1) * T::kBytes, kM), v[i].y * a_scale);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      if (!wait_on(&bbar[st], (uint32_t)((c >> 1) & 1))) s_fail = 1;
+    }
+    if (tid == 0 && !s_fail) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int ksteps = kRowBytes / 32;          // 32 bytes of K per MMA
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const int kbyte = ks * 32;
+        const uint32_t ao = (kbyte >> 7) * kM * 128 + (kbyte & 127);
+        const uint32_t bo = (kbyte >> 7) * a.Np * 128 + (kbyte & 127);
+        const uint64_t ad = sw128_desc(smem_u32(sA[st]) + ao);
+        const uint64_t bd = sw128_desc(smem_u32(sB[st]) + bo);
+        const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+        if (OP == OP_TF32)
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        else
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&bar[st]))
+          : "memory");
+    }
+  }
+  // wait for the last MMAs (the commits track all earlier ones too)
+  bool ok = !s_fail;
+  if (ok && nchunks > 0) {
+    const int last = nchunks - 1;
+    ok = wait_bar(last & 1, (uint32_t)((last >> 1) & 1));
+    if (!ok) s_fail = 1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!s_fail) {
+    // epilogue: warp w reads TMEM lanes 32*(w%4).. and columns of half w/4
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;                  // row within the tile
+    const long long m = m0 + r;
+    const float unscale = 1.0f / (a_scale * a.b_scale);
+    const int ncol32 = (a.Np + 31) / 32;
+    for (int cb = half; cb < ncol32; cb += 2) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+          "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (r < mrows) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = cb * 32 + j;
+          if (n < a.N) {
+            const long long o = (long long)n * a.M + m;
+            float val = __uint_as_float(v[j]) * unscale;
+            if (a.inv_lam) val *= a.inv_lam[o];
+            if (a.out_f64) ((double *)a.out)[o] = (double)val;
+            else ((float *)a.out)[o] = val;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(a.err, (int)IGAFD_ERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+}
+
+// U_k^T (row-major, FP32) for the forward products
+__global__ void transpose_f32_kernel(const float *U, float *UT, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n * n) UT[(size_t)(i % n) * n + i / n] = U[i];
+}
+
+// Shared-memory image of B (n x n, row-major FP32, K contiguous) for every
+// K chunk: rows padded to Np and K to whole chunks with zeros, rounded to the
+// operand type, scaled by a power of two, in the swizzled stage layout.
+template <int OP>
+__global__ void b_image_kernel(const float *B, int n, int Np, float scale, unsigned char *img) {
+  using T = Op<OP>;
+  const int nchunks = (n + kKC - 1) / kKC;
+  const long long total = (long long)nchunks * Np * kKC;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int kk = (int)(i % kKC);
+  const int r = (int)((i / kKC) % Np);
+  const int c = (int)(i / ((long long)kKC * Np));
+  const int k = c * kKC + kk;
+  const float v = (r < n && k < n) ? B[(size_t)r * n + k] * scale : 0.0f;
+  T::put(img + (size_t)c * Np * kKC * T::kBytes + sw128_off(r, kk * T::kBytes, Np), v);
+}
+
+}  // namespace
+
+struct FDMixed {
+  float *UT[3];                  // U_k^T row-major FP32
+  float scale16[3];              // power of two folded into the FP16 images of U_k
+  unsigned char *img[3][2][3];   // [direction][0: U_k^T, 1: U_k][op] B images
+};
+
+igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
+  FDMixed *F = (FDMixed *)calloc(1, sizeof(FDMixed));
+  if (!F) return IGAFD_ERR_OOM;
+  P->mixed = F;
+  for (int k = 0; k < P->dim; ++k) {
+    const int n = P->n[k];
+    if (cudaMalloc(&F->UT[k], (size_t)n * n * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return IGAFD_ERR_OOM;
+    }
+    transpose_f32_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(P->U32[k], F->UT[k], n);
+    IGAFD_CUDA(cudaGetLastError());
+    // FP16 staging scale: largest power of two with max|U_k| * scale <= 2^14
+    std::vector<float> h((size_t)n * n);
+    IGAFD_CUDA(cudaMemcpyAsync(h.data(), P->U32[k], h.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    IGAFD_CUDA(cudaStreamSynchronize(s));
+    float mx = 0.f;
+    for (float v : h) mx = fmaxf(mx, fabsf(v));
+    F->scale16[k] = mx > 0.f ? exp2f(14.0f - ceilf(log2f(mx))) : 1.0f;
+    if (n > 256) continue;   // tensor-core FD limited to n_k <= 256
+    const int Np = (n + 15) / 16 * 16;
+    const int nchunks = (n + kKC - 1) / kKC;
+    for (int dir = 0; dir < 2; ++dir) {
+      const float *B = dir == 0 ? F->UT[k] : P->U32[k];
+      for (int op = 0; op < 3; ++op) {
+        const int bytes = op == OP_TF32 ? 4 : 2;
+        const size_t sz = (size_t)nchunks * Np * kKC * bytes;
+        if (cudaMalloc(&F->img[k][dir][op], sz) != cudaSuccess) {
+          cudaGetLastError();
+          return IGAFD_ERR_OOM;
+        }
+        const long long total = (long long)nchunks * Np * kKC;
+        const unsigned blocks = (unsigned)((total + 255) / 256);
+        if (op == OP_TF32) b_image_kernel<OP_TF32><<<blocks, 256, 0, s>>>(B, n, Np, 1.0f, F->img[k][dir][op]);
+        else if (op == OP_BF16) b_image_kernel<OP_BF16><<<blocks, 256, 0, s>>>(B, n, Np, 1.0f, F->img[k][dir][op]);
+        else b_image_kernel<OP_FP16><<<blocks, 256, 0, s>>>(B, n, Np, F->scale16[k], F->img[k][dir][op]);
+        IGAFD_CUDA(cudaGetLastError());
+      }
+    }
+  }
+  return IGAFD_OK;
+}
+
+void igafd_fd_tc_free(igafd_patch *P) {
+  if (!P || !P->mixed) return;
+  for (int k = 0; k < 3; ++k) {
+    cudaFree(P->mixed->UT[k]);
+    for (int d = 0; d < 2; ++d)
+      for (int o = 0; o < 3; ++o) cudaFree(P->mixed->img[k][d][o]);
+  }
+  free(P->mixed);
+  P->mixed = nullptr;
+}
+
+static size_t pass_smem(int op, int Np) {
+  const int bytes = op == OP_TF32 ? 4 : 2;
+  const size_t row = (size_t)kKC * bytes;
+  return 1024 + 2 * (kM * row + (size_t)Np * row);
+}
+
+template <int OP>
+static igafd_status launch_pass(const PassArgs &a, cudaStream_t s) {
+  const size_t smem = pass_smem(OP, a.Np);
+  IGAFD_CUDA(cudaFuncSetAttribute(tc_pass_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  const unsigned grid = (unsigned)((a.M + kM - 1) / kM);
+  tc_pass_kernel<OP><<<grid, kThreads, smem, s>>>(a);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
+  return IGAFD_OK;
+}
+
+// Tensor-core FD. dt selects the operand type: IGAFD_BF16, IGAFD_FP16, or
+// IGAFD_TF32 (declared in igafd.h).
+igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, double *z,
+                               cudaStream_t s, double *done) {
+  FDMixed *F = P->mixed;
+  if (!F) return IGAFD_ERR_ARG;
+  const int op = dt == IGAFD_TF32 ? OP_TF32 : dt == IGAFD_BF16 ? OP_BF16 : OP_FP16;
+  const int dim = P->dim;
+  for (int k = 0; k < dim; ++k)
+    if (P->n[k] > 256) return IGAFD_ERR_ARG;   // one MMA covers N <= 256
+  // current layout: dims[0] slowest .. dims[dim-1] fastest (direction indices)
+  int dims[3];
+  for (int i = 0; i < dim; ++i) dims[i] = dim - 1 - i;
+  float *bufs[2] = {(float *)P->fd_a, (float *)P->fd_b};
+  const void *in = r;
+  int in_f64 = 1, cur = 0;
+  for (int pass = 0; pass < 2 * dim; ++pass) {
+    const bool forward = pass < dim;
+    const int k = dims[dim - 1];                 // contracted direction (fastest)
+    const int n = P->n[k];
+    PassArgs a{};
+    a.in = in;
+    a.in_f64 = in_f64;
+    a.in_aligned = ((uintptr_t)in % 16) == 0;
+    const bool last = pass == 2 * dim - 1;
+    a.out = last ? (void *)z : (void *)bufs[cur];
+    a.out_f64 = last ? 1 : 0;
+    a.Bimg = F->img[k][forward ? 0 : 1][op];
+    a.b_scale = op == OP_FP16 ? F->scale16[k] : 1.0f;
+    a.inv_lam = pass == dim - 1 ? P->inv_lam32 : nullptr;
+    a.M = P->N / n;
+    a.K = n;
+    a.N = n;
+    a.Np = (n + 15) / 16 * 16;
+    int cols = 32;
+    while (cols < a.Np) cols <<= 1;
+    a.tmem_cols = cols;
+    a.done = done;
+    a.err = P->err_flag;
+    if (op == OP_TF32) IGAFD_TRY(launch_pass<OP_TF32>(a, s));
+    else if (op == OP_BF16) IGAFD_TRY(launch_pass<OP_BF16>(a, s));
+    else IGAFD_TRY(launch_pass<OP_FP16>(a, s));
+    // rotate: the new index becomes the slowest
+    for (int i = dim - 1; i > 0; --i) dims[i] = dims[i - 1];
+    dims[0] = k;
+    if (!last) {
+      in = bufs[cur];
+      in_f64 = 0;
+      cur ^= 1;
+    }
+  }
+  return IGAFD_OK;
 }

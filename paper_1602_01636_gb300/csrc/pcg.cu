@@ -164,7 +164,8 @@ static igafd_status fd_apply(igafd_patch *P, igafd_dtype dt, const double *r, do
     case IGAFD_FP64: return igafd_fd64_apply(P, r, z, s, done);
     case IGAFD_FP32: return igafd_fd32_apply(P, r, z, s, done);
     case IGAFD_BF16:
-    case IGAFD_FP16: return igafd_fd_tc_apply(P, dt, r, z, s, done);
+    case IGAFD_FP16:
+    case IGAFD_TF32: return igafd_fd_tc_apply(P, dt, r, z, s, done);
     default: return IGAFD_ERR_ARG;
   }
 }
@@ -213,7 +214,7 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
   if (opts) o = *opts; else igafd_pcg_default_opts(&o);
   if (!(o.tol >= 0.0) || o.max_iter < 0 || o.check_every < 1 || o.true_every < 0)
     return IGAFD_ERR_ARG;
-  if (o.prec_dtype < IGAFD_FP64 || o.prec_dtype > IGAFD_FP16) return IGAFD_ERR_ARG;
+  if (o.prec_dtype < IGAFD_FP64 || o.prec_dtype > IGAFD_TF32) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   cudaStream_t s = (cudaStream_t)stream;
   const long long N = P->N;

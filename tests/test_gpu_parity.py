@@ -87,6 +87,41 @@ def test_apply_prec_fp32(case):
     assert rel(z, F.apply(r)) <= 1e-4
 
 
+TC_TOL = {"tf32": 1e-2, "fp16": 1e-2, "bf16": 4e-2}
+
+
+@pytest.mark.parametrize("dtype", ["tf32", "bf16", "fp16"])
+def test_apply_prec_tensor_core(case, dtype):
+    """tcgen05 FD: operands rounded to the dtype, FP32 accumulation; the
+    error is a few operand roundings (2^-11 for TF32/FP16, 2^-8 for BF16)
+    per product, six products."""
+    prob, disc, S, patch = case
+    F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
+    r = synth.random_vector(disc.N, 14)
+    z = patch.apply_prec(to_dev(r), dtype=dtype).cpu().numpy()
+    err = rel(z, F.apply(r))
+    print(f"{dtype} FD rel err {err:.2e}")
+    assert err <= TC_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["tf32", "bf16", "fp16"])
+def test_pcg_tensor_core_preconditioner(case, dtype):
+    prob, disc, S, patch = case
+    A = assemble.stencil_to_csr(disc, S)
+    F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
+    b = synth.random_rhs(disc.N, 8)
+    ro = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-13, max_iter=500)
+    r8 = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-8, max_iter=500)
+    x, info = patch.pcg(to_dev(b), tol=1e-8, max_iter=500, dtype=dtype)
+    assert info.status == 0
+    # at most two more iterations than the exact preconditioner; when P = A
+    # (identity map) the exact one needs a single step and an inexact FD with
+    # relative error eps needs about log(1e-8)/log(eps) steps instead
+    bound = r8.iters + 2 if r8.iters > 2 else 8
+    assert info.iterations <= bound, (info.iterations, r8.iters)
+    assert rel(x.cpu().numpy(), ro.x) <= 1e-7
+
+
 def test_rhs_sine(case):
     prob, disc, S, patch = case
     f = {2: lambda x, y: 2 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y),
@@ -195,8 +230,11 @@ def test_full_size_sampled(torch):
     assert np.abs(Sg_rows - So).max() <= 1e-13 * np.abs(So).max()
     F = fd.FD([disc.pencil(k) for k in range(3)])
     r = synth.random_vector(disc.N, 21)
+    zo = F.apply(r)
     z = patch.apply_prec(to_dev(r)).cpu().numpy()
-    assert rel(z, F.apply(r)) <= 1e-11
+    assert rel(z, zo) <= 1e-11
+    for dt, tol in TC_TOL.items():
+        assert rel(patch.apply_prec(to_dev(r), dtype=dt).cpu().numpy(), zo) <= tol
     b = synth.random_rhs(disc.N, 22)
     x, info = patch.pcg(to_dev(b), tol=1e-8)
     assert info.status == 0 and info.true_relres <= 1e-8
