@@ -198,12 +198,15 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
     for (int i = 0; i < kAcc; ++i) acc[i] = 0.0;
     long long row = 0;
     bool live = false;
+    int i2r = 0, i3r = 0;
     for (long long s = 0; s < total; ++s) {
       const int g = (int)(s % G);
       if (g == 0) {
         const long long tile = blockIdx.x + (s / G) * (long long)gridDim.x;
         row = tile * kTile + tid;
         live = row < a.N;
+        i2r = (int)((row / a.n1) % a.n2);
+        i3r = DIM == 3 ? (int)(row / n12) : 0;
 #pragma unroll
         for (int i = 0; i < kAcc; ++i) acc[i] = 0.0;
       }
@@ -226,8 +229,14 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
       const double *st = ring + (size_t)slot * Gm::STAGE;
       const double *cf = st + tid;
       const double *xw = st + W * kTile + tid + sh;       // xw[j] = x[row + off - P + j]
+      // rows whose (i_2 + delta_2, i_3 + delta_3) leaves the box have only
+      // zero coefficients in this group; skip when the whole warp is out
+      const bool in23 = live && (i2r + d2 >= 0) && (i2r + d2 < a.n2) &&
+                        (DIM == 2 || ((i3r + d3 >= 0) && (i3r + d3 < a.n3)));
+      if (__any_sync(0xffffffffu, in23)) {
 #pragma unroll
-      for (int j = 0; j < W; ++j) acc[j % kAcc] = fma(cf[j * kTile], xw[j], acc[j % kAcc]);
+        for (int j = 0; j < W; ++j) acc[j % kAcc] = fma(cf[j * kTile], xw[j], acc[j % kAcc]);
+      }
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot])) : "memory");
       if (g == G - 1 && live) {
