@@ -98,9 +98,10 @@ typedef struct {
   int check_every;     /* host polls the device convergence flag every this
                           many iterations (>= 1); later iterations are skipped
                           on the device once converged, so x is unaffected */
-  int timing;          /* 1: record CUDA events around the A stencil and the
-                          FD apply of every iteration (fills the *_ms fields
-                          of igafd_pcg_info); polls at most every 32 iterations */
+  int timing;          /* 1: time the solve with CUDA events and the in-loop
+                          A-stencil launches with device-clock stamps taken by
+                          the stencil kernel itself (fills the *_ms fields of
+                          igafd_pcg_info); polls at most every 32 iterations */
 } igafd_pcg_opts;
 
 typedef struct {
@@ -111,7 +112,8 @@ typedef struct {
   int true_checks;     /* true-residual recomputations performed */
   double solve_ms;     /* device time of the whole solve (timing = 1) */
   double stencil_ms;   /* summed device time of the in-loop A products */
-  double prec_ms;      /* summed device time of the in-loop FD applies */
+  double prec_ms;      /* summed device time of the in-loop FD applies, or -1
+                          when the loop ran as a captured graph */
 } igafd_pcg_info;
 
 /* Build a patch: 1D pencils K_k, M_k by (p+1)-point Gauss quadrature

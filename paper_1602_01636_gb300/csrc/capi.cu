@@ -56,6 +56,9 @@ void free_patch(igafd_patch *P) {
   cudaFree(P->ctrl); cudaFree(P->inv_lam); cudaFree(P->inv_lam32); cudaFree(P->stencil);
   cudaFree(P->fd_a); cudaFree(P->fd_b);
   cudaFree(P->r); cudaFree(P->z); cudaFree(P->pv_base); cudaFree(P->xpad_base);
+  cudaFree(P->xs_base); cudaFree(P->bint); cudaFree(P->tstat);
+  if (P->loop_exec) cudaGraphExecDestroy(P->loop_exec);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   cudaFree(P->q); cudaFree(P->xt);
   cudaFree(P->partial); cudaFree(P->counter); cudaFree(P->scal); cudaFree(P->err_flag);
   igafd_fd_tc_free(P);
@@ -96,8 +99,14 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
   IGAFD_TRY(alloc(&P->xpad_base, (size_t)(N + 2 * P->halo)));
   IGAFD_CUDA(cudaMemsetAsync(P->pv_base, 0, (N + 2 * P->halo) * sizeof(double), s));
   IGAFD_CUDA(cudaMemsetAsync(P->xpad_base, 0, (N + 2 * P->halo) * sizeof(double), s));
+  IGAFD_TRY(alloc(&P->xs_base, (size_t)(N + 2 * P->halo)));
+  IGAFD_CUDA(cudaMemsetAsync(P->xs_base, 0, (N + 2 * P->halo) * sizeof(double), s));
+  IGAFD_TRY(alloc(&P->bint, (size_t)N));
+  IGAFD_TRY(alloc(&P->tstat, (size_t)4));
   P->pv = P->pv_base + P->halo;
   P->xpad = P->xpad_base + P->halo;
+  P->xs = P->xs_base + P->halo;
+  IGAFD_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   IGAFD_TRY(alloc(&P->q, (size_t)N));
   IGAFD_TRY(alloc(&P->xt, (size_t)N));
   IGAFD_TRY(alloc(&P->partial, (size_t)IGAFD_PARTIAL_SLOTS * IGAFD_RED_BLOCKS));

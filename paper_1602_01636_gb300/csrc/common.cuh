@@ -58,6 +58,8 @@ enum {
   S_ITER,         // iterations executed
   S_STATUS,       // 0 ok, -6 breakdown
   S_TRUE_RR,      // last true residual (r, r)
+  S_TOL2,         // tol^2
+  S_MAXIT,        // iteration cap
   S_COUNT
 };
 
@@ -88,7 +90,16 @@ struct igafd_patch {
   // zero-padded vectors read by the stencil (halo elements on both ends):
   // pv = PCG search direction, xpad = copy of a caller's x
   double *pv, *xpad, *pv_base, *xpad_base;
+  double *xs, *xs_base;         // PCG iterate (padded), copied to the caller's x at the end
+  double *bint;                 // copy of the caller's b for the duration of a solve
   long long halo;
+  // captured PCG iteration chunk (replayed by cudaGraphLaunch)
+  cudaStream_t cap_stream;
+  cudaGraphExec_t loop_exec;
+  long long loop_nodes;         // kernels per replay
+  unsigned long long *tstat;    // stencil timing on the device: [0] earliest block start
+                                // of the running launch, [1] summed ns, [2] launches
+  int loop_key[5];              // dtype, flexible, true_every, chunk, valid
   double *partial;              // [PARTIAL_SLOTS][MAX_BLOCKS]
   unsigned int *counter;        // last-block counters
   double *scal;                 // [S_COUNT]
@@ -118,8 +129,11 @@ igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, 
 igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s);
 void igafd_fd_tc_free(igafd_patch *P);
 // y = A x (b == null) or y = b - A x; see stencil.cu
+// every > 0: the kernel only runs when the device iteration counter is a
+// multiple of `every` (periodic true residual inside a captured loop)
 igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
-                                  int pcg, int skip_done, cudaStream_t s);
+                                  int pcg, int skip_done, cudaStream_t s, int every = 0,
+                                  unsigned long long *tstat = nullptr);
 long long igafd_stencil_row_stride(long long N);   // Np for a given N
 long long igafd_stencil_halo(int p, const int *n);   // zero halo of padded vectors
 

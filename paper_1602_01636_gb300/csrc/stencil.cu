@@ -106,7 +106,15 @@ struct StencilArgs {
   int pcg;
   const double *done; // skip when *done != 0
   int *err;           // set on an mbarrier timeout
+  int every;          // > 0: run only when scal[S_ITER] is a multiple of every
+  unsigned long long *tstat;  // optional device timing (see igafd_patch::tstat)
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
 
 template <int P>
 struct Geom {
@@ -126,6 +134,8 @@ struct Geom {
 template <int DIM, int P, int MODE>
 __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) {
   if (a.done && *a.done != 0.0) return;
+  if (a.every > 0 && ((long long)a.scal[S_ITER]) % a.every != 0) return;
+  if (a.tstat && threadIdx.x == 0) atomicMin(&a.tstat[0], global_ns());
   using Gm = Geom<P>;
   constexpr int W = Gm::W;
   constexpr int G = DIM == 3 ? W * W : W;        // (delta_2, delta_3) groups per tile
@@ -270,6 +280,11 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
   const double tot = sum_partials(a.partial, gridDim.x, sh32);
   if (tid == 0) {
     *a.counter = 0u;
+    if (a.tstat) {   // this block finished last: launch duration = now - first start
+      a.tstat[1] += global_ns() - a.tstat[0];
+      a.tstat[2] += 1ull;
+      a.tstat[0] = ~0ull;
+    }
     if (a.pcg) {
       double *scal = a.scal;
       if (MODE == 0) {
@@ -338,10 +353,11 @@ long long igafd_stencil_halo(int p, const int *n) {
 // feeds the PCG scalars; with skip_done != 0 the kernel does nothing once the
 // PCG convergence flag is set.
 igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
-                                  int pcg, int skip_done, cudaStream_t s) {
+                                  int pcg, int skip_done, cudaStream_t s, int every,
+                                  unsigned long long *tstat) {
   // the kernel reads x windows that reach p planes beyond the box: use a
-  // zero-padded copy unless x already is one (the PCG search direction)
-  if (x != P->pv && x != P->xpad) {
+  // zero-padded copy unless x already is one (PCG search direction / iterate)
+  if (x != P->pv && x != P->xpad && x != P->xs) {
     IGAFD_CUDA(cudaMemcpyAsync(P->xpad, x, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     x = P->xpad;
   }
@@ -362,6 +378,8 @@ igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, co
   a.pcg = pcg;
   a.done = skip_done ? P->scal + S_DONE : nullptr;
   a.err = P->err_flag;
+  a.every = every;
+  a.tstat = a.partial ? tstat : nullptr;
   // persistent grid: the resident CTAs of every SM, never more than the
   // tiles or the partial-sum slots
   long long cap = a.ntiles < IGAFD_RED_BLOCKS ? a.ntiles : IGAFD_RED_BLOCKS;
