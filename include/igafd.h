@@ -173,6 +173,22 @@ igafd_status igafd_pcg_solve(igafd_patch *patch, const igafd_pcg_opts *opts,
                              const double *b_dev, double *x_dev,
                              igafd_pcg_info *info, void *stream);
 
+/* Solve count independent problems A_i x_i = b_i (one per patch, patches on
+ * the same device) with the same options. Each problem's chunk of
+ * opts->check_every iterations is captured once as a CUDA graph; one parent
+ * graph holds them all as independent nodes, so a single graph launch
+ * advances every unfinished problem concurrently, each with its own device
+ * convergence flag (finished problems run no-op kernels until the parent
+ * graph is rebuilt without them). b[i], x[i]: device vectors of patch i's
+ * size; infos (optional) receives one igafd_pcg_info per problem. The
+ * results are bitwise those of igafd_pcg_solve on each problem. Returns the
+ * first non-OK problem status (OK if all converged); timing is ignored.
+ * A given patch may appear only once. */
+igafd_status igafd_batch_pcg_solve(igafd_patch *const *patches, int count,
+                                   const double *const *b_dev, double *const *x_dev,
+                                   const igafd_pcg_opts *opts, igafd_pcg_info *infos,
+                                   void *stream);
+
 /* Default options: tol 1e-8, max_iter 1000, true_every 50, FP64,
  * Fletcher-Reeves, x0 = 0, check_every 4, timing off. */
 void igafd_pcg_default_opts(igafd_pcg_opts *opts);

@@ -58,6 +58,7 @@ void free_patch(igafd_patch *P) {
   cudaFree(P->r); cudaFree(P->z); cudaFree(P->pv_base); cudaFree(P->xpad_base);
   cudaFree(P->xs_base); cudaFree(P->bint); cudaFree(P->tstat);
   if (P->loop_exec) cudaGraphExecDestroy(P->loop_exec);
+  if (P->loop_graph) cudaGraphDestroy(P->loop_graph);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   cudaFree(P->q); cudaFree(P->xt);
   cudaFree(P->partial); cudaFree(P->counter); cudaFree(P->scal); cudaFree(P->err_flag);

@@ -96,6 +96,7 @@ struct igafd_patch {
   // captured PCG iteration chunk (replayed by cudaGraphLaunch)
   cudaStream_t cap_stream;
   cudaGraphExec_t loop_exec;
+  cudaGraph_t loop_graph;       // the captured chunk (child of batched parent graphs)
   long long loop_nodes;         // kernels per replay
   unsigned long long *tstat;    // stencil timing on the device: [0] earliest block start
                                 // of the running launch, [1] summed ns, [2] launches

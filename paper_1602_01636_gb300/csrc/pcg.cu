@@ -17,6 +17,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 namespace {
 
@@ -239,7 +240,7 @@ static igafd_status enqueue_iteration(igafd_patch *P, igafd_dtype dt, int flex, 
 // scalars to pinned host memory; with timing, the stencil launches stamp
 // their own start and end on the device clock (CUDA events recorded between
 // the nodes of a captured graph give no elapsed times). Rebuilt when its
-// parameters change.
+// parameters change; the un-instantiated graph is kept for batched solves.
 static igafd_status loop_graph(igafd_patch *P, igafd_dtype dt, int flex, int true_every, int chunk,
                                int timing) {
   const int key[5] = {(int)dt, flex, true_every, chunk, 1 + timing};
@@ -247,6 +248,10 @@ static igafd_status loop_graph(igafd_patch *P, igafd_dtype dt, int flex, int tru
   if (P->loop_exec) {
     cudaGraphExecDestroy(P->loop_exec);
     P->loop_exec = nullptr;
+  }
+  if (P->loop_graph) {
+    cudaGraphDestroy(P->loop_graph);
+    P->loop_graph = nullptr;
   }
   cudaStream_t cs = P->cap_stream;
   const long long l0 = g_igafd_launches.load();
@@ -267,20 +272,37 @@ static igafd_status loop_graph(igafd_patch *P, igafd_dtype dt, int flex, int tru
     return st != IGAFD_OK ? st : IGAFD_ERR_CUDA;
   }
   e = cudaGraphInstantiate(&P->loop_exec, g, 0);
-  cudaGraphDestroy(g);
   if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
     P->loop_exec = nullptr;
     cudaGetLastError();
     return IGAFD_ERR_CUDA;
   }
+  P->loop_graph = g;
   P->loop_nodes = nodes;
   memcpy(P->loop_key, key, sizeof(key));
   return IGAFD_OK;
 }
 
-extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *opts,
-                                        const double *b, double *x, igafd_pcg_info *info,
-                                        void *stream) {
+// Per-solve state of one problem (shared by the single and batched solves).
+struct SolveState {
+  igafd_pcg_opts o;
+  int flex;
+  double bb;
+  int k;                 // iterations enqueued
+  double rec_rr;         // recurrence (r, r) when the flag was raised
+  igafd_status status;
+  bool finished;
+  bool timing;
+  bool graphed;
+  double *x;
+  igafd_pcg_info inf;
+};
+
+// Set-up on patch-internal copies of b and x: r0 = b - A x0, z0 = P^{-1} r0,
+// rho0 = (r0, z0), p0 = z0. Synchronises once (to read (b, b)).
+static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, const double *b,
+                                double *x, cudaStream_t s, SolveState &S) {
   if (!P || !b || !x || b == x) return IGAFD_ERR_ARG;
   igafd_pcg_opts o;
   if (opts) o = *opts; else igafd_pcg_default_opts(&o);
@@ -288,23 +310,23 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
     return IGAFD_ERR_ARG;
   if (o.prec_dtype < IGAFD_FP64 || o.prec_dtype > IGAFD_TF32) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
-  cudaStream_t s = (cudaStream_t)stream;
+  S = SolveState{};
+  S.timing = o.timing != 0;
+  if (S.timing && o.check_every > 32) o.check_every = 32;
+  S.o = o;
+  S.flex = o.flexible ? 1 : 0;
+  S.x = x;
+  S.rec_rr = -1.0;
+  S.status = IGAFD_ERR_NOT_CONVERGED;
   const long long N = P->N;
   const dim3 G(IGAFD_RED_BLOCKS), B(256);
   double *scal = P->scal;
-  const int flex = o.flexible ? 1 : 0;
-  igafd_pcg_info inf{};
-  const bool timing = o.timing != 0;
-  if (timing && o.check_every > 32) o.check_every = 32;
-  cudaEvent_t *ev = P->ev;
-  if (timing) {
-    IGAFD_CUDA(cudaEventRecord(ev[IGAFD_NEV - 2], s));
+  if (S.timing) {
+    IGAFD_CUDA(cudaEventRecord(P->ev[IGAFD_NEV - 2], s));
     const unsigned long long init[3] = {~0ull, 0ull, 0ull};
     IGAFD_CUDA(cudaMemcpyAsync(P->tstat, init, sizeof(init), cudaMemcpyHostToDevice, s));
     IGAFD_CUDA(cudaStreamSynchronize(s));
   }
-
-  // set-up on patch-internal copies of b and x
   IGAFD_CUDA(cudaMemsetAsync(P->err_flag, 0, sizeof(int), s));
   init_scalars_kernel<<<1, 32, 0, s>>>(scal, o.tol * o.tol, (double)o.max_iter);
   IGAFD_LAUNCHED(1);
@@ -319,121 +341,250 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
     IGAFD_CUDA(cudaMemcpyAsync(P->r, P->bint, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   IGAFD_TRY(read_scalars(P, s));
-  const double bb = P->host_scal[S_BB];
-  if (!(bb > 0.0)) {
+  S.bb = P->host_scal[S_BB];
+  if (!(S.bb > 0.0)) {
     // b == 0: x = 0 is the solution; non-finite b: breakdown
-    inf.status = bb == 0.0 ? IGAFD_OK : IGAFD_ERR_BREAKDOWN;
-    if (bb == 0.0) IGAFD_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
-    IGAFD_CUDA(cudaStreamSynchronize(s));
-    if (info) *info = inf;
-    return (igafd_status)inf.status;
+    S.status = S.bb == 0.0 ? IGAFD_OK : IGAFD_ERR_BREAKDOWN;
+    if (S.bb == 0.0) IGAFD_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+    S.finished = true;
+    return IGAFD_OK;
   }
-  // z0 = P^{-1} r0, rho0 = (r0, z0), p0 = z0
   IGAFD_TRY(fd_apply(P, o.prec_dtype, P->r, P->z, s, nullptr));
-  dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 1, flex, 0);
+  dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 1, S.flex, 0);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaMemcpyAsync(P->pv, P->z, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   IGAFD_CUDA(cudaGetLastError());
+  S.finished = o.max_iter == 0;
+  S.graphed = loop_graph(P, o.prec_dtype, S.flex, o.true_every, o.check_every, S.timing ? 1 : 0) ==
+              IGAFD_OK;
+  return IGAFD_OK;
+}
 
-  const int chunk = o.check_every;
-  const bool graphed = loop_graph(P, o.prec_dtype, flex, o.true_every, chunk, timing ? 1 : 0) == IGAFD_OK;
-  int k = 0;               // iterations enqueued
-  double rec_rr = -1.0;    // recurrence (r, r) when the flag was raised
-  igafd_status status = IGAFD_ERR_NOT_CONVERGED;
-  bool finished = o.max_iter == 0;
-  while (!finished) {
-    if (graphed) {
-      IGAFD_CUDA(cudaGraphLaunch(P->loop_exec, s));
-      IGAFD_LAUNCHED(P->loop_nodes);
-      IGAFD_CUDA(cudaStreamSynchronize(s));
-      k += chunk;
-    } else {
-      for (int c = 0; c < chunk; ++c) {
-        ++k;
-        if (timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c], s));
-        IGAFD_TRY(igafd_stencil_launch(P, P->pv, P->q, nullptr, 1, 1, s));
-        if (timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 1], s));
-        update_xr_kernel<<<G, B, 0, s>>>(P->xs, P->r, P->pv, P->q, P->z, N, scal, P->partial,
-                                         P->counter, flex);
-        IGAFD_LAUNCHED(1);
-        if (o.true_every > 0)
-          IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, o.true_every));
-        if (timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 2], s));
-        IGAFD_TRY(fd_apply(P, o.prec_dtype, P->r, P->z, s, P->scal + S_DONE));
-        if (timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 3], s));
-        dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, flex, 1);
-        IGAFD_LAUNCHED(1);
-        update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 1);
-        IGAFD_LAUNCHED(1);
-        IGAFD_CUDA(cudaGetLastError());
-      }
-      IGAFD_TRY(read_scalars(P, s));
-      if (timing) {
-        for (int c = 0; c < chunk; ++c) {
-          float a = 0.f, b2 = 0.f;
-          cudaEventElapsedTime(&a, ev[4 * c], ev[4 * c + 1]);
-          cudaEventElapsedTime(&b2, ev[4 * c + 2], ev[4 * c + 3]);
-          inf.stencil_ms += a;
-          inf.prec_ms += b2;
-        }
-      }
+// A chunk of iterations without a graph (fallback), polled like the graph.
+static igafd_status run_chunk_direct(igafd_patch *P, cudaStream_t s, SolveState &S) {
+  const dim3 G(IGAFD_RED_BLOCKS), B(256);
+  const long long N = P->N;
+  double *scal = P->scal;
+  cudaEvent_t *ev = P->ev;
+  const int chunk = S.o.check_every;
+  for (int c = 0; c < chunk; ++c) {
+    if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c], s));
+    IGAFD_TRY(igafd_stencil_launch(P, P->pv, P->q, nullptr, 1, 1, s));
+    if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 1], s));
+    update_xr_kernel<<<G, B, 0, s>>>(P->xs, P->r, P->pv, P->q, P->z, N, scal, P->partial,
+                                     P->counter, S.flex);
+    IGAFD_LAUNCHED(1);
+    if (S.o.true_every > 0)
+      IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, S.o.true_every));
+    if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 2], s));
+    IGAFD_TRY(fd_apply(P, S.o.prec_dtype, P->r, P->z, s, P->scal + S_DONE));
+    if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 3], s));
+    dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 1);
+    IGAFD_LAUNCHED(1);
+    update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 1);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+  }
+  IGAFD_TRY(read_scalars(P, s));
+  if (S.timing) {
+    for (int c = 0; c < chunk; ++c) {
+      float a = 0.f, b2 = 0.f;
+      cudaEventElapsedTime(&a, ev[4 * c], ev[4 * c + 1]);
+      cudaEventElapsedTime(&b2, ev[4 * c + 2], ev[4 * c + 3]);
+      S.inf.stencil_ms += a;
+      S.inf.prec_ms += b2;
     }
-    const double *h = P->host_scal;
-    if (h[S_DONE] != 0.0) {
-      rec_rr = h[S_RR];
-      if (h[S_STATUS] != 0.0) {
-        status = (igafd_status)(int)h[S_STATUS];
-        break;
-      }
-      // converged by the recurrence: confirm with the true residual
-      IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 0, s));
-      IGAFD_TRY(read_scalars(P, s));
-      if (h[S_TRUE_RR] <= o.tol * o.tol * bb) {
-        status = IGAFD_OK;
-        break;
-      }
-      // not confirmed: continue from the true residual
-      if ((int)h[S_ITER] >= o.max_iter) break;
-      set_scalar_kernel<<<1, 32, 0, s>>>(scal, S_DONE, 0.0);
-      IGAFD_LAUNCHED(1);
-      IGAFD_TRY(fd_apply(P, o.prec_dtype, P->r, P->z, s, nullptr));
-      dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, flex, 0);
-      IGAFD_LAUNCHED(1);
-      update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 0);
-      IGAFD_LAUNCHED(1);
-      IGAFD_CUDA(cudaGetLastError());
-      k = (int)h[S_ITER];
+  }
+  return IGAFD_OK;
+}
+
+// After a chunk (its scalars are in P->host_scal): stopping decisions and,
+// when the recurrence says converged, the true-residual confirmation.
+static igafd_status solve_after_chunk(igafd_patch *P, cudaStream_t s, SolveState &S) {
+  const dim3 G(IGAFD_RED_BLOCKS), B(256);
+  const long long N = P->N;
+  double *scal = P->scal;
+  S.k += S.o.check_every;
+  const double *h = P->host_scal;
+  if (h[S_DONE] != 0.0) {
+    S.rec_rr = h[S_RR];
+    if (h[S_STATUS] != 0.0) {
+      S.status = (igafd_status)(int)h[S_STATUS];
+      S.finished = true;
+      return IGAFD_OK;
     }
-    if (k >= o.max_iter) finished = true;
+    IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 0, s));
+    IGAFD_TRY(read_scalars(P, s));
+    if (h[S_TRUE_RR] <= S.o.tol * S.o.tol * S.bb) {
+      S.status = IGAFD_OK;
+      S.finished = true;
+      return IGAFD_OK;
+    }
+    // not confirmed: continue from the true residual
+    if ((int)h[S_ITER] >= S.o.max_iter) {
+      S.finished = true;
+      return IGAFD_OK;
+    }
+    set_scalar_kernel<<<1, 32, 0, s>>>(scal, S_DONE, 0.0);
+    IGAFD_LAUNCHED(1);
+    IGAFD_TRY(fd_apply(P, S.o.prec_dtype, P->r, P->z, s, nullptr));
+    dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 0);
+    IGAFD_LAUNCHED(1);
+    update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 0);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+    S.k = (int)h[S_ITER];
+  }
+  if (S.k >= S.o.max_iter) S.finished = true;
+  return IGAFD_OK;
+}
+
+static igafd_status solve_end(igafd_patch *P, cudaStream_t s, SolveState &S) {
+  igafd_pcg_info &inf = S.inf;
+  if (!(S.bb > 0.0)) {
+    inf.status = S.status;
+    IGAFD_CUDA(cudaStreamSynchronize(s));
+    return S.status;
   }
   IGAFD_TRY(read_scalars(P, s));
   inf.iterations = (int)P->host_scal[S_ITER];
-  inf.relres = sqrt((rec_rr >= 0.0 && status == IGAFD_OK ? rec_rr : P->host_scal[S_RR]) / bb);
-  if (P->host_scal[S_TRUE_RR] < 0.0 || status != IGAFD_OK) {
+  inf.relres = sqrt((S.rec_rr >= 0.0 && S.status == IGAFD_OK ? S.rec_rr : P->host_scal[S_RR]) / S.bb);
+  if (P->host_scal[S_TRUE_RR] < 0.0 || S.status != IGAFD_OK) {
     // true residual of the returned iterate (into the scratch vector)
     IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->xt, P->bint, 1, 0, s));
     IGAFD_TRY(read_scalars(P, s));
   }
-  inf.true_relres = sqrt(P->host_scal[S_TRUE_RR] / bb);
-  IGAFD_CUDA(cudaMemcpyAsync(x, P->xs, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  inf.true_relres = sqrt(P->host_scal[S_TRUE_RR] / S.bb);
+  IGAFD_CUDA(cudaMemcpyAsync(S.x, P->xs, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   int herr = 0;
   IGAFD_CUDA(cudaMemcpyAsync(&herr, P->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   IGAFD_CUDA(cudaStreamSynchronize(s));
-  if (herr != 0 && status == IGAFD_OK) status = (igafd_status)herr;
-  inf.status = status;
-  if (timing) {
+  if (herr != 0 && S.status == IGAFD_OK) S.status = (igafd_status)herr;
+  inf.status = S.status;
+  if (S.timing) {
+    cudaEvent_t *ev = P->ev;
     IGAFD_CUDA(cudaEventRecord(ev[IGAFD_NEV - 1], s));
     IGAFD_CUDA(cudaEventSynchronize(ev[IGAFD_NEV - 1]));
     float t = 0.f;
     cudaEventElapsedTime(&t, ev[IGAFD_NEV - 2], ev[IGAFD_NEV - 1]);
     inf.solve_ms = t;
-    if (graphed) {   // in-loop stencil launches timed on the device clock
+    if (S.graphed) {   // in-loop stencil launches timed on the device clock
       unsigned long long h[3];
       IGAFD_CUDA(cudaMemcpy(h, P->tstat, sizeof(h), cudaMemcpyDeviceToHost));
       inf.stencil_ms = h[1] * 1e-6;
       inf.prec_ms = -1.0;   // FD applies are not individually timed inside the graph
     }
   }
-  if (info) *info = inf;
-  return status;
+  return S.status;
+}
+
+extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *opts,
+                                        const double *b, double *x, igafd_pcg_info *info,
+                                        void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  SolveState S;
+  IGAFD_TRY(solve_begin(P, opts, b, x, s, S));
+  while (!S.finished) {
+    if (S.graphed) {
+      IGAFD_CUDA(cudaGraphLaunch(P->loop_exec, s));
+      IGAFD_LAUNCHED(P->loop_nodes);
+      IGAFD_CUDA(cudaStreamSynchronize(s));
+    } else {
+      IGAFD_TRY(run_chunk_direct(P, s, S));
+    }
+    IGAFD_TRY(solve_after_chunk(P, s, S));
+  }
+  const igafd_status st = solve_end(P, s, S);
+  if (info) *info = S.inf;
+  return st;
+}
+
+// ---- batched solve -----------------------------------------------------------
+// Every problem keeps its own captured chunk graph; one parent graph holds
+// them as independent child nodes, so a single graph launch advances all
+// unfinished problems concurrently. Problems that have finished are dropped
+// from the parent graph when at least half of its members are done.
+static igafd_status build_parent(igafd_patch *const *ps, const std::vector<int> &active,
+                                 cudaGraphExec_t *exec, long long *nodes) {
+  cudaGraph_t parent = nullptr;
+  IGAFD_CUDA(cudaGraphCreate(&parent, 0));
+  long long n = 0;
+  for (int i : active) {
+    cudaGraphNode_t node;
+    if (cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, ps[i]->loop_graph) != cudaSuccess) {
+      cudaGraphDestroy(parent);
+      cudaGetLastError();
+      return IGAFD_ERR_CUDA;
+    }
+    n += ps[i]->loop_nodes;
+  }
+  cudaError_t e = cudaGraphInstantiate(exec, parent, 0);
+  cudaGraphDestroy(parent);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return IGAFD_ERR_CUDA;
+  }
+  *nodes = n;
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_batch_pcg_solve(igafd_patch *const *patches, int count,
+                                              const double *const *b, double *const *x,
+                                              const igafd_pcg_opts *opts, igafd_pcg_info *infos,
+                                              void *stream) {
+  if (!patches || count < 1 || !b || !x) return IGAFD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  igafd_pcg_opts o;
+  if (opts) o = *opts; else igafd_pcg_default_opts(&o);
+  o.timing = 0;   // per-problem timing is not available inside the batch graph
+  for (int i = 0; i < count; ++i) {
+    if (!patches[i]) return IGAFD_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (patches[j] == patches[i]) return IGAFD_ERR_ARG;   // one problem per patch
+    if (patches[i]->dev != patches[0]->dev) return IGAFD_ERR_ARG;
+  }
+  std::vector<SolveState> S(count);
+  std::vector<int> active;
+  for (int i = 0; i < count; ++i) {
+    IGAFD_TRY(solve_begin(patches[i], &o, b[i], x[i], s, S[i]));
+    if (!S[i].finished) {
+      if (!S[i].graphed) return IGAFD_ERR_CUDA;
+      active.push_back(i);
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  long long nodes = 0;
+  size_t built_for = 0;
+  igafd_status st = IGAFD_OK;
+  while (!active.empty() && st == IGAFD_OK) {
+    if (!exec || active.size() * 2 <= built_for) {
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      st = build_parent(patches, active, &exec, &nodes);
+      if (st != IGAFD_OK) break;
+      built_for = active.size();
+    }
+    if (cudaGraphLaunch(exec, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+      st = IGAFD_ERR_CUDA;
+      break;
+    }
+    IGAFD_LAUNCHED(nodes);
+    std::vector<int> still;
+    for (int i : active) {
+      // problems already finished but still in the parent graph only ran no-op kernels
+      st = solve_after_chunk(patches[i], s, S[i]);
+      if (st != IGAFD_OK) break;
+      if (!S[i].finished) still.push_back(i);
+    }
+    active.swap(still);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (st != IGAFD_OK) return st;
+  igafd_status worst = IGAFD_OK;
+  for (int i = 0; i < count; ++i) {
+    const igafd_status e = solve_end(patches[i], s, S[i]);
+    if (infos) infos[i] = S[i].inf;
+    if (e != IGAFD_OK && worst == IGAFD_OK) worst = e;
+  }
+  return worst;
 }

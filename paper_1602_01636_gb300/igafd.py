@@ -64,7 +64,7 @@ _lib = None
 EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "igafd_get_eigen",
            "igafd_copy_stencil", "igafd_apply_A", "igafd_apply_prec", "igafd_load_rhs_sine",
            "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str",
-           "igafd_kernel_launches"]
+           "igafd_kernel_launches", "igafd_batch_pcg_solve"]
 
 
 def lib():
@@ -87,6 +87,8 @@ def lib():
     L.igafd_apply_prec.argtypes = [vp, C.c_int, vp, vp, vp]
     L.igafd_load_rhs_sine.argtypes = [vp, vp, vp]
     L.igafd_pcg_solve.argtypes = [vp, C.POINTER(PCGOpts), vp, vp, C.POINTER(PCGInfo), vp]
+    L.igafd_batch_pcg_solve.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp),
+                                        C.POINTER(PCGOpts), C.POINTER(PCGInfo), vp]
     L.igafd_pcg_default_opts.argtypes = [C.POINTER(PCGOpts)]
     L.igafd_pcg_default_opts.restype = None
     L.igafd_status_str.argtypes = [C.c_int]
@@ -124,6 +126,36 @@ def _dev_ptr(t, n=None):
     if n is not None and t.numel() != n:
         raise ValueError(f"expected {n} elements, got {t.numel()}")
     return C.c_void_p(t.data_ptr())
+
+
+def _opts(tol, max_iter, dtype, flexible, true_every, check_every, timing=False):
+    o = PCGOpts()
+    lib().igafd_pcg_default_opts(C.byref(o))
+    o.tol, o.max_iter, o.true_every, o.check_every = tol, max_iter, true_every, check_every
+    o.prec_dtype = DTYPES[dtype]
+    o.flexible = int(dtype != "fp64") if flexible is None else int(flexible)
+    o.timing = int(bool(timing))
+    return o
+
+
+def batch_pcg(patches, bs, xs=None, tol=1e-8, max_iter=1000, dtype="fp64", flexible=None,
+              true_every=50, check_every=4, raise_on_error=True):
+    """Solve patches[i] x_i = bs[i] for all i in one batched solve (one CUDA
+    graph launch advances every unfinished problem). Returns (xs, infos)."""
+    import torch
+    n = len(patches)
+    if xs is None:
+        xs = [torch.zeros_like(b) for b in bs]
+    o = _opts(tol, max_iter, dtype, flexible, true_every, check_every)
+    vp = C.c_void_p
+    hp = (vp * n)(*[p.h for p in patches])
+    hb = (vp * n)(*[_dev_ptr(b, p.N) for p, b in zip(patches, bs)])
+    hx = (vp * n)(*[_dev_ptr(x, p.N) for p, x in zip(patches, xs)])
+    infos = (PCGInfo * n)()
+    st = lib().igafd_batch_pcg_solve(hp, n, hb, hx, C.byref(o), infos, _stream())
+    if raise_on_error and st not in (OK, ERR_NOT_CONVERGED):
+        raise IgafdError(st, "batch_pcg_solve")
+    return xs, list(infos)
 
 
 class Patch:

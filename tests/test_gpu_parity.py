@@ -250,3 +250,35 @@ def test_full_size_sampled(torch):
         res.append(b[disc.row_index(i)] - acc)
     assert np.abs(res).max() <= 1e-6 * np.abs(b).max()
     patch.close()
+
+
+def test_batched_solve_matches_single_solves(torch):
+    """Config-4-like batch (uneven n per axis, p in {2,3,4}, a_k ~ U(-0.1, 0.1),
+    N(0,1) right-hand sides): one batched solve gives bitwise the iterates
+    and iteration counts of one-by-one solves, for the FP64 and a tensor-core
+    preconditioner."""
+    from paper_1602_01636_gb300 import igafd
+    g = synth.rng(404)
+    probs = []
+    for i in range(5):
+        n = tuple(int(v) for v in g.integers(10, 24, 3))
+        p = int(g.integers(2, 5))
+        probs.append(synth.Problem(3, n, p, g.uniform(-0.1, 0.1, 3)))
+    probs.append(synth.Problem(2, (33, 17), 3))
+    patches = [make_patch(pr) for pr in probs]
+    bs = [to_dev(synth.random_rhs(p.N, 50 + i)) for i, p in enumerate(patches)]
+    for dt in ("fp64", "bf16"):
+        xs, infos = igafd.batch_pcg(patches, bs, tol=1e-10, dtype=dt)
+        for p, b, x, inf in zip(patches, bs, xs, infos):
+            xr, ir = p.pcg(b, tol=1e-10, dtype=dt)
+            assert inf.status == 0 and inf.iterations == ir.iterations
+            assert torch.equal(x, xr)
+    # and against the oracle for one member
+    disc = assemble.Discretization.from_problem(probs[0])
+    A = assemble.stencil_to_csr(disc, disc.assemble_stencil())
+    F = fd.FD([disc.pencil(k) for k in range(3)])
+    ro = pcg.pcg(lambda v: A @ v, bs[0].cpu().numpy(), F.apply, tol=1e-13, max_iter=500)
+    xs, _ = igafd.batch_pcg(patches, bs, tol=1e-12, dtype="fp64")
+    assert rel(xs[0].cpu().numpy(), ro.x) <= 1e-10
+    for p in patches:
+        p.close()
