@@ -251,6 +251,7 @@ def run_ours(args):
     dtype = args.dtype or "tf32"
     prob = synth.deformed_cube(n, p, seed=0)
     patch = igafd.Patch.from_problem(prob)
+    stages = patch.autotune()          # untimed: picks the stencil pipeline depth
     N = patch.N
     b = patch.load_rhs_sine()
     x = torch.zeros_like(b)
@@ -407,6 +408,7 @@ def run_ours(args):
             "mixed_vs_fp64_solution_rel_diff": diff,
             "true_relres": {"mixed": infos[-1].true_relres, "fp64": inf64.true_relres},
             "setup_ms": patch.info.setup_ms, "eig_ms": patch.info.eig_ms,
+            "autotuned_stencil_stages": stages,
             "phase_ms_per_step": {"stencil": sum(i.stencil_ms for i in infos) / len(infos),
                                   "prec_estimate": it_mixed / aps_mixed * 1e3},
             "roofline": {"bound": "alu", "kernel": "stencil_kernel (q = A p, fused (p, q))",
@@ -470,6 +472,7 @@ def run_batch(args):
                 redraws += 1
         if patch is None:
             raise RuntimeError(f"problem {i}: no unfolded geometry in 100 draws")
+        patch.autotune()
         patches.append(patch)
         bs.append(torch.from_numpy(synth.random_rhs(patch.N, 9000 + i)).cuda())
         meta.append({"n": n, "p": p})

@@ -85,6 +85,7 @@ typedef struct {
   double setup_ms;     /* device time of the last igafd_setup_patch */
   double eig_ms;       /* of which the generalized eigendecompositions */
   long long stencil_bytes;
+  int stencil_stages;  /* ring depth of the stencil pipeline in use (autotuned) */
 } igafd_patch_info;
 
 typedef struct {
@@ -216,6 +217,19 @@ const char *igafd_status_str(igafd_status s);
 igafd_status igafd_apply_prec_static(int dim, const int *n, const double *const *U,
                                      const double *const *D, const double *r_dev,
                                      double *z_dev, void *stream);
+
+/* Time the candidate configurations of the A stencil's pipeline (ring depth
+ * 3, 4 or 6 offset groups in flight per CTA) on this patch and keep the
+ * fastest. Results are cached per process by (dim, p, n_1, n_2, n_3, SM
+ * count) and, if the environment variable IGAFD_TUNE_CACHE names a file,
+ * appended to it (one JSON object per line); igafd_setup_patch applies a
+ * cached choice without measuring. flags bit 0: measure even if cached.
+ * Synchronises the stream; must not overlap a solve on the same patch. */
+igafd_status igafd_autotune(igafd_patch *patch, int flags, void *stream);
+
+/* Set the stencil pipeline's ring depth by hand (3, 4 or 6; else
+ * IGAFD_ERR_ARG). Every depth computes bitwise the same products. */
+igafd_status igafd_set_stencil_stages(igafd_patch *patch, int stages);
 
 /* Number of kernels this library has enqueued in this process so far (all
  * devices, all patches); for launch accounting by benchmarks. */

@@ -131,6 +131,7 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
   }
   IGAFD_TRY(igafd_setup_stencil(P, s));
   IGAFD_TRY(igafd_fd_tc_init(P, s));
+  igafd_tune_lookup(P);
   IGAFD_CUDA(cudaStreamSynchronize(s));
   return IGAFD_OK;
 }
@@ -209,6 +210,7 @@ extern "C" igafd_status igafd_patch_query(const igafd_patch *P, igafd_patch_info
   info->setup_ms = P->setup_ms;
   info->eig_ms = P->eig_ms;
   info->stencil_bytes = (long long)P->n_off * P->N * (long long)sizeof(double);
+  info->stencil_stages = P->stencil_stages > 0 ? P->stencil_stages : 4;
   return IGAFD_OK;
 }
 

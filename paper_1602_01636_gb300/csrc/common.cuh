@@ -83,6 +83,7 @@ struct igafd_patch {
   double *stencil;
   long long Np;
   int num_sms;
+  int stencil_stages;           // ring depth of the stencil pipeline (0: default; autotuned)
   // FD workspace
   double *fd_a, *fd_b;          // N each
   // PCG workspace
@@ -137,6 +138,7 @@ igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, co
                                   unsigned long long *tstat = nullptr);
 long long igafd_stencil_row_stride(long long N);   // Np for a given N
 long long igafd_stencil_halo(int p, const int *n);   // zero halo of padded vectors
+void igafd_tune_lookup(igafd_patch *P);              // apply a cached autotune choice
 
 // Kernels enqueued by this library (process-wide), for launch accounting.
 extern std::atomic<long long> g_igafd_launches;

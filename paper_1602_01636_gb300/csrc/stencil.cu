@@ -21,15 +21,14 @@
 
 namespace {
 
-#ifndef IGAFD_STENCIL_STAGES
-#define IGAFD_STENCIL_STAGES 4
-#endif
 #ifndef IGAFD_STENCIL_NACC
 #define IGAFD_STENCIL_NACC 1
 #endif
 constexpr int kTile = 256;                        // rows per tile = compute threads per CTA
-constexpr int kStages = IGAFD_STENCIL_STAGES;     // offset groups in flight per CTA
 constexpr int kAcc = IGAFD_STENCIL_NACC;          // independent FMA chains per row
+// ring depths (offset groups in flight per CTA) the kernel is built for; the
+// autotuner picks one per (dimension, degree, sizes), default kStagesDefault
+constexpr int kStagesDefault = 4;
 constexpr long long kSpin = 1ll << 26;   // mbarrier poll limit (~seconds)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -131,7 +130,7 @@ struct Geom {
 //
 // MODE 0: y = A x, dot (x, y) -> alpha = rho / (x, y) when pcg.
 // MODE 1: y = b - A x, dot (y, y) -> true (r, r) when pcg.
-template <int DIM, int P, int MODE>
+template <int DIM, int P, int MODE, int kStages>
 __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) {
   if (a.done && *a.done != 0.0) return;
   if (a.every > 0 && ((long long)a.scal[S_ITER]) % a.every != 0) return;
@@ -303,10 +302,10 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
   }
 }
 
-template <int DIM, int P, int MODE>
+template <int DIM, int P, int MODE, int kStages>
 igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, cudaStream_t s) {
   const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
-  auto kern = stencil_tma_kernel<DIM, P, MODE>;
+  auto kern = stencil_tma_kernel<DIM, P, MODE, kStages>;
   static int per_sm = 0;   // resident CTAs per SM for this instantiation
   if (per_sm == 0) {
     IGAFD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -323,16 +322,25 @@ igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, c
   return IGAFD_OK;
 }
 
+template <int DIM, int P, int MODE>
+igafd_status launch_stages(int stages, const StencilArgs &a, long long cap, int sms, cudaStream_t s) {
+  switch (stages) {
+    case 3: return launch_one<DIM, P, MODE, 3>(a, cap, sms, s);
+    case 6: return launch_one<DIM, P, MODE, 6>(a, cap, sms, s);
+    default: return launch_one<DIM, P, MODE, 4>(a, cap, sms, s);
+  }
+}
+
 template <int DIM, int MODE>
-igafd_status launch_p(int p, const StencilArgs &a, long long cap, int sms, cudaStream_t s) {
+igafd_status launch_p(int p, int stages, const StencilArgs &a, long long cap, int sms, cudaStream_t s) {
   switch (p) {
-    case 1: return launch_one<DIM, 1, MODE>(a, cap, sms, s);
-    case 2: return launch_one<DIM, 2, MODE>(a, cap, sms, s);
-    case 3: return launch_one<DIM, 3, MODE>(a, cap, sms, s);
-    case 4: return launch_one<DIM, 4, MODE>(a, cap, sms, s);
-    case 5: return launch_one<DIM, 5, MODE>(a, cap, sms, s);
-    case 6: return launch_one<DIM, 6, MODE>(a, cap, sms, s);
-    case 7: return launch_one<DIM, 7, MODE>(a, cap, sms, s);
+    case 1: return launch_stages<DIM, 1, MODE>(stages, a, cap, sms, s);
+    case 2: return launch_stages<DIM, 2, MODE>(stages, a, cap, sms, s);
+    case 3: return launch_stages<DIM, 3, MODE>(stages, a, cap, sms, s);
+    case 4: return launch_stages<DIM, 4, MODE>(stages, a, cap, sms, s);
+    case 5: return launch_stages<DIM, 5, MODE>(stages, a, cap, sms, s);
+    case 6: return launch_stages<DIM, 6, MODE>(stages, a, cap, sms, s);
+    case 7: return launch_stages<DIM, 7, MODE>(stages, a, cap, sms, s);
     default: return IGAFD_ERR_ARG;
   }
 }
@@ -383,10 +391,11 @@ igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, co
   // persistent grid: the resident CTAs of every SM, never more than the
   // tiles or the partial-sum slots
   long long cap = a.ntiles < IGAFD_RED_BLOCKS ? a.ntiles : IGAFD_RED_BLOCKS;
+  const int st = P->stencil_stages > 0 ? P->stencil_stages : kStagesDefault;
   if (P->dim == 3) {
-    if (b) return launch_p<3, 1>(P->p, a, cap, P->num_sms, s);
-    return launch_p<3, 0>(P->p, a, cap, P->num_sms, s);
+    if (b) return launch_p<3, 1>(P->p, st, a, cap, P->num_sms, s);
+    return launch_p<3, 0>(P->p, st, a, cap, P->num_sms, s);
   }
-  if (b) return launch_p<2, 1>(P->p, a, cap, P->num_sms, s);
-  return launch_p<2, 0>(P->p, a, cap, P->num_sms, s);
+  if (b) return launch_p<2, 1>(P->p, st, a, cap, P->num_sms, s);
+  return launch_p<2, 0>(P->p, st, a, cap, P->num_sms, s);
 }

@@ -1,0 +1,134 @@
+// Autotuner for the hot kernels of a patch.
+//
+// The stencil pipeline is built for several ring depths (offset groups in
+// flight per CTA: 3, 4, 6). The best depth depends on the degree (bytes per
+// stage grow with 2p+1, trading shared memory per CTA against resident CTAs
+// per SM) and on the sizes, so it is measured: each candidate applies A a
+// few times to the patch's own search-direction buffer, timed with CUDA
+// events, and the fastest is kept in the patch. Results are cached per
+// process, keyed by (dim, p, n_1, n_2, n_3, SM count), and, when the
+// environment variable IGAFD_TUNE_CACHE names a file, in that file (one JSON
+// object per line), so later processes reuse them without measuring.
+#include "common.cuh"
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+namespace {
+
+struct TuneEntry {
+  int stages;
+  float ms[3];
+};
+
+std::mutex g_tune_mutex;
+std::map<std::string, TuneEntry> g_tune;
+bool g_tune_loaded = false;
+const int kCandidates[3] = {3, 4, 6};
+
+std::string tune_key(const igafd_patch *P) {
+  char buf[128];
+  snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%d:sm%d", P->dim, P->p, P->n[0], P->n[1], P->n[2],
+           P->num_sms);
+  return buf;
+}
+
+// lines: {"key": "3:3:128:128:128:sm152", "stencil_stages": 4, "ms": [a, b, c]}
+void load_file_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char *path = getenv("IGAFD_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof(line), f)) {
+    char key[128];
+    TuneEntry e{};
+    if (sscanf(line, " {\"key\": \"%127[^\"]\", \"stencil_stages\": %d, \"ms\": [%f, %f, %f]",
+               key, &e.stages, &e.ms[0], &e.ms[1], &e.ms[2]) == 5)
+      g_tune[key] = e;
+  }
+  fclose(f);
+}
+
+void append_file_locked(const std::string &key, const TuneEntry &e) {
+  const char *path = getenv("IGAFD_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"key\": \"%s\", \"stencil_stages\": %d, \"ms\": [%.5f, %.5f, %.5f]}\n",
+          key.c_str(), e.stages, e.ms[0], e.ms[1], e.ms[2]);
+  fclose(f);
+}
+
+}  // namespace
+
+// Apply a cached choice (if any) at set-up time; measures nothing.
+void igafd_tune_lookup(igafd_patch *P) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  load_file_locked();
+  auto it = g_tune.find(tune_key(P));
+  if (it != g_tune.end()) P->stencil_stages = it->second.stages;
+}
+
+extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) {
+  if (!P) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(P->dev));
+  const std::string key = tune_key(P);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    load_file_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end() && !(flags & 1)) {
+      P->stencil_stages = it->second.stages;
+      return IGAFD_OK;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  IGAFD_CUDA(cudaEventCreate(&e0));
+  IGAFD_CUDA(cudaEventCreate(&e1));
+  TuneEntry best{};
+  best.stages = 4;
+  float best_ms = 1e30f;
+  const int saved = P->stencil_stages;
+  igafd_status st = IGAFD_OK;
+  for (int c = 0; c < 3 && st == IGAFD_OK; ++c) {
+    P->stencil_stages = kCandidates[c];
+    st = igafd_stencil_launch(P, P->pv, P->q, nullptr, 0, 0, s);     // warm-up
+    if (st != IGAFD_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 5 && st == IGAFD_OK; ++r) st = igafd_stencil_launch(P, P->pv, P->q, nullptr, 0, 0, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st = IGAFD_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best.ms[c] = ms / 5;
+    if (best.ms[c] < best_ms) {
+      best_ms = best.ms[c];
+      best.stages = kCandidates[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != IGAFD_OK) {
+    P->stencil_stages = saved;
+    return st;
+  }
+  P->stencil_stages = best.stages;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune[key] = best;
+  append_file_locked(key, best);
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_set_stencil_stages(igafd_patch *P, int stages) {
+  if (!P || (stages != 3 && stages != 4 && stages != 6)) return IGAFD_ERR_ARG;
+  P->stencil_stages = stages;
+  return IGAFD_OK;
+}

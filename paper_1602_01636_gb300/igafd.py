@@ -44,7 +44,7 @@ class PatchInfo(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("n", C.c_int * 3), ("N", C.c_longlong),
                 ("nel", C.c_int * 3), ("n_offsets", C.c_int), ("min_detJ", C.c_double),
                 ("q_bound", C.c_double), ("setup_ms", C.c_double), ("eig_ms", C.c_double),
-                ("stencil_bytes", C.c_longlong)]
+                ("stencil_bytes", C.c_longlong), ("stencil_stages", C.c_int)]
 
 
 class PCGOpts(C.Structure):
@@ -64,7 +64,8 @@ _lib = None
 EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "igafd_get_eigen",
            "igafd_copy_stencil", "igafd_apply_A", "igafd_apply_prec", "igafd_load_rhs_sine",
            "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str",
-           "igafd_kernel_launches", "igafd_batch_pcg_solve"]
+           "igafd_kernel_launches", "igafd_batch_pcg_solve", "igafd_autotune",
+           "igafd_set_stencil_stages"]
 
 
 def lib():
@@ -89,6 +90,8 @@ def lib():
     L.igafd_pcg_solve.argtypes = [vp, C.POINTER(PCGOpts), vp, vp, C.POINTER(PCGInfo), vp]
     L.igafd_batch_pcg_solve.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp),
                                         C.POINTER(PCGOpts), C.POINTER(PCGInfo), vp]
+    L.igafd_autotune.argtypes = [vp, C.c_int, vp]
+    L.igafd_set_stencil_stages.argtypes = [vp, C.c_int]
     L.igafd_pcg_default_opts.argtypes = [C.POINTER(PCGOpts)]
     L.igafd_pcg_default_opts.restype = None
     L.igafd_status_str.argtypes = [C.c_int]
@@ -204,6 +207,17 @@ class Patch:
         _check(lib().igafd_get_eigen(self.h, k, U.ctypes.data_as(dp), D.ctypes.data_as(dp)),
                "get_eigen")
         return D, U
+
+    def autotune(self, force=False):
+        """Measure the stencil pipeline's candidate ring depths on this patch
+        and keep the fastest; returns the chosen depth."""
+        _check(lib().igafd_autotune(self.h, int(bool(force)), _stream()), "autotune")
+        self.info = self.query()
+        return self.info.stencil_stages
+
+    def set_stencil_stages(self, stages):
+        _check(lib().igafd_set_stencil_stages(self.h, int(stages)), "set_stencil_stages")
+        self.info = self.query()
 
     def stencil(self):
         import torch
