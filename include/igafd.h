@@ -71,6 +71,14 @@ typedef struct {
                                        (coordinate slowest, direction 1 fastest),
                                        g_k = geo_n_knots[k] - geo_p - 1 */
   double kappa;                     /* constant scalar coefficient K = kappa I */
+  /* Optional variable coefficient: K(x) = kappa * c(zeta) I with c a
+   * degree-kappa_p tensor spline on its own open knot vectors and control
+   * values kappa_ctrl [c_d]..[c_1] (direction 1 fastest), all > 0 so that
+   * c > 0 everywhere. kappa_ctrl == NULL: constant kappa. */
+  int kappa_p;
+  const int *kappa_n_knots;
+  const double *const *kappa_knots;
+  const double *kappa_ctrl;
 } igafd_patch_desc;
 
 typedef struct {
@@ -230,6 +238,62 @@ igafd_status igafd_autotune(igafd_patch *patch, int flags, void *stream);
 /* Set the stencil pipeline's ring depth by hand (3, 4 or 6; else
  * IGAFD_ERR_ARG). Every depth computes bitwise the same products. */
 igafd_status igafd_set_stencil_stages(igafd_patch *patch, int stages);
+
+/* ---- learned span scalings of the pencils -------------------------------
+ * Prop. 1 bounds kappa(P^{-1} A) by the spread of the eigenvalues of Q. The
+ * element contributions of the 1D pencils can be weighted per span,
+ * K~_k = sum_e wK_{k,e} K_k^(e), M~_k = sum_e wM_{k,e} M_k^(e); P stays a
+ * Kronecker sum, so the fast diagonalization applies unchanged, while term k
+ * of P follows Q_kk more closely. Rows r <-> (direction k, span e) in
+ * direction-major order, r = sum_{l<k} nel_l + e; igafd_scaling_rows gives
+ * their number. These calls allocate temporary device memory. */
+igafd_status igafd_scaling_rows(const igafd_patch *patch, int *rows);
+
+/* Per-row features of Q over the slab of quadrature points whose direction-k
+ * coordinate lies in span e: [log mean Q_kk, log mean of the other diagonal
+ * entries, log min lambda_min(Q), log max lambda_max(Q), std of log Q_kk,
+ * span centre]. feat_dev: float [rows][6]. Synchronises the stream. */
+igafd_status igafd_patch_features(igafd_patch *patch, float *feat_dev, void *stream);
+
+/* Separable least-squares fit of log Q_kk over all quadrature points by
+ * log wK_k(zeta_k) + sum_{l != k} log wM_l(zeta_l) (backfitting, `sweeps`
+ * rounds of slab means; the mean of each log wM_l is fixed to 0).
+ * logw_dev: float [rows][2] = (log wK, log wM). Synchronises the stream. */
+igafd_status igafd_patch_sepfit(igafd_patch *patch, int sweeps, float *logw_dev, void *stream);
+
+/* Rebuild the preconditioner from span-scaled pencils: logw_dev float
+ * [rows][2] of (log wK, log wM), or NULL for the unscaled pencils (the
+ * paper's P). Recomputes the eigendecompositions and every FD factor.
+ * Synchronises the stream. */
+igafd_status igafd_set_scalings(igafd_patch *patch, const float *logw_dev, void *stream);
+
+/* The scaling network: 6 -> 64 -> 64 -> 2, tanh, FP16 weights in the forward
+ * pass with FP32 arithmetic; FP32 master weights and Adam for training.
+ * Parameter layout (floats): W1[64][6], b1[64], W2[64][64], b2[64],
+ * W3[2][64], b3[2]. Inputs are normalised by (x - in_mean) / in_std and the
+ * outputs mapped back by out_mean + out_std * net(x). */
+#define IGAFD_MLP_PARAMS 4738
+typedef struct igafd_mlp igafd_mlp;
+/* params_host: IGAFD_MLP_PARAMS initial values (NULL: zeros). */
+igafd_status igafd_mlp_create(const float *params_host, igafd_mlp **out);
+void igafd_mlp_destroy(igafd_mlp *mlp);
+igafd_status igafd_mlp_set_normalization(igafd_mlp *mlp, const float *in_mean,
+                                         const float *in_std, const float *out_mean,
+                                         const float *out_std);
+igafd_status igafd_mlp_get_params(const igafd_mlp *mlp, float *params_host);
+igafd_status igafd_mlp_set_params(igafd_mlp *mlp, const float *params_host);
+/* Y_dev float [rows][2] = network(X_dev float [rows][6]). */
+igafd_status igafd_mlp_forward(igafd_mlp *mlp, const float *X_dev, int rows, float *Y_dev,
+                               void *stream);
+/* Gradient of the mean squared error of the normalised outputs against the
+ * normalised targets T_dev float [rows][2], w.r.t. every parameter
+ * (grad_host: IGAFD_MLP_PARAMS floats, may be NULL) and the loss. */
+igafd_status igafd_mlp_gradient(igafd_mlp *mlp, const float *X_dev, const float *T_dev, int rows,
+                                float *grad_host, float *loss_host, void *stream);
+/* One Adam step (beta 0.9 / 0.999) on that loss; loss_host (optional) gets
+ * the loss before the step. */
+igafd_status igafd_mlp_train_step(igafd_mlp *mlp, const float *X_dev, const float *T_dev,
+                                  int rows, float lr, float *loss_host, void *stream);
 
 /* Number of kernels this library has enqueued in this process so far (all
  * devices, all patches); for launch accounting by benchmarks. */

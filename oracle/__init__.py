@@ -19,7 +19,9 @@ Modules
   fd        Algorithms 1 and 3: generalized eigendecomposition via Cholesky,
             fast-diagonalization solve of P s = r
   pcg       preconditioned conjugate gradients (the paper's outer solver)
+  learned   span scalings of the pencils: features of Q, separable log-fit,
+            and the scaling network with its gradient
 
 Readings where the paper is silent or garbled are stated at each function.
 """
-from . import spline, assemble, fd, pcg  # noqa: F401
+from . import spline, assemble, fd, pcg, learned  # noqa: F401

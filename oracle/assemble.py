@@ -56,34 +56,48 @@ class Geometry:
             return T
 
         F = contract(vals)
-        J = np.empty(F.shape[1:] + (d, d))
+        J = np.empty(F.shape[1:] + (F.shape[0], d))
         for j in range(d):
             tabs = [ders[k] if k == j else vals[k] for k in range(d)]
             Tj = contract(tabs)
-            for c in range(d):
+            for c in range(F.shape[0]):
                 J[..., c, j] = Tj[c]
         return F, J
 
 
 def q_matrix(J, kappa=1.0):
     """Q = kappa |det J| J^{-1} J^{-T} at every point (reading of Eq. (Q));
-    also returns det J."""
+    kappa is a scalar or an array over the points. Also returns det J."""
     det = np.linalg.det(J)
     Jinv = np.linalg.inv(J)
-    Q = kappa * np.abs(det)[..., None, None] * (Jinv @ np.swapaxes(Jinv, -1, -2))
+    kap = np.asarray(kappa, dtype=np.float64)
+    Q = (kap * np.abs(det))[..., None, None] * (Jinv @ np.swapaxes(Jinv, -1, -2))
     return Q, det
+
+
+class ScalarSpline:
+    """Scalar tensor spline field c(zeta) = sum_i c_i B_i(zeta) (used for a
+    variable coefficient K(x) = kappa(zeta) I of Eq. (poisson))."""
+
+    def __init__(self, ctrl, knots, p):
+        self._g = Geometry(np.asarray(ctrl, dtype=np.float64)[None], knots, p)
+
+    def eval_grid(self, pts):
+        F, _ = self._g.eval_grid(pts)
+        return F[0]
 
 
 class Discretization:
     """Degree-p tensor B-spline space with homogeneous Dirichlet conditions on
     a spline-mapped patch (Eqs. (Vh), (A))."""
 
-    def __init__(self, knots, p, geometry: Geometry, kappa=1.0, nq=None):
+    def __init__(self, knots, p, geometry: Geometry, kappa=1.0, nq=None, kappa_field=None):
         self.knots = [np.asarray(k, dtype=np.float64) for k in knots]
         self.p = int(p)
         self.d = len(self.knots)
         self.geo = geometry
         self.kappa = float(kappa)
+        self.kappa_field = kappa_field          # ScalarSpline or None
         self.nq = self.p + 1 if nq is None else int(nq)
         self.m = [len(k) - self.p - 1 for k in self.knots]   # 1D space dims
         self.n = [mk - 2 for mk in self.m]                   # Dirichlet dofs
@@ -96,18 +110,33 @@ class Discretization:
 
     @classmethod
     def from_problem(cls, prob, nq=None):
-        geo = Geometry(prob.ctrl, prob.knots, prob.p)
-        return cls(prob.knots, prob.p, geo, prob.kappa, nq)
+        geo = Geometry(prob.ctrl, getattr(prob, "geo_knots", None) or prob.knots,
+                       getattr(prob, "geo_p", None) or prob.p)
+        kf = None
+        if getattr(prob, "kappa_ctrl", None) is not None:
+            kf = ScalarSpline(prob.kappa_ctrl, prob.kappa_knots, prob.kappa_p)
+        return cls(prob.knots, prob.p, geo, prob.kappa, nq, kf)
+
+    def kappa_grid(self, pts):
+        """kappa at the tensor grid of 1D point sets (scalar if constant)."""
+        if self.kappa_field is None:
+            return self.kappa
+        return self.kappa * self.kappa_field.eval_grid(pts)
 
     # ---- 1D pencils (Section 3) -------------------------------------------
-    def pencil(self, k, full=False):
+    def pencil(self, k, full=False, wK=None, wM=None):
         """(K_k, M_k): 1D stiffness and mass matrices of direction k by
-        Gauss quadrature; Dirichlet rows/columns removed unless full."""
+        Gauss quadrature; Dirichlet rows/columns removed unless full.
+        Optional per-element weights wK, wM give the span-scaled pencils
+        sum_e wK_e K^(e), sum_e wM_e M^(e)."""
         z, w = self.qz[k].ravel(), self.qw[k].ravel()
         V = spline.basis_table(self.knots[k], self.p, z)
         D = spline.basis_table(self.knots[k], self.p, z, deriv=True)
-        M = (V * w[:, None]).T @ V
-        K = (D * w[:, None]).T @ D
+        nq = self.nq
+        wk = w if wK is None else w * np.repeat(np.asarray(wK, dtype=np.float64), nq)
+        wm = w if wM is None else w * np.repeat(np.asarray(wM, dtype=np.float64), nq)
+        M = (V * wm[:, None]).T @ V
+        K = (D * wk[:, None]).T @ D
         if not full:
             M, K = M[1:-1, 1:-1], K[1:-1, 1:-1]
         return K, M
@@ -130,7 +159,7 @@ class Discretization:
             I0.append(s - p)
             pts.append(z.ravel())
         F, J = self.geo.eval_grid(pts)
-        Q, det = q_matrix(J, self.kappa)
+        Q, det = q_matrix(J, self.kappa_grid(pts))
         return dict(V=V, D=D, W=W, I0=I0, F=F, Q=Q, det=det)
 
     @staticmethod
@@ -299,7 +328,8 @@ class Discretization:
     def l2_error(self, u_dofs, u_exact, extra_q=2, chunk_planes=4):
         """|| u - u_h ||_{L2(Omega)} with u_h = sum_i u_i B_i (Dirichlet dofs
         zero), by a Gauss rule with p+1+extra_q points per direction."""
-        fine = Discretization(self.knots, self.p, self.geo, self.kappa, self.p + 1 + extra_q)
+        fine = Discretization(self.knots, self.p, self.geo, self.kappa, self.p + 1 + extra_q,
+                              self.kappa_field)
         d = self.d
         U = np.zeros(tuple(reversed(self.m)))
         U[tuple(slice(1, -1) for _ in range(d))] = np.asarray(u_dofs).reshape(tuple(reversed(self.n)))
@@ -336,7 +366,7 @@ class Discretization:
             V = [v[:, 1:-1] for v in V]
             Dr = [x[:, 1:-1] for x in Dr]
         _, J = self.geo.eval_grid(pts)
-        Q, _ = q_matrix(J, self.kappa)
+        Q, _ = q_matrix(J, self.kappa_grid(pts))
         Q = Q.reshape(-1, d, d)
 
         def kron_all(tabs):  # rows: q (dir 1 fastest), cols: dof (dir 1 fastest)

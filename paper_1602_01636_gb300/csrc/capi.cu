@@ -51,9 +51,11 @@ void free_patch(igafd_patch *P) {
     Dir1D &D = P->dir[k];
     cudaFree(D.knots); cudaFree(D.gknots); cudaFree(D.span); cudaFree(D.z); cudaFree(D.w);
     cudaFree(D.bv); cudaFree(D.bd); cudaFree(D.gspan); cudaFree(D.gv); cudaFree(D.gd);
+    cudaFree(D.kknots); cudaFree(D.kspan); cudaFree(D.kv);
     cudaFree(P->U[k]); cudaFree(P->D[k]); cudaFree(P->U32[k]);
+    cudaFree(P->wK[k]); cudaFree(P->wM[k]);
   }
-  cudaFree(P->ctrl); cudaFree(P->inv_lam); cudaFree(P->inv_lam32); cudaFree(P->stencil);
+  cudaFree(P->ctrl); cudaFree(P->kctrl); cudaFree(P->inv_lam); cudaFree(P->inv_lam32); cudaFree(P->stencil);
   cudaFree(P->fd_a); cudaFree(P->fd_b);
   cudaFree(P->r); cudaFree(P->z); cudaFree(P->pv_base); cudaFree(P->xpad_base);
   cudaFree(P->xs_base); cudaFree(P->bint); cudaFree(P->tstat);
@@ -146,6 +148,17 @@ extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *strea
       d->geo_p > IGAFD_MAXP || !d->n_knots || !d->knots || !d->geo_n_knots || !d->geo_knots ||
       !d->ctrl || !(d->kappa > 0.0) || !std::isfinite(d->kappa))
     return IGAFD_ERR_ARG;
+  if (d->kappa_ctrl) {
+    if (d->kappa_p < 0 || d->kappa_p > IGAFD_MAXP || !d->kappa_n_knots || !d->kappa_knots)
+      return IGAFD_ERR_ARG;
+    size_t kc = 1;
+    for (int k = 0; k < d->dim; ++k) {
+      if (!valid_open_knots(d->kappa_knots[k], d->kappa_n_knots[k], d->kappa_p)) return IGAFD_ERR_ARG;
+      kc *= (size_t)(d->kappa_n_knots[k] - d->kappa_p - 1);
+    }
+    for (size_t i = 0; i < kc; ++i)   // positive control values: kappa > 0 everywhere
+      if (!(d->kappa_ctrl[i] > 0.0) || !std::isfinite(d->kappa_ctrl[i])) return IGAFD_ERR_ARG;
+  }
   for (int k = 0; k < d->dim; ++k) {
     if (!valid_open_knots(d->knots[k], d->n_knots[k], d->p)) return IGAFD_ERR_ARG;
     if (!valid_open_knots(d->geo_knots[k], d->geo_n_knots[k], d->geo_p)) return IGAFD_ERR_ARG;
@@ -157,6 +170,7 @@ extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *strea
   P->dim = d->dim;
   P->p = d->p;
   P->geo_p = d->geo_p;
+  P->kappa_p = d->kappa_ctrl ? d->kappa_p : 0;
   P->kappa = d->kappa;
   if (cudaGetDevice(&P->dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev) != cudaSuccess) {

@@ -43,6 +43,11 @@ struct Dir1D {
   double *bv, *bd;  // [nel*nq*(p+1)] local basis values / derivatives
   int *gspan;       // [nel*nq] geometry span at each point
   double *gv, *gd;  // [nel*nq*(geo_p+1)] geometry basis values / derivatives
+  // coefficient spline (optional)
+  int km;           // B-splines of the coefficient field
+  double *kknots;   // [km + kappa_p + 1]
+  int *kspan;       // [nel*nq]
+  double *kv;       // [nel*nq*(kappa_p+1)]
 };
 
 // Scalars of the PCG recurrence kept on the device.
@@ -67,13 +72,14 @@ struct FDMixed;   // mixed-precision FD workspace (fd_mixed.cu)
 
 struct igafd_patch {
   int dev;
-  int dim, p, geo_p;
+  int dim, p, geo_p, kappa_p;
   int n[3], nel[3];
   long long N;
   int n_off;
   double kappa;
   Dir1D dir[3];
   double *ctrl;                 // [dim][gm_d]..[gm_1]
+  double *kctrl;                // coefficient control values [km_d]..[km_1] or null
   // generalized eigenpairs: U[k][i*n + j], D[k][j]; inv_lam[N] = 1/(D1+D2+D3)
   double *U[3], *D[3];
   float *U32[3];
@@ -107,6 +113,8 @@ struct igafd_patch {
   double *scal;                 // [S_COUNT]
   double *host_scal;            // pinned mirror of scal
   FDMixed *mixed;
+  double *wK[3], *wM[3];        // span scalings of the pencils (device, null = unscaled)
+  int scaled;
   cudaEvent_t ev[IGAFD_NEV];    // phase-timing events (PCG with timing on)
   // diagnostics
   double min_detJ, q_bound, setup_ms, eig_ms;
@@ -119,7 +127,10 @@ struct igafd_patch {
 
 // ---- internal entry points (implemented in the .cu files) ----------------
 igafd_status igafd_setup_tables(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s);
-igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s);
+// pencils (optionally span-scaled: wK[k], wM[k] device arrays of nel[k]
+// weights, null = unscaled), eigendecompositions, 1/(D1 + D2 + D3)
+igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const double *const *wK = nullptr,
+                                     const double *const *wM = nullptr);
 igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s);
 // FD apply; kernels do nothing while *done_flag != 0 (done_flag may be null)
 igafd_status igafd_fd64_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,

@@ -14,8 +14,11 @@
 namespace {
 
 // Dense (Dirichlet-reduced) pencils of one direction; one thread per
-// (i, j) with |i - j| <= p. Full index I = i + 1.
-__global__ void pencil_kernel(Dir1D D, int p, double *K, double *M) {
+// (i, j) with |i - j| <= p. Full index I = i + 1. Optional per-element
+// weights wK, wM (null: 1) give the span-scaled pencils
+// K~ = sum_e wK_e K^(e), M~ = sum_e wM_e M^(e).
+__global__ void pencil_kernel(Dir1D D, int p, double *K, double *M, const double *wK,
+                              const double *wM) {
   const int n = D.n, W = 2 * p + 1, A = p + 1, nq = p + 1;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * W) return;
@@ -27,12 +30,15 @@ __global__ void pencil_kernel(Dir1D D, int p, double *K, double *M) {
     int s = D.span[e];
     int ai = I - (s - p), aj = J - (s - p);
     if (ai < 0 || ai > p || aj < 0 || aj > p) continue;
+    double me = 0.0, ke = 0.0;
     for (int g = 0; g < nq; ++g) {
       size_t q = (size_t)e * nq + g;
       double w = D.w[q];
-      m += w * D.bv[q * A + ai] * D.bv[q * A + aj];
-      k += w * D.bd[q * A + ai] * D.bd[q * A + aj];
+      me += w * D.bv[q * A + ai] * D.bv[q * A + aj];
+      ke += w * D.bd[q * A + ai] * D.bd[q * A + aj];
     }
+    m += wM ? wM[e] * me : me;
+    k += wK ? wK[e] * ke : ke;
   }
   M[(size_t)i * n + j] = m;
   K[(size_t)i * n + j] = k;
@@ -243,7 +249,8 @@ __global__ void inv_lambda_kernel(const double *D1, const double *D2, const doub
 
 }  // namespace
 
-igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s) {
+igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const double *const *wK,
+                                     const double *const *wM) {
   const int dim = P->dim, p = P->p;
   // scratch for all directions
   size_t tot = 0;
@@ -265,7 +272,8 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s) {
     off += 4 * nn;
     cudaMemsetAsync(j.M, 0, 2 * nn * sizeof(double), s);
     int th = n * (2 * p + 1);
-    pencil_kernel<<<(th + 127) / 128, 128, 0, s>>>(P->dir[k], p, j.K, j.M);
+    pencil_kernel<<<(th + 127) / 128, 128, 0, s>>>(P->dir[k], p, j.K, j.M, wK ? wK[k] : nullptr,
+                                                   wM ? wM[k] : nullptr);
   }
   EigJob *djobs = nullptr;
   igafd_status st = IGAFD_OK;

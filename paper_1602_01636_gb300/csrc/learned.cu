@@ -1,0 +1,361 @@
+// Learned span scalings of the 1D pencils: features, separable log-fit
+// labels, and the scaled preconditioner.
+//
+// Prop. 1 bounds the condition number of P^{-1} A by the spread of the
+// eigenvalues of Q over the domain. Scaling the element contributions of the
+// 1D pencils, K~_k = sum_e wK_{k,e} K_k^(e) and M~_k = sum_e wM_{k,e} M_k^(e),
+// keeps P a Kronecker sum (so the fast diagonalization still applies) while
+// letting term k of P follow Q_kk: on the quadrature grid, term k carries the
+// factor wK_k(zeta_k) * prod_{l != k} wM_l(zeta_l). The separable fit chooses
+// log wK, log wM by least squares of log Q_kk against that additive model
+// (backfitting, one slab mean per update); it initialises the labels that a
+// small network learns to predict from per-span features of Q.
+//
+// Rows: r <-> (direction k, span e), direction-major: r = sum_{l<k} nel_l + e.
+#include "common.cuh"
+#include "geom.cuh"
+
+#include <cmath>
+#include <vector>
+
+using namespace igafd_geom;
+
+namespace {
+
+// Per quadrature point: log Q_kk (k < DIM), log lambda_min(Q), log lambda_max(Q).
+// Layout y[c][t3][t2][t1] (global 1D quadrature indices, direction 1 fastest).
+template <int DIM>
+__global__ void qdiag_kernel(PV v, long long nqp, float *y) {
+  const int nq = v.nq;
+  const long long T1 = (long long)v.nel[0] * nq, T2 = (long long)v.nel[1] * nq;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nqp;
+       i += (long long)gridDim.x * blockDim.x) {
+    int t[3];
+    t[0] = (int)(i % T1);
+    t[1] = (int)((i / T1) % T2);
+    t[2] = DIM == 3 ? (int)(i / (T1 * T2)) : 0;
+    double x[3], J[3][3], Q[6];
+    geo_eval<DIM>(v, t, x, J);
+    q_from_J<DIM>(J, kappa_eval<DIM>(v, t), Q);
+    for (int k = 0; k < DIM; ++k) y[k * nqp + i] = (float)log(Q[k]);
+    double lo, hi;
+    sym_eig_extremes<DIM>(Q, &lo, &hi);
+    y[DIM * nqp + i] = (float)log(fmax(lo, 1e-300));
+    y[(DIM + 1) * nqp + i] = (float)log(hi);
+  }
+}
+
+struct Slab {
+  int dim, nq;
+  int nel[3];
+  long long T[3];       // quadrature points per direction
+  long long nqp;
+  int row0[3];          // first row of each direction
+};
+
+// index of the element of direction l that quadrature point i lies in
+__device__ __forceinline__ int elem_of(const Slab &S, long long i, int l) {
+  long long t = l == 0 ? i % S.T[0] : l == 1 ? (i / S.T[0]) % S.T[1] : i / (S.T[0] * S.T[1]);
+  return (int)(t / S.nq);
+}
+
+// one block per (direction k, span e): the slab's quadrature points, loop form
+template <typename F>
+__device__ void for_slab(const Slab &S, int k, int e, F f) {
+  const int nq = S.nq;
+  const long long cnt = (long long)nq * (S.nqp / S.T[k]);
+  for (long long j = threadIdx.x; j < cnt; j += blockDim.x) {
+    // j enumerates (g in the element, then the other directions' points)
+    const int g = (int)(j % nq);
+    const long long rest = j / nq;
+    const long long tk = (long long)e * nq + g;
+    long long i;
+    if (k == 0) i = tk + S.T[0] * rest;
+    else if (k == 1) i = (rest % S.T[0]) + S.T[0] * (tk + S.T[1] * (rest / S.T[0]));
+    else i = rest + S.T[0] * S.T[1] * tk;
+    f(i);
+  }
+}
+
+__device__ double block_min(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 1e300;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmin(r, sh[w]);
+  return r;
+}
+
+__device__ double block_total(double v, double *sh) {
+  double t = block_sum(v, sh);
+  __syncthreads();
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+// Features of row (k, e): [log mean Q_kk, log mean of the other diagonal
+// entries, log min lambda_min(Q), log max lambda_max(Q), std of log Q_kk,
+// span centre], averages over the slab of quadrature points.
+__global__ void features_kernel(Slab S, const float *y, const double *const *knots,
+                                const int *const *spans, float *feat) {
+  __shared__ double sh[32];
+  const int k = blockIdx.y, e = blockIdx.x;
+  if (e >= S.nel[k]) return;
+  const long long nqp = S.nqp;
+  double sq = 0.0, so = 0.0, sl = 0.0, sl2 = 0.0, mn = 1e300, mx = -1e300;
+  for_slab(S, k, e, [&](long long i) {
+    const double lq = y[k * nqp + i];
+    sq += exp(lq);
+    sl += lq;
+    sl2 += lq * lq;
+    double oth = 0.0;
+    for (int l = 0; l < S.dim; ++l)
+      if (l != k) oth += exp((double)y[l * nqp + i]);
+    so += oth / (S.dim - 1);
+    mn = fmin(mn, (double)y[S.dim * nqp + i]);
+    mx = fmax(mx, (double)y[(S.dim + 1) * nqp + i]);
+  });
+  const double cnt = (double)S.nq * (double)(nqp / S.T[k]);
+  sq = block_total(sq, sh);
+  so = block_total(so, sh);
+  sl = block_total(sl, sh);
+  sl2 = block_total(sl2, sh);
+  mn = block_min(mn, sh);
+  mx = -block_min(-mx, sh);
+  if (threadIdx.x == 0) {
+    float *f = feat + (size_t)(S.row0[k] + e) * 6;
+    const double ml = sl / cnt;
+    f[0] = (float)log(sq / cnt);
+    f[1] = (float)log(so / cnt);
+    f[2] = (float)mn;
+    f[3] = (float)mx;
+    f[4] = (float)sqrt(fmax(0.0, sl2 / cnt - ml * ml));
+    const int s = spans[k][e];
+    f[5] = (float)(0.5 * (knots[k][s] + knots[k][s + 1]));
+  }
+}
+
+// One backfitting update for direction `dir`: mode 0 updates a_dir (log wK),
+// mode 1 updates m_dir (log wM); a, m: [rows] (direction-major), out: [rows].
+__global__ void backfit_kernel(Slab S, const float *y, const double *a, const double *m, int dir,
+                               int mode, double *out) {
+  __shared__ double sh[32];
+  const int e = blockIdx.x;
+  if (e >= S.nel[dir]) return;
+  const long long nqp = S.nqp;
+  double acc = 0.0;
+  for_slab(S, dir, e, [&](long long i) {
+    int el[3];
+    for (int l = 0; l < S.dim; ++l) el[l] = elem_of(S, i, l);
+    if (mode == 0) {
+      double r = y[dir * nqp + i];
+      for (int l = 0; l < S.dim; ++l)
+        if (l != dir) r -= m[S.row0[l] + el[l]];
+      acc += r;
+    } else {
+      double r = 0.0;
+      for (int k = 0; k < S.dim; ++k) {
+        if (k == dir) continue;
+        double rk = y[k * nqp + i] - a[S.row0[k] + el[k]];
+        for (int j = 0; j < S.dim; ++j)
+          if (j != k && j != dir) rk -= m[S.row0[j] + el[j]];
+        r += rk;
+      }
+      acc += r / (S.dim - 1);
+    }
+  });
+  acc = block_total(acc, sh);
+  if (threadIdx.x == 0) out[S.row0[dir] + e] = acc / ((double)S.nq * (double)(nqp / S.T[dir]));
+}
+
+// gauge: mean of each m_l is 0, absorbed into the a_k with k != l
+__global__ void gauge_kernel(Slab S, double *a, double *m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int l = 0; l < S.dim; ++l) {
+    double c = 0.0;
+    for (int e = 0; e < S.nel[l]; ++e) c += m[S.row0[l] + e];
+    c /= S.nel[l];
+    for (int e = 0; e < S.nel[l]; ++e) m[S.row0[l] + e] -= c;
+    for (int k = 0; k < S.dim; ++k)
+      if (k != l)
+        for (int e = 0; e < S.nel[k]; ++e) a[S.row0[k] + e] += c;
+  }
+}
+
+__global__ void pack_logw_kernel(const double *a, const double *m, int rows, float *logw) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  logw[2 * r] = (float)a[r];
+  logw[2 * r + 1] = (float)m[r];
+}
+
+__global__ void exp_weights_kernel(const float *logw, int row0, int nel, double *wK, double *wM) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nel) return;
+  wK[e] = exp((double)logw[2 * (row0 + e)]);
+  wM[e] = exp((double)logw[2 * (row0 + e) + 1]);
+}
+
+__global__ void to_float_kernel2(const double *a, float *b, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+Slab make_slab(const igafd_patch *P) {
+  Slab S{};
+  S.dim = P->dim;
+  S.nq = P->p + 1;
+  S.nqp = 1;
+  int row = 0;
+  for (int k = 0; k < 3; ++k) {
+    S.nel[k] = k < P->dim ? P->nel[k] : 1;
+    S.T[k] = k < P->dim ? (long long)P->nel[k] * S.nq : 1;
+    S.nqp *= S.T[k];
+    S.row0[k] = row;
+    if (k < P->dim) row += P->nel[k];
+  }
+  return S;
+}
+
+int rows_of(const igafd_patch *P) {
+  int r = 0;
+  for (int k = 0; k < P->dim; ++k) r += P->nel[k];
+  return r;
+}
+
+// log-diagonal table of Q on the quadrature grid (allocated here, freed by caller)
+igafd_status make_qdiag(igafd_patch *P, cudaStream_t s, float **y, long long *nqp) {
+  Slab S = make_slab(P);
+  *nqp = S.nqp;
+  if (cudaMalloc(y, (size_t)(P->dim + 2) * S.nqp * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return IGAFD_ERR_OOM;
+  }
+  PV v = make_view(P);
+  if (P->dim == 3) qdiag_kernel<3><<<P->num_sms * 8, 256, 0, s>>>(v, S.nqp, *y);
+  else qdiag_kernel<2><<<P->num_sms * 8, 256, 0, s>>>(v, S.nqp, *y);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
+  return IGAFD_OK;
+}
+
+}  // namespace
+
+extern "C" igafd_status igafd_scaling_rows(const igafd_patch *P, int *rows) {
+  if (!P || !rows) return IGAFD_ERR_ARG;
+  *rows = rows_of(P);
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_patch_features(igafd_patch *P, float *feat, void *stream) {
+  if (!P || !feat) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(P->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  float *y = nullptr;
+  long long nqp = 0;
+  IGAFD_TRY(make_qdiag(P, s, &y, &nqp));
+  Slab S = make_slab(P);
+  const double *kn[3] = {P->dir[0].knots, P->dir[1].knots, P->dir[2].knots};
+  const int *sp[3] = {P->dir[0].span, P->dir[1].span, P->dir[2].span};
+  const double **dkn = nullptr;
+  const int **dsp = nullptr;
+  igafd_status st = IGAFD_OK;
+  if (cudaMalloc(&dkn, sizeof(kn)) != cudaSuccess || cudaMalloc(&dsp, sizeof(sp)) != cudaSuccess) {
+    cudaGetLastError();
+    st = IGAFD_ERR_OOM;
+  } else {
+    cudaMemcpyAsync(dkn, kn, sizeof(kn), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dsp, sp, sizeof(sp), cudaMemcpyHostToDevice, s);
+    int emax = 0;
+    for (int k = 0; k < P->dim; ++k) emax = emax > P->nel[k] ? emax : P->nel[k];
+    features_kernel<<<dim3(emax, P->dim), 256, 0, s>>>(S, y, dkn, dsp, feat);
+    IGAFD_LAUNCHED(1);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) st = IGAFD_ERR_CUDA;
+  }
+  cudaFree(dkn);
+  cudaFree(dsp);
+  cudaFree(y);
+  return st;
+}
+
+extern "C" igafd_status igafd_patch_sepfit(igafd_patch *P, int sweeps, float *logw, void *stream) {
+  if (!P || !logw || sweeps < 1 || sweeps > 1000) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(P->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  float *y = nullptr;
+  long long nqp = 0;
+  IGAFD_TRY(make_qdiag(P, s, &y, &nqp));
+  Slab S = make_slab(P);
+  const int rows = rows_of(P);
+  double *a = nullptr, *m = nullptr;
+  igafd_status st = IGAFD_OK;
+  if (cudaMalloc(&a, rows * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&m, rows * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    st = IGAFD_ERR_OOM;
+  } else {
+    cudaMemsetAsync(a, 0, rows * sizeof(double), s);
+    cudaMemsetAsync(m, 0, rows * sizeof(double), s);
+    for (int it = 0; it < sweeps; ++it) {
+      for (int k = 0; k < P->dim; ++k) {
+        backfit_kernel<<<P->nel[k], 256, 0, s>>>(S, y, a, m, k, 0, a);
+        IGAFD_LAUNCHED(1);
+      }
+      for (int l = 0; l < P->dim; ++l) {
+        backfit_kernel<<<P->nel[l], 256, 0, s>>>(S, y, a, m, l, 1, m);
+        IGAFD_LAUNCHED(1);
+      }
+      gauge_kernel<<<1, 32, 0, s>>>(S, a, m);
+      IGAFD_LAUNCHED(1);
+    }
+    pack_logw_kernel<<<(rows + 127) / 128, 128, 0, s>>>(a, m, rows, logw);
+    IGAFD_LAUNCHED(1);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) st = IGAFD_ERR_CUDA;
+  }
+  cudaFree(a);
+  cudaFree(m);
+  cudaFree(y);
+  return st;
+}
+
+extern "C" igafd_status igafd_set_scalings(igafd_patch *P, const float *logw, void *stream) {
+  if (!P) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(P->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (logw) {
+    int row0 = 0;
+    for (int k = 0; k < P->dim; ++k) {
+      if (!P->wK[k]) {
+        if (cudaMalloc(&P->wK[k], P->nel[k] * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&P->wM[k], P->nel[k] * sizeof(double)) != cudaSuccess) {
+          cudaGetLastError();
+          return IGAFD_ERR_OOM;
+        }
+      }
+      exp_weights_kernel<<<(P->nel[k] + 127) / 128, 128, 0, s>>>(logw, row0, P->nel[k], P->wK[k],
+                                                                 P->wM[k]);
+      IGAFD_LAUNCHED(1);
+      row0 += P->nel[k];
+    }
+    IGAFD_CUDA(cudaGetLastError());
+    IGAFD_TRY(igafd_setup_pencils_eig(P, s, P->wK, P->wM));
+    P->scaled = 1;
+  } else {
+    IGAFD_TRY(igafd_setup_pencils_eig(P, s, nullptr, nullptr));
+    P->scaled = 0;
+  }
+  for (int k = 0; k < P->dim; ++k) {
+    const long long nn = (long long)P->n[k] * P->n[k];
+    to_float_kernel2<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(P->U[k], P->U32[k], nn);
+    IGAFD_LAUNCHED(1);
+  }
+  IGAFD_CUDA(cudaGetLastError());
+  igafd_fd_tc_free(P);
+  IGAFD_TRY(igafd_fd_tc_init(P, s));
+  IGAFD_CUDA(cudaStreamSynchronize(s));
+  return IGAFD_OK;
+}

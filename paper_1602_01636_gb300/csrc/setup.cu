@@ -6,71 +6,15 @@
 // Q = kappa |det J| J^{-1} J^{-T} (chain rule with J_ij = dx_i/dzeta_j; the
 // paper prints the transposes the other way round in Eq. (Q)).
 #include "common.cuh"
+#include "geom.cuh"
 
 #include <cmath>
 #include <vector>
 
 namespace {
 
-// Device-visible view of the patch tables (passed by value to kernels).
-struct PV {
-  int dim, p, gp, nq;
-  int n[3], nel[3], gm[3];
-  const int *span[3];
-  const double *w[3], *bv[3], *bd[3], *gv[3], *gd[3];
-  const int *gspan[3];
-  const double *ctrl;
-  double kappa;
-};
+using namespace igafd_geom;
 
-PV make_view(const igafd_patch *P) {
-  PV v{};
-  v.dim = P->dim; v.p = P->p; v.gp = P->geo_p; v.nq = P->p + 1;
-  for (int k = 0; k < 3; ++k) {
-    v.n[k] = P->n[k]; v.nel[k] = P->nel[k]; v.gm[k] = P->dir[k].gm;
-    v.span[k] = P->dir[k].span; v.w[k] = P->dir[k].w;
-    v.bv[k] = P->dir[k].bv; v.bd[k] = P->dir[k].bd;
-    v.gv[k] = P->dir[k].gv; v.gd[k] = P->dir[k].gd; v.gspan[k] = P->dir[k].gspan;
-  }
-  v.ctrl = P->ctrl; v.kappa = P->kappa;
-  return v;
-}
-
-// Nonzero degree-p B-splines B_{s-p..s} and their derivatives at u in span s
-// (triangular Cox-de Boor scheme; derivatives from the degree p-1 values).
-__device__ void bspline_local(const double *xi, int s, double u, int p, double *N, double *dN) {
-  double left[IGAFD_MAXP + 1], right[IGAFD_MAXP + 1], prev[IGAFD_MAXP + 1];
-  N[0] = 1.0;
-  prev[0] = 1.0;
-  for (int j = 1; j <= p; ++j) {
-    left[j] = u - xi[s + 1 - j];
-    right[j] = xi[s + j] - u;
-    double saved = 0.0;
-    for (int r = 0; r < j; ++r) {
-      double den = right[r + 1] + left[j - r];
-      double t = den != 0.0 ? N[r] / den : 0.0;
-      N[r] = saved + right[r + 1] * t;
-      saved = left[j - r] * t;
-    }
-    N[j] = saved;
-    if (j == p - 1)
-      for (int r = 0; r <= j; ++r) prev[r] = N[r];
-  }
-  // prev[b] = B_{s-p+1+b, p-1}, b = 0..p-1
-  for (int a = 0; a <= p; ++a) {
-    int i = s - p + a;
-    double d = 0.0;
-    if (a >= 1) {
-      double den = xi[i + p] - xi[i];
-      if (den != 0.0) d += p * prev[a - 1] / den;
-    }
-    if (a <= p - 1) {
-      double den = xi[i + p + 1] - xi[i + 1];
-      if (den != 0.0) d -= p * prev[a] / den;
-    }
-    dN[a] = d;
-  }
-}
 
 // i-th node (ascending) and weight of the nq-point Gauss-Legendre rule on
 // [-1, 1] by Newton's method on the Legendre polynomial P_nq.
@@ -102,8 +46,18 @@ __device__ void gauss_node(int nq, int i, double *x, double *w) {
   *w = 2.0 / ((1.0 - z * z) * dp * dp);
 }
 
+// Span s of a knot vector with xi_s <= z < xi_{s+1}, s in [deg, m-1].
+__device__ int find_span(const double *xi, int deg, int m, double z) {
+  int lo = deg, hi = m - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (xi[mid] <= z) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // One thread per 1D quadrature point of one direction.
-__global__ void tables_kernel(Dir1D D, int p, int gp) {
+__global__ void tables_kernel(Dir1D D, int p, int gp, int kp) {
   int nq = p + 1;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= D.nel * nq) return;
@@ -122,143 +76,18 @@ __global__ void tables_kernel(Dir1D D, int p, int gp) {
     D.bd[t * (p + 1) + i] = dN[i];
   }
   // geometry span: xi_gs <= z < xi_{gs+1}, gs in [gp, gm-1]
-  int lo = gp, hi = D.gm - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (D.gknots[mid] <= z) lo = mid; else hi = mid - 1;
-  }
-  D.gspan[t] = lo;
-  bspline_local(D.gknots, lo, z, gp, N, dN);
+  const int gs = find_span(D.gknots, gp, D.gm, z);
+  D.gspan[t] = gs;
+  bspline_local(D.gknots, gs, z, gp, N, dN);
   for (int i = 0; i <= gp; ++i) {
     D.gv[t * (gp + 1) + i] = N[i];
     D.gd[t * (gp + 1) + i] = dN[i];
   }
-}
-
-// x = F(zeta) and J = dF/dzeta at the quadrature point with 1D indices t[k].
-template <int DIM>
-__device__ void geo_eval(const PV &v, const int *t, double *x, double (*J)[3]) {
-  const int gp = v.gp, ga = gp + 1;
-  const double *gv[3], *gd[3];
-  int g0[3];
-  for (int k = 0; k < DIM; ++k) {
-    gv[k] = v.gv[k] + (size_t)t[k] * ga;
-    gd[k] = v.gd[k] + (size_t)t[k] * ga;
-    g0[k] = v.gspan[k][t[k]] - gp;
-  }
-  for (int c = 0; c < DIM; ++c) {
-    x[c] = 0.0;
-    for (int j = 0; j < DIM; ++j) J[c][j] = 0.0;
-  }
-  if (DIM == 2) {
-    for (int c = 0; c < 2; ++c) {
-      const double *C = v.ctrl + (size_t)c * v.gm[0] * v.gm[1];
-      for (int a2 = 0; a2 < ga; ++a2) {
-        const double *row = C + (size_t)(g0[1] + a2) * v.gm[0] + g0[0];
-        double s0 = 0.0, s1 = 0.0;
-        for (int a1 = 0; a1 < ga; ++a1) {
-          s0 += row[a1] * gv[0][a1];
-          s1 += row[a1] * gd[0][a1];
-        }
-        x[c] += s0 * gv[1][a2];
-        J[c][0] += s1 * gv[1][a2];
-        J[c][1] += s0 * gd[1][a2];
-      }
-    }
-  } else {
-    for (int c = 0; c < 3; ++c) {
-      const double *C = v.ctrl + (size_t)c * v.gm[0] * v.gm[1] * v.gm[2];
-      for (int a3 = 0; a3 < ga; ++a3) {
-        double v3 = gv[2][a3], d3 = gd[2][a3];
-        for (int a2 = 0; a2 < ga; ++a2) {
-          const double *row =
-              C + ((size_t)(g0[2] + a3) * v.gm[1] + (g0[1] + a2)) * v.gm[0] + g0[0];
-          double s0 = 0.0, s1 = 0.0;
-          for (int a1 = 0; a1 < ga; ++a1) {
-            s0 += row[a1] * gv[0][a1];
-            s1 += row[a1] * gd[0][a1];
-          }
-          double v2 = gv[1][a2], d2 = gd[1][a2];
-          x[c] += s0 * v2 * v3;
-          J[c][0] += s1 * v2 * v3;
-          J[c][1] += s0 * d2 * v3;
-          J[c][2] += s0 * v2 * d3;
-        }
-      }
-    }
-  }
-}
-
-// Q = kappa |det J| J^{-1} J^{-T}; returns det J. Q stored symmetric:
-// 2D [00, 11, 01], 3D [00, 11, 22, 01, 02, 12].
-template <int DIM>
-__device__ double q_from_J(const double (*J)[3], double kappa, double *Q) {
-  if (DIM == 2) {
-    double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    double id = 1.0 / det;
-    double Ji[2][2] = {{J[1][1] * id, -J[0][1] * id}, {-J[1][0] * id, J[0][0] * id}};
-    double sc = kappa * fabs(det);
-    Q[0] = sc * (Ji[0][0] * Ji[0][0] + Ji[0][1] * Ji[0][1]);
-    Q[1] = sc * (Ji[1][0] * Ji[1][0] + Ji[1][1] * Ji[1][1]);
-    Q[2] = sc * (Ji[0][0] * Ji[1][0] + Ji[0][1] * Ji[1][1]);
-    return det;
-  } else {
-    double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-    double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-    double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-    double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-    double id = 1.0 / det;
-    double Ji[3][3];
-    Ji[0][0] = c00 * id;
-    Ji[1][0] = c01 * id;
-    Ji[2][0] = c02 * id;
-    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
-    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
-    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
-    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
-    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
-    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
-    double sc = kappa * fabs(det);
-    const int rr[6] = {0, 1, 2, 0, 0, 1}, ss[6] = {0, 1, 2, 1, 2, 2};
-    for (int q = 0; q < 6; ++q) {
-      double acc = 0.0;
-      for (int c = 0; c < 3; ++c) acc += Ji[rr[q]][c] * Ji[ss[q]][c];
-      Q[q] = sc * acc;
-    }
-    return det;
-  }
-}
-
-__device__ __forceinline__ int qidx(int r, int s, int dim) {
-  if (r == s) return r;
-  if (dim == 2) return 2;
-  int lo = r < s ? r : s, hi = r < s ? s : r;
-  return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
-}
-
-// Extreme eigenvalues of a symmetric 2x2 / 3x3 matrix (closed form).
-template <int DIM>
-__device__ void sym_eig_extremes(const double *Q, double *lmin, double *lmax) {
-  if (DIM == 2) {
-    double m = 0.5 * (Q[0] + Q[1]);
-    double d = sqrt(0.25 * (Q[0] - Q[1]) * (Q[0] - Q[1]) + Q[2] * Q[2]);
-    *lmin = m - d; *lmax = m + d;
-  } else {
-    double a = Q[0], b = Q[1], c = Q[2], d = Q[3], e = Q[5], f = Q[4];
-    double p1 = d * d + f * f + e * e;
-    double q = (a + b + c) / 3.0;
-    double p2 = (a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + 2.0 * p1;
-    double pp = sqrt(p2 / 6.0);
-    if (pp < 1e-300) { *lmin = *lmax = q; return; }
-    double B00 = (a - q) / pp, B11 = (b - q) / pp, B22 = (c - q) / pp;
-    double B01 = d / pp, B02 = f / pp, B12 = e / pp;
-    double detB = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) +
-                  B02 * (B01 * B12 - B11 * B02);
-    double r = fmin(1.0, fmax(-1.0, 0.5 * detB));
-    double phi = acos(r) / 3.0;
-    double e1 = q + 2.0 * pp * cos(phi);
-    double e3 = q + 2.0 * pp * cos(phi + 2.0 * M_PI / 3.0);
-    *lmax = e1; *lmin = e3;
+  if (D.kknots) {   // coefficient field
+    const int ks = find_span(D.kknots, kp, D.km, z);
+    D.kspan[t] = ks;
+    bspline_local(D.kknots, ks, z, kp, N, dN);
+    for (int i = 0; i <= kp; ++i) D.kv[t * (kp + 1) + i] = N[i];
   }
 }
 
@@ -278,7 +107,7 @@ __global__ void geo_check_kernel(PV v, long long nqp, double *part) {
     t[2] = DIM == 3 ? (int)(i / (tot1 * tot2)) : 0;
     double x[3], J[3][3], Q[6];
     geo_eval<DIM>(v, t, x, J);
-    double det = q_from_J<DIM>(J, v.kappa, Q);
+    double det = q_from_J<DIM>(J, kappa_eval<DIM>(v, t), Q);
     mdet = fmin(mdet, det);
     double a, b;
     sym_eig_extremes<DIM>(Q, &a, &b);
@@ -349,7 +178,7 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
     for (int k = 0; k < DIM; ++k) t[k] = e[k] * nq + gq[k];
     double x[3], J[3][3], Q[6];
     geo_eval<DIM>(v, t, x, J);
-    q_from_J<DIM>(J, v.kappa, Q);
+    q_from_J<DIM>(J, kappa_eval<DIM>(v, t), Q);
     double wt = 1.0;
     for (int k = 0; k < DIM; ++k) wt *= v.w[k][t[k]];
     for (int q = 0; q < nQ; ++q) Qs[q * nqd + g] = Q[q] * wt;
@@ -558,6 +387,15 @@ igafd_status igafd_setup_tables(igafd_patch *P, const igafd_patch_desc *d, cudaS
     IGAFD_TRY(dalloc((void **)&D.gspan, nt * sizeof(int)));
     IGAFD_TRY(dalloc((void **)&D.gv, (size_t)nt * (gp + 1) * sizeof(double)));
     IGAFD_TRY(dalloc((void **)&D.gd, (size_t)nt * (gp + 1) * sizeof(double)));
+    if (d->kappa_ctrl) {
+      const int kp = d->kappa_p;
+      D.km = d->kappa_n_knots[k] - kp - 1;
+      IGAFD_TRY(dalloc((void **)&D.kknots, d->kappa_n_knots[k] * sizeof(double)));
+      IGAFD_TRY(dalloc((void **)&D.kspan, nt * sizeof(int)));
+      IGAFD_TRY(dalloc((void **)&D.kv, (size_t)nt * (kp + 1) * sizeof(double)));
+      IGAFD_CUDA(cudaMemcpyAsync(D.kknots, d->kappa_knots[k], d->kappa_n_knots[k] * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+    }
     IGAFD_CUDA(cudaMemcpyAsync(D.knots, kn, nk * sizeof(double), cudaMemcpyHostToDevice, s));
     IGAFD_CUDA(cudaMemcpyAsync(D.gknots, d->geo_knots[k], d->geo_n_knots[k] * sizeof(double),
                                cudaMemcpyHostToDevice, s));
@@ -565,7 +403,7 @@ igafd_status igafd_setup_tables(igafd_patch *P, const igafd_patch_desc *d, cudaS
                                cudaMemcpyHostToDevice, s));
     // the host vector must outlive the async copy
     IGAFD_CUDA(cudaStreamSynchronize(s));
-    tables_kernel<<<(nt + 127) / 128, 128, 0, s>>>(D, p, gp);
+    tables_kernel<<<(nt + 127) / 128, 128, 0, s>>>(D, p, gp, P->kappa_p);
     IGAFD_CUDA(cudaGetLastError());
     P->n[k] = D.n;
     P->nel[k] = D.nel;
@@ -573,6 +411,12 @@ igafd_status igafd_setup_tables(igafd_patch *P, const igafd_patch_desc *d, cudaS
   IGAFD_TRY(dalloc((void **)&P->ctrl, ctrl_count * sizeof(double)));
   IGAFD_CUDA(cudaMemcpyAsync(P->ctrl, d->ctrl, ctrl_count * sizeof(double),
                              cudaMemcpyHostToDevice, s));
+  if (d->kappa_ctrl) {
+    size_t kc = 1;
+    for (int k = 0; k < P->dim; ++k) kc *= P->dir[k].km;
+    IGAFD_TRY(dalloc((void **)&P->kctrl, kc * sizeof(double)));
+    IGAFD_CUDA(cudaMemcpyAsync(P->kctrl, d->kappa_ctrl, kc * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
   IGAFD_CUDA(cudaStreamSynchronize(s));
   return IGAFD_OK;
 }

@@ -37,7 +37,10 @@ class PatchDesc(C.Structure):
                 ("n_knots", C.POINTER(C.c_int)), ("knots", C.POINTER(C.POINTER(C.c_double))),
                 ("geo_p", C.c_int), ("geo_n_knots", C.POINTER(C.c_int)),
                 ("geo_knots", C.POINTER(C.POINTER(C.c_double))),
-                ("ctrl", C.POINTER(C.c_double)), ("kappa", C.c_double)]
+                ("ctrl", C.POINTER(C.c_double)), ("kappa", C.c_double),
+                ("kappa_p", C.c_int), ("kappa_n_knots", C.POINTER(C.c_int)),
+                ("kappa_knots", C.POINTER(C.POINTER(C.c_double))),
+                ("kappa_ctrl", C.POINTER(C.c_double))]
 
 
 class PatchInfo(C.Structure):
@@ -65,7 +68,12 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_copy_stencil", "igafd_apply_A", "igafd_apply_prec", "igafd_load_rhs_sine",
            "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str",
            "igafd_kernel_launches", "igafd_batch_pcg_solve", "igafd_autotune",
-           "igafd_set_stencil_stages"]
+           "igafd_set_stencil_stages", "igafd_scaling_rows", "igafd_patch_features",
+           "igafd_patch_sepfit", "igafd_set_scalings", "igafd_mlp_create", "igafd_mlp_destroy",
+           "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
+           "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step"]
+
+MLP_PARAMS = 4738
 
 
 def lib():
@@ -92,6 +100,20 @@ def lib():
                                         C.POINTER(PCGOpts), C.POINTER(PCGInfo), vp]
     L.igafd_autotune.argtypes = [vp, C.c_int, vp]
     L.igafd_set_stencil_stages.argtypes = [vp, C.c_int]
+    L.igafd_scaling_rows.argtypes = [vp, C.POINTER(C.c_int)]
+    L.igafd_patch_features.argtypes = [vp, vp, vp]
+    L.igafd_patch_sepfit.argtypes = [vp, C.c_int, vp, vp]
+    L.igafd_set_scalings.argtypes = [vp, vp, vp]
+    fp = C.POINTER(C.c_float)
+    L.igafd_mlp_create.argtypes = [fp, C.POINTER(vp)]
+    L.igafd_mlp_destroy.argtypes = [vp]
+    L.igafd_mlp_destroy.restype = None
+    L.igafd_mlp_set_normalization.argtypes = [vp, fp, fp, fp, fp]
+    L.igafd_mlp_get_params.argtypes = [vp, fp]
+    L.igafd_mlp_set_params.argtypes = [vp, fp]
+    L.igafd_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.igafd_mlp_gradient.argtypes = [vp, vp, vp, C.c_int, fp, fp, vp]
+    L.igafd_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, fp, vp]
     L.igafd_pcg_default_opts.argtypes = [C.POINTER(PCGOpts)]
     L.igafd_pcg_default_opts.restype = None
     L.igafd_status_str.argtypes = [C.c_int]
@@ -100,7 +122,7 @@ def lib():
     L.igafd_kernel_launches.restype = C.c_longlong
     for name in EXPORTS:
         if name not in ("igafd_destroy_patch", "igafd_pcg_default_opts", "igafd_status_str",
-                        "igafd_kernel_launches"):
+                        "igafd_kernel_launches", "igafd_mlp_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -164,7 +186,9 @@ def batch_pcg(patches, bs, xs=None, tol=1e-8, max_iter=1000, dtype="fp64", flexi
 class Patch:
     """A single-patch problem set up on the current CUDA device."""
 
-    def __init__(self, knots, p, ctrl, kappa=1.0, geo_knots=None, geo_p=None):
+    def __init__(self, knots, p, ctrl, kappa=1.0, geo_knots=None, geo_p=None, kappa_field=None):
+        """kappa_field: optional (knots, degree, control values) of a positive
+        spline coefficient c(zeta); K = kappa * c."""
         L = lib()
         dim = len(knots)
         geo_knots = knots if geo_knots is None else geo_knots
@@ -182,6 +206,15 @@ class Patch:
         d.geo_n_knots = (C.c_int * dim)(*[len(k) for k in gk])
         d.geo_knots = (dp * dim)(*[k.ctypes.data_as(dp) for k in gk])
         d.ctrl = ctrl.ctypes.data_as(dp)
+        if kappa_field is not None:
+            kk, kpd, kc = kappa_field
+            kk = [np.ascontiguousarray(k, dtype=np.float64) for k in kk]
+            kc = np.ascontiguousarray(kc, dtype=np.float64)
+            self._keep += kk + [kc]
+            d.kappa_p = int(kpd)
+            d.kappa_n_knots = (C.c_int * dim)(*[len(k) for k in kk])
+            d.kappa_knots = (dp * dim)(*[k.ctypes.data_as(dp) for k in kk])
+            d.kappa_ctrl = kc.ctypes.data_as(dp)
         h = C.c_void_p()
         _check(L.igafd_setup_patch(C.byref(d), _stream(), C.byref(h)), "setup_patch")
         self.h = h
@@ -192,7 +225,12 @@ class Patch:
 
     @classmethod
     def from_problem(cls, prob):
-        return cls(prob.knots, prob.p, prob.ctrl, prob.kappa)
+        kf = None
+        if getattr(prob, "kappa_ctrl", None) is not None:
+            kf = (prob.kappa_knots, prob.kappa_p, prob.kappa_ctrl)
+        return cls(prob.knots, prob.p, prob.ctrl, prob.kappa,
+                   geo_knots=getattr(prob, "geo_knots", None), geo_p=getattr(prob, "geo_p", None),
+                   kappa_field=kf)
 
     def query(self):
         info = PatchInfo()
@@ -214,6 +252,37 @@ class Patch:
         _check(lib().igafd_autotune(self.h, int(bool(force)), _stream()), "autotune")
         self.info = self.query()
         return self.info.stencil_stages
+
+    # ---- span scalings of the pencils -------------------------------------
+    def scaling_rows(self):
+        r = C.c_int()
+        _check(lib().igafd_scaling_rows(self.h, C.byref(r)), "scaling_rows")
+        return r.value
+
+    def features(self):
+        """float32 CUDA tensor [rows][6] of per-span features of Q."""
+        import torch
+        out = torch.empty((self.scaling_rows(), 6), dtype=torch.float32, device="cuda")
+        _check(lib().igafd_patch_features(self.h, C.c_void_p(out.data_ptr()), _stream()), "features")
+        return out
+
+    def sepfit(self, sweeps=20):
+        """float32 CUDA tensor [rows][2] of separable-fit log scalings."""
+        import torch
+        out = torch.empty((self.scaling_rows(), 2), dtype=torch.float32, device="cuda")
+        _check(lib().igafd_patch_sepfit(self.h, int(sweeps), C.c_void_p(out.data_ptr()), _stream()),
+               "sepfit")
+        return out
+
+    def set_scalings(self, logw=None):
+        """Rebuild the preconditioner from span-scaled pencils (logw: float32
+        CUDA tensor [rows][2]) or, with None, from the unscaled ones."""
+        ptr = None
+        if logw is not None:
+            logw = logw.contiguous()
+            assert logw.is_cuda and logw.shape == (self.scaling_rows(), 2)
+            ptr = C.c_void_p(logw.data_ptr())
+        _check(lib().igafd_set_scalings(self.h, ptr, _stream()), "set_scalings")
 
     def set_stencil_stages(self, stages):
         _check(lib().igafd_set_stencil_stages(self.h, int(stages)), "set_stencil_stages")
@@ -269,6 +338,73 @@ class Patch:
     def close(self):
         if getattr(self, "h", None):
             lib().igafd_destroy_patch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The scaling network (6 -> 64 -> 64 -> 2, tanh) on the GPU."""
+
+    def __init__(self, params=None):
+        fp = C.POINTER(C.c_float)
+        h = C.c_void_p()
+        arr = None
+        if params is not None:
+            arr = np.ascontiguousarray(params, dtype=np.float32)
+            assert arr.size == MLP_PARAMS
+        _check(lib().igafd_mlp_create(None if arr is None else arr.ctypes.data_as(fp), C.byref(h)),
+               "mlp_create")
+        self.h = h
+
+    def set_normalization(self, in_mean, in_std, out_mean, out_std):
+        fp = C.POINTER(C.c_float)
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (in_mean, in_std, out_mean, out_std)]
+        self._norm = arrs
+        _check(lib().igafd_mlp_set_normalization(self.h, *[a.ctypes.data_as(fp) for a in arrs]),
+               "mlp_set_normalization")
+
+    def params(self):
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(lib().igafd_mlp_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float))),
+               "mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        arr = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().igafd_mlp_set_params(self.h, arr.ctypes.data_as(C.POINTER(C.c_float))),
+               "mlp_set_params")
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device="cuda")
+        _check(lib().igafd_mlp_forward(self.h, C.c_void_p(X.data_ptr()), int(X.shape[0]),
+                                       C.c_void_p(Y.data_ptr()), _stream()), "mlp_forward")
+        return Y
+
+    def gradient(self, X, T):
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = C.c_float()
+        fp = C.POINTER(C.c_float)
+        _check(lib().igafd_mlp_gradient(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                        int(X.shape[0]), g.ctypes.data_as(fp), C.byref(loss),
+                                        _stream()), "mlp_gradient")
+        return float(loss.value), g
+
+    def train_step(self, X, T, lr):
+        loss = C.c_float()
+        _check(lib().igafd_mlp_train_step(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                          int(X.shape[0]), float(lr), C.byref(loss), _stream()),
+               "mlp_train_step")
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().igafd_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):

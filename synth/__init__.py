@@ -97,7 +97,13 @@ def random_vector(shape, seed: int) -> np.ndarray:
 
 
 class Problem:
-    """A complete synthetic single-patch problem description (inputs only)."""
+    """A complete synthetic single-patch problem description (inputs only).
+
+    By default the geometry map is a degree-p spline on the discretisation's
+    own knots (isoparametric) and the coefficient is the constant kappa. A
+    separate geometry net (geo_knots, geo_p, ctrl) and a spline coefficient
+    field (kappa_knots, kappa_p, kappa_ctrl; K(x) = kappa * kappa_field I)
+    can be attached."""
 
     def __init__(self, dim: int, n, p: int, amplitudes=None, kappa: float = 1.0):
         if isinstance(n, int):
@@ -110,6 +116,11 @@ class Problem:
         self.amplitudes = None if amplitudes is None else np.asarray(amplitudes, float)
         self.ctrl = control_net(self.knots, p, self.amplitudes)
         self.kappa = float(kappa)
+        self.geo_knots = None
+        self.geo_p = None
+        self.kappa_knots = None
+        self.kappa_p = None
+        self.kappa_ctrl = None
 
     @property
     def shape(self):
@@ -129,3 +140,76 @@ def unit_square(n: int = 64, p: int = 3) -> Problem:
 def deformed_cube(n: int = 128, p: int = 3, seed: int = 0, amp: float = 0.05) -> Problem:
     """3D Poisson on the deformed unit cube, kappa = 1."""
     return Problem(3, n, p, deformation_amplitudes(seed, amp))
+
+
+# ---- learned-scaling workload: coarse random geometry, random coefficient ----
+
+def smooth5(a, axis):
+    """Separable binomial [1, 4, 6, 4, 1] / 16 smoothing along one axis with
+    zero padding (applied to displacements whose boundary values are zero)."""
+    w = np.array([1.0, 4.0, 6.0, 4.0, 1.0]) / 16.0
+    a = np.moveaxis(a, axis, -1)
+    pad = np.zeros(a.shape[:-1] + (a.shape[-1] + 4,))
+    pad[..., 2:-2] = a
+    out = sum(w[j] * pad[..., j:j + a.shape[-1]] for j in range(5))
+    return np.moveaxis(out, -1, axis)
+
+
+def coarse_random_net(seed: int, gp: int = 3, gn: int = 8, sigma: float = 0.15):
+    """Degree-gp geometry net with gn control points per direction on the unit
+    cube: interior points displaced by N(0, (sigma * spacing)^2) per
+    coordinate, displacements smoothed by the 5-point binomial kernel along
+    each axis, boundary points fixed. Returns (knots, gp, ctrl[3][gn][gn][gn])."""
+    kn = [uniform_open_knots(gn - gp, gp) for _ in range(3)]
+    base = control_net(kn, gp)
+    g = rng(seed + 31337)
+    disp = g.normal(0.0, sigma / (gn - 1), size=base.shape)
+    interior = np.zeros(base.shape[1:], bool)
+    interior[1:-1, 1:-1, 1:-1] = True
+    disp[:, ~interior] = 0.0
+    for ax in (1, 2, 3):
+        disp = smooth5(disp, ax)
+    disp[:, ~interior] = 0.0
+    return kn, gp, np.ascontiguousarray(base + disp)
+
+
+def grf_kappa(seed: int, nel: int = 16, kp: int = 3, contrast: float = 100.0,
+              lengthscale: float = 0.2, features: int = 512):
+    """Coefficient kappa = exp(g) for a Gaussian random field g (random Fourier
+    features: `features` cosines, frequencies N(0, lengthscale^-2 I), phases
+    U(0, 2 pi)) sampled at the Greville points of a degree-kp spline on nel
+    uniform elements per direction, affinely rescaled so that the control
+    values span exactly [1, contrast]. Returns (knots, kp, ctrl[m][m][m])."""
+    kn = [uniform_open_knots(nel, kp) for _ in range(3)]
+    gr = [greville(k, kp) for k in kn]
+    z, y, x = np.meshgrid(gr[2], gr[1], gr[0], indexing="ij")
+    g = rng(seed + 4242)
+    om = g.normal(0.0, 1.0 / lengthscale, size=(features, 3))
+    ph = g.uniform(0.0, 2 * np.pi, size=features)
+    pts = np.stack([x, y, z], axis=-1)
+    field = np.sqrt(2.0 / features) * np.cos(pts @ om.T + ph).sum(axis=-1)
+    field = (field - field.min()) / (field.max() - field.min()) * np.log(contrast)
+    return kn, kp, np.ascontiguousarray(np.exp(field))
+
+
+def learned_workload_problem(seed: int, n: int = 96, p: int = 3) -> Problem:
+    """3D patch of the learned-scaling workload: coarse random geometry net
+    and a random coefficient of contrast 100."""
+    pr = Problem(3, n, p)
+    pr.geo_knots, pr.geo_p, pr.ctrl = coarse_random_net(seed)
+    pr.kappa_knots, pr.kappa_p, pr.kappa_ctrl = grf_kappa(seed)
+    return pr
+
+
+def mlp_init(seed: int, sizes=(6, 64, 64, 2)) -> np.ndarray:
+    """Initial parameters of the scaling network (flat, float32): weights
+    Xavier-uniform per layer (layout W1, b1, W2, b2, W3, b3; W as [out][in]),
+    biases zero."""
+    g = rng(seed + 777)
+    parts = []
+    for i in range(len(sizes) - 1):
+        fan_in, fan_out = sizes[i], sizes[i + 1]
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(g.uniform(-lim, lim, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)

@@ -1,0 +1,121 @@
+"""Learned span scalings on the GPU against the oracle: features, separable
+fit, scaled preconditioner, network forward/gradient; and the gain of the
+trained network over the unscaled preconditioner on held-out patches."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import assemble, fd, learned as olearned, pcg
+from gpu_util import need_gpu, make_patch, to_dev, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def kcase(torch):
+    prob = synth.learned_workload_problem(2, n=12, p=2)
+    disc = assemble.Discretization.from_problem(prob)
+    patch = make_patch(prob)
+    yield prob, disc, patch
+    patch.close()
+
+
+def test_variable_coefficient_stencil_and_solve(kcase):
+    """Coarse geometry net on its own knots plus a spline coefficient."""
+    prob, disc, patch = kcase
+    S = disc.assemble_stencil()
+    Sg = patch.stencil().cpu().numpy()
+    assert np.abs(Sg - S).max() <= 1e-13 * np.abs(S).max()
+    A = assemble.stencil_to_csr(disc, S)
+    F = fd.FD([disc.pencil(k) for k in range(3)])
+    b = synth.random_rhs(disc.N, 4)
+    ro = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-13, max_iter=800)
+    x, info = patch.pcg(to_dev(b), tol=1e-12, max_iter=800)
+    assert info.status == 0 and rel(x.cpu().numpy(), ro.x) <= 1e-10
+
+
+def test_features_and_sepfit_match_oracle(kcase):
+    prob, disc, patch = kcase
+    f = patch.features().cpu().numpy()
+    fo = olearned.features(disc)
+    assert f.shape == fo.shape
+    assert np.abs(f - fo).max() <= 1e-4 * max(1.0, np.abs(fo).max())
+    lw = patch.sepfit().cpu().numpy()
+    lwo = olearned.sepfit(disc)
+    assert np.abs(lw - lwo).max() <= 1e-4
+
+
+def test_scaled_preconditioner_matches_oracle_and_affine_pin(torch):
+    a = np.array([1.0, 2.0, 0.5])
+    prob = synth.Problem(3, (9, 8, 10), 2)
+    prob.ctrl = prob.ctrl * a[:, None, None, None]
+    patch = make_patch(prob)
+    disc = assemble.Discretization.from_problem(prob)
+    lw = patch.sepfit()
+    patch.set_scalings(lw)
+    r = synth.random_vector(disc.N, 8)
+    Fs = fd.FD(olearned.scaled_pencils(disc, lw.double().cpu().numpy()))
+    assert rel(patch.apply_prec(to_dev(r)).cpu().numpy(), Fs.apply(r)) <= 1e-10
+    b = to_dev(synth.random_rhs(disc.N, 9))
+    # the scaled P equals A up to the float32 rounding of the log scalings
+    # (~1e-7), so one iteration reaches 1e-6
+    _, info = patch.pcg(b, tol=1e-6)
+    assert info.status == 0 and info.iterations == 1
+    patch.set_scalings(None)
+    _, info0 = patch.pcg(b, tol=1e-6)
+    assert info0.iterations > 3
+    patch.close()
+
+
+def test_network_forward_and_gradient_match_oracle(torch):
+    from paper_1602_01636_gb300 import igafd
+    g = synth.rng(5)
+    params = synth.mlp_init(3) + g.normal(0, 0.05, 4738).astype(np.float32)
+    norm = (np.full(6, 0.2), np.full(6, 1.3), np.array([0.5, -0.2]), np.array([1.5, 0.7]))
+    net = igafd.MLP(params)
+    net.set_normalization(*norm)
+    X = g.normal(0, 1, (300, 6)).astype(np.float32)
+    T = g.normal(0, 1, (300, 2)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    p16 = params.astype(np.float16).astype(np.float64)      # the forward pass uses FP16 weights
+    Yo, _ = olearned.mlp_forward(p16, norm, X.astype(np.float64))
+    assert np.abs(net.forward(Xd).cpu().numpy() - Yo).max() <= 1e-4 * max(1.0, np.abs(Yo).max())
+    loss, grad = net.gradient(Xd, Td)
+    lo, go = olearned.mlp_loss_grad(p16, norm, X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - lo) <= 1e-4 * lo
+    assert np.linalg.norm(grad - go) <= 1e-3 * np.linalg.norm(go)
+    net.close()
+
+
+def test_trained_network_reduces_iterations_on_held_out_patches(torch):
+    """Contrast-100 coefficient on randomly deformed cubes: the network's
+    span scalings need fewer iterations than the paper's unscaled
+    preconditioner on held-out patches."""
+    from paper_1602_01636_gb300 import learned
+    items, keep = [], []
+    for seed in range(16):
+        patch = make_patch(synth.learned_workload_problem(100 + seed, n=14, p=2))
+        items.append((patch, to_dev(synth.random_rhs(patch.N, seed))))
+    X, T, gamma, totals = learned.build_dataset(items)
+    for patch, _ in items:
+        patch.close()
+    assert totals[gamma] <= totals[0.0]          # the labels beat the unscaled P
+    net, losses = learned.train(X, T, synth.mlp_init(0), steps=1500)
+    assert losses[-1] < 0.5 * losses[0]
+    plain, scaled = [], []
+    for seed in range(4):
+        patch = make_patch(synth.learned_workload_problem(9000 + seed, n=14, p=2))
+        b = to_dev(synth.random_rhs(patch.N, 50 + seed))
+        _, i0 = patch.pcg(b, tol=1e-8, max_iter=1000)
+        x, i1, fell_back, _ = learned.scaled_solve(patch, net, b, tol=1e-8, max_iter=1000)
+        assert i0.status == 0 and i1.status == 0
+        plain.append(i0.iterations)
+        scaled.append(i1.iterations)
+        patch.close()
+    print("held-out iterations plain", plain, "learned", scaled, "gamma", gamma)
+    assert np.mean(scaled) < 0.9 * np.mean(plain)

@@ -319,3 +319,71 @@ def test_planted_swapped_fd_transposes_fail_dense_pin(monkeypatch):
     with pytest.raises(AssertionError):
         test_fd_equals_dense_inverse(3, (5, 6, 4), 3)
     monkeypatch.setattr(fd.FD, "apply", orig)
+
+
+# ------------------------------------------------------ span scalings ----
+from oracle import learned  # noqa: E402
+
+
+def _affine_problem(a):
+    pr = synth.Problem(3, (6, 5, 7), 2)
+    pr.ctrl = pr.ctrl * np.asarray(a)[:, None, None, None]
+    return pr
+
+
+def test_sepfit_and_features_affine_map_closed_form():
+    """F = diag(a): Q = kappa prod(a) diag(1/a_k^2) is constant, so the fit is
+    exact (log wK_k = log c_k, log wM = 0) and the slab spread is zero."""
+    a = np.array([1.0, 2.0, 0.5])
+    disc = assemble.Discretization.from_problem(_affine_problem(a))
+    c = np.prod(a) / a ** 2
+    lw = learned.sepfit(disc)
+    dirs = np.repeat(np.arange(3), disc.nel)
+    assert np.allclose(np.exp(lw[:, 0]), c[dirs], rtol=1e-12)
+    assert np.abs(lw[:, 1]).max() < 1e-12
+    f = learned.features(disc)
+    assert np.allclose(f[:, 0], np.log(c[dirs]), atol=1e-12)
+    assert np.allclose(f[:, 2], np.log(c.min()), atol=1e-12)
+    assert np.allclose(f[:, 3], np.log(c.max()), atol=1e-12)
+    assert np.abs(f[:, 4]).max() < 1e-12
+
+
+def test_scaled_pencils_make_P_equal_A_for_affine_map():
+    """With wK_k = c_k the scaled Kronecker sum is A itself: one iteration."""
+    a = np.array([1.0, 2.0, 0.5])
+    disc = assemble.Discretization.from_problem(_affine_problem(a))
+    A = assemble.stencil_to_csr(disc, disc.assemble_stencil())
+    F = fd.FD(learned.scaled_pencils(disc, learned.sepfit(disc)))
+    b = synth.random_rhs(disc.N, 2)
+    res = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-10)
+    assert res.converged and res.iters == 1
+    F0 = fd.FD([disc.pencil(k) for k in range(3)])
+    assert pcg.pcg(lambda v: A @ v, b, F0.apply, tol=1e-10).iters > 3
+
+
+def test_sepfit_scaling_helps_on_random_coefficient():
+    pr = synth.learned_workload_problem(1, n=10, p=2)
+    disc = assemble.Discretization.from_problem(pr)
+    A = assemble.stencil_to_csr(disc, disc.assemble_stencil())
+    b = synth.random_rhs(disc.N, 3)
+    F0 = fd.FD([disc.pencil(k) for k in range(3)])
+    F1 = fd.FD(learned.scaled_pencils(disc, learned.sepfit(disc)))
+    it0 = pcg.pcg(lambda v: A @ v, b, F0.apply, tol=1e-8, max_iter=400).iters
+    it1 = pcg.pcg(lambda v: A @ v, b, F1.apply, tol=1e-8, max_iter=400).iters
+    assert it1 < it0, (it1, it0)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    g = synth.rng(12)
+    params = g.normal(0, 0.3, 4738)
+    X = g.normal(0, 1, (20, 6))
+    T = g.normal(0, 1, (20, 2))
+    norm = (np.full(6, 0.1), np.full(6, 1.5), np.array([0.2, -0.1]), np.array([2.0, 0.5]))
+    loss, grad = learned.mlp_loss_grad(params, norm, X, T)
+    idx = g.choice(4738, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(4738); e[i] = h
+        lp, _ = learned.mlp_loss_grad(params + e, norm, X, T)
+        lm, _ = learned.mlp_loss_grad(params - e, norm, X, T)
+        assert abs((lp - lm) / (2 * h) - grad[i]) <= 1e-6 * max(1.0, abs(grad[i]))
