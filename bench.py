@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="batched workload: COUNT independent 3D problems in one graph launch")
     ap.add_argument("--count", type=int, default=64)
+    ap.add_argument("--learned", action="store_true",
+                    help="learned span scalings: train on generated patches, compare on held-out ones")
+    ap.add_argument("--train", type=int, default=48)
+    ap.add_argument("--test", type=int, default=8)
     return ap.parse_args()
 
 
@@ -524,8 +528,96 @@ def run_batch(args):
         p_.close()
 
 
+def run_learned(args):
+    """Train the scaling network on generated contrast-100 patches and compare
+    PCG with its scalings against the unscaled preconditioner on held-out
+    patches (FP64 FD, tol 1e-8)."""
+    import torch
+    import synth
+    from paper_1602_01636_gb300 import igafd, learned, build as libbuild
+    libbuild.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n, p = args.n if args.n != 128 else 96, args.p
+
+    def make(seed):
+        for attempt in range(50):     # re-draw folded geometries
+            try:
+                return igafd.Patch.from_problem(synth.learned_workload_problem(seed + 100000 * attempt, n=n, p=p))
+            except igafd.IgafdError as e:
+                if e.status != igafd.ERR_FOLDED:
+                    raise
+        raise RuntimeError("no unfolded draw")
+
+    t0 = time.perf_counter()
+    items = []
+    X_parts, T_parts, totals = [], [], {}
+    for i in range(args.train):
+        patch = make(100 + i)
+        b = torch.from_numpy(synth.random_rhs(patch.N, i)).cuda()
+        fit, its = learned.label_patch(patch, b)
+        X_parts.append(patch.features())
+        T_parts.append(fit)
+        for g, v in its.items():
+            totals[g] = totals.get(g, 0) + v
+        patch.close()
+    gamma = min(totals, key=lambda g: (totals[g], g))
+    X = torch.cat(X_parts)
+    T = torch.cat(T_parts) * gamma
+    label_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    net, losses = learned.train(X, T, synth.mlp_init(0), steps=2000)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    res = {"plain_it": [], "learned_it": [], "plain_s": [], "learned_s": [], "prep_s": [], "fallback": 0}
+    for i in range(args.test):
+        patch = make(10000 + i)
+        b = torch.from_numpy(synth.random_rhs(patch.N, 500 + i)).cuda()
+        patch.pcg(b, tol=args.tol, max_iter=2000)          # warm-up (graph capture)
+        a, c = ev(), ev()
+        a.record()
+        _, i0 = patch.pcg(b, tol=args.tol, max_iter=2000)
+        c.record()
+        torch.cuda.synchronize()
+        res["plain_s"].append(a.elapsed_time(c) / 1e3)
+        res["plain_it"].append(i0.iterations)
+        _, i1, fb, prep = learned.scaled_solve(patch, net, b, tol=args.tol, max_iter=2000)
+        a.record()
+        _, i1 = patch.pcg(b, tol=args.tol, max_iter=2000)   # same scalings, timed
+        c.record()
+        torch.cuda.synchronize()
+        res["learned_s"].append(a.elapsed_time(c) / 1e3)
+        res["learned_it"].append(i1.iterations)
+        res["prep_s"].append(prep)
+        res["fallback"] += int(fb)
+        patch.close()
+    mean = lambda v: sum(v) / len(v)
+    line = {"metric": f"learned span scalings: held-out PCG iterations, contrast-100 coefficient, n={n} p={p} @1e-8",
+            "value": mean(res["learned_it"]), "unit": "iterations", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "randomly deformed cube (8^3 degree-3 net, sigma 0.15 spacing, binomial "
+                                   "smoothing), kappa = exp(GRF, lengthscale 0.2) with contrast 100, N(0,1) RHS",
+                       "n": n, "p": p, "train_patches": args.train, "test_patches": args.test,
+                       "rows": int(X.shape[0])},
+            "plain_iterations_mean": mean(res["plain_it"]), "learned_iterations_mean": mean(res["learned_it"]),
+            "plain_iterations": res["plain_it"], "learned_iterations": res["learned_it"],
+            "plain_solve_s_mean": mean(res["plain_s"]), "learned_solve_s_mean": mean(res["learned_s"]),
+            "learned_prep_s_mean": mean(res["prep_s"]), "fallbacks": res["fallback"],
+            "label_gamma": gamma, "label_total_iterations": {str(k): v for k, v in totals.items()},
+            "train_loss": {"first": losses[0], "last": losses[-1]},
+            "label_s": label_s, "train_s": train_s}
+    print(json.dumps(line), flush=True)
+    net.close()
+
+
 def main():
     args = parse()
+    if args.learned:
+        run_learned(args)
+        return
     if args.batch:
         run_batch(args)
         return
