@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--learned", action="store_true",
                     help="learned span scalings: train on generated patches, compare on held-out ones")
+    ap.add_argument("--sweep", action="store_true",
+                    help="precision sweep: n in {128, 192}, p in {2..5}, every FD dtype")
     ap.add_argument("--train", type=int, default=48)
     ap.add_argument("--test", type=int, default=8)
     return ap.parse_args()
@@ -613,8 +615,50 @@ def run_learned(args):
     net.close()
 
 
+def run_sweep(args):
+    """Precision sweep on the deformed cube: for n in {128, 192} and p in
+    {2, 3, 4, 5}, PCG (tol 1e-8) with the FD in FP64, FP32, TF32, BF16 and
+    FP16: iterations, solve time and the solution's relative difference from
+    the all-FP64 solve (the FP64 GPU path is the reference at these sizes; it
+    matches the oracle to 1e-10 where the oracle can assemble A)."""
+    import torch
+    import synth
+    from paper_1602_01636_gb300 import igafd, build as libbuild
+    libbuild.build()
+    out = []
+    for n in (128, 192):
+        for p in (2, 3, 4, 5):
+            t0 = time.perf_counter()
+            patch = igafd.Patch.from_problem(synth.deformed_cube(n, p, seed=0))
+            patch.autotune()
+            setup_s = time.perf_counter() - t0
+            b = patch.load_rhs_sine()
+            x64, i64 = patch.pcg(b, tol=args.tol, dtype="fp64")
+            row = {"n": n, "p": p, "setup_s": setup_s, "stencil_GB": patch.info.stencil_bytes / 1e9}
+            for dt in ("fp64", "fp32", "tf32", "bf16", "fp16"):
+                patch.pcg(b, tol=args.tol, dtype=dt)
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                x, inf = patch.pcg(b, tol=args.tol, dtype=dt)
+                c.record()
+                torch.cuda.synchronize()
+                row[dt] = {"iterations": inf.iterations, "solve_ms": a.elapsed_time(c),
+                           "rel_diff_vs_fp64": float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64)),
+                           "true_relres": inf.true_relres}
+            out.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            patch.close()
+            torch.cuda.empty_cache()
+    line = {"metric": "precision sweep: PCG iterations and solve ms per FD dtype, deformed cube, n in {128,192}, p in {2..5} @1e-8",
+            "value": None, "unit": "table", "data": "synthetic", "n_gpus": 1, "rows": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.learned:
         run_learned(args)
         return

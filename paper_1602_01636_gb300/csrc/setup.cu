@@ -145,7 +145,12 @@ __global__ void geo_check_kernel(PV v, long long nqp, double *part) {
 // (r, s) contract direction 1, then direction 2, and accumulate by the
 // derivative pattern of direction 3 (or 2 in 2D), then contract the last
 // direction per output entry.
-template <int DIM>
+//
+// PERPAT: keep the partial sums of one derivative pattern of direction 3 at
+// a time in shared memory (each (r, s) term belongs to exactly one pattern,
+// so nothing is recomputed; the stencil is accumulated once per pattern).
+// Needed for p >= 5 in 3D, where all four patterns would not fit.
+template <int DIM, bool PERPAT>
 __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
                                 double *__restrict__ stencil, long long Np) {
   extern __shared__ double sm[];
@@ -163,14 +168,14 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
   double *T1 = F + DIM * 2 * A * nq;        // 3D: [A*A][nq][nq], 2D: unused
   double *G = T1 + (DIM == 3 ? A * A * nq * nq : 0);  // 3D: [4][A*A][A*A][nq], 2D: [4][A*A][nq]
   const int AA = A * A;
-  const int Gsz = DIM == 3 ? 4 * AA * AA * nq : 4 * AA * nq;
+  constexpr int kSlots = PERPAT ? 1 : 4;
+  const int Gsz = DIM == 3 ? kSlots * AA * AA * nq : 4 * AA * nq;
   // tables
   for (int i = threadIdx.x; i < DIM * 2 * A * nq; i += blockDim.x) {
     int g = i % nq, a = (i / nq) % A, vd = (i / (nq * A)) % 2, k = i / (2 * nq * A);
     size_t t = (size_t)e[k] * nq + g;
     F[i] = (vd ? v.bd[k] : v.bv[k])[t * A + a];
   }
-  for (int i = threadIdx.x; i < Gsz; i += blockDim.x) G[i] = 0.0;
   // Q at the element's quadrature points, with weights folded in
   for (int g = threadIdx.x; g < nqd; g += blockDim.x) {
     int gq[3] = {g % nq, (g / nq) % nq, DIM == 3 ? g / (nq * nq) : 0};
@@ -185,8 +190,12 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
   }
   __syncthreads();
 #define FV(k, vd, a, g) F[(((k) * 2 + (vd)) * A + (a)) * nq + (g)]
+  for (int pp = 0; pp < (PERPAT ? 4 : 1); ++pp) {
+  for (int i = threadIdx.x; i < Gsz; i += blockDim.x) G[i] = 0.0;
+  __syncthreads();
   for (int r = 0; r < DIM; ++r) {
     for (int s = 0; s < DIM; ++s) {
+      if (PERPAT && 2 * (r == 2) + (s == 2) != pp) continue;
       const double *Qrs = Qs + qidx(r, s, DIM) * nqd;
       const int ra = (r == 0), sa = (s == 0);       // derivative pattern, dir 1
       const int rb = (r == 1), sb = (s == 1);       // dir 2
@@ -202,7 +211,7 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
         }
         __syncthreads();
         // G[pat3][a1b1][a2b2][g3] += sum_g2 f2(a2,g2) f2'(b2,g2) T1[a1b1][g2][g3]
-        const int pat = 2 * (r == 2) + (s == 2);
+        const int pat = PERPAT ? 0 : 2 * (r == 2) + (s == 2);
         double *Gp = G + (size_t)pat * AA * AA * nq;
         for (int i = threadIdx.x; i < AA * AA * nq; i += blockDim.x) {
           int g3 = i % nq, ab2 = (i / nq) % AA, ab1 = i / (nq * AA);
@@ -232,7 +241,6 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
   // Output entries (a, delta): consecutive threads take consecutive a_1 with
   // the same offset, so their stencil addresses are contiguous.
   const int last = DIM - 1;
-  long long Nn1 = v.n[0], Nn2 = v.n[1];
   int nent = 1;
   for (int k = 0; k < DIM; ++k) nent *= A * W;
   for (int i = threadIdx.x; i < nent; i += blockDim.x) {
@@ -259,8 +267,8 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
     double val = 0.0;
     if (DIM == 3) {
       int ab1 = a[0] + A * b[0], ab2 = a[1] + A * b[1];
-      for (int pat = 0; pat < 4; ++pat) {
-        const double *Gp = G + (((size_t)pat * AA + ab1) * AA + ab2) * nq;
+      for (int pat = (PERPAT ? pp : 0); pat < (PERPAT ? pp + 1 : 4); ++pat) {
+        const double *Gp = G + (((size_t)(PERPAT ? 0 : pat) * AA + ab1) * AA + ab2) * nq;
         int da = pat >> 1, db = pat & 1;
         for (int g3 = 0; g3 < nq; ++g3)
           val += FV(last, da, a[2], g3) * FV(last, db, b[2], g3) * Gp[g3];
@@ -278,7 +286,8 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
     for (int k = 0; k < DIM; ++k) { o += (dl[k] + p) * ws; ws *= W; }
     stencil[(size_t)o * Np + row] += val;
   }
-  (void)Nn1; (void)Nn2;
+  __syncthreads();
+  }   // pattern pass
 #undef FV
 }
 
@@ -335,12 +344,12 @@ __global__ void rhs_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2, doubl
   }
 }
 
-size_t assemble_smem(int dim, int p) {
+size_t assemble_smem(int dim, int p, bool perpat) {
   size_t A = p + 1, nq = p + 1, AA = A * A;
   size_t nqd = dim == 3 ? nq * nq * nq : nq * nq;
   size_t nQ = dim == 3 ? 6 : 3;
   size_t s = nQ * nqd + dim * 2 * A * nq;
-  if (dim == 3) s += AA * nq * nq + 4 * AA * AA * nq;
+  if (dim == 3) s += AA * nq * nq + (perpat ? 1 : 4) * AA * AA * nq;
   else s += 4 * AA * nq;
   return s * sizeof(double);
 }
@@ -446,14 +455,17 @@ igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s) {
   if (!(mdet > 0.0)) return IGAFD_ERR_FOLDED;
   // stiffness stencil
   IGAFD_CUDA(cudaMemsetAsync(P->stencil, 0, (size_t)P->n_off * P->Np * sizeof(double), s));
-  size_t smem = assemble_smem(dim, p);
+  const bool perpat = dim == 3 && assemble_smem(dim, p, false) > 200 * 1024;
+  size_t smem = assemble_smem(dim, p, perpat);
   if (smem > 200 * 1024) return IGAFD_ERR_ARG;
   if (dim == 3) {
-    IGAFD_CUDA(cudaFuncSetAttribute(assemble_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+    IGAFD_CUDA(cudaFuncSetAttribute(assemble_kernel<3, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    IGAFD_CUDA(cudaFuncSetAttribute(assemble_kernel<3, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   } else {
-    IGAFD_CUDA(cudaFuncSetAttribute(assemble_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+    IGAFD_CUDA(cudaFuncSetAttribute(assemble_kernel<2, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   const int C = p + 1;
   for (int c3 = 0; c3 < (dim == 3 ? C : 1); ++c3)
@@ -464,10 +476,12 @@ igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s) {
         int ne3 = dim == 3 ? (c3 < P->nel[2] ? (P->nel[2] - c3 + C - 1) / C : 0) : 1;
         long long nb = (long long)ne1 * ne2 * ne3;
         if (nb == 0) continue;
-        if (dim == 3)
-          assemble_kernel<3><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, P->Np);
+        if (dim == 3 && perpat)
+          assemble_kernel<3, true><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, P->Np);
+        else if (dim == 3)
+          assemble_kernel<3, false><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, P->Np);
         else
-          assemble_kernel<2><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, 0, ne1, ne2, P->stencil, P->Np);
+          assemble_kernel<2, false><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, 0, ne1, ne2, P->stencil, P->Np);
         IGAFD_CUDA(cudaGetLastError());
       }
   return IGAFD_OK;
