@@ -239,6 +239,16 @@ igafd_status igafd_autotune(igafd_patch *patch, int flags, void *stream);
  * IGAFD_ERR_ARG). Every depth computes bitwise the same products. */
 igafd_status igafd_set_stencil_stages(igafd_patch *patch, int stages);
 
+/* Choose how the tensor-core preconditioner (IGAFD_TF32, IGAFD_BF16) runs
+ * the six mode products of Sec. 4.1's fast diagonalization when every n_k is
+ * at most 128: fused = 1 (the default) uses three kernels, each chaining two
+ * mode products through on-chip memory (modes 1 and 2 forward; mode 3
+ * forward, the divide by D_1 (+) D_2 (+) D_3 and mode 3 backward; modes 2 and
+ * 1 backward); fused = 0 runs one kernel per mode product through global
+ * memory. Both round the operands the same way; results agree to FP32
+ * accumulation order. Other values: IGAFD_ERR_ARG. */
+igafd_status igafd_set_fd_fused(igafd_patch *patch, int fused);
+
 /* ---- learned span scalings of the pencils -------------------------------
  * Prop. 1 bounds kappa(P^{-1} A) by the spread of the eigenvalues of Q. The
  * element contributions of the 1D pencils can be weighted per span,

@@ -172,6 +172,7 @@ extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *strea
   P->geo_p = d->geo_p;
   P->kappa_p = d->kappa_ctrl ? d->kappa_p : 0;
   P->kappa = d->kappa;
+  P->fd_fused = 1;
   if (cudaGetDevice(&P->dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev) != cudaSuccess) {
     free(P);

@@ -114,6 +114,7 @@ struct igafd_patch {
   double *host_scal;            // pinned mirror of scal
   FDMixed *mixed;
   double *wK[3], *wM[3];        // span scalings of the pencils (device, null = unscaled)
+  int fd_fused;                 // 1: fused tensor-core FD (3 kernels) when n_k <= 128
   int scaled;
   cudaEvent_t ev[IGAFD_NEV];    // phase-timing events (PCG with timing on)
   // diagnostics

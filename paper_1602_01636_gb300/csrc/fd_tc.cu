@@ -21,6 +21,8 @@
 // overflows; the scales are removed exactly in the epilogue.
 #include "common.cuh"
 
+#include <atomic>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -348,6 +350,365 @@ __global__ void b_image_kernel(const float *B, int n, int Np, float scale, unsig
   T::put(img + (size_t)c * Np * kKC * T::kBytes + sw128_off(r, kk * T::kBytes, Np), v);
 }
 
+
+// ---------------------------------------------------------------------------
+// Fused FD for n_k <= 128 with TF32 or BF16 operands: three kernels, each CTA
+// running two dependent MMAs with the intermediate passed from TMEM through
+// shared memory (never through global memory):
+//   SLAB_FWD  (one CTA per slab i3):  Y = X_s U1 (lanes i2, cols j1), then
+//             Z^T = Y^T U2 (lanes j1, cols j2): writes T[i3][j2][j1]
+//             (2D: the whole tensor is one slab and the divide is fused here)
+//   PENCIL    (one CTA per 128 columns c = (j2, j1)): D = T^T U3 (lanes c,
+//             cols j3), divide by D1 (+) D2 (+) D3, then Z = D U3^T (lanes c,
+//             cols i3): writes T2[i3][c]
+//   SLAB_BWD  (one CTA per slab): Y = T2_s U1^T (lanes j2, cols i1), then
+//             Z^T = Y^T U2^T (lanes i1, cols i2): writes z[i3][i2][i1] (FP64)
+// The accumulator lanes of the second MMA are always the contiguous index of
+// the output, so every global store is coalesced.
+enum FusedKind { SLAB_FWD = 0, PENCIL = 1, SLAB_BWD = 2 };
+
+struct FusedArgs {
+  const void *in;            // SLAB_FWD: r (double); others: float
+  int in_f64, in_aligned;
+  void *out;                 // SLAB_BWD: z (double); others: float
+  int out_f64;
+  const unsigned char *B1, *B2;   // images of the first / second B operand
+  int Np1, Np2;              // their rows (N of each MMA, multiple of 16)
+  int K1, K2;                // contraction lengths (valid)
+  int Kp1, Kp2;              // the same padded to whole 64-element chunks (the images' K)
+  int Kpad;                  // max(Kp1, Kp2): sizes the shared-memory regions
+  int rowsA;                 // valid rows of the first A operand (lanes)
+  int n1, n2, n3;
+  long long n12;
+  const float *inv_lam;      // divide (PENCIL, or SLAB_FWD in 2D), null: none
+  const double *done;
+  int *err;
+};
+
+// Pack E = 16 / kBytes operand values into one 16-byte chunk of the
+// swizzled layout (the values are consecutive K elements of one row).
+template <int OP> __device__ __forceinline__ uint4 pack_chunk(const float *v);
+template <> __device__ __forceinline__ uint4 pack_chunk<OP_TF32>(const float *v) {
+  uint32_t t[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t[e]) : "f"(v[e]));
+  return make_uint4(t[0], t[1], t[2], t[3]);
+}
+template <> __device__ __forceinline__ uint4 pack_chunk<OP_BF16>(const float *v) {
+  uint32_t t[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+    t[e] = *reinterpret_cast<uint32_t *>(&h);
+  }
+  return make_uint4(t[0], t[1], t[2], t[3]);
+}
+
+// Stage A[r][k] = in[(row0 + r) * K + k] (r < rowsA, k < K, zero elsewhere)
+// as a K-major swizzled operand of kM rows and Kp columns. Each thread owns
+// one 16-byte chunk (E consecutive k of a row) per step, issues the loads of
+// U chunks before storing any, and stores each chunk with one 16-byte write:
+// consecutive threads take consecutive chunks of a row, so global loads are
+// coalesced and the eight threads of a store phase hit eight distinct banks.
+template <int OP>
+__device__ void stage_rows(unsigned char *R, const void *in, int in_f64, long long row0,
+                           int rowsA, int K, int Kp, int aligned, int tid) {
+  constexpr int E = 16 / Op<OP>::kBytes;
+  constexpr int U = 32 / E;
+  const int cpr = Kp / E;
+  const int total = kM * cpr;
+  const bool vec = aligned && (in_f64 ? (K % 2 == 0) : (K % 4 == 0));
+  for (int b0 = 0; b0 < total; b0 += kThreads * U) {
+    float v[U][E];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int id = b0 + u * kThreads + tid;
+      const int r = id / cpr, k0 = (id - r * cpr) * E;
+      const bool rowok = id < total && r < rowsA;
+      const long long g = (row0 + r) * K + k0;
+      if (in_f64) {
+        const double *src = (const double *)in + g;
+        if (vec) {
+#pragma unroll
+          for (int e = 0; e < E; e += 2) {
+            double2 d = make_double2(0.0, 0.0);
+            if (rowok && k0 + e < K) d = __ldg(reinterpret_cast<const double2 *>(src + e));
+            v[u][e] = (float)d.x;
+            v[u][e + 1] = (float)d.y;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) v[u][e] = (rowok && k0 + e < K) ? (float)__ldg(src + e) : 0.0f;
+        }
+      } else {
+        const float *src = (const float *)in + g;
+        if (vec) {
+#pragma unroll
+          for (int e = 0; e < E; e += 4) {
+            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rowok && k0 + e < K) f = __ldg(reinterpret_cast<const float4 *>(src + e));
+            v[u][e] = f.x; v[u][e + 1] = f.y; v[u][e + 2] = f.z; v[u][e + 3] = f.w;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) v[u][e] = (rowok && k0 + e < K) ? __ldg(src + e) : 0.0f;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int id = b0 + u * kThreads + tid;
+      if (id < total) {
+        const int r = id / cpr, k0 = (id - r * cpr) * E;
+        *reinterpret_cast<uint4 *>(R + sw128_off(r, k0 * Op<OP>::kBytes, kM)) = pack_chunk<OP>(v[u]);
+      }
+    }
+  }
+}
+
+// Stage A[c][k] = in[k * n12 + c0 + c] (c0 + c < n12, k < K, zero elsewhere):
+// the transpose of a block of 128 columns. A thread loads E consecutive k
+// at one c (each load instruction of a warp reads 32 consecutive c) and
+// writes them as one chunk of row c; a store phase covers eight consecutive
+// rows, whose swizzle puts the chunk in eight distinct banks.
+template <int OP>
+__device__ void stage_cols(unsigned char *R, const float *in, long long n12, long long c0, int K,
+                           int Kp, int aligned, int tid) {
+  (void)aligned;
+  constexpr int E = 16 / Op<OP>::kBytes;
+  constexpr int U = 32 / E;
+  const int total = kM * (Kp / E);
+  for (int b0 = 0; b0 < total; b0 += kThreads * U) {
+    float v[U][E];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int id = b0 + u * kThreads + tid;
+      const int c = id % kM, k0 = (id / kM) * E;
+      const bool ok = id < total && c0 + c < n12;
+      const float *src = in + (long long)k0 * n12 + c0 + c;
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[u][e] = (ok && k0 + e < K) ? __ldg(src + (long long)e * n12) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int id = b0 + u * kThreads + tid;
+      if (id < total) {
+        const int c = id % kM, k0 = (id / kM) * E;
+        *reinterpret_cast<uint4 *>(R + sw128_off(c, k0 * Op<OP>::kBytes, kM)) = pack_chunk<OP>(v[u]);
+      }
+    }
+  }
+}
+
+template <int OP, int KIND>
+__global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
+  if (a.done && *a.done != 0.0) return;
+  using T = Op<OP>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base =
+      (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int rowBytes = a.Kpad * T::kBytes;              // bytes of K per row
+  unsigned char *R1 = base;                              // A operands: 128 rows
+  unsigned char *R2 = base + (size_t)kM * rowBytes;      // B operands: up to 128 rows
+  __shared__ uint64_t bar_mma, bar_b;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int blk = blockIdx.x;
+
+  auto wait_on = [&](uint64_t *b, uint32_t parity) -> bool {
+    for (long long it = 0; it < kSpin; ++it) {
+      uint32_t ok;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(smem_u32(b)), "r"(parity)
+          : "memory");
+      if (ok) return true;
+    }
+    return false;
+  };
+  auto load_b = [&](const unsigned char *img, int Np, int Kp) {
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)(Np * Kp * T::kBytes);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar_b)),
+                   "r"(bytes)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(R2)),
+          "l"(img), "r"(bytes), "r"(smem_u32(&bar_b))
+          : "memory");
+    }
+  };
+  auto mma = [&](int Np, int Kp, uint32_t tmem) {
+    const uint32_t idesc = (1u << 4) | (T::kFmt << 7) | (T::kFmt << 10) |
+                           ((uint32_t)(Np >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int ksteps = Kp * T::kBytes / 32;     // 32 bytes of K per MMA
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const int kbyte = ks * 32;
+      const uint64_t ad = sw128_desc(smem_u32(R1) + (kbyte >> 7) * kM * 128 + (kbyte & 127));
+      const uint64_t bd = sw128_desc(smem_u32(R2) + (kbyte >> 7) * Np * 128 + (kbyte & 127));
+      const uint32_t acc = ks > 0 ? 1u : 0u;
+      if (OP == OP_TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&bar_mma))
+        : "memory");
+  };
+  // read 32 TMEM columns [c0, c0+32) of this warp's lane quarter
+  auto tmem_ld32 = [&](uint32_t tmem, int q, int c0, uint32_t *v) {
+    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  };
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_b)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+        smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  load_b(a.B1, a.Np1, a.Kp1);
+
+  // ---- first A operand: rows = lanes of the first accumulator ----
+  if (KIND == PENCIL)
+    stage_cols<OP>(R1, (const float *)a.in, a.n12, (long long)blk * kM, a.K1, a.Kp1, a.in_aligned, tid);
+  else
+    stage_rows<OP>(R1, a.in, a.in_f64, (long long)blk * a.n2, a.rowsA, a.K1, a.Kp1, a.in_aligned, tid);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid == 0) {
+    if (!wait_on(&bar_b, 0)) s_fail = 1;
+    else mma(a.Np1, a.Kp1, tmem);
+  }
+  __syncthreads();
+  if (!s_fail && !wait_on(&bar_mma, 0)) s_fail = 1;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int q = warp & 3, half = warp >> 2;
+  const int lane_row = q * 32 + lane;              // accumulator lane of this thread
+  if (!s_fail) {
+    // second B image into R2 (the first MMA is done with it)
+    load_b(a.B2, a.Np2, a.Kp2);
+    // zero R1, then write the second A operand from the first accumulator
+    const int row2 = a.Kp2 * T::kBytes;
+    for (int i = tid; i < kM * row2 / 16; i += kThreads)
+      reinterpret_cast<uint4 *>(R1)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const int ncol32 = (a.Np1 + 31) / 32;
+    for (int cb = half; cb < ncol32; cb += 2) {
+      uint32_t v[32];
+      tmem_ld32(tmem, q, cb * 32, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = cb * 32 + j;
+        float x = __uint_as_float(v[j]);
+        if (KIND == PENCIL) {
+          // divide by D1 (+) D2 (+) D3 at (j3 = col, c = c0 + lane_row); row = lane, k = col
+          const long long c = (long long)blk * kM + lane_row;
+          if (col < a.K2 && c < a.n12) x *= a.inv_lam[(long long)col * a.n12 + c];
+          else x = 0.0f;
+          v[j] = __float_as_uint(x);
+        } else {
+          // row = col (the new lanes), k = lane
+          if (col < a.Np1 && lane_row * T::kBytes < row2)
+            T::put(R1 + sw128_off(col, lane_row * T::kBytes, kM), lane_row < a.K2 ? x : 0.0f);
+        }
+      }
+      if (KIND == PENCIL) {
+        // row = lane, k = the 32 columns: whole 16-byte chunks
+        constexpr int E = 16 / T::kBytes;
+#pragma unroll
+        for (int e0 = 0; e0 < 32; e0 += E) {
+          const int k0 = cb * 32 + e0;
+          if (k0 * T::kBytes < row2) {
+            float f[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) f[e] = __uint_as_float(v[e0 + e]);
+            *reinterpret_cast<uint4 *>(R1 + sw128_off(lane_row, k0 * T::kBytes, kM)) = pack_chunk<OP>(f);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      if (!wait_on(&bar_b, 1)) s_fail = 1;
+      else mma(a.Np2, a.Kp2, tmem);
+    }
+    __syncthreads();
+    if (!s_fail && !wait_on(&bar_mma, 1)) s_fail = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (!s_fail) {
+    // ---- epilogue: lanes = contiguous output index, columns = strided one ----
+    long long obase, ostride;
+    int nlanes, ncols;
+    if (KIND == PENCIL) {
+      obase = (long long)blk * kM; ostride = a.n12;
+      nlanes = (int)((a.n12 - obase) < kM ? (a.n12 - obase) : kM); ncols = a.n3;
+    } else {
+      obase = (long long)blk * a.n12; ostride = a.n1;
+      nlanes = a.n1; ncols = a.n2;
+    }
+    const int ncol32 = (a.Np2 + 31) / 32;
+    for (int cb = half; cb < ncol32; cb += 2) {
+      uint32_t v[32];
+      tmem_ld32(tmem, q, cb * 32, v);
+      if (lane_row < nlanes) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = cb * 32 + j;
+          if (col < ncols) {
+            const long long o = obase + (long long)col * ostride + lane_row;
+            float x = __uint_as_float(v[j]);
+            if (KIND == SLAB_FWD && a.inv_lam) x *= a.inv_lam[o];
+            if (a.out_f64) ((double *)a.out)[o] = (double)x;
+            else ((float *)a.out)[o] = x;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(a.err, (int)IGAFD_ERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
 }  // namespace
 
 struct FDMixed {
@@ -430,12 +791,88 @@ static igafd_status launch_pass(const PassArgs &a, cudaStream_t s) {
 
 // Tensor-core FD. dt selects the operand type: IGAFD_BF16, IGAFD_FP16, or
 // IGAFD_TF32 (declared in igafd.h).
+constexpr int kFusedMaxSmem = 1024 + (kM + 128) * 128 * 4;
+
+template <int OP, int KIND>
+static igafd_status launch_fused(const FusedArgs &a, int grid, cudaStream_t s, int dev) {
+  const int bytes = OP == OP_TF32 ? 4 : 2;
+  const size_t smem = 1024 + (size_t)(kM + 128) * a.Kpad * bytes;
+  // the largest size this kernel is launched with, set once per device
+  static std::atomic<unsigned long long> attr_set{0};
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_set.load() & bit)) {
+    IGAFD_CUDA(cudaFuncSetAttribute(tc_fused_kernel<OP, KIND>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedMaxSmem));
+    attr_set.fetch_or(bit);
+  }
+  tc_fused_kernel<OP, KIND><<<grid, kThreads, smem, s>>>(a);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
+  return IGAFD_OK;
+}
+
+template <int OP>
+static igafd_status fused_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
+                                double *done) {
+  FDMixed *F = P->mixed;
+  const int op = OP;
+  const int dim = P->dim;
+  const int n1 = P->n[0], n2 = P->n[1], n3 = dim == 3 ? P->n[2] : 1;
+  int kmax = n1 > n2 ? n1 : n2;
+  if (dim == 3 && n3 > kmax) kmax = n3;
+  FusedArgs a{};
+  a.n1 = n1; a.n2 = n2; a.n3 = n3;
+  a.n12 = (long long)n1 * n2;
+  a.Kpad = (kmax + kKC - 1) / kKC * kKC;
+  auto kp = [](int n) { return (n + kKC - 1) / kKC * kKC; };
+  a.done = done;
+  a.err = P->err_flag;
+  auto np = [](int n) { return (n + 15) / 16 * 16; };
+  // images are padded to whole 64-element K chunks; use the largest K
+  float *t1 = (float *)P->fd_a, *t2 = (float *)P->fd_b;
+  // slab forward (modes 1 and 2; the divide too in 2D)
+  a.in = r; a.in_f64 = 1; a.in_aligned = ((uintptr_t)r % 16) == 0;
+  a.out = t1; a.out_f64 = 0;
+  a.B1 = F->img[0][0][op]; a.Np1 = np(n1); a.K1 = n1; a.Kp1 = kp(n1);
+  a.B2 = F->img[1][0][op]; a.Np2 = np(n2); a.K2 = n2; a.Kp2 = kp(n2);
+  a.rowsA = n2;
+  a.inv_lam = dim == 2 ? P->inv_lam32 : nullptr;
+  IGAFD_TRY((launch_fused<OP, SLAB_FWD>(a, n3, s, P->dev)));
+  const float *mid = t1;
+  if (dim == 3) {
+    FusedArgs c = a;
+    c.in = t1; c.in_f64 = 0; c.in_aligned = 1;
+    c.out = t2; c.out_f64 = 0;
+    c.B1 = F->img[2][0][op]; c.Np1 = np(n3); c.K1 = n3; c.Kp1 = kp(n3);
+    c.B2 = F->img[2][1][op]; c.Np2 = np(n3); c.K2 = n3; c.Kp2 = kp(n3);
+    c.rowsA = kM;
+    c.inv_lam = P->inv_lam32;
+    IGAFD_TRY((launch_fused<OP, PENCIL>(c, (int)((a.n12 + kM - 1) / kM), s, P->dev)));
+    mid = t2;
+  }
+  FusedArgs b = a;
+  b.in = mid; b.in_f64 = 0; b.in_aligned = 1;
+  b.out = z; b.out_f64 = 1;
+  b.B1 = F->img[0][1][op]; b.Np1 = np(n1); b.K1 = n1; b.Kp1 = kp(n1);
+  b.B2 = F->img[1][1][op]; b.Np2 = np(n2); b.K2 = n2; b.Kp2 = kp(n2);
+  b.rowsA = n2;
+  b.inv_lam = nullptr;
+  IGAFD_TRY((launch_fused<OP, SLAB_BWD>(b, n3, s, P->dev)));
+  return IGAFD_OK;
+}
+
 igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, double *z,
                                cudaStream_t s, double *done) {
   FDMixed *F = P->mixed;
   if (!F) return IGAFD_ERR_ARG;
   const int op = dt == IGAFD_TF32 ? OP_TF32 : dt == IGAFD_BF16 ? OP_BF16 : OP_FP16;
   const int dim = P->dim;
+  bool fusable = op != OP_FP16 && P->fd_fused;
+  for (int k = 0; k < dim; ++k) fusable = fusable && P->n[k] <= 128;
+  if (fusable) {
+    if (op == OP_TF32) return fused_apply<OP_TF32>(P, r, z, s, done);
+    return fused_apply<OP_BF16>(P, r, z, s, done);
+  }
   for (int k = 0; k < dim; ++k)
     if (P->n[k] > 256) return IGAFD_ERR_ARG;   // one MMA covers N <= 256
   // current layout: dims[0] slowest .. dims[dim-1] fastest (direction indices)

@@ -132,3 +132,9 @@ extern "C" igafd_status igafd_set_stencil_stages(igafd_patch *P, int stages) {
   P->stencil_stages = stages;
   return IGAFD_OK;
 }
+
+extern "C" igafd_status igafd_set_fd_fused(igafd_patch *P, int fused) {
+  if (!P || (fused != 0 && fused != 1)) return IGAFD_ERR_ARG;
+  P->fd_fused = fused;
+  return IGAFD_OK;
+}

@@ -68,7 +68,7 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_copy_stencil", "igafd_apply_A", "igafd_apply_prec", "igafd_load_rhs_sine",
            "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str",
            "igafd_kernel_launches", "igafd_batch_pcg_solve", "igafd_autotune",
-           "igafd_set_stencil_stages", "igafd_scaling_rows", "igafd_patch_features",
+           "igafd_set_stencil_stages", "igafd_set_fd_fused", "igafd_scaling_rows", "igafd_patch_features",
            "igafd_patch_sepfit", "igafd_set_scalings", "igafd_mlp_create", "igafd_mlp_destroy",
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step"]
@@ -100,6 +100,7 @@ def lib():
                                         C.POINTER(PCGOpts), C.POINTER(PCGInfo), vp]
     L.igafd_autotune.argtypes = [vp, C.c_int, vp]
     L.igafd_set_stencil_stages.argtypes = [vp, C.c_int]
+    L.igafd_set_fd_fused.argtypes = [vp, C.c_int]
     L.igafd_scaling_rows.argtypes = [vp, C.POINTER(C.c_int)]
     L.igafd_patch_features.argtypes = [vp, vp, vp]
     L.igafd_patch_sepfit.argtypes = [vp, C.c_int, vp, vp]
@@ -287,6 +288,9 @@ class Patch:
     def set_stencil_stages(self, stages):
         _check(lib().igafd_set_stencil_stages(self.h, int(stages)), "set_stencil_stages")
         self.info = self.query()
+
+    def set_fd_fused(self, fused):
+        _check(lib().igafd_set_fd_fused(self.h, int(fused)), "set_fd_fused")
 
     def stencil(self):
         import torch

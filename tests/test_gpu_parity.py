@@ -105,6 +105,34 @@ def test_apply_prec_tensor_core(case, dtype):
     assert err <= TC_TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", ["tf32", "bf16"])
+def test_apply_prec_fused_matches_per_mode(case, dtype):
+    """The fused three-kernel FD (two mode products per kernel, the
+    intermediate kept on chip) and the one-kernel-per-mode-product FD round
+    the same operands to the same type; they differ only in the order of the
+    backward products, so they agree to a few operand roundings, and each
+    meets the oracle bound."""
+    prob, disc, S, patch = case
+    F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
+    r = synth.random_vector(disc.N, 15)
+    zo = F.apply(r)
+    from paper_1602_01636_gb300 import igafd
+    rd = to_dev(r)
+    patch.set_fd_fused(0)
+    l0 = igafd.kernel_launches()
+    z_pass = patch.apply_prec(rd, dtype=dtype).cpu().numpy()
+    l1 = igafd.kernel_launches()
+    patch.set_fd_fused(1)
+    z_fused = patch.apply_prec(rd, dtype=dtype).cpu().numpy()
+    l2 = igafd.kernel_launches()
+    # one kernel per mode product, against one per pair of them
+    assert (l1 - l0, l2 - l1) == (2 * prob.dim, prob.dim)
+    e_pass, e_fused, e_mut = rel(z_pass, zo), rel(z_fused, zo), rel(z_fused, z_pass)
+    print(f"{dtype}: per-mode {e_pass:.2e} fused {e_fused:.2e} mutual {e_mut:.2e}")
+    assert e_pass <= TC_TOL[dtype] and e_fused <= TC_TOL[dtype]
+    assert e_mut <= TC_TOL[dtype]
+
+
 @pytest.mark.parametrize("dtype", ["tf32", "bf16", "fp16"])
 def test_pcg_tensor_core_preconditioner(case, dtype):
     prob, disc, S, patch = case
