@@ -94,6 +94,7 @@ typedef struct {
   double eig_ms;       /* of which the generalized eigendecompositions */
   long long stencil_bytes;
   int stencil_stages;  /* ring depth of the stencil pipeline in use (autotuned) */
+  int stencil_rows;    /* rows per compute thread of the stencil in use (1, or 2 in 3D; autotuned) */
 } igafd_patch_info;
 
 typedef struct {
@@ -227,8 +228,8 @@ igafd_status igafd_apply_prec_static(int dim, const int *n, const double *const 
                                      double *z_dev, void *stream);
 
 /* Time the candidate configurations of the A stencil's pipeline (ring depth
- * 3, 4 or 6 offset groups in flight per CTA) on this patch and keep the
- * fastest. Results are cached per process by (dim, p, n_1, n_2, n_3, SM
+ * 3, 4 or 6 offset groups in flight per CTA; in 3D also one or two rows per
+ * compute thread) on this patch and keep the fastest. Results are cached per process by (dim, p, n_1, n_2, n_3, SM
  * count) and, if the environment variable IGAFD_TUNE_CACHE names a file,
  * appended to it (one JSON object per line); igafd_setup_patch applies a
  * cached choice without measuring. flags bit 0: measure even if cached.
@@ -238,6 +239,11 @@ igafd_status igafd_autotune(igafd_patch *patch, int flags, void *stream);
 /* Set the stencil pipeline's ring depth by hand (3, 4 or 6; else
  * IGAFD_ERR_ARG). Every depth computes bitwise the same products. */
 igafd_status igafd_set_stencil_stages(igafd_patch *patch, int stages);
+
+/* Set the stencil's rows per compute thread by hand: 1, or 2 (3D only; else
+ * IGAFD_ERR_ARG). Each row's FMAs run in the same order either way, so the
+ * product is bitwise the same; only the fused dot's summation order moves. */
+igafd_status igafd_set_stencil_rows(igafd_patch *patch, int rows);
 
 /* Choose how the tensor-core preconditioner (IGAFD_TF32, IGAFD_BF16) runs
  * the six mode products of Sec. 4.1's fast diagonalization when every n_k is

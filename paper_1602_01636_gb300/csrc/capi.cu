@@ -173,6 +173,7 @@ extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *strea
   P->kappa_p = d->kappa_ctrl ? d->kappa_p : 0;
   P->kappa = d->kappa;
   P->fd_fused = 1;
+  P->stencil_rows = 1;
   if (cudaGetDevice(&P->dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev) != cudaSuccess) {
     free(P);
@@ -226,6 +227,7 @@ extern "C" igafd_status igafd_patch_query(const igafd_patch *P, igafd_patch_info
   info->eig_ms = P->eig_ms;
   info->stencil_bytes = (long long)P->n_off * P->N * (long long)sizeof(double);
   info->stencil_stages = P->stencil_stages > 0 ? P->stencil_stages : 4;
+  info->stencil_rows = P->stencil_rows == 2 ? 2 : 1;
   return IGAFD_OK;
 }
 

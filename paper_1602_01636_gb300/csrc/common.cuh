@@ -90,6 +90,7 @@ struct igafd_patch {
   long long Np;
   int num_sms;
   int stencil_stages;           // ring depth of the stencil pipeline (0: default; autotuned)
+  int stencil_rows;             // rows per compute thread of the stencil (1 or 2 in 3D; autotuned)
   // FD workspace
   double *fd_a, *fd_b;          // N each
   // PCG workspace

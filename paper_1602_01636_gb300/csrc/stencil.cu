@@ -21,11 +21,7 @@
 
 namespace {
 
-#ifndef IGAFD_STENCIL_NACC
-#define IGAFD_STENCIL_NACC 1
-#endif
-constexpr int kTile = 256;                        // rows per tile = compute threads per CTA
-constexpr int kAcc = IGAFD_STENCIL_NACC;          // independent FMA chains per row
+constexpr int kTile = 256;                        // rows per tile
 // ring depths (offset groups in flight per CTA) the kernel is built for; the
 // autotuner picks one per (dimension, degree, sizes), default kStagesDefault
 constexpr int kStagesDefault = 4;
@@ -122,16 +118,19 @@ struct Geom {
   static constexpr int STAGE = W * kTile + XW;               // doubles per ring stage
 };
 
-// Warp-specialised pipeline: warps 0..7 compute one row each per tile;
-// warp 8 (one elected lane) streams, for every (delta_2, delta_3) group, the
+// Warp-specialised pipeline: the compute warps take R consecutive rows per
+// thread (R = 1: warps 0..7, one row each; R = 2: warps 0..3, two rows each,
+// reading both rows' coefficients and the shared x values with 16-byte
+// shared-memory loads, which halves the load instructions per FMA); the next
+// warp (one elected lane) streams, for every (delta_2, delta_3) group, the
 // 2p+1 coefficient runs of the tile and the x window they multiply into a
 // ring of kStages shared-memory stages (full/empty mbarriers). The FP64 FMAs
 // read both operands from shared memory.
 //
 // MODE 0: y = A x, dot (x, y) -> alpha = rho / (x, y) when pcg.
 // MODE 1: y = b - A x, dot (y, y) -> true (r, r) when pcg.
-template <int DIM, int P, int MODE, int kStages>
-__global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) {
+template <int DIM, int P, int MODE, int kStages, int R>
+__global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs a) {
   if (a.done && *a.done != 0.0) return;
   if (a.every > 0 && ((long long)a.scal[S_ITER]) % a.every != 0) return;
   if (a.tstat && threadIdx.x == 0) atomicMin(&a.tstat[0], global_ns());
@@ -139,6 +138,8 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
   constexpr int W = Gm::W;
   constexpr int G = DIM == 3 ? W * W : W;        // (delta_2, delta_3) groups per tile
   constexpr uint32_t kStageBytes = Gm::STAGE * sizeof(double);
+  constexpr int kCompute = kTile / R;            // compute threads
+  static_assert(R == 1 || R == 2, "one or two rows per thread");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double *ring = reinterpret_cast<double *>(smem_raw);              // [kStages][STAGE]
   uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * Gm::STAGE);
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kTile / 32);
+      mbar_init(&empty[s], kCompute / 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
   __syncthreads();
 
   double dot = 0.0;
-  if (warp == kTile / 32) {
+  if (warp == kCompute / 32) {
     // ---------------- producer warp ----------------
     if (lane == 0) {
       long long issued = 0;
@@ -202,22 +203,26 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
     }
   } else {
     // ---------------- compute warps ----------------
-    double acc[kAcc];
+    double acc[R];
 #pragma unroll
-    for (int i = 0; i < kAcc; ++i) acc[i] = 0.0;
-    long long row = 0;
-    bool live = false;
-    int i2r = 0, i3r = 0;
+    for (int r = 0; r < R; ++r) acc[r] = 0.0;
+    long long row = 0;                       // first of this thread's R rows
+    bool live[R];
+    int i2r[R], i3r[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { live[r] = false; i2r[r] = 0; i3r[r] = 0; }
     for (long long s = 0; s < total; ++s) {
       const int g = (int)(s % G);
       if (g == 0) {
         const long long tile = blockIdx.x + (s / G) * (long long)gridDim.x;
-        row = tile * kTile + tid;
-        live = row < a.N;
-        i2r = (int)((row / a.n1) % a.n2);
-        i3r = DIM == 3 ? (int)(row / n12) : 0;
+        row = tile * kTile + (long long)R * tid;
 #pragma unroll
-        for (int i = 0; i < kAcc; ++i) acc[i] = 0.0;
+        for (int r = 0; r < R; ++r) {
+          live[r] = row + r < a.N;
+          i2r[r] = (int)(((row + r) / a.n1) % a.n2);
+          i3r[r] = DIM == 3 ? (int)((row + r) / n12) : 0;
+          acc[r] = 0.0;
+        }
       }
       const int slot = (int)(s % kStages);
       const uint32_t par = (uint32_t)((s / kStages) & 1);
@@ -232,33 +237,66 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
         break;
       }
       const int d2 = g % W - P, d3 = DIM == 3 ? g / W - P : 0;
-      const long long row0 = row - tid;
+      const long long row0 = row - (long long)R * tid;
       const long long xs0 = row0 + (long long)d3 * n12 + (long long)d2 * a.n1 - P;
       const int sh = (int)(xs0 & 1);                      // window starts at xs0 - sh
       const double *st = ring + (size_t)slot * Gm::STAGE;
-      const double *cf = st + tid;
-      const double *xw = st + W * kTile + tid + sh;       // xw[j] = x[row + off - P + j]
       // rows whose (i_2 + delta_2, i_3 + delta_3) leaves the box have only
       // zero coefficients in this group; skip when the whole warp is out
-      const bool in23 = live && (i2r + d2 >= 0) && (i2r + d2 < a.n2) &&
-                        (DIM == 2 || ((i3r + d3 >= 0) && (i3r + d3 < a.n3)));
-      if (__any_sync(0xffffffffu, in23)) {
+      bool in23 = false;
 #pragma unroll
-        for (int j = 0; j < W; ++j) acc[j % kAcc] = fma(cf[j * kTile], xw[j], acc[j % kAcc]);
+      for (int r = 0; r < R; ++r)
+        in23 = in23 || (live[r] && (i2r[r] + d2 >= 0) && (i2r[r] + d2 < a.n2) &&
+                        (DIM == 2 || ((i3r[r] + d3 >= 0) && (i3r[r] + d3 < a.n3))));
+      if (__any_sync(0xffffffffu, in23)) {
+        if constexpr (R == 1) {
+          const double *cf = st + tid;
+          const double *xw = st + W * kTile + tid + sh;   // xw[j] = x[row + off - P + j]
+#pragma unroll
+          for (int j = 0; j < W; ++j) acc[0] = fma(cf[j * kTile], xw[j], acc[0]);
+        } else {
+          // rows row, row + 1: coefficients cf[j] = (S[o_j][row], S[o_j][row + 1]);
+          // x[row + off - P + j] = xv[j + sh], x[row + 1 + off - P + j] = xv[j + 1 + sh]
+          const double2 *cf = reinterpret_cast<const double2 *>(st + 2 * tid);
+          const double2 *xb = reinterpret_cast<const double2 *>(st + W * kTile + 2 * tid);
+          constexpr int NP = (W + 1) / 2;                  // pairs covering W + 1 values
+          double xv[2 * NP + 2];
+          if (sh == 0) {
+#pragma unroll
+            for (int m = 0; m < NP; ++m) { const double2 v = xb[m]; xv[2 * m] = v.x; xv[2 * m + 1] = v.y; }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+              const double2 c = cf[j * (kTile / 2)];
+              acc[0] = fma(c.x, xv[j], acc[0]);
+              acc[1] = fma(c.y, xv[j + 1], acc[1]);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < NP + 1; ++m) { const double2 v = xb[m]; xv[2 * m] = v.x; xv[2 * m + 1] = v.y; }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+              const double2 c = cf[j * (kTile / 2)];
+              acc[0] = fma(c.x, xv[j + 1], acc[0]);
+              acc[1] = fma(c.y, xv[j + 2], acc[1]);
+            }
+          }
+        }
       }
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot])) : "memory");
-      if (g == G - 1 && live) {
-        double ax = acc[0];
+      if (g == G - 1) {
 #pragma unroll
-        for (int i = 1; i < kAcc; ++i) ax += acc[i];
-        if (MODE == 0) {
-          a.y[row] = ax;
-          dot = fma(a.x[row], ax, dot);
-        } else {
-          const double rr = a.b[row] - ax;
-          a.y[row] = rr;
-          dot = fma(rr, rr, dot);
+        for (int r = 0; r < R; ++r) {
+          if (!live[r]) continue;
+          const double ax = acc[r];
+          if (MODE == 0) {
+            a.y[row + r] = ax;
+            dot = fma(a.x[row + r], ax, dot);
+          } else {
+            const double rr = a.b[row + r] - ax;
+            a.y[row + r] = rr;
+            dot = fma(rr, rr, dot);
+          }
         }
       }
     }
@@ -302,45 +340,56 @@ __global__ void __launch_bounds__(kTile + 32) stencil_tma_kernel(StencilArgs a) 
   }
 }
 
-template <int DIM, int P, int MODE, int kStages>
+template <int DIM, int P, int MODE, int kStages, int R>
 igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, cudaStream_t s) {
   const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
-  auto kern = stencil_tma_kernel<DIM, P, MODE, kStages>;
+  constexpr int kBlock = kTile / R + 32;
+  auto kern = stencil_tma_kernel<DIM, P, MODE, kStages, R>;
   static int per_sm = 0;   // resident CTAs per SM for this instantiation
   if (per_sm == 0) {
     IGAFD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb = 0;
-    IGAFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kTile + 32, smem));
+    IGAFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBlock, smem));
     per_sm = nb > 0 ? nb : 1;
   }
   long long grid = (long long)num_sms * per_sm;
   if (grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
-  kern<<<(int)grid, kTile + 32, smem, s>>>(a);
+  kern<<<(int)grid, kBlock, smem, s>>>(a);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 
+// two rows per thread are built for 3D only (2D patches are small)
+template <int DIM, int P, int MODE, int kStages>
+igafd_status launch_rows(int rows, const StencilArgs &a, long long cap, int sms, cudaStream_t s) {
+  if constexpr (DIM == 3)
+    if (rows == 2) return launch_one<DIM, P, MODE, kStages, 2>(a, cap, sms, s);
+  return launch_one<DIM, P, MODE, kStages, 1>(a, cap, sms, s);
+}
+
 template <int DIM, int P, int MODE>
-igafd_status launch_stages(int stages, const StencilArgs &a, long long cap, int sms, cudaStream_t s) {
+igafd_status launch_stages(int stages, int rows, const StencilArgs &a, long long cap, int sms,
+                           cudaStream_t s) {
   switch (stages) {
-    case 3: return launch_one<DIM, P, MODE, 3>(a, cap, sms, s);
-    case 6: return launch_one<DIM, P, MODE, 6>(a, cap, sms, s);
-    default: return launch_one<DIM, P, MODE, 4>(a, cap, sms, s);
+    case 3: return launch_rows<DIM, P, MODE, 3>(rows, a, cap, sms, s);
+    case 6: return launch_rows<DIM, P, MODE, 6>(rows, a, cap, sms, s);
+    default: return launch_rows<DIM, P, MODE, 4>(rows, a, cap, sms, s);
   }
 }
 
 template <int DIM, int MODE>
-igafd_status launch_p(int p, int stages, const StencilArgs &a, long long cap, int sms, cudaStream_t s) {
+igafd_status launch_p(int p, int stages, int rows, const StencilArgs &a, long long cap, int sms,
+                      cudaStream_t s) {
   switch (p) {
-    case 1: return launch_stages<DIM, 1, MODE>(stages, a, cap, sms, s);
-    case 2: return launch_stages<DIM, 2, MODE>(stages, a, cap, sms, s);
-    case 3: return launch_stages<DIM, 3, MODE>(stages, a, cap, sms, s);
-    case 4: return launch_stages<DIM, 4, MODE>(stages, a, cap, sms, s);
-    case 5: return launch_stages<DIM, 5, MODE>(stages, a, cap, sms, s);
-    case 6: return launch_stages<DIM, 6, MODE>(stages, a, cap, sms, s);
-    case 7: return launch_stages<DIM, 7, MODE>(stages, a, cap, sms, s);
+    case 1: return launch_stages<DIM, 1, MODE>(stages, rows, a, cap, sms, s);
+    case 2: return launch_stages<DIM, 2, MODE>(stages, rows, a, cap, sms, s);
+    case 3: return launch_stages<DIM, 3, MODE>(stages, rows, a, cap, sms, s);
+    case 4: return launch_stages<DIM, 4, MODE>(stages, rows, a, cap, sms, s);
+    case 5: return launch_stages<DIM, 5, MODE>(stages, rows, a, cap, sms, s);
+    case 6: return launch_stages<DIM, 6, MODE>(stages, rows, a, cap, sms, s);
+    case 7: return launch_stages<DIM, 7, MODE>(stages, rows, a, cap, sms, s);
     default: return IGAFD_ERR_ARG;
   }
 }
@@ -392,10 +441,11 @@ igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, co
   // tiles or the partial-sum slots
   long long cap = a.ntiles < IGAFD_RED_BLOCKS ? a.ntiles : IGAFD_RED_BLOCKS;
   const int st = P->stencil_stages > 0 ? P->stencil_stages : kStagesDefault;
+  const int rows = P->stencil_rows == 2 ? 2 : 1;
   if (P->dim == 3) {
-    if (b) return launch_p<3, 1>(P->p, st, a, cap, P->num_sms, s);
-    return launch_p<3, 0>(P->p, st, a, cap, P->num_sms, s);
+    if (b) return launch_p<3, 1>(P->p, st, rows, a, cap, P->num_sms, s);
+    return launch_p<3, 0>(P->p, st, rows, a, cap, P->num_sms, s);
   }
-  if (b) return launch_p<2, 1>(P->p, st, a, cap, P->num_sms, s);
-  return launch_p<2, 0>(P->p, st, a, cap, P->num_sms, s);
+  if (b) return launch_p<2, 1>(P->p, st, 1, a, cap, P->num_sms, s);
+  return launch_p<2, 0>(P->p, st, 1, a, cap, P->num_sms, s);
 }

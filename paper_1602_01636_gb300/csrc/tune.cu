@@ -1,11 +1,12 @@
 // Autotuner for the hot kernels of a patch.
 //
 // The stencil pipeline is built for several ring depths (offset groups in
-// flight per CTA: 3, 4, 6). The best depth depends on the degree (bytes per
-// stage grow with 2p+1, trading shared memory per CTA against resident CTAs
-// per SM) and on the sizes, so it is measured: each candidate applies A a
-// few times to the patch's own search-direction buffer, timed with CUDA
-// events, and the fastest is kept in the patch. Results are cached per
+// flight per CTA: 3, 4, 6) and, in 3D, for one or two rows per compute
+// thread. The best choice depends on the degree (bytes per stage grow with
+// 2p+1, trading shared memory per CTA against resident CTAs per SM) and on
+// the sizes, so it is measured: each candidate applies A a few times to the
+// patch's own search-direction buffer, timed with CUDA events, and the
+// fastest is kept in the patch. Results are cached per
 // process, keyed by (dim, p, n_1, n_2, n_3, SM count), and, when the
 // environment variable IGAFD_TUNE_CACHE names a file, in that file (one JSON
 // object per line), so later processes reuse them without measuring.
@@ -20,9 +21,11 @@
 
 namespace {
 
+constexpr int kNumCand = 6;
+
 struct TuneEntry {
-  int stages;
-  float ms[3];
+  int stages, rows;
+  float ms[kNumCand];   // candidate c: depth kCandidates[c % 3], rows 1 + c / 3
 };
 
 std::mutex g_tune_mutex;
@@ -37,7 +40,8 @@ std::string tune_key(const igafd_patch *P) {
   return buf;
 }
 
-// lines: {"key": "3:3:128:128:128:sm152", "stencil_stages": 4, "ms": [a, b, c]}
+// lines: {"key": "3:3:128:128:128:sm152", "stencil_stages": 4, "stencil_rows": 2,
+//         "ms": [six times, -1 where not measured]}
 void load_file_locked() {
   if (g_tune_loaded) return;
   g_tune_loaded = true;
@@ -49,8 +53,11 @@ void load_file_locked() {
   while (fgets(line, sizeof(line), f)) {
     char key[128];
     TuneEntry e{};
-    if (sscanf(line, " {\"key\": \"%127[^\"]\", \"stencil_stages\": %d, \"ms\": [%f, %f, %f]",
-               key, &e.stages, &e.ms[0], &e.ms[1], &e.ms[2]) == 5)
+    if (sscanf(line,
+               " {\"key\": \"%127[^\"]\", \"stencil_stages\": %d, \"stencil_rows\": %d, "
+               "\"ms\": [%f, %f, %f, %f, %f, %f]",
+               key, &e.stages, &e.rows, &e.ms[0], &e.ms[1], &e.ms[2], &e.ms[3], &e.ms[4],
+               &e.ms[5]) == 9)
       g_tune[key] = e;
   }
   fclose(f);
@@ -61,8 +68,10 @@ void append_file_locked(const std::string &key, const TuneEntry &e) {
   if (!path || !*path) return;
   FILE *f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "{\"key\": \"%s\", \"stencil_stages\": %d, \"ms\": [%.5f, %.5f, %.5f]}\n",
-          key.c_str(), e.stages, e.ms[0], e.ms[1], e.ms[2]);
+  fprintf(f,
+          "{\"key\": \"%s\", \"stencil_stages\": %d, \"stencil_rows\": %d, "
+          "\"ms\": [%.5f, %.5f, %.5f, %.5f, %.5f, %.5f]}\n",
+          key.c_str(), e.stages, e.rows, e.ms[0], e.ms[1], e.ms[2], e.ms[3], e.ms[4], e.ms[5]);
   fclose(f);
 }
 
@@ -73,7 +82,10 @@ void igafd_tune_lookup(igafd_patch *P) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   load_file_locked();
   auto it = g_tune.find(tune_key(P));
-  if (it != g_tune.end()) P->stencil_stages = it->second.stages;
+  if (it != g_tune.end()) {
+    P->stencil_stages = it->second.stages;
+    P->stencil_rows = it->second.rows;
+  }
 }
 
 extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) {
@@ -86,6 +98,7 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
     auto it = g_tune.find(key);
     if (it != g_tune.end() && !(flags & 1)) {
       P->stencil_stages = it->second.stages;
+      P->stencil_rows = it->second.rows;
       return IGAFD_OK;
     }
   }
@@ -95,11 +108,15 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
   IGAFD_CUDA(cudaEventCreate(&e1));
   TuneEntry best{};
   best.stages = 4;
+  best.rows = 1;
   float best_ms = 1e30f;
-  const int saved = P->stencil_stages;
+  const int saved = P->stencil_stages, saved_rows = P->stencil_rows;
+  const int ncand = P->dim == 3 ? kNumCand : 3;
   igafd_status st = IGAFD_OK;
-  for (int c = 0; c < 3 && st == IGAFD_OK; ++c) {
-    P->stencil_stages = kCandidates[c];
+  for (int c = 0; c < kNumCand; ++c) best.ms[c] = -1.0f;
+  for (int c = 0; c < ncand && st == IGAFD_OK; ++c) {
+    P->stencil_stages = kCandidates[c % 3];
+    P->stencil_rows = 1 + c / 3;
     st = igafd_stencil_launch(P, P->pv, P->q, nullptr, 0, 0, s);     // warm-up
     if (st != IGAFD_OK) break;
     cudaEventRecord(e0, s);
@@ -111,16 +128,19 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
     best.ms[c] = ms / 5;
     if (best.ms[c] < best_ms) {
       best_ms = best.ms[c];
-      best.stages = kCandidates[c];
+      best.stages = kCandidates[c % 3];
+      best.rows = 1 + c / 3;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != IGAFD_OK) {
     P->stencil_stages = saved;
+    P->stencil_rows = saved_rows;
     return st;
   }
   P->stencil_stages = best.stages;
+  P->stencil_rows = best.rows;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tune[key] = best;
   append_file_locked(key, best);
@@ -130,6 +150,12 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
 extern "C" igafd_status igafd_set_stencil_stages(igafd_patch *P, int stages) {
   if (!P || (stages != 3 && stages != 4 && stages != 6)) return IGAFD_ERR_ARG;
   P->stencil_stages = stages;
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_set_stencil_rows(igafd_patch *P, int rows) {
+  if (!P || (rows != 1 && rows != 2) || (rows == 2 && P->dim != 3)) return IGAFD_ERR_ARG;
+  P->stencil_rows = rows;
   return IGAFD_OK;
 }
 

@@ -47,7 +47,8 @@ class PatchInfo(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("n", C.c_int * 3), ("N", C.c_longlong),
                 ("nel", C.c_int * 3), ("n_offsets", C.c_int), ("min_detJ", C.c_double),
                 ("q_bound", C.c_double), ("setup_ms", C.c_double), ("eig_ms", C.c_double),
-                ("stencil_bytes", C.c_longlong), ("stencil_stages", C.c_int)]
+                ("stencil_bytes", C.c_longlong), ("stencil_stages", C.c_int),
+                ("stencil_rows", C.c_int)]
 
 
 class PCGOpts(C.Structure):
@@ -68,7 +69,7 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_copy_stencil", "igafd_apply_A", "igafd_apply_prec", "igafd_load_rhs_sine",
            "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str",
            "igafd_kernel_launches", "igafd_batch_pcg_solve", "igafd_autotune",
-           "igafd_set_stencil_stages", "igafd_set_fd_fused", "igafd_scaling_rows", "igafd_patch_features",
+           "igafd_set_stencil_stages", "igafd_set_stencil_rows", "igafd_set_fd_fused", "igafd_scaling_rows", "igafd_patch_features",
            "igafd_patch_sepfit", "igafd_set_scalings", "igafd_mlp_create", "igafd_mlp_destroy",
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step"]
@@ -101,6 +102,7 @@ def lib():
     L.igafd_autotune.argtypes = [vp, C.c_int, vp]
     L.igafd_set_stencil_stages.argtypes = [vp, C.c_int]
     L.igafd_set_fd_fused.argtypes = [vp, C.c_int]
+    L.igafd_set_stencil_rows.argtypes = [vp, C.c_int]
     L.igafd_scaling_rows.argtypes = [vp, C.POINTER(C.c_int)]
     L.igafd_patch_features.argtypes = [vp, vp, vp]
     L.igafd_patch_sepfit.argtypes = [vp, C.c_int, vp, vp]
@@ -248,8 +250,9 @@ class Patch:
         return D, U
 
     def autotune(self, force=False):
-        """Measure the stencil pipeline's candidate ring depths on this patch
-        and keep the fastest; returns the chosen depth."""
+        """Measure the stencil pipeline's candidates on this patch (ring depth,
+        and in 3D one or two rows per thread) and keep the fastest; returns the
+        chosen depth (`info.stencil_rows` holds the rows)."""
         _check(lib().igafd_autotune(self.h, int(bool(force)), _stream()), "autotune")
         self.info = self.query()
         return self.info.stencil_stages
@@ -287,6 +290,10 @@ class Patch:
 
     def set_stencil_stages(self, stages):
         _check(lib().igafd_set_stencil_stages(self.h, int(stages)), "set_stencil_stages")
+        self.info = self.query()
+
+    def set_stencil_rows(self, rows):
+        _check(lib().igafd_set_stencil_rows(self.h, int(rows)), "set_stencil_rows")
         self.info = self.query()
 
     def set_fd_fused(self, fused):

@@ -315,21 +315,27 @@ def test_batched_solve_matches_single_solves(torch):
 
 
 def test_autotune_picks_a_candidate_and_every_depth_agrees(torch):
-    """The autotuner keeps one of the measured ring depths; every depth gives
-    bitwise the same product with A (and the oracle's, to tolerance)."""
+    """The autotuner keeps one of the measured configurations; every ring
+    depth and both row counts per thread give bitwise the same product with A
+    (and the oracle's, to tolerance)."""
     prob = synth.Problem(3, (40, 33, 37), 3, [0.05, 0.02, -0.03])
     patch = make_patch(prob)
     x = to_dev(synth.random_vector(patch.N, 77))
     y0 = patch.apply_A(x)
     assert patch.autotune(force=True) in (3, 4, 6)
-    for st in (3, 4, 6):
-        patch.set_stencil_stages(st)
-        assert patch.info.stencil_stages == st
-        assert torch.equal(patch.apply_A(x), y0)
+    assert patch.info.stencil_rows in (1, 2)
+    for rows in (1, 2):
+        patch.set_stencil_rows(rows)
+        for st in (3, 4, 6):
+            patch.set_stencil_stages(st)
+            assert (patch.info.stencil_stages, patch.info.stencil_rows) == (st, rows)
+            assert torch.equal(patch.apply_A(x), y0)
     disc = assemble.Discretization.from_problem(prob)
     yo = assemble.apply_stencil(disc, disc.assemble_stencil(), x.cpu().numpy())
     assert np.abs(y0.cpu().numpy() - yo).max() <= 1e-12 * np.abs(yo).max()
     from paper_1602_01636_gb300 import igafd
     with pytest.raises(igafd.IgafdError):
         patch.set_stencil_stages(5)
+    with pytest.raises(igafd.IgafdError):
+        patch.set_stencil_rows(3)
     patch.close()
