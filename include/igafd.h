@@ -95,6 +95,10 @@ typedef struct {
   long long stencil_bytes;
   int stencil_stages;  /* ring depth of the stencil pipeline in use (autotuned) */
   int stencil_rows;    /* rows per compute thread of the stencil in use (1, or 2 in 3D; autotuned) */
+  int eig_refined[3];  /* per direction: 1 if the eigenpairs of the last setup of P came from the
+                          FP32 start + FP64 refinement route, 0 if from FP64 Jacobi */
+  double eig_check[3][2]; /* per direction, the refinement route's final check: max |U~^T U~ - I|
+                             and max |offdiag U~^T K~ U~| / max |diag| (accepted if both <= 1e-12) */
 } igafd_patch_info;
 
 typedef struct {
@@ -226,6 +230,28 @@ const char *igafd_status_str(igafd_status s);
 igafd_status igafd_apply_prec_static(int dim, const int *n, const double *const *U,
                                      const double *const *D, const double *r_dev,
                                      double *z_dev, void *stream);
+
+/* Redo P's setup (Section 4.1) in place, on the patch's own buffers (no
+ * allocation): the 1D pencils K_k, M_k (span-scaled if igafd_set_scalings
+ * set scalings), their generalized eigendecompositions K_k U_k = M_k U_k D_k
+ * (Section 3, Eq. (eigen3d)), 1 / (D_1 (+) D_2 (+) D_3) and the FP32 and
+ * tensor-core copies of U_k. The paper's solver timings include this
+ * setup of the preconditioner (Section 5), so a full time-to-solution is
+ * igafd_setup_prec followed by igafd_pcg_solve. igafd_setup_patch runs it
+ * once. Synchronises the stream. Errors: IGAFD_ERR_NOT_SPD (M_k not
+ * positive definite), IGAFD_ERR_EIG (no convergence), IGAFD_ERR_CUDA. */
+igafd_status igafd_setup_prec(igafd_patch *patch, void *stream);
+
+/* Eigen-solver route for the next setup of P: 0 (default) = for every
+ * direction with n_k <= 128, an FP32 start in shared memory (Householder
+ * tridiagonalisation, bisection, inverse iteration) followed by FP64
+ * iterative refinement of the eigenvectors (Ogita and Aishima, 2018) and
+ * exact rotations of nearly degenerate pairs, accepted only if
+ * max |U~^T U~ - I| <= 1e-12 and the off-diagonal of U~^T K~ U~ is <= 1e-12
+ * of its diagonal, else (and for n_k > 128) FP64 cyclic Jacobi; 1 = FP64
+ * Jacobi for every direction. igafd_patch_info.eig_refined reports the
+ * route each direction took. Other values: IGAFD_ERR_ARG. */
+igafd_status igafd_set_eig_route(igafd_patch *patch, int route);
 
 /* Time the candidate configurations of the A stencil's pipeline (ring depth
  * 3, 4 or 6 offset groups in flight per CTA; in 3D also one or two rows per

@@ -64,6 +64,7 @@ void free_patch(igafd_patch *P) {
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   cudaFree(P->q); cudaFree(P->xt);
   cudaFree(P->partial); cudaFree(P->counter); cudaFree(P->scal); cudaFree(P->err_flag);
+  cudaFree(P->eig_work); cudaFree(P->eig_jobs);
   igafd_fd_tc_free(P);
   for (int i = 0; i < IGAFD_NEV; ++i)
     if (P->ev[i]) cudaEventDestroy(P->ev[i]);
@@ -125,20 +126,42 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
   for (int i = 0; i < IGAFD_NEV; ++i) IGAFD_CUDA(cudaEventCreate(&P->ev[i]));
   IGAFD_CUDA(cudaMemsetAsync(P->counter, 0, 8 * sizeof(unsigned), s));
   IGAFD_CUDA(cudaMemsetAsync(P->scal, 0, (S_COUNT + 1) * sizeof(double), s));
-  IGAFD_TRY(igafd_setup_pencils_eig(P, s));
-  for (int k = 0; k < P->dim; ++k) {
-    long long nn = (long long)P->n[k] * P->n[k];
-    to_float_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(P->U[k], P->U32[k], nn);
-    IGAFD_CUDA(cudaGetLastError());
-  }
   IGAFD_TRY(igafd_setup_stencil(P, s));
-  IGAFD_TRY(igafd_fd_tc_init(P, s));
+  IGAFD_TRY(igafd_build_prec(P, s));
   igafd_tune_lookup(P);
   IGAFD_CUDA(cudaStreamSynchronize(s));
   return IGAFD_OK;
 }
 
 }  // namespace
+
+// P's setup (Section 4.1) on the patch's own buffers: pencils (span-scaled
+// when scalings are set), generalized eigendecompositions, 1/(D1 (+) D2 (+)
+// D3), FP32 and tensor-core copies of U_k. Synchronises the stream.
+igafd_status igafd_build_prec(igafd_patch *P, cudaStream_t s) {
+  IGAFD_TRY(igafd_setup_pencils_eig(P, s, P->scaled ? P->wK : nullptr, P->scaled ? P->wM : nullptr));
+  for (int k = 0; k < P->dim; ++k) {
+    long long nn = (long long)P->n[k] * P->n[k];
+    to_float_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(P->U[k], P->U32[k], nn);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+  }
+  IGAFD_TRY(igafd_fd_tc_init(P, s));
+  IGAFD_CUDA(cudaStreamSynchronize(s));
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_setup_prec(igafd_patch *P, void *stream) {
+  if (!P) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(P->dev));
+  return igafd_build_prec(P, (cudaStream_t)stream);
+}
+
+extern "C" igafd_status igafd_set_eig_route(igafd_patch *P, int route) {
+  if (!P || (route != 0 && route != 1)) return IGAFD_ERR_ARG;
+  P->eig_route = route;
+  return IGAFD_OK;
+}
 
 extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *stream,
                                           igafd_patch **out) {
@@ -228,6 +251,11 @@ extern "C" igafd_status igafd_patch_query(const igafd_patch *P, igafd_patch_info
   info->stencil_bytes = (long long)P->n_off * P->N * (long long)sizeof(double);
   info->stencil_stages = P->stencil_stages > 0 ? P->stencil_stages : 4;
   info->stencil_rows = P->stencil_rows == 2 ? 2 : 1;
+  for (int k = 0; k < 3; ++k) {
+    info->eig_refined[k] = k < P->dim && P->eig_used[k] == 0 ? 1 : 0;
+    info->eig_check[k][0] = k < P->dim ? P->eig_check[k][0] : 0.0;
+    info->eig_check[k][1] = k < P->dim ? P->eig_check[k][1] : 0.0;
+  }
   return IGAFD_OK;
 }
 

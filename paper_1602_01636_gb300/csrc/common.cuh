@@ -116,6 +116,11 @@ struct igafd_patch {
   FDMixed *mixed;
   double *wK[3], *wM[3];        // span scalings of the pencils (device, null = unscaled)
   int fd_fused;                 // 1: fused tensor-core FD (3 kernels) when n_k <= 128
+  int eig_route;                // 0: FP32 Jacobi + FP64 refinement where n_k <= 128; 1: FP64 Jacobi
+  int eig_used[3];              // route each direction took: 0 refined, 1 FP64 Jacobi
+  double eig_check[3][2];       // refined route's final check (orthogonality, off-diagonal)
+  double *eig_work;             // eigen-setup scratch (kept for re-setups)
+  void *eig_jobs;
   int scaled;
   cudaEvent_t ev[IGAFD_NEV];    // phase-timing events (PCG with timing on)
   // diagnostics
@@ -131,6 +136,7 @@ struct igafd_patch {
 igafd_status igafd_setup_tables(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s);
 // pencils (optionally span-scaled: wK[k], wM[k] device arrays of nel[k]
 // weights, null = unscaled), eigendecompositions, 1/(D1 + D2 + D3)
+igafd_status igafd_build_prec(igafd_patch *P, cudaStream_t s);
 igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const double *const *wK = nullptr,
                                      const double *const *wM = nullptr);
 igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s);

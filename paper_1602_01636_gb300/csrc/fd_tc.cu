@@ -717,17 +717,23 @@ struct FDMixed {
   unsigned char *img[3][2][3];   // [direction][0: U_k^T, 1: U_k][op] B images
 };
 
+// Allocates on the first call; later calls (a re-setup of P) refill the
+// same buffers.
 igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
-  FDMixed *F = (FDMixed *)calloc(1, sizeof(FDMixed));
-  if (!F) return IGAFD_ERR_OOM;
-  P->mixed = F;
+  FDMixed *F = P->mixed;
+  if (!F) {
+    F = (FDMixed *)calloc(1, sizeof(FDMixed));
+    if (!F) return IGAFD_ERR_OOM;
+    P->mixed = F;
+  }
   for (int k = 0; k < P->dim; ++k) {
     const int n = P->n[k];
-    if (cudaMalloc(&F->UT[k], (size_t)n * n * sizeof(float)) != cudaSuccess) {
+    if (!F->UT[k] && cudaMalloc(&F->UT[k], (size_t)n * n * sizeof(float)) != cudaSuccess) {
       cudaGetLastError();
       return IGAFD_ERR_OOM;
     }
     transpose_f32_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(P->U32[k], F->UT[k], n);
+    IGAFD_LAUNCHED(1);
     IGAFD_CUDA(cudaGetLastError());
     // FP16 staging scale: largest power of two with max|U_k| * scale <= 2^14
     std::vector<float> h((size_t)n * n);
@@ -744,7 +750,7 @@ igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
       for (int op = 0; op < 3; ++op) {
         const int bytes = op == OP_TF32 ? 4 : 2;
         const size_t sz = (size_t)nchunks * Np * kKC * bytes;
-        if (cudaMalloc(&F->img[k][dir][op], sz) != cudaSuccess) {
+        if (!F->img[k][dir][op] && cudaMalloc(&F->img[k][dir][op], sz) != cudaSuccess) {
           cudaGetLastError();
           return IGAFD_ERR_OOM;
         }
@@ -753,6 +759,7 @@ igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
         if (op == OP_TF32) b_image_kernel<OP_TF32><<<blocks, 256, 0, s>>>(B, n, Np, 1.0f, F->img[k][dir][op]);
         else if (op == OP_BF16) b_image_kernel<OP_BF16><<<blocks, 256, 0, s>>>(B, n, Np, 1.0f, F->img[k][dir][op]);
         else b_image_kernel<OP_FP16><<<blocks, 256, 0, s>>>(B, n, Np, F->scale16[k], F->img[k][dir][op]);
+        IGAFD_LAUNCHED(1);
         IGAFD_CUDA(cudaGetLastError());
       }
     }

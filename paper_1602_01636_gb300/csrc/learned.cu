@@ -200,10 +200,6 @@ __global__ void exp_weights_kernel(const float *logw, int row0, int nel, double 
   wM[e] = exp((double)logw[2 * (row0 + e) + 1]);
 }
 
-__global__ void to_float_kernel2(const double *a, float *b, long long n) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (float)a[i];
-}
 
 Slab make_slab(const igafd_patch *P) {
   Slab S{};
@@ -342,20 +338,9 @@ extern "C" igafd_status igafd_set_scalings(igafd_patch *P, const float *logw, vo
       row0 += P->nel[k];
     }
     IGAFD_CUDA(cudaGetLastError());
-    IGAFD_TRY(igafd_setup_pencils_eig(P, s, P->wK, P->wM));
     P->scaled = 1;
   } else {
-    IGAFD_TRY(igafd_setup_pencils_eig(P, s, nullptr, nullptr));
     P->scaled = 0;
   }
-  for (int k = 0; k < P->dim; ++k) {
-    const long long nn = (long long)P->n[k] * P->n[k];
-    to_float_kernel2<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(P->U[k], P->U32[k], nn);
-    IGAFD_LAUNCHED(1);
-  }
-  IGAFD_CUDA(cudaGetLastError());
-  igafd_fd_tc_free(P);
-  IGAFD_TRY(igafd_fd_tc_init(P, s));
-  IGAFD_CUDA(cudaStreamSynchronize(s));
-  return IGAFD_OK;
+  return igafd_build_prec(P, s);
 }

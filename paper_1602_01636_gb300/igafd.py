@@ -48,7 +48,8 @@ class PatchInfo(C.Structure):
                 ("nel", C.c_int * 3), ("n_offsets", C.c_int), ("min_detJ", C.c_double),
                 ("q_bound", C.c_double), ("setup_ms", C.c_double), ("eig_ms", C.c_double),
                 ("stencil_bytes", C.c_longlong), ("stencil_stages", C.c_int),
-                ("stencil_rows", C.c_int)]
+                ("stencil_rows", C.c_int), ("eig_refined", C.c_int * 3),
+                ("eig_check", (C.c_double * 2) * 3)]
 
 
 class PCGOpts(C.Structure):
@@ -69,7 +70,7 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_copy_stencil", "igafd_apply_A", "igafd_apply_prec", "igafd_load_rhs_sine",
            "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str",
            "igafd_kernel_launches", "igafd_batch_pcg_solve", "igafd_autotune",
-           "igafd_set_stencil_stages", "igafd_set_stencil_rows", "igafd_set_fd_fused", "igafd_scaling_rows", "igafd_patch_features",
+           "igafd_set_stencil_stages", "igafd_set_stencil_rows", "igafd_setup_prec", "igafd_set_eig_route", "igafd_set_fd_fused", "igafd_scaling_rows", "igafd_patch_features",
            "igafd_patch_sepfit", "igafd_set_scalings", "igafd_mlp_create", "igafd_mlp_destroy",
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step"]
@@ -103,6 +104,8 @@ def lib():
     L.igafd_set_stencil_stages.argtypes = [vp, C.c_int]
     L.igafd_set_fd_fused.argtypes = [vp, C.c_int]
     L.igafd_set_stencil_rows.argtypes = [vp, C.c_int]
+    L.igafd_setup_prec.argtypes = [vp, vp]
+    L.igafd_set_eig_route.argtypes = [vp, C.c_int]
     L.igafd_scaling_rows.argtypes = [vp, C.POINTER(C.c_int)]
     L.igafd_patch_features.argtypes = [vp, vp, vp]
     L.igafd_patch_sepfit.argtypes = [vp, C.c_int, vp, vp]
@@ -291,6 +294,16 @@ class Patch:
     def set_stencil_stages(self, stages):
         _check(lib().igafd_set_stencil_stages(self.h, int(stages)), "set_stencil_stages")
         self.info = self.query()
+
+    def setup_prec(self):
+        """Redo P's setup (pencils, eigendecompositions, FD tables) in place."""
+        _check(lib().igafd_setup_prec(self.h, _stream()), "setup_prec")
+        self.info = self.query()
+
+    def set_eig_route(self, route):
+        """0: FP32 Jacobi + FP64 refinement where n_k <= 128 (default); 1: FP64 Jacobi.
+        Takes effect at the next setup_prec()."""
+        _check(lib().igafd_set_eig_route(self.h, int(route)), "set_eig_route")
 
     def set_stencil_rows(self, rows):
         _check(lib().igafd_set_stencil_rows(self.h, int(rows)), "set_stencil_rows")

@@ -51,7 +51,7 @@ def test_struct_layouts_match_header(libpath):
             if not decl:
                 continue
             for part in decl.split(","):
-                nm = re.findall(r"\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*(\[\d+\])?\s*$", part.strip())
+                nm = re.findall(r"\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*((?:\[\d+\])*)\s*$", part.strip())
                 names.append(nm[0][0])
         assert names == [f[0] for f in py._fields_], (cname, names)
 

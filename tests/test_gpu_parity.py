@@ -58,6 +58,36 @@ def test_eigen_invariants_and_values(case):
         assert np.abs(U.T @ K @ U - np.diag(D)).max() <= 1e-12 * D.max()
 
 
+def test_eigen_routes(case):
+    """Both eigen routes (FP32 Jacobi + FP64 refinement, and FP64 Jacobi) meet
+    the oracle's invariants; a re-setup of P is bitwise reproducible."""
+    prob, disc, S, patch = case
+    assert list(patch.info.eig_refined)[:prob.dim] == [1] * prob.dim
+    fast = [patch.eigen(k) for k in range(prob.dim)]
+    patch.setup_prec()
+    for k in range(prob.dim):
+        D, U = patch.eigen(k)
+        assert np.array_equal(D, fast[k][0]) and np.array_equal(U, fast[k][1])
+    patch.set_eig_route(1)
+    patch.setup_prec()
+    try:
+        assert list(patch.info.eig_refined)[:prob.dim] == [0] * prob.dim
+        for k in range(prob.dim):
+            K, M = disc.pencil(k)
+            D, U = patch.eigen(k)
+            Do, _ = fd.generalized_eig(K, M)
+            assert np.abs(D - Do).max() <= 1e-12 * Do.max()
+            assert np.abs(U.T @ M @ U - np.eye(len(D))).max() <= 1e-12
+            assert np.abs(U.T @ K @ U - np.diag(D)).max() <= 1e-12 * D.max()
+            assert np.abs(D - fast[k][0]).max() <= 1e-12 * D.max()
+    finally:
+        patch.set_eig_route(0)
+        patch.setup_prec()
+    for k in range(prob.dim):
+        D, U = patch.eigen(k)
+        assert np.array_equal(D, fast[k][0]) and np.array_equal(U, fast[k][1])
+
+
 def test_stencil_entries(case):
     prob, disc, S, patch = case
     Sg = patch.stencil().cpu().numpy()
