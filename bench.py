@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="precision sweep: n in {128, 192}, p in {2..5}, every FD dtype")
     ap.add_argument("--train", type=int, default=48)
+    ap.add_argument("--no-refine", action="store_true",
+                    help="--learned: skip the condition-estimate refinement of the labels")
     ap.add_argument("--test", type=int, default=8)
     return ap.parse_args()
 
@@ -597,20 +599,14 @@ def run_learned(args):
         raise RuntimeError("no unfolded draw")
 
     t0 = time.perf_counter()
-    items = []
-    X_parts, T_parts, totals = [], [], {}
-    for i in range(args.train):
-        patch = make(100 + i)
-        b = torch.from_numpy(synth.random_rhs(patch.N, i)).cuda()
-        fit, its = learned.label_patch(patch, b)
-        X_parts.append(patch.features())
-        T_parts.append(fit)
-        for g, v in its.items():
-            totals[g] = totals.get(g, 0) + v
-        patch.close()
-    gamma = min(totals, key=lambda g: (totals[g], g))
-    X = torch.cat(X_parts)
-    T = torch.cat(T_parts) * gamma
+
+    def maker(i):
+        def build_item():
+            patch = make(100 + i)
+            return patch, torch.from_numpy(synth.random_rhs(patch.N, i)).cuda()
+        return build_item
+    X, T, gamma, totals, records = learned.build_dataset([maker(i) for i in range(args.train)],
+                                                         refine=not args.no_refine)
     label_s = time.perf_counter() - t0
     t1 = time.perf_counter()
     net, losses = learned.train(X, T, synth.mlp_init(0), steps=2000)
@@ -655,6 +651,12 @@ def run_learned(args):
             "plain_solve_s_mean": mean(res["plain_s"]), "learned_solve_s_mean": mean(res["learned_s"]),
             "learned_prep_s_mean": mean(res["prep_s"]), "fallbacks": res["fallback"],
             "label_gamma": gamma, "label_total_iterations": {str(k): v for k, v in totals.items()},
+            "label_refinement": {"patches_changed": sum(r["its"][1] < r["its"][0] or r["kappa"][1] < r["kappa"][0]
+                                                        for r in records),
+                                 "kappa_mean": [mean([r["kappa"][0] for r in records]) if records else None,
+                                                mean([r["kappa"][1] for r in records]) if records else None],
+                                 "iterations_total": [sum(r["its"][0] for r in records),
+                                                      sum(r["its"][1] for r in records)]},
             "train_loss": {"first": losses[0], "last": losses[-1]},
             "label_s": label_s, "train_s": train_s}
     print(json.dumps(line), flush=True)

@@ -253,6 +253,27 @@ igafd_status igafd_setup_prec(igafd_patch *patch, void *stream);
  * route each direction took. Other values: IGAFD_ERR_ARG. */
 igafd_status igafd_set_eig_route(igafd_patch *patch, int route);
 
+/* Condition estimate of P^{-1} A from the last PCG solve on this patch (the
+ * CG-Lanczos relation: with the recorded step lengths alpha_j and direction
+ * factors beta_j, the tridiagonal T with T_00 = 1/alpha_0, T_jj = 1/alpha_j
+ * + beta_{j-1}/alpha_{j-1} and T_{j,j+1} = sqrt(beta_j)/alpha_j has as
+ * eigenvalues the Ritz values of P^{-1} A; Section 4's bounds are on the
+ * spread of that spectrum). steps > 0 uses the first `steps` iterations
+ * only (e.g. 30), else all of them (at most 2048 are recorded). Exact for the
+ * FP64 preconditioner with Fletcher-Reeves beta; with the flexible beta of
+ * the mixed-precision preconditioners it is an estimate of an estimate.
+ * Writes lambda_min, lambda_max of T and kappa = lambda_max / lambda_min;
+ * IGAFD_ERR_ARG when no iteration was recorded. Synchronises the device. */
+igafd_status igafd_pcg_condition_estimate(igafd_patch *patch, int steps, double *kappa,
+                                          double *lambda_min, double *lambda_max);
+
+/* Host-only helper of the above: extreme eigenvalues of the CG-Lanczos
+ * tridiagonal of m steps from alpha[0..m) and beta[0..m-1) (bisection on
+ * Sturm counts). IGAFD_ERR_ARG for m < 1, a non-positive alpha or a
+ * negative beta. Needs no GPU. */
+igafd_status igafd_lanczos_extremes(const double *alpha, const double *beta, int m,
+                                    double *lambda_min, double *lambda_max);
+
 /* Time the candidate configurations of the A stencil's pipeline (ring depth
  * 3, 4 or 6 offset groups in flight per CTA; in 3D also one or two rows per
  * compute thread) on this patch and keep the fastest. Results are cached per process by (dim, p, n_1, n_2, n_3, SM

@@ -16,9 +16,11 @@ import numpy as np
 
 
 class PCGResult:
-    def __init__(self, x, iters, converged, relres, true_relres, history):
+    def __init__(self, x, iters, converged, relres, true_relres, history, alphas=(), betas=()):
         self.x, self.iters, self.converged = x, iters, converged
         self.relres, self.true_relres, self.history = relres, true_relres, history
+        # step lengths alpha_k and direction factors beta_k (p_{k+1} = z_{k+1} + beta_k p_k)
+        self.alphas, self.betas = list(alphas), list(betas)
 
 
 def pcg(apply_A, b, apply_P, tol=1e-8, max_iter=1000, x0=None, flexible=False,
@@ -38,9 +40,11 @@ def pcg(apply_A, b, apply_P, tol=1e-8, max_iter=1000, x0=None, flexible=False,
     iters = 0
     limit = fixed_iters if fixed_iters is not None else max_iter
     converged = False
+    alphas, betas = [], []
     for k in range(1, limit + 1):
         q = apply_A(pdir)
         alpha = rho / (pdir @ q)
+        alphas.append(alpha)
         x = x + alpha * pdir
         r = r - alpha * q
         iters = k
@@ -57,8 +61,9 @@ def pcg(apply_A, b, apply_P, tol=1e-8, max_iter=1000, x0=None, flexible=False,
         zn = apply_P(r)
         rho_new = r @ zn
         beta = (r @ (zn - z)) / rho if flexible else rho_new / rho
+        betas.append(beta)
         rho = rho_new
         pdir = zn + beta * pdir
         z = zn
     true_rel = np.linalg.norm(b - apply_A(x)) / bnorm
-    return PCGResult(x, iters, converged, hist[-1], true_rel, hist)
+    return PCGResult(x, iters, converged, hist[-1], true_rel, hist, alphas, betas)

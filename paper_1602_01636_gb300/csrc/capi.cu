@@ -64,7 +64,7 @@ void free_patch(igafd_patch *P) {
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   cudaFree(P->q); cudaFree(P->xt);
   cudaFree(P->partial); cudaFree(P->counter); cudaFree(P->scal); cudaFree(P->err_flag);
-  cudaFree(P->eig_work); cudaFree(P->eig_jobs);
+  cudaFree(P->eig_work); cudaFree(P->eig_jobs); cudaFree(P->coef);
   igafd_fd_tc_free(P);
   for (int i = 0; i < IGAFD_NEV; ++i)
     if (P->ev[i]) cudaEventDestroy(P->ev[i]);
@@ -116,6 +116,7 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
   IGAFD_TRY(alloc(&P->partial, (size_t)IGAFD_PARTIAL_SLOTS * IGAFD_RED_BLOCKS));
   IGAFD_TRY(alloc(&P->counter, (size_t)8));
   IGAFD_TRY(alloc(&P->scal, (size_t)S_COUNT + 1));
+  IGAFD_TRY(alloc(&P->coef, 2 * (size_t)IGAFD_COEF_CAP));
   IGAFD_TRY(alloc(&P->err_flag, (size_t)1));
   if (cudaHostAlloc((void **)&P->host_scal, (S_COUNT + 1) * sizeof(double), cudaHostAllocDefault) !=
       cudaSuccess) {

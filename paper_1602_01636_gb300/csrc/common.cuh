@@ -9,6 +9,7 @@
 #include "../../include/igafd.h"
 
 #define IGAFD_MAXP 7
+#define IGAFD_COEF_CAP 2048   // PCG alpha/beta recorded per solve (Lanczos relation)
 #define IGAFD_MAXDIM 3
 #define IGAFD_NEV 130   // 4 per iteration for 32 iterations + 2
 
@@ -112,6 +113,7 @@ struct igafd_patch {
   double *partial;              // [PARTIAL_SLOTS][MAX_BLOCKS]
   unsigned int *counter;        // last-block counters
   double *scal;                 // [S_COUNT]
+  double *coef;                 // [2 * IGAFD_COEF_CAP]: alpha_k, beta_k of the last solve
   double *host_scal;            // pinned mirror of scal
   FDMixed *mixed;
   double *wK[3], *wM[3];        // span scalings of the pencils (device, null = unscaled)

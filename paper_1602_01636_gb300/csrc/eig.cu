@@ -80,36 +80,43 @@ struct EigJob {
   int *state;
 };
 
-constexpr int kFastMaxN = 128;       // FP32 Jacobi keeps A and V in shared memory
+constexpr int kFastMaxN = 128;       // the FP32 start keeps A and Z in shared memory
+constexpr int kMaxBand = 8;          // p <= 8: the banded solves keep p values in registers
 
 // ---- banded Cholesky, K~ = L^{-1} K L^{-T} (into A), route choice ----
 __global__ void __launch_bounds__(1024) prep_kernel(EigJob *jobs, int *err, int allow_fast) {
   EigJob jb = jobs[blockIdx.x];
   const int n = jb.n, p = jb.p;
   double *M = jb.M, *K = jb.K, *A = jb.A;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   __shared__ int s_fail;
   __shared__ double s_red[32];
-  if (tid == 0) s_fail = 0;
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (tid == 0) {
-      double d = M[(size_t)k * n + k];
-      if (!(d > 0.0)) s_fail = 1;
-      M[(size_t)k * n + k] = d > 0.0 ? sqrt(d) : 1.0;
+  // banded Cholesky M = L L^T (L in the lower band of M) by one warp: O(n p^2)
+  // work, where a block-wide barrier per column would cost more than the
+  // arithmetic
+  if (tid < 32) {
+    int fail = 0;
+    for (int k = 0; k < n; ++k) {
+      if (lane == 0) {
+        const double d = M[(size_t)k * n + k];
+        if (!(d > 0.0)) fail = 1;
+        M[(size_t)k * n + k] = d > 0.0 ? sqrt(d) : 1.0;
+      }
+      __syncwarp();
+      const double rkk = 1.0 / M[(size_t)k * n + k];
+      const int bw = min(n, k + p + 1) - (k + 1);
+      if (lane < bw) M[(size_t)(k + 1 + lane) * n + k] *= rkk;
+      __syncwarp();
+      for (int t = lane; t < bw * bw; t += 32) {
+        const int i = k + 1 + t / bw, j = k + 1 + t % bw;
+        if (j <= i) M[(size_t)i * n + j] -= M[(size_t)i * n + k] * M[(size_t)j * n + k];
+      }
+      __syncwarp();
     }
-    __syncthreads();
-    double lkk = M[(size_t)k * n + k];
-    int hi = min(n, k + p + 1);
-    for (int i = k + 1 + tid; i < hi; i += nt) M[(size_t)i * n + k] /= lkk;
-    __syncthreads();
-    int bw = hi - (k + 1);
-    for (int t = tid; t < bw * bw; t += nt) {
-      int i = k + 1 + t / bw, j = k + 1 + t % bw;
-      if (j <= i) M[(size_t)i * n + j] -= M[(size_t)i * n + k] * M[(size_t)j * n + k];
-    }
-    __syncthreads();
+    fail = __any_sync(0xffffffffu, fail);
+    if (lane == 0) s_fail = fail;
   }
+  __syncthreads();
   if (s_fail) {
     if (tid == 0) {
       atomicExch(err, (int)IGAFD_ERR_NOT_SPD);
@@ -117,21 +124,45 @@ __global__ void __launch_bounds__(1024) prep_kernel(EigJob *jobs, int *err, int 
     }
     return;
   }
-  // X = L^{-1} K (column-parallel forward substitution), into K
+  // 1 / l_ii once (an FP64 division is many FP64-pipe instructions)
+  __shared__ double rdiag[kFastMaxN];
+  double *rd = n <= kFastMaxN ? rdiag : jb.V;     // V is free until the FP64 route
+  for (int i = tid; i < n; i += nt) rd[i] = 1.0 / M[(size_t)i * n + i];
+  __syncthreads();
+  // X = L^{-1} K (column-parallel forward substitution), into K; the last p
+  // results of a column stay in registers (w[d] = X[i-1-d][c])
   for (int c = tid; c < n; c += nt) {
+    double w[kMaxBand];
+#pragma unroll
+    for (int d = 0; d < kMaxBand; ++d) w[d] = 0.0;
     for (int i = 0; i < n; ++i) {
       double acc = K[(size_t)i * n + c];
-      for (int j = max(0, i - p); j < i; ++j) acc -= M[(size_t)i * n + j] * K[(size_t)j * n + c];
-      K[(size_t)i * n + c] = acc / M[(size_t)i * n + i];
+#pragma unroll
+      for (int d = kMaxBand - 1; d >= 0; --d)
+        if (d < p && i - 1 - d >= 0) acc -= M[(size_t)i * n + i - 1 - d] * w[d];
+      const double x = acc * rd[i];
+      K[(size_t)i * n + c] = x;
+#pragma unroll
+      for (int d = kMaxBand - 1; d > 0; --d) w[d] = w[d - 1];
+      w[0] = x;
     }
   }
   __syncthreads();
-  // K~ = X L^{-T} (row-parallel), into A
+  // K~ = X L^{-T} (row-parallel), into A; w[d] = A[r][j-1-d]
   for (int r = tid; r < n; r += nt) {
+    double w[kMaxBand];
+#pragma unroll
+    for (int d = 0; d < kMaxBand; ++d) w[d] = 0.0;
     for (int j = 0; j < n; ++j) {
       double acc = K[(size_t)r * n + j];
-      for (int l = max(0, j - p); l < j; ++l) acc -= M[(size_t)j * n + l] * A[(size_t)r * n + l];
-      A[(size_t)r * n + j] = acc / M[(size_t)j * n + j];
+#pragma unroll
+      for (int d = kMaxBand - 1; d >= 0; --d)
+        if (d < p && j - 1 - d >= 0) acc -= M[(size_t)j * n + j - 1 - d] * w[d];
+      const double x = acc * rd[j];
+      A[(size_t)r * n + j] = x;
+#pragma unroll
+      for (int d = kMaxBand - 1; d > 0; --d) w[d] = w[d - 1];
+      w[0] = x;
     }
   }
   __syncthreads();
@@ -429,29 +460,31 @@ struct GemmBatch {
   GemmJob j[6];
 };
 
-// 16 x 16 output tile per CTA, K in panels of 64 (fewer barriers and more
-// loads in flight than 16-wide panels; these GEMMs are latency-bound).
-__global__ void __launch_bounds__(256) gemm64_kernel(GemmBatch b) {
+// 8 x 8 output tile per CTA (64 threads), K in panels of 64: at n = 128 a
+// product is 256 CTAs, spread over all SMs (one SM's FP64 rate is low, so
+// the products want as many SMs as possible).
+constexpr int kGT = 8;
+__global__ void __launch_bounds__(64) gemm64_kernel(GemmBatch b) {
   const GemmJob g = b.j[blockIdx.y];
   if (g.n == 0 || *g.state != 0) return;
-  const int n = g.n, tpr = (n + 15) / 16;
+  const int n = g.n, tpr = (n + kGT - 1) / kGT;
   if ((int)blockIdx.x >= tpr * tpr) return;
   const int ti = blockIdx.x / tpr, tj = blockIdx.x % tpr;
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int ty = threadIdx.x / kGT, tx = threadIdx.x % kGT;
   constexpr int KP = 64;
-  __shared__ double As[16][KP + 1], Bs[KP][17];
-  const int row = ti * 16 + ty, col = tj * 16 + tx;
+  __shared__ double As[kGT][KP + 1], Bs[KP][kGT + 1];
+  const int row = ti * kGT + ty, col = tj * kGT + tx;
   double acc = 0.0;
   for (int k0 = 0; k0 < n; k0 += KP) {
-    for (int t = threadIdx.x; t < 16 * KP; t += 256) {
+    for (int t = threadIdx.x; t < kGT * KP; t += kGT * kGT) {
       if (g.transA) {
-        const int kk = t / 16, r = t % 16, ra = ti * 16 + r, ka = k0 + kk;   // coalesced along r
+        const int kk = t / kGT, r = t % kGT, ra = ti * kGT + r, ka = k0 + kk;
         As[r][kk] = (ra < n && ka < n) ? g.A[(size_t)ka * n + ra] : 0.0;
       } else {
-        const int r = t / KP, kk = t % KP, ra = ti * 16 + r, ka = k0 + kk;   // coalesced along k
+        const int r = t / KP, kk = t % KP, ra = ti * kGT + r, ka = k0 + kk;
         As[r][kk] = (ra < n && ka < n) ? g.A[(size_t)ra * n + ka] : 0.0;
       }
-      const int kk = t / 16, c = t % 16, kb = k0 + kk, cb = tj * 16 + c;
+      const int kk = t / kGT, c = t % kGT, kb = k0 + kk, cb = tj * kGT + c;
       double bv = 0.0;
       if (kb < n && cb < n) {
         if (!g.G) {
@@ -758,11 +791,25 @@ __global__ void __launch_bounds__(1024) finish_kernel(EigJob *jobs, int parity) 
   const double *Lam = st == 0 ? jb.S : jb.A;
   const double *M = jb.M;
   double *K = jb.K, *U = jb.U;
+  __shared__ double rdiag[kFastMaxN];
+  double *rd = n <= kFastMaxN ? rdiag : jb.E;     // E is free at this point
+  for (int i = tid; i < n; i += nt) rd[i] = 1.0 / M[(size_t)i * n + i];
+  __syncthreads();
+  // U = L^{-T} V (column-parallel backward substitution); w[d] = U[i+1+d][c]
   for (int c = tid; c < n; c += nt) {
+    double w[kMaxBand];
+#pragma unroll
+    for (int d = 0; d < kMaxBand; ++d) w[d] = 0.0;
     for (int i = n - 1; i >= 0; --i) {
       double acc = Vsrc[(size_t)i * n + c];
-      for (int j = i + 1; j <= min(n - 1, i + jb.p); ++j) acc -= M[(size_t)j * n + i] * K[(size_t)j * n + c];
-      K[(size_t)i * n + c] = acc / M[(size_t)i * n + i];
+#pragma unroll
+      for (int d = 0; d < kMaxBand; ++d)
+        if (d < jb.p && i + 1 + d < n) acc -= M[(size_t)(i + 1 + d) * n + i] * w[d];
+      const double x = acc * rd[i];
+      K[(size_t)i * n + c] = x;
+#pragma unroll
+      for (int d = kMaxBand - 1; d > 0; --d) w[d] = w[d - 1];
+      w[0] = x;
     }
   }
   __syncthreads();
@@ -871,7 +918,7 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
     IGAFD_LAUNCHED(1);
     int tiles = 0;
     for (int k = 0; k < dim; ++k) {
-      const int t = (P->n[k] + 15) / 16;
+      const int t = (P->n[k] + kGT - 1) / kGT;
       tiles = t * t > tiles ? t * t : tiles;
     }
     auto products = [&](bool with_s) -> igafd_status {
@@ -884,10 +931,10 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
         b1.j[2 * k + 1] = gemm_job(j.n, 0, j.A, X, nullptr, j.AX, j.state);
         b2.j[k] = gemm_job(j.n, 1, X, j.AX, nullptr, j.S, j.state);
       }
-      gemm64_kernel<<<dim3(tiles, 2 * dim), 256, 0, s>>>(b1);
+      gemm64_kernel<<<dim3(tiles, 2 * dim), kGT * kGT, 0, s>>>(b1);
       IGAFD_LAUNCHED(1);
       if (with_s) {
-        gemm64_kernel<<<dim3(tiles, dim), 256, 0, s>>>(b2);
+        gemm64_kernel<<<dim3(tiles, dim), kGT * kGT, 0, s>>>(b2);
         IGAFD_LAUNCHED(1);
       }
       IGAFD_CUDA(cudaGetLastError());
@@ -905,7 +952,7 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
         b3.j[k] = gemm_job(j.n, 0, X, nullptr, X, Xnext, j.state);
         b3.j[k].G = j.G; b3.j[k].S = j.S; b3.j[k].lam = j.E; b3.j[k].dl = j.sc + 1;
       }
-      gemm64_kernel<<<dim3(tiles, dim), 256, 0, s>>>(b3);
+      gemm64_kernel<<<dim3(tiles, dim), kGT * kGT, 0, s>>>(b3);
       IGAFD_LAUNCHED(1);
       parity ^= 1;
     }

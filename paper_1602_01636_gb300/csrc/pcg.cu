@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(256) update_xr_kernel(double *__restrict__ x, 
                                                         const double *__restrict__ q,
                                                         const double *__restrict__ z, long long N,
                                                         double *scal, double *partial,
-                                                        unsigned *counter, int flexible) {
+                                                        unsigned *counter, int flexible,
+                                                        double *coef) {
   if (scal[S_DONE] != 0.0) return;
   const double alpha = scal[S_ALPHA];
   double rr = 0.0, rz = 0.0;
@@ -71,6 +72,8 @@ __global__ void __launch_bounds__(256) update_xr_kernel(double *__restrict__ x, 
     *counter = 0u;
     scal[S_RR] = trr;
     scal[S_RZOLD] = trz;
+    const int k = (int)scal[S_ITER];
+    if (k < IGAFD_COEF_CAP) coef[2 * k] = scal[S_ALPHA];     // alpha_k (Lanczos relation)
     scal[S_ITER] += 1.0;
     if (!isfinite(trr)) {
       scal[S_STATUS] = (double)IGAFD_ERR_BREAKDOWN;
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(256) dot_rz_kernel(const double *__restrict__ 
                                                      const double *__restrict__ z, long long N,
                                                      double *scal, double *partial,
                                                      unsigned *counter, int init, int flexible,
-                                                     int skip_done) {
+                                                     int skip_done, double *coef) {
   if (skip_done && scal[S_DONE] != 0.0) return;
   double rz = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -111,6 +114,8 @@ __global__ void __launch_bounds__(256) dot_rz_kernel(const double *__restrict__ 
     } else {
       double rho = scal[S_RHO];
       scal[S_BETA] = flexible ? (t - scal[S_RZOLD]) / rho : t / rho;
+      const int k = (int)scal[S_ITER] - 1;                   // beta_k, after step k
+      if (k >= 0 && k < IGAFD_COEF_CAP) coef[2 * k + 1] = scal[S_BETA];
     }
     scal[S_RHO] = t;
   }
@@ -224,11 +229,11 @@ static igafd_status enqueue_iteration(igafd_patch *P, igafd_dtype dt, int flex, 
   const long long N = P->N;
   IGAFD_TRY(igafd_stencil_launch(P, P->pv, P->q, nullptr, 1, 1, s, 0, timed ? P->tstat : nullptr));
   update_xr_kernel<<<G, B, 0, s>>>(P->xs, P->r, P->pv, P->q, P->z, N, scal, P->partial,
-                                   P->counter, flex);
+                                   P->counter, flex, P->coef);
   IGAFD_LAUNCHED(1);
   if (true_every > 0) IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, true_every));
   IGAFD_TRY(fd_apply(P, dt, P->r, P->z, s, done));
-  dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, flex, 1);
+  dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, flex, 1, P->coef);
   IGAFD_LAUNCHED(1);
   update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 1);
   IGAFD_LAUNCHED(1);
@@ -350,7 +355,7 @@ static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, cons
     return IGAFD_OK;
   }
   IGAFD_TRY(fd_apply(P, o.prec_dtype, P->r, P->z, s, nullptr));
-  dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 1, S.flex, 0);
+  dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 1, S.flex, 0, P->coef);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaMemcpyAsync(P->pv, P->z, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   IGAFD_CUDA(cudaGetLastError());
@@ -372,14 +377,14 @@ static igafd_status run_chunk_direct(igafd_patch *P, cudaStream_t s, SolveState 
     IGAFD_TRY(igafd_stencil_launch(P, P->pv, P->q, nullptr, 1, 1, s));
     if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 1], s));
     update_xr_kernel<<<G, B, 0, s>>>(P->xs, P->r, P->pv, P->q, P->z, N, scal, P->partial,
-                                     P->counter, S.flex);
+                                     P->counter, S.flex, P->coef);
     IGAFD_LAUNCHED(1);
     if (S.o.true_every > 0)
       IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, S.o.true_every));
     if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 2], s));
     IGAFD_TRY(fd_apply(P, S.o.prec_dtype, P->r, P->z, s, P->scal + S_DONE));
     if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 3], s));
-    dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 1);
+    dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 1, P->coef);
     IGAFD_LAUNCHED(1);
     update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 1);
     IGAFD_LAUNCHED(1);
@@ -428,7 +433,7 @@ static igafd_status solve_after_chunk(igafd_patch *P, cudaStream_t s, SolveState
     set_scalar_kernel<<<1, 32, 0, s>>>(scal, S_DONE, 0.0);
     IGAFD_LAUNCHED(1);
     IGAFD_TRY(fd_apply(P, S.o.prec_dtype, P->r, P->z, s, nullptr));
-    dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 0);
+    dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 0, P->coef);
     IGAFD_LAUNCHED(1);
     update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 0);
     IGAFD_LAUNCHED(1);
@@ -587,4 +592,67 @@ extern "C" igafd_status igafd_batch_pcg_solve(igafd_patch *const *patches, int c
     if (e != IGAFD_OK && worst == IGAFD_OK) worst = e;
   }
   return worst;
+}
+
+// ---- condition estimate from the CG-Lanczos relation (host arithmetic) ----
+// Sturm count of the tridiagonal T (diagonal d, squared off-diagonal e2):
+// the number of eigenvalues below x, from the pivots of T - x I = L D L^T.
+static int sturm_count(const std::vector<double> &d, const std::vector<double> &e2, double x) {
+  const int m = (int)d.size();
+  int c = 0;
+  double q = d[0] - x;
+  for (int j = 0;; ++j) {
+    if (fabs(q) < 1e-300) q = -1e-300;
+    c += q < 0.0;
+    if (j == m - 1) break;
+    q = (d[j + 1] - x) - e2[j] / q;
+  }
+  return c;
+}
+
+static double tridiag_eig(const std::vector<double> &d, const std::vector<double> &e2, int idx,
+                          double lo, double hi) {
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(hi - lo > 1e-15 * fmax(fabs(lo), fabs(hi)))) break;
+    if (sturm_count(d, e2, mid) > idx) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+extern "C" igafd_status igafd_lanczos_extremes(const double *alpha, const double *beta, int m,
+                                               double *lmin, double *lmax) {
+  if (!alpha || m < 1 || (m > 1 && !beta) || !lmin || !lmax) return IGAFD_ERR_ARG;
+  std::vector<double> d(m), e2(m > 1 ? m - 1 : 0);
+  for (int j = 0; j < m; ++j) {
+    if (!(alpha[j] > 0.0) || !std::isfinite(alpha[j])) return IGAFD_ERR_ARG;
+    if (j > 0 && (!(beta[j - 1] >= 0.0) || !std::isfinite(beta[j - 1]))) return IGAFD_ERR_ARG;
+    d[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+    if (j < m - 1) e2[j] = beta[j] / (alpha[j] * alpha[j]);
+  }
+  double lo = 1e308, hi = -1e308;
+  for (int j = 0; j < m; ++j) {
+    const double r = (j > 0 ? sqrt(e2[j - 1]) : 0.0) + (j < m - 1 ? sqrt(e2[j]) : 0.0);
+    lo = fmin(lo, d[j] - r);
+    hi = fmax(hi, d[j] + r);
+  }
+  *lmin = tridiag_eig(d, e2, 0, lo, hi);
+  *lmax = tridiag_eig(d, e2, m - 1, lo, hi);
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_pcg_condition_estimate(igafd_patch *P, int steps, double *kappa,
+                                                     double *lmin, double *lmax) {
+  if (!P || !kappa || !lmin || !lmax || !P->host_scal) return IGAFD_ERR_ARG;
+  int m = (int)P->host_scal[S_ITER];
+  if (steps > 0 && steps < m) m = steps;
+  if (m > IGAFD_COEF_CAP) m = IGAFD_COEF_CAP;
+  if (m < 1) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(P->dev));
+  std::vector<double> c(2 * (size_t)m), a(m), b(m);
+  IGAFD_CUDA(cudaMemcpy(c.data(), P->coef, c.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int j = 0; j < m; ++j) { a[j] = c[2 * j]; b[j] = c[2 * j + 1]; }
+  IGAFD_TRY(igafd_lanczos_extremes(a.data(), b.data(), m, lmin, lmax));
+  *kappa = *lmax / *lmin;
+  return IGAFD_OK;
 }

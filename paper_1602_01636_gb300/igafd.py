@@ -70,7 +70,8 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_copy_stencil", "igafd_apply_A", "igafd_apply_prec", "igafd_load_rhs_sine",
            "igafd_pcg_solve", "igafd_pcg_default_opts", "igafd_status_str",
            "igafd_kernel_launches", "igafd_batch_pcg_solve", "igafd_autotune",
-           "igafd_set_stencil_stages", "igafd_set_stencil_rows", "igafd_setup_prec", "igafd_set_eig_route", "igafd_set_fd_fused", "igafd_scaling_rows", "igafd_patch_features",
+           "igafd_set_stencil_stages", "igafd_set_stencil_rows", "igafd_setup_prec", "igafd_set_eig_route",
+           "igafd_pcg_condition_estimate", "igafd_lanczos_extremes", "igafd_set_fd_fused", "igafd_scaling_rows", "igafd_patch_features",
            "igafd_patch_sepfit", "igafd_set_scalings", "igafd_mlp_create", "igafd_mlp_destroy",
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step"]
@@ -105,6 +106,9 @@ def lib():
     L.igafd_set_fd_fused.argtypes = [vp, C.c_int]
     L.igafd_set_stencil_rows.argtypes = [vp, C.c_int]
     L.igafd_setup_prec.argtypes = [vp, vp]
+    dp = C.POINTER(C.c_double)
+    L.igafd_pcg_condition_estimate.argtypes = [vp, C.c_int, dp, dp, dp]
+    L.igafd_lanczos_extremes.argtypes = [dp, dp, C.c_int, dp, dp]
     L.igafd_set_eig_route.argtypes = [vp, C.c_int]
     L.igafd_scaling_rows.argtypes = [vp, C.POINTER(C.c_int)]
     L.igafd_patch_features.argtypes = [vp, vp, vp]
@@ -132,6 +136,19 @@ def lib():
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
+
+
+def lanczos_extremes(alpha, beta):
+    """Extreme eigenvalues of the CG-Lanczos tridiagonal of len(alpha) steps
+    (host arithmetic in the library; no GPU needed)."""
+    import numpy as _np
+    a = _np.ascontiguousarray(alpha, dtype=_np.float64)
+    b = _np.ascontiguousarray(beta if len(beta) else [0.0], dtype=_np.float64)
+    lo, hi = C.c_double(), C.c_double()
+    dp = C.POINTER(C.c_double)
+    _check(lib().igafd_lanczos_extremes(a.ctypes.data_as(dp), b.ctypes.data_as(dp), len(a),
+                                        C.byref(lo), C.byref(hi)), "lanczos_extremes")
+    return lo.value, hi.value
 
 
 def kernel_launches():
@@ -299,6 +316,14 @@ class Patch:
         """Redo P's setup (pencils, eigendecompositions, FD tables) in place."""
         _check(lib().igafd_setup_prec(self.h, _stream()), "setup_prec")
         self.info = self.query()
+
+    def condition_estimate(self, steps=0):
+        """(kappa, lambda_min, lambda_max) of P^-1 A from the last solve's CG-Lanczos
+        tridiagonal (its first `steps` iterations when steps > 0)."""
+        k, lo, hi = C.c_double(), C.c_double(), C.c_double()
+        _check(lib().igafd_pcg_condition_estimate(self.h, int(steps), C.byref(k), C.byref(lo),
+                                                  C.byref(hi)), "condition_estimate")
+        return k.value, lo.value, hi.value
 
     def set_eig_route(self, route):
         """0: FP32 Jacobi + FP64 refinement where n_k <= 128 (default); 1: FP64 Jacobi.

@@ -8,10 +8,14 @@ Labels are chosen by the method itself: the separable log-fit of Q's
 diagonal on each training patch, scaled by one factor gamma in
 {0, 0.5, 0.75, 1, 1.25} (gamma = 0 is the paper's unscaled P) chosen for the
 whole training set by minimising the total iterations of PCG with the FP64
-fast-diagonalization preconditioner. The network learns those labels from
-the six per-span features of Q, so at solve time the scalings come from the
-features alone. The unscaled preconditioner remains the fallback when the
-scaled run breaks down or exceeds its iteration budget.
+fast-diagonalization preconditioner; then, per patch, a coordinate search
+over one multiplier per direction minimises the condition estimate of
+P^-1 A from 30 PCG steps (the CG-Lanczos tridiagonal), and the refined label
+is kept when full PCG needs no more iterations than before. The network
+learns the labels from the six per-span features of Q, so at solve time the
+scalings come from the features alone. The unscaled preconditioner remains
+the fallback when the scaled run breaks down or exceeds its iteration
+budget.
 """
 from __future__ import annotations
 
@@ -37,19 +41,94 @@ def label_patch(patch, b, tol=1e-8, max_iter=1000, gammas=GAMMAS):
     return fit, its
 
 
-def build_dataset(items):
-    """items: iterable of (patch, b). Returns (X [rows][6], T [rows][2],
-    gamma, {gamma: total iterations over the set})."""
+def kappa_estimate(patch, b, steps=30, dtype="fp32"):
+    """Condition estimate of P^-1 A with the patch's current scalings from
+    `steps` PCG steps (Fletcher-Reeves beta, so the CG-Lanczos relation holds;
+    the FP32 fast diagonalization is P to ~1e-6, plenty for an estimate)."""
+    _, info = patch.pcg(b, tol=1e-30, max_iter=steps, dtype=dtype, flexible=False,
+                        true_every=0, raise_on_error=False)
+    return patch.condition_estimate(steps)[0]
+
+
+def direction_rows(patch):
+    """Row ranges of the scaling rows of each direction."""
+    out, r0 = [], 0
+    for k in range(patch.dim):
+        nel = patch.info.nel[k]
+        out.append((r0, r0 + nel))
+        r0 += nel
+    return out
+
+
+def refine_label(patch, b, label, factors=(0.5, 0.75, 1.25, 1.5), steps=30, tol=1e-8,
+                 max_iter=1000):
+    """Coordinate search over one multiplier c_k per direction of the label's
+    log-scalings (rows of direction k times c_k), each step keeping the
+    multiplier that lowers the 30-step condition estimate; the refined label
+    is kept only if full FP64-preconditioned PCG needs no more iterations.
+    Returns (label, {"kappa": (start, refined), "its": (start, refined)})."""
+    rows = direction_rows(patch)
+
+    def scaled(c):
+        L = label.clone()
+        for (r0, r1), ck in zip(rows, c):
+            L[r0:r1] *= ck
+        return L
+
+    def kappa(c):
+        patch.set_scalings(scaled(c))
+        return kappa_estimate(patch, b, steps)
+
+    c = [1.0] * patch.dim
+    k0 = best = kappa(c)
+    for k in range(patch.dim):
+        ck = c[k]
+        for f in factors:
+            trial = list(c)
+            trial[k] = ck * f
+            kt = kappa(trial)
+            if kt < best:
+                best, c = kt, trial
+
+    def iterations(L):
+        patch.set_scalings(L)
+        _, info = patch.pcg(b, tol=tol, max_iter=max_iter, dtype="fp64", raise_on_error=False)
+        return info.iterations if info.status == 0 else 10 ** 9
+
+    it0 = iterations(label)
+    refined = scaled(c)
+    it1 = iterations(refined) if c != [1.0] * patch.dim else it0
+    patch.set_scalings(None)
+    if it1 <= it0:
+        return refined, {"kappa": (k0, best), "its": (it0, it1)}
+    return label, {"kappa": (k0, best), "its": (it0, it0)}
+
+
+def build_dataset(makers, refine=True):
+    """makers: list of callables, each returning a fresh (patch, b) of one
+    training problem (patches are closed after use, so a large set never
+    holds all stencils at once; the refinement pass builds them again).
+    Returns (X [rows][6], T [rows][2], gamma, {gamma: total iterations over
+    the set}, per-patch refinement records)."""
     import torch
     Xs, fits, totals = [], [], {}
-    for patch, b in items:
+    for make in makers:
+        patch, b = make()
         fit, its = label_patch(patch, b)
         Xs.append(patch.features())
         fits.append(fit)
         for g, v in its.items():
             totals[g] = totals.get(g, 0) + v
+        patch.close()
     gamma = min(totals, key=lambda g: (totals[g], g))
-    return torch.cat(Xs), torch.cat(fits) * gamma, gamma, totals
+    labels, records = [f * gamma for f in fits], []
+    if refine and gamma != 0.0:
+        for i, make in enumerate(makers):
+            patch, b = make()
+            labels[i], rec = refine_label(patch, b, labels[i])
+            records.append(rec)
+            patch.close()
+    return torch.cat(Xs), torch.cat(labels), gamma, totals, records
 
 
 def train(X, T, init_params, steps=1500, lr=3e-3, lr_final=3e-4):

@@ -97,14 +97,16 @@ def test_trained_network_reduces_iterations_on_held_out_patches(torch):
     span scalings need fewer iterations than the paper's unscaled
     preconditioner on held-out patches."""
     from paper_1602_01636_gb300 import learned
-    items, keep = [], []
-    for seed in range(16):
-        patch = make_patch(synth.learned_workload_problem(100 + seed, n=14, p=2))
-        items.append((patch, to_dev(synth.random_rhs(patch.N, seed))))
-    X, T, gamma, totals = learned.build_dataset(items)
-    for patch, _ in items:
-        patch.close()
+    def maker(seed):
+        def make():
+            patch = make_patch(synth.learned_workload_problem(100 + seed, n=14, p=2))
+            return patch, to_dev(synth.random_rhs(patch.N, seed))
+        return make
+    X, T, gamma, totals, records = learned.build_dataset([maker(s) for s in range(16)])
     assert totals[gamma] <= totals[0.0]          # the labels beat the unscaled P
+    # the condition-estimate refinement never costs iterations on its patch
+    assert all(r["its"][1] <= r["its"][0] and r["kappa"][1] <= r["kappa"][0] for r in records)
+    print("refinement records", records)
     net, losses = learned.train(X, T, synth.mlp_init(0), steps=1500)
     assert losses[-1] < 0.5 * losses[0]
     plain, scaled = [], []
