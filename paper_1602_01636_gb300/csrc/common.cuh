@@ -79,6 +79,7 @@ struct igafd_patch {
   int n_off;
   double kappa;
   Dir1D dir[3];
+  int twin[3];                  // smallest direction with the same knot vector (same 1D pencils)
   double *ctrl;                 // [dim][gm_d]..[gm_1]
   double *kctrl;                // coefficient control values [km_d]..[km_1] or null
   // generalized eigenpairs: U[k][i*n + j], D[k][j]; inv_lam[N] = 1/(D1+D2+D3)

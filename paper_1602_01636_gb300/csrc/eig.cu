@@ -7,25 +7,32 @@
 //   ascending, each eigenvector signed so that its largest-magnitude entry is
 //   positive.
 //
-// The symmetric eigenproblem K~ = U~ D U~^T has two routes:
-//   fast (n <= 128): an FP32 start in one CTA per direction, all in shared
-//     memory -- Householder tridiagonalisation T = Q^T K~ Q, every
-//     eigenvalue of T by bisection on Sturm counts (one thread each),
-//     eigenvectors of T by inverse iteration (3 steps; members of a cluster
-//     of eigenvalues closer than 1e-5 ||T|| are solved in turn and
-//     orthogonalised against each other), back-transformed by Q -- then FP64
-//     iterative refinement of the eigenvector matrix (Ogita and Aishima,
-//     "Iterative refinement for symmetric eigenvalue decomposition", 2018):
-//     with R = I - X^T X and S = X^T K~ X, lambda_i = s_ii / (1 - r_ii) and
-//     X <- X + X E, E_ii = r_ii / 2, E_ij = (s_ij + lambda_j r_ij) /
-//     (lambda_j - lambda_i) for separated pairs and r_ij / 2 within a
-//     cluster. Pairs closer than 1e-5 ||K~||_inf stay clusters throughout and
-//     are diagonalised at the end by exact 2x2 rotations. The products are
-//     dense FP64 GEMMs spread over many CTAs (GB300's FP64 rate per SM is
-//     low). The result is checked (max |X^T X - I| and max |offdiag S| /
-//     max |diag S| <= 1e-12); a direction that fails takes the other route.
-//   FP64 (n > 128, or fallback): cyclic two-sided Jacobi in FP64 with a
-//     round-robin (tournament) ordering, n/2 disjoint rotations in parallel.
+// Two routes:
+//   fast (n <= 128): an FP32 start in one CTA per pencil, all in shared
+//     memory -- banded Cholesky M = L L^T, K~ = L^{-1} K L^{-T}, Householder
+//     tridiagonalisation T = Q^T K~ Q, every eigenvalue of T by bisection on
+//     Sturm counts, eigenvectors of T by inverse iteration (3 steps; members of
+//     a cluster of eigenvalues closer than 1e-5 ||T|| are solved in turn and
+//     orthogonalised against each other), back-transformed by Q and by L^{-T}
+//     into approximate eigenvectors X of the pencil -- then FP64 iterative
+//     refinement of X on the pencil itself (Ogita and Aishima, "Iterative
+//     refinement for symmetric eigenvalue decomposition", 2018, in the
+//     M-inner product): with R = I - X^T M X and S = X^T K X, lambda_i =
+//     s_ii / (1 - r_ii) and X <- X + X E, E_ii = r_ii / 2, E_ij = (s_ij +
+//     lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs and r_ij / 2
+//     within a cluster. (With Z = L^T X this is the refinement of the
+//     eigenvectors Z of K~, so nothing of K~ is needed in FP64: M X and K X
+//     are banded products.) Pairs closer than 1e-5 ||K~||_inf stay clusters
+//     throughout and are diagonalised at the end by exact 2x2 rotations. The
+//     dense products are FP64 GEMMs spread over many CTAs and the row
+//     reductions use one warp per row (GB300's FP64 rate per SM is low). The
+//     result is checked (max |X^T M X - I| and max |offdiag S| / max |diag S|
+//     <= 1e-12); a pencil that fails takes the other route.
+//   FP64 (n > 128, or fallback): banded Cholesky and K~ in FP64, cyclic
+//     two-sided Jacobi with a round-robin (tournament) ordering, n/2 disjoint
+//     rotations in parallel, U = L^{-T} U~.
+// Directions with the same knot vector have the same pencils; their
+// eigenpairs are computed once and copied.
 #include "common.cuh"
 
 #include <vector>
@@ -63,29 +70,34 @@ __global__ void pencil_kernel(Dir1D D, int p, double *K, double *M, const double
   K[(size_t)i * n + j] = k;
 }
 
-// One block per direction. Work arrays (global, n*n each): M (becomes L),
-// K (becomes X = L^{-1} K, later scratch), A (K~, kept), V (FP64 Jacobi
-// rotations), X/Xn (refined eigenvectors, ping-pong), G (X^T X), AX, S
-// (X^T K~ X), E (correction). U, D: outputs. sc: per-direction scalars
-// [0] = infinity norm of K~, [1] = cluster bound delta, [2] = orthogonality
-// error, [3] = relative off-diagonal of S. state: 0 = refined eigenpairs
-// accepted, 1 = take the FP64 Jacobi route.
+// One block per pencil. Work arrays (global, n*n each): M (the pencil's
+// mass matrix; becomes L on the FP64 route), K (stiffness; X = L^{-1} K on
+// the FP64 route), A (K~ on the FP64 route; K X on the fast one), V (FP64
+// Jacobi rotations), X/Xn (refined eigenvectors, ping-pong), G (X^T M X), AX
+// (M X), S (X^T K X), E (lambda of the refinement). U, D: outputs. sc:
+// per-pencil scalars [0] = infinity norm of K~, [1] = cluster bound delta,
+// [2] = orthogonality error, [3] = relative off-diagonal of S, [4] = route
+// state (int: 0 = refined eigenpairs accepted, 1 = FP64 Jacobi route, 2 =
+// failed), [5] = arrival counter of the row reductions (unsigned), [6..10] =
+// bit patterns of non-negative maxima gathered by atomicMax.
 struct EigJob {
   int n, p;
   double *M, *K, *A, *V;
   double *X, *Xn, *G, *AX, *S, *E;
-  double *W;                          // 2 n^2: FP32 inverse-iteration scratch
+  double *W;                          // 2 n^2: spare
   double *U, *D;
   double *sc;
   int *state;
 };
+constexpr int kScal = 16;             // doubles of sc per pencil
 
 constexpr int kFastMaxN = 128;       // the FP32 start keeps A and Z in shared memory
 constexpr int kMaxBand = 8;          // p <= 8: the banded solves keep p values in registers
 
-// ---- banded Cholesky, K~ = L^{-1} K L^{-T} (into A), route choice ----
-__global__ void __launch_bounds__(1024) prep_kernel(EigJob *jobs, int *err, int allow_fast) {
+// ---- FP64 route: banded Cholesky, K~ = L^{-1} K L^{-T} (into A) ----
+__global__ void __launch_bounds__(1024) prep_kernel(EigJob *jobs, int *err) {
   EigJob jb = jobs[blockIdx.x];
+  if (*jb.state != 1) return;
   const int n = jb.n, p = jb.p;
   double *M = jb.M, *K = jb.K, *A = jb.A;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
@@ -189,8 +201,6 @@ __global__ void __launch_bounds__(1024) prep_kernel(EigJob *jobs, int *err, int 
     double m = 0.0;
     for (int w = 0; w < nt / 32; ++w) m = fmax(m, s_red[w]);
     jb.sc[0] = m;
-    jb.sc[1] = jb.sc[2] = jb.sc[3] = 0.0;
-    *jb.state = (allow_fast && n <= kFastMaxN) ? 0 : 1;
   }
 }
 
@@ -212,28 +222,137 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 constexpr int kInvBatch = 32;        // clusters solved at once by inverse iteration
 constexpr float kInvCluster = 1e-5f; // eigenvalues of T closer than this x ||T|| form a cluster
 
-// shared memory of tri32_kernel (floats): A and Z (n x (n+1) each), eight
-// vectors of n, and the pivot rows of kInvBatch concurrent solves
+// shared memory of tri32_kernel (floats): A and Z (n x (n+1) each), nine
+// vectors of n, the pivot rows of kInvBatch concurrent solves and the band of
+// the Cholesky factor L (n x kMaxBand)
 __host__ __device__ constexpr size_t tri32_smem_floats(int n) {
-  return 2 * (size_t)n * (n + 1) + 8 * (size_t)n + 3 * (size_t)n * kInvBatch;
+  return 2 * (size_t)n * (n + 1) + 9 * (size_t)n + 3 * (size_t)n * kInvBatch +
+         (size_t)n * kMaxBand;
 }
 
-__global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs) {
+// Fast route, step 1 (one CTA per pencil): FP32 approximate eigenvectors X of
+// the pencil (K, M) into jb.X, ||K~||_inf into sc[0], route state 0; state 1
+// (FP64 route) when the fast route does not apply or the FP32 Cholesky of M
+// fails.
+__global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs, int allow_fast) {
   EigJob jb = jobs[blockIdx.x];
-  if (*jb.state != 0) return;
-  const int n = jb.n, ld = n + 1;
+  const int n = jb.n, p = jb.p, ld = n + 1;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0)
+    for (int i = 1; i < kScal; ++i) jb.sc[i] = 0.0;   // also zeroes state, counter, maxima
+  if (!allow_fast || n > kFastMaxN || p >= kMaxBand) {
+    if (tid == 0) *jb.state = 1;
+    return;
+  }
   extern __shared__ float t32[];
-  float *As = t32;                      // K~, then the reflectors below the diagonal
-  float *Zs = As + (size_t)n * ld;      // eigenvectors of T, then of K~
+  float *As = t32;                      // K, K~, then the reflectors below the diagonal
+  float *Zs = As + (size_t)n * ld;      // eigenvectors of T, then of K~, then of the pencil
   float *vv = Zs + (size_t)n * ld;      // current reflector v
   float *pw = vv + n;                   // beta K~ v; later beta v^T Z
   float *dd = pw + n, *ee = dd + n, *e2 = ee + n, *bet = e2 + n, *lam = bet + n;
-  float *Ub = lam + 2 * n;              // [3][n][kInvBatch] pivot rows of the batch's solves
+  float *rdg = lam + 2 * n;             // 1 / l_ii
+  float *Ub = rdg + n;                  // [3][n][kInvBatch] pivot rows of the batch's solves
+  float *Lb = Ub + 3 * (size_t)n * kInvBatch;   // Lb[i * kMaxBand + d] = L[i][i - d]
   __shared__ float s_f[4];
   __shared__ int s_start[kFastMaxN];
-  for (int t = tid; t < n * n; t += nt) As[(t / n) * ld + t % n] = (float)jb.A[t];
+  __shared__ int s_fail;
+  __shared__ float s_nrm[32];
+  for (int t = tid; t < n * n; t += nt) As[(t / n) * ld + t % n] = (float)jb.K[t];
+  for (int t = tid; t < n * kMaxBand; t += nt) {
+    const int i = t / kMaxBand, d = t % kMaxBand;
+    Lb[t] = (d <= p && i - d >= 0) ? (float)jb.M[(size_t)i * n + i - d] : 0.0f;
+  }
   __syncthreads();
+  // -- banded Cholesky M = L L^T in FP32, one warp (O(n p^2) work) --
+  if (warp == 0) {
+    int fail = 0;
+    for (int k = 0; k < n; ++k) {
+      const float dk = Lb[k * kMaxBand];
+      __syncwarp();
+      if (!(dk > 0.0f)) fail = 1;
+      const float lkk = dk > 0.0f ? sqrtf(dk) : 1.0f;
+      const float r = 1.0f / lkk;
+      if (lane == 0) { Lb[k * kMaxBand] = lkk; rdg[k] = r; }
+      if (lane >= 1 && lane <= p && k + lane < n) Lb[(k + lane) * kMaxBand + lane] *= r;
+      __syncwarp();
+      // L[k+a][k+b] -= L[k+a][k] L[k+b][k] for 1 <= b <= a <= p
+      for (int t = lane; t < p * p; t += 32) {
+        const int a = t / p + 1, b = t % p + 1;
+        if (b <= a && k + a < n)
+          Lb[(k + a) * kMaxBand + (a - b)] -= Lb[(k + a) * kMaxBand + a] * Lb[(k + b) * kMaxBand + b];
+      }
+      __syncwarp();
+    }
+    fail = __any_sync(0xffffffffu, fail);
+    if (lane == 0) s_fail = fail;
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) *jb.state = 1;
+    return;
+  }
+  // -- K~ = L^{-1} K L^{-T} in place: columns of X = L^{-1} K by forward
+  //    substitution, then rows of K~ (K~ L^T = X), the last p results of
+  //    each solve kept in registers --
+  for (int c = tid; c < n; c += nt) {
+    float w[kMaxBand - 1];
+#pragma unroll
+    for (int d = 0; d < kMaxBand - 1; ++d) w[d] = 0.0f;
+    for (int i = 0; i < n; ++i) {
+      float acc = As[i * ld + c];
+#pragma unroll
+      for (int d = 0; d < kMaxBand - 1; ++d)
+        if (d < p) acc -= Lb[i * kMaxBand + 1 + d] * w[d];
+      const float x = acc * rdg[i];
+      As[i * ld + c] = x;
+#pragma unroll
+      for (int d = kMaxBand - 2; d > 0; --d) w[d] = w[d - 1];
+      w[0] = x;
+    }
+  }
+  __syncthreads();
+  for (int r = tid; r < n; r += nt) {
+    float w[kMaxBand - 1];
+#pragma unroll
+    for (int d = 0; d < kMaxBand - 1; ++d) w[d] = 0.0f;
+    for (int j = 0; j < n; ++j) {
+      float acc = As[r * ld + j];
+#pragma unroll
+      for (int d = 0; d < kMaxBand - 1; ++d)
+        if (d < p) acc -= Lb[j * kMaxBand + 1 + d] * w[d];
+      const float y = acc * rdg[j];
+      As[r * ld + j] = y;
+#pragma unroll
+      for (int d = kMaxBand - 2; d > 0; --d) w[d] = w[d - 1];
+      w[0] = y;
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < n * n; t += nt) {
+    const int i = t / n, j = t % n;
+    if (i < j) {
+      const float a = 0.5f * (As[i * ld + j] + As[j * ld + i]);
+      As[i * ld + j] = a;
+      As[j * ld + i] = a;
+    }
+  }
+  __syncthreads();
+  {
+    // infinity norm of K~ (bounds its 2-norm): one warp per row
+    float mx = 0.0f;
+    for (int i = warp; i < n; i += nt / 32) {
+      float rs = 0.0f;
+      for (int j = lane; j < n; j += 32) rs += fabsf(As[i * ld + j]);
+      mx = fmaxf(mx, warp_sum_f(rs));
+    }
+    if (lane == 0) s_nrm[warp] = mx;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.0f;
+    for (int w = 0; w < nt / 32; ++w) m = fmaxf(m, s_nrm[w]);
+    jb.sc[0] = (double)m;
+  }
   // -- Householder tridiagonalisation: step k zeroes A[k+2..][k] --
   for (int k = 0; k < n - 2; ++k) {
     const int m = n - k - 1;            // length of x = A[k+1..n-1][k]
@@ -443,7 +562,27 @@ __global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs) {
     }
     __syncthreads();
   }
+  // -- eigenvectors of the pencil: X = L^{-T} Z (backward substitution per
+  //    column; w[d] = x_{i+1+d}) --
+  for (int c = tid; c < n; c += nt) {
+    float w[kMaxBand - 1];
+#pragma unroll
+    for (int d = 0; d < kMaxBand - 1; ++d) w[d] = 0.0f;
+    for (int i = n - 1; i >= 0; --i) {
+      float acc = Zs[i * ld + c];
+#pragma unroll
+      for (int d = 0; d < kMaxBand - 1; ++d)
+        if (d < p && i + 1 + d < n) acc -= Lb[(i + 1 + d) * kMaxBand + 1 + d] * w[d];
+      const float x = acc * rdg[i];
+      Zs[i * ld + c] = x;
+#pragma unroll
+      for (int d = kMaxBand - 2; d > 0; --d) w[d] = w[d - 1];
+      w[0] = x;
+    }
+  }
+  __syncthreads();
   for (int t = tid; t < n * n; t += nt) jb.X[t] = (double)Zs[(t / n) * ld + t % n];
+  if (tid == 0) *jb.state = 0;
 }
 
 // ---- fast route: dense FP64 products C = op(A) B (+ D), many CTAs ----
@@ -511,54 +650,78 @@ __global__ void __launch_bounds__(64) gemm64_kernel(GemmBatch b) {
   if (row < n && col < n) g.C[(size_t)row * n + col] = acc + (g.D ? g.D[(size_t)row * n + col] : 0.0);
 }
 
-// block-wide max of a non-negative value (result valid in every thread)
-__device__ double block_max(double v, double *sh) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double m = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
-  __syncthreads();
-  return m;
+// ---- fast route: banded products M X (into AX) and K X (into A) ----
+__global__ void band_kernel(EigJob *jobs, int parity) {
+  const EigJob jb = jobs[blockIdx.y];
+  if (*jb.state != 0) return;
+  const int n = jb.n, p = jb.p;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int i = t / n, c = t % n;
+  const double *X = parity ? jb.Xn : jb.X;
+  const int j0 = i - p > 0 ? i - p : 0, j1 = i + p < n - 1 ? i + p : n - 1;
+  double mx = 0.0, kx = 0.0;
+  for (int j = j0; j <= j1; ++j) {
+    const double x = X[(size_t)j * n + c];
+    mx = fma(jb.M[(size_t)i * n + j], x, mx);
+    kx = fma(jb.K[(size_t)i * n + j], x, kx);
+  }
+  jb.AX[t] = mx;
+  jb.A[t] = kx;
 }
 
-// ---- fast route, refinement step: E from G = X^T X and S = X^T K~ X ----
+// bit pattern of |v| (ordered like |v| for finite values; NaN and infinity
+// compare above every finite value), so that maxima can use integer atomics
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// ---- fast route, refinement step: E from G = X^T M X and S = X^T K X ----
 constexpr double kClusterRel = 1e-5;   // pairs closer than this x ||K~||_inf stay clusters
 
-// Refinement step, first half: lambda_i = s_ii / g_ii (into E's first row)
-// and the cluster bound delta = 2 (||S - diag(lambda)|| + ||K~|| ||R||)
-// (infinity norms bound the 2-norms), at least kClusterRel ||K~||_inf, into
-// sc[1]. The correction E itself is formed inside the X + X E product.
-__global__ void __launch_bounds__(1024) refine_kernel(EigJob *jobs) {
-  EigJob jb = jobs[blockIdx.x];
-  if (*jb.state != 0) return;
-  const int n = jb.n, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const double *G = jb.G, *S = jb.S;
-  double *lam = jb.E;
-  __shared__ double lam_s[kFastMaxN];
-  __shared__ double sh[32];
-  for (int i = tid; i < n; i += nt) {
-    lam_s[i] = S[(size_t)i * n + i] / G[(size_t)i * n + i];
-    lam[i] = lam_s[i];
+// Refinement step, first half, one warp per row i: lambda_i = s_ii / g_ii
+// (into E) and the row sums of |S - diag(lambda)| and |I - G|; the last row
+// to finish forms the cluster bound delta = 2 (||S - diag(lambda)|| + ||K~||
+// ||R||) (infinity norms bound the 2-norms), at least kClusterRel ||K~||_inf,
+// into sc[1]. The correction E itself is formed inside the X + X E product.
+__global__ void __launch_bounds__(32) refine_kernel(EigJob *jobs) {
+  const EigJob jb = jobs[blockIdx.y];
+  const int n = jb.n, i = blockIdx.x, lane = threadIdx.x;
+  if (i >= n || *jb.state != 0) return;
+  const double *G = jb.G + (size_t)i * n, *S = jb.S + (size_t)i * n;
+  const double lam_i = S[i] / G[i];
+  double a = 0.0, b = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    const double gv = G[j], sv = S[j];
+    a += fabs(j == i ? sv - lam_i : sv);
+    b += fabs(j == i ? 1.0 - gv : gv);
   }
-  __syncthreads();
-  double ns = 0.0, nr = 0.0;
-  for (int i = warp; i < n; i += nt / 32) {
-    double a = 0.0, b = 0.0;
-    for (int j = lane; j < n; j += 32) {
-      const double gv = G[(size_t)i * n + j], sv = S[(size_t)i * n + j];
-      a += fabs(i == j ? sv - lam_s[i] : sv);
-      b += fabs(i == j ? 1.0 - gv : gv);
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane == 0) {
+    jb.E[i] = lam_i;
+    unsigned long long *mx = (unsigned long long *)(jb.sc + 6);
+    unsigned *counter = (unsigned *)(jb.sc + 5);
+    atomicMax(&mx[0], abs_bits(a));
+    atomicMax(&mx[1], abs_bits(b));
+    __threadfence();
+    if (atomicAdd(counter, 1u) == (unsigned)(n - 1)) {
+      __threadfence();
+      const double ns = __longlong_as_double((long long)atomicAdd(&mx[0], 0ull));
+      const double nr = __longlong_as_double((long long)atomicAdd(&mx[1], 0ull));
+      jb.sc[1] = fmax(2.0 * (ns + jb.sc[0] * nr), kClusterRel * jb.sc[0]);
+      mx[0] = 0ull;
+      mx[1] = 0ull;
+      *counter = 0u;
     }
-    a = warp_sum(a);
-    b = warp_sum(b);
-    ns = fmax(ns, a);
-    nr = fmax(nr, b);
   }
-  ns = block_max(ns, sh);
-  nr = block_max(nr, sh);
-  if (tid == 0) jb.sc[1] = fmax(2.0 * (ns + jb.sc[0] * nr), kClusterRel * jb.sc[0]);
 }
 
 // ---- fast route: exact 2x2 rotations for nearly degenerate pairs ----
@@ -648,30 +811,43 @@ __global__ void __launch_bounds__(1024) cluster_kernel(EigJob *jobs, int parity)
   }
 }
 
-// ---- fast route: accept, or send the direction to the FP64 route ----
-__global__ void __launch_bounds__(1024) check_kernel(EigJob *jobs) {
-  EigJob jb = jobs[blockIdx.x];
-  if (*jb.state != 0) return;
-  const int n = jb.n, tid = threadIdx.x, nt = blockDim.x;
-  __shared__ double sh[32];
-  double orth = 0.0, off = 0.0, dm = 0.0;
-  for (int t = tid; t < n * n; t += nt) {
-    const int i = t / n, j = t % n;
-    const double g = jb.G[t], sv = jb.S[t];
-    const double eo = fabs(i == j ? g - 1.0 : g);
-    // fmax drops NaN: a value that is not finite counts as a failure
-    orth = fmax(orth, eo < 1e300 ? eo : 1.0);
-    if (!(fabs(sv) < 1e300)) off = 1e300;
-    else if (i == j) dm = fmax(dm, fabs(sv));
-    else off = fmax(off, fabs(sv));
+// ---- fast route: accept, or send the pencil to the FP64 route ----
+// One warp per row: max |G - I|, max off-diagonal |S| and |s_ii|; the last
+// row to finish decides (not finite counts as a failure).
+__global__ void __launch_bounds__(32) check_kernel(EigJob *jobs) {
+  const EigJob jb = jobs[blockIdx.y];
+  const int n = jb.n, i = blockIdx.x, lane = threadIdx.x;
+  if (i >= n || *jb.state != 0) return;
+  const double *G = jb.G + (size_t)i * n, *S = jb.S + (size_t)i * n;
+  unsigned long long orth = 0ull, off = 0ull, dm = 0ull;
+  for (int j = lane; j < n; j += 32) {
+    const double g = G[j];
+    const unsigned long long eo = abs_bits(j == i ? g - 1.0 : g), sb = abs_bits(S[j]);
+    orth = eo > orth ? eo : orth;
+    if (j == i) dm = sb;
+    else off = sb > off ? sb : off;
   }
-  orth = block_max(orth, sh);
-  off = block_max(off, sh);
-  dm = block_max(dm, sh);
-  if (tid == 0) {
-    jb.sc[2] = orth;
-    jb.sc[3] = dm > 0.0 ? off / dm : 1.0;
-    if (!(orth <= 1e-12) || !(off <= 1e-12 * dm)) *jb.state = 1;
+  orth = warp_max_u64(orth);
+  off = warp_max_u64(off);
+  dm = warp_max_u64(dm);
+  if (lane == 0) {
+    unsigned long long *mx = (unsigned long long *)(jb.sc + 8);
+    unsigned *counter = (unsigned *)(jb.sc + 5);
+    atomicMax(&mx[0], orth);
+    atomicMax(&mx[1], off);
+    atomicMax(&mx[2], dm);
+    __threadfence();
+    if (atomicAdd(counter, 1u) == (unsigned)(n - 1)) {
+      __threadfence();
+      const double o = __longlong_as_double((long long)atomicAdd(&mx[0], 0ull));
+      const double f = __longlong_as_double((long long)atomicAdd(&mx[1], 0ull));
+      const double d = __longlong_as_double((long long)atomicAdd(&mx[2], 0ull));
+      jb.sc[2] = o;
+      jb.sc[3] = d > 0.0 ? f / d : 1.0;
+      if (!(o <= 1e-12) || !(f <= 1e-12 * d)) *jb.state = 1;
+      mx[0] = mx[1] = mx[2] = 0ull;
+      *counter = 0u;
+    }
   }
 }
 
@@ -779,9 +955,9 @@ __global__ void __launch_bounds__(1024) jacobi64_kernel(EigJob *jobs, int *err, 
   }
 }
 
-// ---- U = L^{-T} (eigenvectors of K~), sort ascending, sign-normalise ----
-// Eigenvectors and values come from (X, diag S) on the fast route and from
-// (V, diag A) on the FP64 route.
+// ---- sort ascending, sign-normalise ----
+// Eigenvectors and values come from (X, diag S) on the fast route (already
+// the pencil's) and from (L^{-T} V, diag A) on the FP64 route.
 __global__ void __launch_bounds__(1024) finish_kernel(EigJob *jobs, int parity) {
   EigJob jb = jobs[blockIdx.x];
   const int st = *jb.state;
@@ -791,12 +967,16 @@ __global__ void __launch_bounds__(1024) finish_kernel(EigJob *jobs, int parity) 
   const double *Lam = st == 0 ? jb.S : jb.A;
   const double *M = jb.M;
   double *K = jb.K, *U = jb.U;
+  const double *Y = Vsrc;
   __shared__ double rdiag[kFastMaxN];
   double *rd = n <= kFastMaxN ? rdiag : jb.E;     // E is free at this point
-  for (int i = tid; i < n; i += nt) rd[i] = 1.0 / M[(size_t)i * n + i];
+  if (st == 1) {
+    for (int i = tid; i < n; i += nt) rd[i] = 1.0 / M[(size_t)i * n + i];
+    Y = K;
+  }
   __syncthreads();
-  // U = L^{-T} V (column-parallel backward substitution); w[d] = U[i+1+d][c]
-  for (int c = tid; c < n; c += nt) {
+  // FP64 route: U = L^{-T} V (column-parallel backward substitution); w[d] = U[i+1+d][c]
+  for (int c = tid; st == 1 && c < n; c += nt) {
     double w[kMaxBand];
 #pragma unroll
     for (int d = 0; d < kMaxBand; ++d) w[d] = 0.0;
@@ -823,12 +1003,12 @@ __global__ void __launch_bounds__(1024) finish_kernel(EigJob *jobs, int parity) 
     int imax = 0;
     double vmax = -1.0;
     for (int r = 0; r < n; ++r) {
-      double a = fabs(K[(size_t)r * n + i]);
+      double a = fabs(Y[(size_t)r * n + i]);
       if (a > vmax) { vmax = a; imax = r; }
     }
-    double sg = K[(size_t)imax * n + i] < 0.0 ? -1.0 : 1.0;
+    double sg = Y[(size_t)imax * n + i] < 0.0 ? -1.0 : 1.0;
     jb.D[rank] = li;
-    for (int r = 0; r < n; ++r) U[(size_t)r * n + rank] = sg * K[(size_t)r * n + i];
+    for (int r = 0; r < n; ++r) U[(size_t)r * n + rank] = sg * Y[(size_t)r * n + i];
   }
 }
 
@@ -858,12 +1038,25 @@ static GemmJob gemm_job(int n, int transA, const double *A, const double *B, con
 igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const double *const *wK,
                                      const double *const *wM) {
   const int dim = P->dim, p = P->p;
-  // scratch for all directions, kept by the patch: 12 n^2 doubles, 4 scalars
-  // and a route flag per direction, and the job table
+  // one job per distinct pencil: without span scalings, directions with the
+  // same knot vector share theirs (job[k] = job of direction k)
+  int job_of[3] = {0, 1, 2}, dir_of[3] = {0, 1, 2}, nj = 0;
+  const bool scaled = wK || wM;
+  for (int k = 0; k < dim; ++k) {
+    const int t = scaled ? k : P->twin[k];
+    if (t == k) {
+      dir_of[nj] = k;
+      job_of[k] = nj++;
+    } else {
+      job_of[k] = job_of[t];
+    }
+  }
+  // scratch for all directions, kept by the patch: 12 n^2 doubles and kScal
+  // scalars per direction, and the job table
   constexpr int kMats = 12;
   if (!P->eig_work) {
     size_t tot = 0;
-    for (int k = 0; k < dim; ++k) tot += kMats * (size_t)P->n[k] * P->n[k] + 8;
+    for (int k = 0; k < dim; ++k) tot += kMats * (size_t)P->n[k] * P->n[k] + kScal;
     if (cudaMalloc(&P->eig_work, tot * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&P->eig_jobs, 3 * sizeof(EigJob)) != cudaSuccess) {
       cudaGetLastError();
@@ -872,12 +1065,14 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
   }
   EigJob hjobs[3];
   size_t off = 0;
-  int max_n = 0;
-  for (int k = 0; k < dim; ++k) {
+  int max_n = 0, fast_jobs = 0;
+  for (int u = 0; u < nj; ++u) {
+    const int k = dir_of[u];
     int n = P->n[k];
     max_n = n > max_n ? n : max_n;
+    fast_jobs += n <= kFastMaxN;
     size_t nn = (size_t)n * n;
-    EigJob &j = hjobs[k];
+    EigJob &j = hjobs[u];
     double *w = P->eig_work + off;
     j.n = n; j.p = p;
     j.M = w; j.K = w + nn; j.A = w + 2 * nn; j.V = w + 3 * nn;
@@ -886,7 +1081,7 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
     j.sc = w + kMats * nn;
     j.state = (int *)(j.sc + 4);
     j.U = P->U[k]; j.D = P->D[k];
-    off += kMats * nn + 8;
+    off += kMats * nn + kScal;
     IGAFD_CUDA(cudaMemsetAsync(j.M, 0, 2 * nn * sizeof(double), s));
     int th = n * (2 * p + 1);
     pencil_kernel<<<(th + 127) / 128, 128, 0, s>>>(P->dir[k], p, j.K, j.M, wK ? wK[k] : nullptr,
@@ -894,93 +1089,99 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
     IGAFD_LAUNCHED(1);
   }
   EigJob *djobs = (EigJob *)P->eig_jobs;
-  IGAFD_CUDA(cudaMemcpyAsync(djobs, hjobs, sizeof(hjobs), cudaMemcpyHostToDevice, s));
+  IGAFD_CUDA(cudaMemcpyAsync(djobs, hjobs, nj * sizeof(EigJob), cudaMemcpyHostToDevice, s));
   IGAFD_CUDA(cudaMemsetAsync(P->err_flag, 0, sizeof(int), s));
   cudaEvent_t e0, e1;
   IGAFD_CUDA(cudaEventCreate(&e0));
   IGAFD_CUDA(cudaEventCreate(&e1));
   IGAFD_CUDA(cudaEventRecord(e0, s));
   const int allow_fast = P->eig_route != 1;
-  prep_kernel<<<dim, 1024, 0, s>>>(djobs, P->err_flag, allow_fast);
-  IGAFD_LAUNCHED(1);
-  int parity = 0;
-  if (allow_fast && max_n > 0) {
-    // fast route for the directions with n <= 128 (the kernels skip the others)
+  {
+    // FP32 start (or the route choice) for every pencil
     static bool attr = false;
-    const int nmax = kFastMaxN;
-    const size_t smem32 = tri32_smem_floats(nmax) * sizeof(float);
+    const size_t smem32 = tri32_smem_floats(kFastMaxN) * sizeof(float);
     if (!attr) {
       IGAFD_CUDA(cudaFuncSetAttribute(tri32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem32));
       attr = true;
     }
-    tri32_kernel<<<dim, 1024, smem32, s>>>(djobs);
+    tri32_kernel<<<nj, 1024, smem32, s>>>(djobs, allow_fast);
     IGAFD_LAUNCHED(1);
-    int tiles = 0;
-    for (int k = 0; k < dim; ++k) {
-      const int t = (P->n[k] + kGT - 1) / kGT;
-      tiles = t * t > tiles ? t * t : tiles;
-    }
-    auto products = [&](bool with_s) -> igafd_status {
-      // G = X^T X and AX = K~ X, then S = X^T AX
-      GemmBatch b1{}, b2{};
-      for (int k = 0; k < dim; ++k) {
-        const EigJob &j = hjobs[k];
-        const double *X = parity ? j.Xn : j.X;
-        b1.j[2 * k] = gemm_job(j.n, 1, X, X, nullptr, j.G, j.state);
-        b1.j[2 * k + 1] = gemm_job(j.n, 0, j.A, X, nullptr, j.AX, j.state);
-        b2.j[k] = gemm_job(j.n, 1, X, j.AX, nullptr, j.S, j.state);
-      }
-      gemm64_kernel<<<dim3(tiles, 2 * dim), kGT * kGT, 0, s>>>(b1);
+  }
+  int parity = 0;
+  if (allow_fast && fast_jobs > 0) {
+    // fast route: the kernels skip pencils whose state is not 0
+    int nmax = 0;
+    for (int u = 0; u < nj; ++u) nmax = hjobs[u].n > nmax ? hjobs[u].n : nmax;
+    const int tiles = ((nmax + kGT - 1) / kGT) * ((nmax + kGT - 1) / kGT);
+    auto products = [&]() -> igafd_status {
+      // M X and K X (banded), then G = X^T (M X) and S = X^T (K X)
+      band_kernel<<<dim3((nmax * nmax + 255) / 256, nj), 256, 0, s>>>(djobs, parity);
       IGAFD_LAUNCHED(1);
-      if (with_s) {
-        gemm64_kernel<<<dim3(tiles, dim), kGT * kGT, 0, s>>>(b2);
-        IGAFD_LAUNCHED(1);
+      GemmBatch b1{};
+      for (int u = 0; u < nj; ++u) {
+        const EigJob &j = hjobs[u];
+        const double *X = parity ? j.Xn : j.X;
+        b1.j[2 * u] = gemm_job(j.n, 1, X, j.AX, nullptr, j.G, j.state);
+        b1.j[2 * u + 1] = gemm_job(j.n, 1, X, j.A, nullptr, j.S, j.state);
       }
+      gemm64_kernel<<<dim3(tiles, 2 * nj), kGT * kGT, 0, s>>>(b1);
+      IGAFD_LAUNCHED(1);
       IGAFD_CUDA(cudaGetLastError());
       return IGAFD_OK;
     };
     for (int it = 0; it < 4; ++it) {
-      IGAFD_TRY(products(true));
-      refine_kernel<<<dim, 1024, 0, s>>>(djobs);
+      IGAFD_TRY(products());
+      refine_kernel<<<dim3(nmax, nj), 32, 0, s>>>(djobs);
       IGAFD_LAUNCHED(1);
       GemmBatch b3{};
-      for (int k = 0; k < dim; ++k) {
-        const EigJob &j = hjobs[k];
+      for (int u = 0; u < nj; ++u) {
+        const EigJob &j = hjobs[u];
         const double *X = parity ? j.Xn : j.X;
         double *Xnext = parity ? j.X : j.Xn;
-        b3.j[k] = gemm_job(j.n, 0, X, nullptr, X, Xnext, j.state);
-        b3.j[k].G = j.G; b3.j[k].S = j.S; b3.j[k].lam = j.E; b3.j[k].dl = j.sc + 1;
+        b3.j[u] = gemm_job(j.n, 0, X, nullptr, X, Xnext, j.state);
+        b3.j[u].G = j.G; b3.j[u].S = j.S; b3.j[u].lam = j.E; b3.j[u].dl = j.sc + 1;
       }
-      gemm64_kernel<<<dim3(tiles, dim), kGT * kGT, 0, s>>>(b3);
+      gemm64_kernel<<<dim3(tiles, nj), kGT * kGT, 0, s>>>(b3);
       IGAFD_LAUNCHED(1);
       parity ^= 1;
     }
-    IGAFD_TRY(products(true));
-    cluster_kernel<<<dim, 1024, 0, s>>>(djobs, parity);
+    IGAFD_TRY(products());
+    cluster_kernel<<<nj, 1024, 0, s>>>(djobs, parity);
     IGAFD_LAUNCHED(1);
-    IGAFD_TRY(products(true));
-    check_kernel<<<dim, 1024, 0, s>>>(djobs);
+    IGAFD_TRY(products());
+    check_kernel<<<dim3(nmax, nj), 32, 0, s>>>(djobs);
     IGAFD_LAUNCHED(1);
   }
-  jacobi64_kernel<<<dim, 1024, 0, s>>>(djobs, P->err_flag, 40);
+  // FP64 route for the pencils that need it (state 1)
+  prep_kernel<<<nj, 1024, 0, s>>>(djobs, P->err_flag);
   IGAFD_LAUNCHED(1);
-  finish_kernel<<<dim, 1024, 0, s>>>(djobs, parity);
+  jacobi64_kernel<<<nj, 1024, 0, s>>>(djobs, P->err_flag, 40);
+  IGAFD_LAUNCHED(1);
+  finish_kernel<<<nj, 1024, 0, s>>>(djobs, parity);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaEventRecord(e1, s));
+  // directions that share a pencil: copy its eigenpairs
+  for (int k = 0; k < dim; ++k) {
+    const int k0 = dir_of[job_of[k]];
+    if (k0 == k) continue;
+    const size_t n = (size_t)P->n[k];
+    IGAFD_CUDA(cudaMemcpyAsync(P->U[k], P->U[k0], n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    IGAFD_CUDA(cudaMemcpyAsync(P->D[k], P->D[k0], n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   long long N = P->N;
   inv_lambda_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
       P->D[0], P->D[1], dim == 3 ? P->D[2] : nullptr, P->n[0], P->n[1], N, P->inv_lam,
       P->inv_lam32);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaGetLastError());
-  // route taken per direction (0 fast, 1 FP64 Jacobi, 2 failed) and the error flag
+  // route taken per pencil (0 fast, 1 FP64 Jacobi, 2 failed) and the error flag
   int hstate[3] = {0, 0, 0};
   double hsc[3][4] = {};
   int herr = 0;
-  for (int k = 0; k < dim; ++k) {
-    IGAFD_CUDA(cudaMemcpyAsync(&hstate[k], hjobs[k].state, sizeof(int), cudaMemcpyDeviceToHost, s));
-    IGAFD_CUDA(cudaMemcpyAsync(hsc[k], hjobs[k].sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  for (int u = 0; u < nj; ++u) {
+    IGAFD_CUDA(cudaMemcpyAsync(&hstate[u], hjobs[u].state, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IGAFD_CUDA(cudaMemcpyAsync(hsc[u], hjobs[u].sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   IGAFD_CUDA(cudaMemcpyAsync(&herr, P->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   igafd_status st = IGAFD_OK;
@@ -995,9 +1196,10 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
   cudaEventElapsedTime(&ms, e0, e1);
   P->eig_ms = ms;
   for (int k = 0; k < dim; ++k) {
-    P->eig_used[k] = hstate[k];
-    P->eig_check[k][0] = allow_fast && P->n[k] <= kFastMaxN ? hsc[k][2] : 0.0;
-    P->eig_check[k][1] = allow_fast && P->n[k] <= kFastMaxN ? hsc[k][3] : 0.0;
+    const int u = job_of[k];
+    P->eig_used[k] = hstate[u];
+    P->eig_check[k][0] = allow_fast && P->n[k] <= kFastMaxN ? hsc[u][2] : 0.0;
+    P->eig_check[k][1] = allow_fast && P->n[k] <= kFastMaxN ? hsc[u][3] : 0.0;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

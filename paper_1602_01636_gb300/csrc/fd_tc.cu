@@ -94,7 +94,7 @@ struct PassArgs {
   int out_f64;
   const unsigned char *Bimg;  // B = U_k^T (forward) or U_k, pre-staged: per K chunk the
                               // exact shared-memory image of the B stage
-  float b_scale;         // power of two folded into the FP16 image of B
+  const float *b_scale;  // device: power of two folded into the FP16 image of B (null: 1)
   const float *inv_lam;  // divide epilogue (null: none), indexed like out
   long long M;
   int K, N, Np;          // Np: N padded to a multiple of 16 (MMA N)
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
     const int q = warp & 3, half = warp >> 2;
     const int r = q * 32 + lane;                  // row within the tile
     const long long m = m0 + r;
-    const float unscale = 1.0f / (a_scale * a.b_scale);
+    const float unscale = 1.0f / (a_scale * (a.b_scale ? *a.b_scale : 1.0f));
     const int ncol32 = (a.Np + 31) / 32;
     for (int cb = half; cb < ncol32; cb += 2) {
       uint32_t v[32];
@@ -326,28 +326,61 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
                  "r"(a.tmem_cols));
 }
 
-// U_k^T (row-major, FP32) for the forward products
-__global__ void transpose_f32_kernel(const float *U, float *UT, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n * n) UT[(size_t)(i % n) * n + i / n] = U[i];
-}
+// Shared-memory images of B for every K chunk, one job per (direction,
+// forward/backward, operand type): B = U_k^T (forward) or U_k (backward),
+// U_k row-major FP32; rows padded to Np and K to whole chunks with zeros,
+// rounded to the operand type, FP16 scaled by a power of two, in the
+// swizzled stage layout.
+struct ImgJob {
+  const float *U;
+  int n, Np, op, transpose;
+  const float *scale;       // null: 1
+  unsigned char *img;
+};
+struct ImgBatch {
+  ImgJob j[18];
+};
 
-// Shared-memory image of B (n x n, row-major FP32, K contiguous) for every
-// K chunk: rows padded to Np and K to whole chunks with zeros, rounded to the
-// operand type, scaled by a power of two, in the swizzled stage layout.
-template <int OP>
-__global__ void b_image_kernel(const float *B, int n, int Np, float scale, unsigned char *img) {
-  using T = Op<OP>;
+__global__ void b_image_kernel(ImgBatch b) {
+  const ImgJob J = b.j[blockIdx.y];
+  const int n = J.n, Np = J.Np;
   const int nchunks = (n + kKC - 1) / kKC;
   const long long total = (long long)nchunks * Np * kKC;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= total) return;
-  const int kk = (int)(i % kKC);
-  const int r = (int)((i / kKC) % Np);
-  const int c = (int)(i / ((long long)kKC * Np));
-  const int k = c * kKC + kk;
-  const float v = (r < n && k < n) ? B[(size_t)r * n + k] * scale : 0.0f;
-  T::put(img + (size_t)c * Np * kKC * T::kBytes + sw128_off(r, kk * T::kBytes, Np), v);
+  const float scale = J.scale ? *J.scale : 1.0f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kk = (int)(i % kKC);
+    const int r = (int)((i / kKC) % Np);
+    const int c = (int)(i / ((long long)kKC * Np));
+    const int k = c * kKC + kk;
+    float v = 0.0f;
+    if (r < n && k < n) v = (J.transpose ? J.U[(size_t)k * n + r] : J.U[(size_t)r * n + k]) * scale;
+    if (J.op == OP_TF32)
+      Op<OP_TF32>::put(J.img + (size_t)c * Np * kKC * 4 + sw128_off(r, kk * 4, Np), v);
+    else if (J.op == OP_BF16)
+      Op<OP_BF16>::put(J.img + (size_t)c * Np * kKC * 2 + sw128_off(r, kk * 2, Np), v);
+    else
+      Op<OP_FP16>::put(J.img + (size_t)c * Np * kKC * 2 + sw128_off(r, kk * 2, Np), v);
+  }
+}
+
+// FP16 staging scale of U_k: the largest power of two with
+// max |U_k| * scale <= 2^14 (one block per direction)
+__global__ void scale16_kernel(const float *U0, const float *U1, const float *U2, int n0, int n1,
+                               int n2, float *scale) {
+  const float *U = blockIdx.x == 0 ? U0 : blockIdx.x == 1 ? U1 : U2;
+  const int n = blockIdx.x == 0 ? n0 : blockIdx.x == 1 ? n1 : n2;
+  __shared__ float sh[32];
+  float mx = 0.0f;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) mx = fmaxf(mx, fabsf(U[i]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[w]);
+    scale[blockIdx.x] = m > 0.0f ? exp2f(14.0f - ceilf(log2f(m))) : 1.0f;
+  }
 }
 
 
@@ -712,13 +745,12 @@ __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
 }  // namespace
 
 struct FDMixed {
-  float *UT[3];                  // U_k^T row-major FP32
-  float scale16[3];              // power of two folded into the FP16 images of U_k
+  float *scale16;                // device [3]: power of two folded into the FP16 images of U_k
   unsigned char *img[3][2][3];   // [direction][0: U_k^T, 1: U_k][op] B images
 };
 
 // Allocates on the first call; later calls (a re-setup of P) refill the
-// same buffers.
+// same buffers. Enqueues two kernels and does not synchronise.
 igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
   FDMixed *F = P->mixed;
   if (!F) {
@@ -726,27 +758,24 @@ igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
     if (!F) return IGAFD_ERR_OOM;
     P->mixed = F;
   }
-  for (int k = 0; k < P->dim; ++k) {
+  if (!F->scale16 && cudaMalloc(&F->scale16, 3 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return IGAFD_ERR_OOM;
+  }
+  const int dim = P->dim;
+  scale16_kernel<<<dim, 256, 0, s>>>(P->U32[0], P->U32[1], dim == 3 ? P->U32[2] : nullptr, P->n[0],
+                                     P->n[1], dim == 3 ? P->n[2] : 0, F->scale16);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
+  ImgBatch batch{};
+  int jobs = 0;
+  long long most = 0;
+  for (int k = 0; k < dim; ++k) {
     const int n = P->n[k];
-    if (!F->UT[k] && cudaMalloc(&F->UT[k], (size_t)n * n * sizeof(float)) != cudaSuccess) {
-      cudaGetLastError();
-      return IGAFD_ERR_OOM;
-    }
-    transpose_f32_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(P->U32[k], F->UT[k], n);
-    IGAFD_LAUNCHED(1);
-    IGAFD_CUDA(cudaGetLastError());
-    // FP16 staging scale: largest power of two with max|U_k| * scale <= 2^14
-    std::vector<float> h((size_t)n * n);
-    IGAFD_CUDA(cudaMemcpyAsync(h.data(), P->U32[k], h.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
-    IGAFD_CUDA(cudaStreamSynchronize(s));
-    float mx = 0.f;
-    for (float v : h) mx = fmaxf(mx, fabsf(v));
-    F->scale16[k] = mx > 0.f ? exp2f(14.0f - ceilf(log2f(mx))) : 1.0f;
     if (n > 256) continue;   // tensor-core FD limited to n_k <= 256
     const int Np = (n + 15) / 16 * 16;
     const int nchunks = (n + kKC - 1) / kKC;
     for (int dir = 0; dir < 2; ++dir) {
-      const float *B = dir == 0 ? F->UT[k] : P->U32[k];
       for (int op = 0; op < 3; ++op) {
         const int bytes = op == OP_TF32 ? 4 : 2;
         const size_t sz = (size_t)nchunks * Np * kKC * bytes;
@@ -754,26 +783,30 @@ igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
           cudaGetLastError();
           return IGAFD_ERR_OOM;
         }
+        ImgJob &J = batch.j[jobs++];
+        J.U = P->U32[k]; J.n = n; J.Np = Np; J.op = op; J.transpose = dir == 0;
+        J.scale = op == OP_FP16 ? F->scale16 + k : nullptr;
+        J.img = F->img[k][dir][op];
         const long long total = (long long)nchunks * Np * kKC;
-        const unsigned blocks = (unsigned)((total + 255) / 256);
-        if (op == OP_TF32) b_image_kernel<OP_TF32><<<blocks, 256, 0, s>>>(B, n, Np, 1.0f, F->img[k][dir][op]);
-        else if (op == OP_BF16) b_image_kernel<OP_BF16><<<blocks, 256, 0, s>>>(B, n, Np, 1.0f, F->img[k][dir][op]);
-        else b_image_kernel<OP_FP16><<<blocks, 256, 0, s>>>(B, n, Np, F->scale16[k], F->img[k][dir][op]);
-        IGAFD_LAUNCHED(1);
-        IGAFD_CUDA(cudaGetLastError());
+        most = total > most ? total : most;
       }
     }
+  }
+  if (jobs > 0) {
+    const unsigned blocks = (unsigned)((most + 255) / 256);
+    b_image_kernel<<<dim3(blocks, jobs), 256, 0, s>>>(batch);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
   }
   return IGAFD_OK;
 }
 
 void igafd_fd_tc_free(igafd_patch *P) {
   if (!P || !P->mixed) return;
-  for (int k = 0; k < 3; ++k) {
-    cudaFree(P->mixed->UT[k]);
+  cudaFree(P->mixed->scale16);
+  for (int k = 0; k < 3; ++k)
     for (int d = 0; d < 2; ++d)
       for (int o = 0; o < 3; ++o) cudaFree(P->mixed->img[k][d][o]);
-  }
   free(P->mixed);
   P->mixed = nullptr;
 }
@@ -900,7 +933,7 @@ igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, 
     a.out = last ? (void *)z : (void *)bufs[cur];
     a.out_f64 = last ? 1 : 0;
     a.Bimg = F->img[k][forward ? 0 : 1][op];
-    a.b_scale = op == OP_FP16 ? F->scale16[k] : 1.0f;
+    a.b_scale = op == OP_FP16 ? F->scale16 + k : nullptr;
     a.inv_lam = pass == dim - 1 ? P->inv_lam32 : nullptr;
     a.M = P->N / n;
     a.K = n;

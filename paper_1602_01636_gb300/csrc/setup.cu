@@ -6,6 +6,8 @@
 // Q = kappa |det J| J^{-1} J^{-T} (chain rule with J_ij = dx_i/dzeta_j; the
 // paper prints the transposes the other way round in Eq. (Q)).
 #include "common.cuh"
+
+#include <algorithm>
 #include "geom.cuh"
 
 #include <cmath>
@@ -416,6 +418,14 @@ igafd_status igafd_setup_tables(igafd_patch *P, const igafd_patch_desc *d, cudaS
     IGAFD_CUDA(cudaGetLastError());
     P->n[k] = D.n;
     P->nel[k] = D.nel;
+    // directions with identical knot vectors have identical pencils K_k, M_k
+    P->twin[k] = k;
+    for (int j = 0; j < k; ++j)
+      if (P->twin[j] == j && d->n_knots[j] == nk &&
+          std::equal(kn, kn + nk, d->knots[j])) {
+        P->twin[k] = j;
+        break;
+      }
   }
   IGAFD_TRY(dalloc((void **)&P->ctrl, ctrl_count * sizeof(double)));
   IGAFD_CUDA(cudaMemcpyAsync(P->ctrl, d->ctrl, ctrl_count * sizeof(double),
