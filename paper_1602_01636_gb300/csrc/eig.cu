@@ -219,15 +219,17 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-constexpr int kInvBatch = 32;        // clusters solved at once by inverse iteration
 constexpr float kInvCluster = 1e-5f; // eigenvalues of T closer than this x ||T|| form a cluster
 
-// shared memory of tri32_kernel (floats): A and Z (n x (n+1) each), nine
-// vectors of n, the pivot rows of kInvBatch concurrent solves and the band of
-// the Cholesky factor L (n x kMaxBand)
+constexpr int kInv = 64;             // inverse-iteration solves at once (pivot rows in shared memory)
+
+// shared memory of tri32_kernel (floats): A (kFastMaxN x (n+1); rows past n
+// are zero for the back-transform), Z (n x (n+1)), nine vectors of n, the
+// band of the Cholesky factor L (n x kMaxBand) and two pivot rows of kInv
+// concurrent solves (n x kInv each)
 __host__ __device__ constexpr size_t tri32_smem_floats(int n) {
-  return 2 * (size_t)n * (n + 1) + 9 * (size_t)n + 3 * (size_t)n * kInvBatch +
-         (size_t)n * kMaxBand;
+  return (size_t)(kFastMaxN + n) * (n + 1) + 9 * (size_t)n + (size_t)n * kMaxBand +
+         2 * (size_t)n * kInv;
 }
 
 // Fast route, step 1 (one CTA per pencil): FP32 approximate eigenvectors X of
@@ -246,13 +248,13 @@ __global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs, int allow_fas
   }
   extern __shared__ float t32[];
   float *As = t32;                      // K, K~, then the reflectors below the diagonal
-  float *Zs = As + (size_t)n * ld;      // eigenvectors of T, then of K~, then of the pencil
+  float *Zs = As + (size_t)kFastMaxN * ld;   // eigenvectors of T, then of K~, then of the pencil
   float *vv = Zs + (size_t)n * ld;      // current reflector v
   float *pw = vv + n;                   // beta K~ v; later beta v^T Z
   float *dd = pw + n, *ee = dd + n, *e2 = ee + n, *bet = e2 + n, *lam = bet + n;
   float *rdg = lam + 2 * n;             // 1 / l_ii
-  float *Ub = rdg + n;                  // [3][n][kInvBatch] pivot rows of the batch's solves
-  float *Lb = Ub + 3 * (size_t)n * kInvBatch;   // Lb[i * kMaxBand + d] = L[i][i - d]
+  float *Lb = rdg + n;                  // Lb[i * kMaxBand + d] = L[i][i - d]
+  float *P0 = Lb + (size_t)n * kMaxBand, *P1 = P0 + (size_t)n * kInv;   // pivot rows
   __shared__ float s_f[4];
   __shared__ int s_start[kFastMaxN];
   __shared__ int s_fail;
@@ -270,8 +272,8 @@ __global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs, int allow_fas
       const float dk = Lb[k * kMaxBand];
       __syncwarp();
       if (!(dk > 0.0f)) fail = 1;
-      const float lkk = dk > 0.0f ? sqrtf(dk) : 1.0f;
-      const float r = 1.0f / lkk;
+      const float r = dk > 0.0f ? rsqrtf(dk) : 1.0f;
+      const float lkk = dk > 0.0f ? dk * r : 1.0f;
       if (lane == 0) { Lb[k * kMaxBand] = lkk; rdg[k] = r; }
       if (lane >= 1 && lane <= p && k + lane < n) Lb[(k + lane) * kMaxBand + lane] *= r;
       __syncwarp();
@@ -418,6 +420,12 @@ __global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs, int allow_fas
     bet[n - 1] = 0.0f;
   }
   __syncthreads();
+  // reflector k is column k of As below the diagonal: zero the rest of the
+  // column (and rows n..kFastMaxN-1) so that the back-transform reads v_r = 0
+  for (int t = tid; t < kFastMaxN * n; t += nt) {
+    const int r = t / n, k = t % n;
+    if (r <= k || r >= n) As[r * ld + k] = 0.0f;
+  }
   // -- eigenvalues of T: Gershgorin interval, then 9-way multisection on
   //    Sturm counts (eight threads per eigenvalue, one count each) --
   if (warp == 0) {
@@ -468,18 +476,22 @@ __global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs, int allow_fas
     if (sub == 0 && (tid >> 3) < n) lam[tid >> 3] = 0.5f * (lo + hi);
   }
   __syncthreads();
-  // -- eigenvectors of T by inverse iteration; clusters (gaps <= 1e-3 ||T||)
-  //    are solved in turn by one thread; batches of kInvBatch cluster starts
-  //    keep their pivot rows in shared memory; y lives in Z's column --
+  // -- eigenvectors of T by inverse iteration, kInv cluster starts at once;
+  //    the members of a cluster (eigenvalues closer than kInvCluster ||T||)
+  //    are solved in turn by its start's thread and orthogonalised against
+  //    each other; y lives in Z's column --
   if (tid < n) s_start[tid] = (tid == 0 || lam[tid] - lam[tid - 1] > kInvCluster * tn) ? 1 : 0;
   __syncthreads();
   const float floor = 1.2e-7f * tn;
-  for (int b0 = 0; b0 < n; b0 += kInvBatch) {
+  for (int b0 = 0; b0 < n; b0 += kInv) {
     const int slot = tid - b0;
-    if (slot >= 0 && slot < kInvBatch && tid < n && s_start[tid]) {
+    if (slot >= 0 && slot < kInv && tid < n && s_start[tid]) {
       int last = tid;
       while (last + 1 < n && !s_start[last + 1]) ++last;
-      float *U0 = Ub + slot, *U1 = U0 + n * kInvBatch, *U2 = U1 + n * kInvBatch;
+      // pivot rows of the elimination: U[i][i] in Q0, U[i][i+1] in Q1 (NaN
+      // when rows i, i+1 were swapped: then U[i][i+1] = d_{i+1} - lm and
+      // U[i][i+2] = e_{i+1}, otherwise U[i][i+2] = 0)
+      float *Q0 = P0 + slot, *Q1 = P1 + slot;
       float prev = 0.0f;
       for (int mm = tid; mm <= last; ++mm) {
         float *Y = Zs + mm;             // y_j = Y[j * ld]
@@ -491,36 +503,35 @@ __global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs, int allow_fas
         for (int j = 0; j < n; ++j) Y[j * ld] = (float)((j * 7919 + mm * 104729) % 1000) * 1.0e-3f - 0.5f;
         for (int it = 0; it < 3; ++it) {
           // (T - lm I) y = y: Gaussian elimination with partial pivoting
-          float cd = dd[0] - lm, c1 = n > 1 ? ee[0] : 0.0f, c2 = 0.0f;
+          float cd = dd[0] - lm, c1 = n > 1 ? ee[0] : 0.0f;
           float yc = Y[0];
           for (int i = 0; i < n - 1; ++i) {
             const float nd = dd[i + 1] - lm, n1 = i + 1 < n - 1 ? ee[i + 1] : 0.0f, sdn = ee[i];
             const float yn = Y[(i + 1) * ld];
-            float p0, p1, p2, py;
-            if (fabsf(sdn) > fabsf(cd)) {   // swap: row i+1 is the pivot
-              const float m = cd / sdn;
-              p0 = sdn; p1 = nd; p2 = n1; py = yn;
-              cd = c1 - m * nd; c1 = c2 - m * n1; c2 = 0.0f;
-              yc = yc - m * yn;
-            } else {
-              const float m = cd != 0.0f ? sdn / cd : 0.0f;
-              p0 = cd; p1 = c1; p2 = c2; py = yc;
-              cd = nd - m * c1; c1 = n1 - m * c2; c2 = 0.0f;
-              yc = yn - m * yc;
-            }
-            U0[i * kInvBatch] = p0; U1[i * kInvBatch] = p1; U2[i * kInvBatch] = p2;
-            Y[i * ld] = py;
+            const bool sw = fabsf(sdn) > fabsf(cd);   // row i+1 is the pivot
+            const float num = sw ? cd : sdn, den = sw ? sdn : cd;
+            const float m = den != 0.0f ? __fdividef(num, den) : 0.0f;
+            Q0[i * kInv] = sw ? sdn : cd;
+            Q1[i * kInv] = sw ? __int_as_float(0x7fc00000) : c1;
+            Y[i * ld] = sw ? yn : yc;
+            const float cn = sw ? c1 - m * nd : nd - m * c1;
+            c1 = sw ? -m * n1 : n1;
+            yc = sw ? yc - m * yn : yn - m * yc;
+            cd = cn;
           }
-          U0[(n - 1) * kInvBatch] = cd;
-          U1[(n - 1) * kInvBatch] = 0.0f;
-          U2[(n - 1) * kInvBatch] = 0.0f;
+          Q0[(n - 1) * kInv] = cd;
+          Q1[(n - 1) * kInv] = 0.0f;
           Y[(n - 1) * ld] = yc;
           // back substitution (pivots no smaller than floor in magnitude)
           float x1 = 0.0f, x2 = 0.0f;
           for (int i = n - 1; i >= 0; --i) {
-            float u0 = U0[i * kInvBatch];
-            if (fabsf(u0) < floor) u0 = u0 >= 0.0f ? floor : -floor;
-            const float xi = (Y[i * ld] - U1[i * kInvBatch] * x1 - U2[i * kInvBatch] * x2) / u0;
+            float d = Q0[i * kInv];
+            const float q1 = Q1[i * kInv];
+            const bool sw = q1 != q1;
+            const float u1 = sw ? dd[i + 1] - lm : q1;
+            const float u2 = (sw && i + 2 < n) ? ee[i + 1] : 0.0f;
+            if (fabsf(d) < floor) d = d >= 0.0f ? floor : -floor;
+            const float xi = __fdividef(Y[i * ld] - u1 * x1 - u2 * x2, d);
             Y[i * ld] = xi;
             x2 = x1; x1 = xi;
           }
@@ -539,29 +550,44 @@ __global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs, int allow_fas
     }
     __syncthreads();
   }
-  // -- back-transform: Z <- H_0 ... H_{n-3} Z --
-  for (int k = n - 3; k >= 0; --k) {
-    const float beta = bet[k];
-    if (beta == 0.0f) continue;
-    const int m = n - k - 1;
-    {
-      const int c = tid >> 3, sub = tid & 7;
-      float acc = 0.0f;
-      if (c < n)
-        for (int i = sub; i < m; i += 8) acc += As[(k + 1 + i) * ld + k] * Zs[(k + 1 + i) * ld + c];
-      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      if (c < n && sub == 0) pw[c] = beta * acc;
+  // -- back-transform Z <- H_0 ... H_{n-3} Z: eight threads per column, rows
+  //    g, g + 8, ... of the column in registers; the columns are independent,
+  //    so no block barrier per reflector --
+  {
+    constexpr int kR = kFastMaxN / 8;
+    const int c = tid >> 3, g = tid & 7;
+    float z[kR];
+#pragma unroll
+    for (int t = 0; t < kR; ++t) {
+      const int r = g + 8 * t;
+      z[t] = (c < n && r < n) ? Zs[r * ld + c] : 0.0f;
     }
-    __syncthreads();
-    for (int i = warp; i < m; i += nt / 32) {
-      const float vi = As[(k + 1 + i) * ld + k];
-      float *row = Zs + (k + 1 + i) * ld;
-      for (int c = lane; c < n; c += 32) row[c] -= vi * pw[c];
+    // v_r = As[r][k] (zero for r <= k and r >= n)
+    const float *vcol = As + g * ld;
+    for (int k = n - 3; k >= 0; --k) {
+      const float beta = bet[k];
+      if (beta == 0.0f) continue;
+      float v[kR];
+      float sdot = 0.0f;
+#pragma unroll
+      for (int t = 0; t < kR; ++t) {
+        v[t] = vcol[8 * t * ld + k];
+        sdot += v[t] * z[t];
+      }
+      sdot += __shfl_xor_sync(0xffffffffu, sdot, 1);
+      sdot += __shfl_xor_sync(0xffffffffu, sdot, 2);
+      sdot += __shfl_xor_sync(0xffffffffu, sdot, 4);
+      sdot *= beta;
+#pragma unroll
+      for (int t = 0; t < kR; ++t) z[t] -= sdot * v[t];
     }
-    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kR; ++t) {
+      const int r = g + 8 * t;
+      if (c < n && r < n) Zs[r * ld + c] = z[t];
+    }
   }
+  __syncthreads();
   // -- eigenvectors of the pencil: X = L^{-T} Z (backward substitution per
   //    column; w[d] = x_{i+1+d}) --
   for (int c = tid; c < n; c += nt) {
