@@ -8,11 +8,6 @@
 
 namespace {
 
-__global__ void to_float_kernel(const double *a, float *b, long long n) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (float)a[i];
-}
-
 // Open knot vector on [0, 1]: nondecreasing, first and last value repeated
 // exactly deg+1 times, interior multiplicity <= deg (Eq. (knot-vector)).
 bool valid_open_knots(const double *kn, int nk, int deg) {
@@ -141,13 +136,7 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
 // D3), FP32 and tensor-core copies of U_k. Synchronises the stream.
 igafd_status igafd_build_prec(igafd_patch *P, cudaStream_t s) {
   IGAFD_TRY(igafd_setup_pencils_eig(P, s, P->scaled ? P->wK : nullptr, P->scaled ? P->wM : nullptr));
-  for (int k = 0; k < P->dim; ++k) {
-    long long nn = (long long)P->n[k] * P->n[k];
-    to_float_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(P->U[k], P->U32[k], nn);
-    IGAFD_LAUNCHED(1);
-    IGAFD_CUDA(cudaGetLastError());
-  }
-  IGAFD_TRY(igafd_fd_tc_init(P, s));
+  IGAFD_TRY(igafd_fd_tc_init(P, s));   // also the FP32 copies U32_k
   IGAFD_CUDA(cudaStreamSynchronize(s));
   return IGAFD_OK;
 }

@@ -11,7 +11,7 @@
 //   fast (n <= 128): an FP32 start in one CTA per pencil, all in shared
 //     memory -- banded Cholesky M = L L^T, K~ = L^{-1} K L^{-T}, Householder
 //     tridiagonalisation T = Q^T K~ Q, every eigenvalue of T by bisection on
-//     Sturm counts, eigenvectors of T by inverse iteration (3 steps; members of
+//     Sturm counts, eigenvectors of T by inverse iteration (2 steps; members of
 //     a cluster of eigenvalues closer than 1e-5 ||T|| are solved in turn and
 //     orthogonalised against each other), back-transformed by Q and by L^{-T}
 //     into approximate eigenvectors X of the pencil -- then FP64 iterative
@@ -74,7 +74,8 @@ __global__ void pencil_kernel(Dir1D D, int p, double *K, double *M, const double
 // mass matrix; becomes L on the FP64 route), K (stiffness; X = L^{-1} K on
 // the FP64 route), A (K~ on the FP64 route; K X on the fast one), V (FP64
 // Jacobi rotations), X/Xn (refined eigenvectors, ping-pong), G (X^T M X), AX
-// (M X), S (X^T K X), E (lambda of the refinement). U, D: outputs. sc:
+// (M X), S (X^T K X), E (lambda of the refinement), W (the correction E).
+// U, D: outputs. sc:
 // per-pencil scalars [0] = infinity norm of K~, [1] = cluster bound delta,
 // [2] = orthogonality error, [3] = relative off-diagonal of S, [4] = route
 // state (int: 0 = refined eigenpairs accepted, 1 = FP64 Jacobi route, 2 =
@@ -84,7 +85,7 @@ struct EigJob {
   int n, p;
   double *M, *K, *A, *V;
   double *X, *Xn, *G, *AX, *S, *E;
-  double *W;                          // 2 n^2: spare
+  double *W;                          // 2 n^2: the refinement's correction E
   double *U, *D;
   double *sc;
   int *state;
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs, int allow_fas
         if (mm > tid && lm < prev + pert) lm = prev + pert;
         prev = lm;
         for (int j = 0; j < n; ++j) Y[j * ld] = (float)((j * 7919 + mm * 104729) % 1000) * 1.0e-3f - 0.5f;
-        for (int it = 0; it < 3; ++it) {
+        for (int it = 0; it < 2; ++it) {
           // (T - lm I) y = y: Gaussian elimination with partial pivoting
           float cd = dd[0] - lm, c1 = n > 1 ? ee[0] : 0.0f;
           float yc = Y[0];
@@ -617,9 +618,6 @@ struct GemmJob {
   const double *A, *B, *D;
   double *C;
   const int *state;        // skip unless *state == 0
-  // B = E of the refinement step, formed while loading (B unused): from
-  // G = X^T X, S = X^T K~ X, lambda (lam) and the cluster bound delta (*dl)
-  const double *G, *S, *lam, *dl;
 };
 struct GemmBatch {
   GemmJob j[6];
@@ -650,23 +648,7 @@ __global__ void __launch_bounds__(64) gemm64_kernel(GemmBatch b) {
         As[r][kk] = (ra < n && ka < n) ? g.A[(size_t)ra * n + ka] : 0.0;
       }
       const int kk = t / kGT, c = t % kGT, kb = k0 + kk, cb = tj * kGT + c;
-      double bv = 0.0;
-      if (kb < n && cb < n) {
-        if (!g.G) {
-          bv = g.B[(size_t)kb * n + cb];
-        } else {
-          // E_ii = r_ii / 2; E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)
-          // for separated pairs, r_ij / 2 within a cluster (r = I - G)
-          const double gv = g.G[(size_t)kb * n + cb];
-          if (kb == cb) {
-            bv = 0.5 * (1.0 - gv);
-          } else {
-            const double d = g.lam[cb] - g.lam[kb];
-            bv = fabs(d) > *g.dl ? (g.S[(size_t)kb * n + cb] - g.lam[cb] * gv) / d : -0.5 * gv;
-          }
-        }
-      }
-      Bs[kk][c] = bv;
+      Bs[kk][c] = (kb < n && cb < n) ? g.B[(size_t)kb * n + cb] : 0.0;
     }
     __syncthreads();
 #pragma unroll 16
@@ -716,7 +698,7 @@ constexpr double kClusterRel = 1e-5;   // pairs closer than this x ||K~||_inf st
 // (into E) and the row sums of |S - diag(lambda)| and |I - G|; the last row
 // to finish forms the cluster bound delta = 2 (||S - diag(lambda)|| + ||K~||
 // ||R||) (infinity norms bound the 2-norms), at least kClusterRel ||K~||_inf,
-// into sc[1]. The correction E itself is formed inside the X + X E product.
+// into sc[1].
 __global__ void __launch_bounds__(32) refine_kernel(EigJob *jobs) {
   const EigJob jb = jobs[blockIdx.y];
   const int n = jb.n, i = blockIdx.x, lane = threadIdx.x;
@@ -748,6 +730,27 @@ __global__ void __launch_bounds__(32) refine_kernel(EigJob *jobs) {
       *counter = 0u;
     }
   }
+}
+
+// Refinement step, second half: the correction E (into W), E_ii = r_ii / 2,
+// E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs
+// and r_ij / 2 within a cluster (r = I - G), one element per thread.
+__global__ void correction_kernel(EigJob *jobs) {
+  const EigJob jb = jobs[blockIdx.y];
+  if (*jb.state != 0) return;
+  const int n = jb.n;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int i = t / n, j = t % n;
+  const double g = jb.G[t], *lam = jb.E;
+  double e;
+  if (i == j) {
+    e = 0.5 * (1.0 - g);
+  } else {
+    const double d = lam[j] - lam[i];
+    e = fabs(d) > jb.sc[1] ? (jb.S[t] - lam[j] * g) / d : -0.5 * g;
+  }
+  jb.W[t] = e;
 }
 
 // ---- fast route: exact 2x2 rotations for nearly degenerate pairs ----
@@ -1019,18 +1022,37 @@ __global__ void __launch_bounds__(1024) finish_kernel(EigJob *jobs, int parity) 
     }
   }
   __syncthreads();
+  // eigenvalues ranked and magnitudes compared as integers (a monotone map
+  // of the FP64 bit patterns: GB300's FP64 pipe is slow)
+  __shared__ unsigned long long key[kFastMaxN];
+  auto order_key = [](double v) -> unsigned long long {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+  };
+  if (n <= kFastMaxN)
+    for (int i = tid; i < n; i += nt) key[i] = order_key(Lam[(size_t)i * n + i]);
+  __syncthreads();
   for (int i = tid; i < n; i += nt) {
     double li = Lam[(size_t)i * n + i];
     int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      double lj = Lam[(size_t)j * n + j];
-      if (lj < li || (lj == li && j < i)) ++rank;
+    if (n <= kFastMaxN) {
+      const unsigned long long ki = key[i];
+      for (int j = 0; j < n; ++j) {
+        const unsigned long long kj = key[j];
+        rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+      }
+    } else {
+      for (int j = 0; j < n; ++j) {
+        double lj = Lam[(size_t)j * n + j];
+        if (lj < li || (lj == li && j < i)) ++rank;
+      }
     }
     int imax = 0;
-    double vmax = -1.0;
+    unsigned long long vmax = 0ull;
     for (int r = 0; r < n; ++r) {
-      double a = fabs(Y[(size_t)r * n + i]);
-      if (a > vmax) { vmax = a; imax = r; }
+      const unsigned long long a = (unsigned long long)__double_as_longlong(Y[(size_t)r * n + i]) &
+                                   0x7fffffffffffffffull;
+      if (r == 0 || a > vmax) { vmax = a; imax = r; }
     }
     double sg = Y[(size_t)imax * n + i] < 0.0 ? -1.0 : 1.0;
     jb.D[rank] = li;
@@ -1160,13 +1182,14 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
       IGAFD_TRY(products());
       refine_kernel<<<dim3(nmax, nj), 32, 0, s>>>(djobs);
       IGAFD_LAUNCHED(1);
+      correction_kernel<<<dim3((nmax * nmax + 255) / 256, nj), 256, 0, s>>>(djobs);
+      IGAFD_LAUNCHED(1);
       GemmBatch b3{};
       for (int u = 0; u < nj; ++u) {
         const EigJob &j = hjobs[u];
         const double *X = parity ? j.Xn : j.X;
         double *Xnext = parity ? j.X : j.Xn;
-        b3.j[u] = gemm_job(j.n, 0, X, nullptr, X, Xnext, j.state);
-        b3.j[u].G = j.G; b3.j[u].S = j.S; b3.j[u].lam = j.E; b3.j[u].dl = j.sc + 1;
+        b3.j[u] = gemm_job(j.n, 0, X, j.W, X, Xnext, j.state);
       }
       gemm64_kernel<<<dim3(tiles, nj), kGT * kGT, 0, s>>>(b3);
       IGAFD_LAUNCHED(1);

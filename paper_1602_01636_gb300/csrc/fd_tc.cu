@@ -326,6 +326,37 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
                  "r"(a.tmem_cols));
 }
 
+// U32_k = (float) U_k for every direction (grid.y = direction) and the bit
+// pattern of max |U32_k| (non-negative floats order like their bits) into
+// umax[k] (zeroed before the launch)
+__global__ void u32_kernel(const double *U0, const double *U1, const double *U2, float *V0,
+                           float *V1, float *V2, int n0, int n1, int n2, unsigned *umax) {
+  const int k = blockIdx.y;
+  const double *U = k == 0 ? U0 : k == 1 ? U1 : U2;
+  float *V = k == 0 ? V0 : k == 1 ? V1 : V2;
+  const int n = k == 0 ? n0 : k == 1 ? n1 : n2;
+  unsigned mx = 0u;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x) {
+    const float v = (float)U[i];
+    V[i] = v;
+    const unsigned b = __float_as_uint(v) & 0x7fffffffu;
+    mx = b > mx ? b : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned w = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = w > mx ? w : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&umax[k], mx);
+}
+
+// FP16 staging scale of U_k from max |U_k|: the largest power of two with
+// max |U_k| * scale <= 2^14
+__device__ __forceinline__ float fp16_scale(unsigned maxbits) {
+  const float m = __uint_as_float(maxbits);
+  return m > 0.0f ? exp2f(14.0f - ceilf(log2f(m))) : 1.0f;
+}
+
+
 // Shared-memory images of B for every K chunk, one job per (direction,
 // forward/backward, operand type): B = U_k^T (forward) or U_k (backward),
 // U_k row-major FP32; rows padded to Np and K to whole chunks with zeros,
@@ -334,7 +365,8 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
 struct ImgJob {
   const float *U;
   int n, Np, op, transpose;
-  const float *scale;       // null: 1
+  const unsigned *umax;     // FP16: bit pattern of max |U| (the scale follows); null: scale 1
+  float *scale;             // FP16: where the scale is recorded for the epilogue
   unsigned char *img;
 };
 struct ImgBatch {
@@ -346,7 +378,8 @@ __global__ void b_image_kernel(ImgBatch b) {
   const int n = J.n, Np = J.Np;
   const int nchunks = (n + kKC - 1) / kKC;
   const long long total = (long long)nchunks * Np * kKC;
-  const float scale = J.scale ? *J.scale : 1.0f;
+  const float scale = J.umax ? fp16_scale(*J.umax) : 1.0f;
+  if (J.scale && blockIdx.x == 0 && threadIdx.x == 0) *J.scale = scale;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int kk = (int)(i % kKC);
@@ -363,26 +396,6 @@ __global__ void b_image_kernel(ImgBatch b) {
       Op<OP_FP16>::put(J.img + (size_t)c * Np * kKC * 2 + sw128_off(r, kk * 2, Np), v);
   }
 }
-
-// FP16 staging scale of U_k: the largest power of two with
-// max |U_k| * scale <= 2^14 (one block per direction)
-__global__ void scale16_kernel(const float *U0, const float *U1, const float *U2, int n0, int n1,
-                               int n2, float *scale) {
-  const float *U = blockIdx.x == 0 ? U0 : blockIdx.x == 1 ? U1 : U2;
-  const int n = blockIdx.x == 0 ? n0 : blockIdx.x == 1 ? n1 : n2;
-  __shared__ float sh[32];
-  float mx = 0.0f;
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) mx = fmaxf(mx, fabsf(U[i]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float m = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[w]);
-    scale[blockIdx.x] = m > 0.0f ? exp2f(14.0f - ceilf(log2f(m))) : 1.0f;
-  }
-}
-
 
 // ---------------------------------------------------------------------------
 // Fused FD for n_k <= 128 with TF32 or BF16 operands: three kernels, each CTA
@@ -746,11 +759,14 @@ __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
 
 struct FDMixed {
   float *scale16;                // device [3]: power of two folded into the FP16 images of U_k
+  unsigned *umax;                // device [3]: bit pattern of max |U32_k|
   unsigned char *img[3][2][3];   // [direction][0: U_k^T, 1: U_k][op] B images
 };
 
-// Allocates on the first call; later calls (a re-setup of P) refill the
-// same buffers. Enqueues two kernels and does not synchronise.
+// FP32 copies U32_k of the eigenvector matrices and the tensor-core images
+// of U_k^T and U_k. Allocates on the first call; later calls (a re-setup of
+// P) refill the same buffers. Enqueues a memset and two kernels and does not
+// synchronise.
 igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
   FDMixed *F = P->mixed;
   if (!F) {
@@ -758,15 +774,23 @@ igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
     if (!F) return IGAFD_ERR_OOM;
     P->mixed = F;
   }
-  if (!F->scale16 && cudaMalloc(&F->scale16, 3 * sizeof(float)) != cudaSuccess) {
+  if ((!F->scale16 && cudaMalloc(&F->scale16, 3 * sizeof(float)) != cudaSuccess) ||
+      (!F->umax && cudaMalloc(&F->umax, 3 * sizeof(unsigned)) != cudaSuccess)) {
     cudaGetLastError();
     return IGAFD_ERR_OOM;
   }
   const int dim = P->dim;
-  scale16_kernel<<<dim, 256, 0, s>>>(P->U32[0], P->U32[1], dim == 3 ? P->U32[2] : nullptr, P->n[0],
-                                     P->n[1], dim == 3 ? P->n[2] : 0, F->scale16);
-  IGAFD_LAUNCHED(1);
-  IGAFD_CUDA(cudaGetLastError());
+  int nmax = 0;
+  for (int k = 0; k < dim; ++k) nmax = P->n[k] > nmax ? P->n[k] : nmax;
+  IGAFD_CUDA(cudaMemsetAsync(F->umax, 0, 3 * sizeof(unsigned), s));
+  {
+    const unsigned blocks = (unsigned)(((long long)nmax * nmax + 1023) / 1024);
+    u32_kernel<<<dim3(blocks < 64 ? blocks : 64, dim), 256, 0, s>>>(
+        P->U[0], P->U[1], dim == 3 ? P->U[2] : nullptr, P->U32[0], P->U32[1],
+        dim == 3 ? P->U32[2] : nullptr, P->n[0], P->n[1], dim == 3 ? P->n[2] : 0, F->umax);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+  }
   ImgBatch batch{};
   int jobs = 0;
   long long most = 0;
@@ -785,6 +809,7 @@ igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
         }
         ImgJob &J = batch.j[jobs++];
         J.U = P->U32[k]; J.n = n; J.Np = Np; J.op = op; J.transpose = dir == 0;
+        J.umax = op == OP_FP16 ? F->umax + k : nullptr;
         J.scale = op == OP_FP16 ? F->scale16 + k : nullptr;
         J.img = F->img[k][dir][op];
         const long long total = (long long)nchunks * Np * kKC;
@@ -804,6 +829,7 @@ igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
 void igafd_fd_tc_free(igafd_patch *P) {
   if (!P || !P->mixed) return;
   cudaFree(P->mixed->scale16);
+  cudaFree(P->mixed->umax);
   for (int k = 0; k < 3; ++k)
     for (int d = 0; d < 2; ++d)
       for (int o = 0; o < 3; ++o) cudaFree(P->mixed->img[k][d][o]);
