@@ -615,6 +615,7 @@ __global__ void __launch_bounds__(1024) tri32_kernel(EigJob *jobs, int allow_fas
 // ---- fast route: dense FP64 products C = op(A) B (+ D), many CTAs ----
 struct GemmJob {
   int n, transA;
+  int sym;                 // C is symmetric: only tiles ti <= tj are computed, each written twice
   const double *A, *B, *D;
   double *C;
   const int *state;        // skip unless *state == 0
@@ -632,7 +633,16 @@ __global__ void __launch_bounds__(64) gemm64_kernel(GemmBatch b) {
   if (g.n == 0 || *g.state != 0) return;
   const int n = g.n, tpr = (n + kGT - 1) / kGT;
   if ((int)blockIdx.x >= tpr * tpr) return;
-  const int ti = blockIdx.x / tpr, tj = blockIdx.x % tpr;
+  int ti = blockIdx.x / tpr, tj = blockIdx.x % tpr;
+  if (g.sym) {
+    // upper-triangle tile number blockIdx.x -> (ti, tj), ti <= tj
+    const int nt = tpr * (tpr + 1) / 2;
+    if ((int)blockIdx.x >= nt) return;
+    int r = blockIdx.x;
+    ti = 0;
+    while (r >= tpr - ti) { r -= tpr - ti; ++ti; }
+    tj = ti + r;
+  }
   const int ty = threadIdx.x / kGT, tx = threadIdx.x % kGT;
   constexpr int KP = 64;
   __shared__ double As[kGT][KP + 1], Bs[KP][kGT + 1];
@@ -655,7 +665,11 @@ __global__ void __launch_bounds__(64) gemm64_kernel(GemmBatch b) {
     for (int kk = 0; kk < KP; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
     __syncthreads();
   }
-  if (row < n && col < n) g.C[(size_t)row * n + col] = acc + (g.D ? g.D[(size_t)row * n + col] : 0.0);
+  if (row < n && col < n) {
+    const double c = acc + (g.D ? g.D[(size_t)row * n + col] : 0.0);
+    g.C[(size_t)row * n + col] = c;
+    if (g.sym && ti != tj) g.C[(size_t)col * n + row] = c;
+  }
 }
 
 // ---- fast route: banded products M X (into AX) and K X (into A) ----
@@ -1161,7 +1175,8 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
     // fast route: the kernels skip pencils whose state is not 0
     int nmax = 0;
     for (int u = 0; u < nj; ++u) nmax = hjobs[u].n > nmax ? hjobs[u].n : nmax;
-    const int tiles = ((nmax + kGT - 1) / kGT) * ((nmax + kGT - 1) / kGT);
+    const int tpr = (nmax + kGT - 1) / kGT;
+    const int tiles = tpr * tpr, tiles_sym = tpr * (tpr + 1) / 2;
     auto products = [&]() -> igafd_status {
       // M X and K X (banded), then G = X^T (M X) and S = X^T (K X)
       band_kernel<<<dim3((nmax * nmax + 255) / 256, nj), 256, 0, s>>>(djobs, parity);
@@ -1172,13 +1187,16 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
         const double *X = parity ? j.Xn : j.X;
         b1.j[2 * u] = gemm_job(j.n, 1, X, j.AX, nullptr, j.G, j.state);
         b1.j[2 * u + 1] = gemm_job(j.n, 1, X, j.A, nullptr, j.S, j.state);
+        b1.j[2 * u].sym = b1.j[2 * u + 1].sym = 1;   // X^T M X, X^T K X
       }
-      gemm64_kernel<<<dim3(tiles, 2 * nj), kGT * kGT, 0, s>>>(b1);
+      gemm64_kernel<<<dim3(tiles_sym, 2 * nj), kGT * kGT, 0, s>>>(b1);
       IGAFD_LAUNCHED(1);
       IGAFD_CUDA(cudaGetLastError());
       return IGAFD_OK;
     };
-    for (int it = 0; it < 4; ++it) {
+    // an FP32 start is refined to the FP64 level in two steps; the third
+    // leaves margin below the acceptance test
+    for (int it = 0; it < 3; ++it) {
       IGAFD_TRY(products());
       refine_kernel<<<dim3(nmax, nj), 32, 0, s>>>(djobs);
       IGAFD_LAUNCHED(1);
