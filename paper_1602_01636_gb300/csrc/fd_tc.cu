@@ -64,16 +64,44 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int kbyte, int rows) {
          (((chunk ^ (row & 7)) << 4) | (kb & 15));
 }
 
+// FP64 <-> FP32 by integer operations on the IEEE-754 bit fields (on GB300
+// the conversion instructions issue on the FP64 pipe, two per clock per SM,
+// which would make them the bottleneck of the staging and of the FP64 store).
+// f64_to_f32 truncates the mantissa (below the operand rounding that follows)
+// and flushes magnitudes under 2^-126 to zero; f32_to_f64 is exact for
+// normal numbers and flushes subnormals to zero. Infinities and NaNs are kept.
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u, ed = (hi >> 20) & 0x7ffu;
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const int e = (int)ed - 896;
+  unsigned r;
+  if (ed == 0x7ffu) r = sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);
+  else if (e >= 255) r = sign | 0x7f800000u;
+  else if (e <= 0) r = sign;
+  else r = sign | ((unsigned)e << 23) | mant;
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi = sign, lo = 0u;
+  if (e == 0xffu) { hi = sign | 0x7ff00000u | (m >> 3); lo = m << 29; }
+  else if (e != 0u) { hi = sign | ((e + 896u) << 20) | (m >> 3); lo = m << 29; }
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+// TF32 (10-bit mantissa) rounding to nearest, ties away from zero, on the bits
+__device__ __forceinline__ uint32_t tf32_bits(float v) {
+  return (__float_as_uint(v) + 0x1000u) & 0xffffe000u;
+}
+
 template <int OP> struct Op;
 template <> struct Op<OP_TF32> {
   static constexpr int kBytes = 4;
   static constexpr uint32_t kFmt = 2;
   // round to nearest TF32 (the MMA would otherwise drop the low mantissa bits)
-  __device__ static void put(unsigned char *p, float v) {
-    uint32_t t;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
-    *(uint32_t *)p = t;
-  }
+  __device__ static void put(unsigned char *p, float v) { *(uint32_t *)p = tf32_bits(v); }
 };
 template <> struct Op<OP_BF16> {
   static constexpr int kBytes = 2;
@@ -133,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
     float mx = 0.0f;
     for (int i = tid; i < mrows * K; i += kThreads) {
       const long long idx = (m0 + i / K) * K + i % K;
-      const float v = a.in_f64 ? (float)((const double *)a.in)[idx] : ((const float *)a.in)[idx];
+      const float v = a.in_f64 ? f64_to_f32(((const double *)a.in)[idx]) : ((const float *)a.in)[idx];
       mx = fmaxf(mx, fabsf(v));
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -222,14 +250,14 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
           if (vec) {
             if (a.in_f64) {
               const double2 d = *reinterpret_cast<const double2 *>((const double *)a.in + idx);
-              v[i] = make_float2((float)d.x, (float)d.y);
+              v[i] = make_float2(f64_to_f32(d.x), f64_to_f32(d.y));
             } else {
               v[i] = *reinterpret_cast<const float2 *>((const float *)a.in + idx);
             }
           } else {
-            if (k < K) v[i].x = a.in_f64 ? (float)((const double *)a.in)[idx] : ((const float *)a.in)[idx];
+            if (k < K) v[i].x = a.in_f64 ? f64_to_f32(((const double *)a.in)[idx]) : ((const float *)a.in)[idx];
             if (k + 1 < K)
-              v[i].y = a.in_f64 ? (float)((const double *)a.in)[idx + 1] : ((const float *)a.in)[idx + 1];
+              v[i].y = a.in_f64 ? f64_to_f32(((const double *)a.in)[idx + 1]) : ((const float *)a.in)[idx + 1];
           }
         }
       }
@@ -310,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
             const long long o = (long long)n * a.M + m;
             float val = __uint_as_float(v[j]) * unscale;
             if (a.inv_lam) val *= a.inv_lam[o];
-            if (a.out_f64) ((double *)a.out)[o] = (double)val;
+            if (a.out_f64) ((double *)a.out)[o] = f32_to_f64(val);
             else ((float *)a.out)[o] = val;
           }
         }
@@ -326,18 +354,29 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
                  "r"(a.tmem_cols));
 }
 
-// U32_k = (float) U_k for every direction (grid.y = direction) and the bit
-// pattern of max |U32_k| (non-negative floats order like their bits) into
-// umax[k] (zeroed before the launch)
-__global__ void u32_kernel(const double *U0, const double *U1, const double *U2, float *V0,
-                           float *V1, float *V2, int n0, int n1, int n2, unsigned *umax) {
+// U32_k = (float) U_k and D32_k = (float) D_k for every direction (grid.y =
+// direction) and the bit pattern of max |U32_k| (non-negative floats order
+// like their bits) into umax[k] (zeroed before the launch)
+struct U32Args {
+  const double *U[3], *D[3];
+  float *U32[3], *D32[3];
+  int n[3];
+  unsigned *umax;
+};
+__global__ void u32_kernel(U32Args a) {
   const int k = blockIdx.y;
-  const double *U = k == 0 ? U0 : k == 1 ? U1 : U2;
-  float *V = k == 0 ? V0 : k == 1 ? V1 : V2;
-  const int n = k == 0 ? n0 : k == 1 ? n1 : n2;
+  const int n = k == 0 ? a.n[0] : k == 1 ? a.n[1] : a.n[2];
+  const double *U = k == 0 ? a.U[0] : k == 1 ? a.U[1] : a.U[2];
+  float *V = k == 0 ? a.U32[0] : k == 1 ? a.U32[1] : a.U32[2];
+  const int first = blockIdx.x * blockDim.x + threadIdx.x;
+  if (first < n) {
+    const double *D = k == 0 ? a.D[0] : k == 1 ? a.D[1] : a.D[2];
+    float *D32 = k == 0 ? a.D32[0] : k == 1 ? a.D32[1] : a.D32[2];
+    D32[first] = (float)D[first];
+  }
   unsigned mx = 0u;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x) {
-    const float v = (float)U[i];
+  for (int i = first; i < n * n; i += gridDim.x * blockDim.x) {
+    const float v = f64_to_f32(U[i]);
     V[i] = v;
     const unsigned b = __float_as_uint(v) & 0x7fffffffu;
     mx = b > mx ? b : mx;
@@ -346,7 +385,7 @@ __global__ void u32_kernel(const double *U0, const double *U1, const double *U2,
     const unsigned w = __shfl_xor_sync(0xffffffffu, mx, o);
     mx = w > mx ? w : mx;
   }
-  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&umax[k], mx);
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&a.umax[k], mx);
 }
 
 // FP16 staging scale of U_k from max |U_k|: the largest power of two with
@@ -426,7 +465,8 @@ struct FusedArgs {
   int rowsA;                 // valid rows of the first A operand (lanes)
   int n1, n2, n3;
   long long n12;
-  const float *inv_lam;      // divide (PENCIL, or SLAB_FWD in 2D), null: none
+  const float *inv_lam;      // divide of SLAB_FWD in 2D (null: none)
+  const float *d1, *d2, *d3; // PENCIL: FP32 D_k, divided by d1 + d2 + d3 on the fly
   const double *done;
   int *err;
 };
@@ -437,7 +477,7 @@ template <int OP> __device__ __forceinline__ uint4 pack_chunk(const float *v);
 template <> __device__ __forceinline__ uint4 pack_chunk<OP_TF32>(const float *v) {
   uint32_t t[4];
 #pragma unroll
-  for (int e = 0; e < 4; ++e) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t[e]) : "f"(v[e]));
+  for (int e = 0; e < 4; ++e) t[e] = tf32_bits(v[e]);
   return make_uint4(t[0], t[1], t[2], t[3]);
 }
 template <> __device__ __forceinline__ uint4 pack_chunk<OP_BF16>(const float *v) {
@@ -479,12 +519,12 @@ __device__ void stage_rows(unsigned char *R, const void *in, int in_f64, long lo
           for (int e = 0; e < E; e += 2) {
             double2 d = make_double2(0.0, 0.0);
             if (rowok && k0 + e < K) d = __ldg(reinterpret_cast<const double2 *>(src + e));
-            v[u][e] = (float)d.x;
-            v[u][e + 1] = (float)d.y;
+            v[u][e] = f64_to_f32(d.x);
+            v[u][e + 1] = f64_to_f32(d.y);
           }
         } else {
 #pragma unroll
-          for (int e = 0; e < E; ++e) v[u][e] = (rowok && k0 + e < K) ? (float)__ldg(src + e) : 0.0f;
+          for (int e = 0; e < E; ++e) v[u][e] = (rowok && k0 + e < K) ? f64_to_f32(__ldg(src + e)) : 0.0f;
         }
       } else {
         const float *src = (const float *)in + g;
@@ -673,6 +713,10 @@ __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
       reinterpret_cast<uint4 *>(R1)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     const int ncol32 = (a.Np1 + 31) / 32;
+    // PENCIL: d1[j1] + d2[j2] of this thread's column c = j2 n1 + j1
+    const long long cc = (long long)blk * kM + lane_row;
+    const bool c_ok = KIND == PENCIL && cc < a.n12;
+    const float d12 = c_ok ? a.d1[cc % a.n1] + a.d2[cc / a.n1] : 0.0f;
     for (int cb = half; cb < ncol32; cb += 2) {
       uint32_t v[32];
       tmem_ld32(tmem, q, cb * 32, v);
@@ -682,8 +726,7 @@ __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
         float x = __uint_as_float(v[j]);
         if (KIND == PENCIL) {
           // divide by D1 (+) D2 (+) D3 at (j3 = col, c = c0 + lane_row); row = lane, k = col
-          const long long c = (long long)blk * kM + lane_row;
-          if (col < a.K2 && c < a.n12) x *= a.inv_lam[(long long)col * a.n12 + c];
+          if (col < a.K2 && c_ok) x = __fdividef(x, d12 + a.d3[col]);
           else x = 0.0f;
           v[j] = __float_as_uint(x);
         } else {
@@ -742,11 +785,308 @@ __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
             const long long o = obase + (long long)col * ostride + lane_row;
             float x = __uint_as_float(v[j]);
             if (KIND == SLAB_FWD && a.inv_lam) x *= a.inv_lam[o];
-            if (a.out_f64) ((double *)a.out)[o] = (double)x;
+            if (a.out_f64) ((double *)a.out)[o] = f32_to_f64(x);
             else ((float *)a.out)[o] = x;
           }
         }
       }
+    }
+  } else if (tid == 0) {
+    atomicExch(a.err, (int)IGAFD_ERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
+// ---------------------------------------------------------------------------
+// Fused FD for n_1 = n_2 = n_3 = 128 (3D): the three kernels of the fused path
+// with every size a compile-time constant, 512 threads, both B images fetched
+// at the start, and staging, transposition and epilogue addressed through
+// per-thread constant swizzle offsets (the generic kernels above spend most
+// of their instructions on run-time index arithmetic). Layouts and products
+// are those of tc_fused_kernel.
+constexpr int kN = 128;            // dofs per direction on this path
+constexpr int kT128 = 512;         // threads per CTA
+constexpr int kAtomCol = kN * 128; // bytes of one 128-byte K atom over all 128 rows
+
+// byte offset of (row, kbyte) in a 128-row K-major tile with 128-byte swizzle
+__device__ __forceinline__ uint32_t swz128(uint32_t row, uint32_t kbyte) {
+  return (kbyte >> 7) * kAtomCol + (row >> 3) * 1024 + (row & 7) * 128 +
+         ((((kbyte >> 4) & 7) ^ (row & 7)) << 4) + (kbyte & 15);
+}
+
+// FP64 -> operand bits by integer operations on the IEEE-754 fields, rounded
+// to nearest (ties away from zero) at the operand's precision; magnitudes
+// under 2^-126 flush to zero, above the FP32 range to infinity (NaN kept).
+template <int OP> __device__ __forceinline__ uint32_t op_bits_f64(double d);
+template <> __device__ __forceinline__ uint32_t op_bits_f64<OP_TF32>(double d) {
+  const uint32_t hi = (uint32_t)((unsigned long long)__double_as_longlong(d) >> 32);
+  const uint32_t sign = hi & 0x80000000u;
+  if (((hi >> 20) & 0x7ffu) == 0x7ffu) return sign | 0x7fc00000u | ((hi & 0xfffffu) ? 0u : 0u);
+  const uint32_t mag = (hi & 0x7fffffffu) + 0x200u;          // round at the TF32 mantissa
+  const int e = (int)(mag >> 20) - 896;
+  if (e <= 0) return sign;
+  if (e >= 255) return sign | 0x7f800000u;
+  return sign | ((uint32_t)e << 23) | (((mag >> 10) & 0x3ffu) << 13);
+}
+template <> __device__ __forceinline__ uint32_t op_bits_f64<OP_BF16>(double d) {
+  const uint32_t hi = (uint32_t)((unsigned long long)__double_as_longlong(d) >> 32);
+  const uint32_t sign = hi & 0x80000000u;
+  if (((hi >> 20) & 0x7ffu) == 0x7ffu) return (sign | 0x7fc00000u) >> 16;
+  const uint32_t mag = (hi & 0x7fffffffu) + 0x1000u;         // round at the BF16 mantissa
+  const int e = (int)(mag >> 20) - 896;
+  if (e <= 0) return sign >> 16;
+  if (e >= 255) return (sign | 0x7f800000u) >> 16;
+  return (sign >> 16) | ((uint32_t)e << 7) | ((mag >> 13) & 0x7fu);
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// A[r][k] = src[r * kN + k] (FP64), r, k < 128. Warp w takes half h = w & 1
+// of rows g + 8t (g = w >> 1, t < 16): each lane two consecutive elements
+// per row, so the row's swizzle term is one constant per thread.
+template <int OP>
+__device__ __forceinline__ void stage128_rows_f64(unsigned char *R, const double *src, int warp,
+                                                  int lane) {
+  constexpr int kB = Op<OP>::kBytes;
+  const int h = warp & 1, g = warp >> 1;
+  const int k = 64 * h + 2 * lane;
+  const uint32_t off0 = swz128((uint32_t)g, (uint32_t)(k * kB));
+  double2 d[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) d[t] = __ldg(reinterpret_cast<const double2 *>(src + (g + 8 * t) * kN + k));
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    if (OP == OP_TF32)
+      *reinterpret_cast<uint2 *>(R + off0 + t * 1024) =
+          make_uint2(op_bits_f64<OP_TF32>(d[t].x), op_bits_f64<OP_TF32>(d[t].y));
+    else
+      *reinterpret_cast<uint32_t *>(R + off0 + t * 1024) =
+          op_bits_f64<OP_BF16>(d[t].x) | (op_bits_f64<OP_BF16>(d[t].y) << 16);
+  }
+}
+
+// A[r][k] = src[r * kN + k] (FP32). Warp w takes rows g + 8 (2t + u) (g = w & 7,
+// u = w >> 3, t < 8); each lane four consecutive elements per row.
+template <int OP>
+__device__ __forceinline__ void stage128_rows_f32(unsigned char *R, const float *src, int warp,
+                                                  int lane) {
+  constexpr int kB = Op<OP>::kBytes;
+  const int g = warp & 7, u = warp >> 3;
+  const int k = 4 * lane;
+  const uint32_t off0 = swz128((uint32_t)(g + 8 * u), (uint32_t)(k * kB));
+  float4 f[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    f[t] = __ldg(reinterpret_cast<const float4 *>(src + (g + 8 * (2 * t + u)) * kN + k));
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (OP == OP_TF32)
+      *reinterpret_cast<uint4 *>(R + off0 + t * 2048) =
+          make_uint4(tf32_bits(f[t].x), tf32_bits(f[t].y), tf32_bits(f[t].z), tf32_bits(f[t].w));
+    else
+      *reinterpret_cast<uint2 *>(R + off0 + t * 2048) =
+          make_uint2(bf16x2_bits(f[t].x, f[t].y), bf16x2_bits(f[t].z, f[t].w));
+  }
+}
+
+// A[c][k] = src[k * n12 + c] (FP32, c contiguous in memory): the transpose of
+// a 128 x 128 block. A lane loads four consecutive c at each of the
+// consecutive k of one 16-byte operand chunk and writes four rows' chunks;
+// a store phase's eight lanes of one c-quad hit eight distinct chunks.
+template <int OP>
+__device__ __forceinline__ void stage128_cols(unsigned char *R, const float *src, int warp,
+                                              int lane) {
+  constexpr int kB = Op<OP>::kBytes;
+  constexpr int E = 16 / kB;                  // k per chunk: 4 (TF32) or 8 (BF16)
+  constexpr long long n12 = (long long)kN * kN;
+  constexpr int kBlocks = (kN / (8 * E)) * (kN / 16);   // blocks of 8E k x 16 c
+  const int kq = lane & 7, cq = lane >> 3;
+#pragma unroll
+  for (int b = warp; b < kBlocks; b += kT128 / 32) {
+    const int kb = b % (kN / (8 * E)), cb = b / (kN / (8 * E));
+    const int k0 = kb * 8 * E + kq * E, c0 = cb * 16 + cq * 4;
+    float4 f[E];
+#pragma unroll
+    for (int kk = 0; kk < E; ++kk) f[kk] = __ldg(reinterpret_cast<const float4 *>(src + (k0 + kk) * n12 + c0));
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float v[E];
+#pragma unroll
+      for (int kk = 0; kk < E; ++kk) v[kk] = e == 0 ? f[kk].x : e == 1 ? f[kk].y : e == 2 ? f[kk].z : f[kk].w;
+      *reinterpret_cast<uint4 *>(R + swz128((uint32_t)(c0 + e), (uint32_t)(k0 * kB))) = pack_chunk<OP>(v);
+    }
+  }
+}
+
+template <int OP, int KIND>
+__global__ void __launch_bounds__(kT128, 1) fd128_kernel(FusedArgs a) {
+  if (a.done && *a.done != 0.0) return;
+  using T = Op<OP>;
+  constexpr int kB = T::kBytes;
+  constexpr int kTile = kN * kN * kB;          // bytes of one 128 x 128 operand
+  constexpr long long n12 = (long long)kN * kN;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *R1 = base, *R2 = base + kTile, *R3 = base + 2 * kTile;   // A, B1, B2
+  __shared__ uint64_t bar_b1, bar_b2, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, blk = blockIdx.x;
+
+  auto wait_on = [&](uint64_t *b, uint32_t parity) -> bool {
+    for (long long it = 0; it < kSpin; ++it) {
+      uint32_t ok;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(smem_u32(b)), "r"(parity)
+          : "memory");
+      if (ok) return true;
+    }
+    return false;
+  };
+  auto mma = [&](unsigned char *Bt, uint32_t tmem) {
+    const uint32_t idesc = (1u << 4) | (T::kFmt << 7) | (T::kFmt << 10) |
+                           ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int ks = 0; ks < kN * kB / 32; ++ks) {
+      const uint32_t o = (uint32_t)((ks * 32) >> 7) * kAtomCol + ((ks * 32) & 127);
+      const uint64_t ad = sw128_desc(smem_u32(R1) + o);
+      const uint64_t bd = sw128_desc(smem_u32(Bt) + o);
+      const uint32_t acc = ks > 0 ? 1u : 0u;
+      if (OP == OP_TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&bar_mma))
+        : "memory");
+  };
+  auto bulk = [&](unsigned char *dst, const unsigned char *src, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"((uint32_t)kTile)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"((uint32_t)kTile), "r"(smem_u32(bar))
+        : "memory");
+  };
+  auto tmem_ld32 = [&](uint32_t taddr, uint32_t *v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  };
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_b1)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_b2)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+        smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    bulk(R2, a.B1, &bar_b1);
+    bulk(R3, a.B2, &bar_b2);
+  }
+  // ---- first A operand ----
+  if (KIND == PENCIL) stage128_cols<OP>(R1, (const float *)a.in + (long long)blk * kN, warp, lane);
+  else if (KIND == SLAB_FWD) stage128_rows_f64<OP>(R1, (const double *)a.in + blk * n12, warp, lane);
+  else stage128_rows_f32<OP>(R1, (const float *)a.in + blk * n12, warp, lane);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid == 0) {
+    if (!wait_on(&bar_b1, 0)) s_fail = 1;
+    else mma(R2, tmem);
+  }
+  __syncthreads();
+  if (!s_fail && !wait_on(&bar_mma, 0)) s_fail = 1;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int q = warp & 3, cg = warp >> 2;              // TMEM lane quarter, 32-column group
+  const int lrow = q * 32 + lane;                       // accumulator lane of this thread
+  const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cg * 32);
+  if (!s_fail) {
+    uint32_t v[32];
+    tmem_ld32(taddr, v);
+    if (KIND == PENCIL) {
+      // divide by D1 (+) D2 (+) D3 at column c = blk kN + lrow (= j2 kN + j1), j3 = cg 32 + j;
+      // the row's 32 values are whole operand chunks of the second A (k = j3)
+      const float d12 = a.d1[lrow] + a.d2[blk];
+      constexpr int E = 16 / kB;
+#pragma unroll
+      for (int e0 = 0; e0 < 32; e0 += E) {
+        float f[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) f[e] = __fdividef(__uint_as_float(v[e0 + e]), d12 + a.d3[cg * 32 + e0 + e]);
+        *reinterpret_cast<uint4 *>(R1 + swz128((uint32_t)lrow, (uint32_t)((cg * 32 + e0) * kB))) =
+            pack_chunk<OP>(f);
+      }
+    } else {
+      // transpose: element (row = cg 32 + j, k = lrow)
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        T::put(R1 + swz128((uint32_t)(cg * 32 + j), (uint32_t)(lrow * kB)), __uint_as_float(v[j]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && !s_fail) {
+    if (!wait_on(&bar_b2, 0)) s_fail = 1;
+    else mma(R3, tmem);
+  }
+  __syncthreads();
+  if (!s_fail && !wait_on(&bar_mma, 1)) s_fail = 1;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!s_fail) {
+    uint32_t v[32];
+    tmem_ld32(taddr, v);
+    // lanes: the output's contiguous index; columns: its strided one
+    if (KIND == PENCIL) {
+      float *o = (float *)a.out + (long long)blk * kN + lrow + (long long)cg * 32 * n12;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) o[j * n12] = __uint_as_float(v[j]);
+    } else if (KIND == SLAB_FWD) {
+      float *o = (float *)a.out + blk * n12 + lrow + cg * 32 * kN;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) o[j * kN] = __uint_as_float(v[j]);
+    } else {
+      double *o = (double *)a.out + blk * n12 + lrow + cg * 32 * kN;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) o[j * kN] = f32_to_f64(__uint_as_float(v[j]));
     }
   } else if (tid == 0) {
     atomicExch(a.err, (int)IGAFD_ERR_TIMEOUT);
@@ -760,6 +1100,7 @@ __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
 struct FDMixed {
   float *scale16;                // device [3]: power of two folded into the FP16 images of U_k
   unsigned *umax;                // device [3]: bit pattern of max |U32_k|
+  float *d32[3];                 // FP32 copies of D_k (the fused FD's divide)
   unsigned char *img[3][2][3];   // [direction][0: U_k^T, 1: U_k][op] B images
 };
 
@@ -784,10 +1125,20 @@ igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s) {
   for (int k = 0; k < dim; ++k) nmax = P->n[k] > nmax ? P->n[k] : nmax;
   IGAFD_CUDA(cudaMemsetAsync(F->umax, 0, 3 * sizeof(unsigned), s));
   {
-    const unsigned blocks = (unsigned)(((long long)nmax * nmax + 1023) / 1024);
-    u32_kernel<<<dim3(blocks < 64 ? blocks : 64, dim), 256, 0, s>>>(
-        P->U[0], P->U[1], dim == 3 ? P->U[2] : nullptr, P->U32[0], P->U32[1],
-        dim == 3 ? P->U32[2] : nullptr, P->n[0], P->n[1], dim == 3 ? P->n[2] : 0, F->umax);
+    U32Args ua{};
+    for (int k = 0; k < dim; ++k) {
+      if (!F->d32[k] && cudaMalloc(&F->d32[k], (size_t)P->n[k] * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return IGAFD_ERR_OOM;
+      }
+      ua.U[k] = P->U[k]; ua.D[k] = P->D[k]; ua.U32[k] = P->U32[k]; ua.D32[k] = F->d32[k];
+      ua.n[k] = P->n[k];
+    }
+    ua.umax = F->umax;
+    long long blocks = ((long long)nmax * nmax + 1023) / 1024;
+    if (blocks > 64) blocks = 64;
+    if (blocks * 256 < nmax) blocks = (nmax + 255) / 256;   // the D copy takes one thread per entry
+    u32_kernel<<<dim3((unsigned)blocks, dim), 256, 0, s>>>(ua);
     IGAFD_LAUNCHED(1);
     IGAFD_CUDA(cudaGetLastError());
   }
@@ -830,6 +1181,7 @@ void igafd_fd_tc_free(igafd_patch *P) {
   if (!P || !P->mixed) return;
   cudaFree(P->mixed->scale16);
   cudaFree(P->mixed->umax);
+  for (int k = 0; k < 3; ++k) cudaFree(P->mixed->d32[k]);
   for (int k = 0; k < 3; ++k)
     for (int d = 0; d < 2; ++d)
       for (int o = 0; o < 3; ++o) cudaFree(P->mixed->img[k][d][o]);
@@ -912,7 +1264,8 @@ static igafd_status fused_apply(igafd_patch *P, const double *r, double *z, cuda
     c.B1 = F->img[2][0][op]; c.Np1 = np(n3); c.K1 = n3; c.Kp1 = kp(n3);
     c.B2 = F->img[2][1][op]; c.Np2 = np(n3); c.K2 = n3; c.Kp2 = kp(n3);
     c.rowsA = kM;
-    c.inv_lam = P->inv_lam32;
+    c.inv_lam = nullptr;
+    c.d1 = F->d32[0]; c.d2 = F->d32[1]; c.d3 = F->d32[2];
     IGAFD_TRY((launch_fused<OP, PENCIL>(c, (int)((a.n12 + kM - 1) / kM), s, P->dev)));
     mid = t2;
   }
@@ -927,6 +1280,45 @@ static igafd_status fused_apply(igafd_patch *P, const double *r, double *z, cuda
   return IGAFD_OK;
 }
 
+template <int OP, int KIND>
+static igafd_status launch_fd128(const FusedArgs &a, cudaStream_t s, int dev) {
+  const size_t smem = 1024 + 3 * (size_t)kN * kN * (OP == OP_TF32 ? 4 : 2);
+  static std::atomic<unsigned long long> attr_set{0};
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_set.load() & bit)) {
+    IGAFD_CUDA(cudaFuncSetAttribute(fd128_kernel<OP, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    attr_set.fetch_or(bit);
+  }
+  fd128_kernel<OP, KIND><<<kN, kT128, smem, s>>>(a);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
+  return IGAFD_OK;
+}
+
+// Fused FD with every n_k = 128 in 3D: slab forward (modes 1, 2), pencil
+// (mode 3 forward, divide, mode 3 backward), slab backward (modes 2, 1).
+template <int OP>
+static igafd_status fd128_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
+                                double *done) {
+  FDMixed *F = P->mixed;
+  float *t1 = (float *)P->fd_a, *t2 = (float *)P->fd_b;
+  FusedArgs a{};
+  a.done = done;
+  a.err = P->err_flag;
+  a.in = r; a.out = t1;
+  a.B1 = F->img[0][0][OP]; a.B2 = F->img[1][0][OP];
+  IGAFD_TRY((launch_fd128<OP, SLAB_FWD>(a, s, P->dev)));
+  a.in = t1; a.out = t2;
+  a.B1 = F->img[2][0][OP]; a.B2 = F->img[2][1][OP];
+  a.d1 = F->d32[0]; a.d2 = F->d32[1]; a.d3 = F->d32[2];
+  IGAFD_TRY((launch_fd128<OP, PENCIL>(a, s, P->dev)));
+  a.in = t2; a.out = z;
+  a.B1 = F->img[0][1][OP]; a.B2 = F->img[1][1][OP];
+  IGAFD_TRY((launch_fd128<OP, SLAB_BWD>(a, s, P->dev)));
+  return IGAFD_OK;
+}
+
 igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, double *z,
                                cudaStream_t s, double *done) {
   FDMixed *F = P->mixed;
@@ -936,6 +1328,13 @@ igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, 
   bool fusable = op != OP_FP16 && P->fd_fused;
   for (int k = 0; k < dim; ++k) fusable = fusable && P->n[k] <= 128;
   if (fusable) {
+    // every n_k = 128 in 3D, 16-byte aligned vectors: the compile-time-sized kernels
+    const bool n128 = dim == 3 && P->n[0] == kN && P->n[1] == kN && P->n[2] == kN &&
+                      (uintptr_t)r % 16 == 0 && (uintptr_t)z % 16 == 0;
+    if (n128) {
+      if (op == OP_TF32) return fd128_apply<OP_TF32>(P, r, z, s, done);
+      return fd128_apply<OP_BF16>(P, r, z, s, done);
+    }
     if (op == OP_TF32) return fused_apply<OP_TF32>(P, r, z, s, done);
     return fused_apply<OP_BF16>(P, r, z, s, done);
   }

@@ -312,6 +312,34 @@ def test_full_size_sampled(torch):
     patch.close()
 
 
+@pytest.mark.parametrize("dtype", ["tf32", "bf16"])
+def test_fd_n128_kernels(torch, dtype):
+    """Every n_k = 128 in 3D takes the compile-time-sized fused kernels (three
+    launches): they meet the oracle bound and agree with the per-mode path
+    (p = 1 keeps the stencil small; the FD depends only on the pencils)."""
+    from paper_1602_01636_gb300 import igafd
+    prob = synth.deformed_cube(128, 1, seed=0)
+    disc = assemble.Discretization.from_problem(prob)
+    patch = make_patch(prob)
+    F = fd.FD([disc.pencil(k) for k in range(3)])
+    r = synth.random_vector(disc.N, 31)
+    zo = F.apply(r)
+    rd = to_dev(r)
+    patch.set_fd_fused(0)
+    z_pass = patch.apply_prec(rd, dtype=dtype).cpu().numpy()
+    patch.set_fd_fused(1)
+    l0 = igafd.kernel_launches()
+    z = patch.apply_prec(rd, dtype=dtype).cpu().numpy()
+    assert igafd.kernel_launches() - l0 == 3
+    e, e_pass, e_mut = rel(z, zo), rel(z_pass, zo), rel(z, z_pass)
+    print(f"n=128 {dtype}: fused {e:.2e} per-mode {e_pass:.2e} mutual {e_mut:.2e}")
+    assert e <= TC_TOL[dtype] and e_pass <= TC_TOL[dtype] and e_mut <= TC_TOL[dtype]
+    # a second call on the same input gives the same bits
+    z2 = patch.apply_prec(rd, dtype=dtype).cpu().numpy()
+    assert np.array_equal(z, z2)
+    patch.close()
+
+
 def test_batched_solve_matches_single_solves(torch):
     """Config-4-like batch (uneven n per axis, p in {2,3,4}, a_k ~ U(-0.1, 0.1),
     N(0,1) right-hand sides): one batched solve gives bitwise the iterates
