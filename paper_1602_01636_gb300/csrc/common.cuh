@@ -162,6 +162,36 @@ long long igafd_stencil_row_stride(long long N);   // Np for a given N
 long long igafd_stencil_halo(int p, const int *n);   // zero halo of padded vectors
 void igafd_tune_lookup(igafd_patch *P);              // apply a cached autotune choice
 
+// Programmatic dependent launch. Kernels of the PCG iteration and of the FD
+// are launched with igafd_launch, which lets a kernel start while its
+// predecessor on the stream is still finishing (its launch, barrier set-up,
+// TMEM allocation and constant-table fetches overlap the predecessor's tail).
+// Every such kernel calls pdl_wait() in all threads before reading anything
+// an earlier kernel wrote (the wait returns once the predecessor grid has
+// completed and its writes are visible, so a chain of such kernels stays
+// ordered), then pdl_trigger(), which lets the next kernel launch as soon as
+// all of this grid's blocks have started. Outside a programmatic dependency
+// both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t igafd_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Kernels enqueued by this library (process-wide), for launch accounting.
 extern std::atomic<long long> g_igafd_launches;
 #define IGAFD_LAUNCHED(n) g_igafd_launches.fetch_add((n), std::memory_order_relaxed)

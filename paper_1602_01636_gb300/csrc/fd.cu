@@ -30,6 +30,8 @@ struct GemmArgs {
 // 64x64 output tile, 16-deep K slices, 256 threads with 4x4 outputs each.
 template <typename TA, typename TB, typename TC, typename ACC>
 __global__ void __launch_bounds__(256) mode_gemm_kernel(GemmArgs g) {
+  pdl_wait();
+  pdl_trigger();
   if (g.done && *g.done != 0.0) return;
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ ACC As[BK][BM + 1];
@@ -100,9 +102,8 @@ __global__ void __launch_bounds__(256) mode_gemm_kernel(GemmArgs g) {
 template <typename TA, typename TB, typename TC, typename ACC>
 igafd_status launch_gemm(const GemmArgs &g, cudaStream_t s) {
   dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.batch);
-  mode_gemm_kernel<TA, TB, TC, ACC><<<grid, 256, 0, s>>>(g);
+  IGAFD_CUDA(igafd_launch(mode_gemm_kernel<TA, TB, TC, ACC>, grid, dim3(256), 0, s, g));
   IGAFD_LAUNCHED(1);
-  IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 

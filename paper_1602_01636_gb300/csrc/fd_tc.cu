@@ -133,6 +133,8 @@ struct PassArgs {
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
+  pdl_wait();
+  pdl_trigger();
   if (a.done && *a.done != 0.0) return;
   using T = Op<OP>;
   constexpr int kRowBytes = kKC * T::kBytes;                 // bytes of one stage row
@@ -588,6 +590,8 @@ __device__ void stage_cols(unsigned char *R, const float *in, long long n12, lon
 
 template <int OP, int KIND>
 __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
+  pdl_wait();
+  pdl_trigger();
   if (a.done && *a.done != 0.0) return;
   using T = Op<OP>;
   extern __shared__ unsigned char smem_raw[];
@@ -924,7 +928,6 @@ __device__ __forceinline__ void stage128_cols(unsigned char *R, const float *src
 
 template <int OP, int KIND>
 __global__ void __launch_bounds__(kT128, 1) fd128_kernel(FusedArgs a) {
-  if (a.done && *a.done != 0.0) return;
   using T = Op<OP>;
   constexpr int kB = T::kBytes;
   constexpr int kTile = kN * kN * kB;          // bytes of one 128 x 128 operand
@@ -1019,6 +1022,20 @@ __global__ void __launch_bounds__(kT128, 1) fd128_kernel(FusedArgs a) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     bulk(R2, a.B1, &bar_b1);
     bulk(R3, a.B2, &bar_b2);
+  }
+  // everything above (barriers, TMEM, the constant B images) overlaps the
+  // previous kernel's tail; its outputs are read only from here on
+  pdl_wait();
+  pdl_trigger();
+  if (a.done && *a.done != 0.0) {
+    // skipped (converged): let the image copies land, free TMEM
+    if (tid == 0) {
+      wait_on(&bar_b1, 0);
+      wait_on(&bar_b2, 0);
+    }
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+    return;
   }
   // ---- first A operand ----
   if (KIND == PENCIL) stage128_cols<OP>(R1, (const float *)a.in + (long long)blk * kN, warp, lane);
@@ -1201,9 +1218,8 @@ static igafd_status launch_pass(const PassArgs &a, cudaStream_t s) {
   IGAFD_CUDA(cudaFuncSetAttribute(tc_pass_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
   const unsigned grid = (unsigned)((a.M + kM - 1) / kM);
-  tc_pass_kernel<OP><<<grid, kThreads, smem, s>>>(a);
+  IGAFD_CUDA(igafd_launch(tc_pass_kernel<OP>, dim3(grid), dim3(kThreads), smem, s, a));
   IGAFD_LAUNCHED(1);
-  IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 
@@ -1223,9 +1239,8 @@ static igafd_status launch_fused(const FusedArgs &a, int grid, cudaStream_t s, i
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedMaxSmem));
     attr_set.fetch_or(bit);
   }
-  tc_fused_kernel<OP, KIND><<<grid, kThreads, smem, s>>>(a);
+  IGAFD_CUDA(igafd_launch(tc_fused_kernel<OP, KIND>, dim3(grid), dim3(kThreads), smem, s, a));
   IGAFD_LAUNCHED(1);
-  IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 
@@ -1290,9 +1305,8 @@ static igafd_status launch_fd128(const FusedArgs &a, cudaStream_t s, int dev) {
                                     (int)smem));
     attr_set.fetch_or(bit);
   }
-  fd128_kernel<OP, KIND><<<kN, kT128, smem, s>>>(a);
+  IGAFD_CUDA(igafd_launch(fd128_kernel<OP, KIND>, dim3(kN), dim3(kT128), smem, s, a));
   IGAFD_LAUNCHED(1);
-  IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 

@@ -47,6 +47,8 @@ __global__ void __launch_bounds__(256) update_xr_kernel(double *__restrict__ x, 
                                                         double *scal, double *partial,
                                                         unsigned *counter, int flexible,
                                                         double *coef) {
+  pdl_wait();
+  pdl_trigger();
   if (scal[S_DONE] != 0.0) return;
   const double alpha = scal[S_ALPHA];
   double rr = 0.0, rz = 0.0;
@@ -93,6 +95,8 @@ __global__ void __launch_bounds__(256) dot_rz_kernel(const double *__restrict__ 
                                                      double *scal, double *partial,
                                                      unsigned *counter, int init, int flexible,
                                                      int skip_done, double *coef) {
+  pdl_wait();
+  pdl_trigger();
   if (skip_done && scal[S_DONE] != 0.0) return;
   double rz = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -125,6 +129,8 @@ __global__ void __launch_bounds__(256) dot_rz_kernel(const double *__restrict__ 
 __global__ void __launch_bounds__(256) update_p_kernel(double *__restrict__ p,
                                                        const double *__restrict__ z, long long N,
                                                        const double *scal, int skip_done) {
+  pdl_wait();
+  pdl_trigger();
   if (skip_done && scal[S_DONE] != 0.0) return;
   const double beta = scal[S_BETA];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -136,6 +142,8 @@ __global__ void __launch_bounds__(256) update_p_kernel(double *__restrict__ p,
 __global__ void __launch_bounds__(256) norm2_kernel(const double *__restrict__ v, long long N,
                                                     double *scal, int slot, double *partial,
                                                     unsigned *counter) {
+  pdl_wait();
+  pdl_trigger();
   double s = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x)
@@ -228,14 +236,14 @@ static igafd_status enqueue_iteration(igafd_patch *P, igafd_dtype dt, int flex, 
   double *scal = P->scal, *done = P->scal + S_DONE;
   const long long N = P->N;
   IGAFD_TRY(igafd_stencil_launch(P, P->pv, P->q, nullptr, 1, 1, s, 0, timed ? P->tstat : nullptr));
-  update_xr_kernel<<<G, B, 0, s>>>(P->xs, P->r, P->pv, P->q, P->z, N, scal, P->partial,
-                                   P->counter, flex, P->coef);
+  IGAFD_CUDA(igafd_launch(update_xr_kernel, G, B, 0, s, P->xs, P->r, P->pv, P->q, P->z, N, scal, P->partial,
+                                   P->counter, flex, P->coef));
   IGAFD_LAUNCHED(1);
   if (true_every > 0) IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, true_every));
   IGAFD_TRY(fd_apply(P, dt, P->r, P->z, s, done));
-  dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, flex, 1, P->coef);
+  IGAFD_CUDA(igafd_launch(dot_rz_kernel, G, B, 0, s, P->r, P->z, N, scal, P->partial, P->counter, 0, flex, 1, P->coef));
   IGAFD_LAUNCHED(1);
-  update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 1);
+  IGAFD_CUDA(igafd_launch(update_p_kernel, G, B, 0, s, P->pv, P->z, N, scal, 1));
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
@@ -336,7 +344,7 @@ static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, cons
   init_scalars_kernel<<<1, 32, 0, s>>>(scal, o.tol * o.tol, (double)o.max_iter);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaMemcpyAsync(P->bint, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  norm2_kernel<<<G, B, 0, s>>>(P->bint, N, scal, S_BB, P->partial, P->counter);
+  IGAFD_CUDA(igafd_launch(norm2_kernel, G, B, 0, s, P->bint, N, scal, S_BB, P->partial, P->counter));
   IGAFD_LAUNCHED(1);
   if (o.x0_given) {
     IGAFD_CUDA(cudaMemcpyAsync(P->xs, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -355,7 +363,7 @@ static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, cons
     return IGAFD_OK;
   }
   IGAFD_TRY(fd_apply(P, o.prec_dtype, P->r, P->z, s, nullptr));
-  dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 1, S.flex, 0, P->coef);
+  IGAFD_CUDA(igafd_launch(dot_rz_kernel, G, B, 0, s, P->r, P->z, N, scal, P->partial, P->counter, 1, S.flex, 0, P->coef));
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaMemcpyAsync(P->pv, P->z, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   IGAFD_CUDA(cudaGetLastError());
@@ -376,17 +384,17 @@ static igafd_status run_chunk_direct(igafd_patch *P, cudaStream_t s, SolveState 
     if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c], s));
     IGAFD_TRY(igafd_stencil_launch(P, P->pv, P->q, nullptr, 1, 1, s));
     if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 1], s));
-    update_xr_kernel<<<G, B, 0, s>>>(P->xs, P->r, P->pv, P->q, P->z, N, scal, P->partial,
-                                     P->counter, S.flex, P->coef);
+    IGAFD_CUDA(igafd_launch(update_xr_kernel, G, B, 0, s, P->xs, P->r, P->pv, P->q, P->z, N, scal, P->partial,
+                                     P->counter, S.flex, P->coef));
     IGAFD_LAUNCHED(1);
     if (S.o.true_every > 0)
       IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, S.o.true_every));
     if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 2], s));
     IGAFD_TRY(fd_apply(P, S.o.prec_dtype, P->r, P->z, s, P->scal + S_DONE));
     if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 3], s));
-    dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 1, P->coef);
+    IGAFD_CUDA(igafd_launch(dot_rz_kernel, G, B, 0, s, P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 1, P->coef));
     IGAFD_LAUNCHED(1);
-    update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 1);
+    IGAFD_CUDA(igafd_launch(update_p_kernel, G, B, 0, s, P->pv, P->z, N, scal, 1));
     IGAFD_LAUNCHED(1);
     IGAFD_CUDA(cudaGetLastError());
   }
@@ -433,9 +441,9 @@ static igafd_status solve_after_chunk(igafd_patch *P, cudaStream_t s, SolveState
     set_scalar_kernel<<<1, 32, 0, s>>>(scal, S_DONE, 0.0);
     IGAFD_LAUNCHED(1);
     IGAFD_TRY(fd_apply(P, S.o.prec_dtype, P->r, P->z, s, nullptr));
-    dot_rz_kernel<<<G, B, 0, s>>>(P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 0, P->coef);
+    IGAFD_CUDA(igafd_launch(dot_rz_kernel, G, B, 0, s, P->r, P->z, N, scal, P->partial, P->counter, 0, S.flex, 0, P->coef));
     IGAFD_LAUNCHED(1);
-    update_p_kernel<<<G, B, 0, s>>>(P->pv, P->z, N, scal, 0);
+    IGAFD_CUDA(igafd_launch(update_p_kernel, G, B, 0, s, P->pv, P->z, N, scal, 0));
     IGAFD_LAUNCHED(1);
     IGAFD_CUDA(cudaGetLastError());
     S.k = (int)h[S_ITER];

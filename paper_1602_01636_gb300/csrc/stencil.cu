@@ -131,6 +131,8 @@ struct Geom {
 // MODE 1: y = b - A x, dot (y, y) -> true (r, r) when pcg.
 template <int DIM, int P, int MODE, int kStages, int R>
 __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs a) {
+  pdl_wait();
+  pdl_trigger();
   if (a.done && *a.done != 0.0) return;
   if (a.every > 0 && ((long long)a.scal[S_ITER]) % a.every != 0) return;
   if (a.tstat && threadIdx.x == 0) atomicMin(&a.tstat[0], global_ns());
@@ -355,9 +357,8 @@ igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, c
   long long grid = (long long)num_sms * per_sm;
   if (grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
-  kern<<<(int)grid, kBlock, smem, s>>>(a);
+  IGAFD_CUDA(igafd_launch(kern, dim3((unsigned)grid), dim3(kBlock), smem, s, a));
   IGAFD_LAUNCHED(1);
-  IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 
