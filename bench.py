@@ -265,7 +265,7 @@ def run_ours(args):
     dtype = args.dtype or "tf32"
     prob = synth.deformed_cube(n, p, seed=0)
     patch = igafd.Patch.from_problem(prob)
-    stages = patch.autotune()          # untimed: picks the stencil pipeline depth
+    stages = patch.autotune()          # untimed: stencil pipeline depth, tensor-core FD form
     N = patch.N
     b = patch.load_rhs_sine()
     x = torch.zeros_like(b)
@@ -463,6 +463,8 @@ def run_ours(args):
             "true_relres": {"mixed": infos[-1].true_relres, "fp64": inf64.true_relres},
             "setup_ms": patch.info.setup_ms, "eig_ms": patch.info.eig_ms,
             "autotuned_stencil_stages": stages, "autotuned_stencil_rows": patch.info.stencil_rows,
+            "autotuned_fd_form": {dt: ("fused" if f else "per-mode product")
+                                  for dt, f in zip(("tf32", "bf16", "fp16"), patch.info.fd_fused)},
             "phase_ms_per_step": {"stencil": sum(i.stencil_ms for i in infos) / len(infos),
                                   "prec_estimate": it_mixed / aps_mixed * 1e3},
             "roofline": {"bound": "alu", "kernel": "stencil_kernel (q = A p, fused (p, q))",
@@ -572,6 +574,8 @@ def run_batch(args):
             "all_converged": all(i.status == 0 for i in infos),
             "one_by_one_s": seq_s, "batch_speedup": seq_s / batch_s,
             "dofs_per_s": dofs / batch_s, "setup_s": setup_s, "folded_redraws": redraws,
+            "autotuned_fd_form_bf16": {"fused": sum(int(pt.info.fd_fused[1]) for pt in patches),
+                                       "per-mode product": sum(1 - int(pt.info.fd_fused[1]) for pt in patches)},
             "gpu_launches": launches}
     print(json.dumps(line), flush=True)
     for p_ in patches:

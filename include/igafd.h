@@ -99,6 +99,9 @@ typedef struct {
                           FP32 start + FP64 refinement route, 0 if from FP64 Jacobi */
   double eig_check[3][2]; /* per direction, the refinement route's final check: max |U~^T U~ - I|
                              and max |offdiag U~^T K~ U~| / max |diag| (accepted if both <= 1e-12) */
+  int fd_fused[3];     /* tensor-core FD in use for TF32, BF16, FP16 operands: 1 = fused (two mode
+                          products per kernel; the compile-time-sized kernels where every
+                          n_k = 128 in 3D), 0 = one kernel per mode product (autotuned) */
 } igafd_patch_info;
 
 typedef struct {
@@ -276,7 +279,10 @@ igafd_status igafd_lanczos_extremes(const double *alpha, const double *beta, int
 
 /* Time the candidate configurations of the A stencil's pipeline (ring depth
  * 3, 4 or 6 offset groups in flight per CTA; in 3D also one or two rows per
- * compute thread) on this patch and keep the fastest. Results are cached per process by (dim, p, n_1, n_2, n_3, SM
+ * compute thread) and of the tensor-core FD (for TF32 and BF16 operands: the
+ * fused kernels, two mode products per CTA with the intermediate on chip,
+ * against one kernel per mode product; the fused form needs every n_k <= 128)
+ * on this patch and keep the fastest of each. Results are cached per process by (dim, p, n_1, n_2, n_3, SM
  * count) and, if the environment variable IGAFD_TUNE_CACHE names a file,
  * appended to it (one JSON object per line); igafd_setup_patch applies a
  * cached choice without measuring. flags bit 0: measure even if cached.
@@ -299,7 +305,8 @@ igafd_status igafd_set_stencil_rows(igafd_patch *patch, int rows);
  * forward, the divide by D_1 (+) D_2 (+) D_3 and mode 3 backward; modes 2 and
  * 1 backward); fused = 0 runs one kernel per mode product through global
  * memory. Both round the operands the same way; results agree to FP32
- * accumulation order. Other values: IGAFD_ERR_ARG. */
+ * accumulation order. The choice applies to every operand type and replaces
+ * the per-type choice of igafd_autotune. Other values: IGAFD_ERR_ARG. */
 igafd_status igafd_set_fd_fused(igafd_patch *patch, int fused);
 
 /* ---- learned span scalings of the pencils -------------------------------

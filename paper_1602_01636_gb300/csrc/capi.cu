@@ -186,6 +186,7 @@ extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *strea
   P->kappa_p = d->kappa_ctrl ? d->kappa_p : 0;
   P->kappa = d->kappa;
   P->fd_fused = 1;
+  for (int o = 0; o < 3; ++o) P->fd_fused_op[o] = 1;
   P->stencil_rows = 1;
   if (cudaGetDevice(&P->dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev) != cudaSuccess) {
@@ -245,6 +246,10 @@ extern "C" igafd_status igafd_patch_query(const igafd_patch *P, igafd_patch_info
     info->eig_refined[k] = k < P->dim && P->eig_used[k] == 0 ? 1 : 0;
     info->eig_check[k][0] = k < P->dim ? P->eig_check[k][0] : 0.0;
     info->eig_check[k][1] = k < P->dim ? P->eig_check[k][1] : 0.0;
+    // the form the next apply takes (FP16 and any n_k > 128 run per mode product)
+    bool shape_ok = true;
+    for (int d = 0; d < P->dim; ++d) shape_ok = shape_ok && P->n[d] <= 128;
+    info->fd_fused[k] = P->fd_fused && P->fd_fused_op[k] && k != 2 && shape_ok ? 1 : 0;
   }
   return IGAFD_OK;
 }

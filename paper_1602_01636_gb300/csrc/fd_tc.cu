@@ -1339,7 +1339,7 @@ igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, 
   if (!F) return IGAFD_ERR_ARG;
   const int op = dt == IGAFD_TF32 ? OP_TF32 : dt == IGAFD_BF16 ? OP_BF16 : OP_FP16;
   const int dim = P->dim;
-  bool fusable = op != OP_FP16 && P->fd_fused;
+  bool fusable = op != OP_FP16 && P->fd_fused && P->fd_fused_op[op];
   for (int k = 0; k < dim; ++k) fusable = fusable && P->n[k] <= 128;
   if (fusable) {
     // every n_k = 128 in 3D, 16-byte aligned vectors: the compile-time-sized kernels

@@ -256,7 +256,11 @@ static igafd_status enqueue_iteration(igafd_patch *P, igafd_dtype dt, int flex, 
 // parameters change; the un-instantiated graph is kept for batched solves.
 static igafd_status loop_graph(igafd_patch *P, igafd_dtype dt, int flex, int true_every, int chunk,
                                int timing) {
-  const int key[5] = {(int)dt, flex, true_every, chunk, 1 + timing};
+  // everything that selects the captured kernels: the FD form and the stencil
+  // pipeline too (set by the autotuner or explicitly between solves)
+  const int op = dt == IGAFD_TF32 ? 0 : dt == IGAFD_BF16 ? 1 : 2;
+  const int key[9] = {(int)dt, flex, true_every, chunk, 1 + timing, P->fd_fused,
+                      P->fd_fused_op[op], P->stencil_stages, P->stencil_rows};
   if (P->loop_exec && memcmp(key, P->loop_key, sizeof(key)) == 0) return IGAFD_OK;
   if (P->loop_exec) {
     cudaGraphExecDestroy(P->loop_exec);

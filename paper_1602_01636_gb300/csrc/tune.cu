@@ -6,7 +6,13 @@
 // 2p+1, trading shared memory per CTA against resident CTAs per SM) and on
 // the sizes, so it is measured: each candidate applies A a few times to the
 // patch's own search-direction buffer, timed with CUDA events, and the
-// fastest is kept in the patch. Results are cached per
+// fastest is kept in the patch. The tensor-core FD is built in two forms for
+// TF32 and BF16 operands: fused (two mode products per CTA, 128-row tiles of
+// whole slabs or column blocks, the intermediate kept on chip; three kernels)
+// and one kernel per mode product (128-row tiles, K in 64-wide chunks
+// through a two-stage ring; 2d kernels). Which is faster depends on the
+// sizes (ragged n_k pad the fused tiles), so both are timed on the patch's
+// own residual buffer and the faster is kept per operand type. Results are cached per
 // process, keyed by (dim, p, n_1, n_2, n_3, SM count), and, when the
 // environment variable IGAFD_TUNE_CACHE names a file, in that file (one JSON
 // object per line), so later processes reuse them without measuring.
@@ -26,6 +32,8 @@ constexpr int kNumCand = 6;
 struct TuneEntry {
   int stages, rows;
   float ms[kNumCand];   // candidate c: depth kCandidates[c % 3], rows 1 + c / 3
+  int fd_fused[2];      // TF32, BF16: 1 fused, 0 per mode product
+  float fd_ms[4];       // TF32 fused, TF32 per mode, BF16 fused, BF16 per mode (-1: not timed)
 };
 
 std::mutex g_tune_mutex;
@@ -41,7 +49,8 @@ std::string tune_key(const igafd_patch *P) {
 }
 
 // lines: {"key": "3:3:128:128:128:sm152", "stencil_stages": 4, "stencil_rows": 2,
-//         "ms": [six times, -1 where not measured]}
+//         "ms": [six times, -1 where not measured], "fd_fused": [1, 1],
+//         "fd_ms": [four times]}
 void load_file_locked() {
   if (g_tune_loaded) return;
   g_tune_loaded = true;
@@ -53,12 +62,19 @@ void load_file_locked() {
   while (fgets(line, sizeof(line), f)) {
     char key[128];
     TuneEntry e{};
-    if (sscanf(line,
+    e.fd_fused[0] = e.fd_fused[1] = 1;
+    for (int i = 0; i < 4; ++i) e.fd_ms[i] = -1.0f;
+    const int got = sscanf(line,
                " {\"key\": \"%127[^\"]\", \"stencil_stages\": %d, \"stencil_rows\": %d, "
-               "\"ms\": [%f, %f, %f, %f, %f, %f]",
+               "\"ms\": [%f, %f, %f, %f, %f, %f], \"fd_fused\": [%d, %d], "
+               "\"fd_ms\": [%f, %f, %f, %f]",
                key, &e.stages, &e.rows, &e.ms[0], &e.ms[1], &e.ms[2], &e.ms[3], &e.ms[4],
-               &e.ms[5]) == 9)
+               &e.ms[5], &e.fd_fused[0], &e.fd_fused[1], &e.fd_ms[0], &e.fd_ms[1], &e.fd_ms[2],
+               &e.fd_ms[3]);
+    if (got == 15 || got == 9) {      // 9: a line written before the FD was tuned
+      if (got == 9) e.fd_fused[0] = e.fd_fused[1] = 1;
       g_tune[key] = e;
+    }
   }
   fclose(f);
 }
@@ -70,8 +86,10 @@ void append_file_locked(const std::string &key, const TuneEntry &e) {
   if (!f) return;
   fprintf(f,
           "{\"key\": \"%s\", \"stencil_stages\": %d, \"stencil_rows\": %d, "
-          "\"ms\": [%.5f, %.5f, %.5f, %.5f, %.5f, %.5f]}\n",
-          key.c_str(), e.stages, e.rows, e.ms[0], e.ms[1], e.ms[2], e.ms[3], e.ms[4], e.ms[5]);
+          "\"ms\": [%.5f, %.5f, %.5f, %.5f, %.5f, %.5f], \"fd_fused\": [%d, %d], "
+          "\"fd_ms\": [%.5f, %.5f, %.5f, %.5f]}\n",
+          key.c_str(), e.stages, e.rows, e.ms[0], e.ms[1], e.ms[2], e.ms[3], e.ms[4], e.ms[5],
+          e.fd_fused[0], e.fd_fused[1], e.fd_ms[0], e.fd_ms[1], e.fd_ms[2], e.fd_ms[3]);
   fclose(f);
 }
 
@@ -85,7 +103,25 @@ void igafd_tune_lookup(igafd_patch *P) {
   if (it != g_tune.end()) {
     P->stencil_stages = it->second.stages;
     P->stencil_rows = it->second.rows;
+    P->fd_fused_op[0] = it->second.fd_fused[0];
+    P->fd_fused_op[1] = it->second.fd_fused[1];
   }
+}
+
+// Time `reps` tensor-core FD applies (after one untimed) of operand type dt
+// on the patch's residual buffer; ms per apply into *ms.
+static igafd_status time_fd(igafd_patch *P, igafd_dtype dt, cudaStream_t s, cudaEvent_t e0,
+                            cudaEvent_t e1, float *ms) {
+  constexpr int reps = 5;
+  IGAFD_TRY(igafd_fd_tc_apply(P, dt, P->r, P->z, s, nullptr));
+  IGAFD_CUDA(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) IGAFD_TRY(igafd_fd_tc_apply(P, dt, P->r, P->z, s, nullptr));
+  IGAFD_CUDA(cudaEventRecord(e1, s));
+  IGAFD_CUDA(cudaEventSynchronize(e1));
+  float t = 0.f;
+  IGAFD_CUDA(cudaEventElapsedTime(&t, e0, e1));
+  *ms = t / reps;
+  return IGAFD_OK;
 }
 
 extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) {
@@ -99,6 +135,8 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
     if (it != g_tune.end() && !(flags & 1)) {
       P->stencil_stages = it->second.stages;
       P->stencil_rows = it->second.rows;
+      P->fd_fused_op[0] = it->second.fd_fused[0];
+      P->fd_fused_op[1] = it->second.fd_fused[1];
       return IGAFD_OK;
     }
   }
@@ -132,15 +170,35 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
       best.rows = 1 + c / 3;
     }
   }
+  // tensor-core FD form per operand type (the fused form needs every n_k <= 128)
+  bool shape_ok = P->mixed != nullptr;
+  for (int k = 0; k < P->dim; ++k) shape_ok = shape_ok && P->n[k] <= 128;
+  const int saved_fused = P->fd_fused, saved_op[2] = {P->fd_fused_op[0], P->fd_fused_op[1]};
+  for (int i = 0; i < 4; ++i) best.fd_ms[i] = -1.0f;
+  best.fd_fused[0] = best.fd_fused[1] = shape_ok ? 1 : 0;
+  const igafd_dtype dts[2] = {IGAFD_TF32, IGAFD_BF16};
+  P->fd_fused = 1;
+  for (int o = 0; o < 2 && st == IGAFD_OK && shape_ok; ++o) {
+    for (int form = 0; form < 2 && st == IGAFD_OK; ++form) {
+      P->fd_fused_op[o] = form == 0 ? 1 : 0;
+      st = time_fd(P, dts[o], s, e0, e1, &best.fd_ms[2 * o + form]);
+    }
+    if (st == IGAFD_OK) best.fd_fused[o] = best.fd_ms[2 * o] <= best.fd_ms[2 * o + 1] ? 1 : 0;
+  }
+  P->fd_fused = saved_fused;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != IGAFD_OK) {
     P->stencil_stages = saved;
     P->stencil_rows = saved_rows;
+    P->fd_fused_op[0] = saved_op[0];
+    P->fd_fused_op[1] = saved_op[1];
     return st;
   }
   P->stencil_stages = best.stages;
   P->stencil_rows = best.rows;
+  P->fd_fused_op[0] = best.fd_fused[0];
+  P->fd_fused_op[1] = best.fd_fused[1];
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tune[key] = best;
   append_file_locked(key, best);
@@ -162,5 +220,6 @@ extern "C" igafd_status igafd_set_stencil_rows(igafd_patch *P, int rows) {
 extern "C" igafd_status igafd_set_fd_fused(igafd_patch *P, int fused) {
   if (!P || (fused != 0 && fused != 1)) return IGAFD_ERR_ARG;
   P->fd_fused = fused;
+  for (int o = 0; o < 3; ++o) P->fd_fused_op[o] = 1;   // an explicit choice overrides the autotuner
   return IGAFD_OK;
 }

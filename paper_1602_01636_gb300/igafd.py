@@ -49,7 +49,7 @@ class PatchInfo(C.Structure):
                 ("q_bound", C.c_double), ("setup_ms", C.c_double), ("eig_ms", C.c_double),
                 ("stencil_bytes", C.c_longlong), ("stencil_stages", C.c_int),
                 ("stencil_rows", C.c_int), ("eig_refined", C.c_int * 3),
-                ("eig_check", (C.c_double * 2) * 3)]
+                ("eig_check", (C.c_double * 2) * 3), ("fd_fused", C.c_int * 3)]
 
 
 class PCGOpts(C.Structure):
@@ -271,8 +271,10 @@ class Patch:
 
     def autotune(self, force=False):
         """Measure the stencil pipeline's candidates on this patch (ring depth,
-        and in 3D one or two rows per thread) and keep the fastest; returns the
-        chosen depth (`info.stencil_rows` holds the rows)."""
+        and in 3D one or two rows per thread) and the tensor-core FD's forms
+        (fused or one kernel per mode product, for TF32 and BF16) and keep the
+        fastest; returns the chosen depth (`info.stencil_rows` holds the rows,
+        `info.fd_fused` the FD form per operand type)."""
         _check(lib().igafd_autotune(self.h, int(bool(force)), _stream()), "autotune")
         self.info = self.query()
         return self.info.stencil_stages

@@ -372,6 +372,30 @@ def test_batched_solve_matches_single_solves(torch):
         p.close()
 
 
+def test_autotune_fd_form(torch):
+    """The autotuner times the fused and the per-mode tensor-core FD for TF32
+    and BF16 and keeps one per type; the apply then launches three kernels
+    (fused) or six (per mode), and its result meets the oracle bound."""
+    from paper_1602_01636_gb300 import igafd
+    prob = synth.Problem(3, (40, 33, 37), 3, [0.05, 0.02, -0.03])
+    patch = make_patch(prob)
+    disc = assemble.Discretization.from_problem(prob)
+    F = fd.FD([disc.pencil(k) for k in range(3)])
+    r = synth.random_vector(disc.N, 78)
+    zo = F.apply(r)
+    patch.autotune(force=True)
+    forms = list(patch.info.fd_fused)
+    assert forms[0] in (0, 1) and forms[1] in (0, 1) and forms[2] == 0
+    for i, dt in enumerate(["tf32", "bf16"]):
+        l0 = igafd.kernel_launches()
+        z = patch.apply_prec(to_dev(r), dtype=dt).cpu().numpy()
+        assert igafd.kernel_launches() - l0 == (3 if forms[i] else 6)
+        assert rel(z, zo) <= TC_TOL[dt]
+    patch.set_fd_fused(1)          # an explicit choice replaces the tuned one
+    assert list(patch.query().fd_fused)[:2] == [1, 1]
+    patch.close()
+
+
 def test_autotune_picks_a_candidate_and_every_depth_agrees(torch):
     """The autotuner keeps one of the measured configurations; every ring
     depth and both row counts per thread give bitwise the same product with A
