@@ -53,10 +53,13 @@ def parse():
                     help="learned span scalings: train on generated patches, compare on held-out ones")
     ap.add_argument("--sweep", action="store_true",
                     help="precision sweep: n in {128, 192}, p in {2..5}, every FD dtype")
-    ap.add_argument("--train", type=int, default=48)
+    ap.add_argument("--train", type=int, default=2000,
+                    help="--learned: training patches (the first --select of them choose the label scale)")
+    ap.add_argument("--select", type=int, default=48,
+                    help="--learned: training patches on which the label scale is chosen by PCG iterations")
     ap.add_argument("--no-refine", action="store_true",
                     help="--learned: skip the condition-estimate refinement of the labels")
-    ap.add_argument("--test", type=int, default=8)
+    ap.add_argument("--test", type=int, default=200)
     return ap.parse_args()
 
 
@@ -593,10 +596,11 @@ def run_learned(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     n, p = args.n if args.n != 128 else 96, args.p
 
-    def make(seed):
+    def make(seed, stencil=True):
         for attempt in range(50):     # re-draw folded geometries
             try:
-                return igafd.Patch.from_problem(synth.learned_workload_problem(seed + 100000 * attempt, n=n, p=p))
+                return igafd.Patch.from_problem(synth.learned_workload_problem(seed + 100000 * attempt, n=n, p=p),
+                                                stencil=stencil)
             except igafd.IgafdError as e:
                 if e.status != igafd.ERR_FOLDED:
                     raise
@@ -609,8 +613,10 @@ def run_learned(args):
             patch = make(100 + i)
             return patch, torch.from_numpy(synth.random_rhs(patch.N, i)).cuda()
         return build_item
-    X, T, gamma, totals, records = learned.build_dataset([maker(i) for i in range(args.train)],
-                                                         refine=not args.no_refine)
+    n_sel = min(args.select, args.train)
+    X, T, gamma, totals, records = learned.build_dataset(
+        [maker(i) for i in range(n_sel)], refine=not args.no_refine,
+        geo_makers=[(lambda i=i: make(100 + i, stencil=False)) for i in range(n_sel, args.train)])
     label_s = time.perf_counter() - t0
     t1 = time.perf_counter()
     net, losses = learned.train(X, T, synth.mlp_init(0), steps=2000)
@@ -648,8 +654,8 @@ def run_learned(args):
             "n_gpus": 1, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "randomly deformed cube (8^3 degree-3 net, sigma 0.15 spacing, binomial "
                                    "smoothing), kappa = exp(GRF, lengthscale 0.2) with contrast 100, N(0,1) RHS",
-                       "n": n, "p": p, "train_patches": args.train, "test_patches": args.test,
-                       "rows": int(X.shape[0])},
+                       "n": n, "p": p, "train_patches": args.train, "label_scale_selection_patches": n_sel,
+                       "test_patches": args.test, "rows": int(X.shape[0])},
             "plain_iterations_mean": mean(res["plain_it"]), "learned_iterations_mean": mean(res["learned_it"]),
             "plain_iterations": res["plain_it"], "learned_iterations": res["learned_it"],
             "plain_solve_s_mean": mean(res["plain_s"]), "learned_solve_s_mean": mean(res["learned_s"]),

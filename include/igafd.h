@@ -79,7 +79,17 @@ typedef struct {
   const int *kappa_n_knots;
   const double *const *kappa_knots;
   const double *kappa_ctrl;
+  int flags;                        /* 0, or IGAFD_SETUP_NO_STENCIL */
 } igafd_patch_desc;
+
+/* igafd_patch_desc.flags: build everything but the stiffness stencil (no
+ * (2p+1)^d x N array, no assembly). Such a patch answers the geometry and
+ * preconditioner calls (igafd_patch_query, igafd_get_eigen,
+ * igafd_apply_prec, igafd_patch_features, igafd_patch_sepfit,
+ * igafd_set_scalings, igafd_load_rhs_sine); the calls that need A
+ * (igafd_apply_A, igafd_pcg_solve, igafd_batch_pcg_solve, igafd_copy_stencil,
+ * igafd_autotune, igafd_pcg_condition_estimate) return IGAFD_ERR_ARG. */
+#define IGAFD_SETUP_NO_STENCIL 1
 
 typedef struct {
   int dim, p;

@@ -60,6 +60,7 @@ void free_patch(igafd_patch *P) {
   cudaFree(P->q); cudaFree(P->xt);
   cudaFree(P->partial); cudaFree(P->counter); cudaFree(P->scal); cudaFree(P->err_flag);
   cudaFree(P->eig_work); cudaFree(P->eig_jobs); cudaFree(P->coef);
+  cudaFree(P->lfeat); cudaFree(P->lybar);
   igafd_fd_tc_free(P);
   for (int i = 0; i < IGAFD_NEV; ++i)
     if (P->ev[i]) cudaEventDestroy(P->ev[i]);
@@ -88,7 +89,8 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
   IGAFD_TRY(alloc(&P->inv_lam, (size_t)N));
   IGAFD_TRY(alloc(&P->inv_lam32, (size_t)N));
   P->Np = igafd_stencil_row_stride(N);
-  IGAFD_TRY(alloc(&P->stencil, (size_t)P->n_off * P->Np));
+  const bool with_stencil = !(d->flags & IGAFD_SETUP_NO_STENCIL);
+  if (with_stencil) IGAFD_TRY(alloc(&P->stencil, (size_t)P->n_off * P->Np));
   IGAFD_TRY(alloc(&P->fd_a, (size_t)N));
   IGAFD_TRY(alloc(&P->fd_b, (size_t)N));
   IGAFD_TRY(alloc(&P->r, (size_t)N));
@@ -122,7 +124,7 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
   for (int i = 0; i < IGAFD_NEV; ++i) IGAFD_CUDA(cudaEventCreate(&P->ev[i]));
   IGAFD_CUDA(cudaMemsetAsync(P->counter, 0, 8 * sizeof(unsigned), s));
   IGAFD_CUDA(cudaMemsetAsync(P->scal, 0, (S_COUNT + 1) * sizeof(double), s));
-  IGAFD_TRY(igafd_setup_stencil(P, s));
+  if (with_stencil) IGAFD_TRY(igafd_setup_stencil(P, s));
   IGAFD_TRY(igafd_build_prec(P, s));
   igafd_tune_lookup(P);
   IGAFD_CUDA(cudaStreamSynchronize(s));
@@ -239,7 +241,7 @@ extern "C" igafd_status igafd_patch_query(const igafd_patch *P, igafd_patch_info
   info->q_bound = P->q_bound;
   info->setup_ms = P->setup_ms;
   info->eig_ms = P->eig_ms;
-  info->stencil_bytes = (long long)P->n_off * P->N * (long long)sizeof(double);
+  info->stencil_bytes = P->stencil ? (long long)P->n_off * P->N * (long long)sizeof(double) : 0;
   info->stencil_stages = P->stencil_stages > 0 ? P->stencil_stages : 4;
   info->stencil_rows = P->stencil_rows == 2 ? 2 : 1;
   for (int k = 0; k < 3; ++k) {
@@ -266,7 +268,7 @@ extern "C" igafd_status igafd_get_eigen(const igafd_patch *P, int k, double *U_h
 }
 
 extern "C" igafd_status igafd_copy_stencil(const igafd_patch *P, double *dst, void *stream) {
-  if (!P || !dst) return IGAFD_ERR_ARG;
+  if (!P || !dst || !P->stencil) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   IGAFD_CUDA(cudaMemcpy2DAsync(dst, P->N * sizeof(double), P->stencil, P->Np * sizeof(double),
                                P->N * sizeof(double), P->n_off, cudaMemcpyDeviceToDevice,

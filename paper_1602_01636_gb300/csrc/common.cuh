@@ -127,6 +127,9 @@ struct igafd_patch {
   double *eig_work;             // eigen-setup scratch (kept for re-setups)
   void *eig_jobs;
   int scaled;
+  float *lfeat;                 // learned scalings: per-span features [rows][6] (kept after the first request)
+  double *lybar;                // and slab means of log Q_jj [dim][rows]
+  int lstats_valid;
   cudaEvent_t ev[IGAFD_NEV];    // phase-timing events (PCG with timing on)
   // diagnostics
   double min_detJ, q_bound, setup_ms, eig_ms;

@@ -8,8 +8,13 @@
 // letting term k of P follow Q_kk: on the quadrature grid, term k carries the
 // factor wK_k(zeta_k) * prod_{l != k} wM_l(zeta_l). The separable fit chooses
 // log wK, log wM by least squares of log Q_kk against that additive model
-// (backfitting, one slab mean per update); it initialises the labels that a
-// small network learns to predict from per-span features of Q.
+// (backfitting); it initialises the labels that a small network learns to
+// predict from per-span features of Q. Each backfitting update of a span's
+// log-weight is the slab mean of log Q_kk minus the element means of the
+// other factors (every element carries the same number of quadrature points
+// in each direction), so one pass over the quadrature grid gives both the
+// features and the slab means Ybar[k][dir][e] of every log Q_kk, and the
+// sweeps run on those few numbers. The pass is done once per patch and kept.
 //
 // Rows: r <-> (direction k, span e), direction-major: r = sum_{l<k} nel_l + e.
 #include "common.cuh"
@@ -97,24 +102,35 @@ __device__ double block_total(double v, double *sh) {
   return t;
 }
 
-// Features of row (k, e): [log mean Q_kk, log mean of the other diagonal
-// entries, log min lambda_min(Q), log max lambda_max(Q), std of log Q_kk,
-// span centre], averages over the slab of quadrature points.
-__global__ void features_kernel(Slab S, const float *y, const double *const *knots,
-                                const int *const *spans, float *feat) {
+// One block per row (slab direction k, span e), one pass over the slab's
+// quadrature points:
+//  - features of the row: [log mean Q_kk, log mean of the other diagonal
+//    entries, log min lambda_min(Q), log max lambda_max(Q), std of log Q_kk,
+//    span centre];
+//  - ybar[j * rows + row]: the slab mean of log Q_jj for every j < dim.
+__global__ void slab_stats_kernel(Slab S, const float *y, const double *const *knots,
+                                  const int *const *spans, int rows, float *feat, double *ybar) {
   __shared__ double sh[32];
   const int k = blockIdx.y, e = blockIdx.x;
   if (e >= S.nel[k]) return;
   const long long nqp = S.nqp;
-  double sq = 0.0, so = 0.0, sl = 0.0, sl2 = 0.0, mn = 1e300, mx = -1e300;
+  double sq = 0.0, so = 0.0, sl2 = 0.0, mn = 1e300, mx = -1e300;
+  double sy[3] = {0.0, 0.0, 0.0};
   for_slab(S, k, e, [&](long long i) {
-    const double lq = y[k * nqp + i];
-    sq += exp(lq);
-    sl += lq;
-    sl2 += lq * lq;
-    double oth = 0.0;
-    for (int l = 0; l < S.dim; ++l)
-      if (l != k) oth += exp((double)y[l * nqp + i]);
+    float yj[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      if (j < S.dim) {
+        yj[j] = y[j * nqp + i];
+        sy[j] += yj[j];
+      }
+    const float lq = k == 0 ? yj[0] : k == 1 ? yj[1] : yj[2];
+    sq += expf(lq);
+    sl2 += (double)lq * lq;
+    float oth = 0.f;
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      if (l < S.dim && l != k) oth += expf(yj[l]);
     so += oth / (S.dim - 1);
     mn = fmin(mn, (double)y[S.dim * nqp + i]);
     mx = fmax(mx, (double)y[(S.dim + 1) * nqp + i]);
@@ -122,13 +138,14 @@ __global__ void features_kernel(Slab S, const float *y, const double *const *kno
   const double cnt = (double)S.nq * (double)(nqp / S.T[k]);
   sq = block_total(sq, sh);
   so = block_total(so, sh);
-  sl = block_total(sl, sh);
   sl2 = block_total(sl2, sh);
+  for (int j = 0; j < 3; ++j) sy[j] = block_total(sy[j], sh);
   mn = block_min(mn, sh);
   mx = -block_min(-mx, sh);
   if (threadIdx.x == 0) {
-    float *f = feat + (size_t)(S.row0[k] + e) * 6;
-    const double ml = sl / cnt;
+    const int row = S.row0[k] + e;
+    float *f = feat + (size_t)row * 6;
+    const double ml = (k == 0 ? sy[0] : k == 1 ? sy[1] : sy[2]) / cnt;
     f[0] = (float)log(sq / cnt);
     f[1] = (float)log(so / cnt);
     f[2] = (float)mn;
@@ -136,53 +153,53 @@ __global__ void features_kernel(Slab S, const float *y, const double *const *kno
     f[4] = (float)sqrt(fmax(0.0, sl2 / cnt - ml * ml));
     const int s = spans[k][e];
     f[5] = (float)(0.5 * (knots[k][s] + knots[k][s + 1]));
+    for (int j = 0; j < S.dim; ++j) ybar[(size_t)j * rows + row] = sy[j] / cnt;
   }
 }
 
-// One backfitting update for direction `dir`: mode 0 updates a_dir (log wK),
-// mode 1 updates m_dir (log wM); a, m: [rows] (direction-major), out: [rows].
-__global__ void backfit_kernel(Slab S, const float *y, const double *a, const double *m, int dir,
-                               int mode, double *out) {
-  __shared__ double sh[32];
-  const int e = blockIdx.x;
-  if (e >= S.nel[dir]) return;
-  const long long nqp = S.nqp;
-  double acc = 0.0;
-  for_slab(S, dir, e, [&](long long i) {
-    int el[3];
-    for (int l = 0; l < S.dim; ++l) el[l] = elem_of(S, i, l);
-    if (mode == 0) {
-      double r = y[dir * nqp + i];
-      for (int l = 0; l < S.dim; ++l)
-        if (l != dir) r -= m[S.row0[l] + el[l]];
-      acc += r;
-    } else {
-      double r = 0.0;
-      for (int k = 0; k < S.dim; ++k) {
-        if (k == dir) continue;
-        double rk = y[k * nqp + i] - a[S.row0[k] + el[k]];
-        for (int j = 0; j < S.dim; ++j)
-          if (j != k && j != dir) rk -= m[S.row0[j] + el[j]];
-        r += rk;
-      }
-      acc += r / (S.dim - 1);
-    }
-  });
-  acc = block_total(acc, sh);
-  if (threadIdx.x == 0) out[S.row0[dir] + e] = acc / ((double)S.nq * (double)(nqp / S.T[dir]));
-}
-
-// gauge: mean of each m_l is 0, absorbed into the a_k with k != l
-__global__ void gauge_kernel(Slab S, double *a, double *m) {
+// The backfitting sweeps on the slab means (one thread; a few hundred rows):
+// a_k(e) = Ybar[k][k][e] - sum_{l != k} mean(m_l), then for every l
+// m_l(e) = mean_{k != l} (Ybar[k][l][e] - mean(a_k) - sum_{j != k, l} mean(m_j)),
+// then the gauge (each m_l has mean 0, absorbed into the a_k, k != l).
+__global__ void sepfit_kernel(Slab S, const double *ybar, int rows, int sweeps, double *a,
+                              double *m) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int l = 0; l < S.dim; ++l) {
+  const int dim = S.dim;
+  auto mean = [&](const double *v, int l) {
     double c = 0.0;
-    for (int e = 0; e < S.nel[l]; ++e) c += m[S.row0[l] + e];
-    c /= S.nel[l];
-    for (int e = 0; e < S.nel[l]; ++e) m[S.row0[l] + e] -= c;
-    for (int k = 0; k < S.dim; ++k)
-      if (k != l)
-        for (int e = 0; e < S.nel[k]; ++e) a[S.row0[k] + e] += c;
+    for (int e = 0; e < S.nel[l]; ++e) c += v[S.row0[l] + e];
+    return c / S.nel[l];
+  };
+  for (int r = 0; r < rows; ++r) a[r] = m[r] = 0.0;
+  for (int it = 0; it < sweeps; ++it) {
+    for (int k = 0; k < dim; ++k) {
+      double mb = 0.0;
+      for (int l = 0; l < dim; ++l)
+        if (l != k) mb += mean(m, l);
+      for (int e = 0; e < S.nel[k]; ++e) a[S.row0[k] + e] = ybar[(size_t)k * rows + S.row0[k] + e] - mb;
+    }
+    for (int l = 0; l < dim; ++l) {
+      double rest = 0.0;      // sum over k != l of (mean(a_k) + sum_{j != k, l} mean(m_j))
+      for (int k = 0; k < dim; ++k) {
+        if (k == l) continue;
+        rest += mean(a, k);
+        for (int j = 0; j < dim; ++j)
+          if (j != k && j != l) rest += mean(m, j);
+      }
+      for (int e = 0; e < S.nel[l]; ++e) {
+        double acc = 0.0;
+        for (int k = 0; k < dim; ++k)
+          if (k != l) acc += ybar[(size_t)k * rows + S.row0[l] + e];
+        m[S.row0[l] + e] = (acc - rest) / (dim - 1);
+      }
+    }
+    for (int l = 0; l < dim; ++l) {
+      const double c = mean(m, l);
+      for (int e = 0; e < S.nel[l]; ++e) m[S.row0[l] + e] -= c;
+      for (int k = 0; k < dim; ++k)
+        if (k != l)
+          for (int e = 0; e < S.nel[k]; ++e) a[S.row0[k] + e] += c;
+    }
   }
 }
 
@@ -247,10 +264,19 @@ extern "C" igafd_status igafd_scaling_rows(const igafd_patch *P, int *rows) {
   return IGAFD_OK;
 }
 
-extern "C" igafd_status igafd_patch_features(igafd_patch *P, float *feat, void *stream) {
-  if (!P || !feat) return IGAFD_ERR_ARG;
-  IGAFD_CUDA(cudaSetDevice(P->dev));
-  cudaStream_t s = (cudaStream_t)stream;
+// Features and slab means of the patch's quadrature grid, computed on the
+// first request and kept (the geometry and the coefficient are fixed).
+static igafd_status ensure_stats(igafd_patch *P, cudaStream_t s) {
+  if (P->lstats_valid) return IGAFD_OK;
+  const int rows = rows_of(P);
+  if (!P->lfeat && cudaMalloc(&P->lfeat, (size_t)rows * 6 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return IGAFD_ERR_OOM;
+  }
+  if (!P->lybar && cudaMalloc(&P->lybar, (size_t)P->dim * rows * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return IGAFD_ERR_OOM;
+  }
   float *y = nullptr;
   long long nqp = 0;
   IGAFD_TRY(make_qdiag(P, s, &y, &nqp));
@@ -268,23 +294,33 @@ extern "C" igafd_status igafd_patch_features(igafd_patch *P, float *feat, void *
     cudaMemcpyAsync(dsp, sp, sizeof(sp), cudaMemcpyHostToDevice, s);
     int emax = 0;
     for (int k = 0; k < P->dim; ++k) emax = emax > P->nel[k] ? emax : P->nel[k];
-    features_kernel<<<dim3(emax, P->dim), 256, 0, s>>>(S, y, dkn, dsp, feat);
+    slab_stats_kernel<<<dim3(emax, P->dim), 256, 0, s>>>(S, y, dkn, dsp, rows, P->lfeat, P->lybar);
     IGAFD_LAUNCHED(1);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) st = IGAFD_ERR_CUDA;
   }
   cudaFree(dkn);
   cudaFree(dsp);
   cudaFree(y);
+  if (st == IGAFD_OK) P->lstats_valid = 1;
   return st;
+}
+
+extern "C" igafd_status igafd_patch_features(igafd_patch *P, float *feat, void *stream) {
+  if (!P || !feat) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(P->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  IGAFD_TRY(ensure_stats(P, s));
+  IGAFD_CUDA(cudaMemcpyAsync(feat, P->lfeat, (size_t)rows_of(P) * 6 * sizeof(float),
+                             cudaMemcpyDeviceToDevice, s));
+  IGAFD_CUDA(cudaStreamSynchronize(s));
+  return IGAFD_OK;
 }
 
 extern "C" igafd_status igafd_patch_sepfit(igafd_patch *P, int sweeps, float *logw, void *stream) {
   if (!P || !logw || sweeps < 1 || sweeps > 1000) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   cudaStream_t s = (cudaStream_t)stream;
-  float *y = nullptr;
-  long long nqp = 0;
-  IGAFD_TRY(make_qdiag(P, s, &y, &nqp));
+  IGAFD_TRY(ensure_stats(P, s));
   Slab S = make_slab(P);
   const int rows = rows_of(P);
   double *a = nullptr, *m = nullptr;
@@ -294,27 +330,14 @@ extern "C" igafd_status igafd_patch_sepfit(igafd_patch *P, int sweeps, float *lo
     cudaGetLastError();
     st = IGAFD_ERR_OOM;
   } else {
-    cudaMemsetAsync(a, 0, rows * sizeof(double), s);
-    cudaMemsetAsync(m, 0, rows * sizeof(double), s);
-    for (int it = 0; it < sweeps; ++it) {
-      for (int k = 0; k < P->dim; ++k) {
-        backfit_kernel<<<P->nel[k], 256, 0, s>>>(S, y, a, m, k, 0, a);
-        IGAFD_LAUNCHED(1);
-      }
-      for (int l = 0; l < P->dim; ++l) {
-        backfit_kernel<<<P->nel[l], 256, 0, s>>>(S, y, a, m, l, 1, m);
-        IGAFD_LAUNCHED(1);
-      }
-      gauge_kernel<<<1, 32, 0, s>>>(S, a, m);
-      IGAFD_LAUNCHED(1);
-    }
+    sepfit_kernel<<<1, 32, 0, s>>>(S, P->lybar, rows, sweeps, a, m);
+    IGAFD_LAUNCHED(1);
     pack_logw_kernel<<<(rows + 127) / 128, 128, 0, s>>>(a, m, rows, logw);
     IGAFD_LAUNCHED(1);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) st = IGAFD_ERR_CUDA;
   }
   cudaFree(a);
   cudaFree(m);
-  cudaFree(y);
   return st;
 }
 

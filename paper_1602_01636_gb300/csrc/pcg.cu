@@ -198,7 +198,7 @@ extern "C" igafd_status igafd_apply_prec(igafd_patch *P, igafd_dtype dt, const d
 }
 
 extern "C" igafd_status igafd_apply_A(igafd_patch *P, const double *x, double *y, void *stream) {
-  if (!P || !x || !y || x == y) return IGAFD_ERR_ARG;
+  if (!P || !x || !y || x == y || !P->stencil) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   return igafd_stencil_launch(P, x, y, nullptr, 0, 0, (cudaStream_t)stream);
 }
@@ -320,7 +320,7 @@ struct SolveState {
 // rho0 = (r0, z0), p0 = z0. Synchronises once (to read (b, b)).
 static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, const double *b,
                                 double *x, cudaStream_t s, SolveState &S) {
-  if (!P || !b || !x || b == x) return IGAFD_ERR_ARG;
+  if (!P || !b || !x || b == x || !P->stencil) return IGAFD_ERR_ARG;
   igafd_pcg_opts o;
   if (opts) o = *opts; else igafd_pcg_default_opts(&o);
   if (!(o.tol >= 0.0) || o.max_iter < 0 || o.check_every < 1 || o.true_every < 0)

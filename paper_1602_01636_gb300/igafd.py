@@ -40,7 +40,9 @@ class PatchDesc(C.Structure):
                 ("ctrl", C.POINTER(C.c_double)), ("kappa", C.c_double),
                 ("kappa_p", C.c_int), ("kappa_n_knots", C.POINTER(C.c_int)),
                 ("kappa_knots", C.POINTER(C.POINTER(C.c_double))),
-                ("kappa_ctrl", C.POINTER(C.c_double))]
+                ("kappa_ctrl", C.POINTER(C.c_double)), ("flags", C.c_int)]
+
+SETUP_NO_STENCIL = 1
 
 
 class PatchInfo(C.Structure):
@@ -209,9 +211,11 @@ def batch_pcg(patches, bs, xs=None, tol=1e-8, max_iter=1000, dtype="fp64", flexi
 class Patch:
     """A single-patch problem set up on the current CUDA device."""
 
-    def __init__(self, knots, p, ctrl, kappa=1.0, geo_knots=None, geo_p=None, kappa_field=None):
+    def __init__(self, knots, p, ctrl, kappa=1.0, geo_knots=None, geo_p=None, kappa_field=None,
+                 stencil=True):
         """kappa_field: optional (knots, degree, control values) of a positive
-        spline coefficient c(zeta); K = kappa * c."""
+        spline coefficient c(zeta); K = kappa * c. stencil=False builds the
+        patch without A (geometry, features, separable fit and P only)."""
         L = lib()
         dim = len(knots)
         geo_knots = knots if geo_knots is None else geo_knots
@@ -229,6 +233,7 @@ class Patch:
         d.geo_n_knots = (C.c_int * dim)(*[len(k) for k in gk])
         d.geo_knots = (dp * dim)(*[k.ctypes.data_as(dp) for k in gk])
         d.ctrl = ctrl.ctypes.data_as(dp)
+        d.flags = 0 if stencil else SETUP_NO_STENCIL
         if kappa_field is not None:
             kk, kpd, kc = kappa_field
             kk = [np.ascontiguousarray(k, dtype=np.float64) for k in kk]
@@ -247,13 +252,13 @@ class Patch:
         self.N = int(self.info.N)
 
     @classmethod
-    def from_problem(cls, prob):
+    def from_problem(cls, prob, stencil=True):
         kf = None
         if getattr(prob, "kappa_ctrl", None) is not None:
             kf = (prob.kappa_knots, prob.kappa_p, prob.kappa_ctrl)
         return cls(prob.knots, prob.p, prob.ctrl, prob.kappa,
                    geo_knots=getattr(prob, "geo_knots", None), geo_p=getattr(prob, "geo_p", None),
-                   kappa_field=kf)
+                   kappa_field=kf, stencil=stencil)
 
     def query(self):
         info = PatchInfo()

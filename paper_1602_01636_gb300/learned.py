@@ -104,12 +104,16 @@ def refine_label(patch, b, label, factors=(0.5, 0.75, 1.25, 1.5), steps=30, tol=
     return label, {"kappa": (k0, best), "its": (it0, it0)}
 
 
-def build_dataset(makers, refine=True):
+def build_dataset(makers, refine=True, geo_makers=()):
     """makers: list of callables, each returning a fresh (patch, b) of one
     training problem (patches are closed after use, so a large set never
-    holds all stencils at once; the refinement pass builds them again).
+    holds all stencils at once; the refinement pass builds them again); gamma
+    is selected on these by PCG iterations and their labels are refined.
+    geo_makers: callables returning a patch of a further training problem
+    built without the stencil (features and separable fit need only the
+    geometry); its label is the separable fit times the selected gamma.
     Returns (X [rows][6], T [rows][2], gamma, {gamma: total iterations over
-    the set}, per-patch refinement records)."""
+    the selection set}, per-patch refinement records)."""
     import torch
     Xs, fits, totals = [], [], {}
     for make in makers:
@@ -128,6 +132,11 @@ def build_dataset(makers, refine=True):
             labels[i], rec = refine_label(patch, b, labels[i])
             records.append(rec)
             patch.close()
+    for make in geo_makers:
+        patch = make()
+        Xs.append(patch.features())
+        labels.append(patch.sepfit() * gamma)
+        patch.close()
     return torch.cat(Xs), torch.cat(labels), gamma, totals, records
 
 

@@ -50,6 +50,24 @@ def test_features_and_sepfit_match_oracle(kcase):
     assert np.abs(lw - lwo).max() <= 1e-4
 
 
+def test_patch_without_stencil(kcase):
+    """A patch built without A gives the same features, separable fit and FD
+    apply as the full patch; the calls that need A return an argument error."""
+    from paper_1602_01636_gb300 import igafd
+    prob, disc, patch = kcase
+    g = igafd.Patch.from_problem(prob, stencil=False)
+    assert g.info.stencil_bytes == 0 and patch.info.stencil_bytes > 0
+    assert np.array_equal(g.features().cpu().numpy(), patch.features().cpu().numpy())
+    assert np.array_equal(g.sepfit().cpu().numpy(), patch.sepfit().cpu().numpy())
+    r = to_dev(synth.random_vector(disc.N, 5))
+    assert np.array_equal(g.apply_prec(r).cpu().numpy(), patch.apply_prec(r).cpu().numpy())
+    for call in (lambda: g.apply_A(r), lambda: g.pcg(r), lambda: g.stencil()):
+        with pytest.raises(igafd.IgafdError) as e:
+            call()
+        assert e.value.status == igafd.ERR_ARG
+    g.close()
+
+
 def test_scaled_preconditioner_matches_oracle_and_affine_pin(torch):
     a = np.array([1.0, 2.0, 0.5])
     prob = synth.Problem(3, (9, 8, 10), 2)
@@ -102,7 +120,14 @@ def test_trained_network_reduces_iterations_on_held_out_patches(torch):
             patch = make_patch(synth.learned_workload_problem(100 + seed, n=14, p=2))
             return patch, to_dev(synth.random_rhs(patch.N, seed))
         return make
-    X, T, gamma, totals, records = learned.build_dataset([maker(s) for s in range(16)])
+    from paper_1602_01636_gb300 import igafd
+
+    def geo(seed):      # further training patches, labelled from the geometry alone
+        return lambda: igafd.Patch.from_problem(synth.learned_workload_problem(100 + seed, n=14, p=2),
+                                                stencil=False)
+    X, T, gamma, totals, records = learned.build_dataset([maker(s) for s in range(16)],
+                                                         geo_makers=[geo(s) for s in range(16, 24)])
+    assert X.shape[0] == 24 * 3 * 14 and T.shape[0] == X.shape[0]    # 3 directions x 14 spans
     assert totals[gamma] <= totals[0.0]          # the labels beat the unscaled P
     # the condition-estimate refinement never costs iterations on its patch
     assert all(r["its"][1] <= r["its"][0] and r["kappa"][1] <= r["kappa"][0] for r in records)
