@@ -1107,6 +1107,12 @@ __global__ void __launch_bounds__(kT128, 1) fd128_kernel(FusedArgs a) {
     }
   } else if (tid == 0) {
     atomicExch(a.err, (int)IGAFD_ERR_TIMEOUT);
+    // a wait ran out: give the copies and MMAs this CTA issued a bounded
+    // chance to finish before shared memory and TMEM are released
+    wait_on(&bar_b1, 0);
+    wait_on(&bar_b2, 0);
+    wait_on(&bar_mma, 0);
+    wait_on(&bar_mma, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
