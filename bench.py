@@ -163,6 +163,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, world):
+    """The job's value of a per-rank time: the maximum over the ranks of the
+    process group (all-reduce on the group's device: CUDA tensors for NCCL,
+    host tensors for gloo). With one rank, x itself."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- our arm ------
 class Clocks:
     """nvidia-smi sampling during the timed region."""
@@ -345,11 +359,7 @@ def run_ours(args):
     barrier()
     ck = clocks.stop()
     launches = igafd.kernel_launches() - l0
-    ms_step = t0.elapsed_time(t1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, world)
     it_mixed = infos[-1].iterations
     # per-launch stencil time inside the timed (graph-replayed) solves, from the
     # stencil kernel's own device-clock stamps

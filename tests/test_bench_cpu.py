@@ -1,0 +1,73 @@
+"""CPU checks of bench.py's multi-rank path: the job's time is the maximum
+over the ranks of a process group (two gloo ranks on this host), and the
+reference arm runs on rank 0 only."""
+import contextlib
+import io
+import json
+import os
+import socket
+import sys
+import tempfile
+import types
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, values, out_dir):
+    import torch.distributed as dist
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        got = bench.max_over_ranks(values[rank], world)
+        with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+            json.dump({"rank": rank, "max": got}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    values = [3.25, 7.5]
+    with tempfile.TemporaryDirectory() as d:
+        mp.spawn(_rank_main, args=(2, _free_port(), values, d), nprocs=2, join=True)
+        got = [json.load(open(os.path.join(d, f"rank{r}.json")))["max"] for r in range(2)]
+    assert got == [max(values)] * 2
+
+
+def test_max_over_ranks_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(2.5, 1) == 2.5
+
+
+def _reference_args(gpus):
+    return types.SimpleNamespace(n=16, p=2, tol=1e-8, steps=1, warmup=0, gpus=gpus)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(_reference_args(2))
+    assert buf.getvalue() == ""          # the other ranks exit without work or output
+    monkeypatch.setenv("RANK", "0")
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(_reference_args(2))
+    lines = [l for l in buf.getvalue().splitlines() if l.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
