@@ -27,11 +27,169 @@ using namespace igafd_geom;
 
 namespace {
 
+// The features are FP32 logarithms of Q, so Q is evaluated in FP32 (GB300's
+// FP32 pipe is 64x its FP64 pipe; one pass covers every quadrature point):
+// FP32 copies of the geometry and coefficient tables, the map's Jacobian,
+// Q = kappa |det J| J^{-1} J^{-T} and the extreme eigenvalues of Q.
+struct PVf {
+  int gp, kp;
+  int nel[3], gm[3], km[3];
+  const float *gv[3], *gd[3], *kv[3];
+  const int *gspan[3], *kspan[3];
+  const float *ctrl, *kctrl;
+  float kappa;
+};
+
+template <int DIM>
+__device__ void jacobian_f(const PVf &v, const int *t, float (*J)[3]) {
+  const int gp = v.gp, ga = gp + 1;
+  const float *gv[3], *gd[3];
+  int g0[3];
+  for (int k = 0; k < DIM; ++k) {
+    gv[k] = v.gv[k] + (size_t)t[k] * ga;
+    gd[k] = v.gd[k] + (size_t)t[k] * ga;
+    g0[k] = v.gspan[k][t[k]] - gp;
+  }
+  for (int c = 0; c < DIM; ++c)
+    for (int j = 0; j < DIM; ++j) J[c][j] = 0.0f;
+  for (int c = 0; c < DIM; ++c) {
+    if (DIM == 2) {
+      const float *C = v.ctrl + (size_t)c * v.gm[0] * v.gm[1];
+      for (int a2 = 0; a2 < ga; ++a2) {
+        const float *row = C + (size_t)(g0[1] + a2) * v.gm[0] + g0[0];
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int a1 = 0; a1 < ga; ++a1) {
+          s0 += row[a1] * gv[0][a1];
+          s1 += row[a1] * gd[0][a1];
+        }
+        J[c][0] += s1 * gv[1][a2];
+        J[c][1] += s0 * gd[1][a2];
+      }
+    } else {
+      const float *C = v.ctrl + (size_t)c * v.gm[0] * v.gm[1] * v.gm[2];
+      for (int a3 = 0; a3 < ga; ++a3) {
+        const float v3 = gv[2][a3], d3 = gd[2][a3];
+        for (int a2 = 0; a2 < ga; ++a2) {
+          const float *row = C + ((size_t)(g0[2] + a3) * v.gm[1] + (g0[1] + a2)) * v.gm[0] + g0[0];
+          float s0 = 0.0f, s1 = 0.0f;
+          for (int a1 = 0; a1 < ga; ++a1) {
+            s0 += row[a1] * gv[0][a1];
+            s1 += row[a1] * gd[0][a1];
+          }
+          const float v2 = gv[1][a2], d2 = gd[1][a2];
+          J[c][0] += s1 * v2 * v3;
+          J[c][1] += s0 * d2 * v3;
+          J[c][2] += s0 * v2 * d3;
+        }
+      }
+    }
+  }
+}
+
+template <int DIM>
+__device__ float kappa_f(const PVf &v, const int *t) {
+  if (!v.kctrl) return v.kappa;
+  const int ka = v.kp + 1;
+  const float *kv[3];
+  int k0[3];
+  for (int k = 0; k < DIM; ++k) {
+    kv[k] = v.kv[k] + (size_t)t[k] * ka;
+    k0[k] = v.kspan[k][t[k]] - v.kp;
+  }
+  float acc = 0.0f;
+  if (DIM == 2) {
+    for (int a2 = 0; a2 < ka; ++a2) {
+      const float *row = v.kctrl + (size_t)(k0[1] + a2) * v.km[0] + k0[0];
+      float s0 = 0.0f;
+      for (int a1 = 0; a1 < ka; ++a1) s0 += row[a1] * kv[0][a1];
+      acc += s0 * kv[1][a2];
+    }
+  } else {
+    for (int a3 = 0; a3 < ka; ++a3)
+      for (int a2 = 0; a2 < ka; ++a2) {
+        const float *row = v.kctrl + ((size_t)(k0[2] + a3) * v.km[1] + (k0[1] + a2)) * v.km[0] + k0[0];
+        float s0 = 0.0f;
+        for (int a1 = 0; a1 < ka; ++a1) s0 += row[a1] * kv[0][a1];
+        acc += s0 * kv[1][a2] * kv[2][a3];
+      }
+  }
+  return v.kappa * acc;
+}
+
+// Q = kappa |det J| J^{-1} J^{-T}, stored 2D [00, 11, 01], 3D [00, 11, 22, 01, 02, 12]
+template <int DIM>
+__device__ void q_f(const float (*J)[3], float kappa, float *Q) {
+  if (DIM == 2) {
+    const float det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const float id = 1.0f / det;
+    const float a = J[1][1] * id, b = -J[0][1] * id, c = -J[1][0] * id, d = J[0][0] * id;
+    const float sc = kappa * fabsf(det);
+    Q[0] = sc * (a * a + b * b);
+    Q[1] = sc * (c * c + d * d);
+    Q[2] = sc * (a * c + b * d);
+  } else {
+    float Ji[3][3];
+    const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const float c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const float c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const float det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const float id = 1.0f / det;
+    Ji[0][0] = c00 * id;
+    Ji[1][0] = c01 * id;
+    Ji[2][0] = c02 * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    const float sc = kappa * fabsf(det);
+    const int rr[6] = {0, 1, 2, 0, 0, 1}, ss[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc += Ji[rr[q]][c] * Ji[ss[q]][c];
+      Q[q] = sc * acc;
+    }
+  }
+}
+
+// extreme eigenvalues of the symmetric Q (closed form: the 2x2 formula, and
+// for 3x3 the trigonometric solution of the characteristic cubic)
+template <int DIM>
+__device__ void extremes_f(const float *Q, float *lmin, float *lmax) {
+  if (DIM == 2) {
+    const float m = 0.5f * (Q[0] + Q[1]);
+    const float d = sqrtf(0.25f * (Q[0] - Q[1]) * (Q[0] - Q[1]) + Q[2] * Q[2]);
+    *lmin = m - d;
+    *lmax = m + d;
+  } else {
+    const float a = Q[0], b = Q[1], c = Q[2], d = Q[3], e = Q[5], f = Q[4];
+    const float p1 = d * d + f * f + e * e;
+    const float q = (a + b + c) * (1.0f / 3.0f);
+    const float p2 = (a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + 2.0f * p1;
+    const float pp = sqrtf(p2 * (1.0f / 6.0f));
+    if (!(pp > 1e-30f * fabsf(q))) {
+      *lmin = *lmax = q;
+      return;
+    }
+    const float ip = 1.0f / pp;
+    const float B00 = (a - q) * ip, B11 = (b - q) * ip, B22 = (c - q) * ip;
+    const float B01 = d * ip, B02 = f * ip, B12 = e * ip;
+    const float detB = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) +
+                       B02 * (B01 * B12 - B11 * B02);
+    const float r = fminf(1.0f, fmaxf(-1.0f, 0.5f * detB));
+    const float phi = acosf(r) * (1.0f / 3.0f);
+    *lmax = q + 2.0f * pp * cosf(phi);
+    *lmin = q + 2.0f * pp * cosf(phi + 2.0943951f);   // + 2 pi / 3
+  }
+}
+
 // Per quadrature point: log Q_kk (k < DIM), log lambda_min(Q), log lambda_max(Q).
 // Layout y[c][t3][t2][t1] (global 1D quadrature indices, direction 1 fastest).
 template <int DIM>
-__global__ void qdiag_kernel(PV v, long long nqp, float *y) {
-  const int nq = v.nq;
+__global__ void qdiag_kernel(PVf v, int nq, long long nqp, float *y) {
   const long long T1 = (long long)v.nel[0] * nq, T2 = (long long)v.nel[1] * nq;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nqp;
        i += (long long)gridDim.x * blockDim.x) {
@@ -39,15 +197,21 @@ __global__ void qdiag_kernel(PV v, long long nqp, float *y) {
     t[0] = (int)(i % T1);
     t[1] = (int)((i / T1) % T2);
     t[2] = DIM == 3 ? (int)(i / (T1 * T2)) : 0;
-    double x[3], J[3][3], Q[6];
-    geo_eval<DIM>(v, t, x, J);
-    q_from_J<DIM>(J, kappa_eval<DIM>(v, t), Q);
-    for (int k = 0; k < DIM; ++k) y[k * nqp + i] = (float)log(Q[k]);
-    double lo, hi;
-    sym_eig_extremes<DIM>(Q, &lo, &hi);
-    y[DIM * nqp + i] = (float)log(fmax(lo, 1e-300));
-    y[(DIM + 1) * nqp + i] = (float)log(hi);
+    float J[3][3], Q[6];
+    jacobian_f<DIM>(v, t, J);
+    q_f<DIM>(J, kappa_f<DIM>(v, t), Q);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) y[k * nqp + i] = logf(Q[k]);
+    float lo, hi;
+    extremes_f<DIM>(Q, &lo, &hi);
+    y[DIM * nqp + i] = logf(fmaxf(lo, 1e-30f));
+    y[(DIM + 1) * nqp + i] = logf(hi);
   }
+}
+
+__global__ void narrow_kernel(const double *a, float *b, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
 }
 
 struct Slab {
@@ -240,17 +404,55 @@ int rows_of(const igafd_patch *P) {
   return r;
 }
 
-// log-diagonal table of Q on the quadrature grid (allocated here, freed by caller)
-igafd_status make_qdiag(igafd_patch *P, cudaStream_t s, float **y, long long *nqp) {
+// log-diagonal table of Q on the quadrature grid (allocated here, freed by
+// the caller together with *tables, the FP32 copies of the patch tables)
+igafd_status make_qdiag(igafd_patch *P, cudaStream_t s, float **y, long long *nqp, float **tables) {
   Slab S = make_slab(P);
   *nqp = S.nqp;
-  if (cudaMalloc(y, (size_t)(P->dim + 2) * S.nqp * sizeof(float)) != cudaSuccess) {
+  *y = nullptr;
+  *tables = nullptr;
+  const int dim = P->dim, nq = P->p + 1, ga = P->geo_p + 1, ka = P->kappa_p + 1;
+  const bool kf = P->kctrl != nullptr;
+  long long nctrl = dim, nkc = 1, tot = 0;
+  for (int k = 0; k < dim; ++k) {
+    nctrl *= P->dir[k].gm;
+    nkc *= kf ? P->dir[k].km : 1;
+    tot += 2LL * P->nel[k] * nq * ga + (kf ? (long long)P->nel[k] * nq * ka : 0);
+  }
+  tot += nctrl + (kf ? nkc : 0);
+  if (cudaMalloc(y, (size_t)(dim + 2) * S.nqp * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(tables, (size_t)tot * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     return IGAFD_ERR_OOM;
   }
-  PV v = make_view(P);
-  if (P->dim == 3) qdiag_kernel<3><<<P->num_sms * 8, 256, 0, s>>>(v, S.nqp, *y);
-  else qdiag_kernel<2><<<P->num_sms * 8, 256, 0, s>>>(v, S.nqp, *y);
+  PVf v{};
+  v.gp = P->geo_p; v.kp = P->kappa_p; v.kappa = (float)P->kappa;
+  float *f = *tables;
+  auto narrow = [&](const double *src, long long n) -> const float * {
+    narrow_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, f, n);
+    IGAFD_LAUNCHED(1);
+    const float *out = f;
+    f += n;
+    return out;
+  };
+  for (int k = 0; k < 3; ++k) {
+    v.nel[k] = k < dim ? P->nel[k] : 1;
+    v.gm[k] = P->dir[k].gm;
+    v.km[k] = P->dir[k].km;
+    if (k >= dim) continue;
+    const long long nt = (long long)P->nel[k] * nq;
+    v.gv[k] = narrow(P->dir[k].gv, nt * ga);
+    v.gd[k] = narrow(P->dir[k].gd, nt * ga);
+    v.gspan[k] = P->dir[k].gspan;
+    if (kf) {
+      v.kv[k] = narrow(P->dir[k].kv, nt * ka);
+      v.kspan[k] = P->dir[k].kspan;
+    }
+  }
+  v.ctrl = narrow(P->ctrl, nctrl);
+  v.kctrl = kf ? narrow(P->kctrl, nkc) : nullptr;
+  if (dim == 3) qdiag_kernel<3><<<P->num_sms * 8, 256, 0, s>>>(v, nq, S.nqp, *y);
+  else qdiag_kernel<2><<<P->num_sms * 8, 256, 0, s>>>(v, nq, S.nqp, *y);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
@@ -277,9 +479,14 @@ static igafd_status ensure_stats(igafd_patch *P, cudaStream_t s) {
     cudaGetLastError();
     return IGAFD_ERR_OOM;
   }
-  float *y = nullptr;
+  float *y = nullptr, *tables = nullptr;
   long long nqp = 0;
-  IGAFD_TRY(make_qdiag(P, s, &y, &nqp));
+  igafd_status qs = make_qdiag(P, s, &y, &nqp, &tables);
+  if (qs != IGAFD_OK) {
+    cudaFree(y);
+    cudaFree(tables);
+    return qs;
+  }
   Slab S = make_slab(P);
   const double *kn[3] = {P->dir[0].knots, P->dir[1].knots, P->dir[2].knots};
   const int *sp[3] = {P->dir[0].span, P->dir[1].span, P->dir[2].span};
@@ -301,6 +508,7 @@ static igafd_status ensure_stats(igafd_patch *P, cudaStream_t s) {
   cudaFree(dkn);
   cudaFree(dsp);
   cudaFree(y);
+  cudaFree(tables);
   if (st == IGAFD_OK) P->lstats_valid = 1;
   return st;
 }
