@@ -240,6 +240,65 @@ def test_pcg_matches_direct_solve():
     assert r5.iters == 5 and np.allclose(r5.history[:6], res.history[:6], rtol=1e-12)
 
 
+def test_flexible_beta_equals_fletcher_reeves_for_exact_preconditioner():
+    """With a fixed SPD preconditioner (the exact FD), (r_{k+1}, z_k) = 0 in
+    exact arithmetic, so the flexible beta (r_{k+1}, z_{k+1} - z_k)/(r_k, z_k)
+    equals the Fletcher-Reeves one and the iterates agree to rounding."""
+    disc = _disc(synth.Problem(3, (8, 7, 6), 3, [0.1, -0.06, 0.04]))
+    A = assemble.stencil_to_csr(disc, disc.assemble_stencil())
+    b = synth.random_rhs(disc.N, 41)
+    F = fd.FD([disc.pencil(k) for k in range(3)])
+    fr = pcg.pcg(lambda v: A @ v, b, F.apply, fixed_iters=8)
+    fl = pcg.pcg(lambda v: A @ v, b, F.apply, fixed_iters=8, flexible=True)
+    assert np.linalg.norm(fl.x - fr.x) <= 1e-9 * np.linalg.norm(fr.x)
+    assert np.allclose(fl.betas, fr.betas, rtol=1e-6, atol=1e-12)
+
+
+def _round_mantissa(v, bits):
+    m, e = np.frexp(v)
+    s = 2.0 ** bits
+    return np.ldexp(np.round(m * s) / s, e)
+
+
+def test_flexible_beta_with_a_low_precision_preconditioner():
+    """The FD applied through rounding of its input and output to a few
+    mantissa bits (a stand-in for low-precision operands) is no longer a fixed
+    linear operator, and (r_{k+1}, z_k) is no longer ~0. PCG with the flexible
+    beta (r_{k+1}, z_{k+1} - z_k)/(r_k, z_k) still reaches the direct solution
+    within two iterations of the exact FD at 8 bits, and at 3 bits it needs far
+    fewer iterations than Fletcher-Reeves (a wrong sign in the formula makes
+    the 8-bit run stall)."""
+    disc = _disc(synth.Problem(3, (9, 8, 7), 3, [0.1, -0.06, 0.04]))
+    A = assemble.stencil_to_csr(disc, disc.assemble_stencil())
+    b = synth.random_rhs(disc.N, 42)
+    F = fd.FD([disc.pencil(k) for k in range(3)])
+    x = np.linalg.solve(A.toarray(), b)
+    exact = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-10, max_iter=300)
+
+    def rounded(bits):
+        return lambda r: _round_mantissa(F.apply(_round_mantissa(r, bits)), bits)
+    flex8 = pcg.pcg(lambda v: A @ v, b, rounded(8), tol=1e-10, max_iter=300, flexible=True)
+    assert flex8.converged and flex8.iters <= exact.iters + 2
+    assert np.linalg.norm(flex8.x - x) <= 1e-8 * np.linalg.norm(x)
+    flex3 = pcg.pcg(lambda v: A @ v, b, rounded(3), tol=1e-10, max_iter=300, flexible=True)
+    fr3 = pcg.pcg(lambda v: A @ v, b, rounded(3), tol=1e-10, max_iter=300, flexible=False)
+    assert flex3.converged and flex3.iters < 0.6 * fr3.iters
+
+
+def test_planted_flexible_sign_fails_low_precision_pin(monkeypatch):
+    """A sign error planted in the oracle's flexible beta, (r_{k+1}, z_{k+1} +
+    z_k), passes with the exact FD (where (r_{k+1}, z_k) ~ 0) but fails the
+    low-precision pin above."""
+    import inspect
+    src = inspect.getsource(pcg.pcg).replace("(r @ (zn - z)) / rho", "(r @ (zn + z)) / rho")
+    assert src != inspect.getsource(pcg.pcg)
+    ns = {}
+    exec(src, pcg.__dict__, ns)
+    monkeypatch.setattr(pcg, "pcg", ns["pcg"])
+    with pytest.raises(AssertionError):
+        test_flexible_beta_with_a_low_precision_preconditioner()
+
+
 def test_prop1_condition_bound():
     pr = synth.Problem(3, 6, 2, [0.1, -0.08, 0.05])
     disc = _disc(pr)
