@@ -163,6 +163,49 @@ def test_identity_map_A_equals_P(dim, n, p):
     assert np.abs(A - disc.dense_P()).max() <= 1e-14 * np.abs(A).max()
 
 
+def _weighted_1d(knots, p, weight):
+    """1D stiffness and mass matrices of the Dirichlet-reduced basis with the
+    weight function weight(z), by a 10-point Gauss rule per element (exact
+    for the polynomial weights used here)."""
+    xg, wg = np.polynomial.legendre.leggauss(10)
+    K = M = 0.0
+    for s in spline.elements(knots):
+        a, b = knots[s], knots[s + 1]
+        z = 0.5 * (b - a) * xg + 0.5 * (a + b)
+        w = 0.5 * (b - a) * wg * weight(z)
+        B = spline.basis_table(knots, p, z)[:, 1:-1]
+        D = spline.basis_table(knots, p, z, deriv=True)[:, 1:-1]
+        K = K + D.T @ (w[:, None] * D)
+        M = M + B.T @ (w[:, None] * B)
+    return K, M
+
+
+def test_variable_coefficient_linear_in_zeta1():
+    """Identity map, coefficient kappa = 1 + zeta_1 (a degree-1 spline field):
+    A is the Kronecker sum of 1D matrices with the weight 1 + z along
+    direction 1, K1w (x) M2 (x) M3 + M1w (x) K2 (x) M3 + M1w (x) M2 (x) K3
+    (direction 1 fastest), built here from 1D integrals alone."""
+    p, n = 2, (6, 5, 4)
+    pr = synth.Problem(3, n, p)
+    pr.kappa_knots = [np.array([0.0, 0.0, 1.0, 1.0])] * 3
+    pr.kappa_p = 1
+    ctrl = np.ones((2, 2, 2))
+    ctrl[:, :, 1] = 2.0                   # value 1 at zeta_1 = 0, 2 at zeta_1 = 1
+    pr.kappa_ctrl = ctrl
+    disc = _disc(pr)
+    A = assemble.stencil_to_csr(disc, disc.assemble_stencil()).toarray()
+    K1, M1 = _weighted_1d(pr.knots[0], p, lambda z: 1.0 + z)
+    K2, M2 = _weighted_1d(pr.knots[1], p, lambda z: np.ones_like(z))
+    K3, M3 = _weighted_1d(pr.knots[2], p, lambda z: np.ones_like(z))
+    kron3 = lambda c, b, a: np.kron(c, np.kron(b, a))
+    Ak = kron3(M3, M2, K1) + kron3(M3, K2, M1) + kron3(K3, M2, M1)
+    assert np.abs(A - Ak).max() <= 1e-13 * np.abs(Ak).max()
+    # the weight matters: the unweighted Kronecker sum differs
+    K1u, M1u = _weighted_1d(pr.knots[0], p, lambda z: np.ones_like(z))
+    Au = kron3(M3, M2, K1u) + kron3(M3, K2, M1u) + kron3(K3, M2, M1u)
+    assert np.abs(A - Au).max() > 1e-3 * np.abs(Ak).max()
+
+
 def test_affine_map_closed_form():
     a = np.array([1.0, 2.0, 0.5])
     pr = synth.Problem(3, (5, 4, 6), 2)
