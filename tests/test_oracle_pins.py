@@ -206,6 +206,31 @@ def test_variable_coefficient_linear_in_zeta1():
     assert np.abs(A - Au).max() > 1e-3 * np.abs(Ak).max()
 
 
+def test_rhs_identity_map_separable_load():
+    """Identity map, f = 1 + 2 x: b_i = int (1 + 2 zeta_1) B_i = (I_1 + 2 X_1)
+    (x) I_2 (x) I_3 (direction 1 fastest), with I_k the integrals and X_1 the
+    first moments of the Dirichlet-reduced 1D B-splines (closed form
+    (xi_{i+p+1} - xi_i)/(p+1) for the integrals)."""
+    p, n = 3, (7, 5, 6)
+    pr = synth.Problem(3, n, p)
+    disc = _disc(pr)
+    b = disc.assemble_rhs(lambda x, y, z: 1.0 + 2.0 * x + 0.0 * y * z)
+    ints = []
+    for k in range(3):
+        xi = pr.knots[k]
+        m = len(xi) - p - 1
+        ints.append(np.array([(xi[i + p + 1] - xi[i]) / (p + 1) for i in range(1, m - 1)]))
+    xg, wg = np.polynomial.legendre.leggauss(10)
+    X1 = 0.0
+    xi = pr.knots[0]
+    for s_ in spline.elements(xi):
+        a_, b_ = xi[s_], xi[s_ + 1]
+        z = 0.5 * (b_ - a_) * xg + 0.5 * (a_ + b_)
+        X1 = X1 + (0.5 * (b_ - a_) * wg * z) @ spline.basis_table(xi, p, z)[:, 1:-1]
+    bk = np.kron(ints[2], np.kron(ints[1], ints[0] + 2.0 * X1))
+    assert np.abs(b - bk).max() <= 1e-14 * np.abs(bk).max()
+
+
 def test_affine_map_closed_form():
     a = np.array([1.0, 2.0, 0.5])
     pr = synth.Problem(3, (5, 4, 6), 2)
