@@ -35,6 +35,8 @@
 // eigenpairs are computed once and copied.
 #include "common.cuh"
 
+#include <atomic>
+
 #include <vector>
 
 namespace {
@@ -1160,12 +1162,14 @@ igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const doubl
   const int allow_fast = P->eig_route != 1;
   {
     // FP32 start (or the route choice) for every pencil
-    static bool attr = false;
+    // the shared-memory limit is a per-device attribute of the kernel: set once per device
+    static std::atomic<unsigned long long> attr_set{0};
+    const unsigned long long bit = 1ull << (P->dev & 63);
     const size_t smem32 = tri32_smem_floats(kFastMaxN) * sizeof(float);
-    if (!attr) {
+    if (!(attr_set.load() & bit)) {
       IGAFD_CUDA(cudaFuncSetAttribute(tri32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem32));
-      attr = true;
+      attr_set.fetch_or(bit);
     }
     tri32_kernel<<<nj, 1024, smem32, s>>>(djobs, allow_fast);
     IGAFD_LAUNCHED(1);

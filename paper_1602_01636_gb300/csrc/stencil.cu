@@ -19,6 +19,8 @@
 // deterministic last-block reduction.
 #include "common.cuh"
 
+#include <atomic>
+
 namespace {
 
 constexpr int kTile = 256;                        // rows per tile
@@ -347,13 +349,21 @@ igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, c
   const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
   constexpr int kBlock = kTile / R + 32;
   auto kern = stencil_tma_kernel<DIM, P, MODE, kStages, R>;
-  static int per_sm = 0;   // resident CTAs per SM for this instantiation
-  if (per_sm == 0) {
+  // the shared-memory limit is a per-device attribute of the kernel: set (and
+  // the resident CTAs per SM measured) once per device
+  static std::atomic<unsigned long long> attr_set{0};
+  static std::atomic<int> per_sm_of[64];
+  int dev = 0;
+  IGAFD_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_set.load() & bit)) {
     IGAFD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb = 0;
     IGAFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBlock, smem));
-    per_sm = nb > 0 ? nb : 1;
+    per_sm_of[dev & 63].store(nb > 0 ? nb : 1);
+    attr_set.fetch_or(bit);
   }
+  const int per_sm = per_sm_of[dev & 63].load();
   long long grid = (long long)num_sms * per_sm;
   if (grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
