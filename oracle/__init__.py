@@ -21,7 +21,9 @@ Modules
   pcg       preconditioned conjugate gradients (the paper's outer solver)
   learned   span scalings of the pencils: features of Q, separable log-fit,
             and the scaling network with its gradient
+  adi       Algorithms 2 and 4: two- and three-variable ADI solvers of
+            P s = r, their parameters and error operators
 
 Readings where the paper is silent or garbled are stated at each function.
 """
-from . import spline, assemble, fd, pcg, learned  # noqa: F401
+from . import spline, assemble, fd, pcg, learned, adi  # noqa: F401
