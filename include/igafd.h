@@ -375,6 +375,45 @@ igafd_status igafd_mlp_gradient(igafd_mlp *mlp, const float *X_dev, const float 
 igafd_status igafd_mlp_train_step(igafd_mlp *mlp, const float *X_dev, const float *T_dev,
                                   int rows, float lr, float *loss_host, void *stream);
 
+/* ---- Three-variable ADI preconditioner (Section 5.2, Algorithm 4) ------
+ * An alternative to the fast-diagonalization P^{-1}: J iterations of the
+ * Douglas scheme of Eq. (ADI3D), from s_0 = 0, on the same pencils (span-
+ * scaled when scalings are set at the time of igafd_adi_setup), give
+ * z = P_J^{-1} r with P_J symmetric positive definite and
+ * kappa(P_J^{-1} A) <= (1 + eps)/(1 - eps) kappa(P^{-1} A) when rho_J <= eps
+ * (Theorem 1 and its 3D analogue). 3D patches only, n_k <= 256. */
+
+/* Greedy parameters of Eqs. (greedy1)-(greedy2) over the triples of
+ * eigenvalues of M_k^{-1} K_k (the patch's D_k): omega_host[0..*J-1] get
+ * w_1.., *J the first count with rho_J = max over the triples of
+ * |prod_j g(w_j; l)| <= eps, g(w; l) = 1 - 2 w^2 (l1 + l2 + l3) /
+ * ((w + l1)(w + l2)(w + l3)). The first parameter minimises |g| at the
+ * triple of smallest eigenvalues; each later one minimises |g| at the triple
+ * where the product is largest (first in i3, i2, i1 order); where |g| has
+ * two zeros, the one giving the smaller rho is taken. omega_host must hold
+ * max_J values; 0 < eps < 1. Runs on the host (O(J n1 n2 n3)); synchronises
+ * the device. Returns IGAFD_ERR_NOT_CONVERGED (with *J = max_J) when max_J
+ * parameters do not reach eps. */
+igafd_status igafd_adi_parameters(igafd_patch *patch, double eps, int max_J,
+                                  double *omega_host, int *J);
+
+/* Set up the ADI preconditioner with parameters omega_host[0..J-1] (> 0):
+ * banded pencils and the banded Cholesky factors of K_k + w_j M_k and of M_k
+ * for every direction and parameter, and 6 N-vectors of scratch (the
+ * library's only allocation for ADI). dtype IGAFD_FP64 (the paper's
+ * arithmetic) or IGAFD_FP32 (FP32 scratch, factors and arithmetic; an
+ * inexact P_J). Replaces an earlier ADI set-up; synchronises the stream.
+ * IGAFD_ERR_NOT_SPD if a factorisation fails. */
+igafd_status igafd_adi_setup(igafd_patch *patch, const double *omega_host, int J,
+                             igafd_dtype dtype, void *stream);
+
+/* z = P_J^{-1} r by J Douglas iterations (Algorithm 4): per iteration four
+ * kernels of independent banded line problems along directions 2, 1, 2, 3
+ * (4J + 1 launches in all). r_dev, z_dev: length-N FP64 device vectors, not
+ * overlapping. IGAFD_ERR_ARG without igafd_adi_setup. */
+igafd_status igafd_apply_prec_adi(igafd_patch *patch, const double *r_dev,
+                                  double *z_dev, void *stream);
+
 /* Number of kernels this library has enqueued in this process so far (all
  * devices, all patches); for launch accounting by benchmarks. */
 long long igafd_kernel_launches(void);

@@ -62,6 +62,7 @@ void free_patch(igafd_patch *P) {
   cudaFree(P->eig_work); cudaFree(P->eig_jobs); cudaFree(P->coef);
   cudaFree(P->lfeat); cudaFree(P->lybar);
   igafd_fd_tc_free(P);
+  igafd_adi_free(P);
   for (int i = 0; i < IGAFD_NEV; ++i)
     if (P->ev[i]) cudaEventDestroy(P->ev[i]);
   if (P->host_scal) cudaFreeHost(P->host_scal);

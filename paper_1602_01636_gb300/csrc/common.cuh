@@ -134,6 +134,7 @@ struct igafd_patch {
   // diagnostics
   double min_detJ, q_bound, setup_ms, eig_ms;
   int *err_flag;                // device error flags from setup kernels
+  void *adi;                    // three-variable ADI preconditioner state (adi.cu), or null
 };
 
 // Reductions: fixed-size partial arrays, deterministic order.
@@ -148,6 +149,10 @@ igafd_status igafd_build_prec(igafd_patch *P, cudaStream_t s);
 igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const double *const *wK = nullptr,
                                      const double *const *wM = nullptr);
 igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s);
+// dense (Dirichlet-reduced) pencils K_k, M_k of direction k into K, M (n_k x
+// n_k each, device), span-scaled when the patch carries scalings
+igafd_status igafd_pencils_dense(igafd_patch *P, int k, double *K, double *M, cudaStream_t s);
+void igafd_adi_free(igafd_patch *P);   // releases the ADI state (adi.cu)
 // FD apply; kernels do nothing while *done_flag != 0 (done_flag may be null)
 igafd_status igafd_fd64_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
                               double *done_flag);

@@ -1099,6 +1099,18 @@ static GemmJob gemm_job(int n, int transA, const double *A, const double *B, con
   return g;
 }
 
+igafd_status igafd_pencils_dense(igafd_patch *P, int k, double *K, double *M, cudaStream_t s) {
+  const int n = P->n[k], p = P->p;
+  IGAFD_CUDA(cudaMemsetAsync(K, 0, (size_t)n * n * sizeof(double), s));
+  IGAFD_CUDA(cudaMemsetAsync(M, 0, (size_t)n * n * sizeof(double), s));
+  const int th = n * (2 * p + 1);
+  pencil_kernel<<<(th + 127) / 128, 128, 0, s>>>(P->dir[k], p, K, M, P->scaled ? P->wK[k] : nullptr,
+                                                 P->scaled ? P->wM[k] : nullptr);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
+  return IGAFD_OK;
+}
+
 igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const double *const *wK,
                                      const double *const *wM) {
   const int dim = P->dim, p = P->p;

@@ -76,7 +76,8 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_pcg_condition_estimate", "igafd_lanczos_extremes", "igafd_set_fd_fused", "igafd_scaling_rows", "igafd_patch_features",
            "igafd_patch_sepfit", "igafd_set_scalings", "igafd_mlp_create", "igafd_mlp_destroy",
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
-           "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step"]
+           "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step",
+           "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi"]
 
 MLP_PARAMS = 4738
 
@@ -126,6 +127,9 @@ def lib():
     L.igafd_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
     L.igafd_mlp_gradient.argtypes = [vp, vp, vp, C.c_int, fp, fp, vp]
     L.igafd_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, fp, vp]
+    L.igafd_adi_parameters.argtypes = [vp, C.c_double, C.c_int, dp, C.POINTER(C.c_int)]
+    L.igafd_adi_setup.argtypes = [vp, dp, C.c_int, C.c_int, vp]
+    L.igafd_apply_prec_adi.argtypes = [vp, vp, vp, vp]
     L.igafd_pcg_default_opts.argtypes = [C.POINTER(PCGOpts)]
     L.igafd_pcg_default_opts.restype = None
     L.igafd_status_str.argtypes = [C.c_int]
@@ -363,6 +367,32 @@ class Patch:
         z = torch.empty_like(r) if z is None else z
         _check(lib().igafd_apply_prec(self.h, DTYPES[dtype], _dev_ptr(r, self.N),
                                       _dev_ptr(z, self.N), _stream()), "apply_prec")
+        return z
+
+    def adi_parameters(self, eps, max_J=400):
+        """Greedy three-variable ADI parameters w_1..w_J with rho_J <= eps
+        (host arithmetic in the library over the patch's eigenvalues)."""
+        import numpy as _np
+        w = _np.zeros(max_J, dtype=_np.float64)
+        J = C.c_int()
+        _check(lib().igafd_adi_parameters(self.h, float(eps), int(max_J),
+                                          w.ctypes.data_as(C.POINTER(C.c_double)), C.byref(J)),
+               "adi_parameters")
+        return w[:J.value].copy()
+
+    def adi_setup(self, omega, dtype="fp64"):
+        """Set up the ADI preconditioner P_J with the parameters omega."""
+        import numpy as _np
+        w = _np.ascontiguousarray(omega, dtype=_np.float64)
+        _check(lib().igafd_adi_setup(self.h, w.ctypes.data_as(C.POINTER(C.c_double)), len(w),
+                                     DTYPES[dtype], _stream()), "adi_setup")
+
+    def apply_prec_adi(self, r, z=None):
+        """z = P_J^{-1} r by the ADI iterations set up with adi_setup."""
+        import torch
+        z = torch.empty_like(r) if z is None else z
+        _check(lib().igafd_apply_prec_adi(self.h, _dev_ptr(r, self.N), _dev_ptr(z, self.N),
+                                          _stream()), "apply_prec_adi")
         return z
 
     def load_rhs_sine(self, b=None):

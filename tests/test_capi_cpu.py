@@ -67,3 +67,7 @@ def test_invalid_arguments_are_rejected_without_gpu_work(libpath):
     assert L.igafd_setup_patch(ctypes.byref(d), None, ctypes.byref(h)) == igafd.ERR_ARG
     assert L.igafd_apply_A(None, None, None, None) == igafd.ERR_ARG
     assert L.igafd_pcg_solve(None, None, None, None, None, None) == igafd.ERR_ARG
+    J = ctypes.c_int()
+    assert L.igafd_adi_parameters(None, 0.1, 10, None, ctypes.byref(J)) == igafd.ERR_ARG
+    assert L.igafd_adi_setup(None, None, 1, igafd.FP64, None) == igafd.ERR_ARG
+    assert L.igafd_apply_prec_adi(None, None, None, None) == igafd.ERR_ARG

@@ -1,0 +1,102 @@
+"""Parity of the three-variable ADI preconditioner (Section 5.2, Algorithm 4)
+through the C ABI with the oracle's ADI on the same inputs and parameters.
+
+Tolerances: in FP64 both sides run J contracting Douglas iterations on the
+same pencils; the library solves the shifted systems by banded Cholesky, the
+oracle by dense LU, so entries agree to rounding, 1e-12 of max|z|. The FP32
+variant keeps factors, scratch and arithmetic in FP32: 1e-5 relative (a few
+hundred FP32 ulps over J iterations of n-step recurrences)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import adi, assemble
+from gpu_util import need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("ragged-p3", (37, 9, 11), 3, [0.05, -0.03, 0.02], [0.7, 25.0, 3.0]),
+    ("one-iteration", (5, 40, 6), 2, None, [2.0]),
+    ("p1", (33, 34, 35), 1, None, [1.0, 50.0]),
+    ("p4-long-dir3", (8, 7, 70), 4, None, [3.0, 0.5, 80.0, 9.0]),
+]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+def _patch(prob):
+    from paper_1602_01636_gb300 import igafd
+    return igafd.Patch.from_problem(prob, stencil=False)
+
+
+@pytest.mark.parametrize("name,n,p,amp,omega", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_adi_matches_oracle(torch, name, n, p, amp, omega, dtype):
+    prob = synth.Problem(3, n, p, amp)
+    disc = assemble.Discretization.from_problem(prob)
+    pens = [disc.pencil(k) for k in range(3)]
+    r = synth.random_vector(disc.N, 21)
+    z_ref = adi.ADI3D(pens, omega=np.array(omega)).apply(r)
+    patch = _patch(prob)
+    patch.adi_setup(omega, dtype)
+    z = patch.apply_prec_adi(to_dev(r)).cpu().numpy()
+    if dtype == "fp64":
+        assert np.abs(z - z_ref).max() <= 1e-12 * np.abs(z_ref).max()
+    else:
+        assert np.linalg.norm(z - z_ref) <= 1e-5 * np.linalg.norm(z_ref)
+
+
+def test_adi_greedy_parameters_and_apply(torch):
+    """The library's greedy parameters meet rho_J <= eps on the oracle's own
+    spectra, start where the oracle starts, and the apply with them matches
+    the oracle's ADI with the same parameters."""
+    prob = synth.Problem(3, (12, 10, 14), 3, [0.04, 0.02, -0.03])
+    disc = assemble.Discretization.from_problem(prob)
+    pens = [disc.pencil(k) for k in range(3)]
+    lams = [adi.pencil_spectrum(K, M) for K, M in pens]
+    patch = _patch(prob)
+    for eps in (0.1, 1e-6):
+        w = patch.adi_parameters(eps)
+        w_ref = adi.greedy_parameters_3d(lams, eps)
+        assert abs(w[0] - w_ref[0]) <= 1e-10 * w_ref[0]
+        assert abs(len(w) - len(w_ref)) <= 1
+        assert adi.rho_3d(w, lams) <= eps * (1 + 1e-9)
+    patch.adi_setup(w, "fp64")
+    r = synth.random_vector(disc.N, 4)
+    z = patch.apply_prec_adi(to_dev(r)).cpu().numpy()
+    z_ref = adi.ADI3D(pens, omega=w).apply(r)
+    assert np.abs(z - z_ref).max() <= 1e-12 * np.abs(z_ref).max()
+
+
+def test_adi_full_size_deformed_cube(torch):
+    """The 3D deformed cube at n = 128, p = 3 with the greedy parameters for
+    eps = 0.1: the whole FP64 apply against the oracle."""
+    prob = synth.Problem(3, 128, 3, synth.deformation_amplitudes(0))
+    disc = assemble.Discretization.from_problem(prob)
+    pens = [disc.pencil(k) for k in range(3)]
+    patch = _patch(prob)
+    w = patch.adi_parameters(0.1)
+    patch.adi_setup(w, "fp64")
+    r = synth.random_vector(disc.N, 9)
+    z = patch.apply_prec_adi(to_dev(r)).cpu().numpy()
+    z_ref = adi.ADI3D(pens, omega=w).apply(r)
+    assert np.abs(z - z_ref).max() <= 1e-12 * np.abs(z_ref).max()
+
+
+def test_adi_rejects_bad_calls(torch):
+    from paper_1602_01636_gb300 import igafd
+    patch3 = _patch(synth.Problem(3, (6, 5, 7), 2))
+    r = to_dev(np.ones(6 * 5 * 7))
+    with pytest.raises(igafd.IgafdError):
+        patch3.apply_prec_adi(r)                       # no set-up yet
+    with pytest.raises(igafd.IgafdError):
+        patch3.adi_setup([1.0, -2.0])                  # parameters must be positive
+    with pytest.raises(igafd.IgafdError):
+        patch3.adi_setup([1.0], dtype="bf16")          # FP64 or FP32 only
+    patch2 = _patch(synth.Problem(2, (9, 8), 2))
+    with pytest.raises(igafd.IgafdError):
+        patch2.adi_setup([1.0])                        # 3D only
