@@ -731,12 +731,13 @@ def run_adi(args):
     back-to-back applies timed with CUDA events after 3 warm-ups; the
     six N-vectors of scratch, 16.8 MB each in FP64, stay L2-resident between
     kernels of one apply) and the time per ADI iteration; the FD rates of the
-    same patch beside them."""
+    same patch beside them; then PCG to the tolerance with P_J (eps = 0.1, as
+    the paper uses inside CG) and with the FD, one warm-up solve each."""
     import torch
     import synth
     from paper_1602_01636_gb300 import igafd, build as libbuild
     libbuild.build()
-    patch = igafd.Patch.from_problem(synth.deformed_cube(args.n, args.p, seed=0), stencil=False)
+    patch = igafd.Patch.from_problem(synth.deformed_cube(args.n, args.p, seed=0))
     g = torch.Generator(device="cuda").manual_seed(5)
     r = torch.randn(patch.N, dtype=torch.float64, device="cuda", generator=g)
     z = torch.empty_like(r)
@@ -769,10 +770,27 @@ def run_adi(args):
                          "launches_per_apply": launches})
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     fd = {dt: 1e3 / ms_per(lambda: patch.apply_prec(r, z, dtype=dt)) for dt in ("fp64", "tf32")}
-    line = {"metric": "ADI (three-variable, greedy parameters) vs FD prec-applies/s, deformed cube",
+    # PCG to 1e-8 (manufactured right-hand side) with P_J (eps = 0.1) and with the FD
+    b = patch.load_rhs_sine()
+    w = patch.adi_parameters(0.1)
+    solves = []
+    for prec in ("adi-fp64", "adi-fp32", "fp64", "tf32"):
+        if prec.startswith("adi"):
+            patch.adi_setup(w, prec[4:])
+        dt = "adi" if prec.startswith("adi") else prec
+        patch.pcg(b, tol=args.tol, dtype=dt)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        x, inf = patch.pcg(b, tol=args.tol, dtype=dt)
+        c.record()
+        torch.cuda.synchronize()
+        solves.append({"prec": prec, "iterations": inf.iterations, "solve_ms": a.elapsed_time(c),
+                       "true_relres": inf.true_relres})
+        print(json.dumps(solves[-1]), file=sys.stderr, flush=True)
+    line = {"metric": "ADI (three-variable, greedy parameters) vs FD prec-applies/s and PCG solve ms, deformed cube",
             "value": None, "unit": "table", "data": "synthetic", "n_gpus": 1,
-            "config": {"workload": f"deformed cube n={args.n} p={args.p}"},
-            "rows": rows, "fd_applies_per_s": fd}
+            "config": {"workload": f"deformed cube n={args.n} p={args.p}", "adi_eps_in_pcg": 0.1},
+            "rows": rows, "fd_applies_per_s": fd, "pcg": solves}
     print(json.dumps(line), flush=True)
 
 

@@ -51,7 +51,9 @@ typedef enum {
   IGAFD_BF16 = 2,   /* tcgen05 kind::f16 with bf16 operands, FP32 accumulate */
   IGAFD_FP16 = 3,   /* tcgen05 kind::f16 with fp16 operands (power-of-two scaled
                        per 128-row tile and per U_k), FP32 accumulate */
-  IGAFD_TF32 = 4    /* tcgen05 kind::tf32, FP32 accumulate */
+  IGAFD_TF32 = 4,   /* tcgen05 kind::tf32, FP32 accumulate */
+  IGAFD_ADI = 5     /* not FD: the three-variable ADI preconditioner P_J
+                       set up by igafd_adi_setup (3D; see below) */
 } igafd_dtype;
 
 /* Single-patch problem (Section 2.1, Eqs. (A), (Q)):
@@ -181,8 +183,9 @@ igafd_status igafd_apply_A(igafd_patch *patch, const double *x_dev,
  * forward mode-k products, divide by D_1 (+) ... (+) D_d, backward mode-k
  * products. With IGAFD_FP64 the result equals P^{-1} r up to rounding;
  * other dtypes give an inexact P^{-1}. The tensor-core dtypes (BF16, FP16,
- * TF32) need n_k <= 256 and return IGAFD_ERR_ARG otherwise. r_dev and z_dev
- * must not overlap. */
+ * TF32) need n_k <= 256 and return IGAFD_ERR_ARG otherwise. IGAFD_ADI
+ * applies P_J^{-1} as igafd_apply_prec_adi does. r_dev and z_dev must not
+ * overlap. */
 igafd_status igafd_apply_prec(igafd_patch *patch, igafd_dtype dtype,
                               const double *r_dev, double *z_dev, void *stream);
 
@@ -192,7 +195,8 @@ igafd_status igafd_apply_prec(igafd_patch *patch, igafd_dtype dtype,
 igafd_status igafd_load_rhs_sine(igafd_patch *patch, double *b_dev, void *stream);
 
 /* Solve A x = b by conjugate gradients preconditioned with P (Section 3),
- * P^{-1} applied by fast diagonalization in opts->prec_dtype. x_dev is the
+ * P^{-1} applied by fast diagonalization in opts->prec_dtype (or P_J^{-1}
+ * by ADI with IGAFD_ADI, after igafd_adi_setup). x_dev is the
  * initial guess if opts->x0_given, and receives the solution (the best
  * iterate on failure). Synchronises with the host only to poll the
  * convergence flag. Returns the solve status (also in info->status). */

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 // device state of a patch's ADI preconditioner (owned by the patch)
@@ -53,6 +54,7 @@ struct LineArgs {
   T *rt, *u, *v, *s, *s1, *b;      // N-vectors
   const T *bK, *bM;                // bands of this direction's pencil [n][2p+1]
   const T *fac;                    // Cholesky factor used by the solve [n][p+1]
+  const double *done;              // PCG convergence flag: skip all work while != 0 (or null)
 };
 
 // line l of CTA blk, element i along the line: address in the N-vector
@@ -141,6 +143,7 @@ __host__ __device__ size_t line_smem(int len, int p) {
 template <typename T, int STEP>
 __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
   constexpr int MODE = STEP == ST_S1 ? 0 : (STEP == ST_PRE3 || STEP == ST_S) ? 2 : 1;
+  if (a.done && *a.done != 0.0) return;      // the whole CTA leaves (uniform)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *t0 = reinterpret_cast<T *>(smem_raw);
   T *t1 = t0 + kL * (a.len + 1);
@@ -318,10 +321,11 @@ igafd_status launch_step(const AdiState &S, const LineArgs<T> &base, int dir, in
 }
 
 template <typename T>
-igafd_status apply(igafd_patch *P, const double *r, double *z, cudaStream_t s) {
+igafd_status apply(igafd_patch *P, const double *r, double *z, cudaStream_t s, const double *done) {
   const AdiState &S = *(const AdiState *)P->adi;
   const long long N = P->N;
   LineArgs<T> a{};
+  a.done = done;
   a.n1 = S.n[0]; a.n2 = S.n[1]; a.n3 = S.n[2]; a.p = S.p;
   a.chunks = (S.n[0] + kL - 1) / kL;
   a.r = r; a.z = z;
@@ -380,7 +384,17 @@ void igafd_adi_free(igafd_patch *P) {
   if (P && P->adi) {
     free_state((AdiState *)P->adi);
     P->adi = nullptr;
+    // a captured PCG loop may hold this state's buffers in its kernel
+    // arguments: make the next solve capture it again
+    memset(P->loop_key, 0, sizeof(P->loop_key));
   }
+}
+
+igafd_status igafd_adi_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
+                             double *done) {
+  if (!P || !P->adi || !r || !z || r == z) return IGAFD_ERR_ARG;
+  const AdiState *S = (const AdiState *)P->adi;
+  return S->fp32 ? apply<float>(P, r, z, s, done) : apply<double>(P, r, z, s, done);
 }
 
 extern "C" igafd_status igafd_adi_parameters(igafd_patch *P, double eps, int max_J, double *omega,
@@ -533,6 +547,5 @@ extern "C" igafd_status igafd_adi_setup(igafd_patch *P, const double *omega, int
 extern "C" igafd_status igafd_apply_prec_adi(igafd_patch *P, const double *r, double *z, void *stream) {
   if (!P || !P->adi || !r || !z || r == z) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
-  const AdiState *S = (const AdiState *)P->adi;
-  return S->fp32 ? apply<float>(P, r, z, (cudaStream_t)stream) : apply<double>(P, r, z, (cudaStream_t)stream);
+  return igafd_adi_apply(P, r, z, (cudaStream_t)stream, nullptr);
 }

@@ -153,6 +153,10 @@ igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s);
 // n_k each, device), span-scaled when the patch carries scalings
 igafd_status igafd_pencils_dense(igafd_patch *P, int k, double *K, double *M, cudaStream_t s);
 void igafd_adi_free(igafd_patch *P);   // releases the ADI state (adi.cu)
+// z = P_J^{-1} r by the ADI set up on the patch; kernels do nothing while
+// *done_flag != 0 (done_flag may be null)
+igafd_status igafd_adi_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
+                             double *done_flag);
 // FD apply; kernels do nothing while *done_flag != 0 (done_flag may be null)
 igafd_status igafd_fd64_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
                               double *done_flag);

@@ -186,6 +186,7 @@ static igafd_status fd_apply(igafd_patch *P, igafd_dtype dt, const double *r, do
     case IGAFD_BF16:
     case IGAFD_FP16:
     case IGAFD_TF32: return igafd_fd_tc_apply(P, dt, r, z, s, done);
+    case IGAFD_ADI: return igafd_adi_apply(P, r, z, s, done);
     default: return IGAFD_ERR_ARG;
   }
 }
@@ -325,7 +326,8 @@ static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, cons
   if (opts) o = *opts; else igafd_pcg_default_opts(&o);
   if (!(o.tol >= 0.0) || o.max_iter < 0 || o.check_every < 1 || o.true_every < 0)
     return IGAFD_ERR_ARG;
-  if (o.prec_dtype < IGAFD_FP64 || o.prec_dtype > IGAFD_TF32) return IGAFD_ERR_ARG;
+  if (o.prec_dtype < IGAFD_FP64 || o.prec_dtype > IGAFD_ADI) return IGAFD_ERR_ARG;
+  if (o.prec_dtype == IGAFD_ADI && !P->adi) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   S = SolveState{};
   S.timing = o.timing != 0;

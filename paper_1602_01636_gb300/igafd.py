@@ -15,8 +15,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libigafd.so")
 
-FP64, FP32, BF16, FP16, TF32 = 0, 1, 2, 3, 4
-DTYPES = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16, "tf32": TF32}
+FP64, FP32, BF16, FP16, TF32, ADI = 0, 1, 2, 3, 4, 5
+DTYPES = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16, "tf32": TF32, "adi": ADI}
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error",
           -3: "1D mass matrix not positive definite", -4: "eigen-solve did not converge",

@@ -10,8 +10,8 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import adi, assemble
-from gpu_util import need_gpu, to_dev
+from oracle import adi, assemble, pcg
+from gpu_util import need_gpu, to_dev, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -87,12 +87,48 @@ def test_adi_full_size_deformed_cube(torch):
     assert np.abs(z - z_ref).max() <= 1e-12 * np.abs(z_ref).max()
 
 
+def test_pcg_with_adi_preconditioner(torch):
+    """PCG with P_J (igafd_pcg_solve, prec_dtype IGAFD_ADI, flexible beta):
+    fixed-k iterates equal the oracle's PCG with the oracle's ADI (same
+    parameters) to 1e-10; the converged solution matches the direct solve;
+    Theorem 1 keeps the iteration count near the FD's; apply_prec with the
+    ADI dtype is the ADI apply."""
+    from paper_1602_01636_gb300 import igafd
+    prob = synth.Problem(3, (14, 11, 12), 3, [0.06, -0.04, 0.03])
+    disc = assemble.Discretization.from_problem(prob)
+    pens = [disc.pencil(k) for k in range(3)]
+    A = assemble.stencil_to_csr(disc, disc.assemble_stencil())
+    b = synth.random_rhs(disc.N, 5)
+    patch = igafd.Patch.from_problem(prob)
+    w = patch.adi_parameters(0.1)
+    patch.adi_setup(w, "fp64")
+    P_J = adi.ADI3D(pens, omega=w)
+    k = 6
+    ro = pcg.pcg(lambda v: A @ v, b, P_J.apply, fixed_iters=k, flexible=True)
+    x, info = patch.pcg(to_dev(b), tol=0.0, max_iter=k, dtype="adi")
+    assert info.iterations == k
+    assert rel(x.cpu().numpy(), ro.x) <= 1e-10
+    x, info = patch.pcg(to_dev(b), tol=1e-10, max_iter=500, dtype="adi")
+    xd = np.linalg.solve(A.toarray(), b)
+    assert rel(x.cpu().numpy(), xd) <= 1e-8
+    _, info_fd = patch.pcg(to_dev(b), tol=1e-10, max_iter=500, dtype="fp64")
+    assert info.iterations <= info_fd.iterations + 3
+    r = to_dev(synth.random_vector(disc.N, 2))
+    assert torch.equal(patch.apply_prec(r, dtype="adi"), patch.apply_prec_adi(r))
+    # a new set-up (FP32) replaces the state the captured loop used
+    patch.adi_setup(w, "fp32")
+    x32, info32 = patch.pcg(to_dev(b), tol=1e-10, max_iter=500, dtype="adi")
+    assert rel(x32.cpu().numpy(), xd) <= 1e-8
+
+
 def test_adi_rejects_bad_calls(torch):
     from paper_1602_01636_gb300 import igafd
     patch3 = _patch(synth.Problem(3, (6, 5, 7), 2))
     r = to_dev(np.ones(6 * 5 * 7))
     with pytest.raises(igafd.IgafdError):
         patch3.apply_prec_adi(r)                       # no set-up yet
+    with pytest.raises(igafd.IgafdError):
+        patch3.apply_prec(r, dtype="adi")
     with pytest.raises(igafd.IgafdError):
         patch3.adi_setup([1.0, -2.0])                  # parameters must be positive
     with pytest.raises(igafd.IgafdError):
