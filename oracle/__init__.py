@@ -23,7 +23,10 @@ Modules
             and the scaling network with its gradient
   adi       Algorithms 2 and 4: two- and three-variable ADI solvers of
             P s = r, their parameters and error operators
+  multipatch  Section 6: the C^0 three-patch L-shaped domain, its subdomain
+            restrictions and the additive Schwarz preconditioners of
+            Eqs. (Peas), (Pias)
 
 Readings where the paper is silent or garbled are stated at each function.
 """
-from . import spline, assemble, fd, pcg, learned, adi  # noqa: F401
+from . import spline, assemble, fd, pcg, learned, adi, multipatch  # noqa: F401
