@@ -401,6 +401,14 @@ igafd_status igafd_mlp_train_step(igafd_mlp *mlp, const float *X_dev, const floa
 igafd_status igafd_adi_parameters(igafd_patch *patch, double eps, int max_J,
                                   double *omega_host, int *J);
 
+/* Host-only core of igafd_adi_parameters on given spectra L1[n1], L2[n2],
+ * L3[n3] (positive; the greedy start is at L1[0], L2[0], L3[0], so pass them
+ * ascending): the same parameters and return codes. Multithreaded over the
+ * triples (contiguous chunks, deterministic result). Needs no GPU. */
+igafd_status igafd_adi_greedy(const double *L1, int n1, const double *L2, int n2,
+                              const double *L3, int n3, double eps, int max_J,
+                              double *omega, int *J);
+
 /* Set up the ADI preconditioner with parameters omega_host[0..J-1] (> 0):
  * banded pencils and the banded Cholesky factors of K_k + w_j M_k and of M_k
  * for every direction and parameter, and 6 N-vectors of scratch (the

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 // device state of a patch's ADI preconditioner (owned by the patch)
@@ -397,6 +398,125 @@ igafd_status igafd_adi_apply(igafd_patch *P, const double *r, double *z, cudaStr
   return S->fp32 ? apply<float>(P, r, z, s, done) : apply<double>(P, r, z, s, done);
 }
 
+namespace {
+
+// f(chunk, lo, hi) over [0, NT) split into nthr contiguous chunks, one thread each
+template <typename F>
+void for_chunks(size_t NT, int nthr, F f) {
+  if (nthr <= 1) {
+    f(0, (size_t)0, NT);
+    return;
+  }
+  std::vector<std::thread> th;
+  const size_t per = (NT + nthr - 1) / nthr;
+  for (int c = 0; c < nthr; ++c) {
+    const size_t lo = (size_t)c * per, hi = std::min(NT, lo + per);
+    if (lo < hi) th.emplace_back(f, c, lo, hi);
+  }
+  for (auto &t : th) t.join();
+}
+
+}  // namespace
+
+extern "C" igafd_status igafd_adi_greedy(const double *L1, int n1, const double *L2, int n2,
+                                         const double *L3, int n3, double eps, int max_J,
+                                         double *omega, int *J_out) {
+  if (!L1 || !L2 || !L3 || n1 < 1 || n2 < 1 || n3 < 1 || !omega || !J_out || max_J < 1 ||
+      !(eps > 0.0) || !(eps < 1.0))
+    return IGAFD_ERR_ARG;
+  const size_t NT = (size_t)n1 * n2 * n3;
+  for (int i = 0; i < n1; ++i) if (!(L1[i] > 0.0)) return IGAFD_ERR_ARG;
+  for (int i = 0; i < n2; ++i) if (!(L2[i] > 0.0)) return IGAFD_ERR_ARG;
+  for (int i = 0; i < n3; ++i) if (!(L3[i] > 0.0)) return IGAFD_ERR_ARG;
+  std::vector<double> prod(NT, 1.0);
+  const unsigned hc = std::thread::hardware_concurrency();
+  const int nthr = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(hc ? hc : 1, 16), NT / 65536));
+  std::vector<double> cmax(2 * 16), amax(16);
+  std::vector<size_t> aarg(16);
+  // visit the triples of [lo, hi) in (i3, i2, i1) order: fn(t, l1, l2, l3)
+  auto sweep = [&](size_t lo, size_t hi, auto fn) {
+    size_t i1 = lo % n1, i2 = (lo / n1) % n2, i3 = lo / ((size_t)n1 * n2);
+    for (size_t t = lo; t < hi; ++t) {
+      fn(t, L1[i1], L2[i2], L3[i3]);
+      if (++i1 == (size_t)n1) {
+        i1 = 0;
+        if (++i2 == (size_t)n2) { i2 = 0; ++i3; }
+      }
+    }
+  };
+  // greedy start: the triple of smallest eigenvalues (the empty product is 1 everywhere)
+  double st1 = L1[0], st2 = L2[0], st3 = L3[0];
+  int J = 0;
+  bool met = false;
+  while (J < max_J) {
+    const double S = st1 + st2 + st3;
+    const double e2 = st1 * st2 + st1 * st3 + st2 * st3, e3 = st1 * st2 * st3;
+    double cand[2] = {0.0, 0.0};
+    int nc = 1;
+    cand[0] = stationary_root(e2, e3);
+    if (douglas(cand[0], st1, st2, st3) < 0.0) {           // |g| = 0 at the two zeros of g
+      const double ws = cand[0];
+      cand[0] = bisect_root(S, e2, e3, 0.0, ws);
+      cand[1] = bisect_root(S, e2, e3, ws, 2.0 * S);
+      nc = 2;
+    }
+    int best = 0;
+    if (nc == 2) {   // the zero whose use gives the smaller max |prod * g(w)|
+      std::fill(cmax.begin(), cmax.end(), 0.0);
+      for_chunks(NT, nthr, [&](int c, size_t lo, size_t hi) {
+        double m0 = 0.0, m1 = 0.0;
+        sweep(lo, hi, [&](size_t t, double l1, double l2, double l3) {
+          const double v0 = std::fabs(prod[t] * douglas(cand[0], l1, l2, l3));
+          const double v1 = std::fabs(prod[t] * douglas(cand[1], l1, l2, l3));
+          m0 = v0 > m0 ? v0 : m0;
+          m1 = v1 > m1 ? v1 : m1;
+        });
+        cmax[2 * c] = m0;
+        cmax[2 * c + 1] = m1;
+      });
+      double m0 = 0.0, m1 = 0.0;
+      for (int c = 0; c < nthr; ++c) {
+        m0 = std::max(m0, cmax[2 * c]);
+        m1 = std::max(m1, cmax[2 * c + 1]);
+      }
+      best = m1 < m0 ? 1 : 0;
+    }
+    const double w = cand[best];
+    omega[J++] = w;
+    // apply it, and find the next worst triple (first maximum in i3, i2, i1 order)
+    std::fill(amax.begin(), amax.end(), -1.0);
+    for_chunks(NT, nthr, [&](int c, size_t lo, size_t hi) {
+      double mx = -1.0;
+      size_t arg = lo;
+      sweep(lo, hi, [&](size_t t, double l1, double l2, double l3) {
+        prod[t] = prod[t] * douglas(w, l1, l2, l3);
+        const double v = std::fabs(prod[t]);
+        if (v > mx) {
+          mx = v;
+          arg = t;
+        }
+      });
+      amax[c] = mx;
+      aarg[c] = arg;
+    });
+    double mx = -1.0;
+    size_t arg = 0;
+    for (int c = 0; c < nthr; ++c)
+      if (amax[c] > mx) {        // strict: the earlier chunk keeps a tie
+        mx = amax[c];
+        arg = aarg[c];
+      }
+    if (mx <= eps) {
+      met = true;
+      break;
+    }
+    const size_t i1 = arg % n1, i2 = (arg / n1) % n2, i3 = arg / ((size_t)n1 * n2);
+    st1 = L1[i1]; st2 = L2[i2]; st3 = L3[i3];
+  }
+  *J_out = J;
+  return met ? IGAFD_OK : IGAFD_ERR_NOT_CONVERGED;
+}
+
 extern "C" igafd_status igafd_adi_parameters(igafd_patch *P, double eps, int max_J, double *omega,
                                              int *J_out) {
   if (!P || P->dim != 3 || !omega || !J_out || max_J < 1 || !(eps > 0.0) || !(eps < 1.0))
@@ -408,65 +528,7 @@ extern "C" igafd_status igafd_adi_parameters(igafd_patch *P, double eps, int max
   IGAFD_CUDA(cudaMemcpy(L1.data(), P->D[0], n1 * sizeof(double), cudaMemcpyDeviceToHost));
   IGAFD_CUDA(cudaMemcpy(L2.data(), P->D[1], n2 * sizeof(double), cudaMemcpyDeviceToHost));
   IGAFD_CUDA(cudaMemcpy(L3.data(), P->D[2], n3 * sizeof(double), cudaMemcpyDeviceToHost));
-  const size_t NT = (size_t)n1 * n2 * n3;
-  std::vector<double> prod(NT, 1.0);
-  // greedy start: the triple of smallest eigenvalues (the empty product is 1 everywhere)
-  double st1 = L1[0], st2 = L2[0], st3 = L3[0];
-  int J = 0;
-  bool met = false;
-  while (J < max_J) {
-    const double S = st1 + st2 + st3;
-    const double e2 = st1 * st2 + st1 * st3 + st2 * st3, e3 = st1 * st2 * st3;
-    double cand[2];
-    int nc = 1;
-    cand[0] = stationary_root(e2, e3);
-    if (douglas(cand[0], st1, st2, st3) < 0.0) {           // |g| = 0 at the two zeros of g
-      const double ws = cand[0];
-      cand[0] = bisect_root(S, e2, e3, 0.0, ws);
-      cand[1] = bisect_root(S, e2, e3, ws, 2.0 * S);
-      nc = 2;
-    }
-    // max |prod * g(w)| for each candidate
-    double best_val = 0.0;
-    int best = 0;
-    for (int c = 0; c < nc; ++c) {
-      double mx = 0.0;
-      size_t t = 0;
-      for (int i3 = 0; i3 < n3; ++i3)
-        for (int i2 = 0; i2 < n2; ++i2)
-          for (int i1 = 0; i1 < n1; ++i1, ++t) {
-            const double v = std::fabs(prod[t] * douglas(cand[c], L1[i1], L2[i2], L3[i3]));
-            mx = v > mx ? v : mx;
-          }
-      if (c == 0 || mx < best_val) {
-        best_val = mx;
-        best = c;
-      }
-    }
-    const double w = cand[best];
-    omega[J++] = w;
-    // apply it, and find the next worst triple (first maximum in i3, i2, i1 order)
-    double mx = -1.0;
-    size_t t = 0, arg = 0;
-    for (int i3 = 0; i3 < n3; ++i3)
-      for (int i2 = 0; i2 < n2; ++i2)
-        for (int i1 = 0; i1 < n1; ++i1, ++t) {
-          prod[t] = prod[t] * douglas(w, L1[i1], L2[i2], L3[i3]);
-          const double v = std::fabs(prod[t]);
-          if (v > mx) {
-            mx = v;
-            arg = t;
-          }
-        }
-    if (mx <= eps) {
-      met = true;
-      break;
-    }
-    const size_t i1 = arg % n1, i2 = (arg / n1) % n2, i3 = arg / ((size_t)n1 * n2);
-    st1 = L1[i1]; st2 = L2[i2]; st3 = L3[i3];
-  }
-  *J_out = J;
-  return met ? IGAFD_OK : IGAFD_ERR_NOT_CONVERGED;
+  return igafd_adi_greedy(L1.data(), n1, L2.data(), n2, L3.data(), n3, eps, max_J, omega, J_out);
 }
 
 extern "C" igafd_status igafd_adi_setup(igafd_patch *P, const double *omega, int J, igafd_dtype dtype,

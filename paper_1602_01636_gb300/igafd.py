@@ -77,7 +77,7 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_patch_sepfit", "igafd_set_scalings", "igafd_mlp_create", "igafd_mlp_destroy",
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step",
-           "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi"]
+           "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi", "igafd_adi_greedy"]
 
 MLP_PARAMS = 4738
 
@@ -129,6 +129,8 @@ def lib():
     L.igafd_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, fp, vp]
     L.igafd_adi_parameters.argtypes = [vp, C.c_double, C.c_int, dp, C.POINTER(C.c_int)]
     L.igafd_adi_setup.argtypes = [vp, dp, C.c_int, C.c_int, vp]
+    L.igafd_adi_greedy.argtypes = [dp, C.c_int, dp, C.c_int, dp, C.c_int, C.c_double, C.c_int, dp,
+                                   C.POINTER(C.c_int)]
     L.igafd_apply_prec_adi.argtypes = [vp, vp, vp, vp]
     L.igafd_pcg_default_opts.argtypes = [C.POINTER(PCGOpts)]
     L.igafd_pcg_default_opts.restype = None
@@ -155,6 +157,21 @@ def lanczos_extremes(alpha, beta):
     _check(lib().igafd_lanczos_extremes(a.ctypes.data_as(dp), b.ctypes.data_as(dp), len(a),
                                         C.byref(lo), C.byref(hi)), "lanczos_extremes")
     return lo.value, hi.value
+
+
+def adi_greedy(L1, L2, L3, eps, max_J=400):
+    """Greedy three-variable ADI parameters on the spectra L1, L2, L3 (host
+    arithmetic in the library; no GPU needed). Raises when max_J parameters
+    do not reach eps."""
+    import numpy as _np
+    ls = [_np.ascontiguousarray(v, dtype=_np.float64) for v in (L1, L2, L3)]
+    w = _np.zeros(max_J, dtype=_np.float64)
+    J = C.c_int()
+    dp = C.POINTER(C.c_double)
+    _check(lib().igafd_adi_greedy(ls[0].ctypes.data_as(dp), len(ls[0]), ls[1].ctypes.data_as(dp),
+                                  len(ls[1]), ls[2].ctypes.data_as(dp), len(ls[2]), float(eps),
+                                  int(max_J), w.ctypes.data_as(dp), C.byref(J)), "adi_greedy")
+    return w[:J.value].copy()
 
 
 def kernel_launches():
