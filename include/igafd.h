@@ -147,10 +147,10 @@ typedef struct {
 
 /* Build a patch: 1D pencils K_k, M_k by (p+1)-point Gauss quadrature
  * (Section 3, Eq. (prec)), their FP64 generalized eigendecompositions
- * K_k U_k = M_k U_k D_k, U_k^T M_k U_k = I (Algorithm 1 line 1, Section 4.1,
- * Eq. (eigen3d)), and the stiffness matrix A of Eq. (A) with
- * Q = kappa |det J| J^{-1} J^{-T} as a (2p+1)^d-point FP64 stencil
- * (Section 2.1). Allocates all device memory the patch will use.
+ * K_k U_k = M_k U_k D_k, U_k^T M_k U_k = I (the eigendecompositions of
+ * Algorithm 1, Section 4.1, Eq. (eigen3d)), and the stiffness matrix A of
+ * Eq. (A) with Q = kappa |det J| J^{-1} J^{-T} as a (2p+1)^d-point FP64
+ * stencil (Section 2.1). Allocates all device memory the patch will use.
  * Errors: ARG (bad sizes/knots), OOM, NOT_SPD, EIG, FOLDED, CUDA.
  * On error *out is NULL and nothing is leaked. */
 igafd_status igafd_setup_patch(const igafd_patch_desc *desc, void *stream,

@@ -1,5 +1,5 @@
 // 1D pencils and their generalized eigendecompositions (Section 3 and
-// Algorithm 1 line 1 / Eq. (eigen3d)), in FP64 on the device.
+// the eigendecompositions of Algorithm 1 / Eq. (eigen3d)), in FP64 on the device.
 //
 //   M_k, K_k: (p+1)-point Gauss quadrature of B_i B_j and B_i' B_j'
 //   M = L L^T (banded Cholesky), K~ = L^{-1} K L^{-T} (banded triangular
