@@ -2,8 +2,6 @@
 import numpy as np
 import pytest
 
-import synth
-
 
 def need_gpu():
     torch = pytest.importorskip("torch")

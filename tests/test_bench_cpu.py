@@ -10,7 +10,6 @@ import sys
 import tempfile
 import types
 
-import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 

@@ -10,7 +10,7 @@ import pytest
 import scipy.linalg as sla
 
 import synth
-from oracle import assemble, multipatch as mpm, pcg
+from oracle import multipatch as mpm, pcg
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 

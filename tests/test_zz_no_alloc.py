@@ -6,7 +6,6 @@ a run that stops at the first failure has then already run every other test.
 """
 import ctypes as C
 
-import numpy as np
 import pytest
 
 import synth
