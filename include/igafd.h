@@ -379,15 +379,29 @@ igafd_status igafd_mlp_gradient(igafd_mlp *mlp, const float *X_dev, const float 
 igafd_status igafd_mlp_train_step(igafd_mlp *mlp, const float *X_dev, const float *T_dev,
                                   int rows, float lr, float *loss_host, void *stream);
 
-/* ---- Three-variable ADI preconditioner (Section 5.2, Algorithm 4) ------
- * An alternative to the fast-diagonalization P^{-1}: J iterations of the
- * Douglas scheme of Eq. (ADI3D), from s_0 = 0, on the same pencils (span-
- * scaled when scalings are set at the time of igafd_adi_setup), give
+/* ---- ADI preconditioners (Section 4.2, Algorithm 2; Section 5.2,
+ * Algorithm 4) ----------------------------------------------------------
+ * An alternative to the fast-diagonalization P^{-1}: J iterations from
+ * s_0 = 0 of the Peaceman-Rachford scheme of Eq. (ADI) (2D, gamma_j =
+ * omega_j) or of the Douglas scheme of Eq. (ADI3D) (3D), on the same pencils
+ * (span-scaled when scalings are set at the time of igafd_adi_setup), give
  * z = P_J^{-1} r with P_J symmetric positive definite and
- * kappa(P_J^{-1} A) <= (1 + eps)/(1 - eps) kappa(P^{-1} A) when rho_J <= eps
- * (Theorem 1 and its 3D analogue). 3D patches only, n_k <= 256. */
+ * kappa(P_J^{-1} A) <= (1 + eps)/(1 - eps) kappa(P^{-1} A) when the error
+ * operator has ||T_J|| <= eps (Theorem 1 and its 3D analogue). n_k <= 256. */
 
-/* Greedy parameters of Eqs. (greedy1)-(greedy2) over the triples of
+/* 2D: the optimal parameters for equal spectral intervals [a, b]:
+ * J = ceil(ln(4 b / a) ln(4 / eps) / pi^2) (Eq. (ADIits)) and
+ * omega_host[j-1] = b dn((2j - 1) K / (2J), k), k^2 = 1 - (a/b)^2 (the
+ * elliptic-function solution of the one-variable minimax, by the
+ * arithmetic-geometric mean from k' = a / b). 0 < a <= b, 0 < eps < 1;
+ * omega_host holds max_J values; IGAFD_ERR_NOT_CONVERGED when J > max_J.
+ * Needs no GPU. */
+igafd_status igafd_adi_wachspress(double a, double b, double eps, int max_J,
+                                  double *omega_host, int *J);
+
+/* Parameters for the patch: in 2D igafd_adi_wachspress on the hull of the
+ * spectra of M_1^{-1} K_1 and M_2^{-1} K_2 (the patch's D_k); in 3D the
+ * greedy parameters of Eqs. (greedy1)-(greedy2) over the triples of
  * eigenvalues of M_k^{-1} K_k (the patch's D_k): omega_host[0..*J-1] get
  * w_1.., *J the first count with rho_J = max over the triples of
  * |prod_j g(w_j; l)| <= eps, g(w; l) = 1 - 2 w^2 (l1 + l2 + l3) /
@@ -409,7 +423,7 @@ igafd_status igafd_adi_greedy(const double *L1, int n1, const double *L2, int n2
                               const double *L3, int n3, double eps, int max_J,
                               double *omega, int *J);
 
-/* Set up the ADI preconditioner with parameters omega_host[0..J-1] (> 0):
+/* Set up the ADI preconditioner (2D or 3D) with parameters omega_host[0..J-1] (> 0):
  * banded pencils and the banded Cholesky factors of K_k + w_j M_k and of M_k
  * for every direction and parameter, and 6 N-vectors of scratch (the
  * library's only allocation for ADI). dtype IGAFD_FP64 (the paper's
@@ -419,9 +433,10 @@ igafd_status igafd_adi_greedy(const double *L1, int n1, const double *L2, int n2
 igafd_status igafd_adi_setup(igafd_patch *patch, const double *omega_host, int J,
                              igafd_dtype dtype, void *stream);
 
-/* z = P_J^{-1} r by J Douglas iterations (Algorithm 4): per iteration four
- * kernels of independent banded line problems along directions 2, 1, 2, 3
- * (4J + 1 launches in all). r_dev, z_dev: length-N FP64 device vectors, not
+/* z = P_J^{-1} r by J ADI iterations: in 2D (Algorithm 2) two kernels of
+ * independent banded line problems per iteration, along directions 1 and 2,
+ * and a final M_1 solve (2J + 1 launches); in 3D (Algorithm 4) four per
+ * iteration, along directions 2, 1, 2, 3 (4J + 1 launches in all). r_dev, z_dev: length-N FP64 device vectors, not
  * overlapping. IGAFD_ERR_ARG without igafd_adi_setup. */
 igafd_status igafd_apply_prec_adi(igafd_patch *patch, const double *r_dev,
                                   double *z_dev, void *stream);

@@ -19,6 +19,16 @@
 //   dir 3: s_j = (K3 + w M3)^{-1} M3 b_j,  v_{j+1} = b_j - w s_j
 // after r~ = 2 (I (x) M2 (x) M3)^{-1} r (two more line kernels). Arithmetic is
 // FP64 (the paper's) or FP32 (an inexact P_J, like the mixed FD).
+//
+// Two variables (Section 4.2, Algorithm 2): the Peaceman-Rachford iteration of
+// Eq. (ADI) in the mass-scaled variables s~, with gamma_j = omega_j (the
+// optimal parameters for equal spectral intervals, w_j = b dn((2j-1)K/(2J), k),
+// and J from Eq. (ADIits)). Each half step solves along one direction and
+// forms the next half step's right-hand side along the same direction, so an
+// iteration is two line kernels:
+//   dir 1: s~_{j-1/2} = (K1 + w_j M1)^{-1} r_{j-1},  r_{j-1/2} = r - (K1 - w_j M1) s~_{j-1/2}
+//   dir 2: s~_j = (K2 + w_j M2)^{-1} r_{j-1/2},      r_j = r - (K2 - w_{j+1} M2) s~_j
+// with r_0 = r, and a last dir-1 kernel s_J = M1^{-1} s~_J.
 #include "common.cuh"
 
 #include <algorithm>
@@ -29,7 +39,7 @@
 
 // device state of a patch's ADI preconditioner (owned by the patch)
 struct AdiState {
-  int J = 0, fp32 = 0, p = 0, n[3] = {0, 0, 0};
+  int J = 0, fp32 = 0, p = 0, dim = 3, n[3] = {0, 0, 0};
   size_t esz = 8;                  // bytes per element (8 FP64, 4 FP32)
   double *omega = nullptr;         // [J] host copy
   void *band[3] = {nullptr, nullptr, nullptr};   // [2][n][2p+1]: K band, M band
@@ -43,12 +53,18 @@ constexpr int kL = 32;      // lines per CTA (one solving thread each)
 constexpr int kT = 128;     // threads per CTA
 constexpr int kMaxLen = 256;
 
-enum { ST_PRE2 = 0, ST_PRE3, ST_U, ST_S1, ST_B, ST_S };
+enum { ST_PRE2 = 0, ST_PRE3, ST_U, ST_S1, ST_B, ST_S, ST2_A, ST2_B, ST2_F };
+
+// direction (0-based) whose lines a step works on
+__host__ __device__ constexpr int step_mode(int st) {
+  return (st == ST_S1 || st == ST2_A || st == ST2_F) ? 0 : (st == ST_PRE3 || st == ST_S) ? 2 : 1;
+}
 
 template <typename T>
 struct LineArgs {
   int n1, n2, n3, p, len, chunks;
   double w;                        // w_j of this iteration
+  double w_next;                   // w_{j+1} (two-variable ADI: the next right-hand side)
   int first, last;                 // first / last iteration of the apply
   const double *r;                 // FP64 input (ST_PRE2)
   double *z;                       // FP64 output (ST_S of the last iteration)
@@ -143,7 +159,7 @@ __host__ __device__ size_t line_smem(int len, int p) {
 
 template <typename T, int STEP>
 __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
-  constexpr int MODE = STEP == ST_S1 ? 0 : (STEP == ST_PRE3 || STEP == ST_S) ? 2 : 1;
+  constexpr int MODE = step_mode(STEP);
   if (a.done && *a.done != 0.0) return;      // the whole CTA leaves (uniform)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *t0 = reinterpret_cast<T *>(smem_raw);
@@ -194,10 +210,19 @@ __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
       load_tile<MODE>(t0, a, nv, [&](long long g) { return a.u[g] + w * a.s1[g]; });
     __syncthreads();
     band_product<MODE>(t1, t0, len, p, nv, Mc, zero);                       // M2 (u + w s*)
-  } else {                                                                  // ST_S
+  } else if (STEP == ST_S) {
     load_tile<MODE>(t0, a, nv, [&](long long g) { return a.b[g]; });
     __syncthreads();
     band_product<MODE>(t1, t0, len, p, nv, Mc, zero);                       // M3 b
+  } else if (STEP == ST2_A) {
+    if (a.first)
+      load_tile<MODE>(t1, a, nv, [&](long long g) { return (T)a.r[g]; });  // r_0 = r
+    else
+      load_tile<MODE>(t1, a, nv, [&](long long g) { return a.u[g]; });     // r_{j-1}
+  } else if (STEP == ST2_B) {
+    load_tile<MODE>(t1, a, nv, [&](long long g) { return a.v[g]; });       // r_{j-1/2}
+  } else {                                                                  // ST2_F
+    load_tile<MODE>(t1, a, nv, [&](long long g) { return a.s[g]; });       // s~_J
   }
   __syncthreads();
   if ((int)threadIdx.x < nv) chol_solve<MODE>(res, sF, len, p, threadIdx.x);
@@ -215,6 +240,22 @@ __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
       store_tile<MODE>(t1, a, nv, [&](long long g, T x) { a.b[g] = w * x; });
     else
       store_tile<MODE>(t1, a, nv, [&](long long g, T x) { a.b[g] = a.v[g] + w * x; });
+  } else if (STEP == ST2_A || (STEP == ST2_B && !a.last)) {
+    // the next half step's right-hand side r - (K - w M) s~ along the same lines
+    const T wn = STEP == ST2_A ? w : (T)a.w_next;
+    band_product<MODE>(t0, t1, len, p, nv, [&](int i, int o) { return -(Kc(i, o) - wn * Mc(i, o)); },
+                       [&](int l, int i) {
+                         return (T)a.r[elem_addr<MODE>(a.n1, a.n2, a.chunks, blockIdx.x, l, i)];
+                       });
+    __syncthreads();
+    if (STEP == ST2_A)
+      store_tile<MODE>(t0, a, nv, [&](long long g, T x) { a.v[g] = x; });  // r_{j-1/2}
+    else
+      store_tile<MODE>(t0, a, nv, [&](long long g, T x) { a.u[g] = x; });  // r_j
+  } else if (STEP == ST2_B) {
+    store_tile<MODE>(t1, a, nv, [&](long long g, T x) { a.s[g] = x; });    // s~_J
+  } else if (STEP == ST2_F) {
+    store_tile<MODE>(t1, a, nv, [&](long long g, T x) { a.z[g] = (double)x; });
   } else {
     if (a.last) {
       store_tile<MODE>(t1, a, nv, [&](long long g, T x) { a.z[g] = (double)x; });
@@ -300,7 +341,7 @@ igafd_status launch_step(const AdiState &S, const LineArgs<T> &base, int dir, in
   a.bK = (const T *)S.band[dir];
   a.bM = (const T *)S.band[dir] + (size_t)S.n[dir] * (2 * p + 1);
   a.fac = (const T *)S.fac[dir] + (size_t)fac_index * S.n[dir] * (p + 1);
-  constexpr int MODE = STEP == ST_S1 ? 0 : (STEP == ST_PRE3 || STEP == ST_S) ? 2 : 1;
+  constexpr int MODE = step_mode(STEP);
   const long long grid = MODE == 0 ? ((long long)n2 * n3 + kL - 1) / kL
                                    : (long long)a.chunks * (MODE == 1 ? n3 : n2);
   const size_t smem = line_smem<T>(a.len, p);
@@ -333,6 +374,17 @@ igafd_status apply(igafd_patch *P, const double *r, double *z, cudaStream_t s, c
   T *v0 = (T *)S.vec;
   a.rt = v0; a.u = v0 + N; a.v = v0 + 2 * N; a.s = v0 + 3 * N; a.s1 = v0 + 4 * N; a.b = v0 + 5 * N;
   const int J = S.J;
+  if (S.dim == 2) {
+    for (int j = 0; j < J; ++j) {
+      a.w = S.omega[j];
+      a.w_next = j + 1 < J ? S.omega[j + 1] : 0.0;
+      a.first = j == 0;
+      a.last = j == J - 1;
+      IGAFD_TRY((launch_step<T, ST2_A>(S, a, 0, j, s)));
+      IGAFD_TRY((launch_step<T, ST2_B>(S, a, 1, j, s)));
+    }
+    return launch_step<T, ST2_F>(S, a, 0, J, s);               // s_J = M1^{-1} s~_J
+  }
   IGAFD_TRY((launch_step<T, ST_PRE2>(S, a, 1, J, s)));        // M2^{-1} r
   IGAFD_TRY((launch_step<T, ST_PRE3>(S, a, 2, J, s)));        // r~ = 2 M3^{-1} (M2^{-1} r)
   for (int j = 0; j < J; ++j) {
@@ -517,9 +569,80 @@ extern "C" igafd_status igafd_adi_greedy(const double *L1, int n1, const double 
   return met ? IGAFD_OK : IGAFD_ERR_NOT_CONVERGED;
 }
 
+namespace {
+
+// complete elliptic integral K(k), k^2 = 1 - kp^2, by the arithmetic-geometric
+// mean of 1 and kp (Abramowitz and Stegun 17.6: K = pi / (2 AGM(1, k')))
+double agm_K(double kp) {
+  double a = 1.0, b = kp;
+  for (int it = 0; it < 64 && std::fabs(a - b) > 1e-16 * a; ++it) {
+    const double an = 0.5 * (a + b);
+    b = std::sqrt(a * b);
+    a = an;
+  }
+  return 3.14159265358979323846 / (2.0 * a);
+}
+
+// Jacobi dn(u, k), k^2 = 1 - kp^2, by the AGM method (Abramowitz and Stegun
+// 16.4) started from kp itself: a_0 = 1, b_0 = k', c_0 = k, c_{n+1} =
+// c_n^2 / (4 a_{n+1}) until c_N is negligible; phi_N = 2^N a_N u, then
+// phi_{n-1} = (phi_n + asin((c_n / a_n) sin phi_n)) / 2, and
+// dn = cos(phi_0) / cos(phi_1 - phi_0)
+double agm_dn(double u, double kp) {
+  double a[64], c[64];
+  a[0] = 1.0;
+  c[0] = std::sqrt((1.0 - kp) * (1.0 + kp));
+  double b = kp;
+  int N = 0;
+  while (c[N] > 1e-16 * a[N] && N < 63) {
+    a[N + 1] = 0.5 * (a[N] + b);
+    c[N + 1] = c[N] * c[N] / (4.0 * a[N + 1]);
+    b = std::sqrt(a[N] * b);
+    ++N;
+  }
+  if (N == 0) return 1.0;
+  double phi = std::ldexp(a[N] * u, N);
+  double prev = phi;
+  for (int n = N; n >= 1; --n) {
+    prev = phi;
+    phi = 0.5 * (phi + std::asin(c[n] / a[n] * std::sin(phi)));
+  }
+  return std::cos(phi) / std::cos(prev - phi);
+}
+
+}  // namespace
+
+extern "C" igafd_status igafd_adi_wachspress(double a, double b, double eps, int max_J,
+                                             double *omega, int *J_out) {
+  if (!omega || !J_out || max_J < 1 || !(a > 0.0) || !(b >= a) || !std::isfinite(b) ||
+      !(eps > 0.0) || !(eps < 1.0))
+    return IGAFD_ERR_ARG;
+  // Eq. (ADIits)
+  const double pi = 3.14159265358979323846;
+  const double Jr = std::ceil(std::log(4.0 * b / a) * std::log(4.0 / eps) / (pi * pi));
+  const int J = Jr < 1.0 ? 1 : (int)Jr;
+  if (J > max_J) {
+    *J_out = max_J;
+    return IGAFD_ERR_NOT_CONVERGED;
+  }
+  if (a == b) {
+    for (int j = 0; j < J; ++j) omega[j] = a;
+  } else {
+    const double kp = a / b, K = agm_K(kp);
+    for (int j = 1; j <= J; ++j) {
+      const double u = (2 * j - 1) * K / (2.0 * J);
+      // dn(K - u) = k' / dn(u): evaluate dn only for u <= K / 2
+      omega[j - 1] = (2 * j - 1 <= J) ? b * agm_dn(u, kp) : a / agm_dn(K - u, kp);
+    }
+  }
+  *J_out = J;
+  return IGAFD_OK;
+}
+
 extern "C" igafd_status igafd_adi_parameters(igafd_patch *P, double eps, int max_J, double *omega,
                                              int *J_out) {
-  if (!P || P->dim != 3 || !omega || !J_out || max_J < 1 || !(eps > 0.0) || !(eps < 1.0))
+  if (!P || (P->dim != 2 && P->dim != 3) || !omega || !J_out || max_J < 1 || !(eps > 0.0) ||
+      !(eps < 1.0))
     return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   const int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
@@ -527,13 +650,18 @@ extern "C" igafd_status igafd_adi_parameters(igafd_patch *P, double eps, int max
   IGAFD_CUDA(cudaDeviceSynchronize());
   IGAFD_CUDA(cudaMemcpy(L1.data(), P->D[0], n1 * sizeof(double), cudaMemcpyDeviceToHost));
   IGAFD_CUDA(cudaMemcpy(L2.data(), P->D[1], n2 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (P->dim == 2) {
+    // the hull of the two spectra (Eq. (ADIits) assumes equal intervals)
+    const double a = std::min(L1[0], L2[0]), b = std::max(L1[n1 - 1], L2[n2 - 1]);
+    return igafd_adi_wachspress(a, b, eps, max_J, omega, J_out);
+  }
   IGAFD_CUDA(cudaMemcpy(L3.data(), P->D[2], n3 * sizeof(double), cudaMemcpyDeviceToHost));
   return igafd_adi_greedy(L1.data(), n1, L2.data(), n2, L3.data(), n3, eps, max_J, omega, J_out);
 }
 
 extern "C" igafd_status igafd_adi_setup(igafd_patch *P, const double *omega, int J, igafd_dtype dtype,
                                         void *stream) {
-  if (!P || P->dim != 3 || !omega || J < 1 || J > 100000 ||
+  if (!P || (P->dim != 2 && P->dim != 3) || !omega || J < 1 || J > 100000 ||
       (dtype != IGAFD_FP64 && dtype != IGAFD_FP32))
     return IGAFD_ERR_ARG;
   for (int j = 0; j < J; ++j)
@@ -548,6 +676,7 @@ extern "C" igafd_status igafd_adi_setup(igafd_patch *P, const double *omega, int
   S->fp32 = dtype == IGAFD_FP32;
   S->esz = S->fp32 ? sizeof(float) : sizeof(double);
   S->p = P->p;
+  S->dim = P->dim;
   for (int k = 0; k < 3; ++k) S->n[k] = P->n[k];
   S->omega = new double[J];
   std::copy(omega, omega + J, S->omega);
@@ -568,7 +697,7 @@ extern "C" igafd_status igafd_adi_setup(igafd_patch *P, const double *omega, int
       cudaMalloc(&work, (size_t)(J + 1) * nmax * (p + 1) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&dom, J * sizeof(double)) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess)
     return fail(IGAFD_ERR_OOM);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < P->dim; ++k) {
     const int n = P->n[k];
     if (cudaMalloc(&S->band[k], 2 * (size_t)n * (2 * p + 1) * S->esz) != cudaSuccess ||
         cudaMalloc(&S->fac[k], (size_t)(J + 1) * n * (p + 1) * S->esz) != cudaSuccess)
@@ -577,7 +706,7 @@ extern "C" igafd_status igafd_adi_setup(igafd_patch *P, const double *omega, int
   if (cudaMemcpyAsync(dom, omega, J * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess)
     return fail(IGAFD_ERR_CUDA);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < P->dim; ++k) {
     const int n = P->n[k];
     double *K = dense, *M = dense + (size_t)n * n;
     st = igafd_pencils_dense(P, k, K, M, s);

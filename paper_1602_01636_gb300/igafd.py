@@ -77,7 +77,8 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_patch_sepfit", "igafd_set_scalings", "igafd_mlp_create", "igafd_mlp_destroy",
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step",
-           "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi", "igafd_adi_greedy"]
+           "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi", "igafd_adi_greedy",
+           "igafd_adi_wachspress"]
 
 MLP_PARAMS = 4738
 
@@ -129,6 +130,8 @@ def lib():
     L.igafd_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, fp, vp]
     L.igafd_adi_parameters.argtypes = [vp, C.c_double, C.c_int, dp, C.POINTER(C.c_int)]
     L.igafd_adi_setup.argtypes = [vp, dp, C.c_int, C.c_int, vp]
+    L.igafd_adi_wachspress.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, dp,
+                                       C.POINTER(C.c_int)]
     L.igafd_adi_greedy.argtypes = [dp, C.c_int, dp, C.c_int, dp, C.c_int, C.c_double, C.c_int, dp,
                                    C.POINTER(C.c_int)]
     L.igafd_apply_prec_adi.argtypes = [vp, vp, vp, vp]
@@ -171,6 +174,18 @@ def adi_greedy(L1, L2, L3, eps, max_J=400):
     _check(lib().igafd_adi_greedy(ls[0].ctypes.data_as(dp), len(ls[0]), ls[1].ctypes.data_as(dp),
                                   len(ls[1]), ls[2].ctypes.data_as(dp), len(ls[2]), float(eps),
                                   int(max_J), w.ctypes.data_as(dp), C.byref(J)), "adi_greedy")
+    return w[:J.value].copy()
+
+
+def adi_wachspress(a, b, eps, max_J=400):
+    """Two-variable ADI: J of Eq. (ADIits) and the optimal parameters for the
+    spectral interval [a, b] (host arithmetic in the library; no GPU needed)."""
+    import numpy as _np
+    w = _np.zeros(max_J, dtype=_np.float64)
+    J = C.c_int()
+    _check(lib().igafd_adi_wachspress(float(a), float(b), float(eps), int(max_J),
+                                      w.ctypes.data_as(C.POINTER(C.c_double)), C.byref(J)),
+           "adi_wachspress")
     return w[:J.value].copy()
 
 
@@ -387,7 +402,8 @@ class Patch:
         return z
 
     def adi_parameters(self, eps, max_J=400):
-        """Greedy three-variable ADI parameters w_1..w_J with rho_J <= eps
+        """ADI parameters w_1..w_J for the tolerance eps: the optimal
+        two-variable parameters in 2D, the greedy three-variable ones in 3D
         (host arithmetic in the library over the patch's eigenvalues)."""
         import numpy as _np
         w = _np.zeros(max_J, dtype=_np.float64)

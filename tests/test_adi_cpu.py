@@ -48,3 +48,31 @@ def test_library_greedy_rejects_bad_input(igafd):
         igafd.adi_greedy([1.0], [1.0], [1.0], 1.5)
     with pytest.raises(igafd.IgafdError):           # max_J too small to reach eps
         igafd.adi_greedy([1.0, 1e4], [1.0, 1e4], [1.0, 1e4], 1e-12, max_J=2)
+
+
+@pytest.mark.parametrize("ratio", [1.0, 4.0, 1e2, 3.2e5, 1e8])
+@pytest.mark.parametrize("eps", [1e-1, 1e-8])
+def test_library_wachspress_matches_oracle(igafd, ratio, eps):
+    """Two-variable parameters: J of Eq. (ADIits) and the elliptic-function
+    parameters, the library's C against the oracle's Python (both by the
+    AGM method; rounding near u = K/2 grows like 1e-16 b/a)."""
+    a, b = 3.0, 3.0 * ratio
+    w = igafd.adi_wachspress(a, b, eps)
+    J = adi.adi_iterations_2d(a, b, eps) if ratio > 1 else max(1, adi.adi_iterations_2d(a, b, eps))
+    assert len(w) == J
+    w_ref = adi.wachspress_parameters(a, b, J)
+    assert np.allclose(w, w_ref, rtol=1e-14 + 4e-16 * ratio, atol=0)
+
+
+def test_library_wachspress_table_square(igafd):
+    """The library reproduces the iteration counts of Table "square" from the
+    closed-form p = 1 spectra (as the oracle's pin does)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table_adi_square.txt")
+    for h_s, p_s, J_s, _ in (l.split() for l in open(path) if l.strip() and l[0] != "#"):
+        if int(p_s) != 1:
+            continue
+        nel = int(h_s)
+        t = np.array([1, nel - 1]) * np.pi / nel
+        lam = 6.0 * nel ** 2 * (1 - np.cos(t)) / (2 + np.cos(t))
+        assert len(igafd.adi_wachspress(lam[0], lam[1], 1e-8)) == int(J_s)
