@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--learned", action="store_true",
                     help="learned span scalings: train on generated patches, compare on held-out ones")
     ap.add_argument("--adi", action="store_true",
-                    help="three-variable ADI preconditioner against the FD (applies/s)")
+                    help="three-variable ADI preconditioner against the FD (applies/s, PCG solve ms)")
     ap.add_argument("--sweep", action="store_true",
                     help="precision sweep: n in {128, 192}, p in {2..5}, every FD dtype")
     ap.add_argument("--train", type=int, default=2000,
