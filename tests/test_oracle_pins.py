@@ -514,3 +514,22 @@ def test_mlp_gradient_matches_finite_differences():
         lp, _ = learned.mlp_loss_grad(params + e, norm, X, T)
         lm, _ = learned.mlp_loss_grad(params - e, norm, X, T)
         assert abs((lp - lm) / (2 * h) - grad[i]) <= 1e-6 * max(1.0, abs(grad[i]))
+
+
+@pytest.mark.parametrize("dim,n", [(2, 9), (3, 7)])
+def test_fd_apply_flop_count(monkeypatch, dim, n):
+    """The FD apply costs 8 n^3 FLOPs in 2D and 12 n^4 in 3D (Sections 4.1 and
+    5.1.1): 2d dense mode products of 2 n^(d+1) FLOPs each (the divide by the
+    eigenvalue sums is of lower order). Counted on the oracle's products."""
+    disc = _disc(synth.Problem(dim, n, 2))
+    F = fd.FD([disc.pencil(k) for k in range(dim)])
+    count = [0]
+    real = fd.mode_product
+
+    def counting(X, W, k, d):
+        count[0] += 2 * W.shape[0] * W.shape[1] * (X.size // X.shape[d - 1 - k])
+        return real(X, W, k, d)
+
+    monkeypatch.setattr(fd, "mode_product", counting)
+    F.apply(synth.random_vector(disc.N, 1))
+    assert count[0] == (8 * n ** 3 if dim == 2 else 12 * n ** 4)
