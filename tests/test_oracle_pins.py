@@ -533,3 +533,19 @@ def test_fd_apply_flop_count(monkeypatch, dim, n):
     monkeypatch.setattr(fd, "mode_product", counting)
     F.apply(synth.random_vector(disc.N, 1))
     assert count[0] == (8 * n ** 3 if dim == 2 else 12 * n ** 4)
+
+
+def test_mode_product_is_the_kronecker_product():
+    """Section 2.2's Kronecker identities: the product along direction k of
+    a direction-1-fastest tensor is the matrix I (x) .. W .. (x) I, with W in
+    the factor of direction k (numpy's kron puts its first factor on the
+    slowest index)."""
+    g = synth.rng(3)
+    n = (4, 3, 5)                                       # n_1, n_2, n_3
+    X = g.standard_normal((n[2], n[1], n[0]))
+    for k in range(3):
+        W = g.standard_normal((n[k], n[k]))
+        mats = [np.eye(m) for m in n]
+        mats[k] = W
+        big = np.kron(np.kron(mats[2], mats[1]), mats[0])
+        assert np.allclose(fd.mode_product(X, W, k, 3).ravel(), big @ X.ravel(), atol=1e-13)
