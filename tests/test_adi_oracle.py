@@ -354,3 +354,19 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     monkeypatch.setattr(adi, "douglas_factor", wrong_sign)
     with pytest.raises(AssertionError):
         test_adi3d_equals_error_operator_formula()
+
+
+@pytest.mark.parametrize("ratio", [1e2, 1e4, 1e6, 1e8])
+@pytest.mark.parametrize("eps", [1e-2, 1e-5, 1e-8, 1e-11])
+def test_adiits_count_meets_the_tolerance(ratio, eps):
+    """Eq. (ADIits): with J = ceil(ln(4b/a) ln(4/eps)/pi^2) and the optimal
+    parameters, the bound of Eq. (Tjnorm) (the squared one-variable error on
+    [a, b]) is at most eps, and two iterations fewer do not reach it (the
+    formula overestimates the needed count by at most one)."""
+    a, b = 1.0, ratio
+    J = adi.adi_iterations_2d(a, b, eps)
+    x = np.exp(np.linspace(np.log(a), np.log(b), 200001))
+    err = lambda w: float(np.abs(adi.zolotarev_error(w, x)).max()) ** 2
+    assert err(adi.wachspress_parameters(a, b, J)) <= eps
+    if J > 2:
+        assert err(adi.wachspress_parameters(a, b, J - 2)) > eps
