@@ -128,6 +128,30 @@ class OracleSample:
                 f"(assembly excluded)")
 
 
+def cpu_model():
+    """The host CPU's model string: /proc/cpuinfo's model name, else lscpu's,
+    else the machine type."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip().lower() == "model name" and v.strip():
+                    return v.strip()
+    except OSError:
+        pass
+    try:
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip().lower() == "model name" and v.strip():
+                return v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline_entry(n, p, tol, reps=1):
     o = OracleSample(n, p, tol)
     vals, parts = [], None
@@ -135,7 +159,8 @@ def cpu_baseline_entry(n, p, tol, reps=1):
         v, parts = o.step()
         vals.append(v)
     v = statistics.median(vals)
-    return {"value": v, "unit": UNIT, "cores": o.cores, "kind": "oracle", "sample": o.describe(parts)}
+    return {"value": v, "unit": UNIT, "cores": o.cores, "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": o.describe(parts)}
 
 
 def run_reference(args):
@@ -158,8 +183,8 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": workload_name(args.n, args.p), "n": args.n, "p": args.p,
                        "tol": args.tol, "parallelism": "replicas"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": o.cores, "kind": "oracle",
-                             "sample": o.describe(parts)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": o.cores, "cpu_model": cpu_model(),
+                             "kind": "oracle", "sample": o.describe(parts)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
