@@ -441,6 +441,25 @@ igafd_status igafd_adi_setup(igafd_patch *patch, const double *omega_host, int J
 igafd_status igafd_apply_prec_adi(igafd_patch *patch, const double *r_dev,
                                   double *z_dev, void *stream);
 
+/* ---- Multi-patch numbering (Section 6) ----------------------------------
+ * Global C^0 space of conforming patches glued along whole sides, and its
+ * homogeneous Dirichlet set (every function on a side glued to nothing).
+ * m[q * dim + k]: B-splines of patch q in direction k (>= 2). glue[5 g ..]:
+ * {patch a, side a, patch b, side b, orientation}, side = 2 (direction) +
+ * (0: index 0, 1: last index); the functions of the two sides are matched
+ * in the order of their tangential indices (directions other than the
+ * side's, increasing), with orientation bit 0 reversing the first
+ * tangential direction of side a on side b, bit 1 the second (3D), bit 2
+ * exchanging them (3D). Outputs: global[off_q + local] (local index
+ * direction 1 fastest, patches concatenated; capacity sum_q prod_k m) the
+ * global function of each patch function, numbered in order of first
+ * appearance; fixed[g] = 1 for Dirichlet functions (capacity as global);
+ * *n_global. IGAFD_ERR_ARG for bad indices or sides of different sizes.
+ * Host only; needs no GPU. */
+igafd_status igafd_mp_numbering(int dim, int npatch, const int *m, int nglue,
+                                const int *glue, long long *global,
+                                unsigned char *fixed, long long *n_global);
+
 /* Number of kernels this library has enqueued in this process so far (all
  * devices, all patches); for launch accounting by benchmarks. */
 long long igafd_kernel_launches(void);

@@ -1,0 +1,127 @@
+// Conforming multi-patch numbering (Section 6): patches whose shared sides
+// carry the same trace space are glued C^0 by identifying the functions of
+// the two sides (the side's row of control points, matched in order, with an
+// optional reversal or exchange of the tangential directions). Functions on
+// sides that are glued to nothing carry the homogeneous Dirichlet condition.
+// This is the host-side index map of the multi-patch Schwarz preconditioner:
+// the global space, its Dirichlet set, and so the restriction R_i of each
+// subdomain.
+#include "common.cuh"
+
+#include <vector>
+
+namespace {
+
+// union-find with path halving; the smaller index becomes the root, so the
+// numbering below does not depend on the order of the glued sides
+struct Dsu {
+  std::vector<long long> parent;
+  explicit Dsu(long long n) : parent(n) {
+    for (long long i = 0; i < n; ++i) parent[i] = i;
+  }
+  long long find(long long x) {
+    while (parent[x] != x) {
+      parent[x] = parent[parent[x]];
+      x = parent[x];
+    }
+    return x;
+  }
+  void unite(long long a, long long b) {
+    a = find(a);
+    b = find(b);
+    if (a == b) return;
+    if (a < b) parent[b] = a; else parent[a] = b;
+  }
+};
+
+// local index of the t-th function (tangential coordinates ta, tb) of side s
+// of a patch with m[0..dim) functions per direction, direction 1 fastest
+long long side_index(int dim, const int *m, int side, int ta, int tb) {
+  const int dir = side / 2, hi = side % 2;
+  int idx[3] = {0, 0, 0};
+  idx[dir] = hi ? m[dir] - 1 : 0;
+  int t = 0;
+  for (int k = 0; k < dim; ++k) {
+    if (k == dir) continue;
+    idx[k] = t == 0 ? ta : tb;
+    ++t;
+  }
+  return idx[0] + (long long)m[0] * (idx[1] + (long long)m[1] * idx[2]);
+}
+
+// tangential extents of side s (the directions other than s / 2, in order)
+void side_extent(int dim, const int *m, int side, int *na, int *nb) {
+  const int dir = side / 2;
+  int t = 0, e[2] = {1, 1};
+  for (int k = 0; k < dim; ++k)
+    if (k != dir) e[t++] = m[k];
+  *na = e[0];
+  *nb = e[1];
+}
+
+}  // namespace
+
+extern "C" igafd_status igafd_mp_numbering(int dim, int npatch, const int *m, int nglue, const int *glue,
+                                           long long *global, unsigned char *fixed, long long *n_global) {
+  if ((dim != 2 && dim != 3) || npatch < 1 || !m || nglue < 0 || (nglue > 0 && !glue) || !global ||
+      !fixed || !n_global)
+    return IGAFD_ERR_ARG;
+  std::vector<long long> off(npatch + 1, 0);
+  for (int q = 0; q < npatch; ++q) {
+    long long sz = 1;
+    for (int k = 0; k < dim; ++k) {
+      if (m[q * dim + k] < 2) return IGAFD_ERR_ARG;
+      sz *= m[q * dim + k];
+    }
+    off[q + 1] = off[q] + sz;
+  }
+  const long long total = off[npatch];
+  Dsu dsu(total);
+  std::vector<unsigned char> glued((size_t)npatch * 2 * dim, 0);
+  for (int g = 0; g < nglue; ++g) {
+    const int *e = glue + 5 * g;
+    const int qa = e[0], sa = e[1], qb = e[2], sb = e[3], orient = e[4];
+    if (qa < 0 || qa >= npatch || qb < 0 || qb >= npatch || sa < 0 || sa >= 2 * dim || sb < 0 ||
+        sb >= 2 * dim || orient < 0 || orient > 7 || (qa == qb && sa == sb))
+      return IGAFD_ERR_ARG;
+    const int *ma = m + qa * dim, *mb = m + qb * dim;
+    int na1, na2, nb1, nb2;
+    side_extent(dim, ma, sa, &na1, &na2);
+    side_extent(dim, mb, sb, &nb1, &nb2);
+    const bool swap = (orient & 4) != 0;     // b's tangential directions exchanged
+    if ((swap ? nb2 : nb1) != na1 || (swap ? nb1 : nb2) != na2) return IGAFD_ERR_ARG;   // not conforming
+    for (int tb2 = 0; tb2 < na2; ++tb2)
+      for (int ta1 = 0; ta1 < na1; ++ta1) {
+        // a's (ta1, tb2) meets b's (u, v): orientation bit 0 reverses a's first
+        // tangential direction on b, bit 1 the second, bit 2 exchanges them
+        int u = (orient & 1) ? na1 - 1 - ta1 : ta1;
+        int v = (orient & 2) ? na2 - 1 - tb2 : tb2;
+        if (swap) { const int t = u; u = v; v = t; }
+        dsu.unite(off[qa] + side_index(dim, ma, sa, ta1, tb2), off[qb] + side_index(dim, mb, sb, u, v));
+      }
+    glued[(size_t)qa * 2 * dim + sa] = 1;
+    glued[(size_t)qb * 2 * dim + sb] = 1;
+  }
+  // global ids in order of first appearance (patches in order, direction 1 fastest)
+  std::vector<long long> id_of_root(total, -1);
+  long long ng = 0;
+  for (long long t = 0; t < total; ++t) {
+    const long long r = dsu.find(t);
+    if (id_of_root[r] < 0) id_of_root[r] = ng++;
+    global[t] = id_of_root[r];
+  }
+  for (long long g = 0; g < ng; ++g) fixed[g] = 0;
+  // Dirichlet: every function of a side that is glued to nothing
+  for (int q = 0; q < npatch; ++q) {
+    const int *mq = m + q * dim;
+    for (int side = 0; side < 2 * dim; ++side) {
+      if (glued[(size_t)q * 2 * dim + side]) continue;
+      int n1, n2;
+      side_extent(dim, mq, side, &n1, &n2);
+      for (int b = 0; b < n2; ++b)
+        for (int a = 0; a < n1; ++a) fixed[global[off[q] + side_index(dim, mq, side, a, b)]] = 1;
+    }
+  }
+  *n_global = ng;
+  return IGAFD_OK;
+}

@@ -78,7 +78,7 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step",
            "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi", "igafd_adi_greedy",
-           "igafd_adi_wachspress"]
+           "igafd_adi_wachspress", "igafd_mp_numbering"]
 
 MLP_PARAMS = 4738
 
@@ -130,6 +130,8 @@ def lib():
     L.igafd_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, fp, vp]
     L.igafd_adi_parameters.argtypes = [vp, C.c_double, C.c_int, dp, C.POINTER(C.c_int)]
     L.igafd_adi_setup.argtypes = [vp, dp, C.c_int, C.c_int, vp]
+    L.igafd_mp_numbering.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_longlong), C.POINTER(C.c_ubyte), C.POINTER(C.c_longlong)]
     L.igafd_adi_wachspress.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, dp,
                                        C.POINTER(C.c_int)]
     L.igafd_adi_greedy.argtypes = [dp, C.c_int, dp, C.c_int, dp, C.c_int, C.c_double, C.c_int, dp,
@@ -187,6 +189,32 @@ def adi_wachspress(a, b, eps, max_J=400):
                                       w.ctypes.data_as(C.POINTER(C.c_double)), C.byref(J)),
            "adi_wachspress")
     return w[:J.value].copy()
+
+
+def mp_numbering(m, glue):
+    """Multi-patch numbering (host arithmetic in the library; no GPU needed).
+    m: [npatch][dim] functions per direction; glue: [(patch a, side a,
+    patch b, side b, orientation), ...]. Returns (global ids per patch as a
+    list of arrays shaped [m_d..m_1], fixed flags per global function)."""
+    import numpy as _np
+    m = _np.ascontiguousarray(m, dtype=_np.int32)
+    npatch, dim = m.shape
+    g = _np.ascontiguousarray(glue, dtype=_np.int32).reshape(-1, 5)
+    sizes = [int(_np.prod(row)) for row in m]
+    total = sum(sizes)
+    glob = _np.zeros(total, dtype=_np.int64)
+    fixed = _np.zeros(total, dtype=_np.uint8)
+    ng = C.c_longlong()
+    ip = C.POINTER(C.c_int)
+    _check(lib().igafd_mp_numbering(dim, npatch, m.ctypes.data_as(ip), len(g), g.ctypes.data_as(ip),
+                                    glob.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                    fixed.ctypes.data_as(C.POINTER(C.c_ubyte)), C.byref(ng)),
+           "mp_numbering")
+    out, o = [], 0
+    for q in range(npatch):
+        out.append(glob[o:o + sizes[q]].reshape(tuple(int(v) for v in m[q][::-1])))
+        o += sizes[q]
+    return out, fixed[:ng.value].astype(bool)
 
 
 def kernel_launches():
