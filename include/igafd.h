@@ -460,6 +460,19 @@ igafd_status igafd_mp_numbering(int dim, int npatch, const int *m, int nglue,
                                 const int *glue, long long *global,
                                 unsigned char *fixed, long long *n_global);
 
+/* Subdomain of two glued patches qa, qb (Section 6): the single patch made
+ * of them along direction dir (patch a's functions first, b's after the
+ * shared side; their other directions must match and a's last side in dir
+ * must be glued to b's first one in order). rows[] (capacity the product of
+ * shape) gets, in the merged patch's order with Dirichlet rows removed
+ * (direction 1 fastest), the global function of each of its interior
+ * functions, i.e. the rows of R_i; shape[0..dim) its interior sizes. Inputs
+ * as returned by igafd_mp_numbering. IGAFD_ERR_ARG when the patches are not
+ * glued that way or an interior function is fixed. Host only. */
+igafd_status igafd_mp_subdomain(int dim, int npatch, const int *m,
+                                const long long *global, const unsigned char *fixed,
+                                int qa, int qb, int dir, long long *rows, int *shape);
+
 /* Number of kernels this library has enqueued in this process so far (all
  * devices, all patches); for launch accounting by benchmarks. */
 long long igafd_kernel_launches(void);

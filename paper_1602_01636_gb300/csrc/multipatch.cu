@@ -125,3 +125,46 @@ extern "C" igafd_status igafd_mp_numbering(int dim, int npatch, const int *m, in
   *n_global = ng;
   return IGAFD_OK;
 }
+
+extern "C" igafd_status igafd_mp_subdomain(int dim, int npatch, const int *m, const long long *global,
+                                           const unsigned char *fixed, int qa, int qb, int dir,
+                                           long long *rows, int *shape) {
+  if ((dim != 2 && dim != 3) || !m || !global || !fixed || !rows || !shape || qa < 0 || qa >= npatch ||
+      qb < 0 || qb >= npatch || qa == qb || dir < 0 || dir >= dim)
+    return IGAFD_ERR_ARG;
+  std::vector<long long> off(npatch + 1, 0);
+  for (int q = 0; q < npatch; ++q) {
+    long long sz = 1;
+    for (int k = 0; k < dim; ++k) sz *= m[q * dim + k];
+    off[q + 1] = off[q] + sz;
+  }
+  const int *ma = m + qa * dim, *mb = m + qb * dim;
+  for (int k = 0; k < dim; ++k)
+    if (k != dir && ma[k] != mb[k]) return IGAFD_ERR_ARG;
+  // the merged patch: a's functions, then b's beyond the shared side
+  int mm[3] = {1, 1, 1};
+  for (int k = 0; k < dim; ++k) mm[k] = k == dir ? ma[k] + mb[k] - 1 : ma[k];
+  for (int k = 0; k < dim; ++k) shape[k] = mm[k] - 2;
+  long long t = 0;
+  const int hi3 = dim == 3 ? mm[2] - 1 : 1, lo3 = dim == 3 ? 1 : 0;
+  for (int j3 = lo3; j3 < hi3; ++j3)
+    for (int j2 = 1; j2 < mm[1] - 1; ++j2)
+      for (int j1 = 1; j1 < mm[0] - 1; ++j1) {
+        int j[3] = {j1, j2, j3};
+        const bool in_a = j[dir] <= ma[dir] - 1;
+        const int *mq = in_a ? ma : mb;
+        if (!in_a) j[dir] -= ma[dir] - 1;
+        const long long loc = j[0] + (long long)mq[0] * (j[1] + (long long)mq[1] * (dim == 3 ? j[2] : 0));
+        const long long gid = global[(in_a ? off[qa] : off[qb]) + loc];
+        if (in_a && j[dir] == ma[dir] - 1) {
+          // the shared side: a's last functions must be b's first ones
+          int jb[3] = {j[0], j[1], j[2]};
+          jb[dir] = 0;
+          const long long lb = jb[0] + (long long)mb[0] * (jb[1] + (long long)mb[1] * (dim == 3 ? jb[2] : 0));
+          if (global[off[qb] + lb] != gid) return IGAFD_ERR_ARG;   // not glued in this order
+        }
+        if (fixed[gid]) return IGAFD_ERR_ARG;      // an interior function of the subdomain is fixed
+        rows[t++] = gid;
+      }
+  return IGAFD_OK;
+}

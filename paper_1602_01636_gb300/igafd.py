@@ -78,7 +78,7 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step",
            "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi", "igafd_adi_greedy",
-           "igafd_adi_wachspress", "igafd_mp_numbering"]
+           "igafd_adi_wachspress", "igafd_mp_numbering", "igafd_mp_subdomain"]
 
 MLP_PARAMS = 4738
 
@@ -132,6 +132,9 @@ def lib():
     L.igafd_adi_setup.argtypes = [vp, dp, C.c_int, C.c_int, vp]
     L.igafd_mp_numbering.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
                                      C.POINTER(C.c_longlong), C.POINTER(C.c_ubyte), C.POINTER(C.c_longlong)]
+    L.igafd_mp_subdomain.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                     C.POINTER(C.c_ubyte), C.c_int, C.c_int, C.c_int,
+                                     C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
     L.igafd_adi_wachspress.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, dp,
                                        C.POINTER(C.c_int)]
     L.igafd_adi_greedy.argtypes = [dp, C.c_int, dp, C.c_int, dp, C.c_int, C.c_double, C.c_int, dp,
@@ -215,6 +218,27 @@ def mp_numbering(m, glue):
         out.append(glob[o:o + sizes[q]].reshape(tuple(int(v) for v in m[q][::-1])))
         o += sizes[q]
     return out, fixed[:ng.value].astype(bool)
+
+
+def mp_subdomain(m, glob, fixed, qa, qb, direction):
+    """Rows of R_i for the subdomain of glued patches qa, qb merged along
+    `direction` (host arithmetic in the library): (global ids in the merged
+    patch's interior order, interior shape per direction)."""
+    import numpy as _np
+    m = _np.ascontiguousarray(m, dtype=_np.int32)
+    npatch, dim = m.shape
+    gl = _np.ascontiguousarray(_np.concatenate([g.ravel() for g in glob]), dtype=_np.int64)
+    fx = _np.ascontiguousarray(fixed, dtype=_np.uint8)
+    cap = int(_np.prod([m[qa][k] + (m[qb][k] if k == direction else 0) for k in range(dim)]))
+    rows = _np.zeros(cap, dtype=_np.int64)
+    shape = (C.c_int * 3)()
+    _check(lib().igafd_mp_subdomain(dim, npatch, m.ctypes.data_as(C.POINTER(C.c_int)),
+                                    gl.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                    fx.ctypes.data_as(C.POINTER(C.c_ubyte)), qa, qb, direction,
+                                    rows.ctypes.data_as(C.POINTER(C.c_longlong)), shape),
+           "mp_subdomain")
+    shp = tuple(int(shape[k]) for k in range(dim))
+    return rows[:int(_np.prod(shp))].copy(), shp
 
 
 def kernel_launches():

@@ -82,3 +82,30 @@ def test_numbering_rejects_nonconforming_sides(igafd):
         igafd.mp_numbering([[4, 4], [4, 5]], [(0, 1, 1, 0, 0)])   # sides of 4 and 5 functions
     with pytest.raises(igafd.IgafdError):
         igafd.mp_numbering([[4, 4], [4, 4]], [(0, 7, 1, 0, 0)])   # no side 7 in 2D
+
+
+@pytest.mark.parametrize("nel,p", [(4, 1), (6, 2), (5, 3)])
+def test_lshape_subdomains_match_oracle(igafd, nel, p):
+    """The rows of R_1 and R_2 (library) equal the oracle's, in the merged
+    patches' order."""
+    L = mpm.LShape(synth.uniform_open_knots(nel, p), p)
+    m = L.m
+    glue = [(1, 3, 0, 2, 0), (1, 1, 2, 0, 0)]
+    glob, fixed = igafd.mp_numbering([[m, m]] * 3, glue)
+    lib_ids = np.concatenate([g.ravel() for g in glob])
+    ora_ids = np.concatenate([L.local_to_global[q].ravel() for q in (1, 2, 3)])
+    to_oracle = dict(zip(lib_ids.tolist(), ora_ids.tolist()))
+    # Theta_1 = Omega_2 (patch 1) then Omega_1 (patch 0) along direction 2;
+    # Theta_2 = Omega_2 then Omega_3 (patch 2) along direction 1
+    for i, (qa, qb, d) in enumerate([(1, 0, 1), (1, 2, 0)]):
+        rows, shape = igafd.mp_subdomain([[m, m]] * 3, glob, fixed, qa, qb, d)
+        idx, (n1, n2) = L.sub[i]
+        assert shape == (n1, n2)
+        assert np.array_equal(L.index[[to_oracle[g] for g in rows.tolist()]], idx)
+
+
+def test_subdomain_rejects_unglued_pair(igafd):
+    m = 5
+    glob, fixed = igafd.mp_numbering([[m, m]] * 3, [(1, 3, 0, 2, 0), (1, 1, 2, 0, 0)])
+    with pytest.raises(igafd.IgafdError):
+        igafd.mp_subdomain([[m, m]] * 3, glob, fixed, 0, 2, 0)      # Omega_1 and Omega_3 share no side
