@@ -473,6 +473,24 @@ igafd_status igafd_mp_subdomain(int dim, int npatch, const int *m,
                                 const long long *global, const unsigned char *fixed,
                                 int qa, int qb, int dir, long long *rows, int *shape);
 
+/* Additive Schwarz preconditioner P_IAS = sum_i R_i^T P_i^{-1} R_i
+ * (Eq. (Pias)) of a multi-patch problem: subdomain i is the single patch
+ * patches[i] (e.g. two glued patches merged into one, built without a
+ * stencil), P_i^{-1} its fast-diagonalization solve, and rows[i][0..N_i)
+ * (host, N_i the patch's dofs, distinct, in [0, n_global)) the global
+ * function of each of its dofs. The object does not own the patches, which
+ * must outlive it. Errors: ARG, OOM, CUDA. */
+typedef struct igafd_mp igafd_mp;
+igafd_status igafd_mp_create(int nsub, igafd_patch *const *patches,
+                             const long long *const *rows, long long n_global,
+                             igafd_mp **out);
+void igafd_mp_destroy(igafd_mp *mp);
+/* z = P_IAS r: z = 0, then per subdomain a gather R_i r, the patch's FD in
+ * dtype, and a scatter-add R_i^T (2 kernels + the FD's per subdomain).
+ * r_dev, z_dev: length-n_global FP64 device vectors, not overlapping. */
+igafd_status igafd_mp_apply_ias(igafd_mp *mp, igafd_dtype dtype, const double *r_dev,
+                                double *z_dev, void *stream);
+
 /* Number of kernels this library has enqueued in this process so far (all
  * devices, all patches); for launch accounting by benchmarks. */
 long long igafd_kernel_launches(void);

@@ -8,6 +8,7 @@
 // subdomain.
 #include "common.cuh"
 
+#include <algorithm>
 #include <vector>
 
 namespace {
@@ -166,5 +167,119 @@ extern "C" igafd_status igafd_mp_subdomain(int dim, int npatch, const int *m, co
         if (fixed[gid]) return IGAFD_ERR_ARG;      // an interior function of the subdomain is fixed
         rows[t++] = gid;
       }
+  return IGAFD_OK;
+}
+
+// ---- additive Schwarz preconditioner P_IAS (Eq. (Pias)) on the device ----
+
+struct igafd_mp {
+  int nsub = 0, dev = 0;
+  long long n = 0;                          // global (free) functions
+  std::vector<igafd_patch *> patches;       // subdomain patches (owned by the caller)
+  std::vector<long long *> rows;            // device rows of R_i
+  std::vector<long long> len;               // N_i
+  double *tr = nullptr, *tz = nullptr;      // subdomain vectors, max N_i each
+};
+
+namespace {
+
+// y[t] = x[rows[t]]: R_i x
+__global__ void gather_kernel(const double *__restrict__ x, const long long *__restrict__ rows, long long n,
+                              double *__restrict__ y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] = x[rows[t]];
+}
+
+// z[rows[t]] += y[t]: R_i^T y (the rows of one subdomain are distinct, so
+// one launch per subdomain needs no atomics)
+__global__ void scatter_add_kernel(const double *__restrict__ y, const long long *__restrict__ rows, long long n,
+                                   double *__restrict__ z) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    z[rows[t]] += y[t];
+}
+
+void free_mp(igafd_mp *M) {
+  if (!M) return;
+  for (long long *r : M->rows) cudaFree(r);
+  cudaFree(M->tr);
+  cudaFree(M->tz);
+  delete M;
+}
+
+}  // namespace
+
+extern "C" igafd_status igafd_mp_create(int nsub, igafd_patch *const *patches, const long long *const *rows,
+                                        long long n_global, igafd_mp **out) {
+  if (!out) return IGAFD_ERR_ARG;
+  *out = nullptr;
+  if (nsub < 1 || !patches || !rows || n_global < 1) return IGAFD_ERR_ARG;
+  for (int i = 0; i < nsub; ++i) {
+    if (!patches[i] || !rows[i] || patches[i]->dev != patches[0]->dev) return IGAFD_ERR_ARG;
+    std::vector<unsigned char> seen((size_t)n_global, 0);
+    for (long long t = 0; t < patches[i]->N; ++t) {
+      const long long g = rows[i][t];
+      if (g < 0 || g >= n_global || seen[(size_t)g]) return IGAFD_ERR_ARG;   // in range, distinct
+      seen[(size_t)g] = 1;
+    }
+  }
+  IGAFD_CUDA(cudaSetDevice(patches[0]->dev));
+  igafd_mp *M = new igafd_mp();
+  M->nsub = nsub;
+  M->dev = patches[0]->dev;
+  M->n = n_global;
+  long long nmax = 0;
+  for (int i = 0; i < nsub; ++i) {
+    const long long n = patches[i]->N;
+    long long *d = nullptr;
+    if (cudaMalloc(&d, n * sizeof(long long)) != cudaSuccess) {
+      cudaGetLastError();
+      free_mp(M);
+      return IGAFD_ERR_OOM;
+    }
+    M->rows.push_back(d);
+    if (cudaMemcpy(d, rows[i], n * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_mp(M);
+      return IGAFD_ERR_CUDA;
+    }
+    M->patches.push_back(patches[i]);
+    M->len.push_back(n);
+    nmax = std::max(nmax, n);
+  }
+  if (cudaMalloc(&M->tr, nmax * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&M->tz, nmax * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    free_mp(M);
+    return IGAFD_ERR_OOM;
+  }
+  *out = M;
+  return IGAFD_OK;
+}
+
+extern "C" void igafd_mp_destroy(igafd_mp *M) {
+  if (!M) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(M->dev);
+  free_mp(M);
+  if (cur >= 0) cudaSetDevice(cur);
+}
+
+extern "C" igafd_status igafd_mp_apply_ias(igafd_mp *M, igafd_dtype dtype, const double *r, double *z,
+                                           void *stream) {
+  if (!M || !r || !z || r == z) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(M->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  IGAFD_CUDA(cudaMemsetAsync(z, 0, M->n * sizeof(double), s));
+  for (int i = 0; i < M->nsub; ++i) {
+    const long long n = M->len[i];
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 152 * 8);
+    gather_kernel<<<grid, 256, 0, s>>>(r, M->rows[i], n, M->tr);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+    IGAFD_TRY(igafd_apply_prec(M->patches[i], dtype, M->tr, M->tz, s));   // P_i^{-1}, fast diagonalization
+    scatter_add_kernel<<<grid, 256, 0, s>>>(M->tz, M->rows[i], n, z);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+  }
   return IGAFD_OK;
 }

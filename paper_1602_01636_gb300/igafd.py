@@ -78,7 +78,8 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_mlp_set_normalization", "igafd_mlp_get_params", "igafd_mlp_set_params",
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step",
            "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi", "igafd_adi_greedy",
-           "igafd_adi_wachspress", "igafd_mp_numbering", "igafd_mp_subdomain"]
+           "igafd_adi_wachspress", "igafd_mp_numbering", "igafd_mp_subdomain", "igafd_mp_create",
+           "igafd_mp_destroy", "igafd_mp_apply_ias"]
 
 MLP_PARAMS = 4738
 
@@ -135,6 +136,11 @@ def lib():
     L.igafd_mp_subdomain.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
                                      C.POINTER(C.c_ubyte), C.c_int, C.c_int, C.c_int,
                                      C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+    L.igafd_mp_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(C.POINTER(C.c_longlong)),
+                                  C.c_longlong, C.POINTER(vp)]
+    L.igafd_mp_destroy.argtypes = [vp]
+    L.igafd_mp_destroy.restype = None
+    L.igafd_mp_apply_ias.argtypes = [vp, C.c_int, vp, vp, vp]
     L.igafd_adi_wachspress.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, dp,
                                        C.POINTER(C.c_int)]
     L.igafd_adi_greedy.argtypes = [dp, C.c_int, dp, C.c_int, dp, C.c_int, C.c_double, C.c_int, dp,
@@ -148,7 +154,7 @@ def lib():
     L.igafd_kernel_launches.restype = C.c_longlong
     for name in EXPORTS:
         if name not in ("igafd_destroy_patch", "igafd_pcg_default_opts", "igafd_status_str",
-                        "igafd_kernel_launches", "igafd_mlp_destroy"):
+                        "igafd_kernel_launches", "igafd_mlp_destroy", "igafd_mp_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -509,6 +515,42 @@ class Patch:
     def close(self):
         if getattr(self, "h", None):
             lib().igafd_destroy_patch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Schwarz:
+    """The additive Schwarz preconditioner P_IAS = sum_i R_i^T P_i^{-1} R_i
+    (Eq. (Pias)) on the GPU: patches[i] is subdomain i as one patch, rows[i]
+    the global (free) index of each of its dofs, n the global size."""
+
+    def __init__(self, patches, rows, n):
+        import numpy as _np
+        k = len(patches)
+        self._patches = list(patches)
+        self._rows = [_np.ascontiguousarray(r, dtype=_np.int64) for r in rows]
+        lp = C.POINTER(C.c_longlong)
+        hs = (C.c_void_p * k)(*[pt.h for pt in self._patches])
+        rp = (lp * k)(*[r.ctypes.data_as(lp) for r in self._rows])
+        h = C.c_void_p()
+        _check(lib().igafd_mp_create(k, hs, rp, int(n), C.byref(h)), "mp_create")
+        self.h, self.n = h, int(n)
+
+    def apply(self, r, z=None, dtype="fp64"):
+        import torch
+        z = torch.empty_like(r) if z is None else z
+        _check(lib().igafd_mp_apply_ias(self.h, DTYPES[dtype], _dev_ptr(r, self.n), _dev_ptr(z, self.n),
+                                        _stream()), "mp_apply_ias")
+        return z
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().igafd_mp_destroy(self.h)
             self.h = None
 
     def __del__(self):
