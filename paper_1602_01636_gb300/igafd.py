@@ -534,6 +534,8 @@ class Schwarz:
         k = len(patches)
         self._patches = list(patches)
         self._rows = [_np.ascontiguousarray(r, dtype=_np.int64) for r in rows]
+        if len(self._rows) != k or any(len(r) != pt.N for r, pt in zip(self._rows, self._patches)):
+            raise ValueError("rows[i] must hold one global index per dof of patches[i]")
         lp = C.POINTER(C.c_longlong)
         hs = (C.c_void_p * k)(*[pt.h for pt in self._patches])
         rp = (lp * k)(*[r.ctypes.data_as(lp) for r in self._rows])

@@ -86,3 +86,5 @@ def test_schwarz_rejects_bad_rows(torch):
         igafd.Schwarz(S._patches, bad, S.n)
     with pytest.raises(igafd.IgafdError):
         igafd.Schwarz(S._patches, S._rows, S.n - 5)       # rows out of range
+    with pytest.raises(ValueError):
+        igafd.Schwarz(S._patches, [S._rows[0][:-1], S._rows[1]], S.n)   # one row short
