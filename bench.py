@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--learned", action="store_true",
                     help="learned span scalings: train on generated patches, compare on held-out ones")
+    ap.add_argument("--cube", action="store_true",
+                    help="FD direct solves on the unit cube (P = A) over h and p, as in the paper's cube table")
     ap.add_argument("--adi", action="store_true",
                     help="three-variable ADI preconditioner against the FD (applies/s, PCG solve ms)")
     ap.add_argument("--sweep", action="store_true",
@@ -819,8 +821,59 @@ def run_adi(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cube(args):
+    """The paper's direct-solver workload on the unit cube (Section 7.2, Table
+    "cube", upper part): P = A for the identity map, so one FD apply solves
+    the system; b i.i.d. N(0, 1). For h^-1 in {128, 256, 512, 1024} (n_k =
+    h^-1 + p - 2 <= 1024, the eigensolver's limit) and p = 1..6: the set-up of
+    P (1D pencils, generalized eigendecompositions, FD tables; built without
+    the stiffness stencil, which the solve does not use), and one FD apply in
+    FP64 and in the fastest mixed form available (TF32 tensor cores for
+    n_k <= 256, else FP32), each timed with CUDA events after a warm-up. The
+    paper's times (MATLAB, one core) include its set-up."""
+    import torch
+    import synth
+    from paper_1602_01636_gb300 import igafd, build as libbuild
+    libbuild.build()
+    rows = []
+    for nel in (128, 256, 512, 1024):
+        for p in range(1, 7):
+            n = nel + p - 2
+            if n > 1024:
+                continue
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            patch = igafd.Patch.from_problem(synth.Problem(3, n, p), stencil=False)
+            torch.cuda.synchronize()
+            setup_s = time.perf_counter() - t0
+            g = torch.Generator(device="cuda").manual_seed(nel + p)
+            b = torch.randn(patch.N, dtype=torch.float64, device="cuda", generator=g)
+            x = torch.empty_like(b)
+            row = {"h_inv": nel, "p": p, "n": n, "N": patch.N, "setup_s": setup_s,
+                   "eig_ms": patch.info.eig_ms}
+            for dt in ("fp64", "tf32" if n <= 256 else "fp32"):
+                patch.apply_prec(b, x, dtype=dt)
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                patch.apply_prec(b, x, dtype=dt)
+                c.record()
+                torch.cuda.synchronize()
+                row[f"apply_{dt}_s"] = a.elapsed_time(c) / 1e3
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            patch.close()
+            del b, x
+            torch.cuda.empty_cache()
+    line = {"metric": "FD direct solve on the unit cube (P = A): set-up and apply seconds per h and p",
+            "value": None, "unit": "table", "data": "synthetic", "n_gpus": 1, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.cube:
+        run_cube(args)
+        return
     if args.adi:
         run_adi(args)
         return
