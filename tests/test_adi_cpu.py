@@ -76,3 +76,21 @@ def test_library_wachspress_table_square(igafd):
         t = np.array([1, nel - 1]) * np.pi / nel
         lam = 6.0 * nel ** 2 * (1 - np.cos(t)) / (2 + np.cos(t))
         assert len(igafd.adi_wachspress(lam[0], lam[1], 1e-8)) == int(J_s)
+
+
+def test_library_wachspress_table_square_all_degrees(igafd):
+    """Every printed J of Table "square" at h^-1 = 512 from the library's
+    Eq. (ADIits) on the exact pencil extremes, and ||T_J|| of the library's
+    parameters within the printed final error and 1e-8 (Table "relerr")."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table_adi_square.txt")
+    for h_s, p_s, J_s, err_s in (l.split() for l in open(path) if l.strip() and l[0] != "#"):
+        if int(h_s) != 512:
+            continue
+        p = int(p_s)
+        kn = synth.uniform_open_knots(512, p)
+        geo = assemble.Geometry(np.zeros((1, len(kn) - p - 1)), [kn], p)
+        lam = adi.pencil_spectrum(*assemble.Discretization([kn], p, geo).pencil(0))
+        w = igafd.adi_wachspress(lam[0], lam[-1], 1e-8)
+        assert len(w) == int(J_s)
+        assert float(err_s) <= adi.t_norm_2d(w, w, lam, lam) <= 1e-8
