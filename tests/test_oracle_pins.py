@@ -549,3 +549,41 @@ def test_mode_product_is_the_kronecker_product():
         mats[k] = W
         big = np.kron(np.kron(mats[2], mats[1]), mats[0])
         assert np.allclose(fd.mode_product(X, W, k, 3).ravel(), big @ X.ravel(), atol=1e-13)
+
+
+def _pencil_triple(knots, p):
+    """1D M, K and the mixed G_ij = int B_i' B_j (Dirichlet rows and columns
+    removed), from the basis at a Gauss rule exact for their integrands."""
+    z, w, _ = spline.gauss_points(knots, p + 1)
+    z, w = z.ravel(), w.ravel()
+    V = spline.basis_table(knots, p, z)
+    D = spline.basis_table(knots, p, z, deriv=True)
+    M = (V * w[:, None]).T @ V
+    K = (D * w[:, None]).T @ D
+    G = (D * w[:, None]).T @ V
+    return M[1:-1, 1:-1], K[1:-1, 1:-1], G[1:-1, 1:-1]
+
+
+def test_general_affine_map_closed_form():
+    """x = B zeta with a full matrix B (det > 0): Q = |det B| B^-1 B^-T is
+    constant and A = sum_{k,l} Q_kl (x)_m F_m with F_m = K_m (m = k = l),
+    G_m (m = k != l), G_m^T (m = l != k), M_m otherwise (direction 1
+    fastest). Pins every entry of Q, its transposition included."""
+    B = np.array([[1.1, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.3]])
+    p = 2
+    pr = synth.Problem(3, (5, 4, 6), p)
+    pr.ctrl = np.einsum("ij,j...->i...", B, pr.ctrl)    # Greville net of the identity, mapped by B
+    disc = _disc(pr)
+    A = assemble.stencil_to_csr(disc, disc.assemble_stencil()).toarray()
+    Binv = np.linalg.inv(B)
+    Q = abs(np.linalg.det(B)) * Binv @ Binv.T
+    F = [_pencil_triple(kn, p) for kn in pr.knots]      # (M, K, G) per direction
+    expect = 0
+    for k in range(3):
+        for l in range(3):
+            fac = []
+            for m in range(3):
+                Mm, Km, Gm = F[m]
+                fac.append(Km if m == k == l else Gm if m == k else Gm.T if m == l else Mm)
+            expect = expect + Q[k, l] * np.kron(fac[2], np.kron(fac[1], fac[0]))
+    assert np.abs(A - expect).max() <= 1e-13 * np.abs(A).max()
