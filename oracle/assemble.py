@@ -15,6 +15,7 @@ Readings of the paper used here:
 from __future__ import annotations
 
 import itertools
+import os
 
 import numpy as np
 import scipy.sparse as sp
@@ -200,13 +201,17 @@ class Discretization:
         V = [box["V"][k][eidx[k]] for k in range(d)]
         D = [box["D"][k][eidx[k]] for k in range(d)]
         W = self._tprod([box["W"][k][eidx[k]][:, :, None] for k in range(d)])[:, :, 0]
+        # dB_a/dzeta_r at the element's quadrature points g: G[e, a, r, g]
         G = np.stack([self._tprod([D[k] if k == r else V[k] for k in range(d)])
-                      for r in range(d)], axis=-1)            # [E, G, A, r]
-        Qe = self._gather_grid(box["Q"], eidx)                # [E, G, r, s]
-        H = np.einsum("eg,egrs,egbs->egbr", W, Qe, G)
-        E, Gn, A, _ = G.shape
-        L = np.matmul(G.transpose(0, 2, 1, 3).reshape(E, A, Gn * d),
-                      H.transpose(0, 1, 3, 2).reshape(E, Gn * d, A))
+                      for r in range(d)], axis=-1)
+        G = np.ascontiguousarray(G.transpose(0, 2, 3, 1))
+        Qe = self._gather_grid(box["Q"], eidx)                # [E, g, r, s]
+        QW = np.ascontiguousarray((Qe * W[:, :, None, None]).transpose(0, 2, 3, 1))  # [E, r, s, g]
+        # H[e, b, r, g] = w_g sum_s Q_rs(g) dB_b/dzeta_s(g), the d-term sum written out
+        H = sum(QW[:, None, :, s, :] * G[:, :, s, None, :] for s in range(d))
+        E, A, _, Gn = G.shape
+        # L[e, a, b] = sum_{r, g} G[e, a, r, g] H[e, b, r, g]
+        L = np.matmul(G.reshape(E, A, d * Gn), H.reshape(E, A, d * Gn).transpose(0, 2, 1))
         return L
 
     def _local_full_indices(self, box, eidx):
@@ -240,25 +245,84 @@ class Discretization:
             s *= self.n[k]
         return r
 
-    def assemble_stencil(self, chunk_planes=1):
-        """Full stiffness matrix A as the offset array S[o, row]."""
-        d, p = self.d, self.p
-        S = np.zeros(self.n_offsets() * self.N)
+    def assemble_stencil(self, chunk_planes=1, workers=1):
+        """Full stiffness matrix A as the offset array S[o, row]: the element
+        matrices of Eq. (A) summed into the rows of their basis functions,
+        element planes of the slowest direction in increasing order (each
+        plane in blocks along the next direction).
+
+        workers > 1 splits the planes into that many contiguous ranges, each
+        summed by its own (spawned) process from zero in plane order; the
+        range sums are then added in range order. Only the association of the
+        per-row sums changes (entries agree with workers=1 to rounding)."""
+        d = self.d
         last = d - 1
-        for e0 in range(0, self.nel[last], chunk_planes):
+        planes = [(e0, min(e0 + chunk_planes, self.nel[last]))
+                  for e0 in range(0, self.nel[last], chunk_planes)]
+        S = np.zeros((self.n_offsets(), self.N))
+        workers = max(1, min(int(workers), len(planes)))
+        if workers == 1:
+            for e0, e1 in planes:
+                for elo, ehi in self._plane_boxes(e0, e1):
+                    self._scatter_box(S, elo, ehi)
+            return S
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        bounds = np.linspace(0, len(planes), workers + 1).round().astype(int)
+        jobs = [planes[bounds[w]:bounds[w + 1]] for w in range(workers)]
+        # one BLAS thread per worker (the workers already use every core);
+        # spawned children read these variables before they import numpy
+        saved = {v: os.environ.get(v) for v in _BLAS_THREAD_VARS}
+        os.environ.update({v: "1" for v in _BLAS_THREAD_VARS})
+        try:
+            with cf.ProcessPoolExecutor(max_workers=workers,
+                                        mp_context=mp.get_context("spawn")) as ex:
+                for r0, part in ex.map(_assemble_planes, [self] * workers, jobs):
+                    if part is not None:
+                        S[:, r0:r0 + part.shape[1]] += part
+        finally:
+            for v, val in saved.items():
+                if val is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = val
+        return S
+
+    def _plane_boxes(self, e0, e1, max_elems=4096):
+        """Element boxes covering planes [e0, e1) of the slowest direction,
+        the next-slowest direction cut into blocks so that a box holds about
+        max_elems elements at most (bounds the temporaries of one box)."""
+        d = self.d
+        per_line = int(np.prod(self.nel[:d - 2])) * (e1 - e0) if d > 2 else (e1 - e0)
+        n2 = self.nel[d - 2]
+        step = max(1, min(n2, max_elems // max(per_line, 1)))
+        out = []
+        for b0 in range(0, n2, step):
             elo = [0] * d
             ehi = list(self.nel)
-            elo[last], ehi[last] = e0, min(e0 + chunk_planes, self.nel[last])
-            self._scatter_box(S, elo, ehi, rows=None)
-        return S.reshape(self.n_offsets(), self.N)
+            elo[-1], ehi[-1] = e0, e1
+            elo[-2], ehi[-2] = b0, min(b0 + step, n2)
+            out.append((elo, ehi))
+        return out
 
-    def _scatter_box(self, S, elo, ehi, rows=None):
+    def _row_range(self, e0, e1):
+        """Half-open range of scalar rows that the elements of planes
+        [e0, e1) of the slowest direction couple to."""
+        last, p = self.d - 1, self.p
+        stride = int(np.prod(self.n[:last]))
+        i_lo = max(int(self.spans[last][e0]) - p - 1, 0)
+        i_hi = min(int(self.spans[last][e1 - 1]) - 1, self.n[last] - 1)
+        return i_lo * stride, (i_hi + 1) * stride
+
+    def _scatter_box(self, S, elo, ehi, rows=None, row0=0):
+        """Add the element matrices of a box into S[o, row - row0] (S 2D, its
+        columns a contiguous range of rows starting at row0); with `rows`,
+        only into those rows."""
         d = self.d
         box = self._box(elo, ehi)
         eidx = self._element_lists(box, elo, ehi)
         L = self.element_matrices(box, eidx)
         I = self._local_full_indices(box, eidx)               # full indices
-        A = L.shape[1]
         valid_r = np.ones(L.shape[:2], bool)
         for k in range(d):
             valid_r &= (I[k] >= 1) & (I[k] <= self.m[k] - 2)
@@ -266,15 +330,22 @@ class Discretization:
         # pairs (a, b): row from a, column offset from b - a
         rowp = np.broadcast_to(row[:, :, None], L.shape)
         valid = valid_r[:, :, None] & valid_r[:, None, :]
-        delta = [I[k][:, None, :] - I[k][:, :, None] for k in range(d)]
-        o = self.offset_index(delta)
+        # the offset of a local pair (a, b) is I_b - I_a, the same in every
+        # element (local indices are consecutive from the element's first)
+        delta = [I[k][0, None, :] - I[k][0, :, None] for k in range(d)]
+        o = np.broadcast_to(self.offset_index(delta), L.shape)
         if rows is not None:
             valid &= np.isin(rowp, rows)
-        flat = (o * self.N + rowp)[valid]
-        if rows is not None:
-            np.add.at(S, flat, L[valid])
-        else:
-            S += np.bincount(flat, weights=L[valid], minlength=S.size)
+            np.add.at(S, (o[valid], rowp[valid] - row0), L[valid])
+            return S
+        if not valid.any():
+            return S
+        rsel = rowp[valid]
+        r0, r1 = int(rsel.min()), int(rsel.max()) + 1
+        R = r1 - r0
+        part = np.bincount(o[valid] * R + (rsel - r0), weights=L[valid],
+                           minlength=S.shape[0] * R)
+        S[:, r0 - row0:r1 - row0] += part.reshape(S.shape[0], R)
         return S
 
     def assemble_rows(self, rows_multi):
@@ -290,10 +361,10 @@ class Discretization:
                 I = i[k] + 1
                 es = [e for e, s in enumerate(self.spans[k]) if s - p <= I <= s]
                 elo.append(min(es)); ehi.append(max(es) + 1)
-            S = np.zeros(self.n_offsets() * self.N)
             row = int(self.row_index(i))
-            self._scatter_box(S, elo, ehi, rows=np.array([row]))
-            out[r] = S.reshape(self.n_offsets(), self.N)[:, row]
+            S = np.zeros((self.n_offsets(), 1))
+            self._scatter_box(S, elo, ehi, rows=np.array([row]), row0=row)
+            out[r] = S[:, 0]
         return out
 
     # ---- right-hand side ----------------------------------------------------
@@ -392,6 +463,24 @@ class Discretization:
                 T = np.kron(T, pens[l][0] if l == k else pens[l][1])
             P = P + T
         return P
+
+
+_BLAS_THREAD_VARS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _assemble_planes(disc: Discretization, planes):
+    """One worker of Discretization.assemble_stencil: the sum, from zero and
+    in plane order, of the element matrices of the given planes of the
+    slowest direction, over the contiguous rows they couple to.
+    Returns (first row, S_part[o, rows])."""
+    if not planes:
+        return 0, None
+    r0, r1 = disc._row_range(planes[0][0], planes[-1][1])
+    part = np.zeros((disc.n_offsets(), r1 - r0))
+    for e0, e1 in planes:
+        for elo, ehi in disc._plane_boxes(e0, e1):
+            disc._scatter_box(part, elo, ehi, row0=r0)
+    return r0, part
 
 
 def stencil_to_csr(disc: Discretization, S):
