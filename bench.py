@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle leg (its solve of the same workload and vs_oracle)")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="--impl reference: seconds of timed oracle solves (at least one solve)")
     ap.add_argument("--profile", action="store_true",
                     help="only set-up, warm-up and the timed mixed solves (for ncu launch lists)")
     ap.add_argument("--batch", action="store_true",
@@ -74,60 +77,99 @@ def workload_name(n, p):
 
 
 # ----------------------------------------------------------------- oracle leg --
-class OracleSample:
-    """The FP64 CPU oracle on a bounded sample of the workload: its iteration
-    count from a full solve of the same recipe at n=16, its setup of P at the
-    full size (pencils and generalized eigendecompositions of the three
-    directions) and its per-iteration cost measured at the full size (one FD
-    apply, one stencil apply with the full-size (2p+1)^3 x N coefficient
-    array, five vector operations)."""
+def host_workers(per_worker_gb=3.0, reserve_gb=16.0):
+    """Processes for the oracle's assembly: every host core, fewer when the
+    host's available memory (per /proc/meminfo) would not hold them."""
+    cores = os.cpu_count() or 1
+    try:
+        with open("/proc/meminfo") as f:
+            kb = next(int(l.split()[1]) for l in f if l.startswith("MemAvailable:"))
+        avail = kb / 2 ** 20
+        return max(1, min(cores, int((avail - reserve_gb) / per_worker_gb)))
+    except (OSError, StopIteration, ValueError):
+        return max(1, cores // 2)
 
-    def __init__(self, n, p, tol):
+
+def _openblas_libs():
+    """(library, set, get) for every loaded OpenBLAS that exports a
+    thread-count setter (names differ between numpy builds)."""
+    import ctypes
+    out = []
+    try:
+        maps = open("/proc/self/maps").read()
+    except OSError:
+        return out
+    for path in sorted(set(re.findall(r"(/\S*openblas\S*\.so\S*)", maps))):
+        try:
+            L = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for suffix in ("64_", "", "_64"):
+            for pre in ("scipy_openblas_", "openblas_"):
+                st, gt = pre + "set_num_threads" + suffix, pre + "get_num_threads" + suffix
+                if hasattr(L, st) and hasattr(L, gt):
+                    out.append((path, getattr(L, st), getattr(L, gt)))
+                    break
+            else:
+                continue
+            break
+    return out
+
+
+class blas_threads:
+    """Context manager: every loaded OpenBLAS limited to n threads (restored
+    on exit). .ok is False when no thread-count control was found."""
+
+    def __init__(self, n):
+        self.n, self.saved = n, []
+
+    def __enter__(self):
         import numpy as np
+        np.ones(4) @ np.ones(4)          # make sure numpy's BLAS is loaded
+        for path, st, gt in _openblas_libs():
+            self.saved.append((st, gt()))
+            st(self.n)
+        self.ok = bool(self.saved)
+        return self
+
+    def __exit__(self, *exc):
+        for st, old in self.saved:
+            st(old)
+
+
+class OracleRun:
+    """The FP64 CPU oracle on the bench workload itself (3D deformed cube,
+    n dofs per direction, degree p, manufactured load): its own A and b
+    (assembled once, untimed, in spawned processes over the host cores), then
+    PCG solves from x0 = 0 exactly as the oracle states them. A timed solve
+    is the paper's time-to-solution: the setup of P (1D pencils, generalized
+    eigendecompositions) plus the PCG iterations; assembly is excluded."""
+
+    def __init__(self, n, p, workers=None):
         import synth
-        from oracle import assemble, fd, pcg
-        self.np, self.fd_mod, self.assemble = np, fd, assemble
-        small = synth.deformed_cube(16, p, seed=0)
-        ds = assemble.Discretization.from_problem(small)
-        A = assemble.stencil_to_csr(ds, ds.assemble_stencil())
-        Fs = fd.FD([ds.pencil(k) for k in range(3)])
-        f = lambda x, y, z: 3 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
-        res = pcg.pcg(lambda v: A @ v, ds.assemble_rhs(f), Fs.apply, tol=tol)
-        self.iters = res.iters
-        prob = synth.deformed_cube(n, p, seed=0)
-        self.disc = assemble.Discretization.from_problem(prob)
-        self.F = fd.FD([self.disc.pencil(k) for k in range(3)])
-        self.S = np.ones((self.disc.n_offsets(), self.disc.N))
-        self.r = synth.random_vector(self.disc.N, 3)
+        from oracle import assemble
+        self.assemble = assemble
+        self.n, self.p = n, p
+        self.disc = assemble.Discretization.from_problem(synth.deformed_cube(n, p, seed=0))
+        self.workers = workers or host_workers()
+        t0 = time.perf_counter()
+        self.S = self.disc.assemble_stencil(workers=self.workers)
+        t1 = time.perf_counter()
+        self.b = self.disc.assemble_rhs(assemble.sine_load, workers=self.workers)
+        self.assembly_s = {"A": t1 - t0, "b": time.perf_counter() - t1}
         self.cores = os.cpu_count()
 
-    def step(self):
-        np = self.np
-        ts = time.perf_counter()
-        self.F = self.fd_mod.FD([self.disc.pencil(k) for k in range(3)])
-        t0 = time.perf_counter()
-        z = self.F.apply(self.r)
-        t1 = time.perf_counter()
-        y = self.assemble.apply_stencil(self.disc, self.S, self.r)
-        t2 = time.perf_counter()
-        x = np.zeros_like(self.r)
-        a = float(self.r @ y)
-        x += 1e-3 * z
-        r2 = self.r - 1e-3 * y
-        rr = float(r2 @ r2)
-        z2 = z + 1e-3 * x
-        t3 = time.perf_counter()
-        del a, rr, z2
-        per_it = (t1 - t0) + (t2 - t1) + (t3 - t2)
-        return (t0 - ts) + self.iters * per_it, dict(setup_s=t0 - ts, fd_s=t1 - t0,
-                                                     stencil_s=t2 - t1, vec_s=t3 - t2)
+    def apply_A(self, v):
+        return self.assemble.apply_stencil(self.disc, self.S, v)
 
-    def describe(self, parts):
-        return (f"oracle iteration count {self.iters} from its full n=16 solve of the same recipe; "
-                f"timed at n={self.disc.n[0]}: setup of P {parts['setup_s']:.3f}s, per iteration "
-                f"FD apply {parts['fd_s']:.3f}s (numpy/BLAS), stencil apply {parts['stencil_s']:.3f}s, "
-                f"vector ops {parts['vec_s']:.3f}s; value = setup + iterations x per-iteration cost "
-                f"(assembly excluded)")
+    def solve(self, tol, x0=None, max_iter=2000):
+        """(PCG result, seconds of setup of P + solve, seconds of the setup)."""
+        from oracle import fd, pcg
+        t0 = time.perf_counter()
+        F = fd.FD([self.disc.pencil(k) for k in range(3)])
+        t1 = time.perf_counter()
+        res = pcg.pcg(self.apply_A, self.b, F.apply, tol=tol, max_iter=max_iter, x0=x0)
+        return res, time.perf_counter() - t0, t1 - t0
 
 
 def cpu_model():
@@ -142,7 +184,6 @@ def cpu_model():
     except OSError:
         pass
     try:
-        import subprocess
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
         for line in out.splitlines():
             k, _, v = line.partition(":")
@@ -154,41 +195,84 @@ def cpu_model():
     return platform.machine()
 
 
-def cpu_baseline_entry(n, p, tol, reps=1):
-    o = OracleSample(n, p, tol)
-    vals, parts = [], None
-    for _ in range(reps):
-        v, parts = o.step()
-        vals.append(v)
-    v = statistics.median(vals)
-    return {"value": v, "unit": UNIT, "cores": o.cores, "cpu_model": cpu_model(), "kind": "oracle",
-            "sample": o.describe(parts)}
+def oracle_baseline(n, p, tol, x_gpu, workers=None):
+    """The oracle leg of the bench line: the oracle's real PCG solve of the
+    same workload to tol on all host cores and on one thread (timed), its
+    solution to 1e-13 (warm-started from its tol solution; reading O17) and
+    the GPU solutions' entry-wise and 2-norm differences from it.
+    x_gpu: {"fp64": x, "<dtype>": x} host arrays of the GPU solves at tol.
+    Returns (cpu_baseline dict, vs_oracle dict)."""
+    import numpy as np
+    o = OracleRun(n, p, workers)
+    res8, t_all, t_setup = o.solve(tol)
+    with blas_threads(1) as bt:
+        if bt.ok:
+            res1, t_one, _ = o.solve(tol)
+    res13, _, _ = o.solve(1e-13, x0=res8.x)
+
+    def diff(x, ref):
+        return {"max_rel": float(np.abs(x - ref).max() / np.abs(ref).max()),
+                "l2_rel": float(np.linalg.norm(x - ref) / np.linalg.norm(ref))}
+
+    cpu = {"value": t_all, "unit": UNIT, "cores": o.cores, "cpu_model": cpu_model(),
+           "nproc": os.cpu_count(), "kind": "oracle", "iterations": res8.iters,
+           "converged": bool(res8.converged),
+           "single_thread_s": t_one if bt.ok else None,
+           "setup_of_P_s": t_setup,
+           "sample": (f"the oracle's full PCG solve of this workload (3D deformed cube n={n}, p={p}, "
+                      f"tol {tol:g}, x0 = 0): setup of P (pencils, generalized eigendecompositions) "
+                      f"+ {res8.iters} iterations, on all {o.cores} host cores (numpy/BLAS threads); "
+                      f"single_thread_s: the same solve with BLAS limited to one thread; assembly of "
+                      f"A and b excluded ({o.assembly_s['A']:.0f} s and {o.assembly_s['b']:.0f} s in "
+                      f"{o.workers} processes)")}
+    vs = {"oracle_solution": f"oracle PCG to 1e-13 (warm start from its tol {tol:g} solution; "
+                             f"{res13.iters} more iterations, true relres {res13.true_relres:.1e})",
+          "oracle_iterations_at_tol": res8.iters}
+    for name, x in x_gpu.items():
+        vs[name] = {"vs_converged": diff(x, res13.x)}
+    if "fp64" in x_gpu:
+        # same algorithm and stopping rule: the FP64 path follows the oracle's iterates
+        vs["fp64"]["vs_oracle_same_tol"] = diff(x_gpu["fp64"], res8.x)
+    return cpu, vs
 
 
 def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle's real time-to-solution on the same
+    workload. A step is one full oracle solve (about 20 s on 16 cores at
+    n = 128), so the run takes at most one warm-up solve and as many timed
+    solves as fit in --ref-budget seconds (at least one)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    o = OracleSample(args.n, args.p, args.tol)
-    for _ in range(args.warmup):
-        o.step()
-    vals, parts = [], None
+    o = OracleRun(args.n, args.p, getattr(args, "workers", None))
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        o.solve(args.tol)
+    vals, iters = [], []
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        v, parts = o.step()
-        vals.append(v)
+    while len(vals) < args.steps:
+        res, t, _ = o.solve(args.tol)
+        vals.append(t)
+        iters.append(res.iters)
+        if time.perf_counter() - t0 + t > args.ref_budget:
+            break
     wall = time.perf_counter() - t0
     v = statistics.median(vals)
+    sample = (f"the oracle's full PCG solve (setup of P + {iters[-1]} iterations, tol {args.tol:g}, "
+              f"x0 = 0) of this workload on all {o.cores} host cores; one step = one solve; assembly "
+              f"of A and b excluded ({o.assembly_s['A']:.0f} s + {o.assembly_s['b']:.0f} s in "
+              f"{o.workers} processes)")
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "steps": len(vals), "steps_requested": args.steps, "warmup": warm,
+            "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.n, args.p), "n": args.n, "p": args.p,
                        "tol": args.tol, "parallelism": "replicas"},
+            "iterations": iters[-1],
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": o.cores, "cpu_model": cpu_model(),
-                             "kind": "oracle", "sample": o.describe(parts)},
+                             "nproc": os.cpu_count(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": wall}
+            "wall_s_timed": wall}
     print(json.dumps(line), flush=True)
 
 
@@ -478,9 +562,18 @@ def run_ours(args):
     fp64_peak = 152 * 2 * 2 * sm_clk * 1e6 / 1e12      # TFLOP/s
     traffic = stencil_traffic(p, n)
 
-    cpu = None
+    # the oracle leg runs after every GPU measurement (its processes load the
+    # host cores): its real solve of this workload, timed, and the GPU
+    # solutions compared with its solution
+    cpu = vs_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_entry(n, p, args.tol)
+        cpu, vs_oracle = oracle_baseline(n, p, args.tol, {"fp64": x64.cpu().numpy(),
+                                                           dtype: x_mixed.cpu().numpy()})
+        vs_oracle[dtype]["iterations"] = it_mixed
+        vs_oracle["fp64"]["iterations"] = inf64.iterations
+        vs_oracle["targets"] = {"fp64_vs_oracle_same_tol": 1e-10, f"{dtype}_vs_converged": 1e-7}
+        vs_oracle["pass"] = bool(vs_oracle["fp64"]["vs_oracle_same_tol"]["max_rel"] <= 1e-10 and
+                                 vs_oracle[dtype]["vs_converged"]["max_rel"] <= 1e-7)
 
     if rank == 0:
         line = {
@@ -527,6 +620,7 @@ def run_ours(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+            line["vs_oracle"] = vs_oracle
         print(json.dumps(line), flush=True)
     patch.close()
     if world > 1:

@@ -88,7 +88,8 @@ typedef struct {
  * (2p+1)^d x N array, no assembly). Such a patch answers the geometry and
  * preconditioner calls (igafd_patch_query, igafd_get_eigen,
  * igafd_apply_prec, igafd_patch_features, igafd_patch_sepfit,
- * igafd_set_scalings, igafd_load_rhs_sine); the calls that need A
+ * igafd_set_scalings, igafd_quad_points, igafd_load_rhs, igafd_load_rhs_sine);
+ * the calls that need A
  * (igafd_apply_A, igafd_pcg_solve, igafd_batch_pcg_solve, igafd_copy_stencil,
  * igafd_autotune, igafd_pcg_condition_estimate) return IGAFD_ERR_ARG. */
 #define IGAFD_SETUP_NO_STENCIL 1
@@ -189,9 +190,25 @@ igafd_status igafd_apply_A(igafd_patch *patch, const double *x_dev,
 igafd_status igafd_apply_prec(igafd_patch *patch, igafd_dtype dtype,
                               const double *r_dev, double *z_dev, void *stream);
 
-/* b_i = int f(F(zeta)) B_i(zeta) |det J| dzeta for the manufactured
- * solution u = prod_k sin(pi x_k), f = d pi^2 u (Eq. (poisson) with
- * kappa = 1, right-hand side of the Galerkin system). */
+/* Quadrature points of the patch: Q = prod_k nel_k (p + 1) points, the
+ * tensor grid of the (p + 1)-point Gauss rule of every element, indexed
+ * q = t_1 + T_1 (t_2 + T_2 t_3) with T_k = nel_k (p + 1) and t_k = e_k (p + 1)
+ * + g_k (element e_k, Gauss point g_k, increasing zeta_k; direction 1
+ * fastest). x_dev (device, [dim][Q], caller-owned) receives the physical
+ * coordinates x_c = F_c(zeta_q) (Section 2.1: the map F of the patch), so a
+ * caller can evaluate its load f there for igafd_load_rhs. */
+igafd_status igafd_quad_points(const igafd_patch *patch, double *x_dev, void *stream);
+
+/* Right-hand side of the Galerkin system of Eq. (poisson) (Section 2.1: the
+ * load vector of Eq. (A)'s system): b_i = int f(F(zeta)) B_i(zeta) |det J|
+ * dzeta by the patch's Gauss rule, with f given at the quadrature points:
+ * f_qp (device, length Q, caller-owned, order of igafd_quad_points). b_dev:
+ * length-N device vector, overwritten, not overlapping f_qp. Errors: ARG
+ * (null pointers), CUDA. */
+igafd_status igafd_load_rhs(igafd_patch *patch, const double *f_qp, double *b_dev, void *stream);
+
+/* igafd_load_rhs for the manufactured solution u = prod_k sin(pi x_k),
+ * f = d pi^2 u (Eq. (poisson) with kappa = 1), f evaluated on the device. */
 igafd_status igafd_load_rhs_sine(igafd_patch *patch, double *b_dev, void *stream);
 
 /* Solve A x = b by conjugate gradients preconditioned with P (Section 3),
@@ -239,21 +256,26 @@ const char *igafd_status_str(igafd_status s);
  * a file-scope static device array of 2 * IGAFD_STATIC_FD_MAX_DOFS doubles
  * (16 MiB), which every GPU that loads the library holds until the process
  * exits. N = prod n_k above IGAFD_STATIC_FD_MAX_DOFS returns IGAFD_ERR_ARG
- * (with a message on stderr). The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current) and caches
- * it; make that first call before any stream capture. All calls share the
- * array, so calls whose kernels overlap on the GPU race: serialise them. */
+ * (with a message on stderr). Every call whose stream is not capturing looks
+ * up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and caches it per device; a call made during a stream capture
+ * uses the cached address, so the first call on a device must come before
+ * any stream capture (a captured first call returns IGAFD_ERR_ARG), and
+ * after a context reset a call outside a capture must come first. All calls
+ * share the array, so calls whose kernels overlap on the GPU race:
+ * serialise them. */
 #define IGAFD_STATIC_FD_MAX_DOFS 1048576
 igafd_status igafd_apply_prec_static(int dim, const int *n, const double *const *U,
                                      const double *const *D, const double *r_dev,
                                      double *z_dev, void *stream);
 
-/* Redo P's setup (Section 4.1) in place, on the patch's own buffers (no
- * allocation): the 1D pencils K_k, M_k (span-scaled if igafd_set_scalings
- * set scalings), their generalized eigendecompositions K_k U_k = M_k U_k D_k
- * (Section 3, Eq. (eigen3d)), 1 / (D_1 (+) D_2 (+) D_3) and the FP32 and
- * tensor-core copies of U_k. The paper's solver timings include this
- * setup of the preconditioner (Section 5), so a full time-to-solution is
+/* Redo P's setup (Section 4.1 in 2D, Section 5.1 in 3D) in place, on the
+ * patch's own buffers (no allocation): the 1D pencils K_k, M_k (span-scaled
+ * if igafd_set_scalings set scalings), their generalized eigendecompositions
+ * K_k U_k = M_k U_k D_k (Section 5.1, Eq. (eigen3d)), 1 / (D_1 (+) D_2 (+) D_3)
+ * and the FP32 and tensor-core copies of U_k. The paper's solver timings
+ * include this setup of the preconditioner (Section 7.1), so a full
+ * time-to-solution is
  * igafd_setup_prec followed by igafd_pcg_solve. igafd_setup_patch runs it
  * once. Synchronises the stream. Errors: IGAFD_ERR_NOT_SPD (M_k not
  * positive definite), IGAFD_ERR_EIG (no convergence), IGAFD_ERR_CUDA. */

@@ -143,9 +143,10 @@ class Discretization:
         return K, M
 
     # ---- element-by-element quantities ------------------------------------
-    def _box(self, elo, ehi):
+    def _box(self, elo, ehi, need_q=True):
         """Quadrature data on a box of elements [elo_k, ehi_k) per direction:
-        local basis values/derivatives, weights, Q and det J on the box grid."""
+        local basis values/derivatives, weights, det J and (need_q) Q on the
+        box grid."""
         p, nq, d = self.p, self.nq, self.d
         V, D, W, I0, pts = [], [], [], [], []
         for k in range(d):
@@ -160,7 +161,10 @@ class Discretization:
             I0.append(s - p)
             pts.append(z.ravel())
         F, J = self.geo.eval_grid(pts)
-        Q, det = q_matrix(J, self.kappa_grid(pts))
+        if need_q:
+            Q, det = q_matrix(J, self.kappa_grid(pts))
+        else:
+            Q, det = None, np.linalg.det(J)
         return dict(V=V, D=D, W=W, I0=I0, F=F, Q=Q, det=det)
 
     @staticmethod
@@ -266,27 +270,17 @@ class Discretization:
                 for elo, ehi in self._plane_boxes(e0, e1):
                     self._scatter_box(S, elo, ehi)
             return S
-        import concurrent.futures as cf
-        import multiprocessing as mp
-        bounds = np.linspace(0, len(planes), workers + 1).round().astype(int)
-        jobs = [planes[bounds[w]:bounds[w + 1]] for w in range(workers)]
-        # one BLAS thread per worker (the workers already use every core);
-        # spawned children read these variables before they import numpy
-        saved = {v: os.environ.get(v) for v in _BLAS_THREAD_VARS}
-        os.environ.update({v: "1" for v in _BLAS_THREAD_VARS})
-        try:
-            with cf.ProcessPoolExecutor(max_workers=workers,
-                                        mp_context=mp.get_context("spawn")) as ex:
-                for r0, part in ex.map(_assemble_planes, [self] * workers, jobs):
-                    if part is not None:
-                        S[:, r0:r0 + part.shape[1]] += part
-        finally:
-            for v, val in saved.items():
-                if val is None:
-                    os.environ.pop(v, None)
-                else:
-                    os.environ[v] = val
+        for r0, part in _spawn_map(_assemble_planes, [self] * workers, _split(planes, workers)):
+            if part is not None:
+                S[:, r0:r0 + part.shape[1]] += part
         return S
+
+    def _plane_box_full(self, e0, e1):
+        """Element box of whole planes [e0, e1) of the slowest direction."""
+        elo = [0] * self.d
+        ehi = list(self.nel)
+        elo[-1], ehi[-1] = e0, e1
+        return elo, ehi
 
     def _plane_boxes(self, e0, e1, max_elems=4096):
         """Element boxes covering planes [e0, e1) of the slowest direction,
@@ -368,32 +362,44 @@ class Discretization:
         return out
 
     # ---- right-hand side ----------------------------------------------------
-    def assemble_rhs(self, f, chunk_planes=4):
+    def assemble_rhs(self, f, chunk_planes=4, workers=1):
         """b_i = int f(F(zeta)) B_i(zeta) |det J| dzeta with f a callable of
-        the physical coordinates (x_1, ..., x_d)."""
-        d = self.d
+        the physical coordinates (x_1, ..., x_d). workers > 1: contiguous
+        plane ranges summed by spawned processes (f must then be picklable,
+        e.g. a module-level function), range sums added in order."""
+        last = self.d - 1
+        planes = [(e0, min(e0 + chunk_planes, self.nel[last]))
+                  for e0 in range(0, self.nel[last], chunk_planes)]
+        workers = max(1, min(int(workers), len(planes)))
         b = np.zeros(self.N)
-        last = d - 1
-        for e0 in range(0, self.nel[last], chunk_planes):
-            elo = [0] * d
-            ehi = list(self.nel)
-            elo[last], ehi[last] = e0, min(e0 + chunk_planes, self.nel[last])
-            box = self._box(elo, ehi)
-            eidx = self._element_lists(box, elo, ehi)
-            V = [box["V"][k][eidx[k]] for k in range(d)]
-            W = self._tprod([box["W"][k][eidx[k]][:, :, None] for k in range(d)])[:, :, 0]
-            Bh = self._tprod(V)                                   # [E, G, A]
-            X = [self._gather_grid(box["F"][c], eidx) for c in range(d)]
-            det = self._gather_grid(box["det"], eidx)
-            fv = f(*X) * np.abs(det) * W                          # [E, G]
-            loc = np.einsum("eg,ega->ea", fv, Bh)
-            I = self._local_full_indices(box, eidx)
-            valid = np.ones(loc.shape, bool)
-            for k in range(d):
-                valid &= (I[k] >= 1) & (I[k] <= self.m[k] - 2)
-            row = self.row_index([I[k] - 1 for k in range(d)])
-            b += np.bincount(row[valid], weights=loc[valid], minlength=self.N)
+        if workers == 1:
+            r0, part = _rhs_planes(self, f, planes)
+            b[r0:r0 + len(part)] += part
+            return b
+        for r0, part in _spawn_map(_rhs_planes, [self] * workers, [f] * workers,
+                                   _split(planes, workers)):
+            if part is not None:
+                b[r0:r0 + len(part)] += part
         return b
+
+    def _rhs_box(self, f, elo, ehi, out, row0):
+        """Add the element load vectors of a box into out[row - row0]."""
+        d = self.d
+        box = self._box(elo, ehi, need_q=False)
+        eidx = self._element_lists(box, elo, ehi)
+        V = [box["V"][k][eidx[k]] for k in range(d)]
+        W = self._tprod([box["W"][k][eidx[k]][:, :, None] for k in range(d)])[:, :, 0]
+        Bh = self._tprod(V)                                   # [E, G, A]
+        X = [self._gather_grid(box["F"][c], eidx) for c in range(d)]
+        det = self._gather_grid(box["det"], eidx)
+        fv = f(*X) * np.abs(det) * W                          # [E, G]
+        loc = np.einsum("eg,ega->ea", fv, Bh)
+        I = self._local_full_indices(box, eidx)
+        valid = np.ones(loc.shape, bool)
+        for k in range(d):
+            valid &= (I[k] >= 1) & (I[k] <= self.m[k] - 2)
+        row = self.row_index([I[k] - 1 for k in range(d)])
+        out += np.bincount(row[valid] - row0, weights=loc[valid], minlength=len(out))
 
     # ---- discretization error ------------------------------------------------
     def l2_error(self, u_dofs, u_exact, extra_q=2, chunk_planes=4):
@@ -410,7 +416,7 @@ class Discretization:
             elo = [0] * d
             ehi = list(fine.nel)
             elo[last], ehi[last] = e0, min(e0 + chunk_planes, fine.nel[last])
-            box = fine._box(elo, ehi)
+            box = fine._box(elo, ehi, need_q=False)
             eidx = fine._element_lists(box, elo, ehi)
             V = [box["V"][k][eidx[k]] for k in range(d)]
             W = fine._tprod([box["W"][k][eidx[k]][:, :, None] for k in range(d)])[:, :, 0]
@@ -466,6 +472,55 @@ class Discretization:
 
 
 _BLAS_THREAD_VARS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def sine_load(*x):
+    """The manufactured load f = d pi^2 prod_k sin(pi x_k) of u = prod_k
+    sin(pi x_k) (-Laplace u = f, kappa = 1; the right-hand side used for the
+    3D workloads, which the paper does not state)."""
+    v = len(x) * np.pi ** 2
+    for xk in x:
+        v = v * np.sin(np.pi * xk)
+    return v
+
+
+def _split(items, parts):
+    """items cut into `parts` contiguous, nearly equal runs."""
+    bounds = np.linspace(0, len(items), parts + 1).round().astype(int)
+    return [items[bounds[w]:bounds[w + 1]] for w in range(parts)]
+
+
+def _spawn_map(fn, *iterables):
+    """fn over the iterables in spawned worker processes (one per item), in
+    order, each with a single BLAS thread (the workers use every core)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    n = len(iterables[0])
+    saved = {v: os.environ.get(v) for v in _BLAS_THREAD_VARS}
+    os.environ.update({v: "1" for v in _BLAS_THREAD_VARS})
+    try:
+        with cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(fn, *iterables))
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+
+
+def _rhs_planes(disc: Discretization, f, planes):
+    """Load-vector sum over the given element planes of the slowest
+    direction, from zero in plane order, over the rows they couple to.
+    Returns (first row, b_part)."""
+    if not planes:
+        return 0, None
+    r0, r1 = disc._row_range(planes[0][0], planes[-1][1])
+    part = np.zeros(r1 - r0)
+    for e0, e1 in planes:
+        elo, ehi = disc._plane_box_full(e0, e1)
+        disc._rhs_box(f, elo, ehi, part, r0)
+    return r0, part
 
 
 def _assemble_planes(disc: Discretization, planes):

@@ -168,10 +168,12 @@ igafd_status igafd_fd_tc_init(igafd_patch *P, cudaStream_t s);
 void igafd_fd_tc_free(igafd_patch *P);
 // y = A x (b == null) or y = b - A x; see stencil.cu
 // every > 0: the kernel only runs when the device iteration counter is a
-// multiple of `every` (periodic true residual inside a captured loop)
+// multiple of `every` (periodic true residual inside a captured loop);
+// z (with b and pcg): the true residual also gives (r, z) to the flexible beta
 igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
                                   int pcg, int skip_done, cudaStream_t s, int every = 0,
-                                  unsigned long long *tstat = nullptr);
+                                  unsigned long long *tstat = nullptr,
+                                  const double *z = nullptr);
 long long igafd_stencil_row_stride(long long N);   // Np for a given N
 long long igafd_stencil_halo(int p, const int *n);   // zero halo of padded vectors
 void igafd_tune_lookup(igafd_patch *P);              // apply a cached autotune choice

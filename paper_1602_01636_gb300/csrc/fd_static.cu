@@ -10,9 +10,12 @@
 // every GPU that loads the library holds until the process exits.
 //
 // The host-side name of that array is only a stand-in, never a device
-// address: the address is obtained once per device with cudaGetSymbolAddress
-// (with that device current) and cached. The first call on a device does this
-// set-up, so it should happen before any stream capture. No element of the
+// address: the address is obtained with cudaGetSymbolAddress (with the
+// device current) on every call whose stream is not capturing, and cached
+// per device for calls made during a stream capture (which must not query
+// it). So the first call on a device should come before any stream capture,
+// and after a context reset (cudaDeviceReset) the next call outside a capture
+// picks up the reloaded module's address. No element of the
 // scratch needs to start at zero: every product writes each element of its
 // output before the next product reads it. All calls share the one array, so
 // calls whose kernels overlap on the GPU (different streams, or concurrent
@@ -29,12 +32,18 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 double *g_scratch_addr[kMaxDevices] = {};
 
-igafd_status scratch_address(double **out) {
+igafd_status scratch_address(cudaStream_t s, double **out) {
   int dev = -1;
   IGAFD_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return IGAFD_ERR_ARG;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  IGAFD_CUDA(cudaStreamIsCapturing(s, &cap));
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
+  if (cap != cudaStreamCaptureStatusNone && !g_scratch_addr[dev]) {
+    fprintf(stderr, "igafd_apply_prec_static: the first call on a device must not be captured\n");
+    return IGAFD_ERR_ARG;
+  }
+  if (cap == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_fd_static_scratch);
     if (e != cudaSuccess || !p) {
@@ -52,6 +61,7 @@ struct StaticGemm {
   const double *A, *B;
   double *C;
   int M, N, K, batch;
+  int b_off;          // first batch index of this launch (grid.z covers at most 65535)
   long long sam, sak, sbk, sbn, scm, scn, batA, batB, batC;
   // divide epilogue: C[i] /= D1[i1] + D2[i2] + D3[i3] for the linear index i
   const double *D1, *D2, *D3;
@@ -67,7 +77,7 @@ __global__ void __launch_bounds__(256) static_mode_gemm(StaticGemm g) {
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const long long b = blockIdx.z;
+  const long long b = (long long)blockIdx.z + g.b_off;
   const double *A = g.A + b * g.batA;
   const double *B = g.B + b * g.batB;
   double *C = g.C + b * g.batC;
@@ -144,6 +154,21 @@ StaticGemm mode_desc(const int *n, int dim, int k, const double *U, bool forward
   return g;
 }
 
+// One mode product; the batch index runs over launches of at most 65535
+// (the grid's z extent), so every shape within the dof limit launches.
+igafd_status launch_mode(StaticGemm g, cudaStream_t s) {
+  const int total = g.batch;
+  for (int b0 = 0; b0 < total; b0 += 65535) {
+    g.b_off = b0;
+    const int nb = total - b0 < 65535 ? total - b0 : 65535;
+    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, nb);
+    static_mode_gemm<<<grid, 256, 0, s>>>(g);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+  }
+  return IGAFD_OK;
+}
+
 }  // namespace
 
 extern "C" igafd_status igafd_apply_prec_static(int dim, const int *n, const double *const *U,
@@ -162,9 +187,9 @@ extern "C" igafd_status igafd_apply_prec_static(int dim, const int *n, const dou
             N, IGAFD_STATIC_FD_MAX_DOFS);
     return IGAFD_ERR_ARG;
   }
-  double *scratch = nullptr;
-  IGAFD_TRY(scratch_address(&scratch));
   cudaStream_t s = (cudaStream_t)stream;
+  double *scratch = nullptr;
+  IGAFD_TRY(scratch_address(s, &scratch));
   double *bufs[2] = {scratch, scratch + IGAFD_STATIC_FD_MAX_DOFS};
   const double *in = r;
   int cur = 0;
@@ -174,20 +199,14 @@ extern "C" igafd_status igafd_apply_prec_static(int dim, const int *n, const dou
       g.D1 = D[0]; g.D2 = D[1]; g.D3 = dim == 3 ? D[2] : nullptr;
       g.n1 = n[0]; g.n2 = n[1];
     }
-    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.batch);
-    static_mode_gemm<<<grid, 256, 0, s>>>(g);
-    IGAFD_LAUNCHED(1);
-    IGAFD_CUDA(cudaGetLastError());
+    IGAFD_TRY(launch_mode(g, s));
     in = bufs[cur];
     cur ^= 1;
   }
   for (int k = dim - 1; k >= 0; --k) {       // backward U_k, the last writes z
     double *out = k == 0 ? z : bufs[cur];
     StaticGemm g = mode_desc(n, dim, k, U[k], false, in, out);
-    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.batch);
-    static_mode_gemm<<<grid, 256, 0, s>>>(g);
-    IGAFD_LAUNCHED(1);
-    IGAFD_CUDA(cudaGetLastError());
+    IGAFD_TRY(launch_mode(g, s));
     in = out;
     cur ^= 1;
   }

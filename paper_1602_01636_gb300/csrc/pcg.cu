@@ -240,7 +240,9 @@ static igafd_status enqueue_iteration(igafd_patch *P, igafd_dtype dt, int flex, 
   IGAFD_CUDA(igafd_launch(update_xr_kernel, G, B, 0, s, P->xs, P->r, P->pv, P->q, P->z, N, scal, P->partial,
                                    P->counter, flex, P->coef));
   IGAFD_LAUNCHED(1);
-  if (true_every > 0) IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, true_every));
+  if (true_every > 0)
+    IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, true_every, nullptr,
+                                   flex ? P->z : nullptr));
   IGAFD_TRY(fd_apply(P, dt, P->r, P->z, s, done));
   IGAFD_CUDA(igafd_launch(dot_rz_kernel, G, B, 0, s, P->r, P->z, N, scal, P->partial, P->counter, 0, flex, 1, P->coef));
   IGAFD_LAUNCHED(1);
@@ -394,7 +396,8 @@ static igafd_status run_chunk_direct(igafd_patch *P, cudaStream_t s, SolveState 
                                      P->counter, S.flex, P->coef));
     IGAFD_LAUNCHED(1);
     if (S.o.true_every > 0)
-      IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, S.o.true_every));
+      IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 1, s, S.o.true_every, nullptr,
+                                     S.flex ? P->z : nullptr));
     if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 2], s));
     IGAFD_TRY(fd_apply(P, S.o.prec_dtype, P->r, P->z, s, P->scal + S_DONE));
     if (S.timing) IGAFD_CUDA(cudaEventRecord(ev[4 * c + 3], s));
@@ -432,7 +435,8 @@ static igafd_status solve_after_chunk(igafd_patch *P, cudaStream_t s, SolveState
       S.finished = true;
       return IGAFD_OK;
     }
-    IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 0, s));
+    IGAFD_TRY(igafd_stencil_launch(P, P->xs, P->r, P->bint, 1, 0, s, 0, nullptr,
+                                   S.flex ? P->z : nullptr));
     IGAFD_TRY(read_scalars(P, s));
     if (h[S_TRUE_RR] <= S.o.tol * S.o.tol * S.bb) {
       S.status = IGAFD_OK;

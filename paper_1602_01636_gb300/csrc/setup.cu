@@ -293,10 +293,14 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
 #undef FV
 }
 
-// Right-hand side for u = prod sin(pi x_k), f = d pi^2 u, one block per
-// element of a colour class (same colouring as the stiffness assembly).
+// Right-hand side b_i = sum_q f(x_q) B_i(zeta_q) |det J(zeta_q)| w_q, one
+// block per element of a colour class (same colouring as the stiffness
+// assembly): f from fq[q] at the tensor quadrature point q = t_1 + T_1 (t_2 +
+// T_2 t_3) (T_k = nel_k (p + 1) 1D points of direction k), or, with fq null,
+// the manufactured f = d pi^2 prod sin(pi x_k).
 template <int DIM>
-__global__ void rhs_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2, double *b) {
+__global__ void rhs_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2, const double *fq,
+                           double *b) {
   extern __shared__ double sm[];
   const int p = v.p, A = p + 1, nq = p + 1;
   const int nqd = DIM == 3 ? nq * nq * nq : nq * nq;
@@ -313,12 +317,16 @@ __global__ void rhs_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2, doubl
     double x[3], J[3][3], Q[6];
     geo_eval<DIM>(v, t, x, J);
     double det = q_from_J<DIM>(J, 1.0, Q);
-    double f = DIM * M_PI * M_PI;
-    double wt = fabs(det);
-    for (int k = 0; k < DIM; ++k) {
-      f *= sin(M_PI * x[k]);
-      wt *= v.w[k][t[k]];
+    double f;
+    if (fq) {
+      const long long T0 = (long long)v.nel[0] * nq, T1 = (long long)v.nel[1] * nq;
+      f = fq[t[0] + T0 * (t[1] + (DIM == 3 ? T1 * t[2] : 0))];
+    } else {
+      f = DIM * M_PI * M_PI;
+      for (int k = 0; k < DIM; ++k) f *= sin(M_PI * x[k]);
     }
+    double wt = fabs(det);
+    for (int k = 0; k < DIM; ++k) wt *= v.w[k][t[k]];
     fw[g] = f * wt;
   }
   __syncthreads();
@@ -343,6 +351,21 @@ __global__ void rhs_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2, doubl
       acc += bv * fw[g];
     }
     b[row] += acc;
+  }
+}
+
+// Physical coordinates x = F(zeta_q) of every tensor quadrature point,
+// x[c * Qn + q] with q as in rhs_kernel.
+template <int DIM>
+__global__ void quad_points_kernel(PV v, long long Qn, double *xout) {
+  const int nq = v.p + 1;
+  const long long T0 = (long long)v.nel[0] * nq, T1 = (long long)v.nel[1] * nq;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Qn;
+       q += (long long)gridDim.x * blockDim.x) {
+    int t[3] = {(int)(q % T0), (int)((q / T0) % T1), DIM == 3 ? (int)(q / (T0 * T1)) : 0};
+    double x[3], J[3][3];
+    geo_eval<DIM>(v, t, x, J);
+    for (int c = 0; c < DIM; ++c) xout[c * Qn + q] = x[c];
   }
 }
 
@@ -497,9 +520,7 @@ igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s) {
   return IGAFD_OK;
 }
 
-extern "C" igafd_status igafd_load_rhs_sine(igafd_patch *P, double *b, void *stream) {
-  if (!P || !b) return IGAFD_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+static igafd_status load_rhs(igafd_patch *P, const double *fq, double *b, cudaStream_t s) {
   IGAFD_CUDA(cudaSetDevice(P->dev));
   PV v = make_view(P);
   const int p = P->p, dim = P->dim, C = p + 1;
@@ -513,9 +534,37 @@ extern "C" igafd_status igafd_load_rhs_sine(igafd_patch *P, double *b, void *str
         int ne3 = dim == 3 ? (c3 < P->nel[2] ? (P->nel[2] - c3 + C - 1) / C : 0) : 1;
         long long nb = (long long)ne1 * ne2 * ne3;
         if (nb == 0) continue;
-        if (dim == 3) rhs_kernel<3><<<(unsigned)nb, 128, smem, s>>>(v, c1, c2, c3, ne1, ne2, b);
-        else rhs_kernel<2><<<(unsigned)nb, 128, smem, s>>>(v, c1, c2, 0, ne1, ne2, b);
+        if (dim == 3) rhs_kernel<3><<<(unsigned)nb, 128, smem, s>>>(v, c1, c2, c3, ne1, ne2, fq, b);
+        else rhs_kernel<2><<<(unsigned)nb, 128, smem, s>>>(v, c1, c2, 0, ne1, ne2, fq, b);
+        IGAFD_LAUNCHED(1);
         IGAFD_CUDA(cudaGetLastError());
       }
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_load_rhs_sine(igafd_patch *P, double *b, void *stream) {
+  if (!P || !b) return IGAFD_ERR_ARG;
+  return load_rhs(P, nullptr, b, (cudaStream_t)stream);
+}
+
+extern "C" igafd_status igafd_load_rhs(igafd_patch *P, const double *f_qp, double *b,
+                                       void *stream) {
+  if (!P || !f_qp || !b || (const void *)f_qp == (const void *)b) return IGAFD_ERR_ARG;
+  return load_rhs(P, f_qp, b, (cudaStream_t)stream);
+}
+
+extern "C" igafd_status igafd_quad_points(const igafd_patch *P, double *x, void *stream) {
+  if (!P || !x) return IGAFD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  IGAFD_CUDA(cudaSetDevice(P->dev));
+  PV v = make_view(P);
+  long long Qn = 1;
+  for (int k = 0; k < P->dim; ++k) Qn *= (long long)P->nel[k] * (P->p + 1);
+  long long nb = (Qn + 255) / 256;
+  if (nb > 4 * 1184) nb = 4 * 1184;
+  if (P->dim == 3) quad_points_kernel<3><<<(unsigned)nb, 256, 0, s>>>(v, Qn, x);
+  else quad_points_kernel<2><<<(unsigned)nb, 256, 0, s>>>(v, Qn, x);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }

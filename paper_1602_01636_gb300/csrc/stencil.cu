@@ -94,6 +94,7 @@ struct StencilArgs {
   const double *x;    // interior pointer of a zero-padded vector (halo H)
   double *y;
   const double *b;    // MODE 1
+  const double *z;    // MODE 1, optional: also (y, z) -> scal[S_RZOLD] (flexible beta)
   int n1, n2, n3;
   long long N, Np;
   long long ntiles;
@@ -130,7 +131,9 @@ struct Geom {
 // read both operands from shared memory.
 //
 // MODE 0: y = A x, dot (x, y) -> alpha = rho / (x, y) when pcg.
-// MODE 1: y = b - A x, dot (y, y) -> true (r, r) when pcg.
+// MODE 1: y = b - A x, dot (y, y) -> true (r, r) when pcg; with z given also
+// (y, z) -> (r, z_old) of the flexible beta, so that a recomputed residual
+// replaces the recurrence one in every scalar that uses it.
 template <int DIM, int P, int MODE, int kStages, int R>
 __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs a) {
   pdl_wait();
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
   }
   __syncthreads();
 
-  double dot = 0.0;
+  double dot = 0.0, dot2 = 0.0;
   if (warp == kCompute / 32) {
     // ---------------- producer warp ----------------
     if (lane == 0) {
@@ -300,6 +303,7 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
             const double rr = a.b[row + r] - ax;
             a.y[row + r] = rr;
             dot = fma(rr, rr, dot);
+            if (a.z) dot2 = fma(rr, a.z[row + r], dot2);
           }
         }
       }
@@ -316,9 +320,14 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
   if (!a.partial) return;
   __shared__ double sh32[32];
   const double bs = block_sum(dot, sh32);
-  if (tid == 0) a.partial[blockIdx.x] = bs;
+  const double bs2 = (MODE == 1 && a.z) ? block_sum(dot2, sh32) : 0.0;
+  if (tid == 0) {
+    a.partial[blockIdx.x] = bs;
+    if (MODE == 1 && a.z) a.partial[gridDim.x + blockIdx.x] = bs2;
+  }
   if (!last_block(a.counter)) return;
   const double tot = sum_partials(a.partial, gridDim.x, sh32);
+  const double tot2 = (MODE == 1 && a.z) ? sum_partials(a.partial + gridDim.x, gridDim.x, sh32) : 0.0;
   if (tid == 0) {
     *a.counter = 0u;
     if (a.tstat) {   // this block finished last: launch duration = now - first start
@@ -339,6 +348,7 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
       } else {
         scal[S_TRUE_RR] = tot;
         scal[S_RR] = tot;
+        if (a.z) scal[S_RZOLD] = tot2;
       }
     }
   }
@@ -422,7 +432,7 @@ long long igafd_stencil_halo(int p, const int *n) {
 // PCG convergence flag is set.
 igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
                                   int pcg, int skip_done, cudaStream_t s, int every,
-                                  unsigned long long *tstat) {
+                                  unsigned long long *tstat, const double *z) {
   // the kernel reads x windows that reach p planes beyond the box: use a
   // zero-padded copy unless x already is one (PCG search direction / iterate)
   if (x != P->pv && x != P->xpad && x != P->xs) {
@@ -434,6 +444,7 @@ igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, co
   a.x = x;
   a.y = y;
   a.b = b;
+  a.z = (b && pcg) ? z : nullptr;
   a.n1 = P->n[0];
   a.n2 = P->n[1];
   a.n3 = P->n[2];

@@ -79,7 +79,7 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step",
            "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi", "igafd_adi_greedy",
            "igafd_adi_wachspress", "igafd_mp_numbering", "igafd_mp_subdomain", "igafd_mp_create",
-           "igafd_mp_destroy", "igafd_mp_apply_ias"]
+           "igafd_mp_destroy", "igafd_mp_apply_ias", "igafd_quad_points", "igafd_load_rhs"]
 
 MLP_PARAMS = 4738
 
@@ -103,6 +103,8 @@ def lib():
     L.igafd_apply_A.argtypes = [vp, vp, vp, vp]
     L.igafd_apply_prec.argtypes = [vp, C.c_int, vp, vp, vp]
     L.igafd_load_rhs_sine.argtypes = [vp, vp, vp]
+    L.igafd_load_rhs.argtypes = [vp, vp, vp, vp]
+    L.igafd_quad_points.argtypes = [vp, vp, vp]
     L.igafd_pcg_solve.argtypes = [vp, C.POINTER(PCGOpts), vp, vp, C.POINTER(PCGInfo), vp]
     L.igafd_batch_pcg_solve.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp),
                                         C.POINTER(PCGOpts), C.POINTER(PCGInfo), vp]
@@ -485,6 +487,26 @@ class Patch:
         _check(lib().igafd_apply_prec_adi(self.h, _dev_ptr(r, self.N), _dev_ptr(z, self.N),
                                           _stream()), "apply_prec_adi")
         return z
+
+    def n_quad_points(self):
+        return int(np.prod([self.info.nel[k] * (self.info.p + 1) for k in range(self.dim)]))
+
+    def quad_points(self):
+        """float64 CUDA tensor [dim][Q]: physical coordinates of the patch's
+        quadrature points (order of igafd_quad_points)."""
+        import torch
+        x = torch.empty((self.dim, self.n_quad_points()), dtype=torch.float64, device="cuda")
+        _check(lib().igafd_quad_points(self.h, C.c_void_p(x.data_ptr()), _stream()), "quad_points")
+        return x
+
+    def load_rhs(self, f_qp, b=None):
+        """b_i = int f B_i |det J| from f at the quadrature points (a float64
+        CUDA tensor of n_quad_points() values, order of quad_points())."""
+        import torch
+        b = torch.empty(self.N, dtype=torch.float64, device="cuda") if b is None else b
+        _check(lib().igafd_load_rhs(self.h, _dev_ptr(f_qp.reshape(-1), self.n_quad_points()),
+                                    _dev_ptr(b, self.N), _stream()), "load_rhs")
+        return b
 
     def load_rhs_sine(self, b=None):
         import torch

@@ -14,8 +14,8 @@ P^-1 A from 30 PCG steps (the CG-Lanczos tridiagonal), and the refined label
 is kept when full PCG needs no more iterations than before. The network
 learns the labels from the six per-span features of Q, so at solve time the
 scalings come from the features alone. The unscaled preconditioner remains
-the fallback when the scaled run breaks down or exceeds its iteration
-budget.
+the fallback when the scaled run breaks down or exceeds the unscaled
+preconditioner's iteration budget (or the scaled pencils cannot be set up).
 """
 from __future__ import annotations
 
@@ -161,17 +161,35 @@ def predict_scalings(patch, net):
     return net.forward(patch.features())
 
 
-def scaled_solve(patch, net, b, tol=1e-8, max_iter=1000, dtype="fp64"):
-    """Solve with the learned scalings; fall back to the unscaled
-    preconditioner when the scaled solve does not succeed within max_iter.
-    Returns (x, info, used_fallback, prep_seconds)."""
-    t0 = time.perf_counter()
-    logw = predict_scalings(patch, net)
-    patch.set_scalings(logw)
-    prep = time.perf_counter() - t0
-    x, info = patch.pcg(b, tol=tol, max_iter=max_iter, dtype=dtype, raise_on_error=False)
-    if info.status != 0:
+def solve_with_scalings(patch, logw, b, tol=1e-8, max_iter=1000, dtype="fp64", budget=None):
+    """PCG with the span scalings logw ([rows][2] CUDA tensor), capped at
+    `budget` iterations (the unscaled preconditioner's iteration budget;
+    default max_iter). Falls back to the paper's unscaled P -- a fresh solve
+    from x0 = 0 with up to max_iter iterations -- when the scalings cannot be
+    set up (a pencil that is not positive definite or an eigen-solve that
+    fails), or when the scaled solve breaks down or has not converged within
+    the budget. Returns (x, info, used_fallback)."""
+    cap = max_iter if budget is None else min(int(budget), max_iter)
+    try:
+        patch.set_scalings(logw)
+    except igafd.IgafdError:
         patch.set_scalings(None)
         x, info = patch.pcg(b, tol=tol, max_iter=max_iter, dtype=dtype, raise_on_error=False)
-        return x, info, True, prep
-    return x, info, False, prep
+        return x, info, True
+    x, info = patch.pcg(b, tol=tol, max_iter=cap, dtype=dtype, raise_on_error=False)
+    if info.status != igafd.OK:
+        patch.set_scalings(None)
+        x, info = patch.pcg(b, tol=tol, max_iter=max_iter, dtype=dtype, raise_on_error=False)
+        return x, info, True
+    return x, info, False
+
+
+def scaled_solve(patch, net, b, tol=1e-8, max_iter=1000, dtype="fp64", budget=None):
+    """Solve with the network's span scalings, under the fallback rule of
+    solve_with_scalings. Returns (x, info, used_fallback, prep_seconds)."""
+    t0 = time.perf_counter()
+    logw = predict_scalings(patch, net)
+    prep = time.perf_counter() - t0
+    x, info, fell_back = solve_with_scalings(patch, logw, b, tol=tol, max_iter=max_iter,
+                                             dtype=dtype, budget=budget)
+    return x, info, fell_back, prep

@@ -23,5 +23,13 @@ def to_dev(a):
 
 
 def rel(a, b):
+    """2-norm relative difference ||a - b|| / ||b||."""
     a = np.asarray(a); b = np.asarray(b)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def maxrel(a, b):
+    """Entry-wise difference max_i |a_i - b_i| / max_i |b_i|: a few wrong
+    entries (a boundary slab of a tile, a ragged edge) cannot hide in it."""
+    a = np.asarray(a); b = np.asarray(b)
+    return float(np.abs(a - b).max() / np.abs(b).max())

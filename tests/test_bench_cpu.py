@@ -50,7 +50,8 @@ def test_max_over_ranks_single_rank_is_identity():
 
 
 def _reference_args(gpus):
-    return types.SimpleNamespace(n=16, p=2, tol=1e-8, steps=1, warmup=0, gpus=gpus)
+    return types.SimpleNamespace(n=16, p=2, tol=1e-8, steps=1, warmup=0, gpus=gpus,
+                                 ref_budget=60.0, workers=2)
 
 
 def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
@@ -71,3 +72,36 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
     assert isinstance(line["cpu_baseline"]["cpu_model"], str) and line["cpu_baseline"]["cpu_model"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_reference_arm_counts_only_the_solves_it_ran(monkeypatch):
+    """A step of the reference arm is one full oracle solve; with a budget of
+    zero seconds it stops after the first timed solve and says so."""
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    args = _reference_args(1)
+    args.steps, args.ref_budget, args.workers = 5, 0.0, 1
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(args)
+    line = json.loads(buf.getvalue().strip())
+    assert line["steps"] == 1 and line["steps_requested"] == 5
+    assert line["iterations"] > 0 and line["ms_per_step"] == 1e3 * line["value"]
+
+
+def test_oracle_leg_reports_solution_differences():
+    """The oracle leg solves the workload itself: fed its own tol solution as
+    the 'GPU' FP64 solution, the same-tolerance difference is exactly 0 and the
+    difference from the converged (1e-13) solution is the algebraic error of
+    a 1e-8 solve (small, but not 0)."""
+    import numpy as np
+    import bench
+    o = bench.OracleRun(12, 2, workers=1)
+    res, _, _ = o.solve(1e-8)
+    cpu, vs = bench.oracle_baseline(12, 2, 1e-8, {"fp64": res.x, "tf32": res.x + 1e-9}, workers=1)
+    assert cpu["kind"] == "oracle" and cpu["iterations"] == res.iters and cpu["value"] > 0
+    assert vs["fp64"]["vs_oracle_same_tol"]["max_rel"] == 0.0
+    assert 0.0 < vs["fp64"]["vs_converged"]["max_rel"] < 1e-6
+    assert vs["tf32"]["vs_converged"]["max_rel"] > 0.0
+    assert vs["oracle_iterations_at_tol"] == res.iters
+    assert np.isfinite(vs["fp64"]["vs_converged"]["l2_rel"])

@@ -5,14 +5,16 @@ Tolerances (FP64 path): the GPU and the oracle evaluate the same sums in a
 different order, so entries agree to a few ulps of the largest term:
 stencil 1e-13 of max|A|, products with A 1e-12 of max|y|, the FD apply
 1e-11 relative (two triangular-factor eigenbases, six dense products),
-PCG iterates and converged solutions 1e-10 relative.
+PCG iterates and converged solutions 1e-10 relative. Every vector is
+compared entry by entry (max|a - b| <= tol max|b|) and, where the bound was
+derived for it, also in the 2-norm.
 """
 import numpy as np
 import pytest
 
 import synth
 from oracle import assemble, fd, pcg
-from gpu_util import need_gpu, make_patch, to_dev, rel
+from gpu_util import need_gpu, make_patch, to_dev, rel, maxrel
 
 pytestmark = pytest.mark.gpu
 
@@ -107,7 +109,8 @@ def test_apply_prec_fp64(case):
     F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
     r = synth.random_vector(disc.N, 12)
     z = patch.apply_prec(to_dev(r)).cpu().numpy()
-    assert rel(z, F.apply(r)) <= 1e-11
+    zo = F.apply(r)
+    assert rel(z, zo) <= 1e-11 and maxrel(z, zo) <= 1e-11
 
 
 def test_apply_prec_fp32(case):
@@ -115,7 +118,8 @@ def test_apply_prec_fp32(case):
     F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
     r = synth.random_vector(disc.N, 13)
     z = patch.apply_prec(to_dev(r), dtype="fp32").cpu().numpy()
-    assert rel(z, F.apply(r)) <= 1e-4
+    zo = F.apply(r)
+    assert rel(z, zo) <= 1e-4 and maxrel(z, zo) <= 1e-4
 
 
 TC_TOL = {"tf32": 1e-2, "fp16": 1e-2, "bf16": 4e-2}
@@ -130,9 +134,10 @@ def test_apply_prec_tensor_core(case, dtype):
     F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
     r = synth.random_vector(disc.N, 14)
     z = patch.apply_prec(to_dev(r), dtype=dtype).cpu().numpy()
-    err = rel(z, F.apply(r))
-    print(f"{dtype} FD rel err {err:.2e}")
-    assert err <= TC_TOL[dtype]
+    zo = F.apply(r)
+    err, emax = rel(z, zo), maxrel(z, zo)
+    print(f"{dtype} FD rel err {err:.2e} entry-wise {emax:.2e}")
+    assert err <= TC_TOL[dtype] and emax <= TC_TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", ["tf32", "bf16"])
@@ -157,10 +162,11 @@ def test_apply_prec_fused_matches_per_mode(case, dtype):
     l2 = igafd.kernel_launches()
     # one kernel per mode product, against one per pair of them
     assert (l1 - l0, l2 - l1) == (2 * prob.dim, prob.dim)
-    e_pass, e_fused, e_mut = rel(z_pass, zo), rel(z_fused, zo), rel(z_fused, z_pass)
-    print(f"{dtype}: per-mode {e_pass:.2e} fused {e_fused:.2e} mutual {e_mut:.2e}")
+    e_pass, e_fused, e_mut = maxrel(z_pass, zo), maxrel(z_fused, zo), maxrel(z_fused, z_pass)
+    print(f"{dtype} entry-wise: per-mode {e_pass:.2e} fused {e_fused:.2e} mutual {e_mut:.2e}")
     assert e_pass <= TC_TOL[dtype] and e_fused <= TC_TOL[dtype]
     assert e_mut <= TC_TOL[dtype]
+    assert rel(z_pass, zo) <= TC_TOL[dtype] and rel(z_fused, zo) <= TC_TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", ["tf32", "bf16", "fp16"])
@@ -178,7 +184,8 @@ def test_pcg_tensor_core_preconditioner(case, dtype):
     # relative error eps needs about log(1e-8)/log(eps) steps instead
     bound = r8.iters + 2 if r8.iters > 2 else 8
     assert info.iterations <= bound, (info.iterations, r8.iters)
-    assert rel(x.cpu().numpy(), ro.x) <= 1e-7
+    xg = x.cpu().numpy()
+    assert rel(xg, ro.x) <= 1e-7 and maxrel(xg, ro.x) <= 1e-7
 
 
 def test_rhs_sine(case):
@@ -187,6 +194,30 @@ def test_rhs_sine(case):
          3: lambda x, y, z: 3 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)}
     bo = disc.assemble_rhs(f[prob.dim])
     b = patch.load_rhs_sine().cpu().numpy()
+    assert np.abs(b - bo).max() <= 1e-13 * np.abs(bo).max()
+
+
+def test_quad_points_and_general_rhs(case):
+    """igafd_quad_points gives the oracle's physical quadrature points (the map
+    F on the tensor Gauss grid), and igafd_load_rhs with a load sampled there
+    gives the oracle's right-hand side for that load (not a manufactured one)."""
+    prob, disc, S, patch = case
+    torch = pytest.importorskip("torch")
+    X = patch.quad_points()
+    pts = [disc.qz[k].ravel() for k in range(prob.dim)]
+    Fo, _ = disc.geo.eval_grid(pts)                  # [c][q_d]..[q_1], direction 1 fastest
+    Fo = Fo.reshape(prob.dim, -1)
+    assert X.shape == Fo.shape
+    assert np.abs(X.cpu().numpy() - Fo).max() <= 1e-14
+    if prob.dim == 2:
+        f_np = lambda x, y: np.exp(x) * np.cos(3.0 * y) + 2.0 * x * y
+        f_t = lambda x, y: torch.exp(x) * torch.cos(3.0 * y) + 2.0 * x * y
+    else:
+        f_np = lambda x, y, z: np.exp(x) * np.cos(3.0 * y) + 2.0 * x * y * z - z
+        f_t = lambda x, y, z: torch.exp(x) * torch.cos(3.0 * y) + 2.0 * x * y * z - z
+    fq = f_t(*[X[c] for c in range(prob.dim)]).contiguous()
+    b = patch.load_rhs(fq).cpu().numpy()
+    bo = disc.assemble_rhs(f_np)
     assert np.abs(b - bo).max() <= 1e-13 * np.abs(bo).max()
 
 
@@ -200,7 +231,31 @@ def test_pcg_fixed_iterates(case):
     ro = pcg.pcg(lambda v: A @ v, b, F.apply, fixed_iters=k)
     x, info = patch.pcg(to_dev(b), tol=0.0, max_iter=k)
     assert info.iterations == k
-    assert rel(x.cpu().numpy(), ro.x) <= 1e-10
+    xg = x.cpu().numpy()
+    assert rel(xg, ro.x) <= 1e-10 and maxrel(xg, ro.x) <= 1e-10
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+def test_pcg_fixed_iterates_periodic_true_residual(case, flexible):
+    """The periodic true residual r = b - A x (every 3 iterations here, so it
+    replaces the recurrence residual at k = 3 and 6 of 8) gives the oracle's
+    x_8 on both sides, with Fletcher-Reeves and with the flexible beta (whose
+    (r, z_old) must then come from the recomputed residual); a wrong
+    predicate on the iteration counter or a stale scalar would move x_8."""
+    prob, disc, S, patch = case
+    A = assemble.stencil_to_csr(disc, S)
+    F = fd.FD([disc.pencil(k) for k in range(prob.dim)])
+    b = synth.random_rhs(disc.N, 15)
+    k = 8
+    ro = pcg.pcg(lambda v: A @ v, b, F.apply, fixed_iters=k, true_every=3, flexible=flexible)
+    x, info = patch.pcg(to_dev(b), tol=0.0, max_iter=k, true_every=3, flexible=flexible)
+    assert info.iterations == k
+    xg = x.cpu().numpy()
+    assert rel(xg, ro.x) <= 1e-10 and maxrel(xg, ro.x) <= 1e-10
+    # without the recomputation the iterate differs from this one (the pin
+    # would catch a predicate that never fires)
+    rn = pcg.pcg(lambda v: A @ v, b, F.apply, fixed_iters=k, true_every=0, flexible=flexible)
+    assert not np.array_equal(rn.x, ro.x)
 
 
 def test_pcg_converged_solution(case):
@@ -213,7 +268,8 @@ def test_pcg_converged_solution(case):
     assert ro.converged
     x, info = patch.pcg(to_dev(b), tol=1e-12, max_iter=500)
     assert info.status == 0 and info.true_relres <= 1e-12
-    assert rel(x.cpu().numpy(), ro.x) <= 1e-10
+    xg = x.cpu().numpy()
+    assert rel(xg, ro.x) <= 1e-10 and maxrel(xg, ro.x) <= 1e-10
     # the iteration count equals the oracle's at the same tolerance
     r8 = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-8, max_iter=500)
     _, i8 = patch.pcg(to_dev(b), tol=1e-8, max_iter=500)
@@ -230,7 +286,8 @@ def test_pcg_fp32_preconditioner(case):
     x, info = patch.pcg(to_dev(b), tol=1e-8, max_iter=500, dtype="fp32")
     assert info.status == 0
     assert info.iterations <= r8.iters + 2
-    assert rel(x.cpu().numpy(), ro.x) <= 1e-7
+    xg = x.cpu().numpy()
+    assert rel(xg, ro.x) <= 1e-7 and maxrel(xg, ro.x) <= 1e-7
 
 
 def test_identity_map_one_iteration(torch):
@@ -245,7 +302,7 @@ def test_identity_map_one_iteration(torch):
     A = assemble.stencil_to_csr(disc, S)
     bo = disc.assemble_rhs(lambda x, y: 2 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y))
     xo = np.linalg.solve(A.toarray(), bo)
-    assert rel(x.cpu().numpy(), xo) <= 1e-10
+    assert rel(x.cpu().numpy(), xo) <= 1e-10 and maxrel(x.cpu().numpy(), xo) <= 1e-10
     patch.close()
 
 
@@ -292,9 +349,11 @@ def test_full_size_sampled(torch):
     r = synth.random_vector(disc.N, 21)
     zo = F.apply(r)
     z = patch.apply_prec(to_dev(r)).cpu().numpy()
-    assert rel(z, zo) <= 1e-11
+    assert rel(z, zo) <= 1e-11 and maxrel(z, zo) <= 1e-11
     for dt, tol in TC_TOL.items():
-        assert rel(patch.apply_prec(to_dev(r), dtype=dt).cpu().numpy(), zo) <= tol
+        zt = patch.apply_prec(to_dev(r), dtype=dt).cpu().numpy()
+        print(f"n=128 {dt} FD: 2-norm {rel(zt, zo):.2e} entry-wise {maxrel(zt, zo):.2e}")
+        assert rel(zt, zo) <= tol and maxrel(zt, zo) <= tol
     b = synth.random_rhs(disc.N, 22)
     x, info = patch.pcg(to_dev(b), tol=1e-8)
     assert info.status == 0 and info.true_relres <= 1e-8
@@ -331,9 +390,10 @@ def test_fd_n128_kernels(torch, dtype):
     l0 = igafd.kernel_launches()
     z = patch.apply_prec(rd, dtype=dtype).cpu().numpy()
     assert igafd.kernel_launches() - l0 == 3
-    e, e_pass, e_mut = rel(z, zo), rel(z_pass, zo), rel(z, z_pass)
-    print(f"n=128 {dtype}: fused {e:.2e} per-mode {e_pass:.2e} mutual {e_mut:.2e}")
+    e, e_pass, e_mut = maxrel(z, zo), maxrel(z_pass, zo), maxrel(z, z_pass)
+    print(f"n=128 {dtype} entry-wise: fused {e:.2e} per-mode {e_pass:.2e} mutual {e_mut:.2e}")
     assert e <= TC_TOL[dtype] and e_pass <= TC_TOL[dtype] and e_mut <= TC_TOL[dtype]
+    assert rel(z, zo) <= TC_TOL[dtype] and rel(z_pass, zo) <= TC_TOL[dtype]
     # a second call on the same input gives the same bits
     z2 = patch.apply_prec(rd, dtype=dtype).cpu().numpy()
     assert np.array_equal(z, z2)
@@ -367,7 +427,7 @@ def test_batched_solve_matches_single_solves(torch):
     F = fd.FD([disc.pencil(k) for k in range(3)])
     ro = pcg.pcg(lambda v: A @ v, bs[0].cpu().numpy(), F.apply, tol=1e-13, max_iter=500)
     xs, _ = igafd.batch_pcg(patches, bs, tol=1e-12, dtype="fp64")
-    assert rel(xs[0].cpu().numpy(), ro.x) <= 1e-10
+    assert rel(xs[0].cpu().numpy(), ro.x) <= 1e-10 and maxrel(xs[0].cpu().numpy(), ro.x) <= 1e-10
     for p in patches:
         p.close()
 
@@ -390,7 +450,7 @@ def test_autotune_fd_form(torch):
         l0 = igafd.kernel_launches()
         z = patch.apply_prec(to_dev(r), dtype=dt).cpu().numpy()
         assert igafd.kernel_launches() - l0 == (3 if forms[i] else 6)
-        assert rel(z, zo) <= TC_TOL[dt]
+        assert rel(z, zo) <= TC_TOL[dt] and maxrel(z, zo) <= TC_TOL[dt]
     patch.set_fd_fused(1)          # an explicit choice replaces the tuned one
     assert list(patch.query().fd_fused)[:2] == [1, 1]
     patch.close()

@@ -13,7 +13,7 @@ import pytest
 
 import synth
 from oracle import multipatch as mpm
-from gpu_util import need_gpu, to_dev
+from gpu_util import need_gpu, to_dev, maxrel
 
 pytestmark = pytest.mark.gpu
 
@@ -74,6 +74,7 @@ def test_schwarz_apply_matches_oracle(torch, nel, p):
     if 2 * L.m - 3 <= 256:                                # the tensor-core FD takes n_k <= 256
         z32 = S.apply(to_dev(r), dtype="tf32").cpu().numpy()
         assert np.linalg.norm(z32 - z_o) <= 1e-2 * np.linalg.norm(z_o)
+        assert maxrel(z32, z_o) <= 1e-2
 
 
 def test_schwarz_rejects_bad_rows(torch):

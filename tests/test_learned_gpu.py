@@ -6,7 +6,7 @@ import pytest
 
 import synth
 from oracle import assemble, fd, learned as olearned, pcg
-from gpu_util import need_gpu, make_patch, to_dev, rel
+from gpu_util import need_gpu, make_patch, to_dev, rel, maxrel
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +37,7 @@ def test_variable_coefficient_stencil_and_solve(kcase):
     ro = pcg.pcg(lambda v: A @ v, b, F.apply, tol=1e-13, max_iter=800)
     x, info = patch.pcg(to_dev(b), tol=1e-12, max_iter=800)
     assert info.status == 0 and rel(x.cpu().numpy(), ro.x) <= 1e-10
+    assert maxrel(x.cpu().numpy(), ro.x) <= 1e-10
 
 
 def test_features_and_sepfit_match_oracle(kcase):
@@ -78,7 +79,8 @@ def test_scaled_preconditioner_matches_oracle_and_affine_pin(torch):
     patch.set_scalings(lw)
     r = synth.random_vector(disc.N, 8)
     Fs = fd.FD(olearned.scaled_pencils(disc, lw.double().cpu().numpy()))
-    assert rel(patch.apply_prec(to_dev(r)).cpu().numpy(), Fs.apply(r)) <= 1e-10
+    zs = patch.apply_prec(to_dev(r)).cpu().numpy()
+    assert rel(zs, Fs.apply(r)) <= 1e-10 and maxrel(zs, Fs.apply(r)) <= 1e-10
     b = to_dev(synth.random_rhs(disc.N, 9))
     # the scaled P equals A up to the float32 rounding of the log scalings
     # (~1e-7), so one iteration reaches 1e-6
@@ -88,6 +90,30 @@ def test_scaled_preconditioner_matches_oracle_and_affine_pin(torch):
     _, info0 = patch.pcg(b, tol=1e-6)
     assert info0.iterations > 3
     patch.close()
+
+
+def test_fallback_when_the_scaled_solve_exceeds_the_unscaled_budget(kcase, torch):
+    """Span scalings of the wrong sign (the separable fit negated and tripled)
+    make P a poor model of A: the scaled solve runs out of the unscaled
+    solve's iteration budget and the unscaled preconditioner's solve is
+    returned, bitwise that of the plain solve. With the fit itself the scaled
+    solve is kept whenever it converges within the budget."""
+    from paper_1602_01636_gb300 import learned
+    prob, disc, patch = kcase
+    b = to_dev(synth.random_rhs(disc.N, 12))
+    patch.set_scalings(None)
+    x0, i0 = patch.pcg(b, tol=1e-8)
+    assert i0.status == 0
+    fit = patch.sepfit()
+    x, info, fell_back = learned.solve_with_scalings(patch, -3.0 * fit, b, tol=1e-8,
+                                                     budget=i0.iterations)
+    assert fell_back and info.status == 0 and info.iterations == i0.iterations
+    assert torch.equal(x, x0)
+    x, info, fell_back = learned.solve_with_scalings(patch, fit, b, tol=1e-8, budget=i0.iterations)
+    assert info.status == 0
+    if not fell_back:
+        assert info.iterations <= i0.iterations
+    patch.set_scalings(None)
 
 
 def test_network_forward_and_gradient_match_oracle(torch):

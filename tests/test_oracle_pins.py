@@ -587,3 +587,20 @@ def test_general_affine_map_closed_form():
                 fac.append(Km if m == k == l else Gm if m == k else Gm.T if m == l else Mm)
             expect = expect + Q[k, l] * np.kron(fac[2], np.kron(fac[1], fac[0]))
     assert np.abs(A - expect).max() <= 1e-13 * np.abs(A).max()
+
+
+def test_parallel_assembly_matches_serial():
+    """The process-parallel assembly (plane ranges summed by spawned workers,
+    range sums added in order) gives the serial A and b up to the association
+    of each row's element sums."""
+    prob = synth.Problem(3, (9, 8, 10), 2, [0.03, -0.02, 0.04])
+    disc = assemble.Discretization.from_problem(prob)
+    S1, S2 = disc.assemble_stencil(), disc.assemble_stencil(workers=3)
+    assert np.abs(S1 - S2).max() <= 1e-14 * np.abs(S1).max()
+    b1 = disc.assemble_rhs(assemble.sine_load)
+    b2 = disc.assemble_rhs(assemble.sine_load, workers=3)
+    assert np.abs(b1 - b2).max() <= 1e-14 * np.abs(b1).max()
+    # the module-level manufactured load is f = 3 pi^2 sin sin sin
+    x = np.array([0.3, 0.7]), np.array([0.2, 0.5]), np.array([0.9, 0.4])
+    ref = 3 * np.pi ** 2 * np.sin(np.pi * x[0]) * np.sin(np.pi * x[1]) * np.sin(np.pi * x[2])
+    assert np.allclose(assemble.sine_load(*x), ref, rtol=1e-15, atol=0)
