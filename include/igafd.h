@@ -14,8 +14,10 @@
  *    n_k = m_k - 2 counts the B-splines of direction k that vanish on the
  *    boundary (homogeneous Dirichlet conditions). Device vectors must be
  *    8-byte aligned; 256-byte alignment gives the best bandwidth.
- *  - The patch owns every device buffer it uses. Only igafd_setup_patch
- *    allocates; apply/solve entry points never allocate.
+ *  - The patch owns every device buffer it uses. Only the set-up calls
+ *    (igafd_setup_patch, igafd_batch_create, ...) allocate; apply/solve entry
+ *    points never allocate (igafd_batch_pcg_solve, which creates and destroys
+ *    a batch, is the documented exception).
  *  - Errors are returned as igafd_status, never trapped on the device. After a
  *    device-side limit is hit, the status says so and the context stays usable.
  *  - Calls on one patch must not overlap in time on different streams (the
@@ -81,7 +83,7 @@ typedef struct {
   const int *kappa_n_knots;
   const double *const *kappa_knots;
   const double *kappa_ctrl;
-  int flags;                        /* 0, or IGAFD_SETUP_NO_STENCIL */
+  int flags;                        /* 0, IGAFD_SETUP_NO_STENCIL or IGAFD_SETUP_FULL_SPACE */
 } igafd_patch_desc;
 
 /* igafd_patch_desc.flags: build everything but the stiffness stencil (no
@@ -93,6 +95,17 @@ typedef struct {
  * (igafd_apply_A, igafd_pcg_solve, igafd_batch_pcg_solve, igafd_copy_stencil,
  * igafd_autotune, igafd_pcg_condition_estimate) return IGAFD_ERR_ARG. */
 #define IGAFD_SETUP_NO_STENCIL 1
+
+/* igafd_patch_desc.flags: keep every B-spline of every direction (the full
+ * space, n_k = m_k: no homogeneous Dirichlet removal), for a patch that is
+ * one piece of a multi-patch operator (igafd_mp_set_operator). Such a patch
+ * has the stiffness stencil over its full index box and no preconditioner
+ * (its full 1D stiffness matrices are singular): igafd_apply_prec,
+ * igafd_pcg_solve, igafd_setup_prec, igafd_get_eigen, igafd_set_scalings, the
+ * ADI calls and igafd_autotune return IGAFD_ERR_ARG; igafd_apply_A,
+ * igafd_copy_stencil, igafd_quad_points and the load vectors work on the full
+ * space. May be combined with nothing else. */
+#define IGAFD_SETUP_FULL_SPACE 2
 
 typedef struct {
   int dim, p;
@@ -221,17 +234,39 @@ igafd_status igafd_pcg_solve(igafd_patch *patch, const igafd_pcg_opts *opts,
                              const double *b_dev, double *x_dev,
                              igafd_pcg_info *info, void *stream);
 
-/* Solve count independent problems A_i x_i = b_i (one per patch, patches on
- * the same device) with the same options. Each problem's chunk of
- * opts->check_every iterations is captured once as a CUDA graph; one parent
- * graph holds them all as independent nodes, so a single graph launch
- * advances every unfinished problem concurrently, each with its own device
- * convergence flag (finished problems run no-op kernels until the parent
- * graph is rebuilt without them). b[i], x[i]: device vectors of patch i's
- * size; infos (optional) receives one igafd_pcg_info per problem. The
- * results are bitwise those of igafd_pcg_solve on each problem. Returns the
- * first non-OK problem status (OK if all converged); timing is ignored.
- * A given patch may appear only once. */
+/* Batched solve of count independent problems A_i x_i = b_i (one per patch,
+ * patches on the same device, each at most once) with the same options,
+ * driven on the device: one CUDA graph whose conditional while-node repeats
+ * one PCG iteration of every unfinished problem until all are finished, each
+ * problem with its own device convergence state (recurrence test, true-
+ * residual confirmation and restart, iteration cap, breakdown). An iteration
+ * is a few launches over all problems: the stencil as one persistent launch
+ * per (dim, p, rows per thread) class whose CTAs take (problem, CTA) work
+ * items from a device queue, the vector updates and dot products as one
+ * launch each, and the tensor-core FD as one launch per kernel kind for
+ * problems on the fused kernels (other FD forms run their own launches).
+ * Each work item is a CTA of the problem's own single-problem grid, so the
+ * results are bitwise those of igafd_pcg_solve on each problem.
+ *
+ * igafd_batch_create allocates the batch's device tables and builds the
+ * graph for these patches and options (opts->check_every and timing are not
+ * used); it must be re-created when a patch's autotuned choices or its
+ * preconditioner set-up change. igafd_batch_solve allocates nothing: b[i],
+ * x[i] are device vectors of patch i's size (x[i] the initial guess when
+ * opts->x0_given); infos (optional) receives one igafd_pcg_info per problem.
+ * It synchronises the stream twice (before the loop, to read every (b, b),
+ * and after it). Returns the first non-OK problem status (OK if all
+ * converged; IGAFD_ERR_TIMEOUT for a problem still unfinished when the loop
+ * guard of 2 max_iter + 16 passes ran out). Errors: ARG, OOM, CUDA. */
+typedef struct igafd_batch igafd_batch;
+igafd_status igafd_batch_create(igafd_patch *const *patches, int count,
+                                const igafd_pcg_opts *opts, igafd_batch **out);
+igafd_status igafd_batch_solve(igafd_batch *batch, const double *const *b_dev,
+                               double *const *x_dev, igafd_pcg_info *infos, void *stream);
+void igafd_batch_destroy(igafd_batch *batch);
+
+/* igafd_batch_create, igafd_batch_solve and igafd_batch_destroy in one call
+ * (allocates and frees the batch's tables each time). */
 igafd_status igafd_batch_pcg_solve(igafd_patch *const *patches, int count,
                                    const double *const *b_dev, double *const *x_dev,
                                    const igafd_pcg_opts *opts, igafd_pcg_info *infos,
@@ -512,6 +547,38 @@ void igafd_mp_destroy(igafd_mp *mp);
  * r_dev, z_dev: length-n_global FP64 device vectors, not overlapping. */
 igafd_status igafd_mp_apply_ias(igafd_mp *mp, igafd_dtype dtype, const double *r_dev,
                                 double *z_dev, void *stream);
+
+/* The multi-patch stiffness matrix (Section 6: the global C^0 space of glued
+ * patches, Eq. (A) summed over the patches): A = sum_q R_q^T A_q R_q, where
+ * A_q is patch q's stiffness on its full index box (patches[q] built with
+ * IGAFD_SETUP_FULL_SPACE) and R_q takes a global free vector to the patch's
+ * local functions: free_of_local[q][t] (host, one per local function,
+ * direction 1 fastest) is the global free index of local function t, or -1
+ * for a function fixed by the Dirichlet condition (from igafd_mp_numbering:
+ * the rank of its global function among the free ones). The indices of one
+ * patch must be distinct. Replaces an earlier operator; the patches must
+ * outlive mp. Errors: ARG (not full-space, no stencil, bad indices), OOM. */
+igafd_status igafd_mp_set_operator(igafd_mp *mp, int npatch, igafd_patch *const *patches,
+                                   const long long *const *free_of_local);
+
+/* y = A x with the operator of igafd_mp_set_operator: y = 0, then per patch
+ * a gather to its full index box (fixed functions 0), the patch's own
+ * stencil, and a scatter-add of the free rows (patches one after the other
+ * on the stream, so no atomics). x_dev, y_dev: length n_global, not
+ * overlapping. */
+igafd_status igafd_mp_apply_A(igafd_mp *mp, const double *x_dev, double *y_dev, void *stream);
+
+/* Conjugate gradients on the multi-patch system A x = b (Section 6, Table
+ * "L"), preconditioned by P_IAS (igafd_mp_apply_ias with opts->prec_dtype:
+ * FP64, FP32 or the tensor-core types), with the stopping rule of
+ * igafd_pcg_solve (recurrence residual, confirmed by the true residual;
+ * periodic true residual every opts->true_every; Fletcher-Reeves or, with
+ * opts->flexible, the flexible beta). The host drives the loop and reads the
+ * dot products back every iteration (the multi-patch problems are small 2D
+ * ones); uses workspace allocated by igafd_mp_set_operator. b_dev, x_dev:
+ * length n_global (x_dev the initial guess when opts->x0_given). */
+igafd_status igafd_mp_pcg_solve(igafd_mp *mp, const igafd_pcg_opts *opts, const double *b_dev,
+                                double *x_dev, igafd_pcg_info *info, void *stream);
 
 /* Number of kernels this library has enqueued in this process so far (all
  * devices, all patches); for launch accounting by benchmarks. */

@@ -641,6 +641,7 @@ extern "C" igafd_status igafd_adi_wachspress(double a, double b, double eps, int
 
 extern "C" igafd_status igafd_adi_parameters(igafd_patch *P, double eps, int max_J, double *omega,
                                              int *J_out) {
+  if (P && !P->dshift) return IGAFD_ERR_ARG;   // a full-space patch has no preconditioner
   if (!P || (P->dim != 2 && P->dim != 3) || !omega || !J_out || max_J < 1 || !(eps > 0.0) ||
       !(eps < 1.0))
     return IGAFD_ERR_ARG;
@@ -661,6 +662,7 @@ extern "C" igafd_status igafd_adi_parameters(igafd_patch *P, double eps, int max
 
 extern "C" igafd_status igafd_adi_setup(igafd_patch *P, const double *omega, int J, igafd_dtype dtype,
                                         void *stream) {
+  if (P && !P->dshift) return IGAFD_ERR_ARG;   // a full-space patch has no preconditioner
   if (!P || (P->dim != 2 && P->dim != 3) || !omega || J < 1 || J > 100000 ||
       (dtype != IGAFD_FP64 && dtype != IGAFD_FP32))
     return IGAFD_ERR_ARG;

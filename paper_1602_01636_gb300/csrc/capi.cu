@@ -126,7 +126,9 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
   IGAFD_CUDA(cudaMemsetAsync(P->counter, 0, 8 * sizeof(unsigned), s));
   IGAFD_CUDA(cudaMemsetAsync(P->scal, 0, (S_COUNT + 1) * sizeof(double), s));
   if (with_stencil) IGAFD_TRY(igafd_setup_stencil(P, s));
-  IGAFD_TRY(igafd_build_prec(P, s));
+  // a full-space patch (a piece of a multi-patch operator) has no P: its
+  // pencils include the boundary functions, so its K_k are singular
+  if (P->dshift) IGAFD_TRY(igafd_build_prec(P, s));
   igafd_tune_lookup(P);
   IGAFD_CUDA(cudaStreamSynchronize(s));
   return IGAFD_OK;
@@ -145,6 +147,7 @@ igafd_status igafd_build_prec(igafd_patch *P, cudaStream_t s) {
 }
 
 extern "C" igafd_status igafd_setup_prec(igafd_patch *P, void *stream) {
+  if (P && !P->dshift) return IGAFD_ERR_ARG;   // a full-space patch has no preconditioner
   if (!P) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   return igafd_build_prec(P, (cudaStream_t)stream);
@@ -185,6 +188,7 @@ extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *strea
   if (!P) return IGAFD_ERR_OOM;
   P->dim = d->dim;
   P->p = d->p;
+  P->dshift = (d->flags & IGAFD_SETUP_FULL_SPACE) ? 0 : 1;
   P->geo_p = d->geo_p;
   P->kappa_p = d->kappa_ctrl ? d->kappa_p : 0;
   P->kappa = d->kappa;
@@ -259,6 +263,7 @@ extern "C" igafd_status igafd_patch_query(const igafd_patch *P, igafd_patch_info
 
 extern "C" igafd_status igafd_get_eigen(const igafd_patch *P, int k, double *U_host,
                                         double *D_host) {
+  if (P && !P->dshift) return IGAFD_ERR_ARG;   // a full-space patch has no preconditioner
   if (!P || k < 0 || k >= P->dim) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   IGAFD_CUDA(cudaDeviceSynchronize());

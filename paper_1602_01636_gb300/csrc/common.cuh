@@ -66,6 +66,8 @@ enum {
   S_TRUE_RR,      // last true residual (r, r)
   S_TOL2,         // tol^2
   S_MAXIT,        // iteration cap
+  S_FIN,          // batched solve: 1.0 once the problem is finished (confirmed, capped or broken)
+  S_REC_RR,       // the recurrence (r, r) when it first met the tolerance
   S_COUNT
 };
 
@@ -75,6 +77,7 @@ struct igafd_patch {
   int dev;
   int dim, p, geo_p, kappa_p;
   int n[3], nel[3];
+  int dshift;                   // 1: Dirichlet functions removed (n_k = m_k - 2); 0: full space
   long long N;
   int n_off;
   double kappa;
@@ -175,6 +178,30 @@ igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, co
                                   unsigned long long *tstat = nullptr,
                                   const double *z = nullptr);
 long long igafd_stencil_row_stride(long long N);   // Np for a given N
+// batched solve (stencil.cu): the PCG stencil launches of a patch as
+// StencilArgs bytes (sel 0: q = A p; 1: periodic r = b - A x every `every`
+// iterations; 2: the convergence confirmation) with the single launch's grid,
+// and one persistent launch over many problems of one (dim, p, rows) class
+size_t igafd_stencil_args_bytes();
+igafd_status igafd_stencil_batch_args(igafd_patch *P, int sel, int flexible, int every, void *out,
+                                      long long *vgrid);
+igafd_status igafd_stencil_batch_launch(int dim, int p, int rows, int sel, const void *args_dev,
+                                        const long long *item_start_dev, int nprob,
+                                        unsigned long long *queue, int num_sms, cudaStream_t s);
+// batched solve (fd_tc.cu): true when the patch's tensor-core FD of operand
+// type dt runs as the generic fused kernels (so a batched launch can run it);
+// then the per-kind kernel arguments (FusedArgs bytes) and CTA counts
+bool igafd_fd_tc_fused_generic(const igafd_patch *P, igafd_dtype dt);
+size_t igafd_fd_fused_args_bytes();
+igafd_status igafd_fd_fused_batch_args(igafd_patch *P, igafd_dtype dt, void *args3, int *blocks3,
+                                       size_t *smem);
+// one batched launch of fused kind (0 slab forward, 1 pencil, 2 slab backward)
+igafd_status igafd_fd_fused_batch_launch(igafd_dtype dt, int kind, const void *args_dev,
+                                         const int *block_start_dev, int nprob, int total_blocks,
+                                         size_t smem, cudaStream_t s);
+// number of CTAs of the PCG vector kernels for N dofs (the same in single and
+// batched solves, so their reductions agree bitwise)
+int igafd_red_blocks(long long N);
 long long igafd_stencil_halo(int p, const int *n);   // zero halo of padded vectors
 void igafd_tune_lookup(igafd_patch *P);              // apply a cached autotune choice
 
@@ -192,6 +219,9 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// While set (on this thread), igafd_launch issues ordinary launches: the
+// batched solve captures its loop body that way.
+extern thread_local bool g_igafd_plain_launch;
 template <typename... KArgs, typename... Args>
 inline cudaError_t igafd_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                                 cudaStream_t s, Args... args) {
@@ -204,7 +234,7 @@ inline cudaError_t igafd_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, s
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = g_igafd_plain_launch ? 0 : 1;
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 

@@ -27,6 +27,7 @@
 #include <cuda_fp16.h>
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 namespace {
@@ -589,10 +590,7 @@ __device__ void stage_cols(unsigned char *R, const float *in, long long n12, lon
 }
 
 template <int OP, int KIND>
-__global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  if (a.done && *a.done != 0.0) return;
+__device__ __forceinline__ void tc_fused_cta(const FusedArgs &a, const int blk) {
   using T = Op<OP>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base =
@@ -604,7 +602,6 @@ __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int blk = blockIdx.x;
 
   auto wait_on = [&](uint64_t *b, uint32_t parity) -> bool {
     for (long long it = 0; it < kSpin; ++it) {
@@ -803,13 +800,49 @@ __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
+template <int OP, int KIND>
+__global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  if (a.done && *a.done != 0.0) return;
+  tc_fused_cta<OP, KIND>(a, blockIdx.x);
+}
+
+// The same kernel for many problems in one launch: CTA b runs CTA
+// b - block_start[i] of problem i's own launch (block_start[i] <= b <
+// block_start[i + 1]), with problem i's arguments; problems whose PCG is done
+// are skipped as in their own launch.
+template <int OP, int KIND>
+__global__ void __launch_bounds__(kThreads) tc_fused_batch_kernel(const FusedArgs *args,
+                                                                  const int *block_start, int nprob) {
+  __shared__ FusedArgs s_a;
+  __shared__ int s_blk, s_run;
+  if (threadIdx.x == 0) {
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = nprob - 1;                 // last problem with block_start <= b
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (block_start[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    s_a = args[lo];
+    s_blk = b - block_start[lo];
+    s_run = (b < block_start[lo + 1]) && !(s_a.done && *s_a.done != 0.0);
+  }
+  __syncthreads();
+  if (!s_run) return;
+  tc_fused_cta<OP, KIND>(s_a, s_blk);
+}
+
 // ---------------------------------------------------------------------------
 // Fused FD for n_1 = n_2 = n_3 = 128 (3D): the three kernels of the fused path
 // with every size a compile-time constant, 512 threads, both B images fetched
 // at the start, and staging, transposition and epilogue addressed through
 // per-thread constant swizzle offsets (the generic kernels above spend most
-// of their instructions on run-time index arithmetic). Layouts and products
-// are those of tc_fused_kernel.
+// of their instructions on run-time index arithmetic). Products are those of
+// tc_fused_kernel; the slab-forward kernel writes its result as [j2][i3][j1],
+// so that the pencil kernel's 128 x 128 input block (j2 = its CTA) is one
+// contiguous 64 KB run: a single bulk copy into shared memory and a transpose
+// there replace 128 strided row reads from L2.
 constexpr int kN = 128;            // dofs per direction on this path
 constexpr int kT128 = 512;         // threads per CTA
 constexpr int kAtomCol = kN * 128; // bytes of one 128-byte K atom over all 128 rows
@@ -897,32 +930,23 @@ __device__ __forceinline__ void stage128_rows_f32(unsigned char *R, const float 
   }
 }
 
-// A[c][k] = src[k * n12 + c] (FP32, c contiguous in memory): the transpose of
-// a 128 x 128 block. A lane loads four consecutive c at each of the
-// consecutive k of one 16-byte operand chunk and writes four rows' chunks;
-// a store phase's eight lanes of one c-quad hit eight distinct chunks.
+// A[c][k] = raw[k * kN + c] (FP32, the contiguous 128 x 128 block [k][c]
+// already in shared memory): the transpose of the block into the K-major
+// operand. A warp reads 32 consecutive c of E consecutive k (conflict-free
+// 128-byte rows) and writes one 16-byte operand chunk per lane.
 template <int OP>
-__device__ __forceinline__ void stage128_cols(unsigned char *R, const float *src, int warp,
-                                              int lane) {
+__device__ __forceinline__ void stage128_cols_smem(unsigned char *R, const float *raw, int warp,
+                                                   int lane) {
   constexpr int kB = Op<OP>::kBytes;
   constexpr int E = 16 / kB;                  // k per chunk: 4 (TF32) or 8 (BF16)
-  constexpr long long n12 = (long long)kN * kN;
-  constexpr int kBlocks = (kN / (8 * E)) * (kN / 16);   // blocks of 8E k x 16 c
-  const int kq = lane & 7, cq = lane >> 3;
+  constexpr int kTasks = (kN / 32) * (kN / E);
+#pragma unroll 2
+  for (int t = warp; t < kTasks; t += kT128 / 32) {
+    const int c = (t % (kN / 32)) * 32 + lane, k0 = (t / (kN / 32)) * E;
+    float v[E];
 #pragma unroll
-  for (int b = warp; b < kBlocks; b += kT128 / 32) {
-    const int kb = b % (kN / (8 * E)), cb = b / (kN / (8 * E));
-    const int k0 = kb * 8 * E + kq * E, c0 = cb * 16 + cq * 4;
-    float4 f[E];
-#pragma unroll
-    for (int kk = 0; kk < E; ++kk) f[kk] = __ldg(reinterpret_cast<const float4 *>(src + (k0 + kk) * n12 + c0));
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      float v[E];
-#pragma unroll
-      for (int kk = 0; kk < E; ++kk) v[kk] = e == 0 ? f[kk].x : e == 1 ? f[kk].y : e == 2 ? f[kk].z : f[kk].w;
-      *reinterpret_cast<uint4 *>(R + swz128((uint32_t)(c0 + e), (uint32_t)(k0 * kB))) = pack_chunk<OP>(v);
-    }
+    for (int e = 0; e < E; ++e) v[e] = raw[(k0 + e) * kN + c];
+    *reinterpret_cast<uint4 *>(R + swz128((uint32_t)c, (uint32_t)(k0 * kB))) = pack_chunk<OP>(v);
   }
 }
 
@@ -1021,26 +1045,54 @@ __global__ void __launch_bounds__(kT128, 1) fd128_kernel(FusedArgs a) {
   if (tid == 0) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     bulk(R2, a.B1, &bar_b1);
-    bulk(R3, a.B2, &bar_b2);
+    // the pencil kernel stages its input block through R3 first and fetches
+    // the second B image into it after the transpose
+    if (KIND != PENCIL) bulk(R3, a.B2, &bar_b2);
   }
   // everything above (barriers, TMEM, the constant B images) overlaps the
   // previous kernel's tail; its outputs are read only from here on
   pdl_wait();
   pdl_trigger();
-  if (a.done && *a.done != 0.0) {
+  const bool skip = a.done && *a.done != 0.0;
+  if (skip) {
     // skipped (converged): let the image copies land, free TMEM
     if (tid == 0) {
       wait_on(&bar_b1, 0);
-      wait_on(&bar_b2, 0);
+      if (KIND != PENCIL) wait_on(&bar_b2, 0);
     }
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
     return;
   }
   // ---- first A operand ----
-  if (KIND == PENCIL) stage128_cols<OP>(R1, (const float *)a.in + (long long)blk * kN, warp, lane);
-  else if (KIND == SLAB_FWD) stage128_rows_f64<OP>(R1, (const double *)a.in + blk * n12, warp, lane);
-  else stage128_rows_f32<OP>(R1, (const float *)a.in + blk * n12, warp, lane);
+  if (KIND == PENCIL) {
+    // input block j2 = blk of the slab pass's [j2][i3][j1] output: contiguous
+    // 64 KB of FP32 [i3][j1], one bulk copy into R3, transposed into R1
+    constexpr uint32_t kRaw = (uint32_t)(n12 * sizeof(float));
+    if (tid == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar_b2)),
+                   "r"(kRaw)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(R3)),
+          "l"((const float *)a.in + (long long)blk * n12), "r"(kRaw), "r"(smem_u32(&bar_b2))
+          : "memory");
+    }
+    if (!wait_on(&bar_b2, 0)) s_fail = 1;    // every thread waits for the block
+    __syncthreads();
+    if (!s_fail) stage128_cols_smem<OP>(R1, reinterpret_cast<const float *>(R3), warp, lane);
+    __syncthreads();
+    // R3 is free again: the second B image (phase 1 of bar_b2)
+    if (tid == 0 && !s_fail) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk(R3, a.B2, &bar_b2);
+    }
+  } else if (KIND == SLAB_FWD) {
+    stage128_rows_f64<OP>(R1, (const double *)a.in + blk * n12, warp, lane);
+  } else {
+    stage128_rows_f32<OP>(R1, (const float *)a.in + blk * n12, warp, lane);
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if (tid == 0) {
@@ -1081,7 +1133,7 @@ __global__ void __launch_bounds__(kT128, 1) fd128_kernel(FusedArgs a) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if (tid == 0 && !s_fail) {
-    if (!wait_on(&bar_b2, 0)) s_fail = 1;
+    if (!wait_on(&bar_b2, KIND == PENCIL ? 1 : 0)) s_fail = 1;
     else mma(R3, tmem);
   }
   __syncthreads();
@@ -1097,9 +1149,10 @@ __global__ void __launch_bounds__(kT128, 1) fd128_kernel(FusedArgs a) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) o[j * n12] = __uint_as_float(v[j]);
     } else if (KIND == SLAB_FWD) {
-      float *o = (float *)a.out + blk * n12 + lrow + cg * 32 * kN;
+      // [j2][i3][j1]: the pencil kernel's block j2 is then contiguous
+      float *o = (float *)a.out + (long long)blk * kN + lrow + (long long)cg * 32 * n12;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) o[j * kN] = __uint_as_float(v[j]);
+      for (int j = 0; j < 32; ++j) o[j * n12] = __uint_as_float(v[j]);
     } else {
       double *o = (double *)a.out + blk * n12 + lrow + cg * 32 * kN;
 #pragma unroll
@@ -1111,6 +1164,7 @@ __global__ void __launch_bounds__(kT128, 1) fd128_kernel(FusedArgs a) {
     // chance to finish before shared memory and TMEM are released
     wait_on(&bar_b1, 0);
     wait_on(&bar_b2, 0);
+    if (KIND == PENCIL) wait_on(&bar_b2, 1);
     wait_on(&bar_mma, 0);
     wait_on(&bar_mma, 1);
   }
@@ -1250,11 +1304,11 @@ static igafd_status launch_fused(const FusedArgs &a, int grid, cudaStream_t s, i
   return IGAFD_OK;
 }
 
-template <int OP>
-static igafd_status fused_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
-                                double *done) {
+// Arguments and CTA counts of the fused FD's kernels (slab forward, pencil in
+// 3D, slab backward; grid 0 = not launched) for z = P^{-1} r.
+static void fused_args(igafd_patch *P, int op, const double *r, double *z, double *done,
+                       FusedArgs out[3], int grid[3]) {
   FDMixed *F = P->mixed;
-  const int op = OP;
   const int dim = P->dim;
   const int n1 = P->n[0], n2 = P->n[1], n3 = dim == 3 ? P->n[2] : 1;
   int kmax = n1 > n2 ? n1 : n2;
@@ -1276,8 +1330,10 @@ static igafd_status fused_apply(igafd_patch *P, const double *r, double *z, cuda
   a.B2 = F->img[1][0][op]; a.Np2 = np(n2); a.K2 = n2; a.Kp2 = kp(n2);
   a.rowsA = n2;
   a.inv_lam = dim == 2 ? P->inv_lam32 : nullptr;
-  IGAFD_TRY((launch_fused<OP, SLAB_FWD>(a, n3, s, P->dev)));
+  out[0] = a;
+  grid[0] = n3;
   const float *mid = t1;
+  grid[1] = 0;
   if (dim == 3) {
     FusedArgs c = a;
     c.in = t1; c.in_f64 = 0; c.in_aligned = 1;
@@ -1287,7 +1343,8 @@ static igafd_status fused_apply(igafd_patch *P, const double *r, double *z, cuda
     c.rowsA = kM;
     c.inv_lam = nullptr;
     c.d1 = F->d32[0]; c.d2 = F->d32[1]; c.d3 = F->d32[2];
-    IGAFD_TRY((launch_fused<OP, PENCIL>(c, (int)((a.n12 + kM - 1) / kM), s, P->dev)));
+    out[1] = c;
+    grid[1] = (int)((a.n12 + kM - 1) / kM);
     mid = t2;
   }
   FusedArgs b = a;
@@ -1297,13 +1354,27 @@ static igafd_status fused_apply(igafd_patch *P, const double *r, double *z, cuda
   b.B2 = F->img[1][1][op]; b.Np2 = np(n2); b.K2 = n2; b.Kp2 = kp(n2);
   b.rowsA = n2;
   b.inv_lam = nullptr;
-  IGAFD_TRY((launch_fused<OP, SLAB_BWD>(b, n3, s, P->dev)));
+  out[2] = b;
+  grid[2] = n3;
+}
+
+template <int OP>
+static igafd_status fused_apply(igafd_patch *P, const double *r, double *z, cudaStream_t s,
+                                double *done) {
+  FusedArgs a[3];
+  int grid[3];
+  fused_args(P, OP, r, z, done, a, grid);
+  IGAFD_TRY((launch_fused<OP, SLAB_FWD>(a[0], grid[0], s, P->dev)));
+  if (grid[1] > 0) IGAFD_TRY((launch_fused<OP, PENCIL>(a[1], grid[1], s, P->dev)));
+  IGAFD_TRY((launch_fused<OP, SLAB_BWD>(a[2], grid[2], s, P->dev)));
   return IGAFD_OK;
 }
 
 template <int OP, int KIND>
 static igafd_status launch_fd128(const FusedArgs &a, cudaStream_t s, int dev) {
-  const size_t smem = 1024 + 3 * (size_t)kN * kN * (OP == OP_TF32 ? 4 : 2);
+  // R1, R2 (operands) and R3 (second B image; the pencil's FP32 input block first)
+  const size_t tile = (size_t)kN * kN * (OP == OP_TF32 ? 4 : 2);
+  const size_t smem = 1024 + 2 * tile + (KIND == PENCIL ? (size_t)kN * kN * 4 : tile);
   static std::atomic<unsigned long long> attr_set{0};
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_set.load() & bit)) {
@@ -1402,4 +1473,62 @@ igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, 
     }
   }
   return IGAFD_OK;
+}
+
+// ---- batched solve -----------------------------------------------------------
+bool igafd_fd_tc_fused_generic(const igafd_patch *P, igafd_dtype dt) {
+  if (!P->mixed || (dt != IGAFD_TF32 && dt != IGAFD_BF16)) return false;
+  const int op = dt == IGAFD_TF32 ? OP_TF32 : OP_BF16;
+  bool fusable = P->fd_fused && P->fd_fused_op[op];
+  for (int k = 0; k < P->dim; ++k) fusable = fusable && P->n[k] <= 128;
+  const bool n128 = P->dim == 3 && P->n[0] == kN && P->n[1] == kN && P->n[2] == kN;
+  return fusable && !n128;
+}
+
+size_t igafd_fd_fused_args_bytes() { return sizeof(FusedArgs); }
+
+// The fused FD's arguments on the PCG's buffers (z = P^{-1} r, skipped once
+// the PCG is done), CTA counts per kind and the dynamic shared memory.
+igafd_status igafd_fd_fused_batch_args(igafd_patch *P, igafd_dtype dt, void *args3, int *blocks3,
+                                       size_t *smem) {
+  if (!igafd_fd_tc_fused_generic(P, dt)) return IGAFD_ERR_ARG;
+  const int op = dt == IGAFD_TF32 ? OP_TF32 : OP_BF16;
+  FusedArgs a[3];
+  fused_args(P, op, P->r, P->z, P->scal + S_DONE, a, blocks3);
+  memcpy(args3, a, sizeof(a));
+  *smem = 1024 + (size_t)(kM + 128) * a[0].Kpad * (op == OP_TF32 ? 4 : 2);
+  return IGAFD_OK;
+}
+
+template <int OP, int KIND>
+static igafd_status batch_fused(const FusedArgs *args, const int *block_start, int nprob,
+                                int total, size_t smem, cudaStream_t s) {
+  static std::atomic<unsigned long long> attr_set{0};
+  int dev = 0;
+  IGAFD_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_set.load() & bit)) {
+    IGAFD_CUDA(cudaFuncSetAttribute(tc_fused_batch_kernel<OP, KIND>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedMaxSmem));
+    attr_set.fetch_or(bit);
+  }
+  tc_fused_batch_kernel<OP, KIND><<<total, kThreads, smem, s>>>(args, block_start, nprob);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
+  return IGAFD_OK;
+}
+
+igafd_status igafd_fd_fused_batch_launch(igafd_dtype dt, int kind, const void *args_dev,
+                                         const int *block_start_dev, int nprob, int total_blocks,
+                                         size_t smem, cudaStream_t s) {
+  if (total_blocks <= 0) return IGAFD_OK;
+  const FusedArgs *a = (const FusedArgs *)args_dev;
+  if (dt == IGAFD_TF32) {
+    if (kind == 0) return batch_fused<OP_TF32, SLAB_FWD>(a, block_start_dev, nprob, total_blocks, smem, s);
+    if (kind == 1) return batch_fused<OP_TF32, PENCIL>(a, block_start_dev, nprob, total_blocks, smem, s);
+    return batch_fused<OP_TF32, SLAB_BWD>(a, block_start_dev, nprob, total_blocks, smem, s);
+  }
+  if (kind == 0) return batch_fused<OP_BF16, SLAB_FWD>(a, block_start_dev, nprob, total_blocks, smem, s);
+  if (kind == 1) return batch_fused<OP_BF16, PENCIL>(a, block_start_dev, nprob, total_blocks, smem, s);
+  return batch_fused<OP_BF16, SLAB_BWD>(a, block_start_dev, nprob, total_blocks, smem, s);
 }

@@ -11,6 +11,7 @@ namespace igafd_geom {
 // Device-visible view of the patch tables (passed by value to kernels).
 struct PV {
   int dim, p, gp, nq, kp;
+  int ds;                        // first function kept per direction (1: Dirichlet removed, 0: full)
   int n[3], nel[3], gm[3], km[3];
   const int *span[3];
   const double *w[3], *bv[3], *bd[3], *gv[3], *gd[3], *kv[3];
@@ -22,6 +23,7 @@ struct PV {
 inline PV make_view(const igafd_patch *P) {
   PV v{};
   v.dim = P->dim; v.p = P->p; v.gp = P->geo_p; v.nq = P->p + 1; v.kp = P->kappa_p;
+  v.ds = P->dshift;
   for (int k = 0; k < 3; ++k) {
     v.n[k] = P->n[k]; v.nel[k] = P->nel[k]; v.gm[k] = P->dir[k].gm;
     v.span[k] = P->dir[k].span; v.w[k] = P->dir[k].w;

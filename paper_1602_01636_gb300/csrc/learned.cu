@@ -550,6 +550,7 @@ extern "C" igafd_status igafd_patch_sepfit(igafd_patch *P, int sweeps, float *lo
 }
 
 extern "C" igafd_status igafd_set_scalings(igafd_patch *P, const float *logw, void *stream) {
+  if (P && !P->dshift) return IGAFD_ERR_ARG;   // a full-space patch has no preconditioner
   if (!P) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   cudaStream_t s = (cudaStream_t)stream;

@@ -8,6 +8,8 @@
 // subdomain.
 #include "common.cuh"
 
+#include <cmath>
+
 #include <algorithm>
 #include <vector>
 
@@ -179,6 +181,15 @@ struct igafd_mp {
   std::vector<long long *> rows;            // device rows of R_i
   std::vector<long long> len;               // N_i
   double *tr = nullptr, *tz = nullptr;      // subdomain vectors, max N_i each
+  // the operator A (igafd_mp_set_operator): full-space patches and the free
+  // index of each of their local functions (-1: Dirichlet)
+  std::vector<igafd_patch *> ops;
+  std::vector<long long *> omap;
+  double *ox = nullptr, *oy = nullptr;      // gathered patch vectors, max over the patches
+  // PCG workspace: 7 vectors of n, dot slots (device and pinned host), reduction scratch
+  double *w = nullptr;
+  double *dots = nullptr, *hdots = nullptr, *partial = nullptr;
+  unsigned *counter = nullptr;
 };
 
 namespace {
@@ -198,12 +209,92 @@ __global__ void scatter_add_kernel(const double *__restrict__ y, const long long
     z[rows[t]] += y[t];
 }
 
+void free_operator(igafd_mp *M) {
+  for (long long *d : M->omap) cudaFree(d);
+  M->omap.clear();
+  M->ops.clear();
+  cudaFree(M->ox); cudaFree(M->oy); cudaFree(M->w); cudaFree(M->dots); cudaFree(M->partial);
+  cudaFree(M->counter);
+  if (M->hdots) cudaFreeHost(M->hdots);
+  M->ox = M->oy = M->w = M->dots = M->hdots = M->partial = nullptr;
+  M->counter = nullptr;
+}
+
 void free_mp(igafd_mp *M) {
   if (!M) return;
   for (long long *r : M->rows) cudaFree(r);
   cudaFree(M->tr);
   cudaFree(M->tz);
+  free_operator(M);
   delete M;
+}
+
+// y[t] = x[map[t]] (0 where map[t] < 0): a global vector on a patch's full
+// index box, Dirichlet functions zero
+__global__ void gather_full_kernel(const double *__restrict__ x, const long long *__restrict__ map,
+                                   long long n, double *__restrict__ y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long g = map[t];
+    y[t] = g >= 0 ? x[g] : 0.0;
+  }
+}
+
+// z[map[t]] += y[t] where map[t] >= 0 (a patch's functions map to distinct
+// global ones; patches are added one launch after the other, no atomics)
+__global__ void scatter_add_full_kernel(const double *__restrict__ y, const long long *__restrict__ map,
+                                        long long n, double *__restrict__ z) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long g = map[t];
+    if (g >= 0) z[g] += y[t];
+  }
+}
+
+constexpr int kDotBlocks = 296;      // 2 x 148: fixed grid, fixed summation order
+
+// out = (a, b): CTA partial sums, then the last CTA sums them in order
+__global__ void __launch_bounds__(256) mp_dot_kernel(const double *__restrict__ a,
+                                                     const double *__restrict__ b, long long n,
+                                                     double *partial, unsigned *counter, double *out) {
+  double v = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v = fma(a[i], b[i], v);
+  __shared__ double sh32[32];
+  __shared__ bool am_last;
+  const double bs = block_sum(v, sh32);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!am_last) return;
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += ((volatile double *)partial)[i];
+  t = block_sum(t, sh32);
+  if (threadIdx.x == 0) {
+    *out = t;
+    *counter = 0u;
+  }
+}
+
+// y += alpha x (alpha from the host)
+__global__ void mp_axpy_kernel(double alpha, const double *__restrict__ x, double *__restrict__ y,
+                               long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(alpha, x[i], y[i]);
+}
+
+// p = z + beta p
+__global__ void mp_xpby_kernel(const double *__restrict__ z, double beta, double *__restrict__ p,
+                               long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+// r = b - t
+__global__ void mp_sub_kernel(const double *__restrict__ b, const double *__restrict__ t,
+                              double *__restrict__ r, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = b[i] - t[i];
 }
 
 }  // namespace
@@ -282,4 +373,190 @@ extern "C" igafd_status igafd_mp_apply_ias(igafd_mp *M, igafd_dtype dtype, const
     IGAFD_CUDA(cudaGetLastError());
   }
   return IGAFD_OK;
+}
+
+// ---- the multi-patch operator and its PCG ------------------------------------
+extern "C" igafd_status igafd_mp_set_operator(igafd_mp *M, int npatch, igafd_patch *const *patches,
+                                              const long long *const *free_of_local) {
+  if (!M || npatch < 1 || !patches || !free_of_local) return IGAFD_ERR_ARG;
+  for (int q = 0; q < npatch; ++q) {
+    igafd_patch *P = patches[q];
+    if (!P || !free_of_local[q] || P->dev != M->dev || P->dshift != 0 || !P->stencil)
+      return IGAFD_ERR_ARG;                  // full-space patches with a stencil
+    std::vector<unsigned char> seen((size_t)M->n, 0);
+    for (long long t = 0; t < P->N; ++t) {
+      const long long g = free_of_local[q][t];
+      if (g < -1 || g >= M->n || (g >= 0 && seen[(size_t)g])) return IGAFD_ERR_ARG;
+      if (g >= 0) seen[(size_t)g] = 1;
+    }
+  }
+  IGAFD_CUDA(cudaSetDevice(M->dev));
+  free_operator(M);
+  long long nmax = 0;
+  for (int q = 0; q < npatch; ++q) {
+    const long long n = patches[q]->N;
+    long long *d = nullptr;
+    if (cudaMalloc(&d, n * sizeof(long long)) != cudaSuccess) {
+      cudaGetLastError();
+      free_operator(M);
+      return IGAFD_ERR_OOM;
+    }
+    M->omap.push_back(d);
+    if (cudaMemcpy(d, free_of_local[q], n * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_operator(M);
+      return IGAFD_ERR_CUDA;
+    }
+    M->ops.push_back(patches[q]);
+    nmax = std::max(nmax, n);
+  }
+  if (cudaMalloc(&M->ox, nmax * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&M->oy, nmax * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&M->w, 7 * M->n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&M->dots, 8 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&M->partial, kDotBlocks * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&M->counter, sizeof(unsigned)) != cudaSuccess ||
+      cudaHostAlloc((void **)&M->hdots, 8 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    free_operator(M);
+    return IGAFD_ERR_OOM;
+  }
+  IGAFD_CUDA(cudaMemset(M->counter, 0, sizeof(unsigned)));
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_mp_apply_A(igafd_mp *M, const double *x, double *y, void *stream) {
+  if (!M || !x || !y || x == y || M->ops.empty()) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(M->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  IGAFD_CUDA(cudaMemsetAsync(y, 0, M->n * sizeof(double), s));
+  for (size_t q = 0; q < M->ops.size(); ++q) {
+    igafd_patch *P = M->ops[q];
+    const unsigned grid = (unsigned)std::min<long long>((P->N + 255) / 256, 152 * 8);
+    gather_full_kernel<<<grid, 256, 0, s>>>(x, M->omap[q], P->N, M->ox);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+    IGAFD_TRY(igafd_apply_A(P, M->ox, M->oy, s));       // the patch's own stencil (Eq. (A))
+    scatter_add_full_kernel<<<grid, 256, 0, s>>>(M->oy, M->omap[q], P->N, y);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+  }
+  return IGAFD_OK;
+}
+
+namespace {
+
+// (a, b) into dot slot k, read back to the host (synchronises the stream)
+igafd_status mp_dots(igafd_mp *M, cudaStream_t s, int cnt, const double *const *a,
+                     const double *const *b) {
+  for (int k = 0; k < cnt; ++k) {
+    mp_dot_kernel<<<kDotBlocks, 256, 0, s>>>(a[k], b[k], M->n, M->partial, M->counter, M->dots + k);
+    IGAFD_LAUNCHED(1);
+  }
+  IGAFD_CUDA(cudaGetLastError());
+  IGAFD_CUDA(cudaMemcpyAsync(M->hdots, M->dots, cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
+  IGAFD_CUDA(cudaStreamSynchronize(s));
+  return IGAFD_OK;
+}
+
+}  // namespace
+
+extern "C" igafd_status igafd_mp_pcg_solve(igafd_mp *M, const igafd_pcg_opts *opts, const double *b,
+                                           double *x, igafd_pcg_info *info, void *stream) {
+  if (!M || !b || !x || b == x || M->ops.empty()) return IGAFD_ERR_ARG;
+  igafd_pcg_opts o;
+  if (opts) o = *opts; else igafd_pcg_default_opts(&o);
+  if (!(o.tol >= 0.0) || o.max_iter < 0 || o.true_every < 0) return IGAFD_ERR_ARG;
+  if (o.prec_dtype < IGAFD_FP64 || o.prec_dtype > IGAFD_TF32) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(M->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = M->n;
+  const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 152 * 8);
+  double *xs = M->w, *r = M->w + n, *z = M->w + 2 * n, *zn = M->w + 3 * n, *p = M->w + 4 * n,
+         *q = M->w + 5 * n, *t = M->w + 6 * n;
+  const double *h = M->hdots;
+  igafd_pcg_info inf{};
+  inf.status = IGAFD_ERR_NOT_CONVERGED;
+  auto finish = [&](igafd_status st) -> igafd_status {
+    inf.status = st;
+    IGAFD_CUDA(cudaMemcpyAsync(x, xs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    IGAFD_CUDA(cudaStreamSynchronize(s));
+    if (info) *info = inf;
+    return st;
+  };
+  const double *bb_args[1] = {b};
+  IGAFD_TRY(mp_dots(M, s, 1, bb_args, bb_args));
+  const double bb = h[0];
+  if (!(bb >= 0.0) || !std::isfinite(bb)) {
+    IGAFD_CUDA(cudaMemsetAsync(xs, 0, n * sizeof(double), s));
+    return finish(IGAFD_ERR_BREAKDOWN);
+  }
+  if (bb == 0.0) {
+    IGAFD_CUDA(cudaMemsetAsync(xs, 0, n * sizeof(double), s));
+    return finish(IGAFD_OK);
+  }
+  // x0 = 0 or the caller's; r0 = b - A x0; z0 = P_IAS r0; p0 = z0
+  if (o.x0_given) {
+    IGAFD_CUDA(cudaMemcpyAsync(xs, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    IGAFD_TRY(igafd_mp_apply_A(M, xs, t, s));
+    mp_sub_kernel<<<grid, 256, 0, s>>>(b, t, r, n);
+    IGAFD_LAUNCHED(1);
+  } else {
+    IGAFD_CUDA(cudaMemsetAsync(xs, 0, n * sizeof(double), s));
+    IGAFD_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  IGAFD_TRY(igafd_mp_apply_ias(M, o.prec_dtype, r, z, s));
+  IGAFD_CUDA(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  const double *rz_a[1] = {r}, *rz_b[1] = {z};
+  IGAFD_TRY(mp_dots(M, s, 1, rz_a, rz_b));
+  double rho = h[0];
+  const double tol2 = o.tol * o.tol * bb;
+  for (int k = 1; k <= o.max_iter; ++k) {
+    IGAFD_TRY(igafd_mp_apply_A(M, p, q, s));                          // q = A p
+    const double *pq_a[1] = {p}, *pq_b[1] = {q};
+    IGAFD_TRY(mp_dots(M, s, 1, pq_a, pq_b));
+    const double alpha = rho / h[0];
+    if (!(h[0] > 0.0) || !std::isfinite(alpha)) return finish(IGAFD_ERR_BREAKDOWN);
+    mp_axpy_kernel<<<grid, 256, 0, s>>>(alpha, p, xs, n);            // x += alpha p
+    mp_axpy_kernel<<<grid, 256, 0, s>>>(-alpha, q, r, n);            // r -= alpha q
+    IGAFD_LAUNCHED(2);
+    IGAFD_TRY(mp_dots(M, s, 1, rz_a, rz_a));
+    inf.iterations = k;
+    inf.relres = sqrt(h[0] / bb);
+    if (!std::isfinite(h[0])) return finish(IGAFD_ERR_BREAKDOWN);
+    if (h[0] <= tol2) {                                              // confirm by the true residual
+      IGAFD_TRY(igafd_mp_apply_A(M, xs, t, s));
+      mp_sub_kernel<<<grid, 256, 0, s>>>(b, t, t, n);
+      IGAFD_LAUNCHED(1);
+      const double *tt[1] = {t};
+      IGAFD_TRY(mp_dots(M, s, 1, tt, tt));
+      inf.true_relres = sqrt(h[0] / bb);
+      inf.true_checks++;
+      if (h[0] <= tol2) return finish(IGAFD_OK);
+      IGAFD_CUDA(cudaMemcpyAsync(r, t, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else if (o.true_every > 0 && k % o.true_every == 0) {
+      IGAFD_TRY(igafd_mp_apply_A(M, xs, t, s));
+      mp_sub_kernel<<<grid, 256, 0, s>>>(b, t, r, n);
+      IGAFD_LAUNCHED(1);
+      inf.true_checks++;
+    }
+    if (k == o.max_iter) break;
+    IGAFD_TRY(igafd_mp_apply_ias(M, o.prec_dtype, r, zn, s));       // z_new = P_IAS r
+    const double *a2[2] = {r, r}, *b2[2] = {zn, z};
+    IGAFD_TRY(mp_dots(M, s, 2, a2, b2));
+    const double rho_new = h[0];
+    const double beta = o.flexible ? (h[0] - h[1]) / rho : rho_new / rho;
+    if (!(rho_new > 0.0) || !std::isfinite(beta)) return finish(IGAFD_ERR_BREAKDOWN);
+    mp_xpby_kernel<<<grid, 256, 0, s>>>(zn, beta, p, n);             // p = z_new + beta p
+    IGAFD_LAUNCHED(1);
+    std::swap(z, zn);
+    rho = rho_new;
+  }
+  // not converged: the true residual of the last iterate
+  IGAFD_TRY(igafd_mp_apply_A(M, xs, t, s));
+  mp_sub_kernel<<<grid, 256, 0, s>>>(b, t, t, n);
+  IGAFD_LAUNCHED(1);
+  const double *tt[1] = {t};
+  IGAFD_TRY(mp_dots(M, s, 1, tt, tt));
+  inf.true_relres = sqrt(h[0] / bb);
+  return finish(IGAFD_ERR_NOT_CONVERGED);
 }

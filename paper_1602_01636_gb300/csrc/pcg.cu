@@ -21,13 +21,13 @@
 
 namespace {
 
-__device__ __forceinline__ bool last_block(unsigned int *counter) {
+__device__ __forceinline__ bool last_block(unsigned int *counter, unsigned blocks) {
   __shared__ bool am_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned t = atomicAdd(counter, 1u);
-    am_last = (t == gridDim.x - 1);
+    am_last = (t == blocks - 1);
   }
   __syncthreads();
   return am_last;
@@ -39,21 +39,21 @@ __device__ double sum_partials(const double *part, int n, double *sh32) {
   return block_sum(v, sh32);
 }
 
+// The vector kernels below are written per CTA vb of a grid of vg CTAs, so
+// that a single problem's launch (vb = blockIdx.x, vg = gridDim.x) and a
+// batched launch (one work item per (problem, vb)) reduce in the same order.
+
 // x += alpha p, r -= alpha q; partials (r, r) and (r, z_old).
-__global__ void __launch_bounds__(256) update_xr_kernel(double *__restrict__ x, double *__restrict__ r,
-                                                        const double *__restrict__ p,
-                                                        const double *__restrict__ q,
-                                                        const double *__restrict__ z, long long N,
-                                                        double *scal, double *partial,
-                                                        unsigned *counter, int flexible,
-                                                        double *coef) {
-  pdl_wait();
-  pdl_trigger();
-  if (scal[S_DONE] != 0.0) return;
+__device__ __forceinline__ void update_xr_cta(double *__restrict__ x, double *__restrict__ r,
+                                              const double *__restrict__ p,
+                                              const double *__restrict__ q,
+                                              const double *__restrict__ z, long long N,
+                                              double *scal, double *partial, unsigned *counter,
+                                              int flexible, double *coef, long long vb,
+                                              long long vg) {
   const double alpha = scal[S_ALPHA];
   double rr = 0.0, rz = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = vb * (long long)blockDim.x + threadIdx.x; i < N; i += vg * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
     double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
@@ -64,12 +64,12 @@ __global__ void __launch_bounds__(256) update_xr_kernel(double *__restrict__ x, 
   double a = block_sum(rr, sh32);
   double b = flexible ? block_sum(rz, sh32) : 0.0;
   if (threadIdx.x == 0) {
-    partial[blockIdx.x] = a;
-    partial[gridDim.x + blockIdx.x] = b;
+    partial[vb] = a;
+    partial[vg + vb] = b;
   }
-  if (!last_block(counter)) return;
-  double trr = sum_partials(partial, gridDim.x, sh32);
-  double trz = flexible ? sum_partials(partial + gridDim.x, gridDim.x, sh32) : 0.0;
+  if (!last_block(counter, (unsigned)vg)) return;
+  double trr = sum_partials(partial, (int)vg, sh32);
+  double trz = flexible ? sum_partials(partial + vg, (int)vg, sh32) : 0.0;
   if (threadIdx.x == 0) {
     *counter = 0u;
     scal[S_RR] = trr;
@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(256) update_xr_kernel(double *__restrict__ x, 
       scal[S_STATUS] = (double)IGAFD_ERR_BREAKDOWN;
       scal[S_DONE] = 1.0;
     } else if (trr <= scal[S_TOL2] * scal[S_BB]) {
-      scal[S_DONE] = 1.0;   // converged by the recurrence; the host confirms
+      scal[S_DONE] = 1.0;   // converged by the recurrence; the true residual confirms
+      scal[S_REC_RR] = trr;
     } else if (scal[S_ITER] >= scal[S_MAXIT]) {
       scal[S_STATUS] = (double)IGAFD_ERR_NOT_CONVERGED;
       scal[S_DONE] = 1.0;   // iteration cap
@@ -90,23 +91,18 @@ __global__ void __launch_bounds__(256) update_xr_kernel(double *__restrict__ x, 
 }
 
 // (r, z) -> rho (init) or beta and rho (iteration).
-__global__ void __launch_bounds__(256) dot_rz_kernel(const double *__restrict__ r,
-                                                     const double *__restrict__ z, long long N,
-                                                     double *scal, double *partial,
-                                                     unsigned *counter, int init, int flexible,
-                                                     int skip_done, double *coef) {
-  pdl_wait();
-  pdl_trigger();
-  if (skip_done && scal[S_DONE] != 0.0) return;
+__device__ __forceinline__ void dot_rz_cta(const double *__restrict__ r,
+                                           const double *__restrict__ z, long long N, double *scal,
+                                           double *partial, unsigned *counter, int init,
+                                           int flexible, double *coef, long long vb, long long vg) {
   double rz = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x)
+  for (long long i = vb * (long long)blockDim.x + threadIdx.x; i < N; i += vg * blockDim.x)
     rz = fma(r[i], z[i], rz);
   __shared__ double sh32[32];
   double a = block_sum(rz, sh32);
-  if (threadIdx.x == 0) partial[blockIdx.x] = a;
-  if (!last_block(counter)) return;
-  double t = sum_partials(partial, gridDim.x, sh32);
+  if (threadIdx.x == 0) partial[vb] = a;
+  if (!last_block(counter, (unsigned)vg)) return;
+  double t = sum_partials(partial, (int)vg, sh32);
   if (threadIdx.x == 0) {
     *counter = 0u;
     if (!(t > 0.0) || !isfinite(t)) {
@@ -126,16 +122,45 @@ __global__ void __launch_bounds__(256) dot_rz_kernel(const double *__restrict__ 
 }
 
 // p = z + beta p
+__device__ __forceinline__ void update_p_cta(double *__restrict__ p, const double *__restrict__ z,
+                                             long long N, const double *scal, long long vb,
+                                             long long vg) {
+  const double beta = scal[S_BETA];
+  for (long long i = vb * (long long)blockDim.x + threadIdx.x; i < N; i += vg * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void __launch_bounds__(256) update_xr_kernel(double *__restrict__ x, double *__restrict__ r,
+                                                        const double *__restrict__ p,
+                                                        const double *__restrict__ q,
+                                                        const double *__restrict__ z, long long N,
+                                                        double *scal, double *partial,
+                                                        unsigned *counter, int flexible,
+                                                        double *coef) {
+  pdl_wait();
+  pdl_trigger();
+  if (scal[S_DONE] != 0.0) return;
+  update_xr_cta(x, r, p, q, z, N, scal, partial, counter, flexible, coef, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) dot_rz_kernel(const double *__restrict__ r,
+                                                     const double *__restrict__ z, long long N,
+                                                     double *scal, double *partial,
+                                                     unsigned *counter, int init, int flexible,
+                                                     int skip_done, double *coef) {
+  pdl_wait();
+  pdl_trigger();
+  if (skip_done && scal[S_DONE] != 0.0) return;
+  dot_rz_cta(r, z, N, scal, partial, counter, init, flexible, coef, blockIdx.x, gridDim.x);
+}
+
 __global__ void __launch_bounds__(256) update_p_kernel(double *__restrict__ p,
                                                        const double *__restrict__ z, long long N,
                                                        const double *scal, int skip_done) {
   pdl_wait();
   pdl_trigger();
   if (skip_done && scal[S_DONE] != 0.0) return;
-  const double beta = scal[S_BETA];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x)
-    p[i] = fma(beta, p[i], z[i]);
+  update_p_cta(p, z, N, scal, blockIdx.x, gridDim.x);
 }
 
 // (v, v) -> scal[slot]
@@ -151,12 +176,94 @@ __global__ void __launch_bounds__(256) norm2_kernel(const double *__restrict__ v
   __shared__ double sh32[32];
   double a = block_sum(s, sh32);
   if (threadIdx.x == 0) partial[blockIdx.x] = a;
-  if (!last_block(counter)) return;
+  if (!last_block(counter, gridDim.x)) return;
   double t = sum_partials(partial, gridDim.x, sh32);
   if (threadIdx.x == 0) {
     *counter = 0u;
     scal[slot] = t;
   }
+}
+
+// ---- batched solve: kernels over many problems --------------------------------
+struct VecArgs {             // one problem's PCG vectors and reduction state
+  double *x, *r, *p, *q, *z;
+  double *scal, *partial, *coef;
+  unsigned *counter;
+  long long N;
+  int flexible;
+};
+
+// One launch runs a PCG vector step of every unfinished problem: work item
+// (problem i, CTA v of i's own grid), items taken in a fixed stride by a
+// persistent grid. op 0: update_xr, 1: dot_rz of the iteration, 2: update_p.
+__global__ void __launch_bounds__(256) vec_batch_kernel(const VecArgs *args,
+                                                        const long long *item_start, int nprob,
+                                                        int op) {
+  const long long total = item_start[nprob];
+  __shared__ int s_prob;
+  __shared__ VecArgs s_a;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = nprob - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_start[mid] <= it) lo = mid; else hi = mid - 1;
+      }
+      s_prob = lo;
+      s_a = args[lo];
+    }
+    __syncthreads();
+    const VecArgs a = s_a;
+    const long long vb = it - item_start[s_prob], vg = item_start[s_prob + 1] - item_start[s_prob];
+    __syncthreads();                       // s_prob, s_a are rewritten by the next item
+    if (a.scal[S_DONE] != 0.0) continue;   // uniform over the CTA
+    if (op == 0)
+      update_xr_cta(a.x, a.r, a.p, a.q, a.z, a.N, a.scal, a.partial, a.counter, a.flexible, a.coef,
+                    vb, vg);
+    else if (op == 1)
+      dot_rz_cta(a.r, a.z, a.N, a.scal, a.partial, a.counter, 0, a.flexible, a.coef, vb, vg);
+    else
+      update_p_cta(a.p, a.z, a.N, a.scal, vb, vg);
+  }
+}
+
+// After the convergence confirmation (true residual computed for every
+// problem the recurrence called converged): confirmed -> finished; not
+// confirmed at the iteration cap -> finished, not converged; otherwise the
+// iteration continues from the recomputed residual (done flag cleared, as
+// the single solve's restart does). Problems stopped by breakdown or the cap
+// are finished.
+__global__ void batch_decide_kernel(double *const *scal, int nprob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  double *sc = scal[i];
+  if (sc[S_FIN] != 0.0 || sc[S_DONE] == 0.0) return;
+  if (sc[S_STATUS] != 0.0) {
+    sc[S_FIN] = 1.0;
+  } else if (sc[S_TRUE_RR] <= sc[S_TOL2] * sc[S_BB]) {
+    sc[S_FIN] = 1.0;
+  } else if (sc[S_ITER] >= sc[S_MAXIT]) {
+    sc[S_STATUS] = (double)IGAFD_ERR_NOT_CONVERGED;
+    sc[S_FIN] = 1.0;
+  } else {
+    sc[S_DONE] = 0.0;
+  }
+}
+
+// Loop condition of the batched solve: another iteration while any problem is
+// unfinished, bounded by `guard` passes (every problem finishes within its
+// iteration cap plus its confirmation restarts).
+__global__ void batch_cond_kernel(cudaGraphConditionalHandle h, double *const *scal, int nprob,
+                                  unsigned *passes, unsigned guard) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  bool more = false;
+  for (int i = 0; i < nprob && !more; ++i) more = scal[i][S_FIN] == 0.0;
+  const unsigned n = ++*passes;
+  cudaGraphSetConditional(h, (more && n < guard) ? 1u : 0u);
+}
+
+__global__ void batch_reset_kernel(unsigned *passes) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *passes = 0u;
 }
 
 __global__ void init_scalars_kernel(double *scal, double tol2, double maxit) {
@@ -169,6 +276,7 @@ __global__ void init_scalars_kernel(double *scal, double tol2, double maxit) {
     scal[S_TRUE_RR] = -1.0;
     scal[S_TOL2] = tol2;
     scal[S_MAXIT] = maxit;
+    scal[S_FIN] = 0.0;
   }
 }
 
@@ -193,6 +301,7 @@ static igafd_status fd_apply(igafd_patch *P, igafd_dtype dt, const double *r, do
 
 extern "C" igafd_status igafd_apply_prec(igafd_patch *P, igafd_dtype dt, const double *r,
                                          double *z, void *stream) {
+  if (P && !P->dshift) return IGAFD_ERR_ARG;   // a full-space patch has no preconditioner
   if (!P || !r || !z || r == z) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   return fd_apply(P, dt, r, z, (cudaStream_t)stream, nullptr);
@@ -202,6 +311,13 @@ extern "C" igafd_status igafd_apply_A(igafd_patch *P, const double *x, double *y
   if (!P || !x || !y || x == y || !P->stencil) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   return igafd_stencil_launch(P, x, y, nullptr, 0, 0, (cudaStream_t)stream);
+}
+
+// CTAs of the PCG vector kernels: about 1024 elements per CTA (four per
+// thread), at most IGAFD_RED_BLOCKS (the partial-sum slots).
+int igafd_red_blocks(long long N) {
+  const long long b = (N + 1023) / 1024;
+  return (int)(b < 1 ? 1 : b > IGAFD_RED_BLOCKS ? IGAFD_RED_BLOCKS : b);
 }
 
 extern "C" void igafd_pcg_default_opts(igafd_pcg_opts *o) {
@@ -217,6 +333,7 @@ extern "C" void igafd_pcg_default_opts(igafd_pcg_opts *o) {
 }
 
 std::atomic<long long> g_igafd_launches{0};
+thread_local bool g_igafd_plain_launch = false;
 
 extern "C" long long igafd_kernel_launches(void) { return g_igafd_launches.load(); }
 
@@ -233,7 +350,7 @@ static igafd_status read_scalars(igafd_patch *P, cudaStream_t s) {
 // Every kernel returns at once when the device flag S_DONE is set.
 static igafd_status enqueue_iteration(igafd_patch *P, igafd_dtype dt, int flex, int true_every,
                                       cudaStream_t s, bool timed) {
-  const dim3 G(IGAFD_RED_BLOCKS), B(256);
+  const dim3 G(igafd_red_blocks(P->N)), B(256);
   double *scal = P->scal, *done = P->scal + S_DONE;
   const long long N = P->N;
   IGAFD_TRY(igafd_stencil_launch(P, P->pv, P->q, nullptr, 1, 1, s, 0, timed ? P->tstat : nullptr));
@@ -319,10 +436,11 @@ struct SolveState {
   igafd_pcg_info inf;
 };
 
-// Set-up on patch-internal copies of b and x: r0 = b - A x0, z0 = P^{-1} r0,
-// rho0 = (r0, z0), p0 = z0. Synchronises once (to read (b, b)).
-static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, const double *b,
-                                double *x, cudaStream_t s, SolveState &S) {
+// Set-up on patch-internal copies of b and x, first part (no synchronisation):
+// scalars, b and x copied in, (b, b) and r0 = b - A x0 enqueued.
+static igafd_status solve_begin_enqueue(igafd_patch *P, const igafd_pcg_opts *opts, const double *b,
+                                        double *x, cudaStream_t s, SolveState &S) {
+  if (P && !P->dshift) return IGAFD_ERR_ARG;   // a full-space patch has no preconditioner
   if (!P || !b || !x || b == x || !P->stencil) return IGAFD_ERR_ARG;
   igafd_pcg_opts o;
   if (opts) o = *opts; else igafd_pcg_default_opts(&o);
@@ -340,7 +458,7 @@ static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, cons
   S.rec_rr = -1.0;
   S.status = IGAFD_ERR_NOT_CONVERGED;
   const long long N = P->N;
-  const dim3 G(IGAFD_RED_BLOCKS), B(256);
+  const dim3 G(igafd_red_blocks(P->N)), B(256);
   double *scal = P->scal;
   if (S.timing) {
     IGAFD_CUDA(cudaEventRecord(P->ev[IGAFD_NEV - 2], s));
@@ -361,7 +479,17 @@ static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, cons
     IGAFD_CUDA(cudaMemsetAsync(P->xs, 0, N * sizeof(double), s));
     IGAFD_CUDA(cudaMemcpyAsync(P->r, P->bint, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
-  IGAFD_TRY(read_scalars(P, s));
+  return IGAFD_OK;
+}
+
+// Second part, with (b, b) in P->host_scal: z0 = P^{-1} r0, rho0 = (r0, z0),
+// p0 = z0, and (graph) the captured iteration chunk of the single solve.
+static igafd_status solve_begin_finish(igafd_patch *P, cudaStream_t s, SolveState &S, bool graph) {
+  const igafd_pcg_opts &o = S.o;
+  const long long N = P->N;
+  const dim3 G(igafd_red_blocks(P->N)), B(256);
+  double *scal = P->scal;
+  double *x = S.x;
   S.bb = P->host_scal[S_BB];
   if (!(S.bb > 0.0)) {
     // b == 0: x = 0 is the solution; non-finite b: breakdown
@@ -376,14 +504,24 @@ static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, cons
   IGAFD_CUDA(cudaMemcpyAsync(P->pv, P->z, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   IGAFD_CUDA(cudaGetLastError());
   S.finished = o.max_iter == 0;
-  S.graphed = loop_graph(P, o.prec_dtype, S.flex, o.true_every, o.check_every, S.timing ? 1 : 0) ==
-              IGAFD_OK;
+  if (graph)
+    S.graphed = loop_graph(P, o.prec_dtype, S.flex, o.true_every, o.check_every,
+                           S.timing ? 1 : 0) == IGAFD_OK;
   return IGAFD_OK;
+}
+
+// r0 = b - A x0, z0 = P^{-1} r0, rho0 = (r0, z0), p0 = z0. Synchronises once
+// (to read (b, b)).
+static igafd_status solve_begin(igafd_patch *P, const igafd_pcg_opts *opts, const double *b,
+                                double *x, cudaStream_t s, SolveState &S) {
+  IGAFD_TRY(solve_begin_enqueue(P, opts, b, x, s, S));
+  IGAFD_TRY(read_scalars(P, s));
+  return solve_begin_finish(P, s, S, true);
 }
 
 // A chunk of iterations without a graph (fallback), polled like the graph.
 static igafd_status run_chunk_direct(igafd_patch *P, cudaStream_t s, SolveState &S) {
-  const dim3 G(IGAFD_RED_BLOCKS), B(256);
+  const dim3 G(igafd_red_blocks(P->N)), B(256);
   const long long N = P->N;
   double *scal = P->scal;
   cudaEvent_t *ev = P->ev;
@@ -423,7 +561,7 @@ static igafd_status run_chunk_direct(igafd_patch *P, cudaStream_t s, SolveState 
 // After a chunk (its scalars are in P->host_scal): stopping decisions and,
 // when the recurrence says converged, the true-residual confirmation.
 static igafd_status solve_after_chunk(igafd_patch *P, cudaStream_t s, SolveState &S) {
-  const dim3 G(IGAFD_RED_BLOCKS), B(256);
+  const dim3 G(igafd_red_blocks(P->N)), B(256);
   const long long N = P->N;
   double *scal = P->scal;
   S.k += S.o.check_every;
@@ -523,93 +661,336 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
 }
 
 // ---- batched solve -----------------------------------------------------------
-// Every problem keeps its own captured chunk graph; one parent graph holds
-// them as independent child nodes, so a single graph launch advances all
-// unfinished problems concurrently. Problems that have finished are dropped
-// from the parent graph when at least half of its members are done.
-static igafd_status build_parent(igafd_patch *const *ps, const std::vector<int> &active,
-                                 cudaGraphExec_t *exec, long long *nodes) {
-  cudaGraph_t parent = nullptr;
-  IGAFD_CUDA(cudaGraphCreate(&parent, 0));
-  long long n = 0;
-  for (int i : active) {
-    cudaGraphNode_t node;
-    if (cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, ps[i]->loop_graph) != cudaSuccess) {
-      cudaGraphDestroy(parent);
-      cudaGetLastError();
-      return IGAFD_ERR_CUDA;
-    }
-    n += ps[i]->loop_nodes;
-  }
-  cudaError_t e = cudaGraphInstantiate(exec, parent, 0);
-  cudaGraphDestroy(parent);
-  if (e != cudaSuccess) {
+// Many problems advance together, driven on the device: one CUDA graph holds a
+// conditional while-node whose body is one PCG iteration of every unfinished
+// problem, as a few launches over all of them -- the stencil q = A p (one
+// persistent work-queue launch per (dim, p, rows) class), x/r update,
+// periodic true residual, convergence confirmation and its decision, the FD
+// (one launch per fused kind for problems on the generic tensor-core FD,
+// the problem's own FD launches otherwise), (r, z) and p update -- and a
+// kernel that keeps the loop going while any problem is unfinished. Every
+// problem's work items are CTAs of its own single-problem grids, so the
+// iterates are bitwise those of igafd_pcg_solve. The host synchronises once
+// before the loop (to read every (b, b)) and once after it.
+
+struct BatchClass {             // problems whose stencil shares (dim, p, rows)
+  int dim, p, rows;
+  std::vector<int> members;
+  void *args[3];                // StencilArgs per member, for sel 0, 1, 2 (device)
+  long long *start[3];          // item prefix per sel (device)
+};
+
+struct igafd_batch {
+  int count, dev, num_sms;
+  igafd_pcg_opts o;
+  int flex;
+  std::vector<igafd_patch *> ps;
+  std::vector<BatchClass> classes;
+  std::vector<int> other_fd;    // problems whose FD is launched on its own
+  int nfused;
+  void *fused_args[3];          // FusedArgs per fused problem and kind (device)
+  int *fused_start[3];          // CTA prefix per kind (device)
+  int fused_total[3];
+  size_t fused_smem;
+  VecArgs *vec_args;            // per problem (device)
+  long long *vec_start;         // items of the vector kernels (device)
+  long long vec_total;
+  double **scal_ptrs;           // per problem (device)
+  unsigned long long *queue;    // work-queue counter (device)
+  unsigned *passes;             // loop passes (device)
+  std::vector<void *> allocs;
+  cudaStream_t cap;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  long long body_launches;
+};
+
+template <typename T>
+static igafd_status batch_upload(igafd_batch *B, const std::vector<T> &v, T **out) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, (v.empty() ? 1 : v.size()) * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
-    return IGAFD_ERR_CUDA;
+    return IGAFD_ERR_OOM;
   }
-  *nodes = n;
+  B->allocs.push_back(p);
+  if (!v.empty()) IGAFD_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = (T *)p;
   return IGAFD_OK;
+}
+
+// One PCG iteration of every problem (the while-node's body), enqueued on s.
+static igafd_status batch_body(igafd_batch *B, cudaStream_t s, cudaGraphConditionalHandle h) {
+  const int nvb = B->num_sms * 8;
+  auto vec = [&](int op) -> igafd_status {
+    const long long want = B->vec_total < nvb ? B->vec_total : nvb;
+    vec_batch_kernel<<<(unsigned)(want > 0 ? want : 1), 256, 0, s>>>(B->vec_args, B->vec_start,
+                                                                     B->count, op);
+    IGAFD_LAUNCHED(1);
+    IGAFD_CUDA(cudaGetLastError());
+    return IGAFD_OK;
+  };
+  auto stencil = [&](int sel) -> igafd_status {
+    for (BatchClass &c : B->classes)
+      IGAFD_TRY(igafd_stencil_batch_launch(c.dim, c.p, c.rows, sel, c.args[sel], c.start[sel],
+                                           (int)c.members.size(), B->queue, B->num_sms, s));
+    return IGAFD_OK;
+  };
+  IGAFD_TRY(stencil(0));                                    // q = A p, alpha
+  IGAFD_TRY(vec(0));                                        // x, r, (r, r), stopping test
+  if (B->o.true_every > 0) IGAFD_TRY(stencil(1));           // periodic true residual
+  IGAFD_TRY(stencil(2));                                    // confirm a recurrence convergence
+  batch_decide_kernel<<<(B->count + 127) / 128, 128, 0, s>>>(B->scal_ptrs, B->count);
+  IGAFD_LAUNCHED(1);
+  for (int k = 0; k < 3; ++k)                               // z = P^{-1} r (fused FD)
+    IGAFD_TRY(igafd_fd_fused_batch_launch(B->o.prec_dtype, k, B->fused_args[k],
+                                          B->fused_start[k], B->nfused, B->fused_total[k],
+                                          B->fused_smem, s));
+  for (int i : B->other_fd)                                 // z = P^{-1} r (own launches)
+    IGAFD_TRY(fd_apply(B->ps[i], B->o.prec_dtype, B->ps[i]->r, B->ps[i]->z, s,
+                       B->ps[i]->scal + S_DONE));
+  IGAFD_TRY(vec(1));                                        // (r, z), beta
+  IGAFD_TRY(vec(2));                                        // p = z + beta p
+  // bounded: every problem stops at its cap; a failed confirmation costs
+  // one pass without an iteration
+  const unsigned guard = (unsigned)(2 * B->o.max_iter + 16);
+  batch_cond_kernel<<<1, 32, 0, s>>>(h, B->scal_ptrs, B->count, B->passes, guard);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
+  return IGAFD_OK;
+}
+
+extern "C" void igafd_batch_destroy(igafd_batch *B) {
+  if (!B) return;
+  cudaSetDevice(B->dev);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  for (void *p : B->allocs) cudaFree(p);
+  delete B;
+}
+
+extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int count,
+                                           const igafd_pcg_opts *opts, igafd_batch **out) {
+  if (!out) return IGAFD_ERR_ARG;
+  *out = nullptr;
+  if (!patches || count < 1) return IGAFD_ERR_ARG;
+  igafd_pcg_opts o;
+  if (opts) o = *opts; else igafd_pcg_default_opts(&o);
+  if (!(o.tol >= 0.0) || o.max_iter < 0 || o.true_every < 0) return IGAFD_ERR_ARG;
+  if (o.prec_dtype < IGAFD_FP64 || o.prec_dtype > IGAFD_ADI) return IGAFD_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    igafd_patch *P = patches[i];
+    if (!P || !P->stencil || P->dev != patches[0]->dev) return IGAFD_ERR_ARG;
+    if (o.prec_dtype == IGAFD_ADI && !P->adi) return IGAFD_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (patches[j] == P) return IGAFD_ERR_ARG;            // one problem per patch
+  }
+  IGAFD_CUDA(cudaSetDevice(patches[0]->dev));
+  igafd_batch *B = new igafd_batch{};
+  B->count = count;
+  B->dev = patches[0]->dev;
+  B->num_sms = patches[0]->num_sms;
+  o.timing = 0;
+  o.check_every = 1;            // the loop runs on the device; nothing is polled
+  B->o = o;
+  B->flex = o.flexible ? 1 : 0;
+  B->ps.assign(patches, patches + count);
+  igafd_status st = IGAFD_OK;
+  auto fail = [&](igafd_status e) {
+    igafd_batch_destroy(B);
+    return e;
+  };
+  // stencil classes and their work items
+  const size_t sab = igafd_stencil_args_bytes();
+  for (int i = 0; i < count; ++i) {
+    igafd_patch *P = B->ps[i];
+    const int rows = P->dim == 3 && P->stencil_rows == 2 ? 2 : 1;
+    BatchClass *c = nullptr;
+    for (BatchClass &q : B->classes)
+      if (q.dim == P->dim && q.p == P->p && q.rows == rows) c = &q;
+    if (!c) {
+      B->classes.push_back(BatchClass{});
+      c = &B->classes.back();
+      c->dim = P->dim; c->p = P->p; c->rows = rows;
+    }
+    c->members.push_back(i);
+  }
+  for (BatchClass &c : B->classes) {
+    for (int sel = 0; sel < 3; ++sel) {
+      std::vector<unsigned char> args(sab * c.members.size());
+      std::vector<long long> start(c.members.size() + 1, 0);
+      for (size_t m = 0; m < c.members.size(); ++m) {
+        long long vg = 0;
+        st = igafd_stencil_batch_args(B->ps[c.members[m]], sel, B->flex, o.true_every,
+                                      args.data() + m * sab, &vg);
+        if (st != IGAFD_OK) return fail(st);
+        start[m + 1] = start[m] + vg;
+      }
+      unsigned char *ad = nullptr;
+      if ((st = batch_upload(B, args, &ad)) != IGAFD_OK) return fail(st);
+      c.args[sel] = ad;
+      if ((st = batch_upload(B, start, &c.start[sel])) != IGAFD_OK) return fail(st);
+    }
+  }
+  // FD: problems on the generic fused tensor-core kernels run batched
+  const size_t fab = igafd_fd_fused_args_bytes();
+  std::vector<unsigned char> fargs[3];
+  std::vector<int> fstart[3];
+  for (int k = 0; k < 3; ++k) fstart[k].push_back(0);
+  B->nfused = 0;
+  B->fused_smem = 0;
+  for (int i = 0; i < count; ++i) {
+    igafd_patch *P = B->ps[i];
+    if (!igafd_fd_tc_fused_generic(P, o.prec_dtype)) {
+      B->other_fd.push_back(i);
+      continue;
+    }
+    std::vector<unsigned char> a3(3 * fab);
+    int blocks[3];
+    size_t smem = 0;
+    if ((st = igafd_fd_fused_batch_args(P, o.prec_dtype, a3.data(), blocks, &smem)) != IGAFD_OK)
+      return fail(st);
+    for (int k = 0; k < 3; ++k) {
+      fargs[k].insert(fargs[k].end(), a3.begin() + k * fab, a3.begin() + (k + 1) * fab);
+      fstart[k].push_back(fstart[k].back() + blocks[k]);
+    }
+    if (smem > B->fused_smem) B->fused_smem = smem;
+    ++B->nfused;
+  }
+  for (int k = 0; k < 3; ++k) {
+    unsigned char *ad = nullptr;
+    if ((st = batch_upload(B, fargs[k], &ad)) != IGAFD_OK) return fail(st);
+    B->fused_args[k] = ad;
+    if ((st = batch_upload(B, fstart[k], &B->fused_start[k])) != IGAFD_OK) return fail(st);
+    B->fused_total[k] = B->nfused > 0 ? fstart[k].back() : 0;
+  }
+  // vector kernels, scalars, queue, pass counter
+  std::vector<VecArgs> va(count);
+  std::vector<long long> vs(count + 1, 0);
+  std::vector<double *> sp(count);
+  for (int i = 0; i < count; ++i) {
+    igafd_patch *P = B->ps[i];
+    va[i] = VecArgs{P->xs, P->r, P->pv, P->q, P->z, P->scal, P->partial, P->coef, P->counter,
+                    P->N, B->flex};
+    vs[i + 1] = vs[i] + igafd_red_blocks(P->N);
+    sp[i] = P->scal;
+  }
+  B->vec_total = vs[count];
+  if ((st = batch_upload(B, va, &B->vec_args)) != IGAFD_OK) return fail(st);
+  if ((st = batch_upload(B, vs, &B->vec_start)) != IGAFD_OK) return fail(st);
+  if ((st = batch_upload(B, sp, &B->scal_ptrs)) != IGAFD_OK) return fail(st);
+  std::vector<unsigned long long> q1(1, 0);
+  if ((st = batch_upload(B, q1, &B->queue)) != IGAFD_OK) return fail(st);
+  std::vector<unsigned> p1(1, 0);
+  if ((st = batch_upload(B, p1, &B->passes)) != IGAFD_OK) return fail(st);
+  // the graph: reset the pass counter, then while (any unfinished) { body }
+  if (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(IGAFD_ERR_CUDA);
+  if (cudaGraphCreate(&B->graph, 0) != cudaSuccess) return fail(IGAFD_ERR_CUDA);
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, B->graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail(IGAFD_ERR_CUDA);
+  cudaGraphNode_t reset_node, while_node;
+  {
+    cudaKernelNodeParams kp = {};
+    void *kargs[1] = {&B->passes};
+    kp.func = (void *)batch_reset_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = kargs;
+    if (cudaGraphAddKernelNode(&reset_node, B->graph, nullptr, 0, &kp) != cudaSuccess)
+      return fail(IGAFD_ERR_CUDA);
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (cudaGraphAddNode(&while_node, B->graph, &reset_node, nullptr, 1, &cp) != cudaSuccess)
+    return fail(IGAFD_ERR_CUDA);
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(B->cap, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(IGAFD_ERR_CUDA);
+  const long long l0 = g_igafd_launches.load();
+  g_igafd_plain_launch = true;
+  st = batch_body(B, B->cap, h);
+  g_igafd_plain_launch = false;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(B->cap, &captured);
+  B->body_launches = g_igafd_launches.load() - l0;
+  g_igafd_launches.fetch_sub(B->body_launches);              // captured, not executed
+  if (st != IGAFD_OK || e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(st != IGAFD_OK ? st : IGAFD_ERR_CUDA);
+  }
+  if (cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IGAFD_ERR_CUDA);
+  }
+  *out = B;
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_batch_solve(igafd_batch *B, const double *const *b,
+                                          double *const *x, igafd_pcg_info *infos, void *stream) {
+  if (!B || !b || !x) return IGAFD_ERR_ARG;
+  for (int i = 0; i < B->count; ++i)
+    if (!b[i] || !x[i] || b[i] == x[i]) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(B->dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = B->count;
+  std::vector<SolveState> S(n);
+  for (int i = 0; i < n; ++i) IGAFD_TRY(solve_begin_enqueue(B->ps[i], &B->o, b[i], x[i], s, S[i]));
+  for (int i = 0; i < n; ++i)
+    IGAFD_CUDA(cudaMemcpyAsync(B->ps[i]->host_scal, B->ps[i]->scal, S_COUNT * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+  IGAFD_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) {
+    igafd_patch *P = B->ps[i];
+    IGAFD_TRY(solve_begin_finish(P, s, S[i], false));
+    if (S[i].finished) {                 // b == 0, non-finite b or no iterations
+      set_scalar_kernel<<<1, 32, 0, s>>>(P->scal, S_DONE, 1.0);
+      set_scalar_kernel<<<1, 32, 0, s>>>(P->scal, S_FIN, 1.0);
+      IGAFD_LAUNCHED(2);
+    }
+  }
+  IGAFD_CUDA(cudaGraphLaunch(B->exec, s));
+  for (int i = 0; i < n; ++i)
+    IGAFD_CUDA(cudaMemcpyAsync(B->ps[i]->host_scal, B->ps[i]->scal, S_COUNT * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+  IGAFD_CUDA(cudaStreamSynchronize(s));
+  unsigned passes = 0;
+  IGAFD_CUDA(cudaMemcpy(&passes, B->passes, sizeof(passes), cudaMemcpyDeviceToHost));
+  IGAFD_LAUNCHED((long long)passes * B->body_launches);
+  igafd_status worst = IGAFD_OK;
+  for (int i = 0; i < n; ++i) {
+    igafd_patch *P = B->ps[i];
+    const double *h = P->host_scal;
+    if (S[i].bb > 0.0 && !S[i].finished) {
+      const bool fin = h[S_FIN] != 0.0;
+      S[i].status = !fin ? IGAFD_ERR_TIMEOUT
+                         : h[S_STATUS] != 0.0 ? (igafd_status)(int)h[S_STATUS] : IGAFD_OK;
+      S[i].rec_rr = h[S_REC_RR];
+    } else if (S[i].bb > 0.0 && S[i].o.max_iter == 0) {
+      S[i].status = IGAFD_ERR_NOT_CONVERGED;
+    }
+    const igafd_status e = solve_end(P, s, S[i]);
+    if (infos) infos[i] = S[i].inf;
+    if (e != IGAFD_OK && worst == IGAFD_OK) worst = e;
+  }
+  return worst;
 }
 
 extern "C" igafd_status igafd_batch_pcg_solve(igafd_patch *const *patches, int count,
                                               const double *const *b, double *const *x,
                                               const igafd_pcg_opts *opts, igafd_pcg_info *infos,
                                               void *stream) {
-  if (!patches || count < 1 || !b || !x) return IGAFD_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  igafd_pcg_opts o;
-  if (opts) o = *opts; else igafd_pcg_default_opts(&o);
-  o.timing = 0;   // per-problem timing is not available inside the batch graph
-  for (int i = 0; i < count; ++i) {
-    if (!patches[i]) return IGAFD_ERR_ARG;
-    for (int j = 0; j < i; ++j)
-      if (patches[j] == patches[i]) return IGAFD_ERR_ARG;   // one problem per patch
-    if (patches[i]->dev != patches[0]->dev) return IGAFD_ERR_ARG;
-  }
-  std::vector<SolveState> S(count);
-  std::vector<int> active;
-  for (int i = 0; i < count; ++i) {
-    IGAFD_TRY(solve_begin(patches[i], &o, b[i], x[i], s, S[i]));
-    if (!S[i].finished) {
-      if (!S[i].graphed) return IGAFD_ERR_CUDA;
-      active.push_back(i);
-    }
-  }
-  cudaGraphExec_t exec = nullptr;
-  long long nodes = 0;
-  size_t built_for = 0;
-  igafd_status st = IGAFD_OK;
-  while (!active.empty() && st == IGAFD_OK) {
-    if (!exec || active.size() * 2 <= built_for) {
-      if (exec) cudaGraphExecDestroy(exec);
-      exec = nullptr;
-      st = build_parent(patches, active, &exec, &nodes);
-      if (st != IGAFD_OK) break;
-      built_for = active.size();
-    }
-    if (cudaGraphLaunch(exec, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
-      st = IGAFD_ERR_CUDA;
-      break;
-    }
-    IGAFD_LAUNCHED(nodes);
-    std::vector<int> still;
-    for (int i : active) {
-      // problems already finished but still in the parent graph only ran no-op kernels
-      st = solve_after_chunk(patches[i], s, S[i]);
-      if (st != IGAFD_OK) break;
-      if (!S[i].finished) still.push_back(i);
-    }
-    active.swap(still);
-  }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (st != IGAFD_OK) return st;
-  igafd_status worst = IGAFD_OK;
-  for (int i = 0; i < count; ++i) {
-    const igafd_status e = solve_end(patches[i], s, S[i]);
-    if (infos) infos[i] = S[i].inf;
-    if (e != IGAFD_OK && worst == IGAFD_OK) worst = e;
-  }
-  return worst;
+  if (!b || !x) return IGAFD_ERR_ARG;
+  igafd_batch *B = nullptr;
+  IGAFD_TRY(igafd_batch_create(patches, count, opts, &B));
+  const igafd_status st = igafd_batch_solve(B, b, x, infos, stream);
+  igafd_batch_destroy(B);
+  return st;
 }
 
 // ---- condition estimate from the CG-Lanczos relation (host arithmetic) ----

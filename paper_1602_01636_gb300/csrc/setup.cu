@@ -256,13 +256,14 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
       ok = ok && b[k] >= 0 && b[k] < A;
     }
     if (!ok) continue;
-    // global Dirichlet indices: full index I = span - p + a, reduced i = I - 1
+    // global indices: full index I = span - p + a, kept i = I - ds (ds = 1:
+    // Dirichlet functions removed, 0: the full space)
     long long row = 0, stride = 1;
     for (int k = 0; k < DIM; ++k) {
       int I = v.span[k][e[k]] - p + a[k];
       int J = I + dl[k];
-      if (I < 1 || I > v.n[k] || J < 1 || J > v.n[k]) { ok = false; break; }
-      row += (long long)(I - 1) * stride;
+      if (I < v.ds || I >= v.ds + v.n[k] || J < v.ds || J >= v.ds + v.n[k]) { ok = false; break; }
+      row += (long long)(I - v.ds) * stride;
       stride *= v.n[k];
     }
     if (!ok) continue;
@@ -338,8 +339,8 @@ __global__ void rhs_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2, const
     bool ok = true;
     for (int k = 0; k < DIM; ++k) {
       int I = v.span[k][e[k]] - p + a[k];
-      if (I < 1 || I > v.n[k]) { ok = false; break; }
-      row += (long long)(I - 1) * stride;
+      if (I < v.ds || I >= v.ds + v.n[k]) { ok = false; break; }
+      row += (long long)(I - v.ds) * stride;
       stride *= v.n[k];
     }
     if (!ok) continue;
@@ -406,7 +407,7 @@ igafd_status igafd_setup_tables(igafd_patch *P, const igafd_patch_desc *d, cudaS
     for (int i = p; i < nk - p - 1; ++i)
       if (kn[i] < kn[i + 1]) spans.push_back(i);
     D.m = nk - p - 1;
-    D.n = D.m - 2;
+    D.n = D.m - 2 * P->dshift;
     D.nel = (int)spans.size();
     D.gm = d->geo_n_knots[k] - gp - 1;
     ctrl_count *= D.gm;

@@ -20,6 +20,7 @@
 #include "common.cuh"
 
 #include <atomic>
+#include <cstring>
 
 namespace {
 
@@ -71,13 +72,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 
 // Last block of a grid-stride reduction: returns true in every thread of the
 // block that finished last (all partials visible).
-__device__ __forceinline__ bool last_block(unsigned int *counter) {
+__device__ __forceinline__ bool last_block(unsigned int *counter, unsigned blocks) {
   __shared__ bool am_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned t = atomicAdd(counter, 1u);
-    am_last = (t == gridDim.x - 1);
+    am_last = (t == blocks - 1);
   }
   __syncthreads();
   return am_last;
@@ -134,39 +135,26 @@ struct Geom {
 // MODE 1: y = b - A x, dot (y, y) -> true (r, r) when pcg; with z given also
 // (y, z) -> (r, z_old) of the flexible beta, so that a recomputed residual
 // replaces the recurrence one in every scalar that uses it.
+// One CTA's share of the product, as CTA vb of a grid of vgrid CTAs: tiles
+// vb, vb + vgrid, ..., the fused dot, and (in the CTA that finishes last) the
+// dot's fixed-order sum over the vgrid partial sums. The ring's barriers are
+// initialised by the caller; gstage counts the ring stages this CTA has
+// passed through so far, so a persistent CTA can keep its ring across calls.
 template <int DIM, int P, int MODE, int kStages, int R>
-__global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  if (a.done && *a.done != 0.0) return;
-  if (a.every > 0 && ((long long)a.scal[S_ITER]) % a.every != 0) return;
-  if (a.tstat && threadIdx.x == 0) atomicMin(&a.tstat[0], global_ns());
+__device__ __forceinline__ void stencil_cta(const StencilArgs &a, long long vb, long long vgrid,
+                                            double *ring, uint64_t *full, uint64_t *empty,
+                                            long long &gstage, volatile int *s_abort) {
   using Gm = Geom<P>;
   constexpr int W = Gm::W;
   constexpr int G = DIM == 3 ? W * W : W;        // (delta_2, delta_3) groups per tile
   constexpr uint32_t kStageBytes = Gm::STAGE * sizeof(double);
   constexpr int kCompute = kTile / R;            // compute threads
   static_assert(R == 1 || R == 2, "one or two rows per thread");
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  double *ring = reinterpret_cast<double *>(smem_raw);              // [kStages][STAGE]
-  uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * Gm::STAGE);
-  uint64_t *empty = full + kStages;
-  __shared__ volatile int s_abort;
-
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long my_tiles =
-      a.ntiles > blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long my_tiles = a.ntiles > vb ? (a.ntiles - 1 - vb) / vgrid + 1 : 0;
   const long long total = my_tiles * G;
   const long long n12 = (long long)a.n1 * a.n2;
-  if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kCompute / 32);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = 0;
-  }
-  __syncthreads();
+  const long long g0 = gstage;                   // global index of this call's first stage
 
   double dot = 0.0, dot2 = 0.0;
   if (warp == kCompute / 32) {
@@ -175,16 +163,17 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
       long long issued = 0;
       bool ok = true;
       for (long long s = 0; s < total && ok; ++s) {
-        const int slot = (int)(s % kStages);
-        if (s >= kStages) {
-          const uint32_t par = (uint32_t)(((s / kStages) - 1) & 1);
+        const long long gs = g0 + s;
+        const int slot = (int)(gs % kStages);
+        if (gs >= kStages) {
+          const uint32_t par = (uint32_t)(((gs / kStages) - 1) & 1);
           long long it = 0;
           while (!mbar_try_wait(&empty[slot], par)) {
-            if (s_abort || ++it > kSpin) { ok = false; break; }
+            if (*s_abort || ++it > kSpin) { ok = false; break; }
           }
           if (!ok) break;
         }
-        const long long tile = blockIdx.x + (s / G) * (long long)gridDim.x;
+        const long long tile = vb + (s / G) * vgrid;
         const int g = (int)(s % G);
         const int d2 = g % W - P, d3 = DIM == 3 ? g / W - P : 0;
         const int ob = (DIM == 3 ? (d3 + P) * W * W : 0) + (d2 + P) * W;
@@ -201,12 +190,12 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
         ++issued;
       }
       if (!ok) {
-        s_abort = 1;
+        *s_abort = 1;
         atomicExch(a.err, (int)IGAFD_ERR_TIMEOUT);
       }
       // never leave with copies in flight: wait (bounded) for the last stages issued
       for (long long q = issued - kStages > 0 ? issued - kStages : 0; q < issued; ++q)
-        mbar_wait(&full[q % kStages], (uint32_t)((q / kStages) & 1));
+        mbar_wait(&full[(g0 + q) % kStages], (uint32_t)(((g0 + q) / kStages) & 1));
     }
   } else {
     // ---------------- compute warps ----------------
@@ -221,7 +210,7 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
     for (long long s = 0; s < total; ++s) {
       const int g = (int)(s % G);
       if (g == 0) {
-        const long long tile = blockIdx.x + (s / G) * (long long)gridDim.x;
+        const long long tile = vb + (s / G) * vgrid;
         row = tile * kTile + (long long)R * tid;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -231,15 +220,16 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
           acc[r] = 0.0;
         }
       }
-      const int slot = (int)(s % kStages);
-      const uint32_t par = (uint32_t)((s / kStages) & 1);
+      const long long gs = g0 + s;
+      const int slot = (int)(gs % kStages);
+      const uint32_t par = (uint32_t)((gs / kStages) & 1);
       long long it = 0;
       bool ok = true;
       while (!mbar_try_wait(&full[slot], par)) {
-        if (s_abort || ++it > kSpin) { ok = false; break; }
+        if (*s_abort || ++it > kSpin) { ok = false; break; }
       }
       if (!ok) {
-        s_abort = 1;
+        *s_abort = 1;
         atomicExch(a.err, (int)IGAFD_ERR_TIMEOUT);
         break;
       }
@@ -309,8 +299,9 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
       }
     }
   }
+  gstage = g0 + total;
   __syncthreads();
-  if (s_abort) {
+  if (*s_abort) {
     if (tid == 0 && a.pcg) {
       a.scal[S_STATUS] = (double)IGAFD_ERR_TIMEOUT;
       a.scal[S_DONE] = 1.0;
@@ -322,12 +313,12 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
   const double bs = block_sum(dot, sh32);
   const double bs2 = (MODE == 1 && a.z) ? block_sum(dot2, sh32) : 0.0;
   if (tid == 0) {
-    a.partial[blockIdx.x] = bs;
-    if (MODE == 1 && a.z) a.partial[gridDim.x + blockIdx.x] = bs2;
+    a.partial[vb] = bs;
+    if (MODE == 1 && a.z) a.partial[vgrid + vb] = bs2;
   }
-  if (!last_block(a.counter)) return;
-  const double tot = sum_partials(a.partial, gridDim.x, sh32);
-  const double tot2 = (MODE == 1 && a.z) ? sum_partials(a.partial + gridDim.x, gridDim.x, sh32) : 0.0;
+  if (!last_block(a.counter, (unsigned)vgrid)) return;
+  const double tot = sum_partials(a.partial, (int)vgrid, sh32);
+  const double tot2 = (MODE == 1 && a.z) ? sum_partials(a.partial + vgrid, (int)vgrid, sh32) : 0.0;
   if (tid == 0) {
     *a.counter = 0u;
     if (a.tstat) {   // this block finished last: launch duration = now - first start
@@ -354,29 +345,155 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
   }
 }
 
+// Initialise the ring's full/empty barriers of a CTA (thread 0; the caller syncs).
+template <int kStages, int kCompute>
+__device__ __forceinline__ void ring_init(uint64_t *full, uint64_t *empty) {
+  for (int s = 0; s < kStages; ++s) {
+    mbar_init(&full[s], 1);
+    mbar_init(&empty[s], kCompute / 32);
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Warp-specialised pipeline: the compute warps take R consecutive rows per
+// thread (R = 1: warps 0..7, one row each; R = 2: warps 0..3, two rows each,
+// reading both rows' coefficients and the shared x values with 16-byte
+// shared-memory loads, which halves the load instructions per FMA); the next
+// warp (one elected lane) streams, for every (delta_2, delta_3) group, the
+// 2p+1 coefficient runs of the tile and the x window they multiply into a
+// ring of kStages shared-memory stages (full/empty mbarriers). The FP64 FMAs
+// read both operands from shared memory.
+//
+// MODE 0: y = A x, dot (x, y) -> alpha = rho / (x, y) when pcg.
+// MODE 1: y = b - A x, dot (y, y) -> true (r, r) when pcg; with z given also
+// (y, z) -> (r, z_old) of the flexible beta, so that a recomputed residual
+// replaces the recurrence one in every scalar that uses it.
 template <int DIM, int P, int MODE, int kStages, int R>
-igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, cudaStream_t s) {
-  const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
-  constexpr int kBlock = kTile / R + 32;
-  auto kern = stencil_tma_kernel<DIM, P, MODE, kStages, R>;
-  // the shared-memory limit is a per-device attribute of the kernel: set (and
-  // the resident CTAs per SM measured) once per device
-  static std::atomic<unsigned long long> attr_set{0};
-  static std::atomic<int> per_sm_of[64];
+__global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  if (a.done && *a.done != 0.0) return;
+  if (a.every > 0 && ((long long)a.scal[S_ITER]) % a.every != 0) return;
+  if (a.tstat && threadIdx.x == 0) atomicMin(&a.tstat[0], global_ns());
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double *ring = reinterpret_cast<double *>(smem_raw);              // [kStages][STAGE]
+  uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * Geom<P>::STAGE);
+  uint64_t *empty = full + kStages;
+  __shared__ volatile int s_abort;
+  if (threadIdx.x == 0) {
+    ring_init<kStages, kTile / R>(full, empty);
+    s_abort = 0;
+  }
+  __syncthreads();
+  long long gstage = 0;
+  stencil_cta<DIM, P, MODE, kStages, R>(a, blockIdx.x, gridDim.x, ring, full, empty, gstage, &s_abort);
+}
+
+// Many problems in one persistent launch: every CTA takes work items
+// (problem i, virtual CTA v) from an atomic queue, in order, and runs CTA v of
+// problem i's own single-problem grid (vgrid_i CTAs) -- the same tiles, the
+// same fused dot and the same last-CTA sum -- so each problem's result is
+// bitwise that of its own launch. item_start[i] .. item_start[i + 1] are
+// problem i's items. sel: 0 = q = A p of the PCG iteration (problems not yet
+// done), 1 = the periodic true residual (running problems whose iteration
+// count is a multiple of args.every), 2 = the convergence confirmation
+// (problems the recurrence says converged, status ok, not yet finished).
+// The ring's barriers persist across items (one running stage count).
+template <int DIM, int P, int MODE, int kStages, int R>
+__global__ void __launch_bounds__(kTile / R + 32) stencil_batch_kernel(const StencilArgs *args,
+                                                                      const long long *item_start,
+                                                                      int nprob, int sel,
+                                                                      unsigned long long *queue) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double *ring = reinterpret_cast<double *>(smem_raw);
+  uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * Geom<P>::STAGE);
+  uint64_t *empty = full + kStages;
+  __shared__ volatile int s_abort;
+  __shared__ long long s_item;
+  __shared__ int s_prob, s_run;
+  __shared__ StencilArgs s_args;
+  const long long total = item_start[nprob];
+  if (threadIdx.x == 0) {
+    ring_init<kStages, kTile / R>(full, empty);
+    s_abort = 0;
+  }
+  __syncthreads();
+  long long gstage = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(queue, 1ull);
+      s_item = it;
+      if (it < total) {
+        int lo = 0, hi = nprob - 1;             // last problem with item_start <= it
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (item_start[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        s_prob = lo;
+        const double *sc = args[lo].scal;
+        const bool done = sc[S_DONE] != 0.0;
+        bool run;
+        if (sel == 0) run = !done;
+        else if (sel == 1) run = !done && args[lo].every > 0 &&
+                                 ((long long)sc[S_ITER]) % args[lo].every == 0;
+        else run = done && sc[S_STATUS] == 0.0 && sc[S_FIN] == 0.0;
+        s_run = run ? 1 : 0;
+        if (run) s_args = args[lo];
+      }
+    }
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= total) break;
+    if (s_run) {
+      const int i = s_prob;
+      stencil_cta<DIM, P, MODE, kStages, R>(s_args, it - item_start[i],
+                                            item_start[i + 1] - item_start[i], ring, full, empty,
+                                            gstage, &s_abort);
+    }
+    __syncthreads();
+    if (s_abort) break;
+  }
+}
+
+// Resident CTAs per SM of a kernel with `smem` bytes of dynamic shared
+// memory: the attribute and the occupancy are per device, set and measured
+// once per device.
+template <typename Kern>
+igafd_status per_sm_of(Kern kern, int block, size_t smem, std::atomic<unsigned long long> &set,
+                       std::atomic<int> *per_sm, int *out) {
   int dev = 0;
   IGAFD_CUDA(cudaGetDevice(&dev));
   const unsigned long long bit = 1ull << (dev & 63);
-  if (!(attr_set.load() & bit)) {
+  if (!(set.load() & bit)) {
     IGAFD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb = 0;
-    IGAFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBlock, smem));
-    per_sm_of[dev & 63].store(nb > 0 ? nb : 1);
-    attr_set.fetch_or(bit);
+    IGAFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, block, smem));
+    per_sm[dev & 63].store(nb > 0 ? nb : 1);
+    set.fetch_or(bit);
   }
-  const int per_sm = per_sm_of[dev & 63].load();
+  *out = per_sm[dev & 63].load();
+  return IGAFD_OK;
+}
+
+// One launch of the single-problem kernel, or with grid_out only its grid
+// (the resident CTAs of every SM, at most grid_cap).
+template <int DIM, int P, int MODE, int kStages, int R>
+igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, cudaStream_t s,
+                        long long *grid_out) {
+  const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
+  constexpr int kBlock = kTile / R + 32;
+  auto kern = stencil_tma_kernel<DIM, P, MODE, kStages, R>;
+  static std::atomic<unsigned long long> attr_set{0};
+  static std::atomic<int> per_sm_tab[64];
+  int per_sm = 1;
+  IGAFD_TRY(per_sm_of(kern, kBlock, smem, attr_set, per_sm_tab, &per_sm));
   long long grid = (long long)num_sms * per_sm;
   if (grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
+  if (grid_out) {
+    *grid_out = grid;
+    return IGAFD_OK;
+  }
   IGAFD_CUDA(igafd_launch(kern, dim3((unsigned)grid), dim3(kBlock), smem, s, a));
   IGAFD_LAUNCHED(1);
   return IGAFD_OK;
@@ -384,35 +501,77 @@ igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, c
 
 // two rows per thread are built for 3D only (2D patches are small)
 template <int DIM, int P, int MODE, int kStages>
-igafd_status launch_rows(int rows, const StencilArgs &a, long long cap, int sms, cudaStream_t s) {
+igafd_status launch_rows(int rows, const StencilArgs &a, long long cap, int sms, cudaStream_t s,
+                         long long *grid_out) {
   if constexpr (DIM == 3)
-    if (rows == 2) return launch_one<DIM, P, MODE, kStages, 2>(a, cap, sms, s);
-  return launch_one<DIM, P, MODE, kStages, 1>(a, cap, sms, s);
+    if (rows == 2) return launch_one<DIM, P, MODE, kStages, 2>(a, cap, sms, s, grid_out);
+  return launch_one<DIM, P, MODE, kStages, 1>(a, cap, sms, s, grid_out);
 }
 
 template <int DIM, int P, int MODE>
 igafd_status launch_stages(int stages, int rows, const StencilArgs &a, long long cap, int sms,
-                           cudaStream_t s) {
+                           cudaStream_t s, long long *grid_out) {
   switch (stages) {
-    case 3: return launch_rows<DIM, P, MODE, 3>(rows, a, cap, sms, s);
-    case 6: return launch_rows<DIM, P, MODE, 6>(rows, a, cap, sms, s);
-    default: return launch_rows<DIM, P, MODE, 4>(rows, a, cap, sms, s);
+    case 3: return launch_rows<DIM, P, MODE, 3>(rows, a, cap, sms, s, grid_out);
+    case 6: return launch_rows<DIM, P, MODE, 6>(rows, a, cap, sms, s, grid_out);
+    default: return launch_rows<DIM, P, MODE, 4>(rows, a, cap, sms, s, grid_out);
   }
 }
 
 template <int DIM, int MODE>
 igafd_status launch_p(int p, int stages, int rows, const StencilArgs &a, long long cap, int sms,
-                      cudaStream_t s) {
+                      cudaStream_t s, long long *grid_out = nullptr) {
   switch (p) {
-    case 1: return launch_stages<DIM, 1, MODE>(stages, rows, a, cap, sms, s);
-    case 2: return launch_stages<DIM, 2, MODE>(stages, rows, a, cap, sms, s);
-    case 3: return launch_stages<DIM, 3, MODE>(stages, rows, a, cap, sms, s);
-    case 4: return launch_stages<DIM, 4, MODE>(stages, rows, a, cap, sms, s);
-    case 5: return launch_stages<DIM, 5, MODE>(stages, rows, a, cap, sms, s);
-    case 6: return launch_stages<DIM, 6, MODE>(stages, rows, a, cap, sms, s);
-    case 7: return launch_stages<DIM, 7, MODE>(stages, rows, a, cap, sms, s);
+    case 1: return launch_stages<DIM, 1, MODE>(stages, rows, a, cap, sms, s, grid_out);
+    case 2: return launch_stages<DIM, 2, MODE>(stages, rows, a, cap, sms, s, grid_out);
+    case 3: return launch_stages<DIM, 3, MODE>(stages, rows, a, cap, sms, s, grid_out);
+    case 4: return launch_stages<DIM, 4, MODE>(stages, rows, a, cap, sms, s, grid_out);
+    case 5: return launch_stages<DIM, 5, MODE>(stages, rows, a, cap, sms, s, grid_out);
+    case 6: return launch_stages<DIM, 6, MODE>(stages, rows, a, cap, sms, s, grid_out);
+    case 7: return launch_stages<DIM, 7, MODE>(stages, rows, a, cap, sms, s, grid_out);
     default: return IGAFD_ERR_ARG;
   }
+}
+
+// ---- batched launches (one persistent launch for many problems) ----------
+template <int DIM, int P, int MODE, int R>
+igafd_status batch_launch_one(const StencilArgs *args, const long long *item_start, int nprob,
+                              int sel, unsigned long long *queue, int num_sms, cudaStream_t s) {
+  constexpr int kStages = kStagesDefault;
+  const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
+  constexpr int kBlock = kTile / R + 32;
+  auto kern = stencil_batch_kernel<DIM, P, MODE, kStages, R>;
+  static std::atomic<unsigned long long> attr_set{0};
+  static std::atomic<int> per_sm_tab[64];
+  int per_sm = 1;
+  IGAFD_TRY(per_sm_of(kern, kBlock, smem, attr_set, per_sm_tab, &per_sm));
+  const unsigned grid = (unsigned)(num_sms * per_sm);
+  IGAFD_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
+  kern<<<grid, kBlock, smem, s>>>(args, item_start, nprob, sel, queue);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
+  return IGAFD_OK;
+}
+
+template <int DIM, int MODE>
+igafd_status batch_launch_p(int p, int rows, const StencilArgs *args, const long long *item_start,
+                            int nprob, int sel, unsigned long long *queue, int sms, cudaStream_t s) {
+#define IGAFD_BATCH_P(PP)                                                                     \
+  case PP:                                                                                     \
+    if (DIM == 3 && rows == 2)                                                                 \
+      return batch_launch_one<DIM, PP, MODE, 2>(args, item_start, nprob, sel, queue, sms, s); \
+    return batch_launch_one<DIM, PP, MODE, 1>(args, item_start, nprob, sel, queue, sms, s);
+  switch (p) {
+    IGAFD_BATCH_P(1)
+    IGAFD_BATCH_P(2)
+    IGAFD_BATCH_P(3)
+    IGAFD_BATCH_P(4)
+    IGAFD_BATCH_P(5)
+    IGAFD_BATCH_P(6)
+    IGAFD_BATCH_P(7)
+    default: return IGAFD_ERR_ARG;
+  }
+#undef IGAFD_BATCH_P
 }
 
 }  // namespace
@@ -430,15 +589,8 @@ long long igafd_stencil_halo(int p, const int *n) {
 // Internal: y = A x (b == null) or y = b - A x. With pcg != 0 the fused dot
 // feeds the PCG scalars; with skip_done != 0 the kernel does nothing once the
 // PCG convergence flag is set.
-igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
-                                  int pcg, int skip_done, cudaStream_t s, int every,
-                                  unsigned long long *tstat, const double *z) {
-  // the kernel reads x windows that reach p planes beyond the box: use a
-  // zero-padded copy unless x already is one (PCG search direction / iterate)
-  if (x != P->pv && x != P->xpad && x != P->xs) {
-    IGAFD_CUDA(cudaMemcpyAsync(P->xpad, x, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    x = P->xpad;
-  }
+static StencilArgs make_args(igafd_patch *P, const double *x, double *y, const double *b, int pcg,
+                             int skip_done, int every, unsigned long long *tstat, const double *z) {
   StencilArgs a{};
   a.S = P->stencil;
   a.x = x;
@@ -459,9 +611,27 @@ igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, co
   a.err = P->err_flag;
   a.every = every;
   a.tstat = a.partial ? tstat : nullptr;
+  return a;
+}
+
+static long long grid_cap(igafd_patch *P) {
+  const long long ntiles = (P->N + kTile - 1) / kTile;
+  return ntiles < IGAFD_RED_BLOCKS ? ntiles : IGAFD_RED_BLOCKS;
+}
+
+igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, const double *b,
+                                  int pcg, int skip_done, cudaStream_t s, int every,
+                                  unsigned long long *tstat, const double *z) {
+  // the kernel reads x windows that reach p planes beyond the box: use a
+  // zero-padded copy unless x already is one (PCG search direction / iterate)
+  if (x != P->pv && x != P->xpad && x != P->xs) {
+    IGAFD_CUDA(cudaMemcpyAsync(P->xpad, x, P->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    x = P->xpad;
+  }
+  const StencilArgs a = make_args(P, x, y, b, pcg, skip_done, every, tstat, z);
   // persistent grid: the resident CTAs of every SM, never more than the
   // tiles or the partial-sum slots
-  long long cap = a.ntiles < IGAFD_RED_BLOCKS ? a.ntiles : IGAFD_RED_BLOCKS;
+  const long long cap = grid_cap(P);
   const int st = P->stencil_stages > 0 ? P->stencil_stages : kStagesDefault;
   const int rows = P->stencil_rows == 2 ? 2 : 1;
   if (P->dim == 3) {
@@ -470,4 +640,42 @@ igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, co
   }
   if (b) return launch_p<2, 1>(P->p, st, 1, a, cap, P->num_sms, s);
   return launch_p<2, 0>(P->p, st, 1, a, cap, P->num_sms, s);
+}
+
+// ---- for the batched solve -------------------------------------------------
+size_t igafd_stencil_args_bytes() { return sizeof(StencilArgs); }
+
+// The arguments of the PCG's stencil launches on the patch (bytes of a
+// StencilArgs): sel 0 q = A p (search direction), else r = b - A x of the
+// iterate, with (r, z_old) when flexible; and the single launch's grid,
+// whose CTAs a batched launch runs as work items.
+igafd_status igafd_stencil_batch_args(igafd_patch *P, int sel, int flexible, int every, void *out,
+                                      long long *vgrid) {
+  const StencilArgs a = sel == 0 ? make_args(P, P->pv, P->q, nullptr, 1, 0, 0, nullptr, nullptr)
+                                 : make_args(P, P->xs, P->r, P->bint, 1, 0, sel == 1 ? every : 0,
+                                             nullptr, flexible ? P->z : nullptr);
+  memcpy(out, &a, sizeof(a));
+  const long long cap = grid_cap(P);
+  const int st = P->stencil_stages > 0 ? P->stencil_stages : kStagesDefault;
+  const int rows = P->dim == 3 && P->stencil_rows == 2 ? 2 : 1;
+  if (P->dim == 3) {
+    if (sel) return launch_p<3, 1>(P->p, st, rows, a, cap, P->num_sms, nullptr, vgrid);
+    return launch_p<3, 0>(P->p, st, rows, a, cap, P->num_sms, nullptr, vgrid);
+  }
+  if (sel) return launch_p<2, 1>(P->p, st, 1, a, cap, P->num_sms, nullptr, vgrid);
+  return launch_p<2, 0>(P->p, st, 1, a, cap, P->num_sms, nullptr, vgrid);
+}
+
+// One persistent launch over the problems of one class (dim, p, rows per
+// thread): args_dev [nprob] StencilArgs, item_start_dev [nprob + 1].
+igafd_status igafd_stencil_batch_launch(int dim, int p, int rows, int sel, const void *args_dev,
+                                        const long long *item_start_dev, int nprob,
+                                        unsigned long long *queue, int num_sms, cudaStream_t s) {
+  const StencilArgs *args = (const StencilArgs *)args_dev;
+  if (dim == 3) {
+    if (sel) return batch_launch_p<3, 1>(p, rows, args, item_start_dev, nprob, sel, queue, num_sms, s);
+    return batch_launch_p<3, 0>(p, rows, args, item_start_dev, nprob, sel, queue, num_sms, s);
+  }
+  if (sel) return batch_launch_p<2, 1>(p, 1, args, item_start_dev, nprob, sel, queue, num_sms, s);
+  return batch_launch_p<2, 0>(p, 1, args, item_start_dev, nprob, sel, queue, num_sms, s);
 }

