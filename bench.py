@@ -171,6 +171,9 @@ class OracleRun:
         path = oracle_cache_path(n, p) if cache else None
         self.cached = False
         t0 = time.perf_counter()
+        log = lambda msg: print(f"[oracle {time.strftime('%H:%M:%S')}] n={n} p={p}: {msg}",
+                                file=sys.stderr, flush=True)
+        self.log = log
         if path and os.path.exists(path):
             try:
                 with np.load(path) as z:
@@ -179,10 +182,13 @@ class OracleRun:
             except (OSError, ValueError, KeyError):
                 self.cached = False
         if not self.cached:
+            log(f"assembling A in {self.workers} processes")
             self.S = self.disc.assemble_stencil(workers=self.workers)
             t1 = time.perf_counter()
+            log(f"A assembled in {t1 - t0:.1f} s; assembling b")
             self.b = self.disc.assemble_rhs(assemble.sine_load, workers=self.workers)
             self.assembly_s = {"A": t1 - t0, "b": time.perf_counter() - t1}
+            log(f"b assembled in {self.assembly_s['b']:.1f} s")
             if path:
                 try:       # best effort: the other arm of the same run can reuse it
                     tmp = path + f".{os.getpid()}.tmp.npz"
@@ -204,7 +210,9 @@ class OracleRun:
         F = fd.FD([self.disc.pencil(k) for k in range(3)])
         t1 = time.perf_counter()
         res = pcg.pcg(self.apply_A, self.b, F.apply, tol=tol, max_iter=max_iter, x0=x0)
-        return res, time.perf_counter() - t0, t1 - t0
+        t2 = time.perf_counter()
+        self.log(f"PCG to {tol:g}: {res.iters} iterations in {t2 - t0:.1f} s")
+        return res, t2 - t0, t1 - t0
 
 
 def cpu_model():

@@ -128,6 +128,9 @@ typedef struct {
   int fd_fused[3];     /* tensor-core FD in use for TF32, BF16, FP16 operands: 1 = fused (two mode
                           products per kernel; the compile-time-sized kernels where every
                           n_k = 128 in 3D), 0 = one kernel per mode product (autotuned) */
+  int fd_tile[3][4];   /* tile shape per operand type (TF32, BF16, FP16; autotuned, see
+                          igafd_set_fd_tile): rows per CTA of the per-mode kernel, its column
+                          tiles (1 or 2), its K stages, columns per CTA of the fused pencil kernel */
 } igafd_patch_info;
 
 typedef struct {
@@ -379,6 +382,18 @@ igafd_status igafd_set_stencil_rows(igafd_patch *patch, int rows);
  * accumulation order. The choice applies to every operand type and replaces
  * the per-type choice of igafd_autotune. Other values: IGAFD_ERR_ARG. */
 igafd_status igafd_set_fd_fused(igafd_patch *patch, int fused);
+
+/* Tile shape of the tensor-core FD for operand type dtype (IGAFD_TF32,
+ * IGAFD_BF16 or IGAFD_FP16), set by hand (igafd_autotune searches the same
+ * space and keeps the fastest; every shape computes the same products, so
+ * results agree to the FP32 accumulation order): tile[0] rows of the input
+ * per CTA of the per-mode kernel (128, or 64 on a half-filled 128-row MMA
+ * tile), tile[1] its output columns split into 1 or 2 tiles (more CTAs,
+ * each reading its part of the B image), tile[2] K stages in its shared-
+ * memory ring (2 or 3), tile[3] columns per CTA of the fused pencil kernel
+ * (128 or 64). IGAFD_ERR_ARG for other values or a shape whose ring does not
+ * fit in shared memory. */
+igafd_status igafd_set_fd_tile(igafd_patch *patch, igafd_dtype dtype, const int *tile);
 
 /* ---- learned span scalings of the pencils -------------------------------
  * Prop. 1 bounds kappa(P^{-1} A) by the spread of the eigenvalues of Q. The

@@ -151,6 +151,59 @@ __device__ __forceinline__ void chol_solve(T *tile, const T *F, int len, int p, 
   }
 }
 
+// The same two substitutions with the last P solved values of the line kept
+// in registers, so each step's dependency runs from register to register
+// (the tile supplies only the right-hand side and takes the result); the
+// products are summed in the order of chol_solve. The factor's slots left of
+// the band in the first P rows are never read.
+template <int MODE, typename T, int P>
+__device__ __forceinline__ void chol_solve_reg(T *tile, const T *F, int len, int l) {
+  constexpr int W = P + 1;
+  T win[P];                               // win[k - 1] = x[i - k] (forward), x[i + k] (backward)
+#pragma unroll
+  for (int k = 0; k < P; ++k) win[k] = (T)0;
+#pragma unroll 2
+  for (int i = 0; i < len; ++i) {
+    T acc = tile[tix<MODE>(len, l, i)];
+#pragma unroll
+    for (int k = P; k >= 1; --k)
+      if (k <= i) acc -= F[i * W + P - k] * win[k - 1];
+    const T x = acc * F[i * W + P];
+    tile[tix<MODE>(len, l, i)] = x;
+#pragma unroll
+    for (int k = P - 1; k >= 1; --k) win[k] = win[k - 1];
+    win[0] = x;
+  }
+#pragma unroll
+  for (int k = 0; k < P; ++k) win[k] = (T)0;
+#pragma unroll 2
+  for (int i = len - 1; i >= 0; --i) {
+    T acc = tile[tix<MODE>(len, l, i)];
+#pragma unroll
+    for (int k = P; k >= 1; --k)
+      if (k <= len - 1 - i) acc -= F[(i + k) * W + P - k] * win[k - 1];
+    const T x = acc * F[i * W + P];
+    tile[tix<MODE>(len, l, i)] = x;
+#pragma unroll
+    for (int k = P - 1; k >= 1; --k) win[k] = win[k - 1];
+    win[0] = x;
+  }
+}
+
+template <int MODE, typename T>
+__device__ __forceinline__ void chol_solve_line(T *tile, const T *F, int len, int p, int l) {
+  switch (p) {
+    case 1: chol_solve_reg<MODE, T, 1>(tile, F, len, l); break;
+    case 2: chol_solve_reg<MODE, T, 2>(tile, F, len, l); break;
+    case 3: chol_solve_reg<MODE, T, 3>(tile, F, len, l); break;
+    case 4: chol_solve_reg<MODE, T, 4>(tile, F, len, l); break;
+    case 5: chol_solve_reg<MODE, T, 5>(tile, F, len, l); break;
+    case 6: chol_solve_reg<MODE, T, 6>(tile, F, len, l); break;
+    case 7: chol_solve_reg<MODE, T, 7>(tile, F, len, l); break;
+    default: chol_solve<MODE>(tile, F, len, p, l);
+  }
+}
+
 // dynamic shared memory: two tiles, the two bands and one factor
 template <typename T>
 __host__ __device__ size_t line_smem(int len, int p) {
@@ -225,7 +278,7 @@ __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
     load_tile<MODE>(t1, a, nv, [&](long long g) { return a.s[g]; });       // s~_J
   }
   __syncthreads();
-  if ((int)threadIdx.x < nv) chol_solve<MODE>(res, sF, len, p, threadIdx.x);
+  if ((int)threadIdx.x < nv) chol_solve_line<MODE>(res, sF, len, p, threadIdx.x);
   __syncthreads();
   if (STEP == ST_PRE2) {
     store_tile<MODE>(t1, a, nv, [&](long long g, T x) { a.b[g] = x; });               // M2^{-1} r

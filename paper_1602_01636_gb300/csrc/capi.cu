@@ -257,6 +257,10 @@ extern "C" igafd_status igafd_patch_query(const igafd_patch *P, igafd_patch_info
     bool shape_ok = true;
     for (int d = 0; d < P->dim; ++d) shape_ok = shape_ok && P->n[d] <= 128;
     info->fd_fused[k] = P->fd_fused && P->fd_fused_op[k] && k != 2 && shape_ok ? 1 : 0;
+    info->fd_tile[k][0] = P->fd_tile[k][0] == 64 ? 64 : 128;
+    info->fd_tile[k][1] = P->fd_tile[k][1] == 2 ? 2 : 1;
+    info->fd_tile[k][2] = P->fd_tile[k][2] == 3 ? 3 : 2;
+    info->fd_tile[k][3] = P->fd_tile[k][3] == 64 ? 64 : 128;
   }
   return IGAFD_OK;
 }

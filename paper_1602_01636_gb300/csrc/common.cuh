@@ -113,8 +113,8 @@ struct igafd_patch {
   long long loop_nodes;         // kernels per replay
   unsigned long long *tstat;    // stencil timing on the device: [0] earliest block start
                                 // of the running launch, [1] summed ns, [2] launches
-  int loop_key[9];              // dtype, flexible, true_every, chunk, valid, FD form (2),
-                                // stencil depth, stencil rows
+  int loop_key[13];             // dtype, flexible, true_every, chunk, valid, FD form (2),
+                                // stencil depth, stencil rows, FD tile shape (4)
   double *partial;              // [PARTIAL_SLOTS][MAX_BLOCKS]
   unsigned int *counter;        // last-block counters
   double *scal;                 // [S_COUNT]
@@ -124,6 +124,9 @@ struct igafd_patch {
   double *wK[3], *wM[3];        // span scalings of the pencils (device, null = unscaled)
   int fd_fused;                 // 1: fused tensor-core FD (3 kernels) when n_k <= 128
   int fd_fused_op[3];           // the same per operand type (TF32, BF16, FP16), set by the autotuner
+  int fd_tile[3][4];            // per operand type: per-mode kernel's rows per CTA (64 or 128; 0 =
+                                // 128), column split (2 = two column tiles, else one), K stages (3,
+                                // else 2); pencil kernel's columns per CTA (64 or 128; 0 = 128)
   int eig_route;                // 0: FP32 Jacobi + FP64 refinement where n_k <= 128; 1: FP64 Jacobi
   int eig_used[3];              // route each direction took: 0 refined, 1 FP64 Jacobi
   double eig_check[3][2];       // refined route's final check (orthogonality, off-diagonal)

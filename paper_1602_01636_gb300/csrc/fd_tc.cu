@@ -130,6 +130,10 @@ struct PassArgs {
   int tmem_cols;
   const double *done;    // skip when *done != 0
   int *err;
+  // tile shape (autotuned): rows of the input per CTA (128, or 64 with the
+  // 128-row MMA on a half-filled A tile), output columns per CTA (a multiple
+  // of 16; grid.y covers Np), and K stages in the shared-memory ring (2 or 3)
+  int m_tile, n_tile, stages;
 };
 
 template <int OP>
@@ -142,19 +146,26 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base =
       (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = a.stages;                                    // 2 or 3
+  const int n0 = (int)blockIdx.y * a.n_tile;                 // first output column of this CTA
+  const int nN = a.Np - n0 < a.n_tile ? a.Np - n0 : a.n_tile; // its columns (multiple of 16)
   const int stageA = kM * kRowBytes;                         // multiple of 1024
-  const int stageB = a.Np * kRowBytes;
-  unsigned char *sA[2] = {base, base + stageA + stageB};
-  unsigned char *sB[2] = {base + stageA, base + 2 * stageA + stageB};
-  __shared__ uint64_t bar[2];     // MMA completion per stage
-  __shared__ uint64_t bbar[2];    // B-image bulk copy per stage
+  const int stageB = nN * kRowBytes;
+  const int stageStride = stageA + a.n_tile * kRowBytes;     // multiple of 1024
+  unsigned char *sA[3], *sB[3];
+  for (int st = 0; st < 3; ++st) {
+    sA[st] = base + st * stageStride;
+    sB[st] = sA[st] + stageA;
+  }
+  __shared__ uint64_t bar[3];     // MMA completion per stage
+  __shared__ uint64_t bbar[3];    // B-image bulk copy per stage
   __shared__ uint32_t tmem_base;
   __shared__ float s_red[kThreads / 32];
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long m0 = (long long)blockIdx.x * kM;
-  const int mrows = (int)((a.M - m0) < kM ? (a.M - m0) : kM);
+  const long long m0 = (long long)blockIdx.x * a.m_tile;
+  const int mrows = (int)((a.M - m0) < a.m_tile ? (a.M - m0) : a.m_tile);
   const int K = a.K;
   const int nchunks = (K + kKC - 1) / kKC;
 
@@ -182,10 +193,10 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
   }
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[1])));
+    for (int st = 0; st < 3; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[st])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[st])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -200,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = (1u << 4) | (T::kFmt << 7) | (T::kFmt << 10) |
-                         ((uint32_t)(a.Np >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+                         ((uint32_t)(nN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
 
   auto wait_on = [&](uint64_t *b, uint32_t parity) -> bool {
     for (long long it = 0; it < kSpin; ++it) {
@@ -218,25 +229,30 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
   auto wait_bar = [&](int st, uint32_t parity) -> bool { return wait_on(&bar[st], parity); };
 
   for (int c = 0; c < nchunks; ++c) {
-    const int st = c & 1;
-    if (c >= 2) {   // the MMAs that read this stage two chunks ago must be done
-      if (!wait_bar(st, (uint32_t)(((c - 2) >> 1) & 1))) s_fail = 1;
+    const int st = c % S;
+    if (c >= S) {   // the MMAs that read this stage S chunks ago must be done
+      if (!wait_bar(st, (uint32_t)(((c - S) / S) & 1))) s_fail = 1;
       __syncthreads();
       if (s_fail) break;
     }
     const int k0 = c * kKC;
-    // stage B: one bulk copy of the pre-staged image of this K chunk
+    // stage B: rows n0 .. n0 + nN of the pre-staged image of this K chunk, one
+    // bulk copy per 128-byte K atom (the image is [atom][Np rows][128 B]; the
+    // rows of a tile starting at a multiple of 8 keep their swizzle phase)
     if (tid == 0) {
       const uint32_t bytes = (uint32_t)stageB;
+      constexpr int kAtoms = kRowBytes / 128;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bbar[st])),
                    "r"(bytes)
                    : "memory");
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              smem_u32(sB[st])),
-          "l"(a.Bimg + (size_t)c * stageB), "r"(bytes), "r"(smem_u32(&bbar[st]))
-          : "memory");
+      for (int at = 0; at < kAtoms; ++at)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sB[st] + at * nN * 128)),
+            "l"(a.Bimg + (size_t)c * a.Np * kRowBytes + (size_t)at * a.Np * 128 + (size_t)n0 * 128),
+            "r"((uint32_t)(nN * 128)), "r"(smem_u32(&bbar[st]))
+            : "memory");
     }
     // stage A: warp w takes rows 16w..16w+15, lane l columns k0+2l, k0+2l+1;
     // all sixteen loads are issued before the swizzled, rounded stores
@@ -274,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
-      if (!wait_on(&bbar[st], (uint32_t)((c >> 1) & 1))) s_fail = 1;
+      if (!wait_on(&bbar[st], (uint32_t)((c / S) & 1))) s_fail = 1;
     }
     if (tid == 0 && !s_fail) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -282,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
       for (int ks = 0; ks < ksteps; ++ks) {
         const int kbyte = ks * 32;
         const uint32_t ao = (kbyte >> 7) * kM * 128 + (kbyte & 127);
-        const uint32_t bo = (kbyte >> 7) * a.Np * 128 + (kbyte & 127);
+        const uint32_t bo = (kbyte >> 7) * nN * 128 + (kbyte & 127);
         const uint64_t ad = sw128_desc(smem_u32(sA[st]) + ao);
         const uint64_t bd = sw128_desc(smem_u32(sB[st]) + bo);
         const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
@@ -307,7 +323,7 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
   bool ok = !s_fail;
   if (ok && nchunks > 0) {
     const int last = nchunks - 1;
-    ok = wait_bar(last & 1, (uint32_t)((last >> 1) & 1));
+    ok = wait_bar(last % S, (uint32_t)((last / S) & 1));
     if (!ok) s_fail = 1;
   }
   __syncthreads();
@@ -318,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
     const int r = q * 32 + lane;                  // row within the tile
     const long long m = m0 + r;
     const float unscale = 1.0f / (a_scale * (a.b_scale ? *a.b_scale : 1.0f));
-    const int ncol32 = (a.Np + 31) / 32;
+    const int ncol32 = (nN + 31) / 32;
     for (int cb = half; cb < ncol32; cb += 2) {
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
@@ -336,8 +352,8 @@ __global__ void __launch_bounds__(kThreads) tc_pass_kernel(PassArgs a) {
       if (r < mrows) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int n = cb * 32 + j;
-          if (n < a.N) {
+          const int n = n0 + cb * 32 + j;
+          if (cb * 32 + j < nN && n < a.N) {
             const long long o = (long long)n * a.M + m;
             float val = __uint_as_float(v[j]) * unscale;
             if (a.inv_lam) val *= a.inv_lam[o];
@@ -472,6 +488,7 @@ struct FusedArgs {
   const float *d1, *d2, *d3; // PENCIL: FP32 D_k, divided by d1 + d2 + d3 on the fly
   const double *done;
   int *err;
+  int ctile;                 // PENCIL: columns per CTA, 128 or 64 (a half-filled MMA tile; autotuned)
 };
 
 // Pack E = 16 / kBytes operand values into one 16-byte chunk of the
@@ -562,7 +579,7 @@ __device__ void stage_rows(unsigned char *R, const void *in, int in_f64, long lo
 // rows, whose swizzle puts the chunk in eight distinct banks.
 template <int OP>
 __device__ void stage_cols(unsigned char *R, const float *in, long long n12, long long c0, int K,
-                           int Kp, int aligned, int tid) {
+                           int Kp, int aligned, int tid, int ctile) {
   (void)aligned;
   constexpr int E = 16 / Op<OP>::kBytes;
   constexpr int U = 32 / E;
@@ -573,7 +590,7 @@ __device__ void stage_cols(unsigned char *R, const float *in, long long n12, lon
     for (int u = 0; u < U; ++u) {
       const int id = b0 + u * kThreads + tid;
       const int c = id % kM, k0 = (id / kM) * E;
-      const bool ok = id < total && c0 + c < n12;
+      const bool ok = id < total && c0 + c < n12 && c < ctile;
       const float *src = in + (long long)k0 * n12 + c0 + c;
 #pragma unroll
       for (int e = 0; e < E; ++e) v[u][e] = (ok && k0 + e < K) ? __ldg(src + (long long)e * n12) : 0.0f;
@@ -689,8 +706,10 @@ __device__ __forceinline__ void tc_fused_cta(const FusedArgs &a, const int blk) 
   load_b(a.B1, a.Np1, a.Kp1);
 
   // ---- first A operand: rows = lanes of the first accumulator ----
+  const int ctile = KIND == PENCIL && a.ctile == 64 ? 64 : kM;
   if (KIND == PENCIL)
-    stage_cols<OP>(R1, (const float *)a.in, a.n12, (long long)blk * kM, a.K1, a.Kp1, a.in_aligned, tid);
+    stage_cols<OP>(R1, (const float *)a.in, a.n12, (long long)blk * ctile, a.K1, a.Kp1, a.in_aligned,
+                   tid, ctile);
   else
     stage_rows<OP>(R1, a.in, a.in_f64, (long long)blk * a.n2, a.rowsA, a.K1, a.Kp1, a.in_aligned, tid);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -715,8 +734,8 @@ __device__ __forceinline__ void tc_fused_cta(const FusedArgs &a, const int blk) 
     __syncthreads();
     const int ncol32 = (a.Np1 + 31) / 32;
     // PENCIL: d1[j1] + d2[j2] of this thread's column c = j2 n1 + j1
-    const long long cc = (long long)blk * kM + lane_row;
-    const bool c_ok = KIND == PENCIL && cc < a.n12;
+    const long long cc = (long long)blk * ctile + lane_row;
+    const bool c_ok = KIND == PENCIL && cc < a.n12 && lane_row < ctile;
     const float d12 = c_ok ? a.d1[cc % a.n1] + a.d2[cc / a.n1] : 0.0f;
     for (int cb = half; cb < ncol32; cb += 2) {
       uint32_t v[32];
@@ -768,8 +787,8 @@ __device__ __forceinline__ void tc_fused_cta(const FusedArgs &a, const int blk) 
     long long obase, ostride;
     int nlanes, ncols;
     if (KIND == PENCIL) {
-      obase = (long long)blk * kM; ostride = a.n12;
-      nlanes = (int)((a.n12 - obase) < kM ? (a.n12 - obase) : kM); ncols = a.n3;
+      obase = (long long)blk * ctile; ostride = a.n12;
+      nlanes = (int)((a.n12 - obase) < ctile ? (a.n12 - obase) : ctile); ncols = a.n3;
     } else {
       obase = (long long)blk * a.n12; ostride = a.n1;
       nlanes = a.n1; ncols = a.n2;
@@ -1266,19 +1285,20 @@ void igafd_fd_tc_free(igafd_patch *P) {
   P->mixed = nullptr;
 }
 
-static size_t pass_smem(int op, int Np) {
+static size_t pass_smem(int op, int n_tile, int stages) {
   const int bytes = op == OP_TF32 ? 4 : 2;
   const size_t row = (size_t)kKC * bytes;
-  return 1024 + 2 * (kM * row + (size_t)Np * row);
+  return 1024 + (size_t)stages * (kM * row + (size_t)n_tile * row);
 }
 
 template <int OP>
 static igafd_status launch_pass(const PassArgs &a, cudaStream_t s) {
-  const size_t smem = pass_smem(OP, a.Np);
+  const size_t smem = pass_smem(OP, a.n_tile, a.stages);
   IGAFD_CUDA(cudaFuncSetAttribute(tc_pass_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-  const unsigned grid = (unsigned)((a.M + kM - 1) / kM);
-  IGAFD_CUDA(igafd_launch(tc_pass_kernel<OP>, dim3(grid), dim3(kThreads), smem, s, a));
+  const dim3 grid((unsigned)((a.M + a.m_tile - 1) / a.m_tile),
+                  (unsigned)((a.Np + a.n_tile - 1) / a.n_tile));
+  IGAFD_CUDA(igafd_launch(tc_pass_kernel<OP>, grid, dim3(kThreads), smem, s, a));
   IGAFD_LAUNCHED(1);
   return IGAFD_OK;
 }
@@ -1343,8 +1363,9 @@ static void fused_args(igafd_patch *P, int op, const double *r, double *z, doubl
     c.rowsA = kM;
     c.inv_lam = nullptr;
     c.d1 = F->d32[0]; c.d2 = F->d32[1]; c.d3 = F->d32[2];
+    c.ctile = P->fd_tile[op][3] == 64 ? 64 : kM;
     out[1] = c;
-    grid[1] = (int)((a.n12 + kM - 1) / kM);
+    grid[1] = (int)((a.n12 + c.ctile - 1) / c.ctile);
     mid = t2;
   }
   FusedArgs b = a;
@@ -1455,8 +1476,15 @@ igafd_status igafd_fd_tc_apply(igafd_patch *P, igafd_dtype dt, const double *r, 
     a.K = n;
     a.N = n;
     a.Np = (n + 15) / 16 * 16;
+    // tile shape of this operand type (autotuned; 128 rows, all columns and
+    // two stages by default); a 256-row ring tile would not fit in TMEM
+    const int *tile = P->fd_tile[op];
+    a.m_tile = tile[0] == 64 ? 64 : kM;
+    a.n_tile = a.Np;
+    if (tile[1] == 2 && a.Np >= 32) a.n_tile = (a.Np / 2 + 15) / 16 * 16;
+    a.stages = tile[2] == 3 ? 3 : 2;
     int cols = 32;
-    while (cols < a.Np) cols <<= 1;
+    while (cols < a.n_tile) cols <<= 1;
     a.tmem_cols = cols;
     a.done = done;
     a.err = P->err_flag;

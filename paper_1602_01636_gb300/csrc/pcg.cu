@@ -15,6 +15,7 @@
 // grid and a last-block sum in fixed order (bitwise reproducible).
 #include "common.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -379,8 +380,9 @@ static igafd_status loop_graph(igafd_patch *P, igafd_dtype dt, int flex, int tru
   // everything that selects the captured kernels: the FD form and the stencil
   // pipeline too (set by the autotuner or explicitly between solves)
   const int op = dt == IGAFD_TF32 ? 0 : dt == IGAFD_BF16 ? 1 : 2;
-  const int key[9] = {(int)dt, flex, true_every, chunk, 1 + timing, P->fd_fused,
-                      P->fd_fused_op[op], P->stencil_stages, P->stencil_rows};
+  const int key[13] = {(int)dt, flex, true_every, chunk, 1 + timing, P->fd_fused,
+                       P->fd_fused_op[op], P->stencil_stages, P->stencil_rows, P->fd_tile[op][0],
+                       P->fd_tile[op][1], P->fd_tile[op][2], P->fd_tile[op][3]};
   if (P->loop_exec && memcmp(key, P->loop_key, sizeof(key)) == 0) return IGAFD_OK;
   if (P->loop_exec) {
     cudaGraphExecDestroy(P->loop_exec);
@@ -675,9 +677,12 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
 
 struct BatchClass {             // problems whose stencil shares (dim, p, rows)
   int dim, p, rows;
-  std::vector<int> members;
+  std::vector<int> members;     // largest work item first (shorter tails of the queue)
   void *args[3];                // StencilArgs per member, for sel 0, 1, 2 (device)
   long long *start[3];          // item prefix per sel (device)
+  unsigned long long *queue;    // the class's work-queue counter (device)
+  cudaStream_t side;            // capture stream of its branch (classes run concurrently)
+  cudaEvent_t done;
 };
 
 struct igafd_batch {
@@ -696,8 +701,8 @@ struct igafd_batch {
   long long *vec_start;         // items of the vector kernels (device)
   long long vec_total;
   double **scal_ptrs;           // per problem (device)
-  unsigned long long *queue;    // work-queue counter (device)
   unsigned *passes;             // loop passes (device)
+  cudaEvent_t fork;             // start of a forked stencil phase
   std::vector<void *> allocs;
   cudaStream_t cap;
   cudaGraph_t graph;
@@ -729,10 +734,20 @@ static igafd_status batch_body(igafd_batch *B, cudaStream_t s, cudaGraphConditio
     IGAFD_CUDA(cudaGetLastError());
     return IGAFD_OK;
   };
+  // the classes' launches are independent: each on its own branch of the
+  // graph (forked from and joined back to s), so their queues drain together
   auto stencil = [&](int sel) -> igafd_status {
-    for (BatchClass &c : B->classes)
+    IGAFD_CUDA(cudaEventRecord(B->fork, s));
+    for (size_t i = 0; i < B->classes.size(); ++i) {
+      BatchClass &c = B->classes[i];
+      cudaStream_t cs = i == 0 ? s : c.side;
+      if (i > 0) IGAFD_CUDA(cudaStreamWaitEvent(cs, B->fork, 0));
       IGAFD_TRY(igafd_stencil_batch_launch(c.dim, c.p, c.rows, sel, c.args[sel], c.start[sel],
-                                           (int)c.members.size(), B->queue, B->num_sms, s));
+                                           (int)c.members.size(), c.queue, B->num_sms, cs));
+      if (i > 0) IGAFD_CUDA(cudaEventRecord(c.done, cs));
+    }
+    for (size_t i = 1; i < B->classes.size(); ++i)
+      IGAFD_CUDA(cudaStreamWaitEvent(s, B->classes[i].done, 0));
     return IGAFD_OK;
   };
   IGAFD_TRY(stencil(0));                                    // q = A p, alpha
@@ -765,6 +780,11 @@ extern "C" void igafd_batch_destroy(igafd_batch *B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
   if (B->cap) cudaStreamDestroy(B->cap);
+  for (BatchClass &c : B->classes) {
+    if (c.side) cudaStreamDestroy(c.side);
+    if (c.done) cudaEventDestroy(c.done);
+  }
+  if (B->fork) cudaEventDestroy(B->fork);
   for (void *p : B->allocs) cudaFree(p);
   delete B;
 }
@@ -815,7 +835,25 @@ extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int coun
     }
     c->members.push_back(i);
   }
+  std::vector<unsigned char> tmp_args(sab);
   for (BatchClass &c : B->classes) {
+    // largest item (tiles per CTA of the problem's own grid) first
+    std::vector<std::pair<double, int>> order;
+    for (int i : c.members) {
+      long long vg = 1;
+      if ((st = igafd_stencil_batch_args(B->ps[i], 0, B->flex, o.true_every, tmp_args.data(), &vg)) !=
+          IGAFD_OK)
+        return fail(st);
+      const double tiles = (double)((B->ps[i]->N + 255) / 256);
+      order.push_back({-tiles / (double)(vg > 0 ? vg : 1), i});
+    }
+    std::stable_sort(order.begin(), order.end());
+    for (size_t m = 0; m < order.size(); ++m) c.members[m] = order[m].second;
+    std::vector<unsigned long long> q0(1, 0);
+    if ((st = batch_upload(B, q0, &c.queue)) != IGAFD_OK) return fail(st);
+    if (cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess)
+      return fail(IGAFD_ERR_CUDA);
     for (int sel = 0; sel < 3; ++sel) {
       std::vector<unsigned char> args(sab * c.members.size());
       std::vector<long long> start(c.members.size() + 1, 0);
@@ -879,8 +917,8 @@ extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int coun
   if ((st = batch_upload(B, va, &B->vec_args)) != IGAFD_OK) return fail(st);
   if ((st = batch_upload(B, vs, &B->vec_start)) != IGAFD_OK) return fail(st);
   if ((st = batch_upload(B, sp, &B->scal_ptrs)) != IGAFD_OK) return fail(st);
-  std::vector<unsigned long long> q1(1, 0);
-  if ((st = batch_upload(B, q1, &B->queue)) != IGAFD_OK) return fail(st);
+  if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess)
+    return fail(IGAFD_ERR_CUDA);
   std::vector<unsigned> p1(1, 0);
   if ((st = batch_upload(B, p1, &B->passes)) != IGAFD_OK) return fail(st);
   // the graph: reset the pass counter, then while (any unfinished) { body }

@@ -33,8 +33,18 @@ struct TuneEntry {
   int stages, rows;
   float ms[kNumCand];   // candidate c: depth kCandidates[c % 3], rows 1 + c / 3
   int fd_fused[2];      // TF32, BF16: 1 fused, 0 per mode product
-  float fd_ms[4];       // TF32 fused, TF32 per mode, BF16 fused, BF16 per mode (-1: not timed)
+  float fd_ms[4];       // TF32 fused, TF32 per mode, BF16 fused, BF16 per mode: the best
+                        // time of each form over its tile shapes (-1: not timed)
+  int fd_tile[3][4];    // TF32, BF16, FP16: the chosen tile shape (igafd_patch::fd_tile)
+  float fp16_ms;        // FP16 (per mode product only): the best time
 };
+
+void default_tiles(TuneEntry &e) {
+  for (int o = 0; o < 3; ++o) {
+    e.fd_tile[o][0] = 128; e.fd_tile[o][1] = 1; e.fd_tile[o][2] = 2; e.fd_tile[o][3] = 128;
+  }
+  e.fp16_ms = -1.0f;
+}
 
 std::mutex g_tune_mutex;
 std::map<std::string, TuneEntry> g_tune;
@@ -58,21 +68,28 @@ void load_file_locked() {
   if (!path || !*path) return;
   FILE *f = fopen(path, "r");
   if (!f) return;
-  char line[512];
+  char line[1024];
   while (fgets(line, sizeof(line), f)) {
     char key[128];
     TuneEntry e{};
     e.fd_fused[0] = e.fd_fused[1] = 1;
     for (int i = 0; i < 4; ++i) e.fd_ms[i] = -1.0f;
+    default_tiles(e);
+    int t[12];
     const int got = sscanf(line,
                " {\"key\": \"%127[^\"]\", \"stencil_stages\": %d, \"stencil_rows\": %d, "
                "\"ms\": [%f, %f, %f, %f, %f, %f], \"fd_fused\": [%d, %d], "
-               "\"fd_ms\": [%f, %f, %f, %f]",
+               "\"fd_ms\": [%f, %f, %f, %f], \"fd_tile\": [[%d, %d, %d, %d], [%d, %d, %d, %d], "
+               "[%d, %d, %d, %d]], \"fp16_ms\": %f",
                key, &e.stages, &e.rows, &e.ms[0], &e.ms[1], &e.ms[2], &e.ms[3], &e.ms[4],
                &e.ms[5], &e.fd_fused[0], &e.fd_fused[1], &e.fd_ms[0], &e.fd_ms[1], &e.fd_ms[2],
-               &e.fd_ms[3]);
-    if (got == 15 || got == 9) {      // 9: a line written before the FD was tuned
+               &e.fd_ms[3], &t[0], &t[1], &t[2], &t[3], &t[4], &t[5], &t[6], &t[7], &t[8], &t[9],
+               &t[10], &t[11], &e.fp16_ms);
+    // 28: every field; 15: written before tile shapes were tuned; 9: before the FD was
+    if (got == 28 || got == 15 || got == 9) {
       if (got == 9) e.fd_fused[0] = e.fd_fused[1] = 1;
+      if (got == 28)
+        for (int i = 0; i < 12; ++i) e.fd_tile[i / 4][i % 4] = t[i];
       g_tune[key] = e;
     }
   }
@@ -84,12 +101,16 @@ void append_file_locked(const std::string &key, const TuneEntry &e) {
   if (!path || !*path) return;
   FILE *f = fopen(path, "a");
   if (!f) return;
+  const int(*t)[4] = e.fd_tile;
   fprintf(f,
           "{\"key\": \"%s\", \"stencil_stages\": %d, \"stencil_rows\": %d, "
           "\"ms\": [%.5f, %.5f, %.5f, %.5f, %.5f, %.5f], \"fd_fused\": [%d, %d], "
-          "\"fd_ms\": [%.5f, %.5f, %.5f, %.5f]}\n",
+          "\"fd_ms\": [%.5f, %.5f, %.5f, %.5f], \"fd_tile\": [[%d, %d, %d, %d], [%d, %d, %d, %d], "
+          "[%d, %d, %d, %d]], \"fp16_ms\": %.5f}\n",
           key.c_str(), e.stages, e.rows, e.ms[0], e.ms[1], e.ms[2], e.ms[3], e.ms[4], e.ms[5],
-          e.fd_fused[0], e.fd_fused[1], e.fd_ms[0], e.fd_ms[1], e.fd_ms[2], e.fd_ms[3]);
+          e.fd_fused[0], e.fd_fused[1], e.fd_ms[0], e.fd_ms[1], e.fd_ms[2], e.fd_ms[3], t[0][0],
+          t[0][1], t[0][2], t[0][3], t[1][0], t[1][1], t[1][2], t[1][3], t[2][0], t[2][1], t[2][2],
+          t[2][3], e.fp16_ms);
   fclose(f);
 }
 
@@ -105,6 +126,7 @@ void igafd_tune_lookup(igafd_patch *P) {
     P->stencil_rows = it->second.rows;
     P->fd_fused_op[0] = it->second.fd_fused[0];
     P->fd_fused_op[1] = it->second.fd_fused[1];
+    memcpy(P->fd_tile, it->second.fd_tile, sizeof(P->fd_tile));
   }
 }
 
@@ -138,6 +160,7 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
       P->stencil_rows = it->second.rows;
       P->fd_fused_op[0] = it->second.fd_fused[0];
       P->fd_fused_op[1] = it->second.fd_fused[1];
+      memcpy(P->fd_tile, it->second.fd_tile, sizeof(P->fd_tile));
       return IGAFD_OK;
     }
   }
@@ -171,21 +194,70 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
       best.rows = 1 + c / 3;
     }
   }
-  // tensor-core FD form per operand type (the fused form needs every n_k <= 128)
-  bool shape_ok = P->mixed != nullptr;
-  for (int k = 0; k < P->dim; ++k) shape_ok = shape_ok && P->n[k] <= 128;
-  const int saved_fused = P->fd_fused, saved_op[2] = {P->fd_fused_op[0], P->fd_fused_op[1]};
-  for (int i = 0; i < 4; ++i) best.fd_ms[i] = -1.0f;
-  best.fd_fused[0] = best.fd_fused[1] = shape_ok ? 1 : 0;
-  const igafd_dtype dts[2] = {IGAFD_TF32, IGAFD_BF16};
-  P->fd_fused = 1;
-  for (int o = 0; o < 2 && st == IGAFD_OK && shape_ok; ++o) {
-    for (int form = 0; form < 2 && st == IGAFD_OK; ++form) {
-      P->fd_fused_op[o] = form == 0 ? 1 : 0;
-      st = time_fd(P, dts[o], s, e0, e1, &best.fd_ms[2 * o + form]);
-    }
-    if (st == IGAFD_OK) best.fd_fused[o] = best.fd_ms[2 * o] <= best.fd_ms[2 * o + 1] ? 1 : 0;
+  // Tensor-core FD per operand type: its form (fused, which needs every
+  // n_k <= 128, or one kernel per mode product) and that form's tile shape,
+  // every candidate timed on the patch. Fused: the pencil kernel's columns
+  // per CTA (128, or 64 on a half-filled MMA tile; the compile-time-sized
+  // n_k = 128 kernels have none). Per mode product: rows per CTA {128, 64},
+  // one or two column tiles, and a third K stage where some n_k > 128 and it
+  // fits in shared memory.
+  const bool have_tc = P->mixed != nullptr;
+  bool shape_ok = have_tc;
+  int nmax = 0, npmin = 1 << 30;
+  for (int k = 0; k < P->dim; ++k) {
+    shape_ok = shape_ok && P->n[k] <= 128;
+    nmax = P->n[k] > nmax ? P->n[k] : nmax;
+    const int np = (P->n[k] + 15) / 16 * 16;
+    npmin = np < npmin ? np : npmin;
   }
+  const bool n128 = P->dim == 3 && P->n[0] == 128 && P->n[1] == 128 && P->n[2] == 128;
+  const int saved_fused = P->fd_fused, saved_op[2] = {P->fd_fused_op[0], P->fd_fused_op[1]};
+  int saved_tile[3][4];
+  memcpy(saved_tile, P->fd_tile, sizeof(saved_tile));
+  for (int i = 0; i < 4; ++i) best.fd_ms[i] = -1.0f;
+  default_tiles(best);
+  best.fd_fused[0] = best.fd_fused[1] = shape_ok ? 1 : 0;
+  const igafd_dtype dts[3] = {IGAFD_TF32, IGAFD_BF16, IGAFD_FP16};
+  P->fd_fused = 1;
+  bool fits256 = true;
+  for (int k = 0; k < P->dim; ++k) fits256 = fits256 && P->n[k] <= 256;
+  for (int o = 0; o < 3 && st == IGAFD_OK && have_tc && fits256; ++o) {
+    const int bytes = o == 0 ? 4 : 2;
+    float best_o = 1e30f;
+    auto trial = [&](int fused, int m, int nd, int stg, int pm) {
+      if (o < 2) P->fd_fused_op[o] = fused;
+      P->fd_tile[o][0] = m; P->fd_tile[o][1] = nd; P->fd_tile[o][2] = stg; P->fd_tile[o][3] = pm;
+      float ms = 0.f;
+      st = time_fd(P, dts[o], s, e0, e1, &ms);
+      if (st != IGAFD_OK) return;
+      float *slot = o < 2 ? &best.fd_ms[2 * o + (fused ? 0 : 1)] : &best.fp16_ms;
+      if (*slot < 0.f || ms < *slot) *slot = ms;
+      if (ms < best_o) {
+        best_o = ms;
+        if (o < 2) best.fd_fused[o] = fused;
+        best.fd_tile[o][0] = m; best.fd_tile[o][1] = nd; best.fd_tile[o][2] = stg;
+        best.fd_tile[o][3] = pm;
+      }
+    };
+    if (o < 2 && shape_ok) {
+      trial(1, 128, 1, 2, 128);
+      if (P->dim == 3 && !n128 && st == IGAFD_OK) trial(1, 128, 1, 2, 64);
+    }
+    for (int m = 128; m >= 64 && st == IGAFD_OK; m -= 64)
+      for (int nd = 1; nd <= 2 && st == IGAFD_OK; ++nd) {
+        if (nd == 2 && npmin < 32) continue;
+        for (int stg = 2; stg <= 3 && st == IGAFD_OK; ++stg) {
+          if (stg == 3) {            // only with more than two K chunks, and if it fits
+            const int npm = (nmax + 15) / 16 * 16;
+            const int nt = nd == 2 ? (npm / 2 + 15) / 16 * 16 : npm;
+            const size_t smem = 1024 + (size_t)3 * (128 + nt) * 64 * bytes;
+            if (nmax <= 128 || smem > 227 * 1024) continue;
+          }
+          trial(0, m, nd, stg, 128);
+        }
+      }
+  }
+  memcpy(P->fd_tile, saved_tile, sizeof(saved_tile));
   P->fd_fused = saved_fused;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -200,6 +272,7 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
   P->stencil_rows = best.rows;
   P->fd_fused_op[0] = best.fd_fused[0];
   P->fd_fused_op[1] = best.fd_fused[1];
+  memcpy(P->fd_tile, best.fd_tile, sizeof(P->fd_tile));
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tune[key] = best;
   append_file_locked(key, best);
@@ -222,5 +295,21 @@ extern "C" igafd_status igafd_set_fd_fused(igafd_patch *P, int fused) {
   if (!P || (fused != 0 && fused != 1)) return IGAFD_ERR_ARG;
   P->fd_fused = fused;
   for (int o = 0; o < 3; ++o) P->fd_fused_op[o] = 1;   // an explicit choice overrides the autotuner
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_set_fd_tile(igafd_patch *P, igafd_dtype dtype, const int *tile) {
+  if (!P || !tile) return IGAFD_ERR_ARG;
+  const int o = dtype == IGAFD_TF32 ? 0 : dtype == IGAFD_BF16 ? 1 : dtype == IGAFD_FP16 ? 2 : -1;
+  if (o < 0 || (tile[0] != 64 && tile[0] != 128) || (tile[1] != 1 && tile[1] != 2) ||
+      (tile[2] != 2 && tile[2] != 3) || (tile[3] != 64 && tile[3] != 128))
+    return IGAFD_ERR_ARG;
+  const int bytes = o == 0 ? 4 : 2;
+  int nmax = 0;
+  for (int k = 0; k < P->dim; ++k) nmax = P->n[k] > nmax ? P->n[k] : nmax;
+  const int npm = (nmax + 15) / 16 * 16;
+  const int nt = tile[1] == 2 ? (npm / 2 + 15) / 16 * 16 : npm;
+  if (1024 + (size_t)tile[2] * (128 + nt) * 64 * bytes > 227 * 1024) return IGAFD_ERR_ARG;
+  for (int i = 0; i < 4; ++i) P->fd_tile[o][i] = tile[i];
   return IGAFD_OK;
 }

@@ -52,7 +52,8 @@ class PatchInfo(C.Structure):
                 ("q_bound", C.c_double), ("setup_ms", C.c_double), ("eig_ms", C.c_double),
                 ("stencil_bytes", C.c_longlong), ("stencil_stages", C.c_int),
                 ("stencil_rows", C.c_int), ("eig_refined", C.c_int * 3),
-                ("eig_check", (C.c_double * 2) * 3), ("fd_fused", C.c_int * 3)]
+                ("eig_check", (C.c_double * 2) * 3), ("fd_fused", C.c_int * 3),
+                ("fd_tile", (C.c_int * 4) * 3)]
 
 
 class PCGOpts(C.Structure):
@@ -82,7 +83,7 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_adi_wachspress", "igafd_mp_numbering", "igafd_mp_subdomain", "igafd_mp_create",
            "igafd_mp_destroy", "igafd_mp_apply_ias", "igafd_quad_points", "igafd_load_rhs",
            "igafd_batch_create", "igafd_batch_solve", "igafd_batch_destroy",
-           "igafd_mp_set_operator", "igafd_mp_apply_A", "igafd_mp_pcg_solve"]
+           "igafd_mp_set_operator", "igafd_mp_apply_A", "igafd_mp_pcg_solve", "igafd_set_fd_tile"]
 
 MLP_PARAMS = 4738
 
@@ -118,6 +119,7 @@ def lib():
     L.igafd_autotune.argtypes = [vp, C.c_int, vp]
     L.igafd_set_stencil_stages.argtypes = [vp, C.c_int]
     L.igafd_set_fd_fused.argtypes = [vp, C.c_int]
+    L.igafd_set_fd_tile.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
     L.igafd_set_stencil_rows.argtypes = [vp, C.c_int]
     L.igafd_setup_prec.argtypes = [vp, vp]
     dp = C.POINTER(C.c_double)
@@ -495,6 +497,18 @@ class Patch:
 
     def set_fd_fused(self, fused):
         _check(lib().igafd_set_fd_fused(self.h, int(fused)), "set_fd_fused")
+
+    def set_fd_tile(self, dtype, tile):
+        """Tile shape of the tensor-core FD for dtype: (rows per CTA of the
+        per-mode kernel, its column tiles, its K stages, columns per CTA of
+        the fused pencil kernel)."""
+        t = (C.c_int * 4)(*[int(v) for v in tile])
+        _check(lib().igafd_set_fd_tile(self.h, DTYPES[dtype], t), "set_fd_tile")
+        self.info = self.query()
+
+    def fd_tile(self, dtype):
+        o = {"tf32": 0, "bf16": 1, "fp16": 2}[dtype]
+        return tuple(self.info.fd_tile[o][i] for i in range(4))
 
     def stencil(self):
         import torch
