@@ -257,7 +257,11 @@ def oracle_baseline(n, p, tol, x_gpu, workers=None):
     with blas_threads(1) as bt:
         if bt.ok:
             res1, t_one, _ = o.solve(tol)
-    res13, _, _ = o.solve(1e-13, x0=res8.x)
+    # the reference solution: PCG towards 1e-13 from the tol solution, capped
+    # (FP64 cannot always confirm 1e-13 at n = 128: the true residual levels
+    # off near 1e-12 while the recurrence keeps falling); its true residual
+    # is reported, and ~1e-11 is far below the 1e-7 the mixed path is held to
+    res13, _, _ = o.solve(1e-13, x0=res8.x, max_iter=3 * res8.iters + 20)
 
     def diff(x, ref):
         return {"max_rel": float(np.abs(x - ref).max() / np.abs(ref).max()),
@@ -273,8 +277,10 @@ def oracle_baseline(n, p, tol, x_gpu, workers=None):
                       f"+ {res8.iters} iterations, on all {o.cores} host cores (numpy/BLAS threads); "
                       f"single_thread_s: the same solve with BLAS limited to one thread; assembly of "
                       f"A and b excluded ({assembly_note(o)})")}
-    vs = {"oracle_solution": f"oracle PCG to 1e-13 (warm start from its tol {tol:g} solution; "
-                             f"{res13.iters} more iterations, true relres {res13.true_relres:.1e})",
+    vs = {"oracle_solution": f"oracle PCG towards 1e-13 (warm start from its tol {tol:g} solution, "
+                             f"at most {3 * res8.iters + 20} iterations): {res13.iters} iterations, "
+                             f"true relres {res13.true_relres:.1e}",
+          "oracle_solution_true_relres": res13.true_relres,
           "oracle_iterations_at_tol": res8.iters}
     for name, x in x_gpu.items():
         vs[name] = {"vs_converged": diff(x, res13.x)}
@@ -660,6 +666,7 @@ def run_ours(args):
                                  "unit": "GB/s", "frac": alg_bytes / st_s / 1e9 / hbm_peak,
                                  "peak_source": hbm_src + " (hbm_gbs)",
                                  "alg_bytes_per_launch": alg_bytes}},
+            "fd_roofline": fd_roofline(patch, dtype, aps_mixed, peaks),
             "clocks": ck,
             "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
                     "d2h_bytes_per_step": 8 * N},
@@ -672,6 +679,35 @@ def run_ours(args):
     patch.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def fd_roofline(patch, dtype, applies_per_s, peaks):
+    """Roofline of one mixed-precision FD apply (the tensor-core kernels): the
+    algorithmic bytes are r read and z written in FP64 (16 B per dof), the
+    FLOPs 4 N sum_k n_k (a forward and a backward product per direction, 2
+    FLOP per multiply-add; 12 n^4 for n_k = n in 3D). Peaks: the measured
+    copy bandwidth and the measured dense BF16 rate (TF32 at half of it, the
+    nominal ratio); the bound is the larger of the two times."""
+    N = patch.N
+    t = 1.0 / applies_per_s
+    alg_bytes = 16.0 * N
+    flops = 4.0 * N * sum(patch.n)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    tc_peak = {"tf32": 0.5 * bf16, "bf16": bf16, "fp16": bf16}.get(dtype)
+    t_hbm = alg_bytes / (hbm_peak * 1e9)
+    out = {"kernel": "tensor-core FD apply (three fused tcgen05 kernels at n = 128)",
+           "apply_us": t * 1e6, "alg_bytes_per_apply": alg_bytes, "flops_per_apply": flops,
+           "hbm": {"achieved": alg_bytes / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                   "frac": t_hbm / t}}
+    if tc_peak:
+        t_tc = flops / (tc_peak * 1e12)
+        out["tensor"] = {"achieved": flops / t / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+                         "frac": t_tc / t, "peak_source": "measured bf16_tflops" +
+                         (" x 0.5 (TF32)" if dtype == "tf32" else "")}
+        out["bound"] = "hbm" if t_hbm >= t_tc else "tensor"
+        out["frac_of_bound"] = max(t_hbm, t_tc) / t
+    return out
 
 
 def batch_problems(count, seed0=0):
@@ -732,11 +768,13 @@ def run_batch(args):
     torch.cuda.synchronize()
     l0 = igafd.kernel_launches()
     a, c = ev(), ev()
+    torch.cuda.nvtx.range_push("solve")          # ncu --nvtx --nvtx-include "solve/"
     a.record()
     for _ in range(args.steps):
         _, infos = batch.solve(bs, xs)
     c.record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = igafd.kernel_launches() - l0
     batch_s = a.elapsed_time(c) / 1e3 / args.steps
     # algorithmic stencil bytes of the solve: every stencil launch streams the
