@@ -189,8 +189,9 @@ size_t igafd_stencil_args_bytes();
 igafd_status igafd_stencil_batch_args(igafd_patch *P, int sel, int flexible, int every, void *out,
                                       long long *vgrid);
 igafd_status igafd_stencil_batch_launch(int dim, int p, int rows, int sel, const void *args_dev,
-                                        const long long *item_start_dev, int nprob,
-                                        unsigned long long *queue, int num_sms, cudaStream_t s);
+                                        const int *act_idx, const long long *act_start,
+                                        const int *act_count, unsigned long long *queue,
+                                        int num_sms, cudaStream_t s);
 // batched solve (fd_tc.cu): true when the patch's tensor-core FD of operand
 // type dt runs as the generic fused kernels (so a batched launch can run it);
 // then the per-kind kernel arguments (FusedArgs bytes) and CTA counts

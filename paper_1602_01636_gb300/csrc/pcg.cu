@@ -194,29 +194,47 @@ struct VecArgs {             // one problem's PCG vectors and reduction state
   int flexible;
 };
 
-// One launch runs a PCG vector step of every unfinished problem: work item
-// (problem i, CTA v of i's own grid), items taken in a fixed stride by a
-// persistent grid. op 0: update_xr, 1: dot_rz of the iteration, 2: update_p.
-__global__ void __launch_bounds__(256) vec_batch_kernel(const VecArgs *args,
-                                                        const long long *item_start, int nprob,
-                                                        int op) {
-  const long long total = item_start[nprob];
-  __shared__ int s_prob;
+// One launch runs a PCG vector step of every listed (unfinished) problem:
+// work item (listed problem k, CTA v of its own grid), items taken in a fixed
+// stride by a persistent grid; act[k] is the problem, act_start[k] ..
+// act_start[k + 1] its items (the pass's compaction kernel writes the list).
+// op 0: update_xr, 1: dot_rz of the iteration, 2: update_p.
+constexpr int kVecCache = 128;
+__global__ void __launch_bounds__(256) vec_batch_kernel(const VecArgs *args, const int *act,
+                                                        const long long *act_start,
+                                                        const int *act_count, int op) {
+  __shared__ long long s_start[kVecCache + 1];
+  __shared__ int s_act[kVecCache];
   __shared__ VecArgs s_a;
+  const int n = *act_count;
+  const bool cached = n <= kVecCache;
+  if (cached) {
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) s_start[k] = act_start[k];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s_act[k] = act[k];
+  }
+  __syncthreads();
+  const long long *st = cached ? s_start : act_start;
+  const int *ax = cached ? s_act : act;
+  const long long total = n > 0 ? st[n] : 0;
+  int cur = -1;                      // listed problem whose arguments s_a holds
   for (long long it = blockIdx.x; it < total; it += gridDim.x) {
-    if (threadIdx.x == 0) {
-      int lo = 0, hi = nprob - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (item_start[mid] <= it) lo = mid; else hi = mid - 1;
-      }
-      s_prob = lo;
-      s_a = args[lo];
+    int lo = 0, hi = n - 1;          // every thread searches the (shared) list
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (st[mid] <= it) lo = mid; else hi = mid - 1;
     }
-    __syncthreads();
-    const VecArgs a = s_a;
-    const long long vb = it - item_start[s_prob], vg = item_start[s_prob + 1] - item_start[s_prob];
-    __syncthreads();                       // s_prob, s_a are rewritten by the next item
+    if (lo != cur) {
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        const unsigned *src = reinterpret_cast<const unsigned *>(&args[ax[lo]]);
+        unsigned *dst = reinterpret_cast<unsigned *>(&s_a);
+        for (int w = threadIdx.x; w < (int)(sizeof(VecArgs) / 4); w += 32) dst[w] = src[w];
+      }
+      __syncthreads();
+      cur = lo;
+    }
+    const VecArgs &a = s_a;
+    const long long vb = it - st[lo], vg = st[lo + 1] - st[lo];
     if (a.scal[S_DONE] != 0.0) continue;   // uniform over the CTA
     if (op == 0)
       update_xr_cta(a.x, a.r, a.p, a.q, a.z, a.N, a.scal, a.partial, a.counter, a.flexible, a.coef,
@@ -225,6 +243,59 @@ __global__ void __launch_bounds__(256) vec_batch_kernel(const VecArgs *args,
       dot_rz_cta(a.r, a.z, a.N, a.scal, a.partial, a.counter, 0, a.flexible, a.coef, vb, vg);
     else
       update_p_cta(a.p, a.z, a.N, a.scal, vb, vg);
+  }
+}
+
+// The lists of one stencil class for a pass (device pointers).
+struct ClassTab {
+  int nmem;
+  const int *prob;                  // problem of each member (the class's order)
+  const long long *vg[3];           // its CTAs (work items) per stencil mode
+  int *act_idx;                     // out: members of the unfinished problems, in order
+  long long *act_start[3];          // out: their item prefix per mode
+  int *act_count;
+};
+
+struct VecTab {
+  int n;
+  const long long *vg;              // CTAs of the vector kernels per problem
+  int *act;                         // out: unfinished problems
+  long long *act_start;             // out: their item prefix
+  int *act_count;
+};
+
+// Start of a pass: the unfinished problems of every stencil class and of the
+// vector kernels, with their work-item prefixes (one thread per list).
+__global__ void batch_compact_kernel(const ClassTab *tabs, int nclass, VecTab vt,
+                                     double *const *scal) {
+  const int t = threadIdx.x;
+  if (t < nclass) {
+    const ClassTab c = tabs[t];
+    int k = 0;
+    long long acc[3] = {0, 0, 0};
+    for (int m = 0; m < c.nmem; ++m) {
+      if (scal[c.prob[m]][S_FIN] != 0.0) continue;
+      c.act_idx[k] = m;
+      for (int sel = 0; sel < 3; ++sel) {
+        c.act_start[sel][k] = acc[sel];
+        acc[sel] += c.vg[sel][m];
+      }
+      ++k;
+    }
+    for (int sel = 0; sel < 3; ++sel) c.act_start[sel][k] = acc[sel];
+    *c.act_count = k;
+  } else if (t == nclass) {
+    int k = 0;
+    long long acc = 0;
+    for (int i = 0; i < vt.n; ++i) {
+      if (scal[i][S_FIN] != 0.0) continue;
+      vt.act[k] = i;
+      vt.act_start[k] = acc;
+      acc += vt.vg[i];
+      ++k;
+    }
+    vt.act_start[k] = acc;
+    *vt.act_count = k;
   }
 }
 
@@ -679,7 +750,9 @@ struct BatchClass {             // problems whose stencil shares (dim, p, rows)
   int dim, p, rows;
   std::vector<int> members;     // largest work item first (shorter tails of the queue)
   void *args[3];                // StencilArgs per member, for sel 0, 1, 2 (device)
-  long long *start[3];          // item prefix per sel (device)
+  int *act_idx;                 // the pass's list of unfinished members (device)
+  long long *act_start[3];      // and their item prefix per sel (device)
+  int *act_count;
   unsigned long long *queue;    // the class's work-queue counter (device)
   cudaStream_t side;            // capture stream of its branch (classes run concurrently)
   cudaEvent_t done;
@@ -698,8 +771,12 @@ struct igafd_batch {
   int fused_total[3];
   size_t fused_smem;
   VecArgs *vec_args;            // per problem (device)
-  long long *vec_start;         // items of the vector kernels (device)
-  long long vec_total;
+  int *vec_act;                 // the pass's list of unfinished problems (device)
+  long long *vec_act_start;
+  int *vec_act_count;
+  long long vec_total;          // items of the vector kernels over all problems
+  ClassTab *tabs;               // the classes' list tables (device)
+  VecTab vtab;
   double **scal_ptrs;           // per problem (device)
   unsigned *passes;             // loop passes (device)
   cudaEvent_t fork;             // start of a forked stencil phase
@@ -728,8 +805,8 @@ static igafd_status batch_body(igafd_batch *B, cudaStream_t s, cudaGraphConditio
   const int nvb = B->num_sms * 8;
   auto vec = [&](int op) -> igafd_status {
     const long long want = B->vec_total < nvb ? B->vec_total : nvb;
-    vec_batch_kernel<<<(unsigned)(want > 0 ? want : 1), 256, 0, s>>>(B->vec_args, B->vec_start,
-                                                                     B->count, op);
+    vec_batch_kernel<<<(unsigned)(want > 0 ? want : 1), 256, 0, s>>>(
+        B->vec_args, B->vec_act, B->vec_act_start, B->vec_act_count, op);
     IGAFD_LAUNCHED(1);
     IGAFD_CUDA(cudaGetLastError());
     return IGAFD_OK;
@@ -742,14 +819,16 @@ static igafd_status batch_body(igafd_batch *B, cudaStream_t s, cudaGraphConditio
       BatchClass &c = B->classes[i];
       cudaStream_t cs = i == 0 ? s : c.side;
       if (i > 0) IGAFD_CUDA(cudaStreamWaitEvent(cs, B->fork, 0));
-      IGAFD_TRY(igafd_stencil_batch_launch(c.dim, c.p, c.rows, sel, c.args[sel], c.start[sel],
-                                           (int)c.members.size(), c.queue, B->num_sms, cs));
+      IGAFD_TRY(igafd_stencil_batch_launch(c.dim, c.p, c.rows, sel, c.args[sel], c.act_idx,
+                                           c.act_start[sel], c.act_count, c.queue, B->num_sms, cs));
       if (i > 0) IGAFD_CUDA(cudaEventRecord(c.done, cs));
     }
     for (size_t i = 1; i < B->classes.size(); ++i)
       IGAFD_CUDA(cudaStreamWaitEvent(s, B->classes[i].done, 0));
     return IGAFD_OK;
   };
+  batch_compact_kernel<<<1, 64, 0, s>>>(B->tabs, (int)B->classes.size(), B->vtab, B->scal_ptrs);
+  IGAFD_LAUNCHED(1);                                        // the pass's unfinished problems
   IGAFD_TRY(stencil(0));                                    // q = A p, alpha
   IGAFD_TRY(vec(0));                                        // x, r, (r, r), stopping test
   if (B->o.true_every > 0) IGAFD_TRY(stencil(1));           // periodic true residual
@@ -836,6 +915,7 @@ extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int coun
     c->members.push_back(i);
   }
   std::vector<unsigned char> tmp_args(sab);
+  std::vector<ClassTab> ctabs;
   for (BatchClass &c : B->classes) {
     // largest item (tiles per CTA of the problem's own grid) first
     std::vector<std::pair<double, int>> order;
@@ -854,22 +934,37 @@ extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int coun
     if (cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess)
       return fail(IGAFD_ERR_CUDA);
+    ClassTab tab{};
+    tab.nmem = (int)c.members.size();
     for (int sel = 0; sel < 3; ++sel) {
       std::vector<unsigned char> args(sab * c.members.size());
-      std::vector<long long> start(c.members.size() + 1, 0);
+      std::vector<long long> vgs(c.members.size(), 0);
       for (size_t m = 0; m < c.members.size(); ++m) {
-        long long vg = 0;
         st = igafd_stencil_batch_args(B->ps[c.members[m]], sel, B->flex, o.true_every,
-                                      args.data() + m * sab, &vg);
+                                      args.data() + m * sab, &vgs[m]);
         if (st != IGAFD_OK) return fail(st);
-        start[m + 1] = start[m] + vg;
       }
       unsigned char *ad = nullptr;
       if ((st = batch_upload(B, args, &ad)) != IGAFD_OK) return fail(st);
       c.args[sel] = ad;
-      if ((st = batch_upload(B, start, &c.start[sel])) != IGAFD_OK) return fail(st);
+      long long *vgd = nullptr;
+      if ((st = batch_upload(B, vgs, &vgd)) != IGAFD_OK) return fail(st);
+      tab.vg[sel] = vgd;
+      std::vector<long long> zero(c.members.size() + 1, 0);
+      if ((st = batch_upload(B, zero, &c.act_start[sel])) != IGAFD_OK) return fail(st);
+      tab.act_start[sel] = c.act_start[sel];
     }
+    std::vector<int> prob(c.members.begin(), c.members.end()), zi(c.members.size(), 0), z1(1, 0);
+    int *pd = nullptr;
+    if ((st = batch_upload(B, prob, &pd)) != IGAFD_OK) return fail(st);
+    tab.prob = pd;
+    if ((st = batch_upload(B, zi, &c.act_idx)) != IGAFD_OK) return fail(st);
+    if ((st = batch_upload(B, z1, &c.act_count)) != IGAFD_OK) return fail(st);
+    tab.act_idx = c.act_idx;
+    tab.act_count = c.act_count;
+    ctabs.push_back(tab);
   }
+  if ((st = batch_upload(B, ctabs, &B->tabs)) != IGAFD_OK) return fail(st);
   // FD: problems on the generic fused tensor-core kernels run batched
   const size_t fab = igafd_fd_fused_args_bytes();
   std::vector<unsigned char> fargs[3];
@@ -904,18 +999,25 @@ extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int coun
   }
   // vector kernels, scalars, queue, pass counter
   std::vector<VecArgs> va(count);
-  std::vector<long long> vs(count + 1, 0);
+  std::vector<long long> vgv(count, 0), vzero(count + 1, 0);
+  std::vector<int> izero(count, 0), i1(1, 0);
   std::vector<double *> sp(count);
+  B->vec_total = 0;
   for (int i = 0; i < count; ++i) {
     igafd_patch *P = B->ps[i];
     va[i] = VecArgs{P->xs, P->r, P->pv, P->q, P->z, P->scal, P->partial, P->coef, P->counter,
                     P->N, B->flex};
-    vs[i + 1] = vs[i] + igafd_red_blocks(P->N);
+    vgv[i] = igafd_red_blocks(P->N);
+    B->vec_total += vgv[i];
     sp[i] = P->scal;
   }
-  B->vec_total = vs[count];
   if ((st = batch_upload(B, va, &B->vec_args)) != IGAFD_OK) return fail(st);
-  if ((st = batch_upload(B, vs, &B->vec_start)) != IGAFD_OK) return fail(st);
+  long long *vgd = nullptr;
+  if ((st = batch_upload(B, vgv, &vgd)) != IGAFD_OK) return fail(st);
+  if ((st = batch_upload(B, izero, &B->vec_act)) != IGAFD_OK) return fail(st);
+  if ((st = batch_upload(B, vzero, &B->vec_act_start)) != IGAFD_OK) return fail(st);
+  if ((st = batch_upload(B, i1, &B->vec_act_count)) != IGAFD_OK) return fail(st);
+  B->vtab = VecTab{count, vgd, B->vec_act, B->vec_act_start, B->vec_act_count};
   if ((st = batch_upload(B, sp, &B->scal_ptrs)) != IGAFD_OK) return fail(st);
   if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess)
     return fail(IGAFD_ERR_CUDA);

@@ -389,20 +389,25 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
   stencil_cta<DIM, P, MODE, kStages, R>(a, blockIdx.x, gridDim.x, ring, full, empty, gstage, &s_abort);
 }
 
-// Many problems in one persistent launch: every CTA takes work items
-// (problem i, virtual CTA v) from an atomic queue, in order, and runs CTA v of
-// problem i's own single-problem grid (vgrid_i CTAs) -- the same tiles, the
-// same fused dot and the same last-CTA sum -- so each problem's result is
-// bitwise that of its own launch. item_start[i] .. item_start[i + 1] are
-// problem i's items. sel: 0 = q = A p of the PCG iteration (problems not yet
-// done), 1 = the periodic true residual (running problems whose iteration
-// count is a multiple of args.every), 2 = the convergence confirmation
-// (problems the recurrence says converged, status ok, not yet finished).
-// The ring's barriers persist across items (one running stage count).
+// Many problems in one persistent launch: every CTA takes work items from
+// an atomic queue, in order, each item (problem i, virtual CTA v) running CTA
+// v of problem i's own single-problem grid -- the same tiles, the same fused
+// dot and the same last-CTA sum -- so each problem's result is bitwise that
+// of its own launch. Only the problems still unfinished at the start of the
+// pass are listed (the pass's compaction kernel writes the list): act_idx[k]
+// is the k-th listed problem's row of args, act_start[k] .. act_start[k + 1]
+// its items, *act_count the list's length. sel: 0 = q = A p of the PCG
+// iteration (problems not yet done), 1 = the periodic true residual (running
+// problems whose iteration count is a multiple of args.every), 2 = the
+// convergence confirmation (problems the recurrence says converged, status
+// ok, not yet finished). The ring's barriers persist across items (one
+// running stage count); the list is cached in shared memory when short.
+constexpr int kListCache = 64;
 template <int DIM, int P, int MODE, int kStages, int R>
 __global__ void __launch_bounds__(kTile / R + 32) stencil_batch_kernel(const StencilArgs *args,
-                                                                      const long long *item_start,
-                                                                      int nprob, int sel,
+                                                                      const int *act_idx,
+                                                                      const long long *act_start,
+                                                                      const int *act_count, int sel,
                                                                       unsigned long long *queue) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double *ring = reinterpret_cast<double *>(smem_raw);
@@ -410,45 +415,61 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_batch_kernel(const Ste
   uint64_t *empty = full + kStages;
   __shared__ volatile int s_abort;
   __shared__ long long s_item;
-  __shared__ int s_prob, s_run;
+  __shared__ int s_k, s_run;
   __shared__ StencilArgs s_args;
-  const long long total = item_start[nprob];
+  __shared__ long long s_start[kListCache + 1];
+  __shared__ int s_idx[kListCache];
+  const int n = *act_count;
+  const bool cached = n <= kListCache;
+  if (cached) {
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) s_start[k] = act_start[k];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s_idx[k] = act_idx[k];
+  }
   if (threadIdx.x == 0) {
     ring_init<kStages, kTile / R>(full, empty);
     s_abort = 0;
   }
   __syncthreads();
+  const long long *st = cached ? s_start : act_start;
+  const int *ix = cached ? s_idx : act_idx;
+  const long long total = n > 0 ? st[n] : 0;
   long long gstage = 0;
   for (;;) {
     if (threadIdx.x == 0) {
-      const long long it = (long long)atomicAdd(queue, 1ull);
+      const long long it = total > 0 ? (long long)atomicAdd(queue, 1ull) : total;
       s_item = it;
       if (it < total) {
-        int lo = 0, hi = nprob - 1;             // last problem with item_start <= it
+        int lo = 0, hi = n - 1;                 // last listed problem with start <= it
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
-          if (item_start[mid] <= it) lo = mid; else hi = mid - 1;
+          if (st[mid] <= it) lo = mid; else hi = mid - 1;
         }
-        s_prob = lo;
-        const double *sc = args[lo].scal;
+        s_k = lo;
+        const StencilArgs &ag = args[ix[lo]];
+        const double *sc = ag.scal;
         const bool done = sc[S_DONE] != 0.0;
         bool run;
         if (sel == 0) run = !done;
-        else if (sel == 1) run = !done && args[lo].every > 0 &&
-                                 ((long long)sc[S_ITER]) % args[lo].every == 0;
+        else if (sel == 1) run = !done && ag.every > 0 && ((long long)sc[S_ITER]) % ag.every == 0;
         else run = done && sc[S_STATUS] == 0.0 && sc[S_FIN] == 0.0;
         s_run = run ? 1 : 0;
-        if (run) s_args = args[lo];
       }
     }
     __syncthreads();
     const long long it = s_item;
     if (it >= total) break;
     if (s_run) {
-      const int i = s_prob;
-      stencil_cta<DIM, P, MODE, kStages, R>(s_args, it - item_start[i],
-                                            item_start[i + 1] - item_start[i], ring, full, empty,
-                                            gstage, &s_abort);
+      // the problem's arguments, copied by one warp
+      if (threadIdx.x < 32) {
+        const int words = (int)(sizeof(StencilArgs) / 4);
+        const unsigned *src = reinterpret_cast<const unsigned *>(&args[ix[s_k]]);
+        unsigned *dst = reinterpret_cast<unsigned *>(&s_args);
+        for (int w = threadIdx.x; w < words; w += 32) dst[w] = src[w];
+      }
+      __syncthreads();
+      const int k = s_k;
+      stencil_cta<DIM, P, MODE, kStages, R>(s_args, it - st[k], st[k + 1] - st[k], ring, full,
+                                            empty, gstage, &s_abort);
     }
     __syncthreads();
     if (s_abort) break;
@@ -535,8 +556,9 @@ igafd_status launch_p(int p, int stages, int rows, const StencilArgs &a, long lo
 
 // ---- batched launches (one persistent launch for many problems) ----------
 template <int DIM, int P, int MODE, int R>
-igafd_status batch_launch_one(const StencilArgs *args, const long long *item_start, int nprob,
-                              int sel, unsigned long long *queue, int num_sms, cudaStream_t s) {
+igafd_status batch_launch_one(const StencilArgs *args, const int *act_idx, const long long *act_start,
+                              const int *act_count, int sel, unsigned long long *queue, int num_sms,
+                              cudaStream_t s) {
   constexpr int kStages = kStagesDefault;
   const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
   constexpr int kBlock = kTile / R + 32;
@@ -547,20 +569,21 @@ igafd_status batch_launch_one(const StencilArgs *args, const long long *item_sta
   IGAFD_TRY(per_sm_of(kern, kBlock, smem, attr_set, per_sm_tab, &per_sm));
   const unsigned grid = (unsigned)(num_sms * per_sm);
   IGAFD_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
-  kern<<<grid, kBlock, smem, s>>>(args, item_start, nprob, sel, queue);
+  kern<<<grid, kBlock, smem, s>>>(args, act_idx, act_start, act_count, sel, queue);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 
 template <int DIM, int MODE>
-igafd_status batch_launch_p(int p, int rows, const StencilArgs *args, const long long *item_start,
-                            int nprob, int sel, unsigned long long *queue, int sms, cudaStream_t s) {
-#define IGAFD_BATCH_P(PP)                                                                     \
-  case PP:                                                                                     \
-    if (DIM == 3 && rows == 2)                                                                 \
-      return batch_launch_one<DIM, PP, MODE, 2>(args, item_start, nprob, sel, queue, sms, s); \
-    return batch_launch_one<DIM, PP, MODE, 1>(args, item_start, nprob, sel, queue, sms, s);
+igafd_status batch_launch_p(int p, int rows, const StencilArgs *args, const int *ai,
+                            const long long *as, const int *ac, int sel, unsigned long long *queue,
+                            int sms, cudaStream_t s) {
+#define IGAFD_BATCH_P(PP)                                                              \
+  case PP:                                                                              \
+    if (DIM == 3 && rows == 2)                                                          \
+      return batch_launch_one<DIM, PP, MODE, 2>(args, ai, as, ac, sel, queue, sms, s); \
+    return batch_launch_one<DIM, PP, MODE, 1>(args, ai, as, ac, sel, queue, sms, s);
   switch (p) {
     IGAFD_BATCH_P(1)
     IGAFD_BATCH_P(2)
@@ -666,16 +689,18 @@ igafd_status igafd_stencil_batch_args(igafd_patch *P, int sel, int flexible, int
   return launch_p<2, 0>(P->p, st, 1, a, cap, P->num_sms, nullptr, vgrid);
 }
 
-// One persistent launch over the problems of one class (dim, p, rows per
-// thread): args_dev [nprob] StencilArgs, item_start_dev [nprob + 1].
+// One persistent launch over the listed (unfinished) problems of one class
+// (dim, p, rows per thread): args_dev [members] StencilArgs, act_* the
+// pass's list (see stencil_batch_kernel).
 igafd_status igafd_stencil_batch_launch(int dim, int p, int rows, int sel, const void *args_dev,
-                                        const long long *item_start_dev, int nprob,
-                                        unsigned long long *queue, int num_sms, cudaStream_t s) {
+                                        const int *act_idx, const long long *act_start,
+                                        const int *act_count, unsigned long long *queue,
+                                        int num_sms, cudaStream_t s) {
   const StencilArgs *args = (const StencilArgs *)args_dev;
   if (dim == 3) {
-    if (sel) return batch_launch_p<3, 1>(p, rows, args, item_start_dev, nprob, sel, queue, num_sms, s);
-    return batch_launch_p<3, 0>(p, rows, args, item_start_dev, nprob, sel, queue, num_sms, s);
+    if (sel) return batch_launch_p<3, 1>(p, rows, args, act_idx, act_start, act_count, sel, queue, num_sms, s);
+    return batch_launch_p<3, 0>(p, rows, args, act_idx, act_start, act_count, sel, queue, num_sms, s);
   }
-  if (sel) return batch_launch_p<2, 1>(p, 1, args, item_start_dev, nprob, sel, queue, num_sms, s);
-  return batch_launch_p<2, 0>(p, 1, args, item_start_dev, nprob, sel, queue, num_sms, s);
+  if (sel) return batch_launch_p<2, 1>(p, 1, args, act_idx, act_start, act_count, sel, queue, num_sms, s);
+  return batch_launch_p<2, 0>(p, 1, args, act_idx, act_start, act_count, sel, queue, num_sms, s);
 }
