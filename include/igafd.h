@@ -239,34 +239,73 @@ igafd_status igafd_pcg_solve(igafd_patch *patch, const igafd_pcg_opts *opts,
 
 /* Batched solve of count independent problems A_i x_i = b_i (one per patch,
  * patches on the same device, each at most once) with the same options,
- * driven on the device: one CUDA graph whose conditional while-node repeats
- * one PCG iteration of every unfinished problem until all are finished, each
+ * driven on the device. The problems are split into groups (below); a
+ * group's loop is a CUDA graph whose conditional while-node repeats one PCG
+ * iteration (a pass) of every unfinished member until all are finished, each
  * problem with its own device convergence state (recurrence test, true-
- * residual confirmation and restart, iteration cap, breakdown). An iteration
- * is a few launches over all problems: the stencil as one persistent launch
- * per (dim, p, rows per thread) class whose CTAs take (problem, CTA) work
- * items from a device queue, the vector updates and dot products as one
- * launch each, and the tensor-core FD as one launch per kernel kind for
- * problems on the fused kernels (other FD forms run their own launches).
- * Each work item is a CTA of the problem's own single-problem grid, so the
- * results are bitwise those of igafd_pcg_solve on each problem.
+ * residual confirmation and restart, iteration cap, breakdown), and the
+ * groups' loops run concurrently, each on its own stream. A pass is a few
+ * launches over the group's unfinished members (a compaction kernel lists
+ * them first): the stencil as one launch per (dim, p, ring stages, rows per
+ * thread) class over (problem, CTA) work items, the vector updates and dot
+ * products as one launch each, and the tensor-core FD as one launch per
+ * kernel kind for problems on the fused kernels (other FD forms run their
+ * own launches). In a group of several problems the stencil and FD CTAs are
+ * persistent and take work items from a device queue; a group of one
+ * problem launches its single solve's grids. Each work item is a CTA of the
+ * problem's own single-problem grid, so the results are bitwise those of
+ * igafd_pcg_solve on each problem.
  *
  * igafd_batch_create allocates the batch's device tables and builds the
- * graph for these patches and options (opts->check_every and timing are not
+ * graphs for these patches and options (opts->check_every and timing are not
  * used); it must be re-created when a patch's autotuned choices or its
  * preconditioner set-up change. igafd_batch_solve allocates nothing: b[i],
  * x[i] are device vectors of patch i's size (x[i] the initial guess when
  * opts->x0_given); infos (optional) receives one igafd_pcg_info per problem.
- * It synchronises the stream twice (before the loop, to read every (b, b),
- * and after it). Returns the first non-OK problem status (OK if all
- * converged; IGAFD_ERR_TIMEOUT for a problem still unfinished when the loop
- * guard of 2 max_iter + 16 passes ran out). Errors: ARG, OOM, CUDA. */
+ * It synchronises the stream twice (before the loops, to read every (b, b),
+ * and after them). Returns the first non-OK problem status (OK if all
+ * converged; IGAFD_ERR_TIMEOUT for a problem still unfinished when its
+ * loop's guard of 2 max_iter + 16 passes ran out). Errors: ARG, OOM, CUDA. */
 typedef struct igafd_batch igafd_batch;
 igafd_status igafd_batch_create(igafd_patch *const *patches, int count,
                                 const igafd_pcg_opts *opts, igafd_batch **out);
+
+/* igafd_batch_create with the problems split into `groups` groups (0 or more
+ * than count: one per problem): consecutive runs of the problems ordered by
+ * the stencil work of an iteration, of near-equal total work, so that each
+ * group holds problems of like size. Each group runs the loop above over its
+ * own members, as its own graph on its own stream, so the groups' loops run
+ * concurrently and a group of problems that need few iterations does not
+ * wait for the others; lighter groups get the higher stream priority. With
+ * passes_per_launch > 0 a launch of a group's graph ends after that many
+ * passes and igafd_batch_solve launches it again while members are
+ * unfinished (it polls the launches' completion events); 0 runs each group's
+ * whole loop in one launch. Iterates are bitwise those of single solves
+ * whatever the grouping. igafd_batch_create is the call with one group per
+ * problem (groups = 0) for up to 64 problems, else 64 groups, and
+ * passes_per_launch = 0. Errors: ARG (also groups or passes_per_launch < 0),
+ * OOM, CUDA. */
+igafd_status igafd_batch_create_grouped(igafd_patch *const *patches, int count,
+                                        const igafd_pcg_opts *opts, int groups,
+                                        int passes_per_launch, igafd_batch **out);
+
+/* The number of groups and (group_of, optional: count ints, host) each
+ * problem's group. Errors: ARG. */
+igafd_status igafd_batch_groups(const igafd_batch *batch, int *groups, int *group_of);
 igafd_status igafd_batch_solve(igafd_batch *batch, const double *const *b_dev,
                                double *const *x_dev, igafd_pcg_info *infos, void *stream);
 void igafd_batch_destroy(igafd_batch *batch);
+
+/* Device-clock record of group `group`'s loop in the last igafd_batch_solve,
+ * one entry per pass (an iteration of each unfinished member): start_us[k]
+ * its start relative to the earliest pass of any group, dur_us[k] its length
+ * (globaltimer, us) and active[k] the members unfinished at its start. Host
+ * arrays of cap entries (cap may be 0 to query the count); *npasses receives
+ * the number of recorded passes (the first min(passes, 65536)). Synchronous
+ * copies; call after the solve's stream has been synchronised. Errors: ARG
+ * (also a group out of range), CUDA. */
+igafd_status igafd_batch_pass_log(const igafd_batch *batch, int group, int cap, double *start_us,
+                                  double *dur_us, int *active, int *npasses);
 
 /* igafd_batch_create, igafd_batch_solve and igafd_batch_destroy in one call
  * (allocates and frees the batch's tables each time). */

@@ -188,10 +188,12 @@ long long igafd_stencil_row_stride(long long N);   // Np for a given N
 size_t igafd_stencil_args_bytes();
 igafd_status igafd_stencil_batch_args(igafd_patch *P, int sel, int flexible, int every, void *out,
                                       long long *vgrid);
-igafd_status igafd_stencil_batch_launch(int dim, int p, int rows, int sel, const void *args_dev,
-                                        const int *act_idx, const long long *act_start,
-                                        const int *act_count, unsigned long long *queue,
-                                        int num_sms, cudaStream_t s);
+igafd_status igafd_stencil_batch_launch(int dim, int p, int stages, int rows, int sel,
+                                        const void *args_dev, const int *act_idx,
+                                        const long long *act_start, const int *act_count,
+                                        unsigned long long *queue, long long items, int num_sms,
+                                        cudaStream_t s);
+int igafd_stencil_batch_stages(const igafd_patch *P);
 // batched solve (fd_tc.cu): true when the patch's tensor-core FD of operand
 // type dt runs as the generic fused kernels (so a batched launch can run it);
 // then the per-kind kernel arguments (FusedArgs bytes) and CTA counts
@@ -199,10 +201,15 @@ bool igafd_fd_tc_fused_generic(const igafd_patch *P, igafd_dtype dt);
 size_t igafd_fd_fused_args_bytes();
 igafd_status igafd_fd_fused_batch_args(igafd_patch *P, igafd_dtype dt, void *args3, int *blocks3,
                                        size_t *smem);
-// one batched launch of fused kind (0 slab forward, 1 pencil, 2 slab backward)
+// one batched launch of fused kind (0 slab forward, 1 pencil, 2 slab
+// backward) over the listed problems: act (indices into the args), their CTA
+// prefix act_start for this kind, *act_count and the zeroed work-queue counter
+// (device; persistent CTAs) or null (one CTA per item); total_blocks bounds
+// the items
 igafd_status igafd_fd_fused_batch_launch(igafd_dtype dt, int kind, const void *args_dev,
-                                         const int *block_start_dev, int nprob, int total_blocks,
-                                         size_t smem, cudaStream_t s);
+                                         const int *act, const int *act_start,
+                                         const int *act_count, unsigned *queue, int total_blocks,
+                                         size_t smem, int num_sms, cudaStream_t s);
 // number of CTAs of the PCG vector kernels for N dofs (the same in single and
 // batched solves, so their reductions agree bitwise)
 int igafd_red_blocks(long long N);

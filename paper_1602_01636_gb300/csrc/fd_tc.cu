@@ -606,8 +606,41 @@ __device__ void stage_cols(unsigned char *R, const float *in, long long n12, lon
   }
 }
 
+// CTA resources of the fused kernels: the two mbarriers (B image copies, MMA
+// completions; each completes twice per block, so every block waits on
+// parities 0 then 1) and 128 TMEM columns, set up once per CTA.
+__device__ __forceinline__ void fused_init(uint64_t *bar_mma, uint64_t *bar_b, uint32_t *tmem_slot,
+                                           int *s_fail) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar_mma)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar_b)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *s_fail = 0;
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+        smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Release of the TMEM columns (after the last block's epilogue, which ends
+// with a CTA barrier).
+__device__ __forceinline__ void fused_fini(uint32_t tmem) {
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
+// One block (CTA tile) of a fused kernel on the CTA's resources; false when a
+// wait ran out (the error is recorded and the CTA must stop: its barriers'
+// phases are then unknown).
 template <int OP, int KIND>
-__device__ __forceinline__ void tc_fused_cta(const FusedArgs &a, const int blk) {
+__device__ __forceinline__ bool tc_fused_item(const FusedArgs &a, const int blk, const uint32_t tmem,
+                                              uint64_t *bar_mma_p, uint64_t *bar_b_p,
+                                              int *s_fail_p) {
   using T = Op<OP>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base =
@@ -615,9 +648,8 @@ __device__ __forceinline__ void tc_fused_cta(const FusedArgs &a, const int blk) 
   const int rowBytes = a.Kpad * T::kBytes;              // bytes of K per row
   unsigned char *R1 = base;                              // A operands: 128 rows
   unsigned char *R2 = base + (size_t)kM * rowBytes;      // B operands: up to 128 rows
-  __shared__ uint64_t bar_mma, bar_b;
-  __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  uint64_t &bar_mma = *bar_mma_p, &bar_b = *bar_b_p;
+  int &s_fail = *s_fail_p;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   auto wait_on = [&](uint64_t *b, uint32_t parity) -> bool {
@@ -688,21 +720,6 @@ __device__ __forceinline__ void tc_fused_cta(const FusedArgs &a, const int blk) 
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
   };
 
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_b)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_fail = 0;
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
-        smem_u32(&tmem_base)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_base;
   load_b(a.B1, a.Np1, a.Kp1);
 
   // ---- first A operand: rows = lanes of the first accumulator ----
@@ -816,7 +833,7 @@ __device__ __forceinline__ void tc_fused_cta(const FusedArgs &a, const int blk) 
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+  return s_fail == 0;
 }
 
 template <int OP, int KIND>
@@ -824,32 +841,79 @@ __global__ void __launch_bounds__(kThreads) tc_fused_kernel(FusedArgs a) {
   pdl_wait();
   pdl_trigger();
   if (a.done && *a.done != 0.0) return;
-  tc_fused_cta<OP, KIND>(a, blockIdx.x);
+  __shared__ uint64_t bar_mma, bar_b;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  fused_init(&bar_mma, &bar_b, &tmem_slot, &s_fail);
+  const uint32_t tmem = tmem_slot;
+  tc_fused_item<OP, KIND>(a, blockIdx.x, tmem, &bar_mma, &bar_b, &s_fail);
+  fused_fini(tmem);
 }
 
-// The same kernel for many problems in one launch: CTA b runs CTA
-// b - block_start[i] of problem i's own launch (block_start[i] <= b <
-// block_start[i + 1]), with problem i's arguments; problems whose PCG is done
-// are skipped as in their own launch.
+// The same kernel for many problems in one persistent launch: the work items
+// are (listed problem k, CTA b of its own launch), act_start[k] <= item <
+// act_start[k + 1], over the problems listed in act (indices into args; the
+// pass's compaction lists the unfinished ones, largest CTAs first, and zeroes
+// *queue). CTAs take items from the queue counter, with the barriers and TMEM
+// columns set up once; with a null queue CTA b runs item b only (a grid of
+// one CTA per item). Problems whose PCG is done are skipped as in their own
+// launch.
+constexpr int kFusedListCache = 128;
 template <int OP, int KIND>
 __global__ void __launch_bounds__(kThreads) tc_fused_batch_kernel(const FusedArgs *args,
-                                                                  const int *block_start, int nprob) {
+                                                                  const int *act,
+                                                                  const int *act_start,
+                                                                  const int *act_count,
+                                                                  unsigned *queue) {
   __shared__ FusedArgs s_a;
-  __shared__ int s_blk, s_run;
-  if (threadIdx.x == 0) {
-    const int b = (int)blockIdx.x;
-    int lo = 0, hi = nprob - 1;                 // last problem with block_start <= b
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (block_start[mid] <= b) lo = mid; else hi = mid - 1;
+  __shared__ int s_st[kFusedListCache + 1];
+  __shared__ int s_it, s_lo, s_run;
+  __shared__ uint64_t bar_mma, bar_b;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  const int n = *act_count;
+  const int total = n > 0 ? act_start[n] : 0;
+  if ((int)blockIdx.x >= total) return;              // uniform over the CTA
+  const bool cached = n <= kFusedListCache;
+  if (cached)
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) s_st[k] = act_start[k];
+  fused_init(&bar_mma, &bar_b, &tmem_slot, &s_fail);  // ends with a CTA barrier
+  const int *st = cached ? s_st : act_start;
+  const uint32_t tmem = tmem_slot;
+  int cur = -1;
+  bool first = true;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      // persistent: items from the queue; otherwise CTA b runs item b only
+      const int it = queue ? (int)atomicAdd(queue, 1u) : (first ? (int)blockIdx.x : total);
+      int lo = cur < 0 ? 0 : cur, hi = n - 1;       // a CTA's items ascend: search from its current one
+      if (it < total)
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (st[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+      s_it = it;
+      s_lo = lo;
     }
-    s_a = args[lo];
-    s_blk = b - block_start[lo];
-    s_run = (b < block_start[lo + 1]) && !(s_a.done && *s_a.done != 0.0);
+    __syncthreads();
+    const int it = s_it, lo = s_lo;
+    if (it >= total) break;                          // uniform
+    if (lo != cur) {
+      if (threadIdx.x < 32) {
+        const unsigned *src = reinterpret_cast<const unsigned *>(&args[act[lo]]);
+        unsigned *dst = reinterpret_cast<unsigned *>(&s_a);
+        for (int w = threadIdx.x; w < (int)(sizeof(FusedArgs) / 4); w += 32) dst[w] = src[w];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_run = !(s_a.done && *s_a.done != 0.0);
+      cur = lo;
+    }
+    __syncthreads();
+    first = false;
+    if (!s_run) continue;                            // uniform
+    if (!tc_fused_item<OP, KIND>(s_a, it - st[lo], tmem, &bar_mma, &bar_b, &s_fail)) break;
   }
-  __syncthreads();
-  if (!s_run) return;
-  tc_fused_cta<OP, KIND>(s_a, s_blk);
+  fused_fini(tmem);
 }
 
 // ---------------------------------------------------------------------------
@@ -1529,8 +1593,9 @@ igafd_status igafd_fd_fused_batch_args(igafd_patch *P, igafd_dtype dt, void *arg
 }
 
 template <int OP, int KIND>
-static igafd_status batch_fused(const FusedArgs *args, const int *block_start, int nprob,
-                                int total, size_t smem, cudaStream_t s) {
+static igafd_status batch_fused(const FusedArgs *args, const int *act, const int *act_start,
+                                const int *act_count, unsigned *queue, int total, size_t smem,
+                                int num_sms, cudaStream_t s) {
   static std::atomic<unsigned long long> attr_set{0};
   int dev = 0;
   IGAFD_CUDA(cudaGetDevice(&dev));
@@ -1540,23 +1605,37 @@ static igafd_status batch_fused(const FusedArgs *args, const int *block_start, i
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedMaxSmem));
     attr_set.fetch_or(bit);
   }
-  tc_fused_batch_kernel<OP, KIND><<<total, kThreads, smem, s>>>(args, block_start, nprob);
+  // persistent: the CTAs that fit on an SM at once, at most 4 (128 of the 512
+  // TMEM columns each), on every SM
+  int occ = 0;
+  IGAFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc_fused_batch_kernel<OP, KIND>,
+                                                           kThreads, smem));
+  occ = occ < 1 ? 1 : occ > 4 ? 4 : occ;
+  const long long cap = queue ? (long long)num_sms * occ : (long long)total;
+  const int grid = (int)(total < cap ? total : cap);
+  tc_fused_batch_kernel<OP, KIND><<<grid, kThreads, smem, s>>>(args, act, act_start, act_count,
+                                                                queue);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 
 igafd_status igafd_fd_fused_batch_launch(igafd_dtype dt, int kind, const void *args_dev,
-                                         const int *block_start_dev, int nprob, int total_blocks,
-                                         size_t smem, cudaStream_t s) {
+                                         const int *act, const int *act_start,
+                                         const int *act_count, unsigned *queue, int total_blocks,
+                                         size_t smem, int num_sms, cudaStream_t s) {
   if (total_blocks <= 0) return IGAFD_OK;
+  if (smem > (size_t)kFusedMaxSmem || num_sms < 1) return IGAFD_ERR_ARG;
   const FusedArgs *a = (const FusedArgs *)args_dev;
+#define IGAFD_BF(O, K) \
+  batch_fused<O, K>(a, act, act_start, act_count, queue, total_blocks, smem, num_sms, s)
   if (dt == IGAFD_TF32) {
-    if (kind == 0) return batch_fused<OP_TF32, SLAB_FWD>(a, block_start_dev, nprob, total_blocks, smem, s);
-    if (kind == 1) return batch_fused<OP_TF32, PENCIL>(a, block_start_dev, nprob, total_blocks, smem, s);
-    return batch_fused<OP_TF32, SLAB_BWD>(a, block_start_dev, nprob, total_blocks, smem, s);
+    if (kind == 0) return IGAFD_BF(OP_TF32, SLAB_FWD);
+    if (kind == 1) return IGAFD_BF(OP_TF32, PENCIL);
+    return IGAFD_BF(OP_TF32, SLAB_BWD);
   }
-  if (kind == 0) return batch_fused<OP_BF16, SLAB_FWD>(a, block_start_dev, nprob, total_blocks, smem, s);
-  if (kind == 1) return batch_fused<OP_BF16, PENCIL>(a, block_start_dev, nprob, total_blocks, smem, s);
-  return batch_fused<OP_BF16, SLAB_BWD>(a, block_start_dev, nprob, total_blocks, smem, s);
+  if (kind == 0) return IGAFD_BF(OP_BF16, SLAB_FWD);
+  if (kind == 1) return IGAFD_BF(OP_BF16, PENCIL);
+  return IGAFD_BF(OP_BF16, SLAB_BWD);
+#undef IGAFD_BF
 }

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -256,6 +257,16 @@ struct ClassTab {
   int *act_count;
 };
 
+struct FusedTab {
+  int nmem;
+  const int *prob;                  // problem of each fused member
+  const int *blocks[3];             // its CTAs per fused kernel kind
+  int *act;                         // out: the members of the unfinished problems
+  int *act_start[3];                // out: their CTA prefix per kind
+  int *act_count;
+  unsigned *queue;                  // out: the kinds' work-queue counters, zeroed
+};
+
 struct VecTab {
   int n;
   const long long *vg;              // CTAs of the vector kernels per problem
@@ -264,11 +275,26 @@ struct VecTab {
   int *act_count;
 };
 
+// Device-clock record of one pass of the batched loop.
+struct PassLog {
+  unsigned long long t0, t1;        // globaltimer (ns) at the pass's start and end
+  int active;                       // unfinished problems at its start
+  int pad;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Start of a pass: the unfinished problems of every stencil class and of the
 // vector kernels, with their work-item prefixes (one thread per list).
-__global__ void batch_compact_kernel(const ClassTab *tabs, int nclass, VecTab vt,
-                                     double *const *scal) {
+__global__ void batch_compact_kernel(const ClassTab *tabs, int nclass, VecTab vt, FusedTab ft,
+                                     double *const *scal, PassLog *log, const unsigned *passes,
+                                     unsigned log_cap) {
   const int t = threadIdx.x;
+  const unsigned long long t0 = global_ns();
   if (t < nclass) {
     const ClassTab c = tabs[t];
     int k = 0;
@@ -296,6 +322,27 @@ __global__ void batch_compact_kernel(const ClassTab *tabs, int nclass, VecTab vt
     }
     vt.act_start[k] = acc;
     *vt.act_count = k;
+    const unsigned n = *passes;
+    if (n < log_cap) {
+      log[n].t0 = t0;
+      log[n].active = k;
+    }
+  } else if (t == nclass + 1 && ft.nmem > 0) {
+    int k = 0, acc[3] = {0, 0, 0};
+    for (int m = 0; m < ft.nmem; ++m) {
+      if (scal[ft.prob[m]][S_FIN] != 0.0) continue;
+      ft.act[k] = m;
+      for (int kind = 0; kind < 3; ++kind) {
+        ft.act_start[kind][k] = acc[kind];
+        acc[kind] += ft.blocks[kind][m];
+      }
+      ++k;
+    }
+    for (int kind = 0; kind < 3; ++kind) {
+      ft.act_start[kind][k] = acc[kind];
+      ft.queue[kind] = 0u;
+    }
+    *ft.act_count = k;
   }
 }
 
@@ -322,20 +369,28 @@ __global__ void batch_decide_kernel(double *const *scal, int nprob) {
   }
 }
 
-// Loop condition of the batched solve: another iteration while any problem is
-// unfinished, bounded by `guard` passes (every problem finishes within its
-// iteration cap plus its confirmation restarts).
+// Loop condition of a group's loop: another pass while any member is
+// unfinished, bounded by `guard` passes in the solve (every problem finishes
+// within its iteration cap plus its confirmation restarts) and by `chunk`
+// passes per launch of the loop's graph (0: no bound); *more (host-mapped)
+// tells the host whether the group needs another launch.
 __global__ void batch_cond_kernel(cudaGraphConditionalHandle h, double *const *scal, int nprob,
-                                  unsigned *passes, unsigned guard) {
+                                  unsigned *passes, unsigned *lpasses, unsigned guard,
+                                  unsigned chunk, PassLog *log, unsigned log_cap,
+                                  volatile int *more_host) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   bool more = false;
   for (int i = 0; i < nprob && !more; ++i) more = scal[i][S_FIN] == 0.0;
-  const unsigned n = ++*passes;
-  cudaGraphSetConditional(h, (more && n < guard) ? 1u : 0u);
+  if (*passes < log_cap) log[*passes].t1 = global_ns();
+  const unsigned n = ++*passes, ln = ++*lpasses;
+  const bool again = more && n < guard;
+  cudaGraphSetConditional(h, (again && (chunk == 0 || ln < chunk)) ? 1u : 0u);
+  if (!(again && (chunk == 0 || ln < chunk))) *more_host = again ? 1 : 0;
 }
 
-__global__ void batch_reset_kernel(unsigned *passes) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *passes = 0u;
+// Start of a launch of a group's loop graph: its per-launch pass count.
+__global__ void batch_reset_kernel(unsigned *lpasses) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *lpasses = 0u;
 }
 
 __global__ void init_scalars_kernel(double *scal, double tol2, double maxit) {
@@ -746,19 +801,23 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
 // iterates are bitwise those of igafd_pcg_solve. The host synchronises once
 // before the loop (to read every (b, b)) and once after it.
 
-struct BatchClass {             // problems whose stencil shares (dim, p, rows)
-  int dim, p, rows;
+struct BatchClass {             // problems whose stencil shares (dim, p, ring stages, rows)
+  int dim, p, stages, rows;
   std::vector<int> members;     // largest work item first (shorter tails of the queue)
   void *args[3];                // StencilArgs per member, for sel 0, 1, 2 (device)
   int *act_idx;                 // the pass's list of unfinished members (device)
   long long *act_start[3];      // and their item prefix per sel (device)
+  long long items[3];           // work items of all members per sel
   int *act_count;
   unsigned long long *queue;    // the class's work-queue counter (device)
   cudaStream_t side;            // capture stream of its branch (classes run concurrently)
   cudaEvent_t done;
 };
 
-struct igafd_batch {
+// One group of a batch: problems that advance together, one pass (an
+// iteration of each unfinished member) per turn of the group's own
+// device-driven loop.
+struct BatchGroup {
   int count, dev, num_sms;
   igafd_pcg_opts o;
   int flex;
@@ -767,8 +826,8 @@ struct igafd_batch {
   std::vector<int> other_fd;    // problems whose FD is launched on its own
   int nfused;
   void *fused_args[3];          // FusedArgs per fused problem and kind (device)
-  int *fused_start[3];          // CTA prefix per kind (device)
-  int fused_total[3];
+  int fused_total[3];           // CTAs per kind over all fused problems
+  FusedTab ftab;                // the fused problems' list tables (device)
   size_t fused_smem;
   VecArgs *vec_args;            // per problem (device)
   int *vec_act;                 // the pass's list of unfinished problems (device)
@@ -778,17 +837,39 @@ struct igafd_batch {
   ClassTab *tabs;               // the classes' list tables (device)
   VecTab vtab;
   double **scal_ptrs;           // per problem (device)
-  unsigned *passes;             // loop passes (device)
+  unsigned *passes;             // loop passes in the solve (device)
+  unsigned *lpasses;            // loop passes in the current launch of the graph (device)
+  unsigned chunk;               // passes per launch (0: the whole solve in one launch)
+  int *more_host;               // pinned, mapped: the group needs another launch
+  int *more_dev;                // its device address
+  PassLog *pass_log;            // one record per pass of the last solve (device)
+  unsigned guard;               // pass bound of the loop
+  unsigned log_cap;             // records in pass_log (the first passes)
   cudaEvent_t fork;             // start of a forked stencil phase
   std::vector<void *> allocs;
-  cudaStream_t cap;
-  cudaGraph_t graph;
+  long long body_launches;      // launches of one pass (captured body)
+  bool persistent;              // stencil and FD as persistent work-queue launches
+  cudaGraph_t graph;            // the group's loop: reset, then while (unfinished) { pass }
   cudaGraphExec_t exec;
-  long long body_launches;
+  cudaStream_t stream;          // the loop's stream (groups run concurrently)
+  cudaEvent_t done;
+};
+
+// The batch: its groups' loops run concurrently, each its own graph launched
+// on its own stream (a group whose problems need few iterations does not wait
+// for the others).
+struct igafd_batch {
+  int count, dev, num_sms;
+  igafd_pcg_opts o;
+  std::vector<igafd_patch *> ps;
+  std::vector<BatchGroup *> groups;
+  std::vector<int> group_of;    // group of each problem
+  cudaStream_t cap;
+  cudaEvent_t fork;             // the caller's stream, before the loops
 };
 
 template <typename T>
-static igafd_status batch_upload(igafd_batch *B, const std::vector<T> &v, T **out) {
+static igafd_status batch_upload(BatchGroup *B, const std::vector<T> &v, T **out) {
   void *p = nullptr;
   if (cudaMalloc(&p, (v.empty() ? 1 : v.size()) * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
@@ -801,7 +882,7 @@ static igafd_status batch_upload(igafd_batch *B, const std::vector<T> &v, T **ou
 }
 
 // One PCG iteration of every problem (the while-node's body), enqueued on s.
-static igafd_status batch_body(igafd_batch *B, cudaStream_t s, cudaGraphConditionalHandle h) {
+static igafd_status batch_body(BatchGroup *B, cudaStream_t s, cudaGraphConditionalHandle h) {
   const int nvb = B->num_sms * 8;
   auto vec = [&](int op) -> igafd_status {
     const long long want = B->vec_total < nvb ? B->vec_total : nvb;
@@ -819,15 +900,18 @@ static igafd_status batch_body(igafd_batch *B, cudaStream_t s, cudaGraphConditio
       BatchClass &c = B->classes[i];
       cudaStream_t cs = i == 0 ? s : c.side;
       if (i > 0) IGAFD_CUDA(cudaStreamWaitEvent(cs, B->fork, 0));
-      IGAFD_TRY(igafd_stencil_batch_launch(c.dim, c.p, c.rows, sel, c.args[sel], c.act_idx,
-                                           c.act_start[sel], c.act_count, c.queue, B->num_sms, cs));
+      IGAFD_TRY(igafd_stencil_batch_launch(c.dim, c.p, c.stages, c.rows, sel, c.args[sel], c.act_idx,
+                                           c.act_start[sel], c.act_count, c.queue,
+                                           B->persistent ? 0 : c.items[sel], B->num_sms, cs));
       if (i > 0) IGAFD_CUDA(cudaEventRecord(c.done, cs));
     }
     for (size_t i = 1; i < B->classes.size(); ++i)
       IGAFD_CUDA(cudaStreamWaitEvent(s, B->classes[i].done, 0));
     return IGAFD_OK;
   };
-  batch_compact_kernel<<<1, 64, 0, s>>>(B->tabs, (int)B->classes.size(), B->vtab, B->scal_ptrs);
+  const int ct = ((int)B->classes.size() + 2 + 31) / 32 * 32;   // a thread per list
+  batch_compact_kernel<<<1, ct, 0, s>>>(B->tabs, (int)B->classes.size(), B->vtab, B->ftab,
+                                        B->scal_ptrs, B->pass_log, B->passes, B->log_cap);
   IGAFD_LAUNCHED(1);                                        // the pass's unfinished problems
   IGAFD_TRY(stencil(0));                                    // q = A p, alpha
   IGAFD_TRY(vec(0));                                        // x, r, (r, r), stopping test
@@ -836,29 +920,29 @@ static igafd_status batch_body(igafd_batch *B, cudaStream_t s, cudaGraphConditio
   batch_decide_kernel<<<(B->count + 127) / 128, 128, 0, s>>>(B->scal_ptrs, B->count);
   IGAFD_LAUNCHED(1);
   for (int k = 0; k < 3; ++k)                               // z = P^{-1} r (fused FD)
-    IGAFD_TRY(igafd_fd_fused_batch_launch(B->o.prec_dtype, k, B->fused_args[k],
-                                          B->fused_start[k], B->nfused, B->fused_total[k],
-                                          B->fused_smem, s));
+    IGAFD_TRY(igafd_fd_fused_batch_launch(B->o.prec_dtype, k, B->fused_args[k], B->ftab.act,
+                                          B->ftab.act_start[k], B->ftab.act_count,
+                                          B->persistent ? B->ftab.queue + k : nullptr,
+                                          B->fused_total[k], B->fused_smem, B->num_sms, s));
   for (int i : B->other_fd)                                 // z = P^{-1} r (own launches)
     IGAFD_TRY(fd_apply(B->ps[i], B->o.prec_dtype, B->ps[i]->r, B->ps[i]->z, s,
                        B->ps[i]->scal + S_DONE));
   IGAFD_TRY(vec(1));                                        // (r, z), beta
   IGAFD_TRY(vec(2));                                        // p = z + beta p
-  // bounded: every problem stops at its cap; a failed confirmation costs
-  // one pass without an iteration
-  const unsigned guard = (unsigned)(2 * B->o.max_iter + 16);
-  batch_cond_kernel<<<1, 32, 0, s>>>(h, B->scal_ptrs, B->count, B->passes, guard);
+  batch_cond_kernel<<<1, 32, 0, s>>>(h, B->scal_ptrs, B->count, B->passes, B->lpasses, B->guard,
+                                     B->chunk, B->pass_log, B->log_cap, B->more_dev);
   IGAFD_LAUNCHED(1);
   IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 
-extern "C" void igafd_batch_destroy(igafd_batch *B) {
+static void group_destroy(BatchGroup *B) {
   if (!B) return;
-  cudaSetDevice(B->dev);
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
-  if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->stream) cudaStreamDestroy(B->stream);
+  if (B->done) cudaEventDestroy(B->done);
+  if (B->more_host) cudaFreeHost(B->more_host);
   for (BatchClass &c : B->classes) {
     if (c.side) cudaStreamDestroy(c.side);
     if (c.done) cudaEventDestroy(c.done);
@@ -868,35 +952,33 @@ extern "C" void igafd_batch_destroy(igafd_batch *B) {
   delete B;
 }
 
-extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int count,
-                                           const igafd_pcg_opts *opts, igafd_batch **out) {
-  if (!out) return IGAFD_ERR_ARG;
+extern "C" void igafd_batch_destroy(igafd_batch *B) {
+  if (!B) return;
+  cudaSetDevice(B->dev);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->fork) cudaEventDestroy(B->fork);
+  for (BatchGroup *g : B->groups) group_destroy(g);
+  delete B;
+}
+
+// A group's device tables (options already checked; o.check_every = 1).
+static igafd_status group_create(igafd_patch *const *patches, int count, const igafd_pcg_opts &o,
+                                 BatchGroup **out) {
   *out = nullptr;
-  if (!patches || count < 1) return IGAFD_ERR_ARG;
-  igafd_pcg_opts o;
-  if (opts) o = *opts; else igafd_pcg_default_opts(&o);
-  if (!(o.tol >= 0.0) || o.max_iter < 0 || o.true_every < 0) return IGAFD_ERR_ARG;
-  if (o.prec_dtype < IGAFD_FP64 || o.prec_dtype > IGAFD_ADI) return IGAFD_ERR_ARG;
-  for (int i = 0; i < count; ++i) {
-    igafd_patch *P = patches[i];
-    if (!P || !P->stencil || P->dev != patches[0]->dev) return IGAFD_ERR_ARG;
-    if (o.prec_dtype == IGAFD_ADI && !P->adi) return IGAFD_ERR_ARG;
-    for (int j = 0; j < i; ++j)
-      if (patches[j] == P) return IGAFD_ERR_ARG;            // one problem per patch
-  }
-  IGAFD_CUDA(cudaSetDevice(patches[0]->dev));
-  igafd_batch *B = new igafd_batch{};
+  BatchGroup *B = new BatchGroup{};
   B->count = count;
   B->dev = patches[0]->dev;
   B->num_sms = patches[0]->num_sms;
-  o.timing = 0;
-  o.check_every = 1;            // the loop runs on the device; nothing is polled
   B->o = o;
   B->flex = o.flexible ? 1 : 0;
   B->ps.assign(patches, patches + count);
+  // a group of one problem launches the grids of its single solve (a CTA per
+  // item): CTAs then end after one item, so the concurrent groups' kernels
+  // interleave on the SMs instead of waiting for persistent CTAs to drain
+  B->persistent = count > 1;
   igafd_status st = IGAFD_OK;
   auto fail = [&](igafd_status e) {
-    igafd_batch_destroy(B);
+    group_destroy(B);
     return e;
   };
   // stencil classes and their work items
@@ -904,13 +986,14 @@ extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int coun
   for (int i = 0; i < count; ++i) {
     igafd_patch *P = B->ps[i];
     const int rows = P->dim == 3 && P->stencil_rows == 2 ? 2 : 1;
+    const int stages = igafd_stencil_batch_stages(P);
     BatchClass *c = nullptr;
     for (BatchClass &q : B->classes)
-      if (q.dim == P->dim && q.p == P->p && q.rows == rows) c = &q;
+      if (q.dim == P->dim && q.p == P->p && q.stages == stages && q.rows == rows) c = &q;
     if (!c) {
       B->classes.push_back(BatchClass{});
       c = &B->classes.back();
-      c->dim = P->dim; c->p = P->p; c->rows = rows;
+      c->dim = P->dim; c->p = P->p; c->stages = stages; c->rows = rows;
     }
     c->members.push_back(i);
   }
@@ -947,6 +1030,8 @@ extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int coun
       unsigned char *ad = nullptr;
       if ((st = batch_upload(B, args, &ad)) != IGAFD_OK) return fail(st);
       c.args[sel] = ad;
+      c.items[sel] = 0;
+      for (long long v : vgs) c.items[sel] += v;
       long long *vgd = nullptr;
       if ((st = batch_upload(B, vgs, &vgd)) != IGAFD_OK) return fail(st);
       tab.vg[sel] = vgd;
@@ -968,34 +1053,65 @@ extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int coun
   // FD: problems on the generic fused tensor-core kernels run batched
   const size_t fab = igafd_fd_fused_args_bytes();
   std::vector<unsigned char> fargs[3];
-  std::vector<int> fstart[3];
-  for (int k = 0; k < 3; ++k) fstart[k].push_back(0);
+  std::vector<int> fblocks[3], fprob;
   B->nfused = 0;
   B->fused_smem = 0;
+  struct FusedMember {
+    int i;
+    std::vector<unsigned char> a3;
+    int blocks[3];
+    size_t smem;
+  };
+  std::vector<FusedMember> fm;
   for (int i = 0; i < count; ++i) {
     igafd_patch *P = B->ps[i];
     if (!igafd_fd_tc_fused_generic(P, o.prec_dtype)) {
       B->other_fd.push_back(i);
       continue;
     }
-    std::vector<unsigned char> a3(3 * fab);
-    int blocks[3];
-    size_t smem = 0;
-    if ((st = igafd_fd_fused_batch_args(P, o.prec_dtype, a3.data(), blocks, &smem)) != IGAFD_OK)
+    FusedMember m{i, std::vector<unsigned char>(3 * fab), {0, 0, 0}, 0};
+    if ((st = igafd_fd_fused_batch_args(P, o.prec_dtype, m.a3.data(), m.blocks, &m.smem)) !=
+        IGAFD_OK)
       return fail(st);
+    fm.push_back(std::move(m));
+  }
+  // longest CTAs first (their K, which sizes the shared memory), so that the
+  // queue's last items are short
+  std::stable_sort(fm.begin(), fm.end(), [&](const FusedMember &a, const FusedMember &b) {
+    if (a.smem != b.smem) return a.smem > b.smem;
+    return B->ps[a.i]->N > B->ps[b.i]->N;
+  });
+  for (const FusedMember &m : fm) {
     for (int k = 0; k < 3; ++k) {
-      fargs[k].insert(fargs[k].end(), a3.begin() + k * fab, a3.begin() + (k + 1) * fab);
-      fstart[k].push_back(fstart[k].back() + blocks[k]);
+      fargs[k].insert(fargs[k].end(), m.a3.begin() + k * fab, m.a3.begin() + (k + 1) * fab);
+      fblocks[k].push_back(m.blocks[k]);
     }
-    if (smem > B->fused_smem) B->fused_smem = smem;
+    fprob.push_back(m.i);
+    if (m.smem > B->fused_smem) B->fused_smem = m.smem;
     ++B->nfused;
   }
-  for (int k = 0; k < 3; ++k) {
-    unsigned char *ad = nullptr;
-    if ((st = batch_upload(B, fargs[k], &ad)) != IGAFD_OK) return fail(st);
-    B->fused_args[k] = ad;
-    if ((st = batch_upload(B, fstart[k], &B->fused_start[k])) != IGAFD_OK) return fail(st);
-    B->fused_total[k] = B->nfused > 0 ? fstart[k].back() : 0;
+  B->ftab = FusedTab{};
+  B->ftab.nmem = B->nfused;
+  {
+    std::vector<int> zi(B->nfused + 1, 0), z1(1, 0);
+    int *pd = nullptr;
+    if ((st = batch_upload(B, fprob, &pd)) != IGAFD_OK) return fail(st);
+    B->ftab.prob = pd;
+    if ((st = batch_upload(B, zi, &B->ftab.act)) != IGAFD_OK) return fail(st);
+    if ((st = batch_upload(B, z1, &B->ftab.act_count)) != IGAFD_OK) return fail(st);
+    std::vector<unsigned> zq(3, 0u);
+    if ((st = batch_upload(B, zq, &B->ftab.queue)) != IGAFD_OK) return fail(st);
+    for (int k = 0; k < 3; ++k) {
+      unsigned char *ad = nullptr;
+      if ((st = batch_upload(B, fargs[k], &ad)) != IGAFD_OK) return fail(st);
+      B->fused_args[k] = ad;
+      int *bd = nullptr;
+      if ((st = batch_upload(B, fblocks[k], &bd)) != IGAFD_OK) return fail(st);
+      B->ftab.blocks[k] = bd;
+      if ((st = batch_upload(B, zi, &B->ftab.act_start[k])) != IGAFD_OK) return fail(st);
+      B->fused_total[k] = 0;
+      for (int b : fblocks[k]) B->fused_total[k] += b;
+    }
   }
   // vector kernels, scalars, queue, pass counter
   std::vector<VecArgs> va(count);
@@ -1023,51 +1139,199 @@ extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int coun
     return fail(IGAFD_ERR_CUDA);
   std::vector<unsigned> p1(1, 0);
   if ((st = batch_upload(B, p1, &B->passes)) != IGAFD_OK) return fail(st);
-  // the graph: reset the pass counter, then while (any unfinished) { body }
-  if (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(IGAFD_ERR_CUDA);
-  if (cudaGraphCreate(&B->graph, 0) != cudaSuccess) return fail(IGAFD_ERR_CUDA);
-  cudaGraphConditionalHandle h;
-  if (cudaGraphConditionalHandleCreate(&h, B->graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+  if ((st = batch_upload(B, p1, &B->lpasses)) != IGAFD_OK) return fail(st);
+  if (cudaHostAlloc(&B->more_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+    B->more_host = nullptr;
+    cudaGetLastError();
+    return fail(IGAFD_ERR_OOM);
+  }
+  *B->more_host = 0;
+  if (cudaHostGetDevicePointer((void **)&B->more_dev, B->more_host, 0) != cudaSuccess)
     return fail(IGAFD_ERR_CUDA);
+  B->guard = (unsigned)(2 * B->o.max_iter + 16);   // bounded: every problem stops at its cap;
+  {                                                // a failed confirmation costs one pass
+    B->log_cap = B->guard < 65536u ? B->guard : 65536u;
+    std::vector<PassLog> zl(B->log_cap, PassLog{0, 0, 0, 0});
+    if ((st = batch_upload(B, zl, &B->pass_log)) != IGAFD_OK) return fail(st);
+  }
+  *out = B;
+  return IGAFD_OK;
+}
+
+// A group's loop graph: reset its pass counter, then while (any member
+// unfinished) { one pass }, the body captured from batch_body; instantiated,
+// with its stream and completion event.
+static igafd_status group_loop(igafd_batch *B, BatchGroup *G, int priority) {
+  if (cudaStreamCreateWithPriority(&G->stream, cudaStreamNonBlocking, priority) != cudaSuccess ||
+      cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaGraphCreate(&G->graph, 0) != cudaSuccess)
+    return IGAFD_ERR_CUDA;
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, G->graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return IGAFD_ERR_CUDA;
   cudaGraphNode_t reset_node, while_node;
   {
     cudaKernelNodeParams kp = {};
-    void *kargs[1] = {&B->passes};
+    void *kargs[1] = {&G->lpasses};
     kp.func = (void *)batch_reset_kernel;
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(32);
     kp.kernelParams = kargs;
-    if (cudaGraphAddKernelNode(&reset_node, B->graph, nullptr, 0, &kp) != cudaSuccess)
-      return fail(IGAFD_ERR_CUDA);
+    if (cudaGraphAddKernelNode(&reset_node, G->graph, nullptr, 0, &kp) != cudaSuccess)
+      return IGAFD_ERR_CUDA;
   }
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
-  if (cudaGraphAddNode(&while_node, B->graph, &reset_node, nullptr, 1, &cp) != cudaSuccess)
-    return fail(IGAFD_ERR_CUDA);
+  if (cudaGraphAddNode(&while_node, G->graph, &reset_node, nullptr, 1, &cp) != cudaSuccess)
+    return IGAFD_ERR_CUDA;
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   if (cudaStreamBeginCaptureToGraph(B->cap, body, nullptr, nullptr, 0,
                                     cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-    return fail(IGAFD_ERR_CUDA);
+    return IGAFD_ERR_CUDA;
   const long long l0 = g_igafd_launches.load();
   g_igafd_plain_launch = true;
-  st = batch_body(B, B->cap, h);
+  const igafd_status st = batch_body(G, B->cap, h);
   g_igafd_plain_launch = false;
   cudaGraph_t captured = nullptr;
   const cudaError_t e = cudaStreamEndCapture(B->cap, &captured);
-  B->body_launches = g_igafd_launches.load() - l0;
-  g_igafd_launches.fetch_sub(B->body_launches);              // captured, not executed
+  G->body_launches = g_igafd_launches.load() - l0;
+  g_igafd_launches.fetch_sub(G->body_launches);              // captured, not executed
   if (st != IGAFD_OK || e != cudaSuccess) {
     cudaGetLastError();
-    return fail(st != IGAFD_OK ? st : IGAFD_ERR_CUDA);
+    return st != IGAFD_OK ? st : IGAFD_ERR_CUDA;
   }
-  if (cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess) {
+  // the group's scheduling priority on every kernel of its pass
+  size_t nn = 0;
+  if (cudaGraphGetNodes(body, nullptr, &nn) != cudaSuccess) return IGAFD_ERR_CUDA;
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn && cudaGraphGetNodes(body, nodes.data(), &nn) != cudaSuccess) return IGAFD_ERR_CUDA;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) return IGAFD_ERR_CUDA;
+    if (t != cudaGraphNodeTypeKernel) continue;
+    cudaLaunchAttributeValue v = {};
+    v.priority = priority;
+    if (cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v) != cudaSuccess)
+      return IGAFD_ERR_CUDA;
+  }
+  if (cudaGraphInstantiate(&G->exec, G->graph, 0) != cudaSuccess) {
     cudaGetLastError();
+    return IGAFD_ERR_CUDA;
+  }
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_batch_create_grouped(igafd_patch *const *patches, int count,
+                                                   const igafd_pcg_opts *opts, int groups,
+                                                   int passes_per_launch, igafd_batch **out) {
+  if (!out) return IGAFD_ERR_ARG;
+  *out = nullptr;
+  if (!patches || count < 1 || groups < 0 || passes_per_launch < 0) return IGAFD_ERR_ARG;
+  igafd_pcg_opts o;
+  if (opts) o = *opts; else igafd_pcg_default_opts(&o);
+  if (!(o.tol >= 0.0) || o.max_iter < 0 || o.true_every < 0) return IGAFD_ERR_ARG;
+  if (o.prec_dtype < IGAFD_FP64 || o.prec_dtype > IGAFD_ADI) return IGAFD_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    igafd_patch *P = patches[i];
+    if (!P || !P->stencil || P->dev != patches[0]->dev) return IGAFD_ERR_ARG;
+    if (o.prec_dtype == IGAFD_ADI && !P->adi) return IGAFD_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (patches[j] == P) return IGAFD_ERR_ARG;            // one problem per patch
+  }
+  IGAFD_CUDA(cudaSetDevice(patches[0]->dev));
+  if (groups == 0 || groups > count) groups = count;       // 0: one loop per problem
+  o.timing = 0;
+  o.check_every = 1;            // the loops run on the device; nothing is polled
+  igafd_batch *B = new igafd_batch{};
+  B->count = count;
+  B->dev = patches[0]->dev;
+  B->num_sms = patches[0]->num_sms;
+  B->o = o;
+  B->ps.assign(patches, patches + count);
+  auto fail = [&](igafd_status e) {
+    igafd_batch_destroy(B);
+    return e;
+  };
+  // groups of problems with similar work per iteration (stencil FMAs):
+  // consecutive runs of the problems ordered by it, of near-equal total work.
+  // A group's passes move at the pace of its heaviest member, so problems of
+  // like size share one, and light groups loop fast.
+  std::vector<std::pair<double, int>> order;
+  double total = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const igafd_patch *P = patches[i];
+    double pts = 1.0;
+    for (int d = 0; d < P->dim; ++d) pts *= 2.0 * P->p + 1.0;
+    order.push_back({-(double)P->N * pts, i});
+    total += (double)P->N * pts;
+  }
+  std::stable_sort(order.begin(), order.end());
+  std::vector<double> load(groups, 0.0);
+  std::vector<std::vector<int>> members(groups);
+  B->group_of.assign(count, 0);
+  {
+    int g = 0;
+    double acc = 0.0;
+    for (size_t r = 0; r < order.size(); ++r) {
+      const int left = (int)(order.size() - r);           // every group gets a problem
+      if (g < groups - 1 && !members[g].empty() &&
+          (acc >= total * (g + 1) / groups || left <= groups - 1 - g))
+        ++g;
+      acc += -order[r].first;
+      load[g] += -order[r].first;
+      members[g].push_back(order[r].second);
+    }
+  }
+  for (int g = 0; g < groups; ++g) {
+    std::sort(members[g].begin(), members[g].end());       // the caller's order within a group
+    for (int i : members[g]) B->group_of[i] = g;
+    std::vector<igafd_patch *> gp;
+    for (int i : members[g]) gp.push_back(patches[i]);
+    BatchGroup *G = nullptr;
+    const igafd_status st = group_create(gp.data(), (int)gp.size(), o, &G);
+    if (st != IGAFD_OK) return fail(st);
+    G->chunk = (unsigned)passes_per_launch;
+    B->groups.push_back(G);
+  }
+  // the groups' loop graphs
+  if (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess)
     return fail(IGAFD_ERR_CUDA);
+  // priorities: the group of the lightest problems first. Its passes are
+  // short chains of small launches whose length is set by latency, so they
+  // run ahead of the throughput-bound passes of large problems instead of
+  // queueing behind their CTAs, at little cost to those.
+  int least = 0, greatest = 0;
+  IGAFD_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  const int levels = least - greatest + 1;
+  std::vector<std::pair<double, int>> by_load;
+  for (int g = 0; g < groups; ++g) by_load.push_back({load[g] / (double)members[g].size(), g});
+  std::stable_sort(by_load.begin(), by_load.end());
+  std::vector<int> prio(groups, least);
+  for (int r = 0; r < groups && groups > 1; ++r)
+    prio[by_load[r].second] = greatest + (int)((long long)r * levels / groups);
+  for (int g = 0; g < groups; ++g) {
+    const igafd_status st = group_loop(B, B->groups[g], prio[g]);
+    if (st != IGAFD_OK) return fail(st);
   }
   *out = B;
+  return IGAFD_OK;
+}
+
+extern "C" igafd_status igafd_batch_create(igafd_patch *const *patches, int count,
+                                           const igafd_pcg_opts *opts, igafd_batch **out) {
+  // one loop per problem (up to 64 loops; then groups of like size)
+  return igafd_batch_create_grouped(patches, count, opts, count <= 64 ? 0 : 64, 0, out);
+}
+
+extern "C" igafd_status igafd_batch_groups(const igafd_batch *B, int *groups, int *group_of) {
+  if (!B || !groups) return IGAFD_ERR_ARG;
+  *groups = (int)B->groups.size();
+  if (group_of)
+    for (int i = 0; i < B->count; ++i) group_of[i] = B->group_of[i];
   return IGAFD_OK;
 }
 
@@ -1094,14 +1358,52 @@ extern "C" igafd_status igafd_batch_solve(igafd_batch *B, const double *const *b
       IGAFD_LAUNCHED(2);
     }
   }
-  IGAFD_CUDA(cudaGraphLaunch(B->exec, s));
+  // the groups' loops, concurrently, between the caller's stream's work; a
+  // group whose launch ended at its pass bound with members unfinished is
+  // launched again (the host polls the launches' completion events)
+  IGAFD_CUDA(cudaEventRecord(B->fork, s));
+  std::vector<BatchGroup *> running;
+  for (BatchGroup *G : B->groups) {
+    IGAFD_CUDA(cudaStreamWaitEvent(G->stream, B->fork, 0));
+    IGAFD_CUDA(cudaMemsetAsync(G->passes, 0, sizeof(unsigned), G->stream));
+    *G->more_host = 0;
+    IGAFD_CUDA(cudaGraphLaunch(G->exec, G->stream));
+    IGAFD_CUDA(cudaEventRecord(G->done, G->stream));
+    if (G->chunk > 0) running.push_back(G);
+  }
+  while (!running.empty()) {
+    bool progressed = false;
+    for (size_t k = 0; k < running.size();) {
+      BatchGroup *G = running[k];
+      const cudaError_t q = cudaEventQuery(G->done);
+      if (q == cudaErrorNotReady) {
+        ++k;
+        continue;
+      }
+      IGAFD_CUDA(q);
+      progressed = true;
+      if (*(volatile int *)G->more_host) {
+        *G->more_host = 0;
+        IGAFD_CUDA(cudaGraphLaunch(G->exec, G->stream));
+        IGAFD_CUDA(cudaEventRecord(G->done, G->stream));
+        ++k;
+      } else {
+        running[k] = running.back();
+        running.pop_back();
+      }
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+  for (BatchGroup *G : B->groups) IGAFD_CUDA(cudaStreamWaitEvent(s, G->done, 0));
   for (int i = 0; i < n; ++i)
     IGAFD_CUDA(cudaMemcpyAsync(B->ps[i]->host_scal, B->ps[i]->scal, S_COUNT * sizeof(double),
                                cudaMemcpyDeviceToHost, s));
   IGAFD_CUDA(cudaStreamSynchronize(s));
-  unsigned passes = 0;
-  IGAFD_CUDA(cudaMemcpy(&passes, B->passes, sizeof(passes), cudaMemcpyDeviceToHost));
-  IGAFD_LAUNCHED((long long)passes * B->body_launches);
+  for (BatchGroup *G : B->groups) {
+    unsigned passes = 0;
+    IGAFD_CUDA(cudaMemcpy(&passes, G->passes, sizeof(passes), cudaMemcpyDeviceToHost));
+    IGAFD_LAUNCHED((long long)passes * G->body_launches);
+  }
   igafd_status worst = IGAFD_OK;
   for (int i = 0; i < n; ++i) {
     igafd_patch *P = B->ps[i];
@@ -1119,6 +1421,40 @@ extern "C" igafd_status igafd_batch_solve(igafd_batch *B, const double *const *b
     if (e != IGAFD_OK && worst == IGAFD_OK) worst = e;
   }
   return worst;
+}
+
+extern "C" igafd_status igafd_batch_pass_log(const igafd_batch *B, int group, int cap,
+                                             double *start_us, double *dur_us, int *active,
+                                             int *npasses) {
+  if (!B || !npasses || cap < 0 || (cap > 0 && (!start_us || !dur_us || !active)))
+    return IGAFD_ERR_ARG;
+  if (group < 0 || group >= (int)B->groups.size()) return IGAFD_ERR_ARG;
+  IGAFD_CUDA(cudaSetDevice(B->dev));
+  // the origin: the earliest pass start over the groups
+  unsigned long long t_origin = ~0ull;
+  for (const BatchGroup *G : B->groups) {
+    unsigned gp = 0;
+    IGAFD_CUDA(cudaMemcpy(&gp, G->passes, sizeof(gp), cudaMemcpyDeviceToHost));
+    if (gp == 0 || G->log_cap == 0) continue;
+    PassLog first;
+    IGAFD_CUDA(cudaMemcpy(&first, G->pass_log, sizeof(first), cudaMemcpyDeviceToHost));
+    if (first.t0 < t_origin) t_origin = first.t0;
+  }
+  const BatchGroup *G = B->groups[group];
+  unsigned passes = 0;
+  IGAFD_CUDA(cudaMemcpy(&passes, G->passes, sizeof(passes), cudaMemcpyDeviceToHost));
+  const unsigned n = passes < G->log_cap ? passes : G->log_cap;
+  *npasses = (int)n;
+  const unsigned m = n < (unsigned)cap ? n : (unsigned)cap;
+  if (m == 0) return IGAFD_OK;
+  std::vector<PassLog> h(m);
+  IGAFD_CUDA(cudaMemcpy(h.data(), G->pass_log, m * sizeof(PassLog), cudaMemcpyDeviceToHost));
+  for (unsigned k = 0; k < m; ++k) {
+    start_us[k] = (double)(long long)(h[k].t0 - t_origin) * 1e-3;
+    dur_us[k] = (double)(long long)(h[k].t1 - h[k].t0) * 1e-3;
+    active[k] = h[k].active;
+  }
+  return IGAFD_OK;
 }
 
 extern "C" igafd_status igafd_batch_pcg_solve(igafd_patch *const *patches, int count,

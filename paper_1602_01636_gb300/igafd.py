@@ -82,7 +82,8 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_adi_parameters", "igafd_adi_setup", "igafd_apply_prec_adi", "igafd_adi_greedy",
            "igafd_adi_wachspress", "igafd_mp_numbering", "igafd_mp_subdomain", "igafd_mp_create",
            "igafd_mp_destroy", "igafd_mp_apply_ias", "igafd_quad_points", "igafd_load_rhs",
-           "igafd_batch_create", "igafd_batch_solve", "igafd_batch_destroy",
+           "igafd_batch_create", "igafd_batch_solve", "igafd_batch_destroy", "igafd_batch_pass_log",
+           "igafd_batch_create_grouped", "igafd_batch_groups",
            "igafd_mp_set_operator", "igafd_mp_apply_A", "igafd_mp_pcg_solve", "igafd_set_fd_tile"]
 
 MLP_PARAMS = 4738
@@ -115,6 +116,11 @@ def lib():
     L.igafd_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(PCGOpts), C.POINTER(vp)]
     L.igafd_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(PCGInfo), vp]
     L.igafd_batch_destroy.argtypes = [vp]
+    L.igafd_batch_pass_log.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.igafd_batch_create_grouped.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(PCGOpts), C.c_int,
+                                             C.c_int, C.POINTER(vp)]
+    L.igafd_batch_groups.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.igafd_batch_destroy.restype = None
     L.igafd_autotune.argtypes = [vp, C.c_int, vp]
     L.igafd_set_stencil_stages.argtypes = [vp, C.c_int]
@@ -303,15 +309,27 @@ class Batch:
     each solve() allocates nothing on the library side."""
 
     def __init__(self, patches, tol=1e-8, max_iter=1000, dtype="fp64", flexible=None,
-                 true_every=50):
+                 true_every=50, groups=1, passes_per_launch=0):
+        """groups: problems split into that many concurrently looping groups
+        (0: one per problem); passes_per_launch: passes per launch of a
+        group's loop graph, relaunched from the host while members are
+        unfinished (0: the whole loop in one launch)."""
         self._patches = list(patches)
         self.n = len(self._patches)
         o = _opts(tol, max_iter, dtype, flexible, true_every, 4)
         vp = C.c_void_p
         hp = (vp * self.n)(*[p.h for p in self._patches])
         h = C.c_void_p()
-        _check(lib().igafd_batch_create(hp, self.n, C.byref(o), C.byref(h)), "batch_create")
+        _check(lib().igafd_batch_create_grouped(hp, self.n, C.byref(o), int(groups),
+                                                int(passes_per_launch), C.byref(h)), "batch_create")
         self.h = h
+
+    def groups(self):
+        """(number of groups, each problem's group)."""
+        g = C.c_int()
+        of = (C.c_int * self.n)()
+        _check(lib().igafd_batch_groups(self.h, C.byref(g), of), "batch_groups")
+        return g.value, list(of)
 
     def solve(self, bs, xs=None, raise_on_error=True):
         """Solve patches[i] x_i = bs[i] for all i; returns (xs, infos)."""
@@ -326,6 +344,19 @@ class Batch:
         if raise_on_error and st not in (OK, ERR_NOT_CONVERGED):
             raise IgafdError(st, "batch_solve")
         return xs, list(infos)
+
+    def pass_log(self, group=0):
+        """Per pass of group `group`'s device loop in the last solve: start
+        (from the earliest pass of any group) and length (us, on the device
+        clock) and the number of unfinished members."""
+        import numpy as np
+        L, n = lib(), C.c_int()
+        _check(L.igafd_batch_pass_log(self.h, group, 0, None, None, None, C.byref(n)),
+               "batch_pass_log")
+        m = n.value
+        st, du, ac = (C.c_double * m)(), (C.c_double * m)(), (C.c_int * m)()
+        _check(L.igafd_batch_pass_log(self.h, group, m, st, du, ac, C.byref(n)), "batch_pass_log")
+        return {"start_us": np.array(st[:]), "dur_us": np.array(du[:]), "active": np.array(ac[:])}
 
     def close(self):
         if getattr(self, "h", None):

@@ -434,14 +434,18 @@ def test_batched_solve_matches_single_solves(torch):
         p.close()
 
 
-def test_batched_solve_device_loop(torch):
+@pytest.mark.parametrize("groups,ppl", [(1, 0), (3, 0), (0, 0), (0, 2), (3, 5)])
+def test_batched_solve_device_loop(torch, groups, ppl):
     """The device-driven batched loop against single solves, bitwise: a
     periodic true residual every 3 iterations with the flexible beta (TF32
     FD), one member on the per-mode tensor-core FD (its own launches inside the
     loop), one with b = 0 (finished before the loop), a reused batch object
     (two solves, the same bits), and an iteration cap that stops one member
-    (NOT_CONVERGED) while the others converge. One pass of the loop is a fixed
-    number of launches, not one set per problem."""
+    (NOT_CONVERGED) while the others converge; in one group, in three
+    concurrently looping groups and in one loop per problem, each with the
+    whole loop in one graph launch or a few passes per launch (relaunched by
+    the host). With one group a pass of the loop is a fixed number of
+    launches, not one set per problem."""
     from paper_1602_01636_gb300 import igafd
     g = synth.rng(505)
     probs = [synth.Problem(3, tuple(int(v) for v in g.integers(9, 20, 3)), int(g.integers(2, 5)),
@@ -452,7 +456,9 @@ def test_batched_solve_device_loop(torch):
     bs = [to_dev(synth.random_rhs(p.N, 70 + i)) for i, p in enumerate(patches)]
     bs[3].zero_()
     opts = dict(tol=1e-10, dtype="tf32", flexible=True, true_every=3)
-    batch = igafd.Batch(patches, **opts)
+    batch = igafd.Batch(patches, groups=groups, passes_per_launch=ppl, **opts)
+    ng, of = batch.groups()
+    assert ng == (groups or len(patches)) and sorted(set(of)) == list(range(ng))
     l0 = igafd.kernel_launches()
     xs1, inf1 = batch.solve(bs)
     launches = igafd.kernel_launches() - l0
@@ -465,10 +471,17 @@ def test_batched_solve_device_loop(torch):
     assert inf1[3].iterations == 0 and float(xs1[3].abs().max()) == 0.0
     # fewer launches than one-by-one would take (7 problems x ~8 kernels per iteration)
     its = max(i.iterations for i in inf1)
-    assert launches < 7 * 8 * its, (launches, its)
+    if groups == 1:
+        assert launches < 7 * 8 * its, (launches, its)
+    for gi in range(ng):                         # one record per pass of each loop
+        log = batch.pass_log(gi)
+        members = [i for i in range(len(patches)) if of[i] == gi]
+        assert len(log["dur_us"]) >= max(inf1[i].iterations for i in members)
+        assert (log["dur_us"] > 0).all() and log["active"][0] <= len(members)
     batch.close()
     # an iteration cap that only some members meet
-    capped = igafd.Batch(patches, tol=1e-12, max_iter=6, dtype="fp64")
+    capped = igafd.Batch(patches, tol=1e-12, max_iter=6, dtype="fp64", groups=groups,
+                         passes_per_launch=ppl)
     xs, infs = capped.solve(bs)
     for i, (p, b) in enumerate(zip(patches, bs)):
         xr, ir = p.pcg(b, tol=1e-12, max_iter=6, dtype="fp64", raise_on_error=False)
