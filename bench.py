@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--groups", type=int, default=0,
                     help="--batch: concurrently looping groups (0: one per problem)")
+    ap.add_argument("--timeline", action="store_true",
+                    help="--batch: add the device-clock pass record of the last timed solve")
     ap.add_argument("--learned", action="store_true",
                     help="learned span scalings: train on generated patches, compare on held-out ones")
     ap.add_argument("--cube", action="store_true",
@@ -725,6 +727,35 @@ def batch_problems(count, seed0=0):
     return out
 
 
+def batch_timeline(batch, infos):
+    """The device-clock pass record of the last solve: per group its members'
+    iterations, passes, first start and last end (ms from the earliest pass);
+    and, over all groups, the passes and their time by the number of
+    unfinished members at the pass's start."""
+    ng, of = batch.groups()
+    groups, buckets = [], {}
+    for g in range(ng):
+        log = batch.pass_log(g)
+        d, st, act = log["dur_us"], log["start_us"], log["active"]
+        if len(d) == 0:
+            continue
+        mem = [i for i in range(len(of)) if of[i] == g]
+        groups.append({"group": g, "iterations": [infos[i].iterations for i in mem],
+                       "passes": int(len(d)), "start_ms": round(float(st[0]) / 1e3, 3),
+                       "end_ms": round(float(st[-1] + d[-1]) / 1e3, 3),
+                       "mean_pass_us": round(float(d.mean()), 1)})
+        for a_, du in zip(act, d):
+            key = "1" if a_ <= 1 else "2-4" if a_ <= 4 else "5-16" if a_ <= 16 else "17+"
+            b = buckets.setdefault(key, [0, 0.0])
+            b[0] += 1
+            b[1] += float(du) / 1e3
+    groups.sort(key=lambda r: -r["end_ms"])
+    return {"groups": ng, "latest_groups": groups[:8],
+            "latest_start_ms": max(r["start_ms"] for r in groups) if groups else 0.0,
+            "passes_by_unfinished_members": {k: {"passes": v[0], "ms": round(v[1], 2)}
+                                             for k, v in sorted(buckets.items())}}
+
+
 def run_batch(args):
     import torch
     import synth
@@ -781,6 +812,7 @@ def run_batch(args):
     torch.cuda.nvtx.range_pop()
     launches = igafd.kernel_launches() - l0
     batch_s = a.elapsed_time(c) / 1e3 / args.steps
+    timeline = batch_timeline(batch, infos) if args.timeline else None
     # algorithmic stencil bytes of the solve: every stencil launch streams the
     # (2p+1)^3 coefficients of every row plus x and y; launches = iterations +
     # the convergence confirmation + the periodic true residuals (every 50)
@@ -846,6 +878,8 @@ def run_batch(args):
             "autotuned_fd_form_bf16": {"fused": sum(int(pt.info.fd_fused[1]) for pt in patches),
                                        "per-mode product": sum(1 - int(pt.info.fd_fused[1]) for pt in patches)},
             "gpu_launches": launches}
+    if timeline is not None:
+        line["timeline"] = timeline
     print(json.dumps(line), flush=True)
     batch.close()
     for p_ in patches:

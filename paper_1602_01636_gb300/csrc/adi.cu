@@ -63,6 +63,7 @@ __host__ __device__ constexpr int step_mode(int st) {
 template <typename T>
 struct LineArgs {
   int n1, n2, n3, p, len, chunks;
+  unsigned len_magic;              // floor(e / len) = umulhi(e, len_magic) for e < 2^16 (0: len = 1)
   double w;                        // w_j of this iteration
   double w_next;                   // w_{j+1} (two-variable ADI: the next right-hand side)
   int first, last;                 // first / last iteration of the apply
@@ -96,24 +97,86 @@ __device__ __forceinline__ int tix(int len, int l, int i) {
   return MODE == 0 ? l * (len + 1) + i : i * kL + l;
 }
 
-// tile(l, i) = f(address) for the CTA's lines, coalesced
-template <int MODE, typename T, typename F>
-__device__ __forceinline__ void load_tile(T *tile, const LineArgs<T> &a, int nv, F f) {
-  const int len = a.len;
-  for (int e = threadIdx.x; e < len * kL; e += kT) {
-    const int l = MODE == 0 ? e / len : e % kL;
-    const int i = MODE == 0 ? e % len : e / kL;
-    if (l < nv) tile[tix<MODE>(len, l, i)] = f(elem_addr<MODE>(a.n1, a.n2, a.chunks, blockIdx.x, l, i));
+// Elements a thread loads (or stores) per batch: the loads of a batch are all
+// issued before their values are written to shared memory, so a thread keeps
+// kU global loads in flight instead of one (the line kernels run few warps
+// per SM, and a load-to-store chain per element left them waiting on memory).
+constexpr int kU = 8;
+template <typename T>
+constexpr int batch_of() { return sizeof(T) == 4 ? 2 * kU : kU; }   // 64 bytes of loads per batch
+
+// (line, element) of the e-th entry of the CTA's tile in load order: lines
+// outermost in direction 1 (whole rows), elements outermost otherwise
+template <int MODE, typename T>
+__device__ __forceinline__ void entry(const LineArgs<T> &a, int e, int &l, int &i) {
+  if (MODE == 0) {
+    l = a.len_magic ? (int)__umulhi((unsigned)e, a.len_magic) : e;   // magic 0: len = 1
+    i = e - l * a.len;
+  } else {
+    l = e % kL;
+    i = e / kL;
   }
 }
 
-// g(address, tile(l, i)) for the CTA's lines, coalesced
+// tile(l, i) = f(address) for the CTA's lines, coalesced
+template <int MODE, typename T, typename F>
+__device__ __forceinline__ void load_tile(T *tile, const LineArgs<T> &a, int nv, F f) {
+  constexpr int U = batch_of<T>();
+  const int len = a.len, total = len * kL;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kT * U) {
+    T v[U];
+    int t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * kT;
+      int l, i;
+      entry<MODE>(a, e, l, i);
+      t[u] = (e < total && l < nv) ? tix<MODE>(len, l, i) : -1;
+      if (t[u] >= 0) v[u] = f(elem_addr<MODE>(a.n1, a.n2, a.chunks, blockIdx.x, l, i));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (t[u] >= 0) tile[t[u]] = v[u];
+  }
+}
+
+// two tiles at once (their loads in flight together)
+template <int MODE, typename T, typename F0, typename F1>
+__device__ __forceinline__ void load_tiles2(T *tile0, F0 f0, T *tile1, F1 f1, const LineArgs<T> &a,
+                                            int nv) {
+  constexpr int U = batch_of<T>() / 2;
+  const int len = a.len, total = len * kL;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kT * U) {
+    T v0[U], v1[U];
+    int t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * kT;
+      int l, i;
+      entry<MODE>(a, e, l, i);
+      t[u] = (e < total && l < nv) ? tix<MODE>(len, l, i) : -1;
+      if (t[u] >= 0) {
+        const long long g = elem_addr<MODE>(a.n1, a.n2, a.chunks, blockIdx.x, l, i);
+        v0[u] = f0(g);
+        v1[u] = f1(g);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (t[u] >= 0) {
+        tile0[t[u]] = v0[u];
+        tile1[t[u]] = v1[u];
+      }
+  }
+}
+
+// g(address, tile(l, i)) for the CTA's lines, coalesced (g only writes)
 template <int MODE, typename T, typename G>
 __device__ __forceinline__ void store_tile(const T *tile, const LineArgs<T> &a, int nv, G g) {
   const int len = a.len;
   for (int e = threadIdx.x; e < len * kL; e += kT) {
-    const int l = MODE == 0 ? e / len : e % kL;
-    const int i = MODE == 0 ? e % len : e / kL;
+    int l, i;
+    entry<MODE>(a, e, l, i);
     if (l < nv) g(elem_addr<MODE>(a.n1, a.n2, a.chunks, blockIdx.x, l, i), tile[tix<MODE>(len, l, i)]);
   }
 }
@@ -121,10 +184,12 @@ __device__ __forceinline__ void store_tile(const T *tile, const LineArgs<T> &a, 
 // out(l, i) = base(l, i) + sum_{|o| <= p} coef(i, o) x(l, i + o) over the
 // CTA's lines; coef(i, o) reads the staged bands
 template <int MODE, typename T, typename C, typename B>
-__device__ __forceinline__ void band_product(T *out, const T *x, int len, int p, int nv, C coef, B base) {
+__device__ __forceinline__ void band_product(const LineArgs<T> &a, T *out, const T *x, int p, int nv,
+                                             C coef, B base) {
+  const int len = a.len;
   for (int e = threadIdx.x; e < len * kL; e += kT) {
-    const int l = MODE == 0 ? e / len : e % kL;
-    const int i = MODE == 0 ? e % len : e / kL;
+    int l, i;
+    entry<MODE>(a, e, l, i);
     if (l >= nv) continue;
     T acc = base(l, i);
     const int olo = i - p < 0 ? -i : -p, ohi = i + p >= len ? len - 1 - i : p;
@@ -204,7 +269,8 @@ __device__ __forceinline__ void chol_solve_line(T *tile, const T *F, int len, in
   }
 }
 
-// dynamic shared memory: two tiles, the two bands and one factor
+// dynamic shared memory: two tiles, two bands (the ones the step's products
+// use, formed from K and M when staged) and one factor
 template <typename T>
 __host__ __device__ size_t line_smem(int len, int p) {
   return ((size_t)2 * kL * (len + 1) + (size_t)2 * len * (2 * p + 1) + (size_t)len * (p + 1)) * sizeof(T);
@@ -219,18 +285,54 @@ __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
   T *t1 = t0 + kL * (a.len + 1);
   T *sK = t1 + kL * (a.len + 1);
   const int len = a.len, p = a.p, BW = 2 * p + 1;
-  T *sM = sK + len * BW;
-  T *sF = sM + len * BW;
+  // the step's bands: K (ST_U); M (ST_B, ST_S); -(K - w M) and -2 M (ST_S1);
+  // -(K - w M) with w of this half step (ST2_A) or the next (ST2_B)
+  T *sX = sK, *sY = sK + len * BW;
+  T *sF = sY + len * BW;
   const int nv = lines_in<MODE>(a.n1, a.n2, a.n3, a.chunks, blockIdx.x);
-  for (int e = threadIdx.x; e < len * BW; e += kT) {
-    sK[e] = a.bK[e];
-    sM[e] = a.bM[e];
-  }
-  for (int e = threadIdx.x; e < len * (p + 1); e += kT) sF[e] = a.fac[e];
   const T w = (T)a.w;
-  auto Kc = [&](int i, int o) { return sK[i * BW + o + p]; };
-  auto Mc = [&](int i, int o) { return sM[i * BW + o + p]; };
+  const T wc = STEP == ST2_B ? (T)a.w_next : w;
+  // bands and factor, kU loads in flight per thread
+  const int nb = len * BW, nf = len * (p + 1);
+  for (int e0 = threadIdx.x; e0 < nb; e0 += kT * kU) {
+    T k[kU], m[kU];   // two loads per entry
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * kT;
+      if (e < nb) {
+        k[u] = STEP == ST_B || STEP == ST_S ? (T)0 : a.bK[e];
+        m[u] = STEP == ST_U ? (T)0 : a.bM[e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * kT;
+      if (e >= nb) continue;
+      if (STEP == ST_U) {
+        sX[e] = k[u];
+      } else if (STEP == ST_B || STEP == ST_S) {
+        sX[e] = m[u];
+      } else if (STEP == ST_S1 || STEP == ST2_A || STEP == ST2_B) {
+        sX[e] = -(k[u] - wc * m[u]);
+        sY[e] = (T)-2 * m[u];
+      }
+    }
+  }
+  for (int e0 = threadIdx.x; e0 < nf; e0 += kT * kU) {
+    T f[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (e0 + u * kT < nf) f[u] = a.fac[e0 + u * kT];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (e0 + u * kT < nf) sF[e0 + u * kT] = f[u];
+  }
+  auto Kc = [&](int i, int o) { return sX[i * BW + o + p]; };
+  auto Mc = [&](int i, int o) { return sX[i * BW + o + p]; };
+  auto Cc = [&](int i, int o) { return sX[i * BW + o + p]; };
+  auto Dc = [&](int i, int o) { return sY[i * BW + o + p]; };
   auto zero = [&](int, int) { return (T)0; };
+  auto same = [&](T *t) { return [t, len](int l, int i) { return t[tix<MODE>(len, l, i)]; }; };
   T *res = t1;                     // the tile the solve works on
   if (STEP == ST_PRE2) {
     load_tile<MODE>(t1, a, nv, [&](long long g) { return (T)a.r[g]; });
@@ -239,22 +341,19 @@ __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
   } else if (STEP == ST_U) {
     load_tile<MODE>(t0, a, nv, [&](long long g) { return a.s[g]; });
     __syncthreads();
-    band_product<MODE>(t1, t0, len, p, nv, Kc, zero);                       // K2 s
+    band_product<MODE>(a, t1, t0, p, nv, Kc, zero);                       // K2 s
   } else if (STEP == ST_S1) {
     if (a.first) {
       load_tile<MODE>(t1, a, nv, [&](long long g) { return a.rt[g]; });      // s = u = v = 0
     } else {
-      load_tile<MODE>(t0, a, nv, [&](long long g) { return a.s[g]; });
+      load_tiles2<MODE>(t0, [&](long long g) { return a.s[g]; }, t1,
+                        [&](long long g) { return a.rt[g]; }, a, nv);
       __syncthreads();
-      band_product<MODE>(t1, t0, len, p, nv, [&](int i, int o) { return -(Kc(i, o) - w * Mc(i, o)); },
-                         [&](int l, int i) {
-                           return a.rt[elem_addr<MODE>(a.n1, a.n2, a.chunks, blockIdx.x, l, i)];
-                         });                                                  // r~ - (K1 - w M1) s
+      band_product<MODE>(a, t1, t0, p, nv, Cc, same(t1));                  // r~ - (K1 - w M1) s
       __syncthreads();
       load_tile<MODE>(t0, a, nv, [&](long long g) { return a.u[g] + a.v[g]; });
       __syncthreads();
-      band_product<MODE>(t1, t0, len, p, nv, [&](int i, int o) { return (T)-2 * Mc(i, o); },
-                         [&](int l, int i) { return t1[tix<MODE>(len, l, i)]; });   // - 2 M1 (u + v)
+      band_product<MODE>(a, t1, t0, p, nv, Dc, same(t1));                  // - 2 M1 (u + v)
     }
   } else if (STEP == ST_B) {
     if (a.first)
@@ -262,11 +361,11 @@ __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
     else
       load_tile<MODE>(t0, a, nv, [&](long long g) { return a.u[g] + w * a.s1[g]; });
     __syncthreads();
-    band_product<MODE>(t1, t0, len, p, nv, Mc, zero);                       // M2 (u + w s*)
+    band_product<MODE>(a, t1, t0, p, nv, Mc, zero);                       // M2 (u + w s*)
   } else if (STEP == ST_S) {
     load_tile<MODE>(t0, a, nv, [&](long long g) { return a.b[g]; });
     __syncthreads();
-    band_product<MODE>(t1, t0, len, p, nv, Mc, zero);                       // M3 b
+    band_product<MODE>(a, t1, t0, p, nv, Mc, zero);                       // M3 b
   } else if (STEP == ST2_A) {
     if (a.first)
       load_tile<MODE>(t1, a, nv, [&](long long g) { return (T)a.r[g]; });  // r_0 = r
@@ -289,17 +388,25 @@ __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
   } else if (STEP == ST_S1) {
     store_tile<MODE>(t1, a, nv, [&](long long g, T x) { a.s1[g] = x; });
   } else if (STEP == ST_B) {
-    if (a.first)
+    if (a.first) {
       store_tile<MODE>(t1, a, nv, [&](long long g, T x) { a.b[g] = w * x; });
-    else
-      store_tile<MODE>(t1, a, nv, [&](long long g, T x) { a.b[g] = a.v[g] + w * x; });
+    } else {
+      load_tile<MODE>(t0, a, nv, [&](long long g) { return a.v[g]; });       // t0 is free
+      __syncthreads();
+      const int len_ = len;
+      for (int e = threadIdx.x; e < len_ * kL; e += kT) {
+        int l, i;
+        entry<MODE>(a, e, l, i);
+        if (l >= nv) continue;
+        const int t = tix<MODE>(len_, l, i);
+        a.b[elem_addr<MODE>(a.n1, a.n2, a.chunks, blockIdx.x, l, i)] = t0[t] + w * t1[t];
+      }
+    }
   } else if (STEP == ST2_A || (STEP == ST2_B && !a.last)) {
     // the next half step's right-hand side r - (K - w M) s~ along the same lines
-    const T wn = STEP == ST2_A ? w : (T)a.w_next;
-    band_product<MODE>(t0, t1, len, p, nv, [&](int i, int o) { return -(Kc(i, o) - wn * Mc(i, o)); },
-                       [&](int l, int i) {
-                         return (T)a.r[elem_addr<MODE>(a.n1, a.n2, a.chunks, blockIdx.x, l, i)];
-                       });
+    load_tile<MODE>(t0, a, nv, [&](long long g) { return (T)a.r[g]; });      // t0 is free
+    __syncthreads();
+    band_product<MODE>(a, t0, t1, p, nv, Cc, same(t0));
     __syncthreads();
     if (STEP == ST2_A)
       store_tile<MODE>(t0, a, nv, [&](long long g, T x) { a.v[g] = x; });  // r_{j-1/2}
@@ -315,8 +422,8 @@ __global__ void __launch_bounds__(kT) adi_line_kernel(LineArgs<T> a) {
     } else {
       const int len_ = len;
       for (int e = threadIdx.x; e < len_ * kL; e += kT) {               // s_j and v_{j+1} = b_j - w s_j
-        const int l = MODE == 0 ? e / len_ : e % kL;
-        const int i = MODE == 0 ? e % len_ : e / kL;
+        int l, i;
+        entry<MODE>(a, e, l, i);
         if (l >= nv) continue;
         const long long g = elem_addr<MODE>(a.n1, a.n2, a.chunks, blockIdx.x, l, i);
         const T x = t1[tix<MODE>(len_, l, i)];
@@ -391,6 +498,7 @@ igafd_status launch_step(const AdiState &S, const LineArgs<T> &base, int dir, in
   LineArgs<T> a = base;
   const int n2 = S.n[1], n3 = S.n[2], p = S.p;
   a.len = S.n[dir];
+  a.len_magic = a.len > 1 ? 0xffffffffu / (unsigned)a.len + 1u : 0u;
   a.bK = (const T *)S.band[dir];
   a.bM = (const T *)S.band[dir] + (size_t)S.n[dir] * (2 * p + 1);
   a.fac = (const T *)S.fac[dir] + (size_t)fac_index * S.n[dir] * (p + 1);
