@@ -198,3 +198,30 @@ def test_adi_rejects_bad_calls(torch):
         patch3.adi_setup([1.0], dtype="bf16")          # FP64 or FP32 only
     with pytest.raises(igafd.IgafdError):
         patch3.adi_parameters(1.5)                     # 0 < eps < 1
+
+
+@pytest.mark.parametrize("groups", [1, 0])
+def test_batched_solve_with_adi(torch, groups):
+    """A batched solve with P_J as every member's preconditioner (the ADI
+    line kernels launched per problem inside the device loop) gives the
+    iterates and iteration counts of the members' single solves, bitwise,
+    in one lockstep loop and in one loop per problem."""
+    from paper_1602_01636_gb300 import igafd
+    probs = [synth.Problem(3, (12, 10, 11), 2, [0.05, -0.03, 0.02]),
+             synth.Problem(3, (9, 13, 10), 3, [-0.04, 0.02, 0.05]),
+             synth.Problem(3, (11, 11, 14), 3, [0.03, 0.04, -0.02])]
+    patches = []
+    for pr in probs:
+        patch = igafd.Patch.from_problem(pr)
+        patch.adi_setup(patch.adi_parameters(0.1), "fp64")
+        patches.append(patch)
+    bs = [to_dev(synth.random_rhs(p.N, 30 + i)) for i, p in enumerate(patches)]
+    batch = igafd.Batch(patches, tol=1e-10, max_iter=300, dtype="adi", groups=groups)
+    xs, infos = batch.solve(bs)
+    batch.close()
+    for p, b, x, inf in zip(patches, bs, xs, infos):
+        xr, ir = p.pcg(b, tol=1e-10, max_iter=300, dtype="adi")
+        assert inf.status == ir.status == 0 and inf.iterations == ir.iterations
+        assert torch.equal(x, xr)
+    for p in patches:
+        p.close()

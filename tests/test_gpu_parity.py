@@ -592,3 +592,35 @@ def test_autotune_picks_a_candidate_and_every_depth_agrees(torch):
     with pytest.raises(igafd.IgafdError):
         patch.set_stencil_rows(3)
     patch.close()
+
+
+def test_batch_grouping_and_argument_errors(torch):
+    """Grouping arguments: more groups than problems gives one per problem,
+    negative counts and an out-of-range pass record are rejected, and the
+    groups hold problems of like size (consecutive in the order of the
+    stencil work of an iteration)."""
+    import ctypes as C
+    from paper_1602_01636_gb300 import igafd
+    g = synth.rng(606)
+    probs = [synth.Problem(3, tuple(int(v) for v in g.integers(9, 18, 3)), int(g.integers(2, 4)),
+                           g.uniform(-0.05, 0.05, 3)) for _ in range(5)]
+    patches = [make_patch(pr) for pr in probs]
+    batch = igafd.Batch(patches, groups=9)
+    ng, of = batch.groups()
+    assert ng == 5 and sorted(of) == list(range(5))
+    batch.close()
+    batch = igafd.Batch(patches, groups=2)
+    ng, of = batch.groups()
+    work = [p.N * (2 * p.info.p + 1) ** 3 for p in patches]
+    order = sorted(range(5), key=lambda i: -work[i])
+    assert ng == 2 and [of[i] for i in order] == sorted(of[i] for i in order)
+    n = C.c_int()
+    st = igafd.lib().igafd_batch_pass_log(batch.h, 2, 0, None, None, None, C.byref(n))
+    assert st == igafd.ERR_ARG
+    batch.close()
+    for kw in (dict(groups=-1), dict(passes_per_launch=-1)):
+        with pytest.raises(igafd.IgafdError) as e:
+            igafd.Batch(patches, **kw)
+        assert e.value.status == igafd.ERR_ARG
+    for p in patches:
+        p.close()
