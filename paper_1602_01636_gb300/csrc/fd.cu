@@ -28,14 +28,18 @@ struct GemmArgs {
 };
 
 // 64x64 output tile, 16-deep K slices, 256 threads with 4x4 outputs each.
+// Double-buffered: the next K slice is read from global memory into
+// registers while the current one is multiplied out of shared memory, and
+// lands in the other shared buffer (one barrier per slice). Each output sums
+// over k in increasing order, as a single-buffered loop would.
 template <typename TA, typename TB, typename TC, typename ACC>
 __global__ void __launch_bounds__(256) mode_gemm_kernel(GemmArgs g) {
   pdl_wait();
   pdl_trigger();
   if (g.done && *g.done != 0.0) return;
   constexpr int BM = 64, BN = 64, BK = 16;
-  __shared__ ACC As[BK][BM + 1];
-  __shared__ ACC Bs[BK][BN + 1];
+  __shared__ ACC As[2][BK][BM + 1];
+  __shared__ ACC Bs[2][BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -50,37 +54,53 @@ __global__ void __launch_bounds__(256) mode_gemm_kernel(GemmArgs g) {
     for (int j = 0; j < 4; ++j) acc[i][j] = (ACC)0;
   const bool a_kfast = g.sak == 1;
   const bool b_nfast = g.sbn == 1;
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
+  // this thread's four (row, k) entries of an A slice and (k, column) of a B slice
+  int am[4], ak[4], bn[4], bk[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int t = tid + 256 * l;
+    if (a_kfast) { am[l] = t / BK; ak[l] = t % BK; } else { ak[l] = t / BM; am[l] = t % BM; }
+    if (b_nfast) { bk[l] = t / BN; bn[l] = t % BN; } else { bn[l] = t / BK; bk[l] = t % BK; }
+  }
+  ACC va[4], vb[4];
+  auto fetch = [&](int k0) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-      int t = tid + 256 * l;
-      int mm, kk;
-      if (a_kfast) { mm = t / BK; kk = t % BK; } else { kk = t / BM; mm = t % BM; }
-      int m = m0 + mm, k = k0 + kk;
-      ACC v = (ACC)0;
-      if (m < g.M && k < g.K) v = (ACC)A[m * g.sam + k * g.sak];
-      As[kk][mm] = v;
-      int nn, kb;
-      if (b_nfast) { kb = t / BN; nn = t % BN; } else { nn = t / BK; kb = t % BK; }
-      int n = n0 + nn, kq = k0 + kb;
-      ACC w = (ACC)0;
-      if (n < g.N && kq < g.K) w = (ACC)B[kq * g.sbk + n * g.sbn];
-      Bs[kb][nn] = w;
+      const int m = m0 + am[l], k = k0 + ak[l];
+      va[l] = (m < g.M && k < g.K) ? (ACC)A[m * g.sam + k * g.sak] : (ACC)0;
+      const int n = n0 + bn[l], kq = k0 + bk[l];
+      vb[l] = (n < g.N && kq < g.K) ? (ACC)B[kq * g.sbk + n * g.sbn] : (ACC)0;
     }
-    __syncthreads();
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      As[buf][ak[l]][am[l]] = va[l];
+      Bs[buf][bk[l]][bn[l]] = vb[l];
+    }
+  };
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    const bool more = k0 + BK < g.K;
+    if (more) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       ACC a[4], bb[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty * 4 + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[buf][kk][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
   const ACC *sc = (const ACC *)g.scale;
 #pragma unroll
