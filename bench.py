@@ -617,6 +617,7 @@ def run_ours(args):
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     sm_clk = peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = 152 * 2 * 2 * sm_clk * 1e6 / 1e12      # TFLOP/s
+    probe = igafd.probe_peaks(torch.cuda.current_device())   # measured rates (untimed)
     traffic = stencil_traffic(p, n)
 
     # the oracle leg runs after every GPU measurement (its processes load the
@@ -663,6 +664,8 @@ def run_ours(args):
                          "achieved": flops / st_s / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": flops / st_s / 1e12 / fp64_peak, "traffic": traffic,
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x sm_max_mhz",
+                         "fp64_probe_tflops": probe["fp64_tflops"],
+                         "frac_of_probe": flops / st_s / 1e12 / probe["fp64_tflops"],
                          "flops_per_launch": flops, "launch_ms": st_ms,
                          "launch_ms_source": "device-clock stamps of the stencil kernel in the timed solves",
                          "launch_ms_cuda_events_apply_A": st_ms_events,
@@ -670,7 +673,8 @@ def run_ours(args):
                                  "unit": "GB/s", "frac": alg_bytes / st_s / 1e9 / hbm_peak,
                                  "peak_source": hbm_src + " (hbm_gbs)",
                                  "alg_bytes_per_launch": alg_bytes}},
-            "fd_roofline": fd_roofline(patch, dtype, aps_mixed, peaks),
+            "fd_roofline": fd_roofline(patch, dtype, aps_mixed, peaks, probe),
+            "probed_peaks": probe,
             "clocks": ck,
             "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
                     "d2h_bytes_per_step": 8 * N},
@@ -685,20 +689,23 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def fd_roofline(patch, dtype, applies_per_s, peaks):
+def fd_roofline(patch, dtype, applies_per_s, peaks, probe=None):
     """Roofline of one mixed-precision FD apply (the tensor-core kernels): the
     algorithmic bytes are r read and z written in FP64 (16 B per dof), the
     FLOPs 4 N sum_k n_k (a forward and a backward product per direction, 2
     FLOP per multiply-add; 12 n^4 for n_k = n in 3D). Peaks: the measured
-    copy bandwidth and the measured dense BF16 rate (TF32 at half of it, the
-    nominal ratio); the bound is the larger of the two times."""
+    copy bandwidth and the dense tensor rate of the operand type -- TF32 from
+    the library's tcgen05 probe, BF16/FP16 the measured cuBLAS BF16 rate (TF32
+    at half of it when no probe ran); the bound is the larger of the two
+    times."""
     N = patch.N
     t = 1.0 / applies_per_s
     alg_bytes = 16.0 * N
     flops = 4.0 * N * sum(patch.n)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     bf16 = peaks.get("bf16_tflops", 1900.0)
-    tc_peak = {"tf32": 0.5 * bf16, "bf16": bf16, "fp16": bf16}.get(dtype)
+    tf32 = probe["tf32_tflops"] if probe and probe.get("tf32_tflops", 0) > 0 else 0.5 * bf16
+    tc_peak = {"tf32": tf32, "bf16": bf16, "fp16": bf16}.get(dtype)
     t_hbm = alg_bytes / (hbm_peak * 1e9)
     out = {"kernel": "tensor-core FD apply (three fused tcgen05 kernels at n = 128)",
            "apply_us": t * 1e6, "alg_bytes_per_apply": alg_bytes, "flops_per_apply": flops,
@@ -707,8 +714,11 @@ def fd_roofline(patch, dtype, applies_per_s, peaks):
     if tc_peak:
         t_tc = flops / (tc_peak * 1e12)
         out["tensor"] = {"achieved": flops / t / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
-                         "frac": t_tc / t, "peak_source": "measured bf16_tflops" +
-                         (" x 0.5 (TF32)" if dtype == "tf32" else "")}
+                         "frac": t_tc / t,
+                         "peak_source": ("measured: tcgen05 TF32 probe (igafd_probe_peaks)"
+                                         if dtype == "tf32" and probe else
+                                         "measured bf16_tflops" +
+                                         (" x 0.5 (TF32)" if dtype == "tf32" else ""))}
         out["bound"] = "hbm" if t_hbm >= t_tc else "tensor"
         out["frac_of_bound"] = max(t_hbm, t_tc) / t
     return out

@@ -314,6 +314,22 @@ igafd_status igafd_batch_pcg_solve(igafd_patch *const *patches, int count,
                                    const igafd_pcg_opts *opts, igafd_pcg_info *infos,
                                    void *stream);
 
+/* Measured arithmetic peaks of a device, for rooflines: the FP64 FMA pipe
+ * (SIMT FMAs, eight independent chains per thread on every SM) and the dense
+ * tcgen05 tensor-core rate with FP32 accumulation for TF32 and for BF16
+ * operands (M = N = 128 MMAs streamed from shared memory into TMEM), in
+ * TFLOP/s (one FMA = 2 FLOP); best of three timed launches after a warm-up,
+ * about 20 ms in all; sm_max_mhz is the device's maximum SM clock.
+ * Allocates and frees a few bytes of device scratch; synchronises the
+ * device. Errors: ARG, OOM, CUDA, TIMEOUT (an MMA completion wait ran out). */
+typedef struct {
+  double fp64_tflops;
+  double tf32_tflops;
+  double bf16_tflops;
+  double sm_max_mhz;
+} igafd_peaks;
+igafd_status igafd_probe_peaks(int device, igafd_peaks *out);
+
 /* Default options: tol 1e-8, max_iter 1000, true_every 50, FP64,
  * Fletcher-Reeves, x0 = 0, check_every 4, timing off. */
 void igafd_pcg_default_opts(igafd_pcg_opts *opts);

@@ -210,6 +210,9 @@ igafd_status igafd_fd_fused_batch_launch(igafd_dtype dt, int kind, const void *a
                                          const int *act, const int *act_start,
                                          const int *act_count, unsigned *queue, int total_blocks,
                                          size_t smem, int num_sms, cudaStream_t s);
+// dense tensor-core FLOP/s for TF32 (op 0) or BF16 (op 1) operands (fd_tc.cu);
+// a bounded wait that runs out sets *err_dev to IGAFD_ERR_TIMEOUT
+igafd_status igafd_tc_probe(int op, int num_sms, int rounds, int *err_dev, double *flop_per_s);
 // number of CTAs of the PCG vector kernels for N dofs (the same in single and
 // batched solves, so their reductions agree bitwise)
 int igafd_red_blocks(long long N);

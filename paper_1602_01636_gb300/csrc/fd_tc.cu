@@ -1639,3 +1639,127 @@ igafd_status igafd_fd_fused_batch_launch(igafd_dtype dt, int kind, const void *a
   return IGAFD_BF(OP_BF16, SLAB_BWD);
 #undef IGAFD_BF
 }
+
+// ---- tensor-core throughput probe ---------------------------------------------
+namespace {
+
+// One CTA per launch slot issues back-to-back M = 128, N = 128 tcgen05 MMAs
+// of the operand type from a constant shared-memory tile (one 128-byte K
+// atom per operand row: four MMAs of 32 bytes of K per round) into one TMEM
+// accumulator, then waits (bounded) for their completion. Operands hold 1.0,
+// so the accumulator grows by K per MMA and stays finite.
+template <int OP>
+__global__ void __launch_bounds__(128) tc_probe_kernel(int rounds, int *err) {
+  using T = Op<OP>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *A = base, *B = base + kM * 128;
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  const uint32_t one = OP == OP_TF32 ? 0x3F800000u : 0x3F803F80u;   // 1.0 (x2 in 16-bit)
+  for (int i = threadIdx.x; i < 2 * kM * 128 / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t *>(A)[i] = one;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+        smem_u32(&tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = (1u << 4) | (T::kFmt << 7) | (T::kFmt << 10) |
+                           ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t ad = sw128_desc(smem_u32(A) + ks * 32);
+        const uint64_t bd = sw128_desc(smem_u32(B) + ks * 32);
+        const uint32_t acc = (r > 0 || ks > 0) ? 1u : 0u;
+        if (OP == OP_TF32)
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        else
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&bar))
+        : "memory");
+    bool ok = false;
+    for (long long it = 0; it < kSpin && !ok; ++it) {
+      uint32_t done;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+          " selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(smem_u32(&bar))
+          : "memory");
+      ok = done != 0;
+    }
+    if (!ok) atomicExch(err, (int)IGAFD_ERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
+template <int OP>
+igafd_status tc_probe(int num_sms, int rounds, int *err, double *flops, float *ms) {
+  const size_t smem = 1024 + 2 * (size_t)kM * 128;
+  IGAFD_CUDA(cudaFuncSetAttribute(tc_probe_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  const int grid = 2 * num_sms;                   // two CTAs per SM (256 of the 512 TMEM columns)
+  cudaEvent_t e0, e1;
+  IGAFD_CUDA(cudaEventCreate(&e0));
+  IGAFD_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {             // the first launch warms up
+    cudaEventRecord(e0);
+    tc_probe_kernel<OP><<<grid, 128, smem>>>(rounds, err);
+    cudaEventRecord(e1);
+    const cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return IGAFD_ERR_CUDA;
+    }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (rep > 0 && t < best) best = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  IGAFD_CUDA(cudaGetLastError());
+  const double k_inst = OP == OP_TF32 ? 8.0 : 16.0;  // K of one 32-byte MMA step
+  *flops = 2.0 * kM * 128 * k_inst * 4.0 * rounds * grid;
+  *ms = best;
+  return IGAFD_OK;
+}
+
+}  // namespace
+
+// Dense tensor-core FLOP/s of this device for TF32 (op 0) or BF16 (op 1)
+// operands with FP32 accumulation in TMEM (M = N = 128 tcgen05 MMAs).
+igafd_status igafd_tc_probe(int op, int num_sms, int rounds, int *err_dev, double *flop_per_s) {
+  double flops = 0.0;
+  float ms = 0.f;
+  if (op == 0) IGAFD_TRY(tc_probe<OP_TF32>(num_sms, rounds, err_dev, &flops, &ms));
+  else IGAFD_TRY(tc_probe<OP_BF16>(num_sms, rounds, err_dev, &flops, &ms));
+  *flop_per_s = ms > 0.f ? flops / (ms * 1e-3) : 0.0;
+  return IGAFD_OK;
+}

@@ -83,7 +83,7 @@ EXPORTS = ["igafd_setup_patch", "igafd_destroy_patch", "igafd_patch_query", "iga
            "igafd_adi_wachspress", "igafd_mp_numbering", "igafd_mp_subdomain", "igafd_mp_create",
            "igafd_mp_destroy", "igafd_mp_apply_ias", "igafd_quad_points", "igafd_load_rhs",
            "igafd_batch_create", "igafd_batch_solve", "igafd_batch_destroy", "igafd_batch_pass_log",
-           "igafd_batch_create_grouped", "igafd_batch_groups",
+           "igafd_batch_create_grouped", "igafd_batch_groups", "igafd_probe_peaks",
            "igafd_mp_set_operator", "igafd_mp_apply_A", "igafd_mp_pcg_solve", "igafd_set_fd_tile"]
 
 MLP_PARAMS = 4738
@@ -121,6 +121,7 @@ def lib():
     L.igafd_batch_create_grouped.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(PCGOpts), C.c_int,
                                              C.c_int, C.POINTER(vp)]
     L.igafd_batch_groups.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.igafd_probe_peaks.argtypes = [C.c_int, C.POINTER(Peaks)]
     L.igafd_batch_destroy.restype = None
     L.igafd_autotune.argtypes = [vp, C.c_int, vp]
     L.igafd_set_stencil_stages.argtypes = [vp, C.c_int]
@@ -266,6 +267,20 @@ def mp_subdomain(m, glob, fixed, qa, qb, direction):
            "mp_subdomain")
     shp = tuple(int(shape[k]) for k in range(dim))
     return rows[:int(_np.prod(shp))].copy(), shp
+
+
+class Peaks(C.Structure):
+    _fields_ = [("fp64_tflops", C.c_double), ("tf32_tflops", C.c_double),
+                ("bf16_tflops", C.c_double), ("sm_max_mhz", C.c_double)]
+
+
+def probe_peaks(device=0):
+    """Measured FP64-pipe and tensor-core (TF32, BF16) rates of the device,
+    TFLOP/s (igafd_probe_peaks)."""
+    pk = Peaks()
+    _check(lib().igafd_probe_peaks(int(device), C.byref(pk)), "probe_peaks")
+    return {"fp64_tflops": pk.fp64_tflops, "tf32_tflops": pk.tf32_tflops,
+            "bf16_tflops": pk.bf16_tflops, "sm_max_mhz": pk.sm_max_mhz}
 
 
 def kernel_launches():

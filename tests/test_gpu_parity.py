@@ -624,3 +624,22 @@ def test_batch_grouping_and_argument_errors(torch):
         assert e.value.status == igafd.ERR_ARG
     for p in patches:
         p.close()
+
+
+def test_probed_peaks_are_plausible(torch):
+    """igafd_probe_peaks: the FP64 FMA rate lies near the pipe's unit count
+    (152 SMs x 2 FMA/clk at the SM clock), the BF16 tensor rate near the
+    measured cuBLAS BF16 rate, and TF32 below BF16 (each MMA step carries half
+    the K of a BF16 one)."""
+    import json
+    import os
+    from paper_1602_01636_gb300 import igafd
+    pk = igafd.probe_peaks(0)
+    derived = 152 * 2 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    assert 0.5 * derived <= pk["fp64_tflops"] <= 1.1 * derived, pk
+    assert 0 < pk["tf32_tflops"] < pk["bf16_tflops"], pk
+    path = os.path.join(os.path.dirname(__file__), "..", "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        bf16 = json.load(open(path))["bf16_tflops"]
+        assert 0.5 * bf16 <= pk["bf16_tflops"] <= 1.5 * bf16, (pk, bf16)
+    print("probed peaks", pk)
