@@ -416,14 +416,25 @@ def gpu_id(torch):
 
 def stencil_traffic(p, n):
     """dram bytes per launch of the stencil kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_1602_01636_gb300", "csrc", "stencil.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    summary, if it was taken on the current kernel source (else None): the
+    single-launch kernel (stencil.cu) and the per-CTA pipeline it runs
+    (stencil_dev.cuh), hashed together."""
+    return _traffic_from_summary(p, n, stencil_source_sha())
+
+
+def stencil_source_sha():
+    h = hashlib.sha256()
+    for f in ("stencil.cu", "stencil_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1602_01636_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_summary(p, n, sha):
     path = os.path.join(ROOT, "profiles", f"stencil_n{n}_p{p}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    m_sha = re.search(r"stencil\.cu sha256\[:16\][^:\n]*:\s*([0-9a-f]+)", txt)
+    m_sha = re.search(r"stencil sources sha256\[:16\][^:\n]*:\s*([0-9a-f]+)", txt)
     m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not m_sha or not m_tr or m_sha.group(1) != sha:
         return None
