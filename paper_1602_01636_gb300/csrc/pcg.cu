@@ -789,17 +789,22 @@ extern "C" igafd_status igafd_pcg_solve(igafd_patch *P, const igafd_pcg_opts *op
 }
 
 // ---- batched solve -----------------------------------------------------------
-// Many problems advance together, driven on the device: one CUDA graph holds a
-// conditional while-node whose body is one PCG iteration of every unfinished
-// problem, as a few launches over all of them -- the stencil q = A p (one
-// persistent work-queue launch per (dim, p, rows) class), x/r update,
-// periodic true residual, convergence confirmation and its decision, the FD
-// (one launch per fused kind for problems on the generic tensor-core FD,
-// the problem's own FD launches otherwise), (r, z) and p update -- and a
-// kernel that keeps the loop going while any problem is unfinished. Every
-// problem's work items are CTAs of its own single-problem grids, so the
-// iterates are bitwise those of igafd_pcg_solve. The host synchronises once
-// before the loop (to read every (b, b)) and once after it.
+// Many problems advance on the device, in groups of like size. A group's loop
+// is a CUDA graph holding a conditional while-node whose body is one pass: a
+// PCG iteration of every unfinished member, as a few launches over all of
+// them -- a compaction that lists the unfinished members, the stencil q = A p
+// (one launch per (dim, p, ring stages, rows) class: persistent and
+// queue-fed in a group of several problems, the single solve's grid in a
+// group of one), x/r update, periodic true residual, convergence
+// confirmation and its decision, the FD (one launch per fused kind for
+// problems on the generic tensor-core FD, the problem's own FD launches
+// otherwise), (r, z) and p update -- and a kernel that keeps the loop going
+// while any member is unfinished. The groups' graphs run concurrently, each
+// on its own stream. Every problem's work items are CTAs of its own
+// single-problem grids, so the iterates are bitwise those of
+// igafd_pcg_solve. The host synchronises once before the loops (to read
+// every (b, b)) and once after them, and in between only polls completion
+// events when a loop's launch is bounded to a number of passes.
 
 struct BatchClass {             // problems whose stencil shares (dim, p, ring stages, rows)
   int dim, p, stages, rows;

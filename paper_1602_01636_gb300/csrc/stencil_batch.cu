@@ -4,8 +4,9 @@
 
 namespace {
 
-// Many problems in one persistent launch: every CTA takes work items from
-// an atomic queue, in order, each item (problem i, virtual CTA v) running CTA
+// Many problems in one launch: with a queue every (persistent) CTA takes work
+// items from it, in order; without one CTA b runs item b. Each item (problem
+// i, virtual CTA v) runs CTA
 // v of problem i's own single-problem grid -- the same tiles, the same fused
 // dot and the same last-CTA sum -- so each problem's result is bitwise that
 // of its own launch. Only the problems still unfinished at the start of the
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_batch_kernel(const Ste
   }
 }
 
-// ---- batched launches (one persistent launch for many problems) ----------
+// ---- batched launches (one launch for many problems) ----------------------
 template <int DIM, int P, int MODE, int kStages, int R>
 igafd_status batch_launch_one(const StencilArgs *args, const int *act_idx, const long long *act_start,
                               const int *act_count, int sel, unsigned long long *queue,
