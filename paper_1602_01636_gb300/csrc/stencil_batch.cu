@@ -6,18 +6,18 @@ namespace {
 
 // Many problems in one launch: with a queue every (persistent) CTA takes work
 // items from it, in order; without one CTA b runs item b. Each item (problem
-// i, virtual CTA v) runs CTA
-// v of problem i's own single-problem grid -- the same tiles, the same fused
-// dot and the same last-CTA sum -- so each problem's result is bitwise that
-// of its own launch. Only the problems still unfinished at the start of the
-// pass are listed (the pass's compaction kernel writes the list): act_idx[k]
-// is the k-th listed problem's row of args, act_start[k] .. act_start[k + 1]
-// its items, *act_count the list's length. sel: 0 = q = A p of the PCG
-// iteration (problems not yet done), 1 = the periodic true residual (running
-// problems whose iteration count is a multiple of args.every), 2 = the
-// convergence confirmation (problems the recurrence says converged, status
-// ok, not yet finished). The ring's barriers persist across items (one
-// running stage count); the list is cached in shared memory when short.
+// i, virtual CTA v) runs CTA v of problem i's own single-problem grid -- the
+// same tiles, the same fused dot and the same last-CTA sum -- so each
+// problem's result is bitwise that of its own launch. Only the problems still
+// unfinished at the start of the pass are listed (the pass's compaction kernel
+// writes the list): act_idx[k] is the k-th listed problem's row of args,
+// act_start[k] .. act_start[k + 1] its items, *act_count the list's length.
+// sel: 0 = q = A p of the PCG iteration (problems not yet done), 1 = the
+// periodic true residual (running problems whose iteration count is a
+// multiple of args.every), 2 = the convergence confirmation (problems the
+// recurrence says converged, status ok, not yet finished). The ring's
+// barriers persist across items (one running stage count); the list is
+// cached in shared memory when short.
 constexpr int kListCache = 64;
 template <int DIM, int P, int MODE, int kStages, int R>
 __global__ void __launch_bounds__(kTile / R + 32) stencil_batch_kernel(const StencilArgs *args,
