@@ -182,19 +182,42 @@ __device__ __forceinline__ void store_tile(const T *tile, const LineArgs<T> &a, 
 }
 
 // out(l, i) = base(l, i) + sum_{|o| <= p} coef(i, o) x(l, i + o) over the
-// CTA's lines; coef(i, o) reads the staged bands
-template <int MODE, typename T, typename C, typename B>
-__device__ __forceinline__ void band_product(const LineArgs<T> &a, T *out, const T *x, int p, int nv,
-                                             C coef, B base) {
+// CTA's lines; coef(i, o) reads the staged bands. Terms are added in
+// increasing o, those outside the line skipped; P > 0 is the compile-time band
+// half-width (an unrolled sum whose skipped terms are predicated off, so the
+// lanes of a warp never split between paths), P = 0 the run-time one.
+template <int MODE, int P, typename T, typename C, typename B>
+__device__ __forceinline__ void band_product_p(const LineArgs<T> &a, T *out, const T *x, int p,
+                                               int nv, C coef, B base) {
   const int len = a.len;
   for (int e = threadIdx.x; e < len * kL; e += kT) {
     int l, i;
     entry<MODE>(a, e, l, i);
     if (l >= nv) continue;
     T acc = base(l, i);
-    const int olo = i - p < 0 ? -i : -p, ohi = i + p >= len ? len - 1 - i : p;
-    for (int o = olo; o <= ohi; ++o) acc += coef(i, o) * x[tix<MODE>(len, l, i + o)];
+    if (P > 0) {
+#pragma unroll
+      for (int o = -P; o <= P; ++o) {
+        const int j = i + o;
+        if (j >= 0 && j < len) acc += coef(i, o) * x[tix<MODE>(len, l, j)];
+      }
+    } else {
+      const int olo = i - p < 0 ? -i : -p, ohi = i + p >= len ? len - 1 - i : p;
+      for (int o = olo; o <= ohi; ++o) acc += coef(i, o) * x[tix<MODE>(len, l, i + o)];
+    }
     out[tix<MODE>(len, l, i)] = acc;
+  }
+}
+
+template <int MODE, typename T, typename C, typename B>
+__device__ __forceinline__ void band_product(const LineArgs<T> &a, T *out, const T *x, int p, int nv,
+                                             C coef, B base) {
+  switch (p) {
+    case 1: band_product_p<MODE, 1>(a, out, x, p, nv, coef, base); break;
+    case 2: band_product_p<MODE, 2>(a, out, x, p, nv, coef, base); break;
+    case 3: band_product_p<MODE, 3>(a, out, x, p, nv, coef, base); break;
+    case 4: band_product_p<MODE, 4>(a, out, x, p, nv, coef, base); break;
+    default: band_product_p<MODE, 0>(a, out, x, p, nv, coef, base);
   }
 }
 
