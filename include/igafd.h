@@ -83,7 +83,8 @@ typedef struct {
   const int *kappa_n_knots;
   const double *const *kappa_knots;
   const double *kappa_ctrl;
-  int flags;                        /* 0, IGAFD_SETUP_NO_STENCIL or IGAFD_SETUP_FULL_SPACE */
+  int flags;                        /* 0, IGAFD_SETUP_NO_STENCIL, IGAFD_SETUP_FULL_SPACE or
+                                       IGAFD_SETUP_HALF_STENCIL */
 } igafd_patch_desc;
 
 /* igafd_patch_desc.flags: build everything but the stiffness stencil (no
@@ -106,6 +107,21 @@ typedef struct {
  * igafd_copy_stencil, igafd_quad_points and the load vectors work on the full
  * space. May be combined with nothing else. */
 #define IGAFD_SETUP_FULL_SPACE 2
+
+/* igafd_patch_desc.flags: store the stiffness stencil by its symmetry
+ * (A_ij = A_ji, Eq. (A)): only the offsets delta >= 0 in the order of the
+ * offset index (delta_d, ..., delta_1) are kept, ((2p+1)^d + 1) / 2 of the
+ * (2p+1)^d, each a row array with zero halos; a coupling with delta < 0 of
+ * row i is the stored coupling -delta of row i + off(delta). The bytes of A
+ * are about halved; the FMAs per row, and so the time of a product on GB300
+ * (bound by the FP64 pipe), are the same. Every call that uses A works on
+ * such a patch (igafd_copy_stencil expands it to the full layout); the
+ * stencil pipeline runs with its default ring depth (the autotuner tunes
+ * the rows per thread only). A product differs from the full stencil's at
+ * the rounding level: the assembled couplings A_ij and A_ji are summed in
+ * different orders, and the half stencil uses A_ij for both. May not be
+ * combined with IGAFD_SETUP_NO_STENCIL or IGAFD_SETUP_FULL_SPACE. */
+#define IGAFD_SETUP_HALF_STENCIL 4
 
 typedef struct {
   int dim, p;
@@ -131,6 +147,8 @@ typedef struct {
   int fd_tile[3][4];   /* tile shape per operand type (TF32, BF16, FP16; autotuned, see
                           igafd_set_fd_tile): rows per CTA of the per-mode kernel, its column
                           tiles (1 or 2), its K stages, columns per CTA of the fused pencil kernel */
+  int stencil_half;    /* 1 if the stencil stores only the offsets from the centre up
+                          (IGAFD_SETUP_HALF_STENCIL), 0 if all (2p+1)^d */
 } igafd_patch_info;
 
 typedef struct {

@@ -91,7 +91,18 @@ igafd_status build(igafd_patch *P, const igafd_patch_desc *d, cudaStream_t s) {
   IGAFD_TRY(alloc(&P->inv_lam32, (size_t)N));
   P->Np = igafd_stencil_row_stride(N);
   const bool with_stencil = !(d->flags & IGAFD_SETUP_NO_STENCIL);
-  if (with_stencil) IGAFD_TRY(alloc(&P->stencil, (size_t)P->n_off * P->Np));
+  P->stencil_half = (d->flags & IGAFD_SETUP_HALF_STENCIL) ? 1 : 0;
+  if (P->stencil_half) {
+    // halo: the largest |off(delta)| plus two rows (the odd-start fetch of a
+    // mirrored run reads one row before it and one after), even
+    long long mo = 1, str = 1;
+    for (int k = 0; k < P->dim; ++k) { mo += (long long)P->p * str; str *= P->n[k]; }
+    P->sh_H = (mo + 2 + 1) / 2 * 2;
+    P->sh_ld = P->Np + 2 * P->sh_H;
+  }
+  if (with_stencil)
+    IGAFD_TRY(alloc(&P->stencil, P->stencil_half ? (size_t)((P->n_off + 1) / 2) * P->sh_ld
+                                                 : (size_t)P->n_off * P->Np));
   IGAFD_TRY(alloc(&P->fd_a, (size_t)N));
   IGAFD_TRY(alloc(&P->fd_b, (size_t)N));
   IGAFD_TRY(alloc(&P->r, (size_t)N));
@@ -184,6 +195,11 @@ extern "C" igafd_status igafd_setup_patch(const igafd_patch_desc *d, void *strea
     if (d->n_knots[k] - d->p - 1 < 3) return IGAFD_ERR_ARG;   // at least one interior dof
     if (d->n_knots[k] - d->p - 3 > 1024) return IGAFD_ERR_ARG; // eigen-solver limit
   }
+  if ((d->flags & IGAFD_SETUP_HALF_STENCIL) &&
+      (d->flags & (IGAFD_SETUP_NO_STENCIL | IGAFD_SETUP_FULL_SPACE)))
+    return IGAFD_ERR_ARG;
+  if (d->flags & ~(IGAFD_SETUP_NO_STENCIL | IGAFD_SETUP_FULL_SPACE | IGAFD_SETUP_HALF_STENCIL))
+    return IGAFD_ERR_ARG;
   igafd_patch *P = (igafd_patch *)calloc(1, sizeof(igafd_patch));
   if (!P) return IGAFD_ERR_OOM;
   P->dim = d->dim;
@@ -246,7 +262,11 @@ extern "C" igafd_status igafd_patch_query(const igafd_patch *P, igafd_patch_info
   info->q_bound = P->q_bound;
   info->setup_ms = P->setup_ms;
   info->eig_ms = P->eig_ms;
-  info->stencil_bytes = P->stencil ? (long long)P->n_off * P->N * (long long)sizeof(double) : 0;
+  info->stencil_bytes =
+      P->stencil ? (long long)(P->stencil_half ? (P->n_off + 1) / 2 : P->n_off) * P->N *
+                       (long long)sizeof(double)
+                 : 0;
+  info->stencil_half = P->stencil_half;
   info->stencil_stages = P->stencil_stages > 0 ? P->stencil_stages : 4;
   info->stencil_rows = P->stencil_rows == 2 ? 2 : 1;
   for (int k = 0; k < 3; ++k) {
@@ -280,6 +300,7 @@ extern "C" igafd_status igafd_get_eigen(const igafd_patch *P, int k, double *U_h
 extern "C" igafd_status igafd_copy_stencil(const igafd_patch *P, double *dst, void *stream) {
   if (!P || !dst || !P->stencil) return IGAFD_ERR_ARG;
   IGAFD_CUDA(cudaSetDevice(P->dev));
+  if (P->stencil_half) return igafd_stencil_expand(P, dst, (cudaStream_t)stream);
   IGAFD_CUDA(cudaMemcpy2DAsync(dst, P->N * sizeof(double), P->stencil, P->Np * sizeof(double),
                                P->N * sizeof(double), P->n_off, cudaMemcpyDeviceToDevice,
                                (cudaStream_t)stream));

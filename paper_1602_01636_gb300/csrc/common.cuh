@@ -90,9 +90,13 @@ struct igafd_patch {
   float *U32[3];
   double *inv_lam;
   float *inv_lam32;
-  // stiffness stencil [n_off][Np], Np = N rounded up to the stencil tile
+  // stiffness stencil [n_off][Np], Np = N rounded up to the stencil tile; with
+  // stencil_half, [(n_off + 1) / 2][sh_ld]: offsets from the centre up, row
+  // i at sh_H + i (zero halos of sh_H rows on both ends, sh_ld = Np + 2 sh_H)
   double *stencil;
   long long Np;
+  int stencil_half;
+  long long sh_H, sh_ld;
   int num_sms;
   int stencil_stages;           // ring depth of the stencil pipeline (0: default; autotuned)
   int stencil_rows;             // rows per compute thread of the stencil (1 or 2 in 3D; autotuned)
@@ -155,6 +159,8 @@ igafd_status igafd_build_prec(igafd_patch *P, cudaStream_t s);
 igafd_status igafd_setup_pencils_eig(igafd_patch *P, cudaStream_t s, const double *const *wK = nullptr,
                                      const double *const *wM = nullptr);
 igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s);
+// a half-stored stencil written out in the full layout [n_off][N] (setup.cu)
+igafd_status igafd_stencil_expand(const igafd_patch *P, double *dst, cudaStream_t s);
 // dense (Dirichlet-reduced) pencils K_k, M_k of direction k into K, M (n_k x
 // n_k each, device), span-scaled when the patch carries scalings
 igafd_status igafd_pencils_dense(igafd_patch *P, int k, double *K, double *M, cudaStream_t s);

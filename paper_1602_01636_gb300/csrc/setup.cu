@@ -152,9 +152,13 @@ __global__ void geo_check_kernel(PV v, long long nqp, double *part) {
 // a time in shared memory (each (r, s) term belongs to exactly one pattern,
 // so nothing is recomputed; the stencil is accumulated once per pattern).
 // Needed for p >= 5 in 3D, where all four patterns would not fit.
+// The stencil entry of offset index o and row i goes to
+// stencil[(o - o_min) ld + H + i]; offsets below o_min are not stored (the
+// full layout: o_min = 0, H = 0, ld = Np; the half layout: o_min the centre).
 template <int DIM, bool PERPAT>
 __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
-                                double *__restrict__ stencil, long long Np) {
+                                double *__restrict__ stencil, long long ld, int o_min,
+                                long long H) {
   extern __shared__ double sm[];
   const int p = v.p, A = p + 1, nq = p + 1, W = 2 * p + 1;
   const int nqd = DIM == 3 ? nq * nq * nq : nq * nq;
@@ -287,7 +291,7 @@ __global__ void assemble_kernel(PV v, int c1, int c2, int c3, int ne1, int ne2,
     }
     int o = 0, ws = 1;
     for (int k = 0; k < DIM; ++k) { o += (dl[k] + p) * ws; ws *= W; }
-    stencil[(size_t)o * Np + row] += val;
+    if (o >= o_min) stencil[(size_t)(o - o_min) * ld + H + row] += val;
   }
   __syncthreads();
   }   // pattern pass
@@ -488,7 +492,9 @@ igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s) {
   P->q_bound = lmax / lmin;
   if (!(mdet > 0.0)) return IGAFD_ERR_FOLDED;
   // stiffness stencil
-  IGAFD_CUDA(cudaMemsetAsync(P->stencil, 0, (size_t)P->n_off * P->Np * sizeof(double), s));
+  const int o_min = P->stencil_half ? P->n_off / 2 : 0;
+  const long long ld = P->stencil_half ? P->sh_ld : P->Np, H = P->stencil_half ? P->sh_H : 0;
+  IGAFD_CUDA(cudaMemsetAsync(P->stencil, 0, (size_t)(P->n_off - o_min) * ld * sizeof(double), s));
   const bool perpat = dim == 3 && assemble_smem(dim, p, false) > 200 * 1024;
   size_t smem = assemble_smem(dim, p, perpat);
   if (smem > 200 * 1024) return IGAFD_ERR_ARG;
@@ -511,13 +517,45 @@ igafd_status igafd_setup_stencil(igafd_patch *P, cudaStream_t s) {
         long long nb = (long long)ne1 * ne2 * ne3;
         if (nb == 0) continue;
         if (dim == 3 && perpat)
-          assemble_kernel<3, true><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, P->Np);
+          assemble_kernel<3, true><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, ld, o_min, H);
         else if (dim == 3)
-          assemble_kernel<3, false><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, P->Np);
+          assemble_kernel<3, false><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, c3, ne1, ne2, P->stencil, ld, o_min, H);
         else
-          assemble_kernel<2, false><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, 0, ne1, ne2, P->stencil, P->Np);
+          assemble_kernel<2, false><<<(unsigned)nb, 256, smem, s>>>(v, c1, c2, 0, ne1, ne2, P->stencil, ld, o_min, H);
         IGAFD_CUDA(cudaGetLastError());
       }
+  return IGAFD_OK;
+}
+
+// dst[o][i] (o < n_off, i < N, row stride N) from a half-stored stencil: the
+// stored offsets as they are, the others as the stored coupling -delta of
+// row i + off(delta) (zero where that row lies outside the box: the halo).
+__global__ void expand_half_kernel(const double *__restrict__ S, long long ld, long long H, int p,
+                                   int dim, int n1, int n2, int n_off, long long N,
+                                   double *__restrict__ dst) {
+  const int W = 2 * p + 1, oc = n_off / 2;
+  const long long total = (long long)n_off * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)(t / N);
+    const long long i = t - (long long)o * N;
+    double v;
+    if (o >= oc) {
+      v = S[(size_t)(o - oc) * ld + H + i];
+    } else {
+      const int d1 = o % W - p, d2 = (o / W) % W - p, d3 = dim == 3 ? o / (W * W) - p : 0;
+      const long long off = d1 + (long long)d2 * n1 + (long long)d3 * n1 * n2;
+      v = S[(size_t)(n_off - 1 - o - oc) * ld + H + i + off];
+    }
+    dst[t] = v;
+  }
+}
+
+igafd_status igafd_stencil_expand(const igafd_patch *P, double *dst, cudaStream_t s) {
+  expand_half_kernel<<<1216, 256, 0, s>>>(P->stencil, P->sh_ld, P->sh_H, P->p, P->dim, P->n[0],
+                                          P->n[1], P->n_off, P->N, dst);
+  IGAFD_LAUNCHED(1);
+  IGAFD_CUDA(cudaGetLastError());
   return IGAFD_OK;
 }
 

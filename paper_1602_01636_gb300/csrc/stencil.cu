@@ -11,7 +11,7 @@ namespace {
 // MODE 1: y = b - A x, dot (y, y) -> true (r, r) when pcg; with z given also
 // (y, z) -> (r, z_old) of the flexible beta, so that a recomputed residual
 // replaces the recurrence one in every scalar that uses it.
-template <int DIM, int P, int MODE, int kStages, int R>
+template <int DIM, int P, int MODE, int kStages, int R, bool HALF>
 __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs a) {
   pdl_wait();
   pdl_trigger();
@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
   if (a.tstat && threadIdx.x == 0) atomicMin(&a.tstat[0], global_ns());
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double *ring = reinterpret_cast<double *>(smem_raw);              // [kStages][STAGE]
-  uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * Geom<P>::STAGE);
+  uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * Geom<P, HALF>::STAGE);
   uint64_t *empty = full + kStages;
   __shared__ volatile int s_abort;
   if (threadIdx.x == 0) {
@@ -29,17 +29,19 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_tma_kernel(StencilArgs
   }
   __syncthreads();
   long long gstage = 0;
-  stencil_cta<DIM, P, MODE, kStages, R>(a, blockIdx.x, gridDim.x, ring, full, empty, gstage, &s_abort);
+  stencil_cta<DIM, P, MODE, kStages, R, HALF>(a, blockIdx.x, gridDim.x, ring, full, empty, gstage,
+                                              &s_abort);
 }
 
 // One launch of the single-problem kernel, or with grid_out only its grid
 // (the resident CTAs of every SM, at most grid_cap).
-template <int DIM, int P, int MODE, int kStages, int R>
+template <int DIM, int P, int MODE, int kStages, int R, bool HALF = false>
 igafd_status launch_one(const StencilArgs &a, long long grid_cap, int num_sms, cudaStream_t s,
                         long long *grid_out) {
-  const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
+  const size_t smem =
+      (size_t)kStages * Geom<P, HALF>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
   constexpr int kBlock = kTile / R + 32;
-  auto kern = stencil_tma_kernel<DIM, P, MODE, kStages, R>;
+  auto kern = stencil_tma_kernel<DIM, P, MODE, kStages, R, HALF>;
   static std::atomic<unsigned long long> attr_set{0};
   static std::atomic<int> per_sm_tab[64];
   int per_sm = 1;
@@ -65,9 +67,19 @@ igafd_status launch_rows(int rows, const StencilArgs &a, long long cap, int sms,
   return launch_one<DIM, P, MODE, kStages, 1>(a, cap, sms, s, grid_out);
 }
 
+// a half-stored stencil runs at the default ring depth
+template <int DIM, int P, int MODE>
+igafd_status launch_half(int rows, const StencilArgs &a, long long cap, int sms, cudaStream_t s,
+                         long long *grid_out) {
+  if constexpr (DIM == 3)
+    if (rows == 2) return launch_one<DIM, P, MODE, kStagesDefault, 2, true>(a, cap, sms, s, grid_out);
+  return launch_one<DIM, P, MODE, kStagesDefault, 1, true>(a, cap, sms, s, grid_out);
+}
+
 template <int DIM, int P, int MODE>
 igafd_status launch_stages(int stages, int rows, const StencilArgs &a, long long cap, int sms,
                            cudaStream_t s, long long *grid_out) {
+  if (stages < 0) return launch_half<DIM, P, MODE>(rows, a, cap, sms, s, grid_out);
   switch (stages) {
     case 3: return launch_rows<DIM, P, MODE, 3>(rows, a, cap, sms, s, grid_out);
     case 6: return launch_rows<DIM, P, MODE, 6>(rows, a, cap, sms, s, grid_out);
@@ -118,7 +130,9 @@ static StencilArgs make_args(igafd_patch *P, const double *x, double *y, const d
   a.n2 = P->n[1];
   a.n3 = P->n[2];
   a.N = P->N;
-  a.Np = P->Np;
+  a.Np = P->stencil_half ? P->sh_ld : P->Np;
+  a.oc = P->stencil_half ? P->n_off / 2 : 0;
+  a.shH = P->stencil_half ? P->sh_H : 0;
   a.ntiles = (P->N + kTile - 1) / kTile;
   a.partial = pcg ? P->partial : nullptr;
   a.counter = P->counter;
@@ -149,7 +163,8 @@ igafd_status igafd_stencil_launch(igafd_patch *P, const double *x, double *y, co
   // persistent grid: the resident CTAs of every SM, never more than the
   // tiles or the partial-sum slots
   const long long cap = grid_cap(P);
-  const int st = P->stencil_stages > 0 ? P->stencil_stages : kStagesDefault;
+  // ring depth; -1 selects the half-stored stencil's kernels (default depth)
+  const int st = P->stencil_half ? -1 : P->stencil_stages > 0 ? P->stencil_stages : kStagesDefault;
   const int rows = P->stencil_rows == 2 ? 2 : 1;
   if (P->dim == 3) {
     if (b) return launch_p<3, 1>(P->p, st, rows, a, cap, P->num_sms, s);
@@ -173,7 +188,8 @@ igafd_status igafd_stencil_batch_args(igafd_patch *P, int sel, int flexible, int
                                              nullptr, flexible ? P->z : nullptr);
   memcpy(out, &a, sizeof(a));
   const long long cap = grid_cap(P);
-  const int st = P->stencil_stages > 0 ? P->stencil_stages : kStagesDefault;
+  // ring depth; -1 selects the half-stored stencil's kernels (default depth)
+  const int st = P->stencil_half ? -1 : P->stencil_stages > 0 ? P->stencil_stages : kStagesDefault;
   const int rows = P->dim == 3 && P->stencil_rows == 2 ? 2 : 1;
   if (P->dim == 3) {
     if (sel) return launch_p<3, 1>(P->p, st, rows, a, cap, P->num_sms, nullptr, vgrid);

@@ -19,7 +19,7 @@ namespace {
 // barriers persist across items (one running stage count); the list is
 // cached in shared memory when short.
 constexpr int kListCache = 64;
-template <int DIM, int P, int MODE, int kStages, int R>
+template <int DIM, int P, int MODE, int kStages, int R, bool HALF>
 __global__ void __launch_bounds__(kTile / R + 32) stencil_batch_kernel(const StencilArgs *args,
                                                                       const int *act_idx,
                                                                       const long long *act_start,
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_batch_kernel(const Ste
                                                                       unsigned long long *queue) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double *ring = reinterpret_cast<double *>(smem_raw);
-  uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * Geom<P>::STAGE);
+  uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * Geom<P, HALF>::STAGE);
   uint64_t *empty = full + kStages;
   __shared__ volatile int s_abort;
   __shared__ long long s_item;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_batch_kernel(const Ste
       }
       __syncthreads();
       const int k = s_k;
-      stencil_cta<DIM, P, MODE, kStages, R>(s_args, it - st[k], st[k + 1] - st[k], ring, full,
+      stencil_cta<DIM, P, MODE, kStages, R, HALF>(s_args, it - st[k], st[k + 1] - st[k], ring, full,
                                             empty, gstage, &s_abort);
     }
     __syncthreads();
@@ -97,13 +97,14 @@ __global__ void __launch_bounds__(kTile / R + 32) stencil_batch_kernel(const Ste
 }
 
 // ---- batched launches (one launch for many problems) ----------------------
-template <int DIM, int P, int MODE, int kStages, int R>
+template <int DIM, int P, int MODE, int kStages, int R, bool HALF = false>
 igafd_status batch_launch_one(const StencilArgs *args, const int *act_idx, const long long *act_start,
                               const int *act_count, int sel, unsigned long long *queue,
                               long long items, int num_sms, cudaStream_t s) {
-  const size_t smem = (size_t)kStages * Geom<P>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
+  const size_t smem =
+      (size_t)kStages * Geom<P, HALF>::STAGE * sizeof(double) + 2 * kStages * sizeof(uint64_t);
   constexpr int kBlock = kTile / R + 32;
-  auto kern = stencil_batch_kernel<DIM, P, MODE, kStages, R>;
+  auto kern = stencil_batch_kernel<DIM, P, MODE, kStages, R, HALF>;
   static std::atomic<unsigned long long> attr_set{0};
   static std::atomic<int> per_sm_tab[64];
   int per_sm = 1;
@@ -129,6 +130,14 @@ template <int DIM, int P, int MODE>
 igafd_status batch_launch_sr(int stages, int rows, const StencilArgs *args, const int *ai,
                              const long long *as, const int *ac, int sel,
                              unsigned long long *queue, long long items, int sms, cudaStream_t s) {
+  if (stages < 0) {                               // half-stored stencils: default depth
+    if constexpr (DIM == 3)
+      if (rows == 2)
+        return batch_launch_one<DIM, P, MODE, kStagesDefault, 2, true>(args, ai, as, ac, sel, queue,
+                                                                       items, sms, s);
+    return batch_launch_one<DIM, P, MODE, kStagesDefault, 1, true>(args, ai, as, ac, sel, queue,
+                                                                   items, sms, s);
+  }
   if constexpr (DIM == 3) {
     if (rows == 2) {
       if (stages == 3) return batch_launch_one<DIM, P, MODE, 3, 2>(args, ai, as, ac, sel, queue, items, sms, s);
@@ -177,13 +186,15 @@ igafd_status igafd_stencil_batch_launch(int dim, int p, int stages, int rows, in
       return batch_launch_p<3, 1>(p, stages, rows, args, ai, as, ac, sel, queue, items, num_sms, s);
     return batch_launch_p<3, 0>(p, stages, rows, args, ai, as, ac, sel, queue, items, num_sms, s);
   }
-  if (sel) return batch_launch_p<2, 1>(p, 0, 1, args, ai, as, ac, sel, queue, items, num_sms, s);
-  return batch_launch_p<2, 0>(p, 0, 1, args, ai, as, ac, sel, queue, items, num_sms, s);
+  const int st2 = stages < 0 ? -1 : 0;            // 2D: the default depth (or the half kernels)
+  if (sel) return batch_launch_p<2, 1>(p, st2, 1, args, ai, as, ac, sel, queue, items, num_sms, s);
+  return batch_launch_p<2, 0>(p, st2, 1, args, ai, as, ac, sel, queue, items, num_sms, s);
 }
 
 // The stage count the batched launch uses for this patch: that of its single
-// launch (3D), the default otherwise.
+// launch (3D), the default otherwise; -1 for a half-stored stencil.
 int igafd_stencil_batch_stages(const igafd_patch *P) {
+  if (P->stencil_half) return -1;                // the half-stored stencil's kernels
   const int st = P->stencil_stages > 0 ? P->stencil_stages : kStagesDefault;
   return P->dim == 3 && (st == 3 || st == 6) ? st : kStagesDefault;
 }

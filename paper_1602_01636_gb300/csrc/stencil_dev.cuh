@@ -110,6 +110,10 @@ struct StencilArgs {
   int *err;           // set on an mbarrier timeout
   int every;          // > 0: run only when scal[S_ITER] is a multiple of every
   unsigned long long *tstat;  // optional device timing (see igafd_patch::tstat)
+  // half-stored stencil (the HALF kernels): S is [(n_off + 1) / 2][Np] with
+  // Np the row stride, offsets from oc (the centre) up, row i at shH + i
+  int oc;
+  long long shH;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -118,11 +122,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-template <int P>
+template <int P, bool HALF = false>
 struct Geom {
   static constexpr int W = 2 * P + 1;
+  // coefficient run stride in a ring stage: a tile, or (half-stored stencil)
+  // a tile and two rows, so that a mirrored run can start one row early
+  static constexpr int RS = HALF ? kTile + 2 : kTile;
   static constexpr int XW = (kTile + 2 * P + 2 + 1) & ~1;   // x window (even count)
-  static constexpr int STAGE = W * kTile + XW;               // doubles per ring stage
+  static constexpr int STAGE = W * RS + XW;                  // doubles per ring stage
 };
 
 // Warp-specialised pipeline: the compute warps take R consecutive rows per
@@ -143,12 +150,22 @@ struct Geom {
 // dot's fixed-order sum over the vgrid partial sums. The ring's barriers are
 // initialised by the caller; gstage counts the ring stages this CTA has
 // passed through so far, so a persistent CTA can keep its ring across calls.
-template <int DIM, int P, int MODE, int kStages, int R>
+//
+// HALF: the stencil is stored by its symmetry (offsets from the centre up).
+// The run of a stored offset o is S[o - oc][shH + row0 ...]; the run of an
+// offset o below the centre (delta < 0) is the mirrored offset's run shifted
+// by off(delta) rows, S[mirror(o) - oc][shH + row0 + off ...], fetched from
+// the even row at or before its start so that every bulk copy is 16-byte
+// aligned; every run is RS = kTile + 2 rows long and the compute warps read a
+// mirrored run one row later when its start was odd.
+template <int DIM, int P, int MODE, int kStages, int R, bool HALF = false>
 __device__ __forceinline__ void stencil_cta(const StencilArgs &a, long long vb, long long vgrid,
                                             double *ring, uint64_t *full, uint64_t *empty,
                                             long long &gstage, volatile int *s_abort) {
-  using Gm = Geom<P>;
+  using Gm = Geom<P, HALF>;
   constexpr int W = Gm::W;
+  constexpr int RS = Gm::RS;
+  constexpr int NOFF = DIM == 3 ? W * W * W : W * W;
   constexpr int G = DIM == 3 ? W * W : W;        // (delta_2, delta_3) groups per tile
   constexpr uint32_t kStageBytes = Gm::STAGE * sizeof(double);
   constexpr int kCompute = kTile / R;            // compute threads
@@ -187,9 +204,24 @@ __device__ __forceinline__ void stencil_cta(const StencilArgs &a, long long vb, 
         uint64_t *bar = &full[slot];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_tx(bar, kStageBytes);
-        for (int d1 = 0; d1 < W; ++d1)
-          bulk_g2s(st + d1 * kTile, a.S + (size_t)(ob + d1) * a.Np + row0, kTile * sizeof(double), bar);
-        bulk_g2s(st + W * kTile, a.x + x0, Gm::XW * sizeof(double), bar);
+        if constexpr (!HALF) {
+          for (int d1 = 0; d1 < W; ++d1)
+            bulk_g2s(st + d1 * kTile, a.S + (size_t)(ob + d1) * a.Np + row0, kTile * sizeof(double),
+                     bar);
+        } else {
+          for (int d1 = 0; d1 < W; ++d1) {
+            const int o = ob + d1;
+            long long start = a.shH + row0;
+            int arr = o - a.oc;
+            if (o < a.oc) {                                 // delta < 0: the mirrored run
+              arr = NOFF - 1 - o - a.oc;
+              start += (d1 - P) + (long long)d2 * a.n1 + (long long)d3 * n12;
+            }
+            start -= (start & 1);
+            bulk_g2s(st + d1 * RS, a.S + (size_t)arr * a.Np + start, RS * sizeof(double), bar);
+          }
+        }
+        bulk_g2s(st + W * RS, a.x + x0, Gm::XW * sizeof(double), bar);
         ++issued;
       }
       if (!ok) {
@@ -248,12 +280,46 @@ __device__ __forceinline__ void stencil_cta(const StencilArgs &a, long long vb, 
       for (int r = 0; r < R; ++r)
         in23 = in23 || (live[r] && (i2r[r] + d2 >= 0) && (i2r[r] + d2 < a.n2) &&
                         (DIM == 2 || ((i3r[r] + d3 >= 0) && (i3r[r] + d3 < a.n3))));
+      // HALF: run j of this group starts one row late when it is mirrored and
+      // its start row was odd
+      int hs[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) hs[j] = 0;
+      if constexpr (HALF) {
+        const int ob = (DIM == 3 ? (d3 + P) * W * W : 0) + (d2 + P) * W;
+        const long long pb = a.shH + row0 + (long long)d2 * a.n1 + (long long)d3 * n12 - P;
+#pragma unroll
+        for (int j = 0; j < W; ++j) hs[j] = ob + j < a.oc ? (int)((pb + j) & 1) : 0;
+      }
       if (__any_sync(0xffffffffu, in23)) {
         if constexpr (R == 1) {
           const double *cf = st + tid;
-          const double *xw = st + W * kTile + tid + sh;   // xw[j] = x[row + off - P + j]
+          const double *xw = st + W * RS + tid + sh;      // xw[j] = x[row + off - P + j]
 #pragma unroll
-          for (int j = 0; j < W; ++j) acc[0] = fma(cf[j * kTile], xw[j], acc[0]);
+          for (int j = 0; j < W; ++j) acc[0] = fma(cf[j * RS + hs[j]], xw[j], acc[0]);
+        } else if constexpr (HALF) {
+          // rows row, row + 1: coefficients st[j RS + 2 tid + hs[j]] and the next;
+          // x[row + off - P + j] = xv[j + sh], x[row + 1 + off - P + j] = xv[j + 1 + sh]
+          const double *cf = st + 2 * tid;
+          const double2 *xb = reinterpret_cast<const double2 *>(st + W * RS + 2 * tid);
+          constexpr int NP = (W + 1) / 2;
+          double xv[2 * NP + 2];
+#pragma unroll
+          for (int m = 0; m < NP + 1; ++m) { const double2 v = xb[m]; xv[2 * m] = v.x; xv[2 * m + 1] = v.y; }
+#pragma unroll
+          for (int j = 0; j < W; ++j) {
+            double c0, c1;
+            if (hs[j] == 0) {
+              const double2 c = *reinterpret_cast<const double2 *>(cf + j * RS);
+              c0 = c.x;
+              c1 = c.y;
+            } else {
+              c0 = cf[j * RS + 1];
+              c1 = cf[j * RS + 2];
+            }
+            acc[0] = fma(c0, xv[j + sh], acc[0]);
+            acc[1] = fma(c1, xv[j + 1 + sh], acc[1]);
+          }
         } else {
           // rows row, row + 1: coefficients cf[j] = (S[o_j][row], S[o_j][row + 1]);
           // x[row + off - P + j] = xv[j + sh], x[row + 1 + off - P + j] = xv[j + 1 + sh]

@@ -53,8 +53,8 @@ const int kCandidates[3] = {3, 4, 6};
 
 std::string tune_key(const igafd_patch *P) {
   char buf[128];
-  snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%d:sm%d", P->dim, P->p, P->n[0], P->n[1], P->n[2],
-           P->num_sms);
+  snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%d:sm%d%s", P->dim, P->p, P->n[0], P->n[1], P->n[2],
+           P->num_sms, P->stencil_half ? ":half" : "");
   return buf;
 }
 
@@ -177,6 +177,8 @@ extern "C" igafd_status igafd_autotune(igafd_patch *P, int flags, void *stream) 
   igafd_status st = IGAFD_OK;
   for (int c = 0; c < kNumCand; ++c) best.ms[c] = -1.0f;
   for (int c = 0; c < ncand && st == IGAFD_OK; ++c) {
+    // a half-stored stencil runs at the default depth: only its rows are tuned
+    if (P->stencil_half && kCandidates[c % 3] != 4) continue;
     P->stencil_stages = kCandidates[c % 3];
     P->stencil_rows = 1 + c / 3;
     st = igafd_stencil_launch(P, P->pv, P->q, nullptr, 0, 0, s);     // warm-up

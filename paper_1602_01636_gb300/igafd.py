@@ -44,6 +44,7 @@ class PatchDesc(C.Structure):
 
 SETUP_NO_STENCIL = 1
 SETUP_FULL_SPACE = 2
+SETUP_HALF_STENCIL = 4
 
 
 class PatchInfo(C.Structure):
@@ -53,7 +54,7 @@ class PatchInfo(C.Structure):
                 ("stencil_bytes", C.c_longlong), ("stencil_stages", C.c_int),
                 ("stencil_rows", C.c_int), ("eig_refined", C.c_int * 3),
                 ("eig_check", (C.c_double * 2) * 3), ("fd_fused", C.c_int * 3),
-                ("fd_tile", (C.c_int * 4) * 3)]
+                ("fd_tile", (C.c_int * 4) * 3), ("stencil_half", C.c_int)]
 
 
 class PCGOpts(C.Structure):
@@ -410,12 +411,13 @@ class Patch:
     """A single-patch problem set up on the current CUDA device."""
 
     def __init__(self, knots, p, ctrl, kappa=1.0, geo_knots=None, geo_p=None, kappa_field=None,
-                 stencil=True, full_space=False):
+                 stencil=True, full_space=False, half_stencil=False):
         """kappa_field: optional (knots, degree, control values) of a positive
         spline coefficient c(zeta); K = kappa * c. stencil=False builds the
         patch without A (geometry, features, separable fit and P only).
         full_space=True keeps every B-spline (no Dirichlet removal) and builds
-        no preconditioner: a piece of a multi-patch operator."""
+        no preconditioner: a piece of a multi-patch operator. half_stencil=True
+        stores A by its symmetry (about half the bytes)."""
         L = lib()
         dim = len(knots)
         geo_knots = knots if geo_knots is None else geo_knots
@@ -433,7 +435,8 @@ class Patch:
         d.geo_n_knots = (C.c_int * dim)(*[len(k) for k in gk])
         d.geo_knots = (dp * dim)(*[k.ctypes.data_as(dp) for k in gk])
         d.ctrl = ctrl.ctypes.data_as(dp)
-        d.flags = (0 if stencil else SETUP_NO_STENCIL) | (SETUP_FULL_SPACE if full_space else 0)
+        d.flags = ((0 if stencil else SETUP_NO_STENCIL) | (SETUP_FULL_SPACE if full_space else 0) |
+                   (SETUP_HALF_STENCIL if half_stencil else 0))
         if kappa_field is not None:
             kk, kpd, kc = kappa_field
             kk = [np.ascontiguousarray(k, dtype=np.float64) for k in kk]
@@ -452,13 +455,13 @@ class Patch:
         self.N = int(self.info.N)
 
     @classmethod
-    def from_problem(cls, prob, stencil=True):
+    def from_problem(cls, prob, stencil=True, half_stencil=False):
         kf = None
         if getattr(prob, "kappa_ctrl", None) is not None:
             kf = (prob.kappa_knots, prob.kappa_p, prob.kappa_ctrl)
         return cls(prob.knots, prob.p, prob.ctrl, prob.kappa,
                    geo_knots=getattr(prob, "geo_knots", None), geo_p=getattr(prob, "geo_p", None),
-                   kappa_field=kf, stencil=stencil)
+                   kappa_field=kf, stencil=stencil, half_stencil=half_stencil)
 
     def query(self):
         info = PatchInfo()
