@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--groups", type=int, default=0,
                     help="--batch: concurrently looping groups (0: one per problem)")
+    ap.add_argument("--half", action="store_true",
+                    help="--batch: store every problem's stencil by its symmetry")
+    ap.add_argument("--stencil-half", action="store_true",
+                    help="full vs symmetric-half stencil: bytes, product time and PCG solve")
     ap.add_argument("--timeline", action="store_true",
                     help="--batch: add the device-clock pass record of the last timed solve")
     ap.add_argument("--learned", action="store_true",
@@ -793,7 +797,7 @@ def run_batch(args):
             amp = g.uniform(-0.1, 0.1, 3)
             prob = synth.Problem(3, n, p, amp)
             try:
-                patch = igafd.Patch.from_problem(prob)
+                patch = igafd.Patch.from_problem(prob, half_stencil=args.half)
                 break
             except igafd.IgafdError as e:
                 if e.status != igafd.ERR_FOLDED:
@@ -879,6 +883,7 @@ def run_batch(args):
             "value": args.count / batch_s, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": batch_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + dtype, "data": "synthetic",
+            "stencil_half": bool(args.half),
             "config": {"workload": "batched deformed cubes (a_k~U(-0.1,0.1)), N(0,1) RHS; "
                                    "device-driven loops (conditional graphs), one per group of "
                                    "problems, concurrent on their own streams",
@@ -1152,8 +1157,61 @@ def run_cube(args):
     print(json.dumps(line), flush=True)
 
 
+def run_stencil_half(args):
+    """The stencil stored in full and by its symmetry, on the deformed cube at
+    (n, p) = (128, 3) and (192, 5): device bytes of A, the product A x (CUDA
+    events, 20 launches after 3) and a TF32-FD PCG solve to 1e-8 with each;
+    the solutions' relative difference."""
+    import torch
+    import synth
+    from paper_1602_01636_gb300 import igafd, build as libbuild
+    libbuild.build()
+    rows = []
+    for n, p in ((128, 3), (192, 5)):
+        prob = synth.deformed_cube(n, p, seed=0)
+        res = {}
+        for half in (False, True):
+            patch = igafd.Patch.from_problem(prob, half_stencil=half)
+            patch.autotune()
+            b = patch.load_rhs_sine()
+            x = torch.randn(patch.N, dtype=torch.float64, device="cuda")
+            for _ in range(3):
+                patch.apply_A(x)
+            torch.cuda.synchronize()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(20):
+                patch.apply_A(x)
+            c.record()
+            torch.cuda.synchronize()
+            patch.pcg(b, tol=args.tol, dtype="tf32")
+            torch.cuda.synchronize()
+            a2, c2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a2.record()
+            xs, inf = patch.pcg(b, tol=args.tol, dtype="tf32")
+            c2.record()
+            torch.cuda.synchronize()
+            res[half] = {"stencil_GB": patch.info.stencil_bytes / 1e9,
+                         "apply_A_ms": a.elapsed_time(c) / 20, "solve_ms": a2.elapsed_time(c2),
+                         "iterations": inf.iterations, "true_relres": inf.true_relres,
+                         "stencil_rows": patch.info.stencil_rows, "x": xs.cpu().numpy()}
+            patch.close()
+            torch.cuda.empty_cache()
+        d = float(abs(res[True]["x"] - res[False]["x"]).max() / abs(res[False]["x"]).max())
+        for h in (False, True):
+            res[h].pop("x")
+        rows.append({"n": n, "p": p, "full": res[False], "half": res[True],
+                     "solution_max_rel_diff": d})
+    line = {"metric": "A stencil stored in full vs by its symmetry: bytes, product ms, TF32-FD solve ms",
+            "value": None, "unit": "table", "data": "synthetic", "n_gpus": 1, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.stencil_half:
+        run_stencil_half(args)
+        return
     if args.cube:
         run_cube(args)
         return

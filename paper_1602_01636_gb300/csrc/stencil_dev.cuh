@@ -306,19 +306,18 @@ __device__ __forceinline__ void stencil_cta(const StencilArgs &a, long long vb, 
           double xv[2 * NP + 2];
 #pragma unroll
           for (int m = 0; m < NP + 1; ++m) { const double2 v = xb[m]; xv[2 * m] = v.x; xv[2 * m + 1] = v.y; }
+          // two 8-byte loads per run (no branch on the shift, so all of the
+          // group's loads issue together)
+          double c0[W], c1[W];
 #pragma unroll
           for (int j = 0; j < W; ++j) {
-            double c0, c1;
-            if (hs[j] == 0) {
-              const double2 c = *reinterpret_cast<const double2 *>(cf + j * RS);
-              c0 = c.x;
-              c1 = c.y;
-            } else {
-              c0 = cf[j * RS + 1];
-              c1 = cf[j * RS + 2];
-            }
-            acc[0] = fma(c0, xv[j + sh], acc[0]);
-            acc[1] = fma(c1, xv[j + 1 + sh], acc[1]);
+            c0[j] = cf[j * RS + hs[j]];
+            c1[j] = cf[j * RS + hs[j] + 1];
+          }
+#pragma unroll
+          for (int j = 0; j < W; ++j) {
+            acc[0] = fma(c0[j], xv[j + sh], acc[0]);
+            acc[1] = fma(c1[j], xv[j + 1 + sh], acc[1]);
           }
         } else {
           // rows row, row + 1: coefficients cf[j] = (S[o_j][row], S[o_j][row + 1]);
