@@ -113,8 +113,11 @@ typedef struct {
  * offset index (delta_d, ..., delta_1) are kept, ((2p+1)^d + 1) / 2 of the
  * (2p+1)^d, each a row array with zero halos; a coupling with delta < 0 of
  * row i is the stored coupling -delta of row i + off(delta). The bytes of A
- * are about halved; the FMAs per row, and so the time of a product on GB300
- * (bound by the FP64 pipe), are the same. Every call that uses A works on
+ * are about halved; the FMAs per row are the same, so a product stays bound
+ * by GB300's FP64 pipe and is not shorter (measured 9-15 % longer: the
+ * mirrored runs are fetched shifted by one row when their start is odd).
+ * It is the format for problems whose full stencil would not fit. Every
+ * call that uses A works on
  * such a patch (igafd_copy_stencil expands it to the full layout); the
  * stencil pipeline runs with its default ring depth (the autotuner tunes
  * the rows per thread only). A product differs from the full stencil's at
@@ -204,7 +207,9 @@ igafd_status igafd_get_eigen(const igafd_patch *patch, int k, double *U_host,
 
 /* Copy the stencil of A to device memory dst_dev[o * N + row], with
  * o = sum_k (delta_k + p) (2p+1)^(k-1): entry A[row, row + delta]; entries
- * whose column leaves the index box are 0 (Section 2.1, sparsity of A). */
+ * whose column leaves the index box are 0 (Section 2.1, sparsity of A). A
+ * half-stored stencil (IGAFD_SETUP_HALF_STENCIL) is written out in this
+ * layout, its lower offsets as the stored mirrored couplings. */
 igafd_status igafd_copy_stencil(const igafd_patch *patch, double *dst_dev,
                                 void *stream);
 
@@ -437,7 +442,8 @@ igafd_status igafd_lanczos_extremes(const double *alpha, const double *beta, int
 igafd_status igafd_autotune(igafd_patch *patch, int flags, void *stream);
 
 /* Set the stencil pipeline's ring depth by hand (3, 4 or 6; else
- * IGAFD_ERR_ARG). Every depth computes bitwise the same products. */
+ * IGAFD_ERR_ARG). Every depth computes bitwise the same products. A
+ * half-stored stencil runs at the default depth whatever is set. */
 igafd_status igafd_set_stencil_stages(igafd_patch *patch, int stages);
 
 /* Set the stencil's rows per compute thread by hand: 1, or 2 (3D only; else
