@@ -105,3 +105,42 @@ def test_oracle_leg_reports_solution_differences():
     assert vs["tf32"]["vs_converged"]["max_rel"] > 0.0
     assert vs["oracle_iterations_at_tol"] == res.iters
     assert np.isfinite(vs["fp64"]["vs_converged"]["l2_rel"])
+
+
+def test_batch_timeline_summary():
+    """bench.batch_timeline: per group its members' iterations, passes, first
+    start and last end; passes and their summed time by the unfinished
+    members at each pass's start; groups listed latest end first."""
+    import numpy as np
+    import bench
+
+    class FakeBatch:
+        def groups(self):
+            return 2, [0, 1, 0]
+
+        def pass_log(self, g):
+            if g == 0:
+                return {"start_us": np.array([0.0, 100.0, 250.0]),
+                        "dur_us": np.array([100.0, 150.0, 50.0]), "active": np.array([2, 2, 1])}
+            return {"start_us": np.array([10.0]), "dur_us": np.array([500.0]),
+                    "active": np.array([1])}
+
+    infos = [types.SimpleNamespace(iterations=i) for i in (3, 1, 2)]
+    t = bench.batch_timeline(FakeBatch(), infos)
+    assert t["groups"] == 2
+    first, second = t["latest_groups"]
+    assert first["group"] == 1 and first["end_ms"] == 0.51 and first["iterations"] == [1]
+    assert second["group"] == 0 and second["iterations"] == [3, 2] and second["passes"] == 3
+    assert second["end_ms"] == 0.3 and second["start_ms"] == 0.0
+    assert t["latest_start_ms"] == 0.01
+    assert t["passes_by_unfinished_members"]["1"] == {"passes": 2, "ms": 0.55}
+    assert t["passes_by_unfinished_members"]["2-4"] == {"passes": 2, "ms": 0.25}
+
+
+def test_stencil_dram_summary_is_current():
+    """The committed DRAM summary of the stencil kernel was taken on the
+    current kernel sources, so the bench reports its traffic (1.072 x the
+    compulsory bytes at n = 128, p = 3) instead of null."""
+    import bench
+    assert bench.stencil_traffic(3, 128) == 5.96e9
+    assert bench.stencil_traffic(3, 96) is None        # no summary for that size
